@@ -1,0 +1,675 @@
+/*
+ * navix_oracle.c -- plain CPU oracle of the batched MiniGrid step of NAVIX
+ * (arXiv 2407.19396).  TEST INFRASTRUCTURE ONLY: see navix_oracle.h.
+ *
+ * Everything here is written as the literal sequence of steps, one env at a
+ * time, with no blocking, fusion or bit tricks, so that a reader can check it
+ * against the paper's systems (Table 3, Appendix A) and the readings stated
+ * beside each function.
+ */
+#include "navix_oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Randomness (reading R1).  The paper draws its randomness from JAX keys
+ * (reset(key), Section 3.2.2; key splitting, Code 1 and Code 3).  Here every
+ * draw is a counter-based Philox4x32-10 value: key = (seed lo, seed hi),
+ * counter = (env index, episode, step, purpose << 24 | draw), word 0.
+ * Philox4x32-10 as defined by Salmon et al., "Parallel Random Numbers: As
+ * Easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 multiplications by
+ * 0xD2511F53 and 0xCD9E8D57, with the key bumped by the Weyl constants
+ * 0x9E3779B9 / 0xBB67AE85 between rounds. */
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    uint32_t n3 = lo0;
+    c[0] = n0;
+    c[1] = n1;
+    c[2] = n2;
+    c[3] = n3;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k[0] += 0x9E3779B9u;
+            k[1] += 0xBB67AE85u;
+        }
+        philox_round(c, k);
+    }
+    out[0] = c[0];
+    out[1] = c[1];
+    out[2] = c[2];
+    out[3] = c[3];
+}
+
+/* Bounded draw in [0, n): multiply-shift (Lemire), no rejection (R1). */
+uint32_t orc_bounded(uint32_t x, uint32_t n) { return (uint32_t)(((uint64_t)x * (uint64_t)n) >> 32); }
+
+uint32_t orc_draw(uint64_t seed, uint32_t env_index, uint32_t episode, uint32_t step, uint32_t purpose, uint32_t draw)
+{
+    uint32_t ctr[4] = {env_index, episode, step, (purpose << 24) | draw};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+enum { PURPOSE_LAYOUT = 1, PURPOSE_BALL = 2, PURPOSE_ACTION = 3 };
+
+/* ------------------------------------------------------------------------ */
+/* Cells (reading R5): the grid stores (entity, colour, state) per cell. */
+static int idx(const orc_env* e, int x, int y) { return y * e->width + x; }
+
+static int in_grid(const orc_env* e, int x, int y) { return x >= 0 && y >= 0 && x < e->width && y < e->height; }
+
+void orc_set_cell(orc_env* e, int32_t x, int32_t y, int32_t ent, int32_t col, int32_t st)
+{
+    int i = idx(e, x, y);
+    e->ent[i] = (uint8_t)ent;
+    e->col[i] = (uint8_t)col;
+    e->st[i] = (uint8_t)st;
+}
+
+static void set_empty(orc_env* e, int x, int y) { orc_set_cell(e, x, y, ORC_EMPTYCELL, 0, 0); }
+
+/* Reads a cell; cells outside the grid read as a grey wall (reading R4). */
+static void get_cell(const orc_env* e, int x, int y, int* ent, int* col, int* st)
+{
+    if (!in_grid(e, x, y)) {
+        *ent = ORC_WALL;
+        *col = ORC_GREY;
+        *st = 0;
+        return;
+    }
+    int i = idx(e, x, y);
+    *ent = e->ent[i];
+    *col = e->col[i];
+    *st = e->st[i];
+}
+
+static int is_empty_cell(const orc_env* e, int x, int y)
+{
+    if (!in_grid(e, x, y)) return 0;
+    int i = idx(e, x, y);
+    return e->ent[i] == ORC_EMPTYCELL && e->col[i] == 0 && e->st[i] == 0;
+}
+
+/* Walkable: empty, floor, goal, lava, or an open door (R5). */
+static int walkable(int ent, int st)
+{
+    if (ent == ORC_EMPTYCELL || ent == ORC_FLOOR || ent == ORC_GOAL || ent == ORC_LAVA) return 1;
+    if (ent == ORC_DOOR && st == ORC_OPEN) return 1;
+    return 0;
+}
+
+/* Transparent: everything but walls and doors that are not open (R5). */
+static int transparent(int ent, int st)
+{
+    if (ent == ORC_WALL) return 0;
+    if (ent == ORC_DOOR && st != ORC_OPEN) return 0;
+    return 1;
+}
+
+/* Directions: 0 = east (+x), 1 = south (+y), 2 = west, 3 = north. */
+static const int DX[4] = {1, 0, -1, 0};
+static const int DY[4] = {0, 1, 0, -1};
+
+void orc_set_agent(orc_env* e, int32_t x, int32_t y, int32_t dir, int32_t carry_ent, int32_t carry_col)
+{
+    e->ax = x;
+    e->ay = y;
+    e->dir = dir;
+    e->carry_ent = carry_ent;
+    e->carry_col = carry_col;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Layouts (Table 8 environment families; concrete generators L1-L5). */
+
+int32_t orc_default_max_steps(int32_t family, int32_t size)
+{
+    /* reading R17: Empty 4S^2 (100 at S = 5), DoorKey 10S^2 (640 at S = 8),
+     * FourRooms 100, LavaGap 4S^2, Dynamic-Obstacles 4S^2 */
+    switch (family) {
+    case ORC_DOORKEY: return 10 * size * size;
+    case ORC_FOURROOMS: return 100;
+    default: return 4 * size * size;
+    }
+}
+
+static void clear_grid(orc_env* e)
+{
+    for (int y = 0; y < e->height; y++)
+        for (int x = 0; x < e->width; x++) set_empty(e, x, y);
+}
+
+static void border_walls(orc_env* e)
+{
+    for (int x = 0; x < e->width; x++) {
+        orc_set_cell(e, x, 0, ORC_WALL, ORC_GREY, 0);
+        orc_set_cell(e, x, e->height - 1, ORC_WALL, ORC_GREY, 0);
+    }
+    for (int y = 0; y < e->height; y++) {
+        orc_set_cell(e, 0, y, ORC_WALL, ORC_GREY, 0);
+        orc_set_cell(e, e->width - 1, y, ORC_WALL, ORC_GREY, 0);
+    }
+}
+
+/* Counts the empty cells of the rectangle [x0,x1]x[y0,y1], not counting the
+ * cell (skip_x, skip_y) (pass -1 to skip nothing). */
+static int count_free(const orc_env* e, int x0, int x1, int y0, int y1, int skip_x, int skip_y)
+{
+    int n = 0;
+    for (int y = y0; y <= y1; y++)
+        for (int x = x0; x <= x1; x++)
+            if (is_empty_cell(e, x, y) && !(x == skip_x && y == skip_y)) n++;
+    return n;
+}
+
+/* The k-th empty cell of the rectangle in row-major order, y outer and x
+ * inner (reading R18), not counting (skip_x, skip_y). */
+static void kth_free(const orc_env* e, int k, int x0, int x1, int y0, int y1, int skip_x, int skip_y, int* ox,
+                     int* oy)
+{
+    int n = 0;
+    for (int y = y0; y <= y1; y++)
+        for (int x = x0; x <= x1; x++) {
+            if (!is_empty_cell(e, x, y) || (x == skip_x && y == skip_y)) continue;
+            if (n == k) {
+                *ox = x;
+                *oy = y;
+                return;
+            }
+            n++;
+        }
+    /* unreachable for valid k: the callers draw k in [0, count) */
+    *ox = -1;
+    *oy = -1;
+}
+
+static uint32_t layout_draw(const orc_env* e, uint32_t k)
+{
+    return orc_draw(e->seed, e->env_index, e->episode, 0, PURPOSE_LAYOUT, k);
+}
+
+/* L1 Empty-S: border walls, agent at (1,1) facing east, goal at (S-2,S-2). */
+static void layout_empty(orc_env* e)
+{
+    orc_set_cell(e, e->width - 2, e->height - 2, ORC_GOAL, ORC_GREEN, 0);
+    orc_set_agent(e, 1, 1, 0, 0, 0);
+}
+
+/* L2 DoorKey-S: a wall column at x_w in 2..W-3 with a locked yellow door at a
+ * row in 1..H-3; agent and yellow key on free cells left of the wall; goal
+ * at (W-2,H-2). */
+static void layout_doorkey(orc_env* e)
+{
+    int W = e->width, H = e->height;
+    orc_set_cell(e, W - 2, H - 2, ORC_GOAL, ORC_GREEN, 0);
+    int xw = 2 + (int)orc_bounded(layout_draw(e, 0), (uint32_t)(W - 4));
+    for (int y = 1; y <= H - 2; y++) orc_set_cell(e, xw, y, ORC_WALL, ORC_GREY, 0);
+    int door_y = 1 + (int)orc_bounded(layout_draw(e, 1), (uint32_t)(H - 3));
+    orc_set_cell(e, xw, door_y, ORC_DOOR, ORC_YELLOW, ORC_LOCKED);
+    int n = count_free(e, 1, xw - 1, 1, H - 2, -1, -1);
+    int ax, ay;
+    kth_free(e, (int)orc_bounded(layout_draw(e, 2), (uint32_t)n), 1, xw - 1, 1, H - 2, -1, -1, &ax, &ay);
+    int dir = (int)orc_bounded(layout_draw(e, 3), 4u);
+    orc_set_agent(e, ax, ay, dir, 0, 0);
+    int kx, ky;
+    kth_free(e, (int)orc_bounded(layout_draw(e, 4), (uint32_t)(n - 1)), 1, xw - 1, 1, H - 2, ax, ay, &kx, &ky);
+    orc_set_cell(e, kx, ky, ORC_KEY, ORC_YELLOW, 0);
+}
+
+/* L3 FourRooms-S: walls on x = m and y = m (m = S/2), one gap per half wall,
+ * goal and agent on random free cells, random direction. */
+static void layout_fourrooms(orc_env* e)
+{
+    int S = e->width, m = S / 2;
+    for (int i = 0; i < S; i++) {
+        orc_set_cell(e, m, i, ORC_WALL, ORC_GREY, 0);
+        orc_set_cell(e, i, m, ORC_WALL, ORC_GREY, 0);
+    }
+    set_empty(e, m, 1 + (int)orc_bounded(layout_draw(e, 0), (uint32_t)(m - 1)));
+    set_empty(e, m, m + 1 + (int)orc_bounded(layout_draw(e, 1), (uint32_t)(S - 2 - m)));
+    set_empty(e, 1 + (int)orc_bounded(layout_draw(e, 2), (uint32_t)(m - 1)), m);
+    set_empty(e, m + 1 + (int)orc_bounded(layout_draw(e, 3), (uint32_t)(S - 2 - m)), m);
+    int n = count_free(e, 1, S - 2, 1, S - 2, -1, -1);
+    int gx, gy;
+    kth_free(e, (int)orc_bounded(layout_draw(e, 4), (uint32_t)n), 1, S - 2, 1, S - 2, -1, -1, &gx, &gy);
+    orc_set_cell(e, gx, gy, ORC_GOAL, ORC_GREEN, 0);
+    int ax, ay;
+    kth_free(e, (int)orc_bounded(layout_draw(e, 5), (uint32_t)(n - 1)), 1, S - 2, 1, S - 2, -1, -1, &ax, &ay);
+    int dir = (int)orc_bounded(layout_draw(e, 6), 4u);
+    orc_set_agent(e, ax, ay, dir, 0, 0);
+}
+
+/* L4 LavaGap-S: agent (1,1) east, goal (S-2,S-2), a lava column at x_l in
+ * 2..S-3 with one gap at a row in 1..S-2. */
+static void layout_lavagap(orc_env* e)
+{
+    int S = e->width;
+    orc_set_cell(e, S - 2, S - 2, ORC_GOAL, ORC_GREEN, 0);
+    orc_set_agent(e, 1, 1, 0, 0, 0);
+    int xl = 2 + (int)orc_bounded(layout_draw(e, 0), (uint32_t)(S - 4));
+    int gap = 1 + (int)orc_bounded(layout_draw(e, 1), (uint32_t)(S - 2));
+    for (int y = 1; y <= S - 2; y++)
+        if (y != gap) orc_set_cell(e, xl, y, ORC_LAVA, 0, 0);
+}
+
+/* L5 Dynamic-Obstacles-S: agent (1,1) east, goal (S-2,S-2), n blue balls on
+ * free interior cells (never the agent's cell), placed in index order. */
+static void layout_dynobs(orc_env* e)
+{
+    int S = e->width;
+    orc_set_cell(e, S - 2, S - 2, ORC_GOAL, ORC_GREEN, 0);
+    orc_set_agent(e, 1, 1, 0, 0, 0);
+    for (int b = 0; b < e->n_balls; b++) {
+        int n = count_free(e, 1, S - 2, 1, S - 2, e->ax, e->ay);
+        int bx, by;
+        kth_free(e, (int)orc_bounded(layout_draw(e, (uint32_t)b), (uint32_t)n), 1, S - 2, 1, S - 2, e->ax, e->ay,
+                 &bx, &by);
+        orc_set_cell(e, bx, by, ORC_BALL, ORC_BLUE, 0);
+        e->ball_x[b] = bx;
+        e->ball_y[b] = by;
+    }
+}
+
+/* reset(key) of Section 3.2.2: sample a start state for the given episode. */
+void orc_reset(orc_env* e, uint32_t episode)
+{
+    e->episode = episode;
+    e->t = 0;
+    e->done = 0;
+    e->carry_ent = 0;
+    e->carry_col = 0;
+    for (int b = 0; b < ORC_MAX_BALLS; b++) {
+        e->ball_x[b] = 0;
+        e->ball_y[b] = 0;
+    }
+    memset(e->ent, 0, sizeof e->ent);
+    memset(e->col, 0, sizeof e->col);
+    memset(e->st, 0, sizeof e->st);
+    clear_grid(e);
+    border_walls(e);
+    switch (e->family) {
+    case ORC_EMPTY: layout_empty(e); break;
+    case ORC_DOORKEY: layout_doorkey(e); break;
+    case ORC_FOURROOMS: layout_fourrooms(e); break;
+    case ORC_LAVAGAP: layout_lavagap(e); break;
+    case ORC_DYNOBS: layout_dynobs(e); break;
+    default: break;
+    }
+}
+
+int32_t orc_env_init(orc_env* e, int32_t family, int32_t size, int32_t max_steps, int32_t n_balls, uint64_t seed,
+                     uint32_t env_index, int32_t reward_mode, float lava_reward)
+{
+    if (family < ORC_EMPTY || family > ORC_DYNOBS) return -1;
+    if (size < ORC_MIN_SIZE || size > ORC_MAX_SIZE) return -1;
+    if (n_balls < 0 || n_balls > ORC_MAX_BALLS) return -1;
+    memset(e, 0, sizeof *e);
+    e->family = family;
+    e->height = size;
+    e->width = size;
+    e->max_steps = max_steps > 0 ? max_steps : orc_default_max_steps(family, size);
+    e->n_balls = family == ORC_DYNOBS ? n_balls : 0;
+    e->reward_mode = reward_mode;
+    e->lava_reward = lava_reward;
+    e->seed = seed;
+    e->env_index = env_index;
+    orc_reset(e, 0);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Random actions (R1 purpose 3, R13): uniform over the 7 actions, or over
+ * left/right/forward in Dynamic-Obstacles. */
+int32_t orc_random_action(const orc_env* e, uint32_t gstep)
+{
+    uint32_t n_act = e->family == ORC_DYNOBS ? 3u : 7u;
+    return (int32_t)orc_bounded(orc_draw(e->seed, e->env_index, 0xFFFFFFFFu, gstep, PURPOSE_ACTION, 0), n_act);
+}
+
+/* Transition system (Table 3, Appendix A) for Dynamic-Obstacles (R12): each
+ * ball, in index order, moves to a uniformly drawn empty cell of its
+ * 8-neighbourhood (never the agent's cell), else stays. */
+static void move_balls(orc_env* e)
+{
+    for (int b = 0; b < e->n_balls; b++) {
+        int bx = e->ball_x[b], by = e->ball_y[b];
+        int cand_x[8], cand_y[8], count = 0;
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                if (dx == 0 && dy == 0) continue;
+                int x = bx + dx, y = by + dy;
+                if (!is_empty_cell(e, x, y)) continue;
+                if (x == e->ax && y == e->ay) continue;
+                cand_x[count] = x;
+                cand_y[count] = y;
+                count++;
+            }
+        if (count == 0) continue;
+        uint32_t d = orc_draw(e->seed, e->env_index, e->episode, (uint32_t)e->t, PURPOSE_BALL, (uint32_t)b);
+        int k = (int)orc_bounded(d, (uint32_t)count);
+        set_empty(e, bx, by);
+        orc_set_cell(e, cand_x[k], cand_y[k], ORC_BALL, ORC_BLUE, 0);
+        e->ball_x[b] = cand_x[k];
+        e->ball_y[b] = cand_y[k];
+    }
+}
+
+/* Eq. 1 (Section 3.2.1) read as MiniGrid's success reward 1 - 0.9 t / T, with
+ * t already counting this step; IEEE single operations in a fixed order:
+ * multiply, divide, subtract (reading R15). */
+static float minigrid_goal_reward(int t, int T)
+{
+    volatile float num = 0.9f * (float)t;
+    volatile float q = num / (float)T;
+    volatile float r = 1.0f - q;
+    return r;
+}
+
+/* One env step in the order of reading R2 / the step-order list:
+ * autoreset, transition, intervention, reward/termination, time, truncation.
+ * The observation is produced separately from the resulting state. */
+void orc_step(orc_env* e, int32_t action, float* reward, uint8_t* terminated, uint8_t* truncated)
+{
+    /* 1. autoreset (Section 3.2.2, Code 1): the call after a terminal or
+     *    truncated step returns the new episode's start with reward padding 0
+     *    and ignores its action. */
+    if (e->done) {
+        orc_reset(e, e->episode + 1);
+        *reward = 0.0f;
+        *terminated = 0;
+        *truncated = 0;
+        return;
+    }
+    /* 2. transition system */
+    if (e->family == ORC_DYNOBS) move_balls(e);
+
+    /* 3. intervention system (Table 3, Appendix A, readings R7-R11, R13) */
+    int goal = 0, lava = 0, hit = 0;
+    int n_act = e->family == ORC_DYNOBS ? 3 : 7;
+    if (action < 0 || action > ORC_DONE) {
+        e->invalid_action = 1; /* executed as a no-op */
+    } else if (action < n_act) {
+        int fx = e->ax + DX[e->dir], fy = e->ay + DY[e->dir];
+        int fent, fcol, fst;
+        get_cell(e, fx, fy, &fent, &fcol, &fst);
+        if (action == ORC_LEFT) {
+            e->dir = (e->dir + 3) % 4;
+        } else if (action == ORC_RIGHT) {
+            e->dir = (e->dir + 1) % 4;
+        } else if (action == ORC_FORWARD) {
+            if (e->family == ORC_DYNOBS && fent == ORC_BALL) {
+                hit = 1; /* hit by an obstacle: the agent does not move */
+            } else if (walkable(fent, fst)) {
+                e->ax = fx;
+                e->ay = fy;
+                if (fent == ORC_GOAL) goal = 1;
+                if (fent == ORC_LAVA) lava = 1;
+            }
+        } else if (action == ORC_PICKUP) {
+            if (e->carry_ent == 0 && (fent == ORC_KEY || fent == ORC_BALL)) {
+                e->carry_ent = fent;
+                e->carry_col = fcol;
+                set_empty(e, fx, fy);
+            }
+        } else if (action == ORC_DROP) {
+            if (e->carry_ent != 0 && is_empty_cell(e, fx, fy)) {
+                orc_set_cell(e, fx, fy, e->carry_ent, e->carry_col, 0);
+                e->carry_ent = 0;
+                e->carry_col = 0;
+            }
+        } else if (action == ORC_TOGGLE) {
+            if (fent == ORC_DOOR) {
+                if (fst == ORC_LOCKED) {
+                    if (e->carry_ent == ORC_KEY && e->carry_col == fcol) orc_set_cell(e, fx, fy, ORC_DOOR, fcol, ORC_OPEN);
+                } else if (fst == ORC_CLOSED) {
+                    orc_set_cell(e, fx, fy, ORC_DOOR, fcol, ORC_OPEN);
+                } else {
+                    orc_set_cell(e, fx, fy, ORC_DOOR, fcol, ORC_CLOSED);
+                }
+            }
+        }
+        /* ORC_DONE: no effect */
+    }
+
+    /* 4. time and truncation (R17) */
+    e->t += 1;
+    int trunc = e->t >= e->max_steps;
+
+    /* 5. reward (Table 5, Table 8 R1/R2/R3; R14, R15) and termination
+     *    (Table 6: terminate when the reward event fires) */
+    float r = 0.0f;
+    int term = 0;
+    if (goal) {
+        r = e->reward_mode == ORC_REWARD_MINIGRID ? minigrid_goal_reward(e->t, e->max_steps) : 1.0f;
+        term = 1;
+    } else if (lava) {
+        r = e->lava_reward;
+        term = 1;
+    } else if (hit) {
+        r = -1.0f;
+        term = 1;
+    }
+    *reward = r;
+    *terminated = (uint8_t)term;
+    *truncated = (uint8_t)trunc;
+    e->done = term || trunc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* symbolic_first_person (Table 4): a 7x7x3 egocentric view.
+ * View geometry (R3, R4): output cell (vx, vy), agent at (3, 6) looking
+ * toward vy = 0, right hand toward +vx; world = pos + (6 - vy) F + (vx - 3) Rt
+ * with F the facing direction and Rt the direction to its right.
+ * Visibility (R6): rows are processed from the agent's row outward; a visible
+ * transparent cell lights its side neighbour and the two cells ahead. */
+static void view_cells(const orc_env* e, int vent[7][7], int vcol[7][7], int vst[7][7])
+{
+    int F = e->dir, Rt = (e->dir + 1) % 4;
+    for (int vy = 0; vy < 7; vy++)
+        for (int vx = 0; vx < 7; vx++) {
+            int x = e->ax + (6 - vy) * DX[F] + (vx - 3) * DX[Rt];
+            int y = e->ay + (6 - vy) * DY[F] + (vx - 3) * DY[Rt];
+            if (vx == 3 && vy == 6) {
+                /* the agent's own cell shows what it carries, else empty */
+                if (e->carry_ent != 0) {
+                    vent[vy][vx] = e->carry_ent;
+                    vcol[vy][vx] = e->carry_col;
+                } else {
+                    vent[vy][vx] = ORC_EMPTYCELL;
+                    vcol[vy][vx] = 0;
+                }
+                vst[vy][vx] = 0;
+            } else {
+                get_cell(e, x, y, &vent[vy][vx], &vcol[vy][vx], &vst[vy][vx]);
+            }
+        }
+}
+
+static void visibility(int vent[7][7], int vst[7][7], int vis[7][7])
+{
+    memset(vis, 0, sizeof(int) * 49);
+    vis[6][3] = 1;
+    for (int j = 6; j >= 0; j--) {
+        for (int i = 0; i <= 5; i++) {
+            if (!vis[j][i]) continue;
+            if (!transparent(vent[j][i], vst[j][i])) continue;
+            vis[j][i + 1] = 1;
+            if (j > 0) {
+                vis[j - 1][i + 1] = 1;
+                vis[j - 1][i] = 1;
+            }
+        }
+        for (int i = 6; i >= 1; i--) {
+            if (!vis[j][i]) continue;
+            if (!transparent(vent[j][i], vst[j][i])) continue;
+            vis[j][i - 1] = 1;
+            if (j > 0) {
+                vis[j - 1][i - 1] = 1;
+                vis[j - 1][i] = 1;
+            }
+        }
+    }
+}
+
+void orc_obs_sym(const orc_env* e, uint8_t obs[ORC_OBS_BYTES])
+{
+    int vent[7][7], vcol[7][7], vst[7][7], vis[7][7];
+    view_cells(e, vent, vcol, vst);
+    visibility(vent, vst, vis);
+    for (int vy = 0; vy < 7; vy++)
+        for (int vx = 0; vx < 7; vx++) {
+            uint8_t* o = obs + (vy * 7 + vx) * 3;
+            if (vis[vy][vx]) {
+                o[0] = (uint8_t)vent[vy][vx];
+                o[1] = (uint8_t)vcol[vy][vx];
+                o[2] = (uint8_t)vst[vy][vx];
+            } else {
+                o[0] = 0;
+                o[1] = 0;
+                o[2] = 0;
+            }
+        }
+}
+
+/* rgb_first_person (Table 4; Sprite component of Table 1): each view cell
+ * becomes a 32x32x3 sprite.  Sprite atlas convention (the atlas is an input,
+ * 397 tiles of 32x32x3 bytes): tile 0 = unseen; a visible cell (e, c, s) uses
+ * tile 1 + 18 e + 3 c + s; the agent's own cell uses the same index + 198
+ * (the agent drawn over what it carries). */
+int32_t orc_tile_index(int32_t visible, int32_t agent_cell, int32_t ent, int32_t col, int32_t st)
+{
+    if (!visible) return 0;
+    int32_t t = 1 + ent * 18 + col * 3 + st;
+    if (agent_cell) t += 198;
+    return t;
+}
+
+void orc_obs_rgb(const orc_env* e, const uint8_t* atlas, uint8_t* img)
+{
+    uint8_t obs[ORC_OBS_BYTES];
+    orc_obs_sym(e, obs);
+    const int row_bytes = 7 * ORC_TILE * 3;
+    for (int vy = 0; vy < 7; vy++)
+        for (int vx = 0; vx < 7; vx++) {
+            const uint8_t* o = obs + (vy * 7 + vx) * 3;
+            int visible = !(o[0] == 0 && o[1] == 0 && o[2] == 0);
+            int agent_cell = (vx == 3 && vy == 6);
+            int tile = orc_tile_index(visible, agent_cell, o[0], o[1], o[2]);
+            const uint8_t* src = atlas + (size_t)tile * ORC_TILE_BYTES;
+            for (int ty = 0; ty < ORC_TILE; ty++)
+                for (int tx = 0; tx < ORC_TILE; tx++)
+                    for (int c = 0; c < 3; c++)
+                        img[(size_t)(vy * ORC_TILE + ty) * row_bytes + (size_t)(vx * ORC_TILE + tx) * 3 + c] =
+                            src[(ty * ORC_TILE + tx) * 3 + c];
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Batch convenience (vmap over environments, Code 3), stepped sequentially. */
+struct orc_batch {
+    int32_t n;
+    uint32_t gstep; /* calls to step since the batch was reset */
+    orc_env* envs;
+};
+
+orc_batch* orc_batch_create(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
+                            int32_t n_balls, uint64_t seed, uint32_t env_index_base, int32_t reward_mode,
+                            float lava_reward)
+{
+    if (n < 0) return NULL;
+    orc_batch* b = (orc_batch*)calloc(1, sizeof *b);
+    if (!b) return NULL;
+    b->n = n;
+    b->envs = (orc_env*)calloc(n > 0 ? (size_t)n : 1u, sizeof(orc_env));
+    if (!b->envs) {
+        free(b);
+        return NULL;
+    }
+    for (int32_t i = 0; i < n; i++) {
+        if (orc_env_init(&b->envs[i], family[i], size[i], max_steps ? max_steps[i] : 0, n_balls, seed,
+                         env_index_base + (uint32_t)i, reward_mode, lava_reward) != 0) {
+            free(b->envs);
+            free(b);
+            return NULL;
+        }
+    }
+    return b;
+}
+
+void orc_batch_destroy(orc_batch* b)
+{
+    if (!b) return;
+    free(b->envs);
+    free(b);
+}
+
+orc_env* orc_batch_env(orc_batch* b, int32_t i) { return (i >= 0 && i < b->n) ? &b->envs[i] : NULL; }
+
+uint32_t orc_batch_gstep(const orc_batch* b) { return b->gstep; }
+
+static void emit(orc_env* e, int32_t i, uint8_t* obs_sym, uint8_t* obs_rgb, const uint8_t* atlas)
+{
+    if (obs_sym) orc_obs_sym(e, obs_sym + (size_t)i * ORC_OBS_BYTES);
+    if (obs_rgb && atlas) orc_obs_rgb(e, atlas, obs_rgb + (size_t)i * ORC_RGB_BYTES);
+}
+
+void orc_batch_reset(orc_batch* b, uint8_t* obs_sym, uint8_t* obs_rgb, const uint8_t* atlas, float* reward,
+                     uint8_t* terminated, uint8_t* truncated)
+{
+    b->gstep = 0;
+    for (int32_t i = 0; i < b->n; i++) {
+        orc_env* e = &b->envs[i];
+        e->invalid_action = 0;
+        orc_reset(e, 0);
+        emit(e, i, obs_sym, obs_rgb, atlas);
+        if (reward) reward[i] = 0.0f;
+        if (terminated) terminated[i] = 0;
+        if (truncated) truncated[i] = 0;
+    }
+}
+
+void orc_batch_step(orc_batch* b, const int8_t* actions, uint8_t* obs_sym, uint8_t* obs_rgb, const uint8_t* atlas,
+                    float* reward, uint8_t* terminated, uint8_t* truncated)
+{
+    for (int32_t i = 0; i < b->n; i++) {
+        orc_env* e = &b->envs[i];
+        int32_t a = actions ? (int32_t)actions[i] : orc_random_action(e, b->gstep);
+        float r;
+        uint8_t te, tr;
+        orc_step(e, a, &r, &te, &tr);
+        emit(e, i, obs_sym, obs_rgb, atlas);
+        if (reward) reward[i] = r;
+        if (terminated) terminated[i] = te;
+        if (truncated) truncated[i] = tr;
+    }
+    b->gstep += 1;
+}
+
+void orc_batch_rollout(orc_batch* b, int32_t T, const int8_t* actions_TN, uint8_t* obs_sym, uint8_t* obs_rgb,
+                       const uint8_t* atlas, float* reward, uint8_t* terminated, uint8_t* truncated)
+{
+    size_t n = (size_t)b->n;
+    for (int32_t t = 0; t < T; t++) {
+        orc_batch_step(b, actions_TN ? actions_TN + (size_t)t * n : NULL,
+                       obs_sym ? obs_sym + (size_t)t * n * ORC_OBS_BYTES : NULL,
+                       obs_rgb ? obs_rgb + (size_t)t * n * ORC_RGB_BYTES : NULL, atlas,
+                       reward ? reward + (size_t)t * n : NULL, terminated ? terminated + (size_t)t * n : NULL,
+                       truncated ? truncated + (size_t)t * n : NULL);
+    }
+}

@@ -1,0 +1,282 @@
+"""Brute-force pins of the oracle on tiny inputs, invariants and layout sweeps (CPU).
+
+* every agent pose (position x direction x carried object) of small layouts:
+  the oracle's symbolic_first_person view (Table 4) equals the independent
+  window-and-rotate model of ``indep_model``;
+* BFS-optimal plans found on the independent rule model, replayed through the
+  oracle, reach the goal with reward exactly 1.0 at exactly the plan length
+  (R1 of Table 8), and the oracle's own state graph has no shorter route;
+* long random rollouts of every family keep the invariants of the entity
+  rules (Tables 1-2: one agent, never inside a wall or closed door, keys and
+  balls conserved, doors only unlock with a matching key);
+* layout generators (Table 8 families) are valid for every size and cover
+  their random choices.
+"""
+import ctypes
+from collections import deque
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import indep_model as M
+
+
+def _clone(env: O.Env) -> O.Env:
+    c = O.Env.__new__(O.Env)
+    c.s = O.OrcEnv.from_buffer_copy(bytes(env.s))
+    return c
+
+
+def _carry(env):
+    return None if env.s.carry_ent == 0 else (env.s.carry_ent, env.s.carry_col)
+
+
+@pytest.mark.parametrize("family,size,seed", [(O.EMPTY, 5, 0), (O.DOORKEY, 5, 1), (O.DOORKEY, 6, 2),
+                                              (O.FOURROOMS, 7, 3), (O.LAVAGAP, 6, 4), (O.DYNOBS, 6, 5),
+                                              (O.FOURROOMS, 11, 6), (O.DOORKEY, 8, 7)])
+def test_view_matches_independent_window_model(family, size, seed):
+    base = O.Env(family, size, seed=seed)
+    ent, col, st = base.grid()
+    # open the door in half of the poses to exercise see-through doors too
+    doors = np.argwhere(ent == 4)
+    n = 0
+    for variant in range(2):
+        env = _clone(base)
+        if variant == 1:
+            for (y, x) in doors:
+                env.set_cell(int(x), int(y), 4, int(col[y, x]), 0)
+        e2, c2, s2 = env.grid()
+        for y in range(size):
+            for x in range(size):
+                for d in range(4):
+                    for carry in (None, (5, 4), (6, 2)):
+                        env.set_agent(x, y, d, *(carry or (0, 0)))
+                        want = M.observe(e2, c2, s2, x, y, d, carry)
+                        np.testing.assert_array_equal(env.obs(), want, err_msg=f"pose {(x, y, d, carry)}")
+                        n += 1
+    assert n > 0
+
+
+def test_view_all_transparent_sees_everything():
+    # special case: no opaque cell in view -> all 49 cells visible
+    env = O.Env(O.EMPTY, 19)
+    env.set_agent(9, 12, 3)
+    o = env.obs()
+    assert (o[:, :, 0] != 0).all()
+
+
+def test_view_facing_wall_point_blank():
+    # a wall row straight ahead at distance 1 and walls all along the agent row:
+    # only the agent row's reachable part and the row ahead are lit
+    env = O.Env(O.EMPTY, 5)
+    env.set_agent(1, 1, 3)  # face north: the border wall is ahead
+    o = env.obs()
+    assert (o[:5, :, 0] == 0).all()
+    assert tuple(o[5, 3]) == (2, 5, 0)
+
+
+def _state_key(env):
+    e, c, s = env.grid()
+    return (env.s.ax, env.s.ay, env.s.dir, env.s.carry_ent, env.s.carry_col, e.tobytes(), c.tobytes(), s.tobytes())
+
+
+def _oracle_bfs_len(env, max_depth=40):
+    """Length of the shortest goal-reaching action sequence in the oracle's own state graph."""
+    start = _clone(env)
+    seen = {_state_key(start)}
+    q = deque([(start, 0)])
+    while q:
+        s, depth = q.popleft()
+        if depth >= max_depth:
+            continue
+        for a in range(6):
+            n = _clone(s)
+            r, te, tr = n.step(a)
+            if te and r == 1.0:
+                return depth + 1
+            if te:
+                continue
+            k = _state_key(n)
+            if k not in seen:
+                seen.add(k)
+                q.append((n, depth + 1))
+    return None
+
+
+@pytest.mark.parametrize("family,size,seed", [(O.EMPTY, 5, 0), (O.EMPTY, 6, 0), (O.EMPTY, 8, 0),
+                                              (O.DOORKEY, 5, 1), (O.DOORKEY, 5, 2), (O.DOORKEY, 6, 3),
+                                              (O.LAVAGAP, 5, 4), (O.LAVAGAP, 6, 5), (O.FOURROOMS, 7, 6)])
+def test_bfs_plans_reach_goal_with_exact_reward(family, size, seed):
+    env = O.Env(family, size, seed=seed)
+    ent, col, st = env.grid()
+    cells = tuple((int(ent[y, x]), int(col[y, x]), int(st[y, x])) for y in range(size) for x in range(size))
+    start = (env.s.ax, env.s.ay, env.s.dir, None, cells)
+    plan = M.bfs_goal(start, size, size, max_depth=40)
+    assert plan is not None
+    if family == O.EMPTY:
+        # closed form: S-3 steps east, one turn, S-3 steps south
+        assert len(plan) == 2 * (size - 3) + 1
+    play = _clone(env)
+    for i, a in enumerate(plan):
+        r, te, tr = play.step(a)
+        if i < len(plan) - 1:
+            assert (r, te) == (0.0, 0), f"early end at step {i}"
+    assert (r, te) == (1.0, 1)
+    assert play.s.t == len(plan)
+    assert _oracle_bfs_len(env) == len(plan)
+
+
+def _count(ent, code):
+    return int((ent == code).sum())
+
+
+@pytest.mark.parametrize("family,size,seed", [(O.EMPTY, 5, 10), (O.EMPTY, 16, 11), (O.DOORKEY, 5, 12),
+                                              (O.DOORKEY, 8, 13), (O.DOORKEY, 16, 14), (O.FOURROOMS, 19, 15),
+                                              (O.LAVAGAP, 7, 16), (O.DYNOBS, 16, 17), (O.DYNOBS, 5, 18)])
+def test_random_rollout_invariants(family, size, seed):
+    n_envs, T = 16, 1500
+    b = O.Batch([family] * n_envs, [size] * n_envs, seed=seed)
+    b.reset()
+    init = []
+    for i in range(n_envs):
+        e = b.env(i)
+        ent = np.frombuffer(bytes(e.ent), np.uint8)[: size * size].reshape(size, size)
+        init.append((_count(ent, 5), _count(ent, 6)))
+    prev = [b.state(i) for i in range(n_envs)]
+    for t in range(T):
+        o = b.step()
+        for i in range(n_envs):
+            s = b.state(i)
+            p = prev[i]
+            ent = np.frombuffer(s["ent"], np.uint8).reshape(size, size)
+            col = np.frombuffer(s["col"], np.uint8).reshape(size, size)
+            st = np.frombuffer(s["st"], np.uint8).reshape(size, size)
+            # border walls
+            assert (ent[0, :] == 2).all() and (ent[-1, :] == 2).all() and (ent[:, 0] == 2).all() and (ent[:, -1] == 2).all()
+            assert not (ent == 10).any()
+            # the agent stands on a walkable cell inside the grid
+            x, y = s["x"], s["y"]
+            assert 1 <= x <= size - 2 and 1 <= y <= size - 2
+            ce, cs = ent[y, x], st[y, x]
+            assert ce in (1, 3, 8, 9) or (ce == 4 and cs == 0)
+            assert 0 <= s["t"] <= s["max_steps"]
+            if p["done"]:
+                # autoreset step
+                assert s["episode"] == p["episode"] + 1 and s["t"] == 0
+                assert o["reward"][i] == 0 and o["terminated"][i] == 0 and o["truncated"][i] == 0
+                continue
+            assert s["episode"] == p["episode"] and s["t"] == p["t"] + 1
+            keys0, balls0 = init[i]
+            keys = _count(ent, 5) + (1 if s["carry_ent"] == 5 else 0)
+            balls = _count(ent, 6) + (1 if s["carry_ent"] == 6 else 0)
+            pe = np.frombuffer(p["ent"], np.uint8).reshape(size, size)
+            pk = _count(pe, 5) + (1 if p["carry_ent"] == 5 else 0)
+            pb = _count(pe, 6) + (1 if p["carry_ent"] == 6 else 0)
+            assert keys == pk and balls == pb
+            # doors unlock only with a key of the door's colour in hand
+            pst = np.frombuffer(p["st"], np.uint8).reshape(size, size)
+            unlocked = (pe == 4) & (pst == 2) & (st != 2)
+            if unlocked.any():
+                yy, xx = np.argwhere(unlocked)[0]
+                assert s["carry_ent"] == 5 and s["carry_col"] == col[yy, xx]
+            # termination exactly on the reward events
+            term = o["terminated"][i]
+            on_goal = ent[y, x] == 8
+            on_lava = ent[y, x] == 9
+            hit = family == O.DYNOBS and term and not on_goal and not on_lava
+            assert bool(term) == bool(on_goal or on_lava or hit)
+            if on_goal:
+                assert o["reward"][i] == 1.0
+            if hit:
+                assert o["reward"][i] == -1.0
+            assert o["truncated"][i] == (1 if s["t"] >= s["max_steps"] else 0)
+            # the agent cell is always visible and shows the carried object
+            oc = tuple(o["obs_sym"][i, 6, 3])
+            assert oc == ((s["carry_ent"], s["carry_col"], 0) if s["carry_ent"] else (1, 0, 0))
+        prev = [b.state(i) for i in range(n_envs)]
+        if t > 300 and family in (O.EMPTY, O.LAVAGAP):
+            break
+
+
+SIZES = {O.EMPTY: range(5, 20), O.DOORKEY: range(5, 20), O.FOURROOMS: range(5, 20), O.LAVAGAP: range(5, 20),
+         O.DYNOBS: range(5, 20)}
+
+
+@pytest.mark.parametrize("family", [O.EMPTY, O.DOORKEY, O.FOURROOMS, O.LAVAGAP, O.DYNOBS])
+def test_layouts_valid_for_every_size(family):
+    for size in SIZES[family]:
+        for seed in range(24):
+            env = O.Env(family, size, seed=seed, env_index=seed * 7 + 1)
+            ent, col, st = env.grid()
+            S = size
+            assert (ent[0] == 2).all() and (ent[-1] == 2).all() and (ent[:, 0] == 2).all() and (ent[:, -1] == 2).all()
+            x, y, d = env.s.ax, env.s.ay, env.s.dir
+            assert 0 <= d < 4 and ent[y, x] == 1
+            if family in (O.EMPTY, O.LAVAGAP, O.DYNOBS):
+                assert (x, y, d) == (1, 1, 0)
+            if family != O.FOURROOMS:
+                assert ent[S - 2, S - 2] == 8 and _count(ent, 8) == 1
+            if family == O.DOORKEY:
+                walls = [c for c in range(2, S - 2) if (ent[1:S - 1, c] != 1).all() and (ent[1:S - 1, c] == 2).sum() == S - 3]
+                assert len(walls) == 1
+                xw = walls[0]
+                dy = np.argwhere(ent[:, xw] == 4).ravel()
+                assert len(dy) == 1 and 1 <= dy[0] <= S - 3 and (col[dy[0], xw], st[dy[0], xw]) == (4, 2)
+                ky, kx = np.argwhere(ent == 5)[0]
+                assert _count(ent, 5) == 1 and col[ky, kx] == 4 and kx < xw and x < xw and (kx, ky) != (x, y)
+            if family == O.FOURROOMS:
+                m = S // 2
+                gaps_v = [r for r in range(1, S - 1) if r != m and ent[r, m] != 2]
+                gaps_h = [c for c in range(1, S - 1) if c != m and ent[m, c] != 2]
+                assert len(gaps_v) == 2 and len(gaps_h) == 2
+                assert gaps_v[0] < m < gaps_v[1] and gaps_h[0] < m < gaps_h[1]
+                assert _count(ent, 8) == 1
+            if family == O.LAVAGAP:
+                cols = np.argwhere((ent == 9).any(axis=0)).ravel()
+                assert len(cols) == 1 and 2 <= cols[0] <= S - 3
+                assert (ent[1:S - 1, cols[0]] == 9).sum() == S - 3
+            if family == O.DYNOBS:
+                assert _count(ent, 6) == 4 and ent[1, 1] == 1
+                bx, by = list(env.s.ball_x), list(env.s.ball_y)
+                assert len({(a, b) for a, b in zip(bx, by)}) == 4
+                for a, b in zip(bx, by):
+                    assert ent[b, a] == 6 and col[b, a] == 2
+
+
+def test_layout_choices_cover_their_ranges():
+    S = 8
+    xs, doors, agents, dirs = set(), set(), set(), set()
+    for ep in range(400):
+        env = O.Env(O.DOORKEY, S, seed=1)
+        env.reset(ep)
+        ent, _, _ = env.grid()
+        xw = [c for c in range(2, S - 2) if (ent[1:S - 1, c] == 2).sum() == S - 3][0]
+        xs.add(xw)
+        doors.add(int(np.argwhere(ent[:, xw] == 4)[0][0]))
+        agents.add((env.s.ax, env.s.ay))
+        dirs.add(env.s.dir)
+    assert xs == set(range(2, S - 2)) and doors == set(range(1, S - 2)) and dirs == {0, 1, 2, 3}
+    assert len(agents) >= 20
+    gaps = set()
+    for ep in range(300):
+        env = O.Env(O.LAVAGAP, 7, seed=2)
+        env.reset(ep)
+        ent, _, _ = env.grid()
+        c = int(np.argwhere((ent == 9).any(axis=0)).ravel()[0])
+        gaps.add((c, int(np.argwhere(ent[1:6, c] != 9).ravel()[0]) + 1))
+    assert gaps == {(c, g) for c in range(2, 5) for g in range(1, 6)}
+
+
+def test_ball_moves_stay_on_free_neighbours():
+    env = O.Env(O.DYNOBS, 8, seed=9)
+    for t in range(300):
+        before = list(zip(env.s.ball_x, env.s.ball_y))
+        r, te, tr = env.step(0)  # turning in place: only the balls move
+        after = list(zip(env.s.ball_x, env.s.ball_y))
+        if env.s.t == 0:
+            continue
+        for (a, b), (c, d) in zip(before, after):
+            assert max(abs(a - c), abs(b - d)) <= 1
+            assert (c, d) != (env.s.ax, env.s.ay)
+        assert len(set(after)) == 4
