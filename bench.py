@@ -1,0 +1,427 @@
+"""Benchmark of the batched MiniGrid step (NAVIX, arXiv 2407.19396) on GB300.
+
+One bench step is one complete rollout of the workload's batch: every env of
+the batch advances ``T`` environment steps through the fused CUDA step kernel
+(action draw, autoreset, transition, rules, reward/termination, egocentric
+view with occlusion, observation stores), run as graph-captured persistent
+chunks.  ``value`` counts env-steps (one env advanced by one step) per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Workloads (synthetic, seeded; no dataset exists for this path):
+  doorkey8  DoorKey-8x8, 4096 envs x 1000 steps, seed 1 (default)
+  empty5    Empty-5x5, 64 envs x 1000 steps, seed 0
+  mixed     65,536 envs over Empty-5/8/16, DoorKey-16, FourRooms-19,
+            LavaGap-7 x 2048 steps, seed 2, 128-step chunks
+  rgb       Dynamic-Obstacles-16, 4 balls, 8192 envs x 512 steps, seed 3,
+            RGB 224x224x3 + symbolic observations
+Multi-GPU: every rank runs the full workload on its own env-index range
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+MIXED = [(0, 5), (0, 8), (0, 16), (1, 16), (2, 19), (3, 7)]
+WORKLOADS = {
+    "empty5": dict(desc="Empty-5x5, 64 envs x 1000 steps, seed 0, uniform random actions over 7, symbolic obs",
+                   parts=[(0, 5)], n=64, T=1000, seed=0, rgb=False, depth=1000),
+    "doorkey8": dict(desc="DoorKey-8x8, 4096 envs x 1000 steps, seed 1, uniform random actions over 7, symbolic obs",
+                     parts=[(1, 8)], n=4096, T=1000, seed=1, rgb=False, depth=1000),
+    "mixed": dict(desc="65,536 envs in contiguous blocks of Empty-5x5/8x8/16x16, DoorKey-16x16, FourRooms-19x19, "
+                       "LavaGap-7x7 x 2048 steps, seed 2, 128-step graph chunks, symbolic obs",
+                  parts=MIXED, n=65536, T=2048, seed=2, rgb=False, depth=128),
+    "rgb": dict(desc="Dynamic-Obstacles-16x16, 4 balls, 8192 envs x 512 steps, seed 3, 3 random actions, "
+                     "RGB 224x224x3 + symbolic obs (8-slot output ring)",
+                parts=[(4, 16)], n=8192, T=512, seed=3, rgb=True, depth=8),
+}
+OUT_BYTES_SYM = 147 + 4 + 2  # symbolic obs + reward + two flags per env-step
+OUT_BYTES_RGB = 150528
+
+
+def descs_of(w, n=None):
+    n = n or w["n"]
+    parts = w["parts"]
+    base, extra = divmod(n, len(parts))
+    out = []
+    for j, p in enumerate(parts):
+        out += [p] * (base + (1 if j < extra else 0))
+    return out
+
+
+def alg_bytes(w, descs, steps_per_launch):
+    """Algorithmic HBM bytes of one rollout: every env-step writes its outputs
+    once; every launch reads and writes each env's state once (three planes of
+    S*S bytes plus a 32-byte agent block)."""
+    T = w["T"]
+    n = len(descs)
+    per_step = OUT_BYTES_SYM + (OUT_BYTES_RGB if w["rgb"] else 0)
+    state = sum(3 * s * s + 32 for _, s in descs)
+    launches = -(-T // steps_per_launch)
+    return n * T * per_step + 2 * state * launches
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2407_19396_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2407_19396_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel sources changed since."""
+    p = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if (args.impl != "reference" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def cpu_oracle_rate(w, seed_offset=0, min_s=10.0, max_s=30.0, n_envs=None, T=None):
+    """Env-steps/s of the oracle on this host (single thread) on the workload's
+    own batch, repeated until at least min_s of work (bounded by max_s)."""
+    import oracle as O
+
+    n_envs = n_envs or w["n"]
+    T = T or w["T"]
+    descs = descs_of(w, n_envs)
+    done, t0 = 0, time.perf_counter()
+    reps = 0
+    while True:
+        b = O.Batch([d[0] for d in descs], [d[1] for d in descs], seed=w["seed"] + seed_offset)
+        b.reset(sym=True)
+        b.rollout(T, sym=True)
+        done += n_envs * T
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_s or el >= max_s:
+            break
+    return done / el, reps, el, n_envs, T
+
+
+def run_reference(args, w, world, rank):
+    """The CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    oracle_T = min(w["T"], 1000)
+    descs = descs_of(w)
+    times = []
+    for k in range(args.warmup + args.steps):
+        b = O.Batch([d[0] for d in descs], [d[1] for d in descs], seed=w["seed"])
+        t0 = time.perf_counter()
+        b.reset(sym=True, rgb=False)
+        b.rollout(oracle_T, sym=True)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    units = len(descs) * oracle_T * len(times)
+    v = units / total
+    sample = f"{len(descs)} envs x {oracle_T} steps per bench step (symbolic obs), {len(times)} timed steps"
+    line = {
+        "impl": "reference", "metric": "env steps/sec", "value": v, "unit": "env-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w["desc"], "n_envs": len(descs), "env_steps_per_bench_step": len(descs) * oracle_T},
+        "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_rollouts(env, w, out, K, W, flush, per_family=False):
+    """W untimed rollouts, then K timed ones with CUDA events on the launching
+    stream; L2 is flushed between timed rollouts, outside the event windows.
+    Returns (per-step ms list, kernel ms, step launches, all launches)."""
+    import torch
+
+    T, depth = w["T"], w["depth"]
+    for _ in range(W):
+        env.rollout(T, depth=depth, out=out, per_family=per_family)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    l0 = env.launch_counts()
+    env.profile_begin()
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(st)
+        env.rollout(T, depth=depth, out=out, per_family=per_family)
+        evs[k][1].record(st)
+    torch.cuda.synchronize()
+    kernel_ms, kl = env.profile_end()
+    l1 = env.launch_counts()
+    return [a.elapsed_time(b) for a, b in evs], kernel_ms, kl, l1[1] - l0[1]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="navixgb", choices=["navixgb", "reference"])
+    ap.add_argument("--workload", default="doorkey8", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extras", action="store_true", help="skip the other configs and the CPU baseline")
+    ap.add_argument("--ncu-case", action="store_true", help="one rollout of the workload for an ncu capture")
+    ap.add_argument("--shape", default="", help="force the launch shape as LANES,ENVS_PER_CTA (no autotuning)")
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.ncu_case:
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    world, rank, local, dist = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, w, world, rank)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return rc
+
+    import torch
+
+    from paper_2407_19396_gb300 import build as nxbuild
+    from paper_2407_19396_gb300 import inputs
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    nxbuild.build()
+    torch.cuda.set_device(local)
+    n = w["n"]
+    descs = descs_of(w)
+    atlas = inputs.atlas() if w["rgb"] else None
+    shape = {}
+    if args.shape:
+        g, e = (int(v) for v in args.shape.split(","))
+        shape = dict(group_lanes=g, envs_per_cta=e, autotune=False)
+    env = nx.Env(descs=descs, seed=w["seed"], obs_rgb=w["rgb"], atlas=atlas, env_index_base=rank * n, **shape)
+    env.reset()
+    out = env.alloc_out(w["depth"])
+    if args.ncu_case:
+        env.rollout(w["T"], depth=w["depth"], out=out)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": args.workload, "info": env.info()}), flush=True)
+        return 0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MiB > 129 MB L2
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    step_ms, kernel_ms, k_launches, all_launches = time_rollouts(env, w, out, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = world * n * w["T"] * args.steps
+    value = units / (total_ms / 1000.0)
+
+    # roofline of the step kernel: algorithmic bytes / live kernel time
+    C = env.info()["steps_per_launch"]
+    per_rollout_bytes = alg_bytes(w, descs, C)
+    achieved = per_rollout_bytes * args.steps / (kernel_ms / 1000.0) / 1e9
+    peak, peak_src = measured_peaks()
+    launches_per_rollout = -(-w["T"] // C)
+    traffic = ncu_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": per_rollout_bytes / launches_per_rollout,
+                "kernel_ms_per_launch": kernel_ms / max(k_launches, 1), "kernel": "nx_step_kernel"}
+
+    # end to end through the C ABI with host buffers: host actions in, host outputs back, every step
+    e2e = None
+    if True:  # every rank: the e2e leg is timed like the device leg (max over ranks)
+        T = w["T"]
+        acts = torch.from_numpy(inputs.random_actions(w["seed"], (T, n), n_actions=3 if w["parts"][0][0] == 4 else 7))
+        acts = acts.pin_memory()
+        hout = {"obs_sym": torch.empty((T, n, 7, 7, 3), dtype=torch.uint8).pin_memory(),
+                "reward": torch.empty((T, n), dtype=torch.float32).pin_memory(),
+                "terminated": torch.empty((T, n), dtype=torch.uint8).pin_memory(),
+                "truncated": torch.empty((T, n), dtype=torch.uint8).pin_memory(),
+                "obs_rgb": None}
+        if w["rgb"]:
+            hout["obs_rgb"] = None  # images stay on the device in this benchmark; see the design doc
+        e2e_env = nx.Env(descs=descs, seed=w["seed"], obs_rgb=w["rgb"], atlas=atlas, env_index_base=rank * n)
+        e2e_env.reset()
+        ks = max(1, min(args.steps, 5))
+        for _ in range(2):
+            e2e_env.rollout_host(T, actions=acts.numpy(), out=hout)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ks):
+            e2e_env.rollout_host(T, actions=acts.numpy(), out=hout)
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        h2d = T * n
+        d2h = T * n * OUT_BYTES_SYM
+        e2e = {"value": world * n * T * ks / el, "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ks, "actions": "host int8, seeded numpy draws"}
+        e2e_env.close()
+
+    line = {
+        "metric": "env steps/sec", "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w["desc"], "n_envs_per_gpu": n, "env_steps_per_bench_step": n * w["T"] * world,
+                   "steps_per_launch": C, "launch_shape": {k: env.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas")},
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": all_launches, "clocks": clk, "wall_s": wall,
+    }
+    env.close()
+    del out
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = {}
+        for name in ("mixed", "rgb", "empty5"):
+            if name == args.workload:
+                continue
+            wx = WORKLOADS[name]
+            dx = descs_of(wx)
+            ex = nx.Env(descs=dx, seed=wx["seed"], obs_rgb=wx["rgb"], atlas=inputs.atlas() if wx["rgb"] else None)
+            ex.reset()
+            ox = ex.alloc_out(wx["depth"])
+            ms, kms, kl, _ = time_rollouts(ex, wx, ox, 2, 1, flush)
+            cx = ex.info()["steps_per_launch"]
+            bx = alg_bytes(wx, dx, cx)
+            rec = {"env_steps_per_s": len(dx) * wx["T"] * len(ms) / (sum(ms) / 1000),
+                   "hbm_frac": bx * len(ms) / (kms / 1000) / 1e9 / peak,
+                   "achieved_GBps": bx * len(ms) / (kms / 1000) / 1e9,
+                   "launch_shape": {k: ex.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas")}}
+            if name == "mixed":
+                ms2, _, _, _ = time_rollouts(ex, wx, ox, 1, 0, flush, per_family=True)
+                rec["per_family_env_steps_per_s"] = len(dx) * wx["T"] / (sum(ms2) / 1000)
+            extras[name] = rec
+            ex.close()
+            del ox
+        line["extras"] = extras
+    if rank == 0 and world == 1 and not args.no_extras:
+        rate, reps, el, ne, nt = cpu_oracle_rate(w)
+        line["cpu_baseline"] = {"value": rate, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{ne} envs x {nt} steps (the full workload) x {reps}, {el:.1f} s, one thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

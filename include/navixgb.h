@@ -1,0 +1,233 @@
+/*
+ * navixgb.h -- C ABI of the GB300-native batched MiniGrid environment step
+ * (NAVIX, arXiv 2407.19396).
+ *
+ * The environment is the paper's tuple M = (h, w, T, O, A, R, d, O, R, gamma,
+ * P) (Section 3.2.1): grid height/width, a timeout T (max_steps), the
+ * symbolic_first_person / rgb_first_person observation functions (Table 4),
+ * the Markovian rewards R1-R3 (Table 8, Table 5), the terminations of
+ * Table 6, the intervention and transition systems (Table 3, Appendix A) and
+ * the timestep/autoreset protocol (Section 3.2.2, Code 1).  The batching over
+ * environments is the paper's vmap (Code 3); nx_rollout is the jitted scan of
+ * Code 2 as persistent, graph-captured chunks.
+ *
+ * Conventions shared by every call:
+ *   - All functions return nx_status (0 = NX_OK, < 0 = error).  Nothing in
+ *     the library aborts, exits or traps; argument errors are reported
+ *     synchronously, device-side problems through nx_sync().
+ *   - A context is bound to one CUDA stream (the one given at creation); all
+ *     work is enqueued on it and is asynchronous to the host unless the call
+ *     says otherwise.  Calls on one context must not run concurrently from
+ *     several host threads.
+ *   - Device pointers passed in are owned by the caller and must stay valid
+ *     until the enqueued work has finished.  Memory the library allocates is
+ *     owned by the context and released by nx_destroy().
+ *   - Cell codes: entity 0 unseen, 1 empty, 2 wall, 3 floor, 4 door, 5 key,
+ *     6 ball, 7 box, 8 goal, 9 lava, 10 agent; colour 0 red, 1 green, 2 blue,
+ *     3 purple, 4 yellow, 5 grey; door state 0 open, 1 closed, 2 locked.
+ *     Directions 0 east (+x), 1 south (+y), 2 west, 3 north.  Actions 0 left,
+ *     1 right, 2 forward, 3 pickup, 4 drop, 5 toggle, 6 done.
+ *   - Randomness: every draw is word 0 of Philox4x32-10 (Salmon et al.,
+ *     SC'11) with key (seed lo, seed hi) and counter (env index, episode,
+ *     step, purpose << 24 | draw); a bounded draw in [0, n) is
+ *     (x * n) >> 32.  Purposes: 1 layout, 2 ball move, 3 random action (the
+ *     episode word is then 0xFFFFFFFF and the step word is the number of
+ *     step calls since nx_reset).  Results therefore do not depend on the
+ *     launch configuration, on the GPU count or on the other envs in a batch.
+ */
+#ifndef NAVIXGB_H
+#define NAVIXGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t nx_status;
+enum {
+    NX_OK = 0,
+    NX_PENDING = 1,          /* nx_poll: the request has not finished */
+    NX_E_INVAL = -1,         /* invalid argument */
+    NX_E_NOMEM = -2,         /* an allocation failed */
+    NX_E_CUDA = -3,          /* a CUDA runtime call failed (see nx_last_error) */
+    NX_E_TIMEOUT = -4,       /* a bounded host wait expired */
+    NX_E_DEVICE_CHECK = -5,  /* a device-side consistency check fired */
+    NX_E_BUDGET = -6,        /* a serving request can never fit the HBM budget */
+    NX_E_STATE = -7          /* call out of order (e.g. step before reset) */
+};
+
+/* environment families of Table 8 */
+enum { NX_EMPTY = 0, NX_DOORKEY = 1, NX_FOURROOMS = 2, NX_LAVAGAP = 3, NX_DYNOBS = 4 };
+/* observation bit flags (Table 4) */
+enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2 };
+/* action sources */
+enum { NX_ACT_BUFFER = 0, NX_ACT_RANDOM = 1 };
+/* reward functions: Markovian (Section 3.2.1, Table 5) or MiniGrid's Eq. 1 */
+enum { NX_REWARD_MARKOV = 0, NX_REWARD_MINIGRID = 1 };
+/* smem staging layouts of the grid (tunable; never changes results) */
+enum { NX_STAGE_AUTO = 0, NX_STAGE_BYTE = 1, NX_STAGE_WORD = 2 };
+
+#define NX_MIN_SIZE 5
+#define NX_MAX_SIZE 19
+#define NX_VIEW 7
+#define NX_OBS_SYM_BYTES 147        /* 7 x 7 x 3 */
+#define NX_OBS_RGB_BYTES 150528     /* 224 x 224 x 3 */
+#define NX_ATLAS_TILES 397
+#define NX_ATLAS_BYTES (397 * 3072) /* 397 tiles of 32 x 32 x 3 */
+#define NX_AGENT_BYTES 32
+#define NX_MAX_BALLS 4
+
+typedef struct nx_env nx_env;
+typedef struct nx_server nx_server;
+
+/* One environment's shape: family, square grid side (height == width,
+ * 5..19), timeout T (<= 0: the family default: Empty/LavaGap/
+ * Dynamic-Obstacles 4 S^2, DoorKey 10 S^2, FourRooms 100; at most 65535). */
+typedef struct {
+    int32_t family, height, width, max_steps;
+} nx_desc;
+
+/* Creation options; nx_options_default() fills the defaults. */
+typedef struct {
+    uint32_t obs_flags;       /* NX_OBS_SYM | NX_OBS_RGB (default NX_OBS_SYM) */
+    int32_t reward_mode;      /* NX_REWARD_MARKOV (default) or NX_REWARD_MINIGRID */
+    float lava_reward;        /* reward on stepping into lava (default 0.0f; the paper's R2 uses -1) */
+    int32_t n_balls;          /* Dynamic-Obstacles balls, 0..4 (default 4) */
+    int32_t steps_per_launch; /* steps per persistent chunk in nx_rollout, 1..1024 (default 128) */
+    int32_t autotune;         /* 1: time the launch shapes once and keep the fastest (default 1) */
+    int32_t group_lanes;      /* lanes per env, 1/2/4/8/16/32; 0 = chosen by the library */
+    int32_t envs_per_cta;     /* envs per thread block; 0 = chosen by the library */
+    int32_t staging;          /* NX_STAGE_*; 0 = chosen by the library */
+    const uint8_t* atlas;     /* host sprite atlas, NX_ATLAS_BYTES (required with NX_OBS_RGB) */
+    /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMallocAsync */
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* alloc_user;
+    /* global index of this context's env 0 in the draw counters (default 0):
+     * contexts over disjoint index ranges reproduce one large batch exactly,
+     * which is how a batch is split over GPUs */
+    uint32_t env_index_base;
+} nx_options;
+
+/* Per-step outputs, device pointers owned by the caller; any may be NULL (not
+ * written).  Shapes are [depth, n_envs, ...] row-major: obs_sym [.., 7, 7, 3]
+ * uint8 laid out [view row vy][view column vx][entity, colour, state] with
+ * the agent at (vx 3, vy 6) facing vy = 0; obs_rgb [.., 224, 224, 3] uint8;
+ * reward [..] float32; terminated / truncated [..] uint8 (0/1).  Step i of a
+ * call writes time slot i % depth (depth <= 0 means 1). */
+typedef struct {
+    uint8_t* obs_sym;
+    uint8_t* obs_rgb;
+    float* reward;
+    uint8_t* terminated;
+    uint8_t* truncated;
+    int32_t depth;
+} nx_out;
+
+/* Launch shape in use (after autotuning). */
+typedef struct {
+    int32_t group_lanes, envs_per_cta, staging, n_items, grid_ctas, smem_bytes, steps_per_launch;
+    int32_t n_envs, n_families;
+    size_t state_bytes, device_bytes;
+} nx_info;
+
+void nx_options_default(nx_options* opts);
+
+/* nx_create: one family and size for all n_envs environments (the paper's
+ * make(id), Code 1, batched as in Code 3).  n_envs >= 1.  seed keys every
+ * draw.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Allocates the device state (about 3 S^2 + 32 bytes per env) but does not
+ * initialise it: call nx_reset before stepping.  NX_E_INVAL on bad
+ * arguments, NX_E_NOMEM / NX_E_CUDA on allocation or device failures. */
+nx_status nx_create(nx_env** env, int32_t family, int32_t size, int32_t n_envs, uint64_t seed,
+                    const nx_options* opts, void* cuda_stream);
+
+/* nx_create_mixed: one descriptor per environment (host array of n_envs).
+ * Environments with equal descriptors should be contiguous: each maximal
+ * run of equal descriptors is batched separately. */
+nx_status nx_create_mixed(nx_env** env, const nx_desc* host_descs, int32_t n_envs, uint64_t seed,
+                          const nx_options* opts, void* cuda_stream);
+
+/* nx_reset: reset(key) of Section 3.2.2 for every env (episode 0), the step
+ * counter of random actions restarts at 0.  Writes the initial observation
+ * with reward 0 and both flags 0 (the paper's reward padding) into slot 0 of
+ * out (out or any pointer in it may be NULL). */
+nx_status nx_reset(nx_env* env, const nx_out* out);
+
+/* nx_step: one step(timestep, action) of Code 1 for every env, with
+ * autoreset: an env whose previous step terminated or truncated starts its
+ * next episode instead (reward 0, flags 0, the action is ignored).
+ * d_actions: device int8 [n_envs]; NULL draws uniform random actions (7, or
+ * 3 in Dynamic-Obstacles).  Out-of-range actions are executed as no-ops and
+ * set a sticky flag (nx_device_flags).  Step order inside one env: autoreset,
+ * transition (Dynamic-Obstacles balls), intervention, reward/termination,
+ * time/truncation, observation. */
+nx_status nx_step(nx_env* env, const int8_t* d_actions, const nx_out* out);
+
+/* nx_rollout: n_steps consecutive nx_step calls fused into persistent,
+ * CUDA-graph-captured chunks of steps_per_launch steps (the jitted scan of
+ * Code 2).  act_mode NX_ACT_RANDOM ignores d_actions_TN; NX_ACT_BUFFER reads
+ * device int8 [n_steps, n_envs].  Step i writes slot i % traj->depth. */
+nx_status nx_rollout(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* d_actions_TN,
+                     const nx_out* traj);
+
+/* nx_rollout_per_family: the plain comparison form of nx_rollout -- the
+ * same results, computed with one single-step launch per family per step
+ * (state round-trips through HBM every step, no graph). */
+nx_status nx_rollout_per_family(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* d_actions_TN,
+                                const nx_out* traj);
+
+/* nx_rollout_host: nx_rollout with HOST buffers (pinned memory gives
+ * overlap): actions are copied in and outputs copied back chunk by chunk on
+ * the context stream; returns when the copies have finished.  host_actions_TN
+ * is int8 [n_steps, n_envs] (ignored for NX_ACT_RANDOM); the host outputs are
+ * [n_steps, n_envs, ...] (depth is ignored).  Any output may be NULL. */
+nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* host_actions_TN,
+                          const nx_out* host_traj);
+
+/* State snapshot (checkpoint/resume).  Blocking.  Layout of the buffer:
+ *   [0, 64)                header: "NXST", version 1, n_envs, gstep (u32 at 12),
+ *                          grid pool bytes (u64 at 16), seed (u64 at 24)
+ *   [64, 64 + 32 n)        per-env agent blocks, NX_AGENT_BYTES each:
+ *       u8 x, y, dir, carry_ent, carry_col, done, invalid, n_balls;
+ *       u16 t, max_steps; u32 episode; u8 ball_x[4], ball_y[4];
+ *       u8 family, size; u16 reserved; u32 grid_offset
+ *   [64 + 32 n, end)       grid pool: for each env at grid_offset, three
+ *                          planes of size*size bytes (entity, colour, state),
+ *                          row-major y * size + x.
+ * nx_set_state accepts only a snapshot of a context with the same
+ * descriptors. */
+size_t nx_state_bytes(const nx_env* env);
+nx_status nx_get_state(nx_env* env, void* host_buf, size_t bytes);
+nx_status nx_set_state(nx_env* env, const void* host_buf, size_t bytes);
+
+/* Waits (bounded by timeout_s, <= 0: no bound) for the context's stream and
+ * surfaces deferred device errors: NX_E_TIMEOUT, NX_E_CUDA or
+ * NX_E_DEVICE_CHECK. */
+nx_status nx_sync(nx_env* env, double timeout_s);
+/* Sticky device flags (bit 0: an out-of-range action was seen; bit 1: an
+ * internal bounds check fired).  Blocking. */
+nx_status nx_device_flags(nx_env* env, uint32_t* flags);
+nx_status nx_get_info(const nx_env* env, nx_info* info);
+
+/* Kernel instrumentation.  nx_profile_begin starts recording a CUDA event
+ * pair on the context stream around every step-kernel launch (a captured
+ * chunk counts as one launch: its step kernel plus the two-word counter
+ * update).  nx_profile_end waits for the stream and returns the summed
+ * device time of those launches in milliseconds and their count.
+ * nx_launch_counts returns the cumulative number of step-kernel launches and
+ * of all kernels this context has enqueued (graph replays count their
+ * nodes); it never blocks. */
+nx_status nx_profile_begin(nx_env* env);
+nx_status nx_profile_end(nx_env* env, double* kernel_ms, int64_t* step_launches);
+nx_status nx_launch_counts(const nx_env* env, int64_t* step_launches, int64_t* all_launches);
+void nx_destroy(nx_env* env);
+const char* nx_status_str(nx_status s);
+const char* nx_last_error(const nx_env* env);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

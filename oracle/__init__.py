@@ -88,6 +88,9 @@ def lib():
             L.orc_batch_create.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_uint64,
                                            ctypes.c_uint32, ctypes.c_int32, ctypes.c_float]
             L.orc_batch_create.restype = ctypes.c_void_p
+            L.orc_batch_create_indexed.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_uint64,
+                                                   P(ctypes.c_uint32), ctypes.c_int32, ctypes.c_float]
+            L.orc_batch_create_indexed.restype = ctypes.c_void_p
             L.orc_batch_destroy.argtypes = [ctypes.c_void_p]
             L.orc_batch_env.argtypes = [ctypes.c_void_p, ctypes.c_int32]
             L.orc_batch_env.restype = P(OrcEnv)
@@ -199,14 +202,21 @@ class Batch:
     """n oracle environments with global indices base..base+n-1 (Code 3's vmap)."""
 
     def __init__(self, families, sizes, seed, max_steps=None, n_balls=4, env_index_base=0, reward_mode=0,
-                 lava_reward=0.0):
+                 lava_reward=0.0, env_indices=None):
         fam = np.ascontiguousarray(families, np.int32)
         siz = np.ascontiguousarray(sizes, np.int32)
         self.n = int(fam.shape[0])
         ms = None if max_steps is None else np.ascontiguousarray(max_steps, np.int32)
-        h = lib().orc_batch_create(self.n, _ptr(fam, ctypes.c_int32), _ptr(siz, ctypes.c_int32),
-                                   _ptr(ms, ctypes.c_int32), n_balls, seed, env_index_base, reward_mode,
-                                   lava_reward)
+        if env_indices is None:
+            h = lib().orc_batch_create(self.n, _ptr(fam, ctypes.c_int32), _ptr(siz, ctypes.c_int32),
+                                       _ptr(ms, ctypes.c_int32), n_balls, seed, env_index_base, reward_mode,
+                                       lava_reward)
+        else:
+            idx = np.ascontiguousarray(env_indices, np.uint32)
+            assert idx.shape == (self.n,)
+            h = lib().orc_batch_create_indexed(self.n, _ptr(fam, ctypes.c_int32), _ptr(siz, ctypes.c_int32),
+                                               _ptr(ms, ctypes.c_int32), n_balls, seed, _ptr(idx, ctypes.c_uint32),
+                                               reward_mode, lava_reward)
         if not h:
             raise ValueError("invalid oracle batch arguments")
         self.h = h

@@ -592,6 +592,18 @@ orc_batch* orc_batch_create(int32_t n, const int32_t* family, const int32_t* siz
                             int32_t n_balls, uint64_t seed, uint32_t env_index_base, int32_t reward_mode,
                             float lava_reward)
 {
+    uint32_t* idx = (uint32_t*)malloc((n > 0 ? (size_t)n : 1u) * sizeof(uint32_t));
+    if (!idx) return NULL;
+    for (int32_t i = 0; i < n; i++) idx[i] = env_index_base + (uint32_t)i;
+    orc_batch* b = orc_batch_create_indexed(n, family, size, max_steps, n_balls, seed, idx, reward_mode, lava_reward);
+    free(idx);
+    return b;
+}
+
+orc_batch* orc_batch_create_indexed(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
+                                    int32_t n_balls, uint64_t seed, const uint32_t* env_index, int32_t reward_mode,
+                                    float lava_reward)
+{
     if (n < 0) return NULL;
     orc_batch* b = (orc_batch*)calloc(1, sizeof *b);
     if (!b) return NULL;
@@ -603,7 +615,7 @@ orc_batch* orc_batch_create(int32_t n, const int32_t* family, const int32_t* siz
     }
     for (int32_t i = 0; i < n; i++) {
         if (orc_env_init(&b->envs[i], family[i], size[i], max_steps ? max_steps[i] : 0, n_balls, seed,
-                         env_index_base + (uint32_t)i, reward_mode, lava_reward) != 0) {
+                         env_index[i], reward_mode, lava_reward) != 0) {
             free(b->envs);
             free(b);
             return NULL;

@@ -102,6 +102,10 @@ typedef struct orc_batch orc_batch;
 orc_batch* orc_batch_create(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
                             int32_t n_balls, uint64_t seed, uint32_t env_index_base, int32_t reward_mode,
                             float lava_reward);
+/* as above, with an explicit global env index per env (a sample of a larger batch) */
+orc_batch* orc_batch_create_indexed(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
+                                    int32_t n_balls, uint64_t seed, const uint32_t* env_index, int32_t reward_mode,
+                                    float lava_reward);
 void orc_batch_destroy(orc_batch* b);
 orc_env* orc_batch_env(orc_batch* b, int32_t i);
 void orc_batch_reset(orc_batch* b, uint8_t* obs_sym, uint8_t* obs_rgb, const uint8_t* atlas, float* reward,

@@ -1,0 +1,107 @@
+// nx_internal.h -- data layout shared by the host runtime and the kernels of
+// libnavixgb (never exposed through the C ABI).
+//
+// HBM layout of one context (all 256-byte aligned, one allocation each):
+//   agents   nx_agent[n_envs]        32 B per env, the documented snapshot block
+//   grids    uint8[pool]             per env three planes (entity, colour,
+//                                    state) of size*size bytes, row-major
+//   items    nx_item[n_items]        work list: runs of <= envs_per_cta
+//                                    consecutive envs sharing a descriptor
+//   reqs     nx_req[n_reqs]          per request: key, step counters, outputs
+//   ctl      nx_ctl                  sticky flags
+//   atlas    uint8[397 * 3072]       sprite atlas (RGB only)
+#pragma once
+#include <stdint.h>
+
+#define NX_ALIGN16 __attribute__((aligned(16)))
+
+// One env's persistent state (exactly the 32-byte agent block of the
+// snapshot format in navixgb.h).
+struct NX_ALIGN16 nx_agent {
+    uint8_t x, y, dir, carry_ent;
+    uint8_t carry_col, done, invalid, n_balls;
+    uint16_t t, max_steps;
+    uint32_t episode;
+    uint8_t ball_x[4];
+    uint8_t ball_y[4];
+    uint8_t family, size;
+    uint16_t reserved;
+    uint32_t grid_offset;
+};
+static_assert(sizeof(nx_agent) == 32, "agent block is 32 bytes");
+
+// A run of consecutive envs with one descriptor, processed by one CTA.
+struct NX_ALIGN16 nx_item {
+    uint32_t env_begin;    // first env (index into agents)
+    uint32_t n_envs;       // number of envs (<= envs_per_cta)
+    uint32_t grid_offset;  // byte offset of env_begin's planes in the grid pool
+    uint32_t req;          // request record index
+    uint32_t local_begin;  // index of env_begin within its request (keys, output rows)
+    uint16_t max_steps;
+    uint8_t family, size;
+    uint32_t pad[2];
+};
+static_assert(sizeof(nx_item) == 32, "item is 32 bytes");
+
+// Per request (a context is one request; the server has one per admitted
+// request).  The kernels read it at item start; the advance kernel moves the
+// counters after each launch.
+struct NX_ALIGN16 nx_req {
+    uint64_t seed;
+    uint32_t gstep;       // step word of random-action draws at the next step
+    uint32_t call_step;   // steps already done in the current call (output slot, action row)
+    int32_t steps;        // steps each launch runs for this request (<= launch steps)
+    int32_t depth;        // output time slots
+    uint32_t n_envs;      // envs of the request (output row stride)
+    int32_t act_mode;     // NX_ACT_*
+    const int8_t* actions;  // [*, n_envs]
+    uint8_t* obs_sym;       // [depth, n_envs, 147]
+    uint8_t* obs_rgb;       // [depth, n_envs, 150528]
+    float* reward;          // [depth, n_envs]
+    uint8_t* terminated;
+    uint8_t* truncated;
+    float* returns;         // [n_envs] running sum of rewards (may be NULL)
+    uint64_t* digest;       // [n_envs] running output digest (may be NULL)
+    uint32_t* episodes;     // [n_envs] finished-episode counter (may be NULL)
+    uint32_t reward_mode;
+    float lava_reward;
+    int32_t n_balls;      // Dynamic-Obstacles balls placed at every reset
+    uint32_t key_base;    // draw-counter env index of the request's env 0
+};
+
+struct NX_ALIGN16 nx_ctl {
+    uint32_t flags;  // bit 0 invalid action seen, bit 1 bounds check
+    uint32_t pad[3];
+};
+
+enum { NX_FLAG_INVALID_ACTION = 1u, NX_FLAG_BOUNDS = 2u };
+
+// Launch arguments of the step kernel.
+struct nx_kparams {
+    const nx_item* items;
+    int32_t n_items;
+    int32_t launch_steps;  // upper bound of steps per item in this launch
+    nx_agent* agents;
+    uint8_t* grids;
+    nx_req* reqs;
+    nx_ctl* ctl;
+    const uint8_t* atlas;
+    int32_t cell_stride;   // smem bytes per env grid (>= max size^2, multiple of 16)
+    int32_t envs_per_cta;
+    int32_t reset_all;     // 1: start every env at episode 0 and emit its observation (no steps)
+    int32_t pad;
+};
+
+// Host-side launch helpers implemented in nx_kernels.cu.
+struct nx_launch_shape {
+    int group_lanes;
+    int envs_per_cta;
+    int rgb;
+};
+int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride);
+int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err);  // resident CTAs on the device
+int nx_launch_step_kernel(const nx_launch_shape& s, const nx_kparams& p, int grid, void* stream);
+int nx_launch_advance(nx_req* reqs, int n_reqs, void* stream);
+int nx_launch_configure(nx_req* r, const nx_req& v, int gstep_mode, void* stream);
+int nx_launch_set_steps(nx_req* r, int steps, void* stream);
+int nx_shape_supported(const nx_launch_shape& s);

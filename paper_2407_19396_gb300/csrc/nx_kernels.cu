@@ -1,0 +1,457 @@
+// nx_kernels.cu -- the fused, persistent MiniGrid step kernel of libnavixgb.
+//
+// One CTA processes one work item at a time (a run of <= envs_per_cta
+// consecutive envs that share a descriptor); a group of G lanes owns one env.
+// Per item: the envs' three int8 planes are packed into one byte per cell in
+// shared memory, then `steps` steps run back to back with the grid and the
+// agent state on chip, and the state is written back at the end.  Per step:
+//   draws (Philox, lanes in parallel) -> autoreset or transition + rules +
+//   reward/termination/truncation -> egocentric view + occlusion (ballots
+//   build the 49-bit transparency mask) -> 147 symbolic bytes staged in smem
+//   (co-aligned with the destination) and the 49 atlas tile ids ->
+//   one CTA barrier -> 16-byte vector stores of the staged block and of the
+//   RGB tiles (streaming stores straight from the L2-resident atlas).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "navixgb.h"
+#include "nx_device.cuh"
+#include "nx_internal.h"
+
+using namespace nxd;
+
+namespace {
+
+constexpr int kMaxThreads = 256;
+
+__host__ __device__ __forceinline__ int align16(int v) { return (v + 15) & ~15; }
+
+// 64-bit FNV-style running digest over 32-bit words
+__device__ __forceinline__ uint64_t digest_word(uint64_t h, uint32_t w) { return (h ^ (uint64_t)w) * 0x100000001B3ull; }
+
+// Intervention (rotate / forward / pickup / drop / toggle / done), the
+// Dynamic-Obstacles transition, then time, truncation, reward and termination.
+template <int G>
+__device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int family, int max_steps, AgentReg& a,
+                                         int action, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
+                                         float& reward, int& term, int& trunc, nx_ctl* ctl)
+{
+    // transition system: each ball, in index order, moves to a uniformly drawn
+    // empty cell of its 8-neighbourhood that is not the agent's cell
+    if (family == NX_DYNOBS) {
+        for (int b = 0; b < a.nb; ++b) {
+            uint32_t cand = 0;
+            int j = 0;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (dx == 0 && dy == 0) continue;
+                    const int x = a.bx[b] + dx, y = a.by[b] + dy;
+                    const bool f = (unsigned)x < (unsigned)S && (unsigned)y < (unsigned)S && g[y * S + x] == C_EMPTY &&
+                                   !(x == a.x && y == a.y);
+                    cand |= (f ? 1u : 0u) << j;
+                    ++j;
+                }
+            const int cnt = __popc(cand);
+            if (cnt > 0) {
+                int k = bounded(d[1 + b], (uint32_t)cnt);
+                uint32_t c = cand;
+                for (int i = 0; i < k; ++i) c &= c - 1u;
+                const int jj = __ffs(c) - 1;          // 0..7 over the 8 neighbours, row-major
+                const int o = jj < 4 ? jj : jj + 1;   // position in the 3x3 block, skipping the centre
+                const int nx = a.bx[b] + (o % 3) - 1, ny = a.by[b] + (o / 3) - 1;
+                grp.sync();
+                if (grp.lane == 0) {
+                    g[a.by[b] * S + a.bx[b]] = (uint8_t)C_EMPTY;
+                    g[ny * S + nx] = (uint8_t)C_BALL_BLUE;
+                }
+                grp.sync();
+                a.bx[b] = nx;
+                a.by[b] = ny;
+            }
+        }
+    }
+    // intervention system
+    int goal = 0, lava = 0, hit = 0;
+    const int n_act = family == NX_DYNOBS ? 3 : 7;
+    if (action < 0 || action > 6) {
+        if (!a.invalid && grp.lane == 0) atomicOr(&ctl->flags, (unsigned)NX_FLAG_INVALID_ACTION);
+        a.invalid = 1;
+    } else if (action < n_act) {
+        const int fxd = (a.dir == 0) - (a.dir == 2), fyd = (a.dir == 1) - (a.dir == 3);
+        const int fx = a.x + fxd, fy = a.y + fyd;
+        const bool in = (unsigned)fx < (unsigned)S && (unsigned)fy < (unsigned)S;
+        const int fi = fy * S + fx;
+        const uint32_t fc = in ? (uint32_t)g[fi] : (uint32_t)C_WALL;
+        const uint32_t fk = cell_kind(fc);
+        int write = -1;
+        uint32_t wcode = 0;
+        if (action == 0) {
+            a.dir = (a.dir + 3) & 3;
+        } else if (action == 1) {
+            a.dir = (a.dir + 1) & 3;
+        } else if (action == 2) {
+            if (family == NX_DYNOBS && fk == K_BALL) {
+                hit = 1;
+            } else if (walkable(fc)) {
+                a.x = fx;
+                a.y = fy;
+                goal = fk == K_GOAL;
+                lava = fk == K_LAVA;
+            }
+        } else if (action == 3) {
+            if (a.carry == 0u && (fk == K_KEY || fk == K_BALL)) {
+                a.carry = fc;
+                write = fi;
+                wcode = C_EMPTY;
+            }
+        } else if (action == 4) {
+            if (a.carry != 0u && in && fc == C_EMPTY) {
+                write = fi;
+                wcode = a.carry;
+                a.carry = 0u;
+            }
+        } else if (action == 5) {
+            if (fk == K_DOOR_LOCKED) {
+                if (a.carry != 0u && cell_kind(a.carry) == K_KEY && cell_col(a.carry) == cell_col(fc)) {
+                    write = fi;
+                    wcode = (K_DOOR_OPEN << 3) | cell_col(fc);
+                }
+            } else if (fk == K_DOOR_CLOSED) {
+                write = fi;
+                wcode = (K_DOOR_OPEN << 3) | cell_col(fc);
+            } else if (fk == K_DOOR_OPEN) {
+                write = fi;
+                wcode = (K_DOOR_CLOSED << 3) | cell_col(fc);
+            }
+        }
+        if (write >= 0) {
+            grp.sync();
+            if (grp.lane == 0) g[write] = (uint8_t)wcode;
+            grp.sync();
+        }
+    }
+    // time and truncation; reward and termination on the goal / lava / hit events
+    a.t += 1;
+    trunc = a.t >= max_steps;
+    reward = 0.0f;
+    term = 0;
+    if (goal) {
+        reward = reward_mode == NX_REWARD_MINIGRID
+                     ? __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(0.9f, (float)a.t), (float)max_steps))
+                     : 1.0f;
+        term = 1;
+    } else if (lava) {
+        reward = lava_reward;
+        term = 1;
+    } else if (hit) {
+        reward = -1.0f;
+        term = 1;
+    }
+    a.done = term || trunc;
+}
+
+// CTA-wide copy from shared to global memory; src and dst are congruent
+// modulo 16, the body moves in 16-byte vectors.
+__device__ __forceinline__ void coop_copy(uint8_t* dst, const uint8_t* src, int nbytes, int tid, int nthreads)
+{
+    const int head = min(nbytes, (int)((16u - ((uint32_t)(uintptr_t)dst & 15u)) & 15u));
+    const int body = (nbytes - head) & ~15;
+    const int tail = nbytes - head - body;
+    for (int i = tid; i < head; i += nthreads) dst[i] = src[i];
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + head);
+    for (int i = tid; i < body / 16; i += nthreads) d4[i] = s4[i];
+    for (int i = tid; i < tail; i += nthreads) dst[head + body + i] = src[head + body + i];
+}
+
+// Writes n envs' 224x224x3 images: 16-byte chunk r of an image is pixel row
+// r / 42, bytes 16 (r % 42) .. of it, i.e. view column (r % 42) / 6, part
+// (r % 42) % 6 of that tile's 96-byte row.
+__device__ __forceinline__ void coop_rgb(uint8_t* dst, const uint16_t* tiles, const uint8_t* atlas, int n, int tid,
+                                         int nthreads)
+{
+    constexpr int kChunks = NX_OBS_RGB_BYTES / 16;  // 9408
+    for (int e = 0; e < n; ++e) {
+        uint4* d4 = reinterpret_cast<uint4*>(dst + (size_t)e * NX_OBS_RGB_BYTES);
+        const uint16_t* te = tiles + e * 49;
+#pragma unroll 4
+        for (int r = tid; r < kChunks; r += nthreads) {
+            const int row = r / 42, c16 = r - row * 42;
+            const int vx = c16 / 6, part = c16 - vx * 6;
+            const int vy = row >> 5, ty = row & 31;
+            const uint32_t tile = te[vy * 7 + vx];
+            const uint4* src = reinterpret_cast<const uint4*>(atlas + (size_t)tile * 3072u + ty * 96 + part * 16);
+            __stcs(d4 + r, __ldg(src));
+        }
+    }
+}
+
+template <int G, bool RGB>
+__global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int E = p.envs_per_cta;
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    uint8_t* sgrid = smem;
+    uint8_t* sstage = smem + E * p.cell_stride;
+    uint16_t* stiles = reinterpret_cast<uint16_t*>(sstage + align16(E * NX_OBS_SYM_BYTES + 16));
+    const int gi = tid / G;
+    const Grp<G> grp(tid);
+    uint8_t* mygrid = sgrid + gi * p.cell_stride;
+
+    for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        const nx_item item = p.items[it];
+        const nx_req* rq = p.reqs + item.req;
+        const uint64_t seed = rq->seed;
+        const uint32_t gstep0 = rq->gstep, call0 = rq->call_step;
+        const int steps = p.reset_all ? 0 : min(rq->steps, p.launch_steps);
+        const int depth = rq->depth > 0 ? rq->depth : 1;
+        const uint32_t nreq = rq->n_envs;
+        const int act_mode = rq->act_mode;
+        const int8_t* actions = rq->actions;
+        uint8_t* obs_sym = rq->obs_sym;
+        uint8_t* obs_rgb = RGB ? rq->obs_rgb : nullptr;
+        float* out_reward = rq->reward;
+        uint8_t* out_term = rq->terminated;
+        uint8_t* out_trunc = rq->truncated;
+        const uint32_t reward_mode = rq->reward_mode;
+        const float lava_reward = rq->lava_reward;
+        const int n_balls = rq->n_balls;
+        float* returns = rq->returns;
+        uint64_t* digest = rq->digest;
+        uint32_t* episodes = rq->episodes;
+
+        const int n = (int)item.n_envs, S = item.size, HW = S * S, family = item.family;
+        const int max_steps = item.max_steps;
+        const bool active = gi < n;
+        const uint32_t local = item.local_begin + (uint32_t)gi;
+        const uint32_t key = rq->key_base + local;  // env index in the draw counters
+        const uint32_t env = item.env_begin + (uint32_t)gi;
+        AgentReg a;
+        float ret = 0.0f;
+        uint64_t dig = 0;
+        uint32_t eps = 0;
+
+        if (!p.reset_all) {
+            const uint8_t* src = p.grids + item.grid_offset;
+            for (int i = tid; i < n * HW; i += nthreads) {
+                const int e = i / HW, c = i - e * HW;
+                const uint8_t* b = src + (size_t)e * 3 * HW;
+                sgrid[e * p.cell_stride + c] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
+            }
+            if (active) load_agent(p.agents + env, a);
+        }
+        if (active) {
+            if (returns) ret = returns[local];
+            if (digest) dig = digest[local];
+            if (episodes) eps = episodes[local];
+        }
+        __syncthreads();
+
+        // steps == 0 with reset_all: one emission of the episode-0 start state
+        const int emissions = p.reset_all ? 1 : steps;
+        for (int s = 0; s < emissions; ++s) {
+            const uint32_t slot = (call0 + (uint32_t)s) % (uint32_t)depth;
+            const size_t row0 = (size_t)slot * nreq + item.local_begin;
+            uint8_t* sym_dst = obs_sym ? obs_sym + row0 * NX_OBS_SYM_BYTES : nullptr;
+            uint8_t* stage = sstage + ((uint32_t)(uintptr_t)sym_dst & 15u);
+            if (active) {
+                float reward = 0.0f;
+                int term = 0, trunc = 0;
+                if (p.reset_all) {
+                    a.invalid = 0;
+                    if (!reset_layout(grp, mygrid, S, family, n_balls, seed, key, 0u, a)) {
+                        if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    }
+                } else if (a.done) {
+                    // autoreset: the next episode's start, reward padding 0, action ignored
+                    if (!reset_layout(grp, mygrid, S, family, n_balls, seed, key, a.episode + 1u, a)) {
+                        if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    }
+                } else {
+                    uint32_t d[8];
+                    const bool rnd = act_mode == NX_ACT_RANDOM;
+                    const int nd = 1 + (family == NX_DYNOBS ? a.nb : 0);
+                    const uint32_t gstep = gstep0 + (uint32_t)s;
+                    const uint32_t episode = a.episode, t = (uint32_t)a.t;
+                    group_draws(grp, nd, d, [&](uint32_t k) -> uint32_t {
+                        if (k == 0) return rnd ? draw(seed, key, 0xFFFFFFFFu, gstep, PURPOSE_ACTION, 0u) : 0u;
+                        return draw(seed, key, episode, t, PURPOSE_BALL, k - 1u);
+                    });
+                    int action;
+                    if (rnd) {
+                        action = bounded(d[0], family == NX_DYNOBS ? 3u : 7u);
+                    } else {
+                        action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
+                    }
+                    env_step(grp, mygrid, S, family, max_steps, a, action, d, reward_mode, lava_reward, reward, term,
+                             trunc, p.ctl);
+                }
+                grp.sync();
+                uint8_t* my_sym = stage + gi * NX_OBS_SYM_BYTES;
+                render_view(grp, mygrid, S, a, my_sym, RGB && obs_rgb ? stiles + gi * 49 : nullptr);
+                if (grp.lane == 0) {
+                    const size_t o = (size_t)slot * nreq + local;
+                    if (out_reward) out_reward[o] = reward;
+                    if (out_term) out_term[o] = (uint8_t)term;
+                    if (out_trunc) out_trunc[o] = (uint8_t)trunc;
+                    ret += reward;
+                    eps += (uint32_t)(term || trunc);
+                }
+                if (digest) {
+                    grp.sync();
+                    if (grp.lane == 0) {
+#pragma unroll 7
+                        for (int c = 0; c < 49; ++c)
+                            dig = digest_word(dig, (uint32_t)my_sym[3 * c] | ((uint32_t)my_sym[3 * c + 1] << 8) |
+                                                       ((uint32_t)my_sym[3 * c + 2] << 16));
+                        dig = digest_word(dig, __float_as_uint(reward));
+                        dig = digest_word(dig, (uint32_t)term | ((uint32_t)trunc << 8));
+                    }
+                }
+            }
+            __syncthreads();
+            if (sym_dst) coop_copy(sym_dst, stage, n * NX_OBS_SYM_BYTES, tid, nthreads);
+            if (RGB && obs_rgb) coop_rgb(obs_rgb + row0 * NX_OBS_RGB_BYTES, stiles, p.atlas, n, tid, nthreads);
+            __syncthreads();
+        }
+
+        // write the state back
+        if (active && grp.lane == 0) {
+            store_agent(p.agents + env, a, item, item.grid_offset + (uint32_t)(gi * 3 * HW));
+            if (returns) returns[local] = ret;
+            if (digest) digest[local] = dig;
+            if (episodes) episodes[local] = eps;
+        }
+        {
+            uint8_t* dst = p.grids + item.grid_offset;
+            for (int i = tid; i < n * HW; i += nthreads) {
+                const int e = i / HW, c = i - e * HW;
+                const uint32_t code = sgrid[e * p.cell_stride + c];
+                uint8_t* b = dst + (size_t)e * 3 * HW;
+                b[c] = (uint8_t)cell_ent(code);
+                b[HW + c] = (uint8_t)cell_col(code);
+                b[2 * HW + c] = (uint8_t)cell_st(code);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Sets the per-call fields of request 0 (arguments by value, so the update is
+// stream-ordered and needs no host buffer).  gstep_mode: 0 keeps the
+// random-action step counter, 1 restarts it at 0, 2 takes v.gstep.
+__global__ void nx_configure_kernel(nx_req* r, nx_req v, int gstep_mode)
+{
+    if (gstep_mode == 0) v.gstep = r->gstep;
+    if (gstep_mode == 1) v.gstep = 0u;
+    *r = v;
+}
+
+__global__ void nx_set_steps_kernel(nx_req* r, int steps) { r->steps = steps; }
+
+// Moves every request's counters past the launch that just ran.
+__global__ void nx_advance_kernel(nx_req* reqs, int n_reqs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_reqs) {
+        const int s = reqs[i].steps;
+        reqs[i].gstep += (uint32_t)s;
+        reqs[i].call_step += (uint32_t)s;
+    }
+}
+
+// The dynamic shared-memory limit is raised once per shape by
+// nx_kernel_max_ctas (outside any stream capture); launches only launch.
+template <int G, bool RGB>
+int launch_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
+{
+    nx_step_kernel<G, RGB><<<grid, p.envs_per_cta * G, smem, st>>>(p);
+    return (int)cudaGetLastError();
+}
+
+// The dynamic shared-memory limit is a per-kernel attribute shared by every
+// context in the process, so it is always raised to the device's opt-in
+// maximum (never lowered to one context's need).
+template <int G, bool RGB>
+int occupancy_t(int threads, int smem, int* err)
+{
+    auto k = nx_step_kernel<G, RGB>;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess && smem > optin) {
+        *err = 0;
+        return 0;
+    }
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    int blocks = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, threads, smem);
+    *err = (int)e;
+    return blocks;
+}
+
+}  // namespace
+
+int nx_shape_supported(const nx_launch_shape& s)
+{
+    const int G = s.group_lanes;
+    if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return 0;
+    if (s.envs_per_cta < 1 || s.envs_per_cta * G > kMaxThreads) return 0;
+    if ((s.envs_per_cta * G) % 32 != 0) return 0;
+    return 1;
+}
+
+int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride)
+{
+    const int E = s.envs_per_cta;
+    int b = E * cell_stride + align16(E * NX_OBS_SYM_BYTES + 16);
+    if (s.rgb) b += align16(E * 49 * 2);
+    return b;
+}
+
+#define NX_DISPATCH(G_, FN, ...)                                                  \
+    switch (G_) {                                                                 \
+    case 1: return s.rgb ? FN<1, true>(__VA_ARGS__) : FN<1, false>(__VA_ARGS__);   \
+    case 2: return s.rgb ? FN<2, true>(__VA_ARGS__) : FN<2, false>(__VA_ARGS__);   \
+    case 4: return s.rgb ? FN<4, true>(__VA_ARGS__) : FN<4, false>(__VA_ARGS__);   \
+    case 8: return s.rgb ? FN<8, true>(__VA_ARGS__) : FN<8, false>(__VA_ARGS__);   \
+    case 16: return s.rgb ? FN<16, true>(__VA_ARGS__) : FN<16, false>(__VA_ARGS__); \
+    case 32: return s.rgb ? FN<32, true>(__VA_ARGS__) : FN<32, false>(__VA_ARGS__); \
+    default: return -1;                                                           \
+    }
+
+int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err)
+{
+    const int smem = nx_kernel_smem_bytes(s, cell_stride);
+    const int threads = s.envs_per_cta * s.group_lanes;
+    NX_DISPATCH(s.group_lanes, occupancy_t, threads, smem, err)
+}
+
+int nx_launch_step_kernel(const nx_launch_shape& s, const nx_kparams& p, int grid, void* stream)
+{
+    const int smem = nx_kernel_smem_bytes(s, p.cell_stride);
+    cudaStream_t st = (cudaStream_t)stream;
+    NX_DISPATCH(s.group_lanes, launch_t, p, grid, smem, st)
+}
+
+int nx_launch_configure(nx_req* r, const nx_req& v, int gstep_mode, void* stream)
+{
+    nx_configure_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(r, v, gstep_mode);
+    return (int)cudaGetLastError();
+}
+
+int nx_launch_set_steps(nx_req* r, int steps, void* stream)
+{
+    nx_set_steps_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(r, steps);
+    return (int)cudaGetLastError();
+}
+
+int nx_launch_advance(nx_req* reqs, int n_reqs, void* stream)
+{
+    if (n_reqs <= 0) return 0;
+    nx_advance_kernel<<<(n_reqs + 127) / 128, 128, 0, (cudaStream_t)stream>>>(reqs, n_reqs);
+    return (int)cudaGetLastError();
+}

@@ -1,0 +1,429 @@
+"""Thin ctypes binding of libnavixgb (include/navixgb.h).
+
+Functions keep the C names (``nx_create``, ``nx_reset``, ``nx_step``,
+``nx_rollout`` ...) and only marshal arguments; every step of the
+environment runs in the CUDA kernels of the library.  PyTorch provides the
+device memory (its caching allocator, passed in as the library's allocator
+callbacks, and output tensors) and the stream.  There is no CPU fallback: if
+the library has not been built this module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libnavixgb.so")
+
+NX_OK, NX_PENDING = 0, 1
+NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET, NX_E_STATE = -1, -2, -3, -4, -5, -6, -7
+NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS = range(5)
+NX_OBS_SYM, NX_OBS_RGB = 1, 2
+NX_ACT_BUFFER, NX_ACT_RANDOM = 0, 1
+NX_REWARD_MARKOV, NX_REWARD_MINIGRID = 0, 1
+OBS_SYM_BYTES, OBS_RGB_BYTES = 147, 150528
+ATLAS_BYTES = 397 * 3072
+AGENT_BYTES = 32
+FAMILIES = {"empty": NX_EMPTY, "doorkey": NX_DOORKEY, "fourrooms": NX_FOURROOMS, "lavagap": NX_LAVAGAP,
+            "dynobs": NX_DYNOBS}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class nx_desc(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("max_steps", ctypes.c_int32)]
+
+
+class nx_options(ctypes.Structure):
+    _fields_ = [("obs_flags", ctypes.c_uint32), ("reward_mode", ctypes.c_int32), ("lava_reward", ctypes.c_float),
+                ("n_balls", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("group_lanes", ctypes.c_int32), ("envs_per_cta", ctypes.c_int32), ("staging", ctypes.c_int32),
+                ("atlas", ctypes.POINTER(ctypes.c_uint8)), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", ctypes.c_void_p), ("env_index_base", ctypes.c_uint32)]
+
+
+class nx_out(ctypes.Structure):
+    _fields_ = [("obs_sym", ctypes.c_void_p), ("obs_rgb", ctypes.c_void_p), ("reward", ctypes.c_void_p),
+                ("terminated", ctypes.c_void_p), ("truncated", ctypes.c_void_p), ("depth", ctypes.c_int32)]
+
+
+class nx_info(ctypes.Structure):
+    _fields_ = [("group_lanes", ctypes.c_int32), ("envs_per_cta", ctypes.c_int32), ("staging", ctypes.c_int32),
+                ("n_items", ctypes.c_int32), ("grid_ctas", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("steps_per_launch", ctypes.c_int32), ("n_envs", ctypes.c_int32), ("n_families", ctypes.c_int32),
+                ("state_bytes", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t)]
+
+
+# every symbol include/navixgb.h declares, with its signature
+_P = ctypes.POINTER
+_vp, _i32, _u32, _u64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
+SIGNATURES = {
+    "nx_options_default": (None, [_P(nx_options)]),
+    "nx_create": (_i32, [_P(_vp), _i32, _i32, _i32, _u64, _P(nx_options), _vp]),
+    "nx_create_mixed": (_i32, [_P(_vp), _P(nx_desc), _i32, _u64, _P(nx_options), _vp]),
+    "nx_reset": (_i32, [_vp, _P(nx_out)]),
+    "nx_step": (_i32, [_vp, _vp, _P(nx_out)]),
+    "nx_rollout": (_i32, [_vp, _i32, _i32, _vp, _P(nx_out)]),
+    "nx_rollout_per_family": (_i32, [_vp, _i32, _i32, _vp, _P(nx_out)]),
+    "nx_rollout_host": (_i32, [_vp, _i32, _i32, _vp, _P(nx_out)]),
+    "nx_state_bytes": (_sz, [_vp]),
+    "nx_get_state": (_i32, [_vp, _vp, _sz]),
+    "nx_set_state": (_i32, [_vp, _vp, _sz]),
+    "nx_sync": (_i32, [_vp, ctypes.c_double]),
+    "nx_device_flags": (_i32, [_vp, _P(_u32)]),
+    "nx_get_info": (_i32, [_vp, _P(nx_info)]),
+    "nx_profile_begin": (_i32, [_vp]),
+    "nx_profile_end": (_i32, [_vp, _P(ctypes.c_double), _P(ctypes.c_int64)]),
+    "nx_launch_counts": (_i32, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
+    "nx_destroy": (None, [_vp]),
+    "nx_status_str": (ctypes.c_char_p, [_i32]),
+    "nx_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Loads libnavixgb.so; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class NavixError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def check(status, env_handle=None):
+    if status < 0:
+        L = lib()
+        msg = L.nx_last_error(env_handle).decode() if env_handle is not None else L.nx_last_error(None).decode()
+        raise NavixError(status, f"{L.nx_status_str(status).decode()}: {msg}")
+    return status
+
+
+# --- C-named wrappers (argument marshalling only) ---------------------------
+
+def nx_options_default() -> nx_options:
+    o = nx_options()
+    lib().nx_options_default(ctypes.byref(o))
+    return o
+
+
+def nx_create(family, size, n_envs, seed, opts=None, stream=0):
+    h = ctypes.c_void_p()
+    st = lib().nx_create(ctypes.byref(h), family, size, n_envs, seed, ctypes.byref(opts) if opts else None,
+                         ctypes.c_void_p(stream))
+    check(st)
+    return h
+
+
+def nx_create_mixed(descs, seed, opts=None, stream=0):
+    arr = (nx_desc * len(descs))(*[nx_desc(int(f), int(s), int(s), int(m)) for f, s, m in descs])
+    h = ctypes.c_void_p()
+    st = lib().nx_create_mixed(ctypes.byref(h), arr, len(descs), seed, ctypes.byref(opts) if opts else None,
+                               ctypes.c_void_p(stream))
+    check(st)
+    return h
+
+
+def nx_reset(h, out):
+    return check(lib().nx_reset(h, ctypes.byref(out) if out is not None else None), h)
+
+
+def nx_step(h, actions_ptr, out):
+    return check(lib().nx_step(h, ctypes.c_void_p(actions_ptr or None), ctypes.byref(out) if out is not None else None), h)
+
+
+def nx_rollout(h, n_steps, act_mode, actions_ptr, out):
+    return check(lib().nx_rollout(h, n_steps, act_mode, ctypes.c_void_p(actions_ptr or None),
+                                  ctypes.byref(out) if out is not None else None), h)
+
+
+def nx_rollout_per_family(h, n_steps, act_mode, actions_ptr, out):
+    return check(lib().nx_rollout_per_family(h, n_steps, act_mode, ctypes.c_void_p(actions_ptr or None),
+                                             ctypes.byref(out) if out is not None else None), h)
+
+
+def nx_rollout_host(h, n_steps, act_mode, actions_ptr, out):
+    return check(lib().nx_rollout_host(h, n_steps, act_mode, ctypes.c_void_p(actions_ptr or None),
+                                       ctypes.byref(out) if out is not None else None), h)
+
+
+def nx_state_bytes(h):
+    return int(lib().nx_state_bytes(h))
+
+
+def nx_get_state(h) -> bytes:
+    n = nx_state_bytes(h)
+    buf = (ctypes.c_uint8 * n)()
+    check(lib().nx_get_state(h, buf, n), h)
+    return bytes(buf)
+
+
+def nx_set_state(h, data: bytes):
+    buf = (ctypes.c_uint8 * len(data)).from_buffer_copy(data)
+    return check(lib().nx_set_state(h, buf, len(data)), h)
+
+
+def nx_sync(h, timeout_s=0.0):
+    return check(lib().nx_sync(h, timeout_s), h)
+
+
+def nx_device_flags(h):
+    f = ctypes.c_uint32()
+    check(lib().nx_device_flags(h, ctypes.byref(f)), h)
+    return int(f.value)
+
+
+def nx_get_info(h) -> dict:
+    i = nx_info()
+    check(lib().nx_get_info(h, ctypes.byref(i)), h)
+    return {k: getattr(i, k) for k, _ in nx_info._fields_}
+
+
+def nx_profile_begin(h):
+    return check(lib().nx_profile_begin(h), h)
+
+
+def nx_profile_end(h):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    check(lib().nx_profile_end(h, ctypes.byref(ms), ctypes.byref(n)), h)
+    return float(ms.value), int(n.value)
+
+
+def nx_launch_counts(h):
+    a = ctypes.c_int64()
+    b = ctypes.c_int64()
+    check(lib().nx_launch_counts(h, ctypes.byref(a), ctypes.byref(b)), h)
+    return int(a.value), int(b.value)
+
+
+def nx_destroy(h):
+    lib().nx_destroy(h)
+
+
+# --- snapshot parsing (format documented in navixgb.h) -----------------------
+
+def parse_state(data: bytes) -> dict:
+    assert data[:4] == b"NXST"
+    n = int.from_bytes(data[8:12], "little")
+    gstep = int.from_bytes(data[12:16], "little")
+    pool = int.from_bytes(data[16:24], "little")
+    ag = np.frombuffer(data, np.uint8, count=n * AGENT_BYTES, offset=64).reshape(n, AGENT_BYTES)
+    grids = np.frombuffer(data, np.uint8, count=pool, offset=64 + n * AGENT_BYTES)
+    envs = []
+    for i in range(n):
+        a = ag[i]
+        size = int(a[25])
+        off = int(a[28:32].view(np.uint32)[0])
+        hw = size * size
+        nb = int(a[7])
+        envs.append({
+            "x": int(a[0]), "y": int(a[1]), "dir": int(a[2]), "carry_ent": int(a[3]), "carry_col": int(a[4]),
+            "done": int(a[5]), "invalid": int(a[6]), "n_balls": nb,
+            "t": int(a[8:10].view(np.uint16)[0]), "max_steps": int(a[10:12].view(np.uint16)[0]),
+            "episode": int(a[12:16].view(np.uint32)[0]),
+            "ball_x": [int(v) for v in a[16:16 + nb]], "ball_y": [int(v) for v in a[20:20 + nb]],
+            "family": int(a[24]), "height": size, "width": size,
+            "ent": grids[off:off + hw].tobytes(), "col": grids[off + hw:off + 2 * hw].tobytes(),
+            "st": grids[off + 2 * hw:off + 3 * hw].tobytes(),
+        })
+    return {"n": n, "gstep": gstep, "envs": envs}
+
+
+# --- convenience class over torch tensors ------------------------------------
+
+class Env:
+    """A batch of environments on the current CUDA device.
+
+    ``descs`` is a list of (family, size[, max_steps]) per env, or use
+    ``family``/``size``/``n_envs`` for a uniform batch.  Outputs are torch
+    tensors on the device, shaped [depth, N, ...] for rollouts and [N, ...]
+    for reset/step.
+    """
+
+    def __init__(self, family=NX_EMPTY, size=5, n_envs=1, seed=0, *, descs=None, obs_sym=True, obs_rgb=False,
+                 atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
+                 autotune=True, group_lanes=0, envs_per_cta=0, env_index_base=0, torch_allocator=True):
+        import torch
+
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("navixgb needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.current_stream(self.device)
+        o = nx_options_default()
+        o.obs_flags = (NX_OBS_SYM if obs_sym else 0) | (NX_OBS_RGB if obs_rgb else 0)
+        o.reward_mode = reward_mode
+        o.lava_reward = lava_reward
+        o.n_balls = n_balls
+        o.steps_per_launch = steps_per_launch
+        o.autotune = 1 if autotune else 0
+        o.group_lanes = group_lanes
+        o.envs_per_cta = envs_per_cta
+        o.env_index_base = env_index_base
+        self._atlas = None
+        if obs_rgb:
+            if atlas is None:
+                from . import inputs
+                atlas = inputs.atlas()
+            self._atlas = np.ascontiguousarray(atlas, np.uint8).reshape(-1)
+            assert self._atlas.size == ATLAS_BYTES
+            o.atlas = self._atlas.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        self._cbs = None
+        if torch_allocator:
+            dev, strm = self.device.index, self.stream.cuda_stream
+
+            def _alloc(size, _user):
+                return torch.cuda.caching_allocator_alloc(int(size), dev, strm)
+
+            def _free(ptr, _user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cbs = (ALLOC_FN(_alloc), FREE_FN(_free))
+            o.alloc, o.free = self._cbs
+        self.opts = o
+        self.obs_sym, self.obs_rgb = obs_sym, obs_rgb
+        if descs is None:
+            self.n = int(n_envs)
+            self.h = nx_create(int(family), int(size), self.n, int(seed), o, self.stream.cuda_stream)
+        else:
+            d = [(f, s, (m[0] if m else 0)) for f, s, *m in descs]
+            self.n = len(d)
+            self.h = nx_create_mixed(d, int(seed), o, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            nx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_out(self, depth=None):
+        torch = self.torch
+        lead = () if depth is None else (depth,)
+        n = self.n
+        o = {
+            "obs_sym": torch.empty(lead + (n, 7, 7, 3), dtype=torch.uint8, device=self.device) if self.obs_sym else None,
+            "obs_rgb": torch.empty(lead + (n, 224, 224, 3), dtype=torch.uint8, device=self.device) if self.obs_rgb else None,
+            "reward": torch.empty(lead + (n,), dtype=torch.float32, device=self.device),
+            "terminated": torch.empty(lead + (n,), dtype=torch.uint8, device=self.device),
+            "truncated": torch.empty(lead + (n,), dtype=torch.uint8, device=self.device),
+        }
+        return o
+
+    @staticmethod
+    def out_struct(o, depth=1):
+        s = nx_out()
+        for k in ("obs_sym", "obs_rgb", "reward", "terminated", "truncated"):
+            t = o.get(k)
+            setattr(s, k, t.data_ptr() if t is not None else None)
+        s.depth = depth
+        return s
+
+    def reset(self, out=None):
+        out = out or self.alloc_out()
+        nx_reset(self.h, self.out_struct(out))
+        return out
+
+    def step(self, actions=None, out=None):
+        out = out or self.alloc_out()
+        ptr = None
+        if actions is not None:
+            assert actions.dtype == self.torch.int8 and actions.is_cuda and actions.numel() == self.n
+            ptr = actions.data_ptr()
+        nx_step(self.h, ptr, self.out_struct(out))
+        return out
+
+    def rollout(self, n_steps, actions=None, depth=None, out=None, per_family=False):
+        depth = depth or n_steps
+        out = out or self.alloc_out(depth)
+        ptr, mode = None, NX_ACT_RANDOM
+        if actions is not None:
+            assert actions.dtype == self.torch.int8 and actions.is_cuda and actions.shape == (n_steps, self.n)
+            ptr, mode = actions.data_ptr(), NX_ACT_BUFFER
+        fn = nx_rollout_per_family if per_family else nx_rollout
+        fn(self.h, n_steps, mode, ptr, self.out_struct(out, depth))
+        return out
+
+    def rollout_host(self, n_steps, actions=None, out=None):
+        """Host numpy in, host numpy out (pinned numpy-backed torch tensors may be passed as ``out``)."""
+        n = self.n
+        if out is None:
+            out = {
+                "obs_sym": np.empty((n_steps, n, 7, 7, 3), np.uint8) if self.obs_sym else None,
+                "obs_rgb": np.empty((n_steps, n, 224, 224, 3), np.uint8) if self.obs_rgb else None,
+                "reward": np.empty((n_steps, n), np.float32),
+                "terminated": np.empty((n_steps, n), np.uint8),
+                "truncated": np.empty((n_steps, n), np.uint8),
+            }
+        s = nx_out()
+        for k in ("obs_sym", "obs_rgb", "reward", "terminated", "truncated"):
+            a = out.get(k)
+            if a is None:
+                setattr(s, k, None)
+            elif isinstance(a, np.ndarray):
+                setattr(s, k, a.ctypes.data)
+            else:
+                setattr(s, k, a.data_ptr())
+        s.depth = n_steps
+        ptr, mode = None, NX_ACT_RANDOM
+        if actions is not None:
+            a = actions if isinstance(actions, np.ndarray) else actions.numpy()
+            assert a.dtype == np.int8 and a.shape == (n_steps, n) and a.flags["C_CONTIGUOUS"]
+            ptr, mode = a.ctypes.data, NX_ACT_BUFFER
+        nx_rollout_host(self.h, n_steps, mode, ptr, s)
+        return out
+
+    def state(self) -> dict:
+        return parse_state(nx_get_state(self.h))
+
+    def state_bytes(self) -> bytes:
+        return nx_get_state(self.h)
+
+    def set_state(self, data: bytes):
+        nx_set_state(self.h, data)
+
+    def flags(self) -> int:
+        return nx_device_flags(self.h)
+
+    def sync(self, timeout_s=0.0):
+        return nx_sync(self.h, timeout_s)
+
+    def info(self) -> dict:
+        return nx_get_info(self.h)
+
+    def profile_begin(self):
+        nx_profile_begin(self.h)
+
+    def profile_end(self):
+        """(summed step-kernel device ms, number of step-kernel launches) since profile_begin."""
+        return nx_profile_end(self.h)
+
+    def launch_counts(self):
+        """(step-kernel launches, all kernel launches) so far."""
+        return nx_launch_counts(self.h)

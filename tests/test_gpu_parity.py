@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA path (through the C-ABI binding) against the CPU oracle,
+byte for byte, on the same seeded inputs.
+
+The environment is all integer work plus float32 rewards computed in a fixed
+operation order, so every comparison is exact (tolerance 0): observations,
+rewards, termination/truncation flags and the full state snapshot.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2407_19396_gb300 import inputs  # noqa: E402
+from tests.gpu_util import (assert_outputs_equal, assert_states_equal, mixed_descs, oracle_batch_for,  # noqa: E402
+                            to_np)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2407_19396_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def nxmod():
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    return nx
+
+
+ALL_FAMILIES = [(O.EMPTY, 5), (O.EMPTY, 8), (O.EMPTY, 16), (O.DOORKEY, 5), (O.DOORKEY, 8), (O.DOORKEY, 16),
+                (O.FOURROOMS, 19), (O.FOURROOMS, 9), (O.LAVAGAP, 5), (O.LAVAGAP, 7), (O.DYNOBS, 5), (O.DYNOBS, 16),
+                (O.DOORKEY, 19), (O.EMPTY, 19), (O.LAVAGAP, 13)]
+
+
+@pytest.mark.parametrize("family,size", ALL_FAMILIES)
+def test_reset_matches_oracle(family, size):
+    nx = nxmod()
+    n = 37  # ragged against every envs-per-CTA choice
+    env = nx.Env(family, size, n, seed=11, autotune=False)
+    out = env.reset()
+    ob = O.Batch([family] * n, [size] * n, seed=11)
+    oo = ob.reset()
+    assert_outputs_equal(out, oo, what="reset")
+    assert_states_equal(env.state()["envs"], ob, what="reset")
+    env.close()
+
+
+@pytest.mark.parametrize("lanes,envs", [(1, 64), (2, 64), (4, 32), (8, 16), (16, 8), (32, 8), (8, 32), (1, 256)])
+def test_rollout_every_shape_every_step(lanes, envs):
+    nx = nxmod()
+    descs = mixed_descs(150, [(O.EMPTY, 5), (O.DOORKEY, 8), (O.FOURROOMS, 19), (O.LAVAGAP, 7), (O.DYNOBS, 8),
+                              (O.DOORKEY, 16)])
+    env = nx.Env(descs=descs, seed=5, group_lanes=lanes, envs_per_cta=envs, autotune=False, steps_per_launch=64)
+    env.reset()
+    T = 300
+    out = env.rollout(T)
+    ob = oracle_batch_for(descs, 5)
+    ob.reset()
+    oo = ob.rollout(T)
+    assert_outputs_equal(out, oo, what=f"G={lanes} E={envs}")
+    assert_states_equal(env.state()["envs"], ob, what=f"G={lanes} E={envs}")
+    env.close()
+
+
+def test_config_empty5x5_64envs_1000steps_full():
+    nx = nxmod()
+    env = nx.Env(O.EMPTY, 5, 64, seed=0)
+    r = env.reset()
+    out = env.rollout(1000)
+    ob = O.Batch([O.EMPTY] * 64, [5] * 64, seed=0)
+    assert_outputs_equal(r, ob.reset(), what="reset")
+    assert_outputs_equal(out, ob.rollout(1000), what="Empty-5x5")
+    assert_states_equal(env.state()["envs"], ob, what="Empty-5x5")
+    assert env.flags() == 0
+    env.close()
+
+
+def test_config_doorkey8x8_4096envs_1000steps_full():
+    nx = nxmod()
+    n, T = 4096, 1000
+    env = nx.Env(O.DOORKEY, 8, n, seed=1)
+    r = env.reset()
+    out = env.rollout(T)
+    ob = O.Batch([O.DOORKEY] * n, [8] * n, seed=1)
+    assert_outputs_equal(r, ob.reset(), what="reset")
+    oo = ob.rollout(T)
+    assert_outputs_equal(out, oo, what="DoorKey-8x8")
+    assert_states_equal(env.state()["envs"], ob, what="DoorKey-8x8")
+    env.close()
+
+
+MIXED = [(O.EMPTY, 5), (O.EMPTY, 8), (O.EMPTY, 16), (O.DOORKEY, 16), (O.FOURROOMS, 19), (O.LAVAGAP, 7)]
+
+
+def _mixed_sample(descs, per_block=48):
+    """Envs to check: both ends of every block, and a spread inside it."""
+    idx = set()
+    start = 0
+    while start < len(descs):
+        end = start
+        while end < len(descs) and descs[end] == descs[start]:
+            end += 1
+        for i in list(range(start, min(start + 8, end))) + list(range(max(start, end - 8), end)):
+            idx.add(i)
+        for i in np.linspace(start, end - 1, per_block).astype(int):
+            idx.add(int(i))
+        start = end
+    return sorted(idx)
+
+
+def test_config_mixed_65536envs_2048steps_sampled():
+    nx = nxmod()
+    n, T, C = 65536, 2048, 128
+    descs = mixed_descs(n, MIXED)
+    env = nx.Env(descs=descs, seed=2, steps_per_launch=C)
+    env.reset()
+    sample = _mixed_sample(descs)
+    ob = oracle_batch_for(descs, 2, indices=sample)
+    ob.reset()
+    sel = torch.tensor(sample, device="cuda")
+    out = env.alloc_out(C)
+    for chunk in range(T // C):
+        env.rollout(C, depth=C, out=out)
+        got = {k: to_np(v.index_select(1, sel)) for k, v in out.items() if v is not None}
+        want = ob.rollout(C)
+        assert_outputs_equal(got, want, what=f"mixed chunk {chunk}")
+    st = env.state()["envs"]
+    assert_states_equal(st, ob, indices=sample, what="mixed final")
+    env.close()
+
+
+def test_config_rgb_dynobs16_8192envs_512steps():
+    nx = nxmod()
+    atlas = inputs.atlas()
+    n, T, D = 8192, 512, 8
+    env = nx.Env(O.DYNOBS, 16, n, seed=3, obs_rgb=True, atlas=atlas)
+    env.reset()
+    out = env.rollout(T, depth=D)
+    torch.cuda.synchronize()
+    # symbolic outputs of every env for the last D steps, and the final state of every env
+    ob = O.Batch([O.DYNOBS] * n, [16] * n, seed=3)
+    ob.reset()
+    ob.rollout(T - D, sym=False)
+    oo = ob.rollout(D)
+    slots = [(T - D + i) % D for i in range(D)]
+    got = {k: to_np(out[k])[slots] for k in ("obs_sym", "reward", "terminated", "truncated")}
+    assert_outputs_equal(got, oo, what="DynObs-16 last steps")
+    assert_states_equal(env.state()["envs"], ob, what="DynObs-16 final")
+    # RGB images of a sample of envs (both ends and a spread) for the last D steps
+    sample = sorted(set(list(range(8)) + list(range(n - 8, n)) + list(np.linspace(0, n - 1, 48).astype(int))))
+    osb = oracle_batch_for([(O.DYNOBS, 16)] * n, 3, indices=sample)
+    osb.reset(sym=False)
+    osb.rollout(T - D, sym=False)
+    orgb = osb.rollout(D, sym=True, rgb=True, atlas=atlas)
+    rgb = to_np(out["obs_rgb"][:, sample])[slots]
+    np.testing.assert_array_equal(rgb, orgb["obs_rgb"])
+    env.close()
+
+
+def test_rgb_every_step_small():
+    nx = nxmod()
+    atlas = inputs.atlas()
+    descs = mixed_descs(40, [(O.DYNOBS, 6), (O.DOORKEY, 8), (O.FOURROOMS, 11)])
+    env = nx.Env(descs=descs, seed=21, obs_rgb=True, atlas=atlas, autotune=False, steps_per_launch=16)
+    r = env.reset()
+    out = env.rollout(48)
+    ob = oracle_batch_for(descs, 21)
+    orr = ob.reset(rgb=True, atlas=atlas)
+    oo = ob.rollout(48, rgb=True, atlas=atlas)
+    assert_outputs_equal(r, orr, keys=("obs_sym", "obs_rgb"), what="rgb reset")
+    assert_outputs_equal(out, oo, keys=("obs_sym", "obs_rgb", "reward", "terminated", "truncated"), what="rgb")
+    env.close()
+
+
+def test_per_family_form_equals_persistent_form():
+    nx = nxmod()
+    descs = mixed_descs(600, MIXED)
+    a = nx.Env(descs=descs, seed=9, autotune=False)
+    b = nx.Env(descs=descs, seed=9, autotune=False)
+    a.reset()
+    b.reset()
+    T = 260
+    oa = a.rollout(T)
+    obb = b.rollout(T, per_family=True)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        assert torch.equal(oa[k], obb[k]), k
+    ob = oracle_batch_for(descs, 9)
+    ob.reset()
+    assert_outputs_equal(oa, ob.rollout(T), what="persistent")
+    assert a.state_bytes() == b.state_bytes()
+    a.close()
+    b.close()
+
+
+def test_autotuned_shape_gives_identical_results():
+    nx = nxmod()
+    descs = mixed_descs(2000, MIXED)
+    a = nx.Env(descs=descs, seed=4, autotune=True)
+    b = nx.Env(descs=descs, seed=4, autotune=False, group_lanes=32, envs_per_cta=4)
+    a.reset()
+    b.reset()
+    oa = a.rollout(200)
+    obb = b.rollout(200)
+    info = a.info()
+    assert info["group_lanes"] in (1, 2, 4, 8, 16, 32) and info["grid_ctas"] >= 1
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        assert torch.equal(oa[k], obb[k]), k
+    assert a.state_bytes()[64:] == b.state_bytes()[64:]
+    a.close()
+    b.close()
+
+
+def test_buffer_actions_with_invalid_entries():
+    nx = nxmod()
+    descs = mixed_descs(70, [(O.DOORKEY, 6), (O.DYNOBS, 7), (O.EMPTY, 9)])
+    T = 400
+    acts = inputs.random_actions(31, (T, 70), n_actions=7, invalid_fraction=0.02)
+    env = nx.Env(descs=descs, seed=31, autotune=False)
+    env.reset()
+    assert env.flags() == 0
+    out = env.rollout(T, actions=torch.from_numpy(acts).cuda())
+    ob = oracle_batch_for(descs, 31)
+    ob.reset()
+    assert_outputs_equal(out, ob.rollout(T, actions=acts), what="buffered actions")
+    assert_states_equal(env.state()["envs"], ob, what="buffered actions")
+    assert env.flags() & 1
+    env.close()
+
+
+def test_single_steps_equal_rollout():
+    nx = nxmod()
+    a = nx.Env(O.DOORKEY, 5, 33, seed=8, autotune=False)
+    b = nx.Env(O.DOORKEY, 5, 33, seed=8, autotune=False)
+    a.reset()
+    b.reset()
+    steps = [a.step() for _ in range(50)]
+    ro = b.rollout(50)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        assert torch.equal(torch.stack([s[k] for s in steps]), ro[k]), k
+    a.close()
+    b.close()
+
+
+def test_snapshot_resume_is_bit_identical():
+    nx = nxmod()
+    descs = mixed_descs(90, [(O.FOURROOMS, 19), (O.DYNOBS, 8), (O.DOORKEY, 8)])
+    a = nx.Env(descs=descs, seed=13, autotune=False)
+    a.reset()
+    a.rollout(77)
+    snap = a.state_bytes()
+    tail_a = a.rollout(150)
+    b = nx.Env(descs=descs, seed=13, autotune=False)
+    b.set_state(snap)
+    tail_b = b.rollout(150)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        assert torch.equal(tail_a[k], tail_b[k]), k
+    assert a.state_bytes() == b.state_bytes()
+    a.close()
+    b.close()
+
+
+def test_two_shards_reproduce_one_batch():
+    nx = nxmod()
+    n = 300
+    whole = nx.Env(O.DOORKEY, 8, n, seed=17, autotune=False)
+    lo = nx.Env(O.DOORKEY, 8, 120, seed=17, autotune=False, env_index_base=0)
+    hi = nx.Env(O.DOORKEY, 8, n - 120, seed=17, autotune=False, env_index_base=120)
+    for e in (whole, lo, hi):
+        e.reset()
+    ow, ol, oh = whole.rollout(200), lo.rollout(200), hi.rollout(200)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        assert torch.equal(ow[k], torch.cat([ol[k], oh[k]], dim=1)), k
+    for e in (whole, lo, hi):
+        e.close()
+
+
+def test_host_buffer_rollout_equals_device_rollout():
+    nx = nxmod()
+    descs = mixed_descs(500, MIXED)
+    a = nx.Env(descs=descs, seed=23, autotune=False, steps_per_launch=32)
+    b = nx.Env(descs=descs, seed=23, autotune=False, steps_per_launch=32)
+    a.reset()
+    b.reset()
+    T = 150
+    dev = a.rollout(T)
+    host = b.rollout_host(T)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        np.testing.assert_array_equal(to_np(dev[k]), host[k], err_msg=k)
+    acts = inputs.random_actions(3, (T, 500))
+    c = nx.Env(descs=descs, seed=23, autotune=False, steps_per_launch=32)
+    c.reset()
+    hc = c.rollout_host(T, actions=acts)
+    ob = oracle_batch_for(descs, 23)
+    ob.reset()
+    assert_outputs_equal(hc, ob.rollout(T, actions=acts), what="host rollout, buffered actions")
+    for e in (a, b, c):
+        e.close()
+
+
+@pytest.mark.parametrize("reward_mode,lava", [(1, 0.0), (0, -1.0), (1, -1.0)])
+def test_reward_variants(reward_mode, lava):
+    nx = nxmod()
+    descs = mixed_descs(120, [(O.EMPTY, 5), (O.LAVAGAP, 5), (O.DYNOBS, 5)])
+    env = nx.Env(descs=descs, seed=29, reward_mode=reward_mode, lava_reward=lava, autotune=False)
+    env.reset()
+    out = env.rollout(500)
+    ob = oracle_batch_for(descs, 29, reward_mode=reward_mode, lava_reward=lava)
+    ob.reset()
+    oo = ob.rollout(500)
+    assert_outputs_equal(out, oo, what=f"reward mode {reward_mode} lava {lava}")
+    r = to_np(out["reward"])
+    assert (r[(r != 0)] != 1.0).any() or reward_mode == 0
+    env.close()
+
+
+def test_nballs_option_and_small_dynobs():
+    nx = nxmod()
+    for nb in (0, 1, 3):
+        env = nx.Env(O.DYNOBS, 6, 40, seed=nb, n_balls=nb, autotune=False)
+        env.reset()
+        out = env.rollout(200)
+        ob = O.Batch([O.DYNOBS] * 40, [6] * 40, seed=nb, n_balls=nb)
+        ob.reset()
+        assert_outputs_equal(out, ob.rollout(200), what=f"n_balls={nb}")
+        env.close()
+
+
+def test_sync_reports_ok_and_timeout_bound():
+    nx = nxmod()
+    env = nx.Env(O.EMPTY, 8, 1000, seed=1, autotune=False)
+    env.reset()
+    env.rollout(64)
+    assert env.sync(timeout_s=30.0) == 0
+    env.close()
