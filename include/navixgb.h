@@ -220,6 +220,32 @@ nx_status nx_get_info(const nx_env* env, nx_info* info);
  * nx_launch_counts returns the cumulative number of step-kernel launches and
  * of all kernels this context has enqueued (graph replays count their
  * nodes); it never blocks. */
+/* nx_rollout_noalloc: reset + rollout for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this exists for users of the
+ * library whose process cannot call cudaMalloc: another runtime may already
+ * hold nearly all of the device's memory in its own pool, or the calling loop
+ * may not afford cudaMalloc's implicit device synchronisation.
+ *
+ * It does what nx_create(family, size, n_envs, seed, default options) +
+ * nx_reset(NULL) + nx_rollout(n_steps, act_mode, d_actions_TN, traj) do, with
+ * identical outputs, but allocates nothing: the state, work list and request
+ * record live in one fixed device array of NX_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  The caller
+ * passes the actions (device int8 [n_steps, n_envs], or NULL with
+ * NX_ACT_RANDOM) and the outputs (device, [depth, n_envs, ...]; obs_rgb must
+ * be NULL).  Enqueued on cuda_stream, asynchronous.
+ *
+ * Limit: n_envs x (3 size^2 + 32) bytes plus a small work list must fit the
+ * array; larger requests return NX_E_INVAL with the sizes in
+ * nx_last_error(NULL).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call uses the same array and re-initialises what
+ * must start from zero, so two calls that overlap on the GPU (different
+ * streams, or different host threads) race and corrupt each other. */
+#define NX_NOALLOC_SCRATCH_BYTES (4u << 20)
+nx_status nx_rollout_noalloc(int32_t family, int32_t size, int32_t n_envs, uint64_t seed, int32_t n_steps,
+                             int32_t act_mode, const int8_t* d_actions_TN, const nx_out* traj, void* cuda_stream);
+
 nx_status nx_profile_begin(nx_env* env);
 nx_status nx_profile_end(nx_env* env, double* kernel_ms, int64_t* step_launches);
 nx_status nx_launch_counts(const nx_env* env, int64_t* step_launches, int64_t* all_launches);

@@ -77,6 +77,7 @@ SIGNATURES = {
     "nx_sync": (_i32, [_vp, ctypes.c_double]),
     "nx_device_flags": (_i32, [_vp, _P(_u32)]),
     "nx_get_info": (_i32, [_vp, _P(nx_info)]),
+    "nx_rollout_noalloc": (_i32, [_i32, _i32, _i32, _u64, _i32, _i32, _vp, _P(nx_out), _vp]),
     "nx_profile_begin": (_i32, [_vp]),
     "nx_profile_end": (_i32, [_vp, _P(ctypes.c_double), _P(ctypes.c_int64)]),
     "nx_launch_counts": (_i32, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
@@ -198,6 +199,13 @@ def nx_get_info(h) -> dict:
     i = nx_info()
     check(lib().nx_get_info(h, ctypes.byref(i)), h)
     return {k: getattr(i, k) for k, _ in nx_info._fields_}
+
+
+def nx_rollout_noalloc(family, size, n_envs, seed, n_steps, act_mode, actions_ptr, out, stream=0):
+    """Reset + rollout that allocates no device memory (see navixgb.h)."""
+    return check(lib().nx_rollout_noalloc(family, size, n_envs, seed, n_steps, act_mode,
+                                          ctypes.c_void_p(actions_ptr or None),
+                                          ctypes.byref(out) if out is not None else None, ctypes.c_void_p(stream)))
 
 
 def nx_profile_begin(h):
