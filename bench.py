@@ -237,6 +237,62 @@ def run_reference(args, w, world, rank):
     return 0
 
 
+def serving_requests(seed, n):
+    """The serving mix: family uniform over the five families, size uniform in
+    5..19, n_envs log-uniform in 1..4096, horizon uniform in 1..512."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        fam = int(rng.integers(0, 5))
+        size = int(rng.integers(5, 20))
+        ne = int(min(4096, max(1, np.floor(np.exp(rng.uniform(0.0, np.log(4097.0)))))))
+        hz = int(rng.integers(1, 513))
+        out.append((fam, size, ne, hz, int(rng.integers(0, 2**63))))
+    return out
+
+
+def run_serving(n_req=2000, budget=2 << 30, load=0.7, seed=4, chunk=64):
+    """Poisson arrivals at `load` x the server's measured capacity; returns
+    latency percentiles and throughput.  Capacity is measured first by
+    submitting a saturating burst of requests from the same mix."""
+    import numpy as np
+
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    srv = nx.Server(budget_bytes=budget, steps_per_launch=chunk)
+    burst = serving_requests(seed + 1000, 300)
+    t0 = time.perf_counter()
+    ts = [srv.submit(*r) for r in burst]
+    for t in ts:
+        srv.wait(t, timeout_s=600.0)
+    cap = sum(r[2] * r[3] for r in burst) / (time.perf_counter() - t0)
+    reqs = serving_requests(seed, n_req)
+    mean_work = sum(r[2] * r[3] for r in reqs) / len(reqs)
+    lam = load * cap / mean_work  # requests per second
+    rng = np.random.default_rng(seed + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+    tickets = []
+    start = time.perf_counter()
+    for r, a in zip(reqs, arrivals):
+        while time.perf_counter() - start < a:
+            pass
+        tickets.append(srv.submit(*r))
+    res = [srv.wait(t, timeout_s=600.0) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    lat = np.array([x["t_done"] - x["t_submit"] for x in res]) * 1000.0
+    first = min(x["t_submit"] for x in res)
+    last = max(x["t_done"] for x in res)
+    work = sum(x["env_steps"] for x in res)
+    return {"requests": n_req, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "env_steps_per_s": work / (last - first),
+            "capacity_env_steps_per_s": cap, "offered_load": load, "arrival_rate_per_s": lam,
+            "budget_bytes": budget, "peak_bytes": st["peak_bytes"], "chunks": st["chunks"],
+            "steps_per_launch": chunk, "mix": "family U{5}, size U{5..19}, n_envs log-U[1, 4096], horizon U{1..512}, seed 4"}
+
+
 def time_rollouts(env, w, out, K, W, flush, per_family=False):
     """W untimed rollouts, then K timed ones with CUDA events on the launching
     stream; L2 is flushed between timed rollouts, outside the event windows.
@@ -411,6 +467,8 @@ def main():
             ex.close()
             del ox
         line["extras"] = extras
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.setdefault("extras", {})["serving"] = run_serving()
     if rank == 0 and world == 1 and not args.no_extras:
         rate, reps, el, ne, nt = cpu_oracle_rate(w)
         line["cpu_baseline"] = {"value": rate, "unit": "env-steps/s", "cores": 1, "kind": "oracle",

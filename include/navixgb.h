@@ -220,6 +220,67 @@ nx_status nx_get_info(const nx_env* env, nx_info* info);
  * nx_launch_counts returns the cumulative number of step-kernel launches and
  * of all kernels this context has enqueued (graph replays count their
  * nodes); it never blocks. */
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of rollout requests (the paper's batch mode,
+ * Section 4.2 and Appendix B, as a request loop).  A request is a fresh batch
+ * of n_envs envs of one family and size, reset to episode 0 and stepped
+ * `horizon` times with uniform random actions keyed by (request seed,
+ * request-local env index, request-local step), exactly as nx_create +
+ * nx_reset + nx_rollout(horizon, NX_ACT_RANDOM) would.  Requests that arrive
+ * while others run are admitted (strictly first come, first served) as soon
+ * as their device memory fits in the server's fixed HBM budget; all admitted
+ * requests advance together in each persistent chunk launch, so results do
+ * not depend on what else is in flight.
+ */
+typedef struct {
+    int32_t family, size, n_envs, horizon;  /* size 5..19, n_envs >= 1, horizon >= 1 */
+    uint64_t seed;
+    /* optional host outputs, written when the request finishes:
+     * returns [n_envs] float32 (sum of rewards over the horizon, in step
+     * order) and final_obs [n_envs, 7, 7, 3] uint8 (the last step's view) */
+    float* returns;
+    uint8_t* final_obs;
+} nx_request;
+
+typedef struct {
+    nx_status status;          /* NX_OK when finished */
+    double t_submit, t_start, t_done;  /* seconds on the server's steady clock */
+    uint64_t digest;           /* 64-bit digest of every per-step output (see below) */
+    uint64_t env_steps;        /* n_envs x horizon */
+    uint32_t episodes;         /* episodes that ended (terminated or truncated) */
+} nx_result;
+/* Digest: per env, h = 0; for the reset record and then every step record
+ * fold the 49 view cells as words (ent | col << 8 | st << 16), the reward's
+ * float32 bits and (terminated | truncated << 8), each by
+ * h = (h ^ w) * 0x100000001B3 (mod 2^64); the request digest folds the
+ * per-env values (low word, then high word, env by env) the same way. */
+
+typedef struct {
+    uint64_t submitted, finished, rejected, env_steps, chunks;
+    double busy_s;             /* time with at least one request on the GPU */
+    size_t budget_bytes, in_use_bytes, peak_bytes;
+} nx_server_stats;
+
+/* nx_server_create: hbm_budget_bytes (at most 4 GiB) is allocated once, up
+ * front, and every admitted request's state and outputs are carved from it.
+ * opts: steps_per_launch is the chunk length (latency vs launch overhead),
+ * group_lanes / envs_per_cta fix the launch shape (0: 4 x 32), reward options
+ * apply to every request; obs_flags must be NX_OBS_SYM. */
+nx_status nx_server_create(nx_server** server, size_t hbm_budget_bytes, const nx_options* opts, void* cuda_stream);
+/* nx_submit: queue a request; NX_E_BUDGET if it can never fit the budget,
+ * NX_E_INVAL on bad arguments.  The host output buffers must stay valid until
+ * the request finishes. */
+nx_status nx_submit(nx_server* server, const nx_request* req, uint64_t* ticket);
+/* nx_poll: NX_OK and the result once finished, NX_PENDING before. */
+nx_status nx_poll(nx_server* server, uint64_t ticket, nx_result* result);
+/* nx_wait: blocks until the request finishes or timeout_s passes
+ * (NX_E_TIMEOUT; <= 0 waits without bound). */
+nx_status nx_wait(nx_server* server, uint64_t ticket, nx_result* result, double timeout_s);
+nx_status nx_server_get_stats(nx_server* server, nx_server_stats* stats);
+/* nx_server_destroy: finishes in-flight work, drops queued requests (their
+ * status becomes NX_E_STATE) and releases everything. */
+void nx_server_destroy(nx_server* server);
+
 /* nx_rollout_noalloc: reset + rollout for callers that cannot allocate
  * device memory.  The paper has no counterpart; this exists for users of the
  * library whose process cannot call cudaMalloc: another runtime may already

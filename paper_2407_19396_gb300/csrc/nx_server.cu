@@ -1,0 +1,588 @@
+// nx_server.cu -- continuous batching of rollout requests (config C5).
+//
+// A worker thread owns the GPU.  Requests wait in a FIFO queue and are
+// admitted, strictly in arrival order, as soon as their device memory fits in
+// the budget (one pool allocated up front, carved first-fit) and a request
+// record is free.  Every chunk launch runs the persistent step kernel over
+// the work items of *all* admitted requests; each request record carries its
+// own seed, step counter and step count for the chunk, so a request advances
+// exactly as it would alone.  The host queues chunk k+1 (uploads, kernel,
+// result copies of the requests it finishes, an event) before it retires
+// chunk k, so the GPU is never idle while requests are waiting.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "navixgb.h"
+#include "nx_internal.h"
+#include "nx_runtime.h"
+
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// First-fit allocator over [0, cap) with coalescing frees (offsets only).
+struct RangeAlloc {
+    std::map<size_t, size_t> free_;  // offset -> length
+    size_t cap = 0, used = 0, peak = 0;
+    void init(size_t c)
+    {
+        cap = c;
+        free_.clear();
+        free_[0] = c;
+        used = peak = 0;
+    }
+    bool alloc(size_t len, size_t* off)
+    {
+        len = up256(len);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= len) {
+                *off = it->first;
+                const size_t rest = it->second - len, o = it->first + len;
+                free_.erase(it);
+                if (rest) free_[o] = rest;
+                used += len;
+                peak = std::max(peak, used);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t len)
+    {
+        len = up256(len);
+        used -= len;
+        auto it = free_.emplace(off, len).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+// Per-request device block: [agents][grids][returns][digest][episodes][obs].
+struct Layout {
+    size_t agents, grids, returns, digest, episodes, obs, total, tail;  // tail = bytes from `returns` to the end
+    static Layout of(int n, int S)
+    {
+        Layout l;
+        l.agents = 0;
+        l.grids = up256((size_t)n * sizeof(nx_agent));
+        l.returns = l.grids + up256((size_t)n * 3 * S * S);
+        l.digest = l.returns + up256((size_t)n * 4);
+        l.episodes = l.digest + up256((size_t)n * 8);
+        l.obs = l.episodes + up256((size_t)n * 4);
+        l.total = l.obs + up256((size_t)n * NX_OBS_SYM_BYTES);
+        l.tail = l.total - l.returns;
+        return l;
+    }
+};
+
+struct SReq {
+    nx_request r{};
+    int max_steps = 0;
+    Layout lay{};
+    size_t dev_off = 0, host_off = 0;
+    int slot = -1;
+    int launched = 0;  // steps enqueued so far
+    bool admitted = false, reset_done = false;
+    nx_result res{};
+    bool finished = false;
+};
+
+struct Chunk {
+    cudaEvent_t ev = nullptr;
+    std::vector<uint64_t> finishing;
+    bool valid = false;
+};
+
+uint64_t fold(uint64_t h, uint32_t w) { return (h ^ (uint64_t)w) * 0x100000001B3ull; }
+
+}  // namespace
+
+struct nx_server {
+    nx_options opt{};
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    int device = 0;
+    int sm_count = 0;
+    nx_launch_shape shape{4, 32, 0};
+    int cell_stride = 0, per_sm = 0, chunk = 128;
+    int max_slots = 4096;
+    size_t max_items = 0;
+
+    uint8_t* d_pool = nullptr;
+    uint8_t* h_pool = nullptr;  // pinned result staging
+    RangeAlloc dev_alloc, host_alloc;
+    nx_req* d_reqs = nullptr;
+    nx_req* h_reqs[2] = {nullptr, nullptr};
+    nx_item* d_items = nullptr;  // [2 staging buffers][2 * max_items]
+    nx_item* h_items[2] = {nullptr, nullptr};
+    nx_ctl* d_ctl = nullptr;
+    Chunk chunks[2];
+
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> waiting;
+    std::unordered_map<uint64_t, SReq> reqs;
+    std::vector<uint64_t> active;
+    std::vector<int> free_slots;
+    bool stop = false;
+    nx_status fatal = NX_OK;
+    std::string fatal_msg;
+    uint64_t next_ticket = 1;
+    nx_server_stats stats{};
+    double busy_since = -1.0;
+};
+
+namespace {
+
+void set_fatal(nx_server* s, nx_status st, const std::string& msg)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->fatal == NX_OK) {
+        s->fatal = st;
+        s->fatal_msg = msg;
+    }
+}
+
+#define SRV_CK(call, what)                                                                               \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            set_fatal(s, NX_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e_));                  \
+            return false;                                                                                \
+        }                                                                                                \
+    } while (0)
+
+nx_req record_of(const nx_server* s, const SReq& q, int steps)
+{
+    nx_req r;
+    memset(&r, 0, sizeof r);
+    uint8_t* base = s->d_pool + q.dev_off;
+    r.seed = q.r.seed;
+    r.gstep = (uint32_t)q.launched;
+    r.call_step = 0;
+    r.steps = steps;
+    r.depth = 1;
+    r.n_envs = (uint32_t)q.r.n_envs;
+    r.act_mode = NX_ACT_RANDOM;
+    r.obs_sym = base + q.lay.obs;
+    r.returns = (float*)(base + q.lay.returns);
+    r.digest = (uint64_t*)(base + q.lay.digest);
+    r.episodes = (uint32_t*)(base + q.lay.episodes);
+    r.reward_mode = (uint32_t)s->opt.reward_mode;
+    r.lava_reward = s->opt.lava_reward;
+    r.n_balls = s->opt.n_balls;
+    r.key_base = 0;
+    return r;
+}
+
+void items_of(const nx_server* s, const SReq& q, std::vector<nx_item>& out)
+{
+    const int E = s->shape.envs_per_cta, n = q.r.n_envs, S = q.r.size;
+    const uint32_t agent0 = (uint32_t)((q.dev_off + q.lay.agents) / sizeof(nx_agent));
+    for (int b = 0; b < n; b += E) {
+        nx_item it;
+        memset(&it, 0, sizeof it);
+        it.env_begin = agent0 + (uint32_t)b;
+        it.n_envs = (uint32_t)std::min(E, n - b);
+        it.grid_offset = (uint32_t)(q.dev_off + q.lay.grids + (size_t)b * 3 * S * S);
+        it.req = (uint32_t)q.slot;
+        it.local_begin = (uint32_t)b;
+        it.max_steps = (uint16_t)q.max_steps;
+        it.family = (uint8_t)q.r.family;
+        it.size = (uint8_t)S;
+        out.push_back(it);
+    }
+}
+
+// Copies a finished request's results into the caller's buffers and releases
+// its memory (the chunk that produced them has completed).
+void retire(nx_server* s, uint64_t t)
+{
+    std::unique_lock<std::mutex> lk(s->mu);
+    SReq& q = s->reqs[t];
+    const int n = q.r.n_envs;
+    const uint8_t* h = s->h_pool + q.host_off;  // same relative layout as the device tail
+    const float* ret = (const float*)h;
+    const uint64_t* dig = (const uint64_t*)(h + (q.lay.digest - q.lay.returns));
+    const uint32_t* eps = (const uint32_t*)(h + (q.lay.episodes - q.lay.returns));
+    const uint8_t* obs = h + (q.lay.obs - q.lay.returns);
+    lk.unlock();
+    if (q.r.returns) memcpy(q.r.returns, ret, (size_t)n * 4);
+    if (q.r.final_obs) memcpy(q.r.final_obs, obs, (size_t)n * NX_OBS_SYM_BYTES);
+    uint64_t d = 0;
+    uint32_t e = 0;
+    for (int i = 0; i < n; ++i) {
+        d = fold(d, (uint32_t)dig[i]);
+        d = fold(d, (uint32_t)(dig[i] >> 32));
+        e += eps[i];
+    }
+    lk.lock();
+    q.res.digest = d;
+    q.res.episodes = e;
+    q.res.env_steps = (uint64_t)n * (uint64_t)q.r.horizon;
+    q.res.status = NX_OK;
+    q.res.t_done = now_s();
+    q.finished = true;
+    s->dev_alloc.release(q.dev_off, q.lay.total);
+    s->host_alloc.release(q.host_off, q.lay.tail);
+    s->free_slots.push_back(q.slot);
+    s->stats.finished += 1;
+    s->stats.env_steps += q.res.env_steps;
+    s->stats.in_use_bytes = s->dev_alloc.used;
+    s->cv_done.notify_all();
+}
+
+bool wait_chunk(nx_server* s, Chunk& c)
+{
+    if (!c.valid) return true;
+    SRV_CK(cudaEventSynchronize(c.ev), "chunk completion");
+    for (uint64_t t : c.finishing) retire(s, t);
+    c.finishing.clear();
+    c.valid = false;
+    return true;
+}
+
+// One iteration: admit, reset the newcomers and launch the next chunk into
+// staging buffer `cur`, then retire the previous chunk (buffer cur ^ 1) while
+// the new one runs.  Returns false on a fatal CUDA error.
+bool iterate(nx_server* s, int& cur, bool* idle)
+{
+    std::vector<uint64_t> fresh;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        while (!s->stop && !s->waiting.empty() && !s->free_slots.empty()) {
+            const uint64_t t = s->waiting.front();
+            SReq& q = s->reqs[t];
+            size_t doff, hoff;
+            if (!s->dev_alloc.alloc(q.lay.total, &doff)) break;
+            if (!s->host_alloc.alloc(q.lay.tail, &hoff)) {
+                s->dev_alloc.release(doff, q.lay.total);
+                break;
+            }
+            s->waiting.pop_front();
+            q.dev_off = doff;
+            q.host_off = hoff;
+            q.slot = s->free_slots.back();
+            s->free_slots.pop_back();
+            q.admitted = true;
+            q.res.t_start = now_s();
+            s->active.push_back(t);
+            fresh.push_back(t);
+        }
+        s->stats.in_use_bytes = s->dev_alloc.used;
+        s->stats.peak_bytes = s->dev_alloc.peak;
+        *idle = s->active.empty();
+        if (*idle && s->busy_since >= 0) {
+            s->stats.busy_s += now_s() - s->busy_since;
+            s->busy_since = -1.0;
+        } else if (!*idle && s->busy_since < 0) {
+            s->busy_since = now_s();
+        }
+    }
+    if (*idle) return wait_chunk(s, s->chunks[0]) && wait_chunk(s, s->chunks[1]);
+
+    Chunk& c = s->chunks[cur];
+    if (!wait_chunk(s, c)) return false;  // normally retired already by the previous iteration
+    nx_req* hr = s->h_reqs[cur];
+    nx_item* hi = s->h_items[cur];
+    std::vector<nx_item> reset_items, step_items;
+    std::vector<uint64_t> finishing, still;
+    int launch_steps = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (uint64_t t : fresh) items_of(s, s->reqs[t], reset_items);
+        for (uint64_t t : s->active) {
+            SReq& q = s->reqs[t];
+            const int k = std::min(s->chunk, q.r.horizon - q.launched);
+            hr[q.slot] = record_of(s, q, k);
+            items_of(s, q, step_items);
+            launch_steps = std::max(launch_steps, k);
+            q.launched += k;
+            if (q.launched >= q.r.horizon)
+                finishing.push_back(t);
+            else
+                still.push_back(t);
+        }
+        s->active = still;
+        s->stats.chunks += 1;
+    }
+    const size_t nr = reset_items.size(), ns = step_items.size();
+    if (nr + ns > 2 * s->max_items) {
+        set_fatal(s, NX_E_INVAL, "work list larger than the server's capacity");
+        return false;
+    }
+    memcpy(hi, reset_items.data(), nr * sizeof(nx_item));
+    memcpy(hi + nr, step_items.data(), ns * sizeof(nx_item));
+    nx_item* di = s->d_items + (size_t)cur * 2 * s->max_items;
+    SRV_CK(cudaMemcpyAsync(di, hi, (nr + ns) * sizeof(nx_item), cudaMemcpyHostToDevice, s->stream), "item upload");
+    SRV_CK(cudaMemcpyAsync(s->d_reqs, hr, sizeof(nx_req) * (size_t)s->max_slots, cudaMemcpyHostToDevice, s->stream),
+           "record upload");
+    nx_kparams p;
+    memset(&p, 0, sizeof p);
+    p.agents = (nx_agent*)s->d_pool;
+    p.grids = s->d_pool;
+    p.reqs = s->d_reqs;
+    p.ctl = s->d_ctl;
+    p.cell_stride = s->cell_stride;
+    p.envs_per_cta = s->shape.envs_per_cta;
+    const int max_grid = s->per_sm * s->sm_count;
+    if (nr) {
+        for (uint64_t t : fresh) {
+            const SReq& q = s->reqs[t];
+            SRV_CK(cudaMemsetAsync(s->d_pool + q.dev_off + q.lay.returns, 0, q.lay.obs - q.lay.returns, s->stream),
+                   "accumulator clear");
+        }
+        p.items = di;
+        p.n_items = (int)nr;
+        p.reset_all = 1;
+        p.launch_steps = 0;
+        int rc = nx_launch_step_kernel(s->shape, p, std::min((int)nr, max_grid), s->stream);
+        if (rc) SRV_CK((cudaError_t)rc, "reset launch");
+    }
+    if (ns) {
+        p.items = di + nr;
+        p.n_items = (int)ns;
+        p.reset_all = 0;
+        p.launch_steps = launch_steps;
+        int rc = nx_launch_step_kernel(s->shape, p, std::min((int)ns, max_grid), s->stream);
+        if (rc) SRV_CK((cudaError_t)rc, "step launch");
+    }
+    for (uint64_t t : finishing) {
+        const SReq& q = s->reqs[t];
+        SRV_CK(cudaMemcpyAsync(s->h_pool + q.host_off, s->d_pool + q.dev_off + q.lay.returns, q.lay.tail,
+                               cudaMemcpyDeviceToHost, s->stream),
+               "result copy");
+    }
+    SRV_CK(cudaEventRecord(c.ev, s->stream), "chunk event");
+    c.finishing = finishing;
+    c.valid = true;
+    cur ^= 1;
+    // the previous chunk finishes while this one is queued behind it
+    return wait_chunk(s, s->chunks[cur]);
+}
+
+void worker_main(nx_server* s)
+{
+    int cur = 0;
+    if (cudaSetDevice(s->device) != cudaSuccess) set_fatal(s, NX_E_CUDA, "worker cannot select the device");
+    for (;;) {
+        bool idle = false;
+        bool ok = iterate(s, cur, &idle);
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (!ok || s->fatal != NX_OK) break;
+        if (s->stop && s->active.empty()) break;
+        if (idle) s->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return s->stop || !s->waiting.empty(); });
+    }
+    // drain what is in flight, then fail whatever cannot finish
+    wait_chunk(s, s->chunks[0]);
+    wait_chunk(s, s->chunks[1]);
+    std::lock_guard<std::mutex> lk(s->mu);
+    const nx_status st = s->fatal != NX_OK ? s->fatal : NX_E_STATE;
+    for (auto& kv : s->reqs) {
+        if (!kv.second.finished) {
+            kv.second.finished = true;
+            kv.second.res.status = st;
+            kv.second.res.t_done = now_s();
+        }
+    }
+    s->waiting.clear();
+    s->active.clear();
+    s->cv_done.notify_all();
+}
+
+}  // namespace
+
+nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opts, void* cuda_stream)
+{
+    if (!out) return nx_fail(nullptr, NX_E_INVAL, "server pointer is NULL");
+    *out = nullptr;
+    nx_options o;
+    if (opts)
+        o = *opts;
+    else
+        nx_options_default(&o);
+    if (budget < (1u << 20) || budget > ((size_t)4 << 30)) return nx_fail(nullptr, NX_E_INVAL, "budget must be 1 MiB..4 GiB");
+    if (o.obs_flags != NX_OBS_SYM) return nx_fail(nullptr, NX_E_INVAL, "the server produces symbolic observations only");
+    if (o.steps_per_launch <= 0) o.steps_per_launch = 128;
+    if (o.steps_per_launch > 1024) return nx_fail(nullptr, NX_E_INVAL, "steps_per_launch must be <= 1024");
+    if (o.n_balls < 0 || o.n_balls > NX_MAX_BALLS) return nx_fail(nullptr, NX_E_INVAL, "n_balls must be in 0..4");
+    nx_server* s = new (std::nothrow) nx_server();
+    if (!s) return nx_fail(nullptr, NX_E_NOMEM, "host allocation failed");
+    s->opt = o;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->budget = budget;
+    s->chunk = o.steps_per_launch;
+    if (o.group_lanes) s->shape = nx_launch_shape{o.group_lanes, o.envs_per_cta, 0};
+    if (!nx_shape_supported(s->shape)) {
+        delete s;
+        return nx_fail(nullptr, NX_E_INVAL, "unsupported launch shape");
+    }
+    s->cell_stride = (NX_MAX_SIZE * NX_MAX_SIZE + 15) & ~15;
+    int dev = 0, err = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return nx_fail(nullptr, NX_E_CUDA, "no CUDA device available");
+    }
+    s->device = dev;
+    s->per_sm = nx_kernel_max_ctas(s->shape, s->cell_stride, &err);
+    if (err || s->per_sm < 1) {
+        delete s;
+        return nx_fail(nullptr, NX_E_CUDA, "occupancy query failed");
+    }
+    // the smallest request (1 env of 5x5) needs about 1.8 KB: bound the work list by that
+    s->max_items = std::min<size_t>(budget / 1536 + 1, (size_t)1 << 20);
+    const size_t host_cap = budget / 4 + (1u << 20);  // result staging: returns, digests, episodes, final views
+    cudaError_t e = cudaMalloc(&s->d_pool, budget);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_reqs, sizeof(nx_req) * (size_t)s->max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_items, sizeof(nx_item) * s->max_items * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ctl, sizeof(nx_ctl));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_pool, host_cap);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaMallocHost(&s->h_reqs[b], sizeof(nx_req) * (size_t)s->max_slots);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->h_items[b], sizeof(nx_item) * 2 * s->max_items);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->chunks[b].ev, cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ctl, 0, sizeof(nx_ctl), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::string m = std::string("server setup: ") + cudaGetErrorString(e);
+        nx_server_destroy(s);
+        return nx_fail(nullptr, e == cudaErrorMemoryAllocation ? NX_E_NOMEM : NX_E_CUDA, m);
+    }
+    for (int b = 0; b < 2; ++b) memset(s->h_reqs[b], 0, sizeof(nx_req) * (size_t)s->max_slots);
+    s->dev_alloc.init(budget);
+    s->host_alloc.init(host_cap);
+    for (int i = s->max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->stats.budget_bytes = budget;
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return NX_OK;
+}
+
+nx_status nx_submit(nx_server* s, const nx_request* r, uint64_t* ticket)
+{
+    if (!s || !r || !ticket) return nx_fail(nullptr, NX_E_INVAL, "NULL argument");
+    if (r->family < NX_EMPTY || r->family > NX_DYNOBS || r->size < NX_MIN_SIZE || r->size > NX_MAX_SIZE ||
+        r->n_envs < 1 || r->horizon < 1)
+        return nx_fail(nullptr, NX_E_INVAL, "request: family 0..4, size 5..19, n_envs >= 1, horizon >= 1");
+    SReq q;
+    q.r = *r;
+    q.max_steps = nx_default_max_steps(r->family, r->size);
+    q.lay = Layout::of(r->n_envs, r->size);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->fatal != NX_OK) return nx_fail(nullptr, s->fatal, s->fatal_msg);
+    if (s->stop) return nx_fail(nullptr, NX_E_STATE, "server is shutting down");
+    if (up256(q.lay.total) > s->budget || up256(q.lay.tail) > s->host_alloc.cap ||
+        (size_t)((r->n_envs + s->shape.envs_per_cta - 1) / s->shape.envs_per_cta) * 2 > s->max_items) {
+        s->stats.rejected += 1;
+        return nx_fail(nullptr, NX_E_BUDGET, "request needs " + std::to_string(q.lay.total) +
+                                                 " bytes, more than the whole budget of " + std::to_string(s->budget));
+    }
+    const uint64_t t = s->next_ticket++;
+    q.res.status = NX_PENDING;
+    q.res.t_submit = now_s();
+    s->reqs.emplace(t, q);
+    s->waiting.push_back(t);
+    s->stats.submitted += 1;
+    *ticket = t;
+    s->cv_work.notify_one();
+    return NX_OK;
+}
+
+nx_status nx_poll(nx_server* s, uint64_t ticket, nx_result* res)
+{
+    if (!s) return nx_fail(nullptr, NX_E_INVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return nx_fail(nullptr, NX_E_INVAL, "unknown ticket");
+    if (!it->second.finished) return NX_PENDING;
+    if (res) *res = it->second.res;
+    return it->second.res.status == NX_OK ? NX_OK : it->second.res.status;
+}
+
+nx_status nx_wait(nx_server* s, uint64_t ticket, nx_result* res, double timeout_s)
+{
+    if (!s) return nx_fail(nullptr, NX_E_INVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return nx_fail(nullptr, NX_E_INVAL, "unknown ticket");
+    auto done = [&] { return it->second.finished; };
+    if (timeout_s > 0) {
+        if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done))
+            return nx_fail(nullptr, NX_E_TIMEOUT, "request did not finish in time");
+    } else {
+        s->cv_done.wait(lk, done);
+    }
+    if (res) *res = it->second.res;
+    return it->second.res.status;
+}
+
+nx_status nx_server_get_stats(nx_server* s, nx_server_stats* st)
+{
+    if (!s || !st) return nx_fail(nullptr, NX_E_INVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *st = s->stats;
+    if (s->busy_since >= 0) st->busy_s += now_s() - s->busy_since;
+    return NX_OK;
+}
+
+void nx_server_destroy(nx_server* s)
+{
+    if (!s) return;
+    if (s->worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+            // queued requests are dropped; admitted ones finish
+            for (uint64_t t : s->waiting) {
+                s->reqs[t].finished = true;
+                s->reqs[t].res.status = NX_E_STATE;
+            }
+            s->waiting.clear();
+        }
+        s->cv_work.notify_all();
+        s->worker.join();
+    }
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (int b = 0; b < 2; ++b) {
+        if (s->chunks[b].ev) cudaEventDestroy(s->chunks[b].ev);
+        if (s->h_reqs[b]) cudaFreeHost(s->h_reqs[b]);
+        if (s->h_items[b]) cudaFreeHost(s->h_items[b]);
+    }
+    if (s->h_pool) cudaFreeHost(s->h_pool);
+    if (s->d_pool) cudaFree(s->d_pool);
+    if (s->d_reqs) cudaFree(s->d_reqs);
+    if (s->d_items) cudaFree(s->d_items);
+    if (s->d_ctl) cudaFree(s->d_ctl);
+    delete s;
+}

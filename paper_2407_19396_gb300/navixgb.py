@@ -59,6 +59,25 @@ class nx_info(ctypes.Structure):
                 ("state_bytes", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t)]
 
 
+class nx_request(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int32), ("size", ctypes.c_int32), ("n_envs", ctypes.c_int32),
+                ("horizon", ctypes.c_int32), ("seed", ctypes.c_uint64), ("returns", ctypes.c_void_p),
+                ("final_obs", ctypes.c_void_p)]
+
+
+class nx_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("digest", ctypes.c_uint64), ("env_steps", ctypes.c_uint64),
+                ("episodes", ctypes.c_uint32)]
+
+
+class nx_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("finished", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("env_steps", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("busy_s", ctypes.c_double),
+                ("budget_bytes", ctypes.c_size_t), ("in_use_bytes", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t)]
+
+
 # every symbol include/navixgb.h declares, with its signature
 _P = ctypes.POINTER
 _vp, _i32, _u32, _u64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
@@ -82,6 +101,12 @@ SIGNATURES = {
     "nx_profile_end": (_i32, [_vp, _P(ctypes.c_double), _P(ctypes.c_int64)]),
     "nx_launch_counts": (_i32, [_vp, _P(ctypes.c_int64), _P(ctypes.c_int64)]),
     "nx_destroy": (None, [_vp]),
+    "nx_server_create": (_i32, [_P(_vp), _sz, _P(nx_options), _vp]),
+    "nx_submit": (_i32, [_vp, _P(nx_request), _P(_u64)]),
+    "nx_poll": (_i32, [_vp, _u64, _P(nx_result)]),
+    "nx_wait": (_i32, [_vp, _u64, _P(nx_result), ctypes.c_double]),
+    "nx_server_get_stats": (_i32, [_vp, _P(nx_server_stats)]),
+    "nx_server_destroy": (None, [_vp]),
     "nx_status_str": (ctypes.c_char_p, [_i32]),
     "nx_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -435,3 +460,105 @@ class Env:
     def launch_counts(self):
         """(step-kernel launches, all kernel launches) so far."""
         return nx_launch_counts(self.h)
+
+
+# --- serving -------------------------------------------------------------------
+
+def _result_dict(r: nx_result) -> dict:
+    return {k: getattr(r, k) for k, _ in nx_result._fields_}
+
+
+def nx_server_create(budget_bytes, opts=None, stream=0):
+    h = ctypes.c_void_p()
+    check(lib().nx_server_create(ctypes.byref(h), budget_bytes, ctypes.byref(opts) if opts else None,
+                                 ctypes.c_void_p(stream)))
+    return h
+
+
+def nx_submit(h, req: nx_request) -> int:
+    t = ctypes.c_uint64()
+    check(lib().nx_submit(h, ctypes.byref(req), ctypes.byref(t)))
+    return int(t.value)
+
+
+def nx_poll(h, ticket):
+    r = nx_result()
+    st = lib().nx_poll(h, ticket, ctypes.byref(r))
+    if st == NX_PENDING:
+        return None
+    check(st)
+    return _result_dict(r)
+
+
+def nx_wait(h, ticket, timeout_s=0.0):
+    r = nx_result()
+    check(lib().nx_wait(h, ticket, ctypes.byref(r), timeout_s))
+    return _result_dict(r)
+
+
+def nx_server_get_stats(h) -> dict:
+    st = nx_server_stats()
+    check(lib().nx_server_get_stats(h, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in nx_server_stats._fields_}
+
+
+def nx_server_destroy(h):
+    lib().nx_server_destroy(h)
+
+
+class Server:
+    """Continuous-batching rollout server; results land in numpy arrays."""
+
+    def __init__(self, budget_bytes=1 << 30, steps_per_launch=128, group_lanes=0, envs_per_cta=0,
+                 reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, stream=None):
+        o = nx_options_default()
+        o.steps_per_launch = steps_per_launch
+        o.group_lanes = group_lanes
+        o.envs_per_cta = envs_per_cta
+        o.reward_mode = reward_mode
+        o.lava_reward = lava_reward
+        o.n_balls = n_balls
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        self.h = nx_server_create(budget_bytes, o, stream)
+        self._bufs = {}
+
+    def submit(self, family, size, n_envs, horizon, seed):
+        ret = np.zeros(n_envs, np.float32)
+        obs = np.zeros((n_envs, 7, 7, 3), np.uint8)
+        r = nx_request(int(family), int(size), int(n_envs), int(horizon), int(seed), ret.ctypes.data, obs.ctypes.data)
+        t = nx_submit(self.h, r)
+        self._bufs[t] = (ret, obs)
+        return t
+
+    def wait(self, ticket, timeout_s=0.0):
+        res = nx_wait(self.h, ticket, timeout_s)
+        ret, obs = self._bufs[ticket]
+        res["returns"], res["final_obs"] = ret, obs
+        return res
+
+    def poll(self, ticket):
+        res = nx_poll(self.h, ticket)
+        if res is not None:
+            ret, obs = self._bufs[ticket]
+            res["returns"], res["final_obs"] = ret, obs
+        return res
+
+    def stats(self):
+        return nx_server_get_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            nx_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -62,3 +62,45 @@ def mixed_descs(n_total, parts):
     for j, p in enumerate(parts):
         out += [p] * (base + (1 if j < extra else 0))
     return out
+
+
+def _fold(h, w):
+    return (h ^ w.astype(np.uint64)) * np.uint64(0x100000001B3)
+
+
+def record_words(obs, reward, term, trunc):
+    """Per env, the 51 digest words of one step record: the 49 view cells
+    (ent | col << 8 | st << 16), the reward's float32 bits, term | trunc << 8."""
+    n = obs.shape[0]
+    c = obs.reshape(n, 49, 3).astype(np.uint32)
+    cells = c[:, :, 0] | (c[:, :, 1] << 8) | (c[:, :, 2] << 16)
+    rbits = np.ascontiguousarray(reward, np.float32).view(np.uint32)
+    flags = term.astype(np.uint32) | (trunc.astype(np.uint32) << 8)
+    return np.concatenate([cells, rbits[:, None], flags[:, None]], axis=1)
+
+
+def oracle_request(family, size, n_envs, horizon, seed, **kw):
+    """What a serving request must return, computed by the oracle: per-env
+    returns (float32, summed in step order), the final view, the number of
+    ended episodes and the digest of the reset record plus every step record."""
+    b = O.Batch([family] * n_envs, [size] * n_envs, seed, **kw)
+    r0 = b.reset()
+    h = np.zeros(n_envs, np.uint64)
+    with np.errstate(over="ignore"):
+        for w in record_words(r0["obs_sym"], r0["reward"], r0["terminated"], r0["truncated"]).T:
+            h = _fold(h, w)
+        ret = np.zeros(n_envs, np.float32)
+        eps = 0
+        last = r0["obs_sym"]
+        for t in range(horizon):
+            o = b.step()
+            for w in record_words(o["obs_sym"], o["reward"], o["terminated"], o["truncated"]).T:
+                h = _fold(h, w)
+            ret = (ret + o["reward"]).astype(np.float32)
+            eps += int((o["terminated"] | o["truncated"]).sum())
+            last = o["obs_sym"]
+        d = np.zeros(1, np.uint64)
+        for i in range(n_envs):
+            d = _fold(d, np.array([int(h[i]) & 0xFFFFFFFF], np.uint64))
+            d = _fold(d, np.array([int(h[i]) >> 32], np.uint64))
+    return {"returns": ret, "final_obs": last, "episodes": eps, "digest": int(d[0])}

@@ -1,0 +1,120 @@
+"""Continuous-batching server (config C5) on the GPU.
+
+Every request's result (per-env returns, final view, ended episodes, digest of
+every per-step output) must be the same when it runs alone and when it shares
+the GPU with other requests admitted before, with and after it, and must equal
+the oracle's.  Exact comparison throughout.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from tests.gpu_util import oracle_request  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2407_19396_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _mix(seed, n, max_envs=300, max_h=300):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(n):
+        fam = int(rng.integers(0, 5))
+        size = int(rng.integers(5, 20))
+        ne = int(min(max_envs, max(1, np.floor(np.exp(rng.uniform(0, np.log(max_envs + 1)))))))
+        h = int(rng.integers(1, max_h + 1))
+        reqs.append((fam, size, ne, h, int(rng.integers(0, 2**63))))
+    return reqs
+
+
+def _same(a, b):
+    np.testing.assert_array_equal(a["returns"], b["returns"])
+    np.testing.assert_array_equal(a["final_obs"], b["final_obs"])
+    assert a["episodes"] == b["episodes"]
+    assert a["digest"] == b["digest"]
+
+
+def test_results_same_alone_in_the_mix_and_in_the_oracle():
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    reqs = _mix(4, 36)
+    srv = nx.Server(budget_bytes=256 << 20, steps_per_launch=32)
+    tickets = [srv.submit(*r) for r in reqs]
+    mixed = [srv.wait(t, timeout_s=120.0) for t in tickets]
+    st = srv.stats()
+    assert st["finished"] == len(reqs) and st["chunks"] >= 2
+    srv.close()
+    for r, m in zip(reqs, mixed):
+        assert m["status"] == 0 and m["env_steps"] == r[2] * r[3]
+        alone_srv = nx.Server(budget_bytes=64 << 20, steps_per_launch=32)
+        alone = alone_srv.wait(alone_srv.submit(*r), timeout_s=120.0)
+        alone_srv.close()
+        _same(m, alone)
+        _same(m, oracle_request(r[0], r[1], r[2], r[3], r[4]))
+
+
+def test_requests_arriving_while_others_run_are_admitted_and_correct():
+    from paper_2407_19396_gb300 import navixgb as nx
+    import time
+
+    reqs = _mix(7, 24, max_envs=400, max_h=500)
+    srv = nx.Server(budget_bytes=256 << 20, steps_per_launch=16)
+    tickets = []
+    for i, r in enumerate(reqs):
+        tickets.append(srv.submit(*r))
+        if i % 4 == 3:
+            time.sleep(0.002)
+    res = [srv.wait(t, timeout_s=120.0) for t in tickets]
+    srv.close()
+    # overlap: some request started before an earlier-submitted one finished
+    starts = [x["t_start"] for x in res]
+    dones = [x["t_done"] for x in res]
+    assert any(starts[j] < dones[i] for i in range(len(res)) for j in range(i + 1, len(res)))
+    for r, m in zip(reqs, res):
+        _same(m, oracle_request(r[0], r[1], r[2], r[3], r[4]))
+
+
+def test_budget_admission_and_rejection():
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    budget = 4 << 20  # room for about two of the requests below at a time
+    srv = nx.Server(budget_bytes=budget, steps_per_launch=64)
+    reqs = [(O.FOURROOMS, 19, 1200, 130, 100 + i) for i in range(5)]
+    tickets = [srv.submit(*r) for r in reqs]
+    res = [srv.wait(t, timeout_s=120.0) for t in tickets]
+    st = srv.stats()
+    assert st["peak_bytes"] <= budget and st["finished"] == 5
+    # strictly first come, first served: later requests start after earlier ones
+    starts = [x["t_start"] for x in res]
+    assert starts == sorted(starts)
+    assert max(starts) > min(x["t_done"] for x in res)  # the budget forced some to wait
+    with pytest.raises(nx.NavixError) as ei:
+        srv.submit(O.FOURROOMS, 19, 4096, 10, 1)
+    assert ei.value.status == nx.NX_E_BUDGET
+    srv.close()
+    for r, m in zip(reqs[:2], res[:2]):
+        _same(m, oracle_request(*r))
+
+
+def test_wait_timeout_is_bounded():
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    srv = nx.Server(budget_bytes=64 << 20, steps_per_launch=128)
+    t = srv.submit(O.DOORKEY, 16, 4000, 4000, 5)
+    with pytest.raises(nx.NavixError) as ei:
+        srv.wait(t, timeout_s=1e-4)
+    assert ei.value.status == nx.NX_E_TIMEOUT
+    r = srv.wait(t, timeout_s=300.0)
+    assert r["status"] == 0
+    srv.close()
