@@ -51,46 +51,54 @@ __device__ __forceinline__ uint32_t draw(uint64_t seed, uint32_t env, uint32_t e
 __device__ __forceinline__ int bounded(uint32_t x, uint32_t n) { return (int)__umulhi(x, n); }
 
 // ---------------------------------------------------------------------------
-// Packed cell code (one byte in shared memory): (kind << 3) | colour, where
-// kind is the entity code except for doors: 4 open, 11 closed, 12 locked.
+// Packed cell code (one byte in shared memory): bits 0-2 colour, bits 3-6
+// kind, bit 7 set when the cell blocks sight.  The kind is the entity code
+// except for doors: 4 open, 11 closed, 12 locked.
 enum : uint32_t {
     K_EMPTY = 1, K_WALL = 2, K_FLOOR = 3, K_DOOR_OPEN = 4, K_KEY = 5, K_BALL = 6, K_BOX = 7, K_GOAL = 8,
     K_LAVA = 9, K_DOOR_CLOSED = 11, K_DOOR_LOCKED = 12
 };
+constexpr uint32_t OPAQUE = 0x80u;
+__host__ __device__ constexpr uint32_t make_code(uint32_t kind, uint32_t col)
+{
+    return (kind << 3) | (col & 7u) | ((kind == K_WALL || kind >= K_DOOR_CLOSED) ? OPAQUE : 0u);
+}
 enum : uint32_t {
-    C_EMPTY = (K_EMPTY << 3),
-    C_WALL = (K_WALL << 3) | 5u,
-    C_GOAL = (K_GOAL << 3) | 1u,
-    C_LAVA = (K_LAVA << 3),
-    C_BALL_BLUE = (K_BALL << 3) | 2u,
-    C_KEY_YELLOW = (K_KEY << 3) | 4u,
-    C_DOOR_LOCKED_YELLOW = (K_DOOR_LOCKED << 3) | 4u
+    C_EMPTY = make_code(K_EMPTY, 0),
+    C_WALL = make_code(K_WALL, 5),
+    C_GOAL = make_code(K_GOAL, 1),
+    C_LAVA = make_code(K_LAVA, 0),
+    C_BALL_BLUE = make_code(K_BALL, 2),
+    C_KEY_YELLOW = make_code(K_KEY, 4),
+    C_DOOR_LOCKED_YELLOW = make_code(K_DOOR_LOCKED, 4)
 };
-// kinds that let light through: all but wall (2), closed (11) and locked (12) doors
-#define NX_TRANSPARENT_KINDS 0x7FBu
 // kinds the agent can enter: empty, floor, open door, goal, lava
 #define NX_WALKABLE_KINDS ((1u << 1) | (1u << 3) | (1u << 4) | (1u << 8) | (1u << 9))
 
 __device__ __forceinline__ uint32_t pack_cell(uint32_t ent, uint32_t col, uint32_t st)
 {
-    uint32_t kind = ent;
+    uint32_t kind = ent & 15u;
     if (ent == 4u) kind = st == 0u ? K_DOOR_OPEN : (st == 1u ? K_DOOR_CLOSED : K_DOOR_LOCKED);
-    return (kind << 3) | (col & 7u);
+    return make_code(kind, col);
 }
-__device__ __forceinline__ uint32_t cell_kind(uint32_t code) { return code >> 3; }
+__device__ __forceinline__ uint32_t cell_kind(uint32_t code) { return (code >> 3) & 15u; }
 __device__ __forceinline__ uint32_t cell_col(uint32_t code) { return code & 7u; }
 __device__ __forceinline__ uint32_t cell_ent(uint32_t code)
 {
-    const uint32_t k = code >> 3;
+    const uint32_t k = cell_kind(code);
     return k >= 11u ? 4u : k;
 }
 __device__ __forceinline__ uint32_t cell_st(uint32_t code)
 {
-    const uint32_t k = code >> 3;
+    const uint32_t k = cell_kind(code);
     return k >= 11u ? k - 10u : 0u;
 }
-__device__ __forceinline__ bool transparent(uint32_t code) { return (NX_TRANSPARENT_KINDS >> (code >> 3)) & 1u; }
-__device__ __forceinline__ bool walkable(uint32_t code) { return (NX_WALKABLE_KINDS >> (code >> 3)) & 1u; }
+__device__ __forceinline__ bool walkable(uint32_t code) { return (NX_WALKABLE_KINDS >> cell_kind(code)) & 1u; }
+// the observation triple (ent | col << 8 | st << 16) of a code
+__device__ __forceinline__ uint32_t cell_triple(uint32_t code)
+{
+    return cell_ent(code) | (cell_col(code) << 8) | (cell_st(code) << 16);
+}
 
 // ---------------------------------------------------------------------------
 // A group of G lanes of one warp owning one environment.
@@ -246,7 +254,7 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
 // Returns false (and leaves a partial layout) only if a free-cell choice found
 // no cell, which cannot happen for sizes 5..19; the caller raises a flag.
 template <int G>
-__device__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int n_balls, uint64_t seed,
+__device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int n_balls, uint64_t seed,
                              uint32_t key_env, uint32_t episode, AgentReg& a)
 {
     const int HW = S * S;
@@ -342,100 +350,202 @@ __device__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int S, int family, i
     return true;
 }
 
+// The same generator run by a whole warp for one env, kept out of line: it is
+// the rare path of narrow groups, and inlining it would raise the register
+// allocation of the whole step kernel.
+__device__ __noinline__ bool reset_layout_warp(uint8_t* g, int S, int family, int n_balls, uint64_t seed,
+                                               uint32_t key_env, uint32_t episode, AgentReg& a)
+{
+    return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, family, n_balls, seed, key_env, episode, a);
+}
+
 // ---------------------------------------------------------------------------
 // Occlusion of the 7x7 view (bit c = vy * 7 + vx of a 49-bit mask).  Rows are
 // processed from the agent's row (vy = 6) outward.  Within a row, light
 // spreads first toward +vx, then toward -vx, through transparent cells (a lit
 // opaque cell is visible but passes nothing on); every lit transparent cell
 // also lights the two cells ahead of it and of its neighbour in that pass,
-// which seeds the next row.  Each pass is a prefix fill done with doubling
-// shifts (propagate masks of length 1, 2, 4).
+// which seeds the next row.  occ_row() evaluates one row with prefix fills by
+// doubling shifts; occ_table holds it for all 2^7 seeds x 2^7 transparency
+// patterns (visible row in bits 0-6, next seed in bits 7-13), built by the
+// compiler, so a row costs one cached load.
+__host__ __device__ constexpr uint32_t occ_row(uint32_t seed, uint32_t t)
+{
+    uint32_t m = seed;
+    const uint32_t p1 = t & 0x3Fu, p2 = p1 & (p1 >> 1), p4 = p2 & (p2 >> 2);  // toward +vx
+    m |= (m & p1) << 1;
+    m |= (m & p2) << 2;
+    m |= (m & p4) << 4;
+    m &= 0x7Fu;
+    const uint32_t fa = m & p1;
+    uint32_t up = fa | (fa << 1);
+    const uint32_t q1 = t & 0x7Eu, q2 = q1 & (q1 << 1), q4 = q2 & (q2 << 2);  // toward -vx
+    m |= (m & q1) >> 1;
+    m |= (m & q2) >> 2;
+    m |= (m & q4) >> 4;
+    const uint32_t ba = m & q1;
+    up |= ba | (ba >> 1);
+    return m | ((up & 0x7Fu) << 7);
+}
+
+struct OccTable {
+    uint16_t v[1 << 14];
+};
+constexpr OccTable make_occ_table()
+{
+    OccTable t{};
+    for (uint32_t i = 0; i < (1u << 14); ++i) t.v[i] = (uint16_t)occ_row(i >> 7, i & 0x7Fu);
+    return t;
+}
+__device__ const OccTable occ_table = make_occ_table();
+
 __device__ __forceinline__ uint64_t occlusion(uint64_t tmask)
 {
     uint64_t vis = 0;
     uint32_t seed = 1u << 3;
-#pragma unroll
-    for (int j = 6; j >= 0; --j) {
+#pragma unroll 1
+    for (int j = 6; j >= 0 && seed != 0u; --j) {
         const uint32_t t = (uint32_t)(tmask >> (7 * j)) & 0x7Fu;
-        uint32_t m = seed;
-        // toward +vx: a lit cell i <= 5 that is transparent lights i + 1
-        const uint32_t p1 = t & 0x3Fu;
-        const uint32_t p2 = p1 & (p1 >> 1);
-        const uint32_t p4 = p2 & (p2 >> 2);
-        m |= (m & p1) << 1;
-        m |= (m & p2) << 2;
-        m |= (m & p4) << 4;
-        m &= 0x7Fu;
-        const uint32_t fa = m & p1;
-        uint32_t up = fa | (fa << 1);
-        // toward -vx: a lit cell i >= 1 that is transparent lights i - 1
-        const uint32_t q1 = t & 0x7Eu;
-        const uint32_t q2 = q1 & (q1 << 1);
-        const uint32_t q4 = q2 & (q2 << 2);
-        m |= (m & q1) >> 1;
-        m |= (m & q2) >> 2;
-        m |= (m & q4) >> 4;
-        const uint32_t ba = m & q1;
-        up |= ba | (ba >> 1);
-        vis |= (uint64_t)m << (7 * j);
-        seed = up & 0x7Fu;
+        const uint32_t e = __ldg(&occ_table.v[(seed << 7) | t]);
+        vis |= (uint64_t)(e & 0x7Fu) << (7 * j);
+        seed = e >> 7;
     }
     return vis;
 }
 
-// Atlas tile of a view cell: 0 unseen; 1 + 18 ent + 3 col + st when visible;
-// + 198 for the agent's own cell.
-__device__ __forceinline__ uint32_t tile_of(bool visible, bool agent_cell, uint32_t code)
+// Geometry of one env's view for one step: view cell (vx, vy) shows world
+// cell pos + (6 - vy) F + (vx - 3) R (F the facing direction, R its
+// right-hand side, y growing downward), i.e. linear index
+// idx0 + vx dR - vy dF; it lies inside the grid iff bit vx of colmask and bit
+// vy of rowmask are set (outside cells read as a grey wall).
+struct ViewGeom {
+    int idx0, dR, dF;
+    uint32_t colmask, rowmask;
+};
+
+__device__ __forceinline__ uint32_t bit_range(int lo, int hi)  // bits lo..hi of 0..6 (empty if lo > hi)
 {
-    if (!visible) return 0u;
-    const uint32_t t = 1u + 18u * cell_ent(code) + 3u * cell_col(code) + cell_st(code) + (agent_cell ? 198u : 0u);
-    return t < (uint32_t)NX_ATLAS_TILES ? t : 0u;  // codes outside the tables cannot index past the atlas
+    lo = max(lo, 0);
+    hi = min(hi, 6);
+    return lo > hi ? 0u : ((2u << hi) - (1u << lo));
 }
 
-// Egocentric view of one env: cell (vx, vy) shows world cell
-// pos + (6 - vy) F + (vx - 3) R (F facing, R its right-hand direction);
-// outside the grid reads as a grey wall; the agent's cell shows what it
-// carries.  Writes the 147 symbolic bytes (row-major [vy][vx][ent, col, st])
-// to `sym` and, if `tiles` is non-null, the 49 atlas tile indices.
+__device__ __forceinline__ ViewGeom view_geom(const AgentReg& a, int S)
+{
+    const int fx = (a.dir == 0) - (a.dir == 2), fy = (a.dir == 1) - (a.dir == 3);
+    const int rx = -fy, ry = fx;
+    ViewGeom g;
+    g.dF = fy * S + fx;
+    g.dR = ry * S + rx;
+    g.idx0 = a.y * S + a.x + 6 * g.dF - 3 * g.dR;
+    // along R: coordinate a_r + (vx - 3) * sign(R)
+    const int ar = rx != 0 ? a.x : a.y, sr = rx + ry;
+    g.colmask = sr > 0 ? bit_range(3 - ar, 3 + (S - 1 - ar)) : bit_range(3 - (S - 1 - ar), 3 + ar);
+    // along F: forward distance d = 6 - vy, coordinate a_f + d * sign(F)
+    const int af = fx != 0 ? a.x : a.y, sf = fx + fy;
+    const int dmax = sf > 0 ? S - 1 - af : af;
+    g.rowmask = bit_range(6 - dmax, 6);
+    return g;
+}
+
+// Code of view cell (vx, vy): the agent's cell shows what it carries (or
+// empty), cells outside the grid read as a grey wall.
+__device__ __forceinline__ uint32_t view_code(const uint8_t* g, const ViewGeom& v, const AgentReg& a, int vx, int vy)
+{
+    if (vx == 3 && vy == 6) return a.carry ? a.carry : (uint32_t)C_EMPTY;
+    const bool in = (v.colmask >> vx) & (v.rowmask >> vy) & 1u;
+    return in ? (uint32_t)g[v.idx0 + vx * v.dR - vy * v.dF] : (uint32_t)C_WALL;
+}
+
+// Atlas tile of a view cell from its triple: 0 unseen; 1 + 18 ent + 3 col +
+// st when visible; + 198 for the agent's own cell.
+__device__ __forceinline__ uint32_t tile_of_triple(bool visible, bool agent_cell, uint32_t tri)
+{
+    if (!visible) return 0u;
+    const uint32_t t = 1u + 18u * (tri & 0xFFu) + 3u * ((tri >> 8) & 0xFFu) + (tri >> 16) + (agent_cell ? 198u : 0u);
+    return t < (uint32_t)NX_ATLAS_TILES ? t : 0u;
+}
+
+// Egocentric view of one env, written as 147 symbolic bytes (row-major
+// [vy][vx][ent, col, st], unseen cells 0) at `sym` and, if `tiles` is
+// non-null, 49 atlas tile indices.
+//
+// G > 1: lane l owns cells c = l, l + G, ...; a ballot per round assembles the
+// transparency mask; each lane writes its cells' three bytes.
+// G = 1: the 49 codes are packed four per register, the transparency mask is
+// gathered four cells at a time from the opaque bits, and the byte stream is
+// written as 36 funnel-shifted 32-bit words plus three single bytes.
 template <int G>
 __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g, int S, const AgentReg& a,
                                             uint8_t* sym, uint16_t* tiles)
 {
-    constexpr int K = (49 + G - 1) / G;
-    const int fx = (a.dir == 0) - (a.dir == 2), fy = (a.dir == 1) - (a.dir == 3);
-    const int rx = -fy, ry = fx;  // right-hand direction = facing rotated clockwise (y grows downward)
-    uint32_t code[K];
-    uint64_t tmask = 0;
+    const ViewGeom v = view_geom(a, S);
+    if constexpr (G == 1) {
+        uint32_t packed[13];
+        uint64_t tmask = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int c = k * G + grp.lane;
-        uint32_t cd = 0;
-        if (c < 49) {
-            const int vy = c / 7, vx = c - 7 * vy;
-            if (c == 45) {
-                cd = a.carry ? a.carry : (uint32_t)C_EMPTY;
-            } else {
-                const int x = a.x + (6 - vy) * fx + (vx - 3) * rx;
-                const int y = a.y + (6 - vy) * fy + (vx - 3) * ry;
-                cd = ((unsigned)x < (unsigned)S && (unsigned)y < (unsigned)S) ? (uint32_t)g[y * S + x]
-                                                                              : (uint32_t)C_WALL;
+        for (int w = 0; w < 13; ++w) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int c = 4 * w + b;
+                if (c < 49) word |= view_code(g, v, a, c % 7, c / 7) << (8 * b);
             }
+            packed[w] = word;
+            // transparency bits of these four cells: the complement of their opaque bits
+            const uint32_t opq = (uint32_t)(((word & 0x80808080u) * 0x00204081u) >> 28);
+            tmask |= (uint64_t)(~opq & 0xFu) << (4 * w);
         }
-        code[k] = cd;
-        const uint32_t bits = grp.ballot(c < 49 && transparent(cd));
-        tmask |= (uint64_t)bits << (k * G);
-    }
-    const uint64_t vis = occlusion(tmask);
+        tmask &= (1ull << 49) - 1ull;
+        const uint64_t vis = occlusion(tmask);
+        uint32_t tri[49];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int c = k * G + grp.lane;
-        if (c < 49) {
-            const bool v = (vis >> c) & 1ull;
-            const uint32_t cd = code[k];
-            sym[3 * c + 0] = v ? (uint8_t)cell_ent(cd) : (uint8_t)0;
-            sym[3 * c + 1] = v ? (uint8_t)cell_col(cd) : (uint8_t)0;
-            sym[3 * c + 2] = v ? (uint8_t)cell_st(cd) : (uint8_t)0;
-            if (tiles) tiles[c] = (uint16_t)tile_of(v, c == 45, cd);
+        for (int c = 0; c < 49; ++c) {
+            const uint32_t code = (packed[c >> 2] >> (8 * (c & 3))) & 0xFFu;
+            const bool vb = (vis >> c) & 1ull;
+            tri[c] = vb ? cell_triple(code) : 0u;
+            if (tiles) tiles[c] = (uint16_t)tile_of_triple(vb, c == 45, tri[c]);
+        }
+        // stream words w_0..w_36 of the 147-byte record
+        uint32_t sw[37];
+#pragma unroll
+        for (int m = 0; m < 12; ++m) {
+            sw[3 * m] = tri[4 * m] | (tri[4 * m + 1] << 24);
+            sw[3 * m + 1] = (tri[4 * m + 1] >> 8) | (tri[4 * m + 2] << 16);
+            sw[3 * m + 2] = (tri[4 * m + 2] >> 16) | (tri[4 * m + 3] << 8);
+        }
+        sw[36] = tri[48];
+        const uint32_t head = (4u - ((uint32_t)(uintptr_t)sym & 3u)) & 3u;  // bytes before the first aligned word
+        for (uint32_t i = 0; i < head; ++i) sym[i] = (uint8_t)(sw[0] >> (8 * i));
+        uint32_t* wd = reinterpret_cast<uint32_t*>(sym + head);
+#pragma unroll
+        for (int i = 0; i < 36; ++i) wd[i] = __funnelshift_r(sw[i], sw[i + 1], 8 * head);
+        for (uint32_t i = head; i < 3; ++i) sym[144 + i] = (uint8_t)(sw[36] >> (8 * i));
+    } else {
+        constexpr int K = (49 + G - 1) / G;
+        uint32_t code[K];
+        uint64_t tmask = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int c = k * G + grp.lane;
+            uint32_t cd = C_WALL;
+            if (c < 49) cd = view_code(g, v, a, c % 7, c / 7);
+            code[k] = cd;
+            const uint32_t bits = grp.ballot(c < 49 && !(cd & OPAQUE));
+            tmask |= (uint64_t)bits << (k * G);
+        }
+        const uint64_t vis = occlusion(tmask);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int c = k * G + grp.lane;
+            if (c < 49) {
+                const bool vb = (vis >> c) & 1ull;
+                const uint32_t tri = vb ? cell_triple(code[k]) : 0u;
+                sym[3 * c + 0] = (uint8_t)tri;
+                sym[3 * c + 1] = (uint8_t)(tri >> 8);
+                sym[3 * c + 2] = (uint8_t)(tri >> 16);
+                if (tiles) tiles[c] = (uint16_t)tile_of_triple(vb, c == 45, tri);
+            }
         }
     }
 }

@@ -39,7 +39,9 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
     // transition system: each ball, in index order, moves to a uniformly drawn
     // empty cell of its 8-neighbourhood that is not the agent's cell
     if (family == NX_DYNOBS) {
-        for (int b = 0; b < a.nb; ++b) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (b >= a.nb) break;
             uint32_t cand = 0;
             int j = 0;
 #pragma unroll
@@ -55,7 +57,7 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
                 }
             const int cnt = __popc(cand);
             if (cnt > 0) {
-                int k = bounded(d[1 + b], (uint32_t)cnt);
+                int k = bounded(d[b], (uint32_t)cnt);
                 uint32_t c = cand;
                 for (int i = 0; i < k; ++i) c &= c - 1u;
                 const int jj = __ffs(c) - 1;          // 0..7 over the 8 neighbours, row-major
@@ -116,14 +118,14 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
             if (fk == K_DOOR_LOCKED) {
                 if (a.carry != 0u && cell_kind(a.carry) == K_KEY && cell_col(a.carry) == cell_col(fc)) {
                     write = fi;
-                    wcode = (K_DOOR_OPEN << 3) | cell_col(fc);
+                    wcode = make_code(K_DOOR_OPEN, cell_col(fc));
                 }
             } else if (fk == K_DOOR_CLOSED) {
                 write = fi;
-                wcode = (K_DOOR_OPEN << 3) | cell_col(fc);
+                wcode = make_code(K_DOOR_OPEN, cell_col(fc));
             } else if (fk == K_DOOR_OPEN) {
                 write = fi;
-                wcode = (K_DOOR_CLOSED << 3) | cell_col(fc);
+                wcode = make_code(K_DOOR_CLOSED, cell_col(fc));
             }
         }
         if (write >= 0) {
@@ -252,37 +254,71 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
 
         // steps == 0 with reset_all: one emission of the episode-0 start state
         const int emissions = p.reset_all ? 1 : steps;
+        const bool rnd = act_mode == NX_ACT_RANDOM;
+        const uint32_t n_act = family == NX_DYNOBS ? 3u : 7u;
+        uint32_t slot = call0 % (uint32_t)depth;
+        uint32_t my_draw = 0;  // G > 1: this lane's random-action draw for step s0 + lane
         for (int s = 0; s < emissions; ++s) {
-            const uint32_t slot = (call0 + (uint32_t)s) % (uint32_t)depth;
             const size_t row0 = (size_t)slot * nreq + item.local_begin;
             uint8_t* sym_dst = obs_sym ? obs_sym + row0 * NX_OBS_SYM_BYTES : nullptr;
             uint8_t* stage = sstage + ((uint32_t)(uintptr_t)sym_dst & 15u);
+            if (G > 1 && rnd && (s % G) == 0) {
+                // the random actions of the next G steps depend only on the step
+                // counter, so the group's lanes draw them in parallel
+                my_draw = (s + grp.lane < steps) ? draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)(s + grp.lane),
+                                                        PURPOSE_ACTION, 0u)
+                                                 : 0u;
+            }
+            // Episode starts (every env on a reset launch; autoreset after a
+            // terminal or truncated step).  Groups of 8 or more lanes lay out
+            // their own env; narrower groups hand every starting env of the
+            // warp to all 32 lanes, one env after another, so one resetting env
+            // never runs its layout generation serially while the rest of its
+            // warp waits.
+            const bool starts = active && (p.reset_all || a.done);
+            if constexpr (G >= 8) {
+                if (starts) {
+                    const int inv = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
+                    if (!reset_layout(grp, mygrid, S, family, n_balls, seed, key, p.reset_all ? 0u : a.episode + 1u, a))
+                        if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    a.invalid = inv;
+                }
+            } else {
+                unsigned lead = __ballot_sync(0xFFFFFFFFu, starts && grp.lane == 0);
+                while (lead) {
+                    const int L = __ffs(lead) - 1;
+                    lead &= lead - 1u;
+                    const uint32_t ep = __shfl_sync(0xFFFFFFFFu, p.reset_all ? 0u : a.episode + 1u, L);
+                    const uint32_t k = __shfl_sync(0xFFFFFFFFu, key, L);
+                    const int owner = ((tid & ~31) + L) / G;  // group (env slot) of lane L
+                    AgentReg na;
+                    const bool ok = reset_layout_warp(sgrid + owner * p.cell_stride, S, family, n_balls, seed, k, ep, na);
+                    if (!ok && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    if (gi == owner) {
+                        na.invalid = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
+                        a = na;
+                    }
+                }
+                __syncwarp();
+            }
             if (active) {
                 float reward = 0.0f;
                 int term = 0, trunc = 0;
-                if (p.reset_all) {
-                    a.invalid = 0;
-                    if (!reset_layout(grp, mygrid, S, family, n_balls, seed, key, 0u, a)) {
-                        if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
-                    }
-                } else if (a.done) {
-                    // autoreset: the next episode's start, reward padding 0, action ignored
-                    if (!reset_layout(grp, mygrid, S, family, n_balls, seed, key, a.episode + 1u, a)) {
-                        if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
-                    }
+                if (starts) {
+                    // the new episode's start: reward padding 0, the action is ignored
                 } else {
                     uint32_t d[8];
-                    const bool rnd = act_mode == NX_ACT_RANDOM;
-                    const int nd = 1 + (family == NX_DYNOBS ? a.nb : 0);
-                    const uint32_t gstep = gstep0 + (uint32_t)s;
-                    const uint32_t episode = a.episode, t = (uint32_t)a.t;
-                    group_draws(grp, nd, d, [&](uint32_t k) -> uint32_t {
-                        if (k == 0) return rnd ? draw(seed, key, 0xFFFFFFFFu, gstep, PURPOSE_ACTION, 0u) : 0u;
-                        return draw(seed, key, episode, t, PURPOSE_BALL, k - 1u);
-                    });
+                    if (family == NX_DYNOBS) {
+                        const uint32_t episode = a.episode, t = (uint32_t)a.t;
+                        group_draws(grp, a.nb, d, [&](uint32_t k) -> uint32_t {
+                            return draw(seed, key, episode, t, PURPOSE_BALL, k);
+                        });
+                    }
                     int action;
                     if (rnd) {
-                        action = bounded(d[0], family == NX_DYNOBS ? 3u : 7u);
+                        const uint32_t x = G > 1 ? grp.shfl(my_draw, s % G)
+                                                 : draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)s, PURPOSE_ACTION, 0u);
+                        action = bounded(x, n_act);
                     } else {
                         action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
                     }
@@ -316,6 +352,7 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
             if (sym_dst) coop_copy(sym_dst, stage, n * NX_OBS_SYM_BYTES, tid, nthreads);
             if (RGB && obs_rgb) coop_rgb(obs_rgb + row0 * NX_OBS_RGB_BYTES, stiles, p.atlas, n, tid, nthreads);
             __syncthreads();
+            slot = slot + 1u == (uint32_t)depth ? 0u : slot + 1u;
         }
 
         // write the state back
