@@ -66,8 +66,10 @@ enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2 };
 enum { NX_ACT_BUFFER = 0, NX_ACT_RANDOM = 1 };
 /* reward functions: Markovian (Section 3.2.1, Table 5) or MiniGrid's Eq. 1 */
 enum { NX_REWARD_MARKOV = 0, NX_REWARD_MINIGRID = 1 };
-/* smem staging layouts of the grid (tunable; never changes results) */
-enum { NX_STAGE_AUTO = 0, NX_STAGE_BYTE = 1, NX_STAGE_WORD = 2 };
+/* staging of the symbolic outputs in shared memory (tunable; never changes
+ * results): the whole thread block's block of observations at once, or in
+ * two halves (half the staging memory, so more envs stay resident) */
+enum { NX_STAGE_AUTO = 0, NX_STAGE_FULL = 1, NX_STAGE_HALF = 2 };
 
 #define NX_MIN_SIZE 5
 #define NX_MAX_SIZE 19
@@ -99,7 +101,7 @@ typedef struct {
     int32_t autotune;         /* 1: time the launch shapes once and keep the fastest (default 1) */
     int32_t group_lanes;      /* lanes per env, 1/2/4/8/16/32; 0 = chosen by the library */
     int32_t envs_per_cta;     /* envs per thread block; 0 = chosen by the library */
-    int32_t staging;          /* NX_STAGE_*; 0 = chosen by the library */
+    int32_t staging;          /* NX_STAGE_*; 0 = chosen by the library (used with group_lanes) */
     const uint8_t* atlas;     /* host sprite atlas, NX_ATLAS_BYTES (required with NX_OBS_RGB) */
     /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMallocAsync */
     void* (*alloc)(size_t bytes, void* user);

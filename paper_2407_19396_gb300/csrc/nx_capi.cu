@@ -294,8 +294,9 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
     env->req_host.key_base = o.env_index_base;
 
     // default launch shape (replaced by the autotuner when enabled)
-    nx_launch_shape s{8, 32, env->rgb ? 1 : 0};
-    if (o.group_lanes) s = nx_launch_shape{o.group_lanes, o.envs_per_cta, env->rgb ? 1 : 0};
+    nx_launch_shape s{8, 32, env->rgb ? 1 : 0, 1};
+    if (o.group_lanes)
+        s = nx_launch_shape{o.group_lanes, o.envs_per_cta, env->rgb ? 1 : 0, o.staging == NX_STAGE_HALF ? 2 : 1};
     nx_status st = nx_apply_shape(env, s);
     if (st != NX_OK) {
         std::string m = env->last_error;
@@ -387,6 +388,7 @@ nx_kparams nx_params(const nx_env* env, int launch_steps, int reset_all)
     p.cell_stride = env->cell_stride;
     p.envs_per_cta = env->shape.envs_per_cta;
     p.reset_all = reset_all;
+    p.phases = env->shape.phases;
     return p;
 }
 
@@ -711,14 +713,16 @@ nx_status nx_autotune(nx_env* env)
     nx_launch_shape best = orig;
     float best_ms = 1e30f;
     for (int G : lanes)
-        for (int th : threads) {
-            nx_launch_shape s{G, th / G, env->rgb ? 1 : 0};
+        for (int th : threads)
+            for (int ph = 1; ph <= 2; ++ph) {
+            nx_launch_shape s{G, th / G, env->rgb ? 1 : 0, ph};
             if (!nx_shape_supported(s)) continue;
             if (nx_apply_shape(env, s) != NX_OK) {
                 cudaGetLastError();
                 continue;
             }
             nx_kparams p = nx_params(env, T, 0);
+            p.phases = s.phases;
             p.agents = sa;
             p.grids = sg;
             p.reqs = sr;
@@ -742,7 +746,7 @@ nx_status nx_autotune(nx_env* env)
                 best = s;
             }
             env->tune_log.push_back(nx_tune_entry{s.group_lanes, s.envs_per_cta, ms_min});
-        }
+            }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(env->stream);
@@ -859,7 +863,7 @@ nx_status nx_get_info(const nx_env* env, nx_info* info)
     memset(info, 0, sizeof *info);
     info->group_lanes = env->shape.group_lanes;
     info->envs_per_cta = env->shape.envs_per_cta;
-    info->staging = NX_STAGE_BYTE;
+    info->staging = env->shape.phases > 1 ? NX_STAGE_HALF : NX_STAGE_FULL;
     info->n_items = env->n_items;
     info->grid_ctas = env->grid_ctas;
     info->smem_bytes = nx_kernel_smem_bytes(env->shape, env->cell_stride);

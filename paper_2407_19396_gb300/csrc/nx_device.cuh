@@ -466,18 +466,28 @@ __device__ __forceinline__ uint32_t tile_of_triple(bool visible, bool agent_cell
     return t < (uint32_t)NX_ATLAS_TILES ? t : 0u;
 }
 
-// Egocentric view of one env, written as 147 symbolic bytes (row-major
-// [vy][vx][ent, col, st], unseen cells 0) at `sym` and, if `tiles` is
-// non-null, 49 atlas tile indices.
+// Egocentric view of one env: render_view computes it into registers (and,
+// if `tiles` is non-null, writes the 49 atlas tile indices); write_view then
+// stores the 147 symbolic bytes (row-major [vy][vx][ent, col, st], unseen
+// cells 0) at `sym`.  `dec` maps a cell code to its observation triple.
 //
 // G > 1: lane l owns cells c = l, l + G, ...; a ballot per round assembles the
-// transparency mask; each lane writes its cells' three bytes.
+// transparency mask; each lane stores its cells' three bytes.
 // G = 1: the 49 codes are packed four per register, the transparency mask is
 // gathered four cells at a time from the opaque bits, and the byte stream is
-// written as 36 funnel-shifted 32-bit words plus three single bytes.
+// stored as 36 funnel-shifted 32-bit words plus three single bytes.
+template <int G>
+struct ViewOut {
+    uint32_t tri[(49 + G - 1) / G];
+};
+template <>
+struct ViewOut<1> {
+    uint32_t sw[37];  // stream words of the 147-byte record
+};
+
 template <int G>
 __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g, int S, const AgentReg& a,
-                                            uint8_t* sym, uint16_t* tiles)
+                                            const uint32_t* dec, ViewOut<G>& out, uint16_t* tiles)
 {
     const ViewGeom v = view_geom(a, S);
     if constexpr (G == 1) {
@@ -503,24 +513,16 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
         for (int c = 0; c < 49; ++c) {
             const uint32_t code = (packed[c >> 2] >> (8 * (c & 3))) & 0xFFu;
             const bool vb = (vis >> c) & 1ull;
-            tri[c] = vb ? cell_triple(code) : 0u;
+            tri[c] = vb ? dec[code] : 0u;
             if (tiles) tiles[c] = (uint16_t)tile_of_triple(vb, c == 45, tri[c]);
         }
-        // stream words w_0..w_36 of the 147-byte record
-        uint32_t sw[37];
 #pragma unroll
         for (int m = 0; m < 12; ++m) {
-            sw[3 * m] = tri[4 * m] | (tri[4 * m + 1] << 24);
-            sw[3 * m + 1] = (tri[4 * m + 1] >> 8) | (tri[4 * m + 2] << 16);
-            sw[3 * m + 2] = (tri[4 * m + 2] >> 16) | (tri[4 * m + 3] << 8);
+            out.sw[3 * m] = tri[4 * m] | (tri[4 * m + 1] << 24);
+            out.sw[3 * m + 1] = (tri[4 * m + 1] >> 8) | (tri[4 * m + 2] << 16);
+            out.sw[3 * m + 2] = (tri[4 * m + 2] >> 16) | (tri[4 * m + 3] << 8);
         }
-        sw[36] = tri[48];
-        const uint32_t head = (4u - ((uint32_t)(uintptr_t)sym & 3u)) & 3u;  // bytes before the first aligned word
-        for (uint32_t i = 0; i < head; ++i) sym[i] = (uint8_t)(sw[0] >> (8 * i));
-        uint32_t* wd = reinterpret_cast<uint32_t*>(sym + head);
-#pragma unroll
-        for (int i = 0; i < 36; ++i) wd[i] = __funnelshift_r(sw[i], sw[i + 1], 8 * head);
-        for (uint32_t i = head; i < 3; ++i) sym[144 + i] = (uint8_t)(sw[36] >> (8 * i));
+        out.sw[36] = tri[48];
     } else {
         constexpr int K = (49 + G - 1) / G;
         uint32_t code[K];
@@ -538,13 +540,33 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int c = k * G + grp.lane;
+            const bool vb = c < 49 && ((vis >> c) & 1ull);
+            out.tri[k] = vb ? dec[code[k]] : 0u;
+            if (tiles && c < 49) tiles[c] = (uint16_t)tile_of_triple(vb, c == 45, out.tri[k]);
+        }
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void write_view(const Grp<G>& grp, const ViewOut<G>& out, uint8_t* sym)
+{
+    if constexpr (G == 1) {
+        const uint32_t head = (4u - ((uint32_t)(uintptr_t)sym & 3u)) & 3u;  // bytes before the first aligned word
+        for (uint32_t i = 0; i < head; ++i) sym[i] = (uint8_t)(out.sw[0] >> (8 * i));
+        uint32_t* wd = reinterpret_cast<uint32_t*>(sym + head);
+#pragma unroll
+        for (int i = 0; i < 36; ++i) wd[i] = __funnelshift_r(out.sw[i], out.sw[i + 1], 8 * head);
+        for (uint32_t i = head; i < 3; ++i) sym[144 + i] = (uint8_t)(out.sw[36] >> (8 * i));
+    } else {
+        constexpr int K = (49 + G - 1) / G;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int c = k * G + grp.lane;
             if (c < 49) {
-                const bool vb = (vis >> c) & 1ull;
-                const uint32_t tri = vb ? cell_triple(code[k]) : 0u;
+                const uint32_t tri = out.tri[k];
                 sym[3 * c + 0] = (uint8_t)tri;
                 sym[3 * c + 1] = (uint8_t)(tri >> 8);
                 sym[3 * c + 2] = (uint8_t)(tri >> 16);
-                if (tiles) tiles[c] = (uint16_t)tile_of_triple(vb, c == 45, tri);
             }
         }
     }

@@ -89,7 +89,7 @@ struct nx_kparams {
     int32_t cell_stride;   // smem bytes per env grid (>= max size^2, multiple of 16)
     int32_t envs_per_cta;
     int32_t reset_all;     // 1: start every env at episode 0 and emit its observation (no steps)
-    int32_t pad;
+    int32_t phases;        // symbolic staging parts per step (1 or 2)
 };
 
 // Host-side launch helpers implemented in nx_kernels.cu.
@@ -97,6 +97,7 @@ struct nx_launch_shape {
     int group_lanes;
     int envs_per_cta;
     int rgb;
+    int phases = 1;  // the symbolic outputs of a CTA are staged and stored in this many parts (1 or 2)
 };
 int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride);
 int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err);  // resident CTAs on the device

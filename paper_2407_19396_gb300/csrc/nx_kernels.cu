@@ -74,65 +74,42 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
             }
         }
     }
-    // intervention system
-    int goal = 0, lava = 0, hit = 0;
+    // intervention system, written as selects so that envs of one warp taking
+    // different actions do not serialise on branches
     const int n_act = family == NX_DYNOBS ? 3 : 7;
-    if (action < 0 || action > 6) {
+    if ((unsigned)action > 6u) {
         if (!a.invalid && grp.lane == 0) atomicOr(&ctl->flags, (unsigned)NX_FLAG_INVALID_ACTION);
         a.invalid = 1;
-    } else if (action < n_act) {
-        const int fxd = (a.dir == 0) - (a.dir == 2), fyd = (a.dir == 1) - (a.dir == 3);
-        const int fx = a.x + fxd, fy = a.y + fyd;
-        const bool in = (unsigned)fx < (unsigned)S && (unsigned)fy < (unsigned)S;
-        const int fi = fy * S + fx;
-        const uint32_t fc = in ? (uint32_t)g[fi] : (uint32_t)C_WALL;
-        const uint32_t fk = cell_kind(fc);
-        int write = -1;
-        uint32_t wcode = 0;
-        if (action == 0) {
-            a.dir = (a.dir + 3) & 3;
-        } else if (action == 1) {
-            a.dir = (a.dir + 1) & 3;
-        } else if (action == 2) {
-            if (family == NX_DYNOBS && fk == K_BALL) {
-                hit = 1;
-            } else if (walkable(fc)) {
-                a.x = fx;
-                a.y = fy;
-                goal = fk == K_GOAL;
-                lava = fk == K_LAVA;
-            }
-        } else if (action == 3) {
-            if (a.carry == 0u && (fk == K_KEY || fk == K_BALL)) {
-                a.carry = fc;
-                write = fi;
-                wcode = C_EMPTY;
-            }
-        } else if (action == 4) {
-            if (a.carry != 0u && in && fc == C_EMPTY) {
-                write = fi;
-                wcode = a.carry;
-                a.carry = 0u;
-            }
-        } else if (action == 5) {
-            if (fk == K_DOOR_LOCKED) {
-                if (a.carry != 0u && cell_kind(a.carry) == K_KEY && cell_col(a.carry) == cell_col(fc)) {
-                    write = fi;
-                    wcode = make_code(K_DOOR_OPEN, cell_col(fc));
-                }
-            } else if (fk == K_DOOR_CLOSED) {
-                write = fi;
-                wcode = make_code(K_DOOR_OPEN, cell_col(fc));
-            } else if (fk == K_DOOR_OPEN) {
-                write = fi;
-                wcode = make_code(K_DOOR_CLOSED, cell_col(fc));
-            }
-        }
-        if (write >= 0) {
-            grp.sync();
-            if (grp.lane == 0) g[write] = (uint8_t)wcode;
-            grp.sync();
-        }
+    }
+    const bool acts = (unsigned)action < (unsigned)n_act;  // out-of-range and restricted actions are no-ops
+    const int fxd = (a.dir == 0) - (a.dir == 2), fyd = (a.dir == 1) - (a.dir == 3);
+    const int fx = a.x + fxd, fy = a.y + fyd;
+    const bool in = (unsigned)fx < (unsigned)S && (unsigned)fy < (unsigned)S;
+    const int fi = fy * S + fx;
+    const uint32_t fc = in ? (uint32_t)g[fi] : (uint32_t)C_WALL;
+    const uint32_t fk = cell_kind(fc), fcol = cell_col(fc);
+    const bool is_fwd = acts && action == 2;
+    const bool hit = is_fwd && family == NX_DYNOBS && fk == K_BALL;
+    const bool move = is_fwd && !hit && walkable(fc);
+    const bool pick = acts && action == 3 && a.carry == 0u && (fk == K_KEY || fk == K_BALL);
+    const bool drop = acts && action == 4 && a.carry != 0u && in && fc == C_EMPTY;
+    const bool tog = acts && action == 5;
+    const bool unlock = tog && fk == K_DOOR_LOCKED && a.carry != 0u && cell_kind(a.carry) == K_KEY &&
+                        cell_col(a.carry) == fcol;
+    const bool open_ = tog && fk == K_DOOR_CLOSED;
+    const bool close_ = tog && fk == K_DOOR_OPEN;
+    const int goal = move && fk == K_GOAL, lava = move && fk == K_LAVA;
+    a.dir = (a.dir + ((acts && action == 1) ? 1 : 0) + ((acts && action == 0) ? 3 : 0)) & 3;
+    a.x = move ? fx : a.x;
+    a.y = move ? fy : a.y;
+    const bool write = pick || drop || unlock || open_ || close_;
+    const uint32_t wcode = pick ? (uint32_t)C_EMPTY
+                                : drop ? a.carry : (close_ ? make_code(K_DOOR_CLOSED, fcol) : make_code(K_DOOR_OPEN, fcol));
+    a.carry = pick ? fc : (drop ? 0u : a.carry);
+    if (write) {
+        grp.sync();
+        if (grp.lane == 0) g[fi] = (uint8_t)wcode;
+        grp.sync();
     }
     // time and truncation; reward and termination on the goal / lava / hit events
     a.t += 1;
@@ -194,14 +171,21 @@ template <int G, bool RGB>
 __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p)
 {
     extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t s_dec[256];  // cell code -> observation triple
     const int E = p.envs_per_cta;
-    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int phases = p.phases > 1 ? 2 : 1;
+    const int tid = threadIdx.x, nthreads = blockDim.x, lane32 = tid & 31, warp = tid >> 5;
+    constexpr int epw = 32 / G;                         // envs per warp
+    const int whalf = (epw + phases - 1) / phases;      // envs staged per part
+    const int wbytes = align16(whalf * NX_OBS_SYM_BYTES + 16);
+    const int wenv0 = warp * epw;                       // the warp's first env slot
     uint8_t* sgrid = smem;
-    uint8_t* sstage = smem + E * p.cell_stride;
-    uint16_t* stiles = reinterpret_cast<uint16_t*>(sstage + align16(E * NX_OBS_SYM_BYTES + 16));
+    uint8_t* wstage = smem + E * p.cell_stride + warp * wbytes;
+    uint16_t* stiles = reinterpret_cast<uint16_t*>(smem + E * p.cell_stride + (nthreads >> 5) * wbytes);
     const int gi = tid / G;
     const Grp<G> grp(tid);
     uint8_t* mygrid = sgrid + gi * p.cell_stride;
+    for (int i = tid; i < 256; i += nthreads) s_dec[i] = cell_triple((uint32_t)i);
 
     for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
         const nx_item item = p.items[it];
@@ -261,7 +245,9 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
         for (int s = 0; s < emissions; ++s) {
             const size_t row0 = (size_t)slot * nreq + item.local_begin;
             uint8_t* sym_dst = obs_sym ? obs_sym + row0 * NX_OBS_SYM_BYTES : nullptr;
-            uint8_t* stage = sstage + ((uint32_t)(uintptr_t)sym_dst & 15u);
+            ViewOut<G> vo;
+            float reward = 0.0f;
+            int term = 0, trunc = 0;
             if (G > 1 && rnd && (s % G) == 0) {
                 // the random actions of the next G steps depend only on the step
                 // counter, so the group's lanes draw them in parallel
@@ -302,8 +288,6 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
                 __syncwarp();
             }
             if (active) {
-                float reward = 0.0f;
-                int term = 0, trunc = 0;
                 if (starts) {
                     // the new episode's start: reward padding 0, the action is ignored
                 } else {
@@ -326,8 +310,7 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
                              trunc, p.ctl);
                 }
                 grp.sync();
-                uint8_t* my_sym = stage + gi * NX_OBS_SYM_BYTES;
-                render_view(grp, mygrid, S, a, my_sym, RGB && obs_rgb ? stiles + gi * 49 : nullptr);
+                render_view(grp, mygrid, S, a, s_dec, vo, RGB && obs_rgb ? stiles + gi * 49 : nullptr);
                 if (grp.lane == 0) {
                     const size_t o = (size_t)slot * nreq + local;
                     if (out_reward) out_reward[o] = reward;
@@ -336,26 +319,45 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
                     ret += reward;
                     eps += (uint32_t)(term || trunc);
                 }
-                if (digest) {
-                    grp.sync();
-                    if (grp.lane == 0) {
+            }
+            // Each warp stages the symbolic outputs of its own envs (placed at
+            // the same address modulo 16 as their destination) and stores them
+            // with 16-byte vectors, in `phases` parts; warps never wait for
+            // each other here.
+            for (int ph = 0; ph < phases; ++ph) {
+                const int lo = wenv0 + ph * whalf, hi = min(n, min(wenv0 + epw, lo + whalf));
+                uint8_t* dst = sym_dst ? sym_dst + (size_t)lo * NX_OBS_SYM_BYTES : nullptr;
+                uint8_t* stage = wstage + ((uint32_t)(uintptr_t)dst & 15u);
+                if (active && gi >= lo && gi < hi) {
+                    uint8_t* my_sym = stage + (gi - lo) * NX_OBS_SYM_BYTES;
+                    write_view(grp, vo, my_sym);
+                    if (digest) {
+                        grp.sync();
+                        if (grp.lane == 0) {
 #pragma unroll 7
-                        for (int c = 0; c < 49; ++c)
-                            dig = digest_word(dig, (uint32_t)my_sym[3 * c] | ((uint32_t)my_sym[3 * c + 1] << 8) |
-                                                       ((uint32_t)my_sym[3 * c + 2] << 16));
-                        dig = digest_word(dig, __float_as_uint(reward));
-                        dig = digest_word(dig, (uint32_t)term | ((uint32_t)trunc << 8));
+                            for (int c = 0; c < 49; ++c)
+                                dig = digest_word(dig, (uint32_t)my_sym[3 * c] | ((uint32_t)my_sym[3 * c + 1] << 8) |
+                                                           ((uint32_t)my_sym[3 * c + 2] << 16));
+                            dig = digest_word(dig, __float_as_uint(reward));
+                            dig = digest_word(dig, (uint32_t)term | ((uint32_t)trunc << 8));
+                        }
                     }
                 }
+                __syncwarp();
+                if (dst && hi > lo) coop_copy(dst, stage, (hi - lo) * NX_OBS_SYM_BYTES, lane32, 32);
+                __syncwarp();
             }
-            __syncthreads();
-            if (sym_dst) coop_copy(sym_dst, stage, n * NX_OBS_SYM_BYTES, tid, nthreads);
-            if (RGB && obs_rgb) coop_rgb(obs_rgb + row0 * NX_OBS_RGB_BYTES, stiles, p.atlas, n, tid, nthreads);
-            __syncthreads();
+            if (RGB && obs_rgb) {
+                __syncthreads();
+                coop_rgb(obs_rgb + row0 * NX_OBS_RGB_BYTES, stiles, p.atlas, n, tid, nthreads);
+                __syncthreads();
+            }
             slot = slot + 1u == (uint32_t)depth ? 0u : slot + 1u;
         }
 
-        // write the state back
+        // write the state back (the grids are written back by every thread of
+        // the CTA, so all groups' last smem writes must be visible first)
+        __syncthreads();
         if (active && grp.lane == 0) {
             store_agent(p.agents + env, a, item, item.grid_offset + (uint32_t)(gi * 3 * HW));
             if (returns) returns[local] = ret;
@@ -410,8 +412,9 @@ int launch_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
 }
 
 // The dynamic shared-memory limit is a per-kernel attribute shared by every
-// context in the process, so it is always raised to the device's opt-in
-// maximum (never lowered to one context's need).
+// context in the process, so it is always raised to the most the device
+// allows next to the kernel's static shared memory (never lowered to one
+// context's need).
 template <int G, bool RGB>
 int occupancy_t(int threads, int smem, int* err)
 {
@@ -419,11 +422,14 @@ int occupancy_t(int threads, int smem, int* err)
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess && smem > optin) {
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+    const int dyn_max = e == cudaSuccess ? optin - (int)fa.sharedSizeBytes : 0;  // static + dynamic <= opt-in limit
+    if (e == cudaSuccess && smem > dyn_max) {
         *err = 0;
         return 0;
     }
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     int blocks = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, threads, smem);
     *err = (int)e;
@@ -444,7 +450,9 @@ int nx_shape_supported(const nx_launch_shape& s)
 int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride)
 {
     const int E = s.envs_per_cta;
-    int b = E * cell_stride + align16(E * NX_OBS_SYM_BYTES + 16);
+    const int epw = 32 / s.group_lanes, warps = E * s.group_lanes / 32;
+    const int whalf = s.phases > 1 ? (epw + 1) / 2 : epw;
+    int b = E * cell_stride + warps * align16(whalf * NX_OBS_SYM_BYTES + 16);
     if (s.rgb) b += align16(E * 49 * 2);
     return b;
 }

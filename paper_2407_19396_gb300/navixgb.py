@@ -24,6 +24,7 @@ NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS = range(5)
 NX_OBS_SYM, NX_OBS_RGB = 1, 2
 NX_ACT_BUFFER, NX_ACT_RANDOM = 0, 1
 NX_REWARD_MARKOV, NX_REWARD_MINIGRID = 0, 1
+NX_STAGE_AUTO, NX_STAGE_FULL, NX_STAGE_HALF = 0, 1, 2
 OBS_SYM_BYTES, OBS_RGB_BYTES = 147, 150528
 ATLAS_BYTES = 397 * 3072
 AGENT_BYTES = 32
@@ -297,7 +298,7 @@ class Env:
 
     def __init__(self, family=NX_EMPTY, size=5, n_envs=1, seed=0, *, descs=None, obs_sym=True, obs_rgb=False,
                  atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
-                 autotune=True, group_lanes=0, envs_per_cta=0, env_index_base=0, torch_allocator=True):
+                 autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, torch_allocator=True):
         import torch
 
         self.torch = torch
@@ -314,6 +315,7 @@ class Env:
         o.autotune = 1 if autotune else 0
         o.group_lanes = group_lanes
         o.envs_per_cta = envs_per_cta
+        o.staging = staging
         o.env_index_base = env_index_base
         self._atlas = None
         if obs_rgb:

@@ -52,20 +52,23 @@ def test_reset_matches_oracle(family, size):
     env.close()
 
 
-@pytest.mark.parametrize("lanes,envs", [(1, 64), (2, 64), (4, 32), (8, 16), (16, 8), (32, 8), (8, 32), (1, 256)])
-def test_rollout_every_shape_every_step(lanes, envs):
+@pytest.mark.parametrize("lanes,envs,staging", [(1, 64, 1), (2, 64, 1), (4, 32, 1), (8, 16, 1), (16, 8, 1), (32, 8, 1),
+                                                (8, 32, 1), (1, 256, 1), (1, 64, 2), (1, 128, 2), (8, 32, 2),
+                                                (32, 2, 2), (4, 64, 2)])
+def test_rollout_every_shape_every_step(lanes, envs, staging):
     nx = nxmod()
     descs = mixed_descs(150, [(O.EMPTY, 5), (O.DOORKEY, 8), (O.FOURROOMS, 19), (O.LAVAGAP, 7), (O.DYNOBS, 8),
                               (O.DOORKEY, 16)])
-    env = nx.Env(descs=descs, seed=5, group_lanes=lanes, envs_per_cta=envs, autotune=False, steps_per_launch=64)
+    env = nx.Env(descs=descs, seed=5, group_lanes=lanes, envs_per_cta=envs, staging=staging, autotune=False,
+                 steps_per_launch=64)
     env.reset()
     T = 300
     out = env.rollout(T)
     ob = oracle_batch_for(descs, 5)
     ob.reset()
     oo = ob.rollout(T)
-    assert_outputs_equal(out, oo, what=f"G={lanes} E={envs}")
-    assert_states_equal(env.state()["envs"], ob, what=f"G={lanes} E={envs}")
+    assert_outputs_equal(out, oo, what=f"G={lanes} E={envs} staging={staging}")
+    assert_states_equal(env.state()["envs"], ob, what=f"G={lanes} E={envs} staging={staging}")
     env.close()
 
 
