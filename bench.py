@@ -47,6 +47,9 @@ WORKLOADS = {
     "rgb": dict(desc="Dynamic-Obstacles-16x16, 4 balls, 8192 envs x 512 steps, seed 3, 3 random actions, "
                      "RGB 224x224x3 + symbolic obs (8-slot output ring)",
                 parts=[(4, 16)], n=8192, T=512, seed=3, rgb=True, depth=8),
+    # a reduced RGB case sized for ncu captures only (about 2.5 GB written per launch)
+    "rgb_small": dict(desc="Dynamic-Obstacles-16x16, 4 balls, 1024 envs x 16 steps, seed 3, RGB + symbolic, 2-slot ring",
+                      parts=[(4, 16)], n=1024, T=16, seed=3, rgb=True, depth=2, steps_per_launch=16),
 }
 OUT_BYTES_SYM = 147 + 4 + 2  # symbolic obs + reward + two flags per env-step
 OUT_BYTES_RGB = 150528
@@ -327,7 +330,7 @@ def main():
     ap.add_argument("--workload", default="doorkey8", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the other configs and the CPU baseline")
     ap.add_argument("--ncu-case", action="store_true", help="one rollout of the workload for an ncu capture")
-    ap.add_argument("--shape", default="", help="force the launch shape as LANES,ENVS_PER_CTA (no autotuning)")
+    ap.add_argument("--shape", default="", help="force the launch shape as LANES,ENVS_PER_CTA[,STAGING] (no autotuning)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.ncu_case:
         args.warmup = 3
@@ -353,8 +356,11 @@ def main():
     atlas = inputs.atlas() if w["rgb"] else None
     shape = {}
     if args.shape:
-        g, e = (int(v) for v in args.shape.split(","))
-        shape = dict(group_lanes=g, envs_per_cta=e, autotune=False)
+        vals = [int(v) for v in args.shape.split(",")]
+        shape = dict(group_lanes=vals[0], envs_per_cta=vals[1], staging=vals[2] if len(vals) > 2 else 1,
+                     autotune=False)
+    if "steps_per_launch" in w:
+        shape["steps_per_launch"] = w["steps_per_launch"]
     env = nx.Env(descs=descs, seed=w["seed"], obs_rgb=w["rgb"], atlas=atlas, env_index_base=rank * n, **shape)
     env.reset()
     out = env.alloc_out(w["depth"])

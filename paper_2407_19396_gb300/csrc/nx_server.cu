@@ -227,7 +227,7 @@ void items_of(const nx_server* s, const SReq& q, std::vector<nx_item>& out)
 void retire(nx_server* s, uint64_t t)
 {
     std::unique_lock<std::mutex> lk(s->mu);
-    SReq& q = s->reqs[t];
+    SReq& q = s->reqs.at(t);
     const int n = q.r.n_envs;
     const uint8_t* h = s->h_pool + q.host_off;  // same relative layout as the device tail
     const float* ret = (const float*)h;
@@ -280,7 +280,7 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         std::unique_lock<std::mutex> lk(s->mu);
         while (!s->stop && !s->waiting.empty() && !s->free_slots.empty()) {
             const uint64_t t = s->waiting.front();
-            SReq& q = s->reqs[t];
+            SReq& q = s->reqs.at(t);
             size_t doff, hoff;
             if (!s->dev_alloc.alloc(q.lay.total, &doff)) break;
             if (!s->host_alloc.alloc(q.lay.tail, &hoff)) {
@@ -315,21 +315,29 @@ bool iterate(nx_server* s, int& cur, bool* idle)
     nx_item* hi = s->h_items[cur];
     std::vector<nx_item> reset_items, step_items;
     std::vector<uint64_t> finishing, still;
+    // element addresses of the request map never move, but lookups must not
+    // race with nx_submit's insertions: take the pointers under the lock
+    std::vector<const SReq*> fresh_q, finishing_q;
     int launch_steps = 0;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        for (uint64_t t : fresh) items_of(s, s->reqs[t], reset_items);
+        for (uint64_t t : fresh) {
+            fresh_q.push_back(&s->reqs.at(t));
+            items_of(s, *fresh_q.back(), reset_items);
+        }
         for (uint64_t t : s->active) {
-            SReq& q = s->reqs[t];
+            SReq& q = s->reqs.at(t);
             const int k = std::min(s->chunk, q.r.horizon - q.launched);
             hr[q.slot] = record_of(s, q, k);
             items_of(s, q, step_items);
             launch_steps = std::max(launch_steps, k);
             q.launched += k;
-            if (q.launched >= q.r.horizon)
+            if (q.launched >= q.r.horizon) {
                 finishing.push_back(t);
-            else
+                finishing_q.push_back(&q);
+            } else {
                 still.push_back(t);
+            }
         }
         s->active = still;
         s->stats.chunks += 1;
@@ -355,8 +363,8 @@ bool iterate(nx_server* s, int& cur, bool* idle)
     p.envs_per_cta = s->shape.envs_per_cta;
     const int max_grid = s->per_sm * s->sm_count;
     if (nr) {
-        for (uint64_t t : fresh) {
-            const SReq& q = s->reqs[t];
+        for (const SReq* qp : fresh_q) {
+            const SReq& q = *qp;
             SRV_CK(cudaMemsetAsync(s->d_pool + q.dev_off + q.lay.returns, 0, q.lay.obs - q.lay.returns, s->stream),
                    "accumulator clear");
         }
@@ -375,8 +383,8 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         int rc = nx_launch_step_kernel(s->shape, p, std::min((int)ns, max_grid), s->stream);
         if (rc) SRV_CK((cudaError_t)rc, "step launch");
     }
-    for (uint64_t t : finishing) {
-        const SReq& q = s->reqs[t];
+    for (const SReq* qp : finishing_q) {
+        const SReq& q = *qp;
         SRV_CK(cudaMemcpyAsync(s->h_pool + q.host_off, s->d_pool + q.dev_off + q.lay.returns, q.lay.tail,
                                cudaMemcpyDeviceToHost, s->stream),
                "result copy");
@@ -536,15 +544,18 @@ nx_status nx_wait(nx_server* s, uint64_t ticket, nx_result* res, double timeout_
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(ticket);
     if (it == s->reqs.end()) return nx_fail(nullptr, NX_E_INVAL, "unknown ticket");
-    auto done = [&] { return it->second.finished; };
+    // an element's address survives insertions (an iterator may not), and the
+    // lock is released while waiting
+    const SReq* q = &it->second;
+    auto done = [&] { return q->finished; };
     if (timeout_s > 0) {
         if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done))
             return nx_fail(nullptr, NX_E_TIMEOUT, "request did not finish in time");
     } else {
         s->cv_done.wait(lk, done);
     }
-    if (res) *res = it->second.res;
-    return it->second.res.status;
+    if (res) *res = q->res;
+    return q->res.status;
 }
 
 nx_status nx_server_get_stats(nx_server* s, nx_server_stats* st)
@@ -565,8 +576,8 @@ void nx_server_destroy(nx_server* s)
             s->stop = true;
             // queued requests are dropped; admitted ones finish
             for (uint64_t t : s->waiting) {
-                s->reqs[t].finished = true;
-                s->reqs[t].res.status = NX_E_STATE;
+                s->reqs.at(t).finished = true;
+                s->reqs.at(t).res.status = NX_E_STATE;
             }
             s->waiting.clear();
         }

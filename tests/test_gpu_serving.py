@@ -118,3 +118,36 @@ def test_wait_timeout_is_bounded():
     r = srv.wait(t, timeout_s=300.0)
     assert r["status"] == 0
     srv.close()
+
+
+def test_concurrent_submitters_and_waiters():
+    """Several client threads submit while others wait (the request table is
+    modified while the worker reads it); every result must still match the
+    oracle."""
+    import threading
+
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    srv = nx.Server(budget_bytes=128 << 20, steps_per_launch=8)
+    reqs = _mix(11, 90, max_envs=64, max_h=60)
+    results = {}
+    lock = threading.Lock()
+
+    def client(part):
+        mine = []
+        for r in part:
+            mine.append((r, srv.submit(*r)))
+        for r, t in mine:
+            res = srv.wait(t, timeout_s=120.0)
+            with lock:
+                results[r] = res
+
+    threads = [threading.Thread(target=client, args=(reqs[i::6],)) for i in range(6)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    srv.close()
+    assert len(results) == len(reqs)
+    for r in reqs[:30]:
+        _same(results[r], oracle_request(*r))
