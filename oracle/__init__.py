@@ -27,8 +27,9 @@ RGB_BYTES = 224 * 224 * 3
 TILE_BYTES = 32 * 32 * 3
 MAX_CELLS = 19 * 19
 
-EMPTY, DOORKEY, FOURROOMS, LAVAGAP, DYNOBS = range(5)
-FAMILY_NAMES = {"empty": EMPTY, "doorkey": DOORKEY, "fourrooms": FOURROOMS, "lavagap": LAVAGAP, "dynobs": DYNOBS}
+EMPTY, DOORKEY, FOURROOMS, LAVAGAP, DYNOBS, EMPTY_RANDOM, LAVA_CROSSING, SIMPLE_CROSSING = range(8)
+FAMILY_NAMES = {"empty": EMPTY, "doorkey": DOORKEY, "fourrooms": FOURROOMS, "lavagap": LAVAGAP, "dynobs": DYNOBS,
+                "empty_random": EMPTY_RANDOM, "lava_crossing": LAVA_CROSSING, "simple_crossing": SIMPLE_CROSSING}
 
 
 def build(force: bool = False) -> str:
@@ -48,7 +49,7 @@ class OrcEnv(ctypes.Structure):
     _fields_ = [
         ("family", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
         ("max_steps", ctypes.c_int32), ("n_balls", ctypes.c_int32), ("reward_mode", ctypes.c_int32),
-        ("lava_reward", ctypes.c_float),
+        ("variant", ctypes.c_int32), ("lava_reward", ctypes.c_float),
         ("seed", ctypes.c_uint64), ("env_index", ctypes.c_uint32), ("episode", ctypes.c_uint32),
         ("t", ctypes.c_int32), ("ax", ctypes.c_int32), ("ay", ctypes.c_int32), ("dir", ctypes.c_int32),
         ("carry_ent", ctypes.c_int32), ("carry_col", ctypes.c_int32), ("done", ctypes.c_int32),
@@ -73,7 +74,10 @@ def lib():
             L.orc_default_max_steps.argtypes = [ctypes.c_int32, ctypes.c_int32]
             L.orc_default_max_steps.restype = ctypes.c_int32
             L.orc_env_init.argtypes = [P(OrcEnv), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_float]
+                                       ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_float,
+                                       ctypes.c_int32]
+            L.orc_max_variant.argtypes = [ctypes.c_int32, ctypes.c_int32]
+            L.orc_max_variant.restype = ctypes.c_int32
             L.orc_env_init.restype = ctypes.c_int32
             L.orc_reset.argtypes = [P(OrcEnv), ctypes.c_uint32]
             L.orc_random_action.argtypes = [P(OrcEnv), ctypes.c_uint32]
@@ -85,11 +89,11 @@ def lib():
             L.orc_tile_index.restype = ctypes.c_int32
             L.orc_set_cell.argtypes = [P(OrcEnv)] + [ctypes.c_int32] * 5
             L.orc_set_agent.argtypes = [P(OrcEnv)] + [ctypes.c_int32] * 5
-            L.orc_batch_create.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_uint64,
+            L.orc_batch_create.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_uint64,
                                            ctypes.c_uint32, ctypes.c_int32, ctypes.c_float]
             L.orc_batch_create.restype = ctypes.c_void_p
-            L.orc_batch_create_indexed.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_int32, ctypes.c_uint64,
-                                                   P(ctypes.c_uint32), ctypes.c_int32, ctypes.c_float]
+            L.orc_batch_create_indexed.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_int32,
+                                                   ctypes.c_uint64, P(ctypes.c_uint32), ctypes.c_int32, ctypes.c_float]
             L.orc_batch_create_indexed.restype = ctypes.c_void_p
             L.orc_batch_destroy.argtypes = [ctypes.c_void_p]
             L.orc_batch_env.argtypes = [ctypes.c_void_p, ctypes.c_int32]
@@ -130,6 +134,10 @@ def default_max_steps(family, size):
     return int(lib().orc_default_max_steps(family, size))
 
 
+def max_variant(family, size):
+    return int(lib().orc_max_variant(family, size))
+
+
 def tile_index(visible, agent_cell, ent, col, st):
     return int(lib().orc_tile_index(visible, agent_cell, ent, col, st))
 
@@ -137,10 +145,11 @@ def tile_index(visible, agent_cell, ent, col, st):
 class Env:
     """One oracle environment (for hand-built states and worked examples)."""
 
-    def __init__(self, family, size, seed=0, env_index=0, max_steps=0, n_balls=4, reward_mode=0, lava_reward=0.0):
+    def __init__(self, family, size, seed=0, env_index=0, max_steps=0, n_balls=4, reward_mode=0, lava_reward=0.0,
+                 variant=0):
         self.s = OrcEnv()
         rc = lib().orc_env_init(ctypes.byref(self.s), family, size, max_steps, n_balls, seed, env_index,
-                                reward_mode, lava_reward)
+                                reward_mode, lava_reward, variant)
         if rc != 0:
             raise ValueError("invalid oracle env arguments")
 
@@ -191,7 +200,7 @@ def env_state(s: OrcEnv) -> dict:
     return {
         "family": s.family, "height": H, "width": W, "max_steps": s.max_steps,
         "x": s.ax, "y": s.ay, "dir": s.dir, "carry_ent": s.carry_ent, "carry_col": s.carry_col,
-        "done": s.done, "t": s.t, "episode": s.episode, "n_balls": s.n_balls,
+        "done": s.done, "t": s.t, "episode": s.episode, "n_balls": s.n_balls, "variant": s.variant,
         "ball_x": list(s.ball_x)[: s.n_balls], "ball_y": list(s.ball_y)[: s.n_balls],
         "invalid": s.invalid_action,
         "ent": bytes(s.ent)[:n], "col": bytes(s.col)[:n], "st": bytes(s.st)[:n],
@@ -202,21 +211,22 @@ class Batch:
     """n oracle environments with global indices base..base+n-1 (Code 3's vmap)."""
 
     def __init__(self, families, sizes, seed, max_steps=None, n_balls=4, env_index_base=0, reward_mode=0,
-                 lava_reward=0.0, env_indices=None):
+                 lava_reward=0.0, env_indices=None, variants=None):
         fam = np.ascontiguousarray(families, np.int32)
         siz = np.ascontiguousarray(sizes, np.int32)
         self.n = int(fam.shape[0])
         ms = None if max_steps is None else np.ascontiguousarray(max_steps, np.int32)
+        var = None if variants is None else np.ascontiguousarray(variants, np.int32)
         if env_indices is None:
             h = lib().orc_batch_create(self.n, _ptr(fam, ctypes.c_int32), _ptr(siz, ctypes.c_int32),
-                                       _ptr(ms, ctypes.c_int32), n_balls, seed, env_index_base, reward_mode,
-                                       lava_reward)
+                                       _ptr(ms, ctypes.c_int32), _ptr(var, ctypes.c_int32), n_balls, seed,
+                                       env_index_base, reward_mode, lava_reward)
         else:
             idx = np.ascontiguousarray(env_indices, np.uint32)
             assert idx.shape == (self.n,)
             h = lib().orc_batch_create_indexed(self.n, _ptr(fam, ctypes.c_int32), _ptr(siz, ctypes.c_int32),
-                                               _ptr(ms, ctypes.c_int32), n_balls, seed, _ptr(idx, ctypes.c_uint32),
-                                               reward_mode, lava_reward)
+                                               _ptr(ms, ctypes.c_int32), _ptr(var, ctypes.c_int32), n_balls, seed,
+                                               _ptr(idx, ctypes.c_uint32), reward_mode, lava_reward)
         if not h:
             raise ValueError("invalid oracle batch arguments")
         self.h = h

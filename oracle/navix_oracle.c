@@ -141,7 +141,8 @@ void orc_set_agent(orc_env* e, int32_t x, int32_t y, int32_t dir, int32_t carry_
 int32_t orc_default_max_steps(int32_t family, int32_t size)
 {
     /* reading R17: Empty 4S^2 (100 at S = 5), DoorKey 10S^2 (640 at S = 8),
-     * FourRooms 100, LavaGap 4S^2, Dynamic-Obstacles 4S^2 */
+     * FourRooms 100, LavaGap 4S^2, Dynamic-Obstacles 4S^2; Empty-Random and the
+     * crossings 4S^2 */
     switch (family) {
     case ORC_DOORKEY: return 10 * size * size;
     case ORC_FOURROOMS: return 100;
@@ -286,6 +287,127 @@ static void layout_dynobs(orc_env* e)
     }
 }
 
+/* L6 Empty-Random-S: Empty-S with the agent on a drawn empty interior cell
+ * (never the goal), facing a drawn direction. */
+static void layout_empty_random(orc_env* e)
+{
+    int S = e->width;
+    orc_set_cell(e, S - 2, S - 2, ORC_GOAL, ORC_GREEN, 0);
+    int n = count_free(e, 1, S - 2, 1, S - 2, -1, -1);
+    int ax, ay;
+    kth_free(e, (int)orc_bounded(layout_draw(e, 0), (uint32_t)n), 1, S - 2, 1, S - 2, -1, -1, &ax, &ay);
+    orc_set_agent(e, ax, ay, (int)orc_bounded(layout_draw(e, 1), 4u), 0, 0);
+}
+
+/* Candidate rivers of an S x S crossing layout: rows 2, 4, .., S-3 (kind 0,
+ * horizontal), then columns 2, 4, .., S-3 (kind 1, vertical). */
+static int crossing_candidates(int S, int* kind, int* pos)
+{
+    int m = 0;
+    for (int y = 2; y <= S - 3; y += 2) {
+        kind[m] = 0;
+        pos[m] = y;
+        m++;
+    }
+    for (int x = 2; x <= S - 3; x += 2) {
+        kind[m] = 1;
+        pos[m] = x;
+        m++;
+    }
+    return m;
+}
+
+int32_t orc_max_variant(int32_t family, int32_t size)
+{
+    if (family != ORC_LAVA_CROSSING && family != ORC_SIMPLE_CROSSING) return 0;
+    int kind[ORC_MAX_SIZE * 2], pos[ORC_MAX_SIZE * 2];
+    return crossing_candidates(size, kind, pos);
+}
+
+static void sort_ints(int* v, int n)
+{
+    for (int i = 1; i < n; i++)
+        for (int j = i; j > 0 && v[j - 1] > v[j]; j--) {
+            int t = v[j];
+            v[j] = v[j - 1];
+            v[j - 1] = t;
+        }
+}
+
+/* L7 Crossings-S with N rivers (the variant) of lava or wall; agent (1,1)
+ * facing east, goal (S-2,S-2).  The layout draws, in this order:
+ *  1. N rivers among the candidates by a partial Fisher-Yates shuffle
+ *     (step i swaps candidate i with candidate i + k(d, m - i));
+ *  2. every interior cell of a chosen row or column becomes the obstacle;
+ *  3. a random order of the crossings: one east move per vertical river and
+ *     one south move per horizontal river, shuffled by Fisher-Yates from the
+ *     last position down (position i swaps with k(d, i + 1));
+ *  4. walking that order from the top-left room, each move opens one cell of
+ *     the river it crosses, drawn uniformly within the current room's span;
+ * so the goal is always reachable and every river has exactly one opening. */
+static void layout_crossing(orc_env* e)
+{
+    int S = e->width, N = e->variant;
+    int obst_ent = e->family == ORC_LAVA_CROSSING ? ORC_LAVA : ORC_WALL;
+    int obst_col = e->family == ORC_LAVA_CROSSING ? 0 : ORC_GREY;
+    int kind[ORC_MAX_SIZE * 2], pos[ORC_MAX_SIZE * 2];
+    int m = crossing_candidates(S, kind, pos);
+    uint32_t k = 0;
+    for (int i = 0; i < N; i++) {
+        int j = i + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(m - i));
+        int tk = kind[i], tp = pos[i];
+        kind[i] = kind[j];
+        pos[i] = pos[j];
+        kind[j] = tk;
+        pos[j] = tp;
+    }
+    int hs[ORC_MAX_SIZE], vs[ORC_MAX_SIZE], nh = 0, nv = 0;
+    for (int i = 0; i < N; i++) {
+        if (kind[i] == 0)
+            hs[nh++] = pos[i];
+        else
+            vs[nv++] = pos[i];
+    }
+    sort_ints(hs, nh);
+    sort_ints(vs, nv);
+    for (int i = 0; i < nh; i++)
+        for (int x = 1; x <= S - 2; x++) orc_set_cell(e, x, hs[i], obst_ent, obst_col, 0);
+    for (int i = 0; i < nv; i++)
+        for (int y = 1; y <= S - 2; y++) orc_set_cell(e, vs[i], y, obst_ent, obst_col, 0);
+    int path[ORC_MAX_SIZE * 2];  /* 1 = east (cross a vertical river), 0 = south */
+    int L = nv + nh;
+    for (int i = 0; i < L; i++) path[i] = i < nv ? 1 : 0;
+    for (int i = L - 1; i >= 1; i--) {
+        int j = (int)orc_bounded(layout_draw(e, k++), (uint32_t)(i + 1));
+        int t = path[i];
+        path[i] = path[j];
+        path[j] = t;
+    }
+    int xb[ORC_MAX_SIZE + 2], yb[ORC_MAX_SIZE + 2];
+    xb[0] = 0;
+    for (int i = 0; i < nv; i++) xb[i + 1] = vs[i];
+    xb[nv + 1] = S - 1;
+    yb[0] = 0;
+    for (int i = 0; i < nh; i++) yb[i + 1] = hs[i];
+    yb[nh + 1] = S - 1;
+    int rx = 0, ry = 0;
+    for (int i = 0; i < L; i++) {
+        if (path[i]) {
+            int x = xb[rx + 1];
+            int y = yb[ry] + 1 + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(yb[ry + 1] - yb[ry] - 1));
+            set_empty(e, x, y);
+            rx++;
+        } else {
+            int y = yb[ry + 1];
+            int x = xb[rx] + 1 + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(xb[rx + 1] - xb[rx] - 1));
+            set_empty(e, x, y);
+            ry++;
+        }
+    }
+    orc_set_cell(e, S - 2, S - 2, ORC_GOAL, ORC_GREEN, 0);
+    orc_set_agent(e, 1, 1, 0, 0, 0);
+}
+
 /* reset(key) of Section 3.2.2: sample a start state for the given episode. */
 void orc_reset(orc_env* e, uint32_t episode)
 {
@@ -309,16 +431,20 @@ void orc_reset(orc_env* e, uint32_t episode)
     case ORC_FOURROOMS: layout_fourrooms(e); break;
     case ORC_LAVAGAP: layout_lavagap(e); break;
     case ORC_DYNOBS: layout_dynobs(e); break;
+    case ORC_EMPTY_RANDOM: layout_empty_random(e); break;
+    case ORC_LAVA_CROSSING:
+    case ORC_SIMPLE_CROSSING: layout_crossing(e); break;
     default: break;
     }
 }
 
 int32_t orc_env_init(orc_env* e, int32_t family, int32_t size, int32_t max_steps, int32_t n_balls, uint64_t seed,
-                     uint32_t env_index, int32_t reward_mode, float lava_reward)
+                     uint32_t env_index, int32_t reward_mode, float lava_reward, int32_t variant)
 {
-    if (family < ORC_EMPTY || family > ORC_DYNOBS) return -1;
+    if (family < ORC_EMPTY || family >= ORC_N_FAMILIES) return -1;
     if (size < ORC_MIN_SIZE || size > ORC_MAX_SIZE) return -1;
     if (n_balls < 0 || n_balls > ORC_MAX_BALLS) return -1;
+    if (variant < 0 || variant > orc_max_variant(family, size)) return -1;
     memset(e, 0, sizeof *e);
     e->family = family;
     e->height = size;
@@ -329,6 +455,7 @@ int32_t orc_env_init(orc_env* e, int32_t family, int32_t size, int32_t max_steps
     e->lava_reward = lava_reward;
     e->seed = seed;
     e->env_index = env_index;
+    e->variant = variant;
     orc_reset(e, 0);
     return 0;
 }
@@ -589,20 +716,21 @@ struct orc_batch {
 };
 
 orc_batch* orc_batch_create(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
-                            int32_t n_balls, uint64_t seed, uint32_t env_index_base, int32_t reward_mode,
-                            float lava_reward)
+                            const int32_t* variant, int32_t n_balls, uint64_t seed, uint32_t env_index_base,
+                            int32_t reward_mode, float lava_reward)
 {
     uint32_t* idx = (uint32_t*)malloc((n > 0 ? (size_t)n : 1u) * sizeof(uint32_t));
     if (!idx) return NULL;
     for (int32_t i = 0; i < n; i++) idx[i] = env_index_base + (uint32_t)i;
-    orc_batch* b = orc_batch_create_indexed(n, family, size, max_steps, n_balls, seed, idx, reward_mode, lava_reward);
+    orc_batch* b =
+        orc_batch_create_indexed(n, family, size, max_steps, variant, n_balls, seed, idx, reward_mode, lava_reward);
     free(idx);
     return b;
 }
 
 orc_batch* orc_batch_create_indexed(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
-                                    int32_t n_balls, uint64_t seed, const uint32_t* env_index, int32_t reward_mode,
-                                    float lava_reward)
+                                    const int32_t* variant, int32_t n_balls, uint64_t seed, const uint32_t* env_index,
+                                    int32_t reward_mode, float lava_reward)
 {
     if (n < 0) return NULL;
     orc_batch* b = (orc_batch*)calloc(1, sizeof *b);
@@ -615,7 +743,7 @@ orc_batch* orc_batch_create_indexed(int32_t n, const int32_t* family, const int3
     }
     for (int32_t i = 0; i < n; i++) {
         if (orc_env_init(&b->envs[i], family[i], size[i], max_steps ? max_steps[i] : 0, n_balls, seed,
-                         env_index[i], reward_mode, lava_reward) != 0) {
+                         env_index[i], reward_mode, lava_reward, variant ? variant[i] : 0) != 0) {
             free(b->envs);
             free(b);
             return NULL;

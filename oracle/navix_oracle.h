@@ -46,8 +46,10 @@ extern "C" {
 #define ORC_RGB_BYTES (ORC_VIEW * ORC_TILE * ORC_VIEW * ORC_TILE * 3)
 #define ORC_MAX_BALLS 4
 
-/* families */
-enum { ORC_EMPTY = 0, ORC_DOORKEY = 1, ORC_FOURROOMS = 2, ORC_LAVAGAP = 3, ORC_DYNOBS = 4 };
+/* families (variant: the number of rivers for the two crossing families) */
+enum { ORC_EMPTY = 0, ORC_DOORKEY = 1, ORC_FOURROOMS = 2, ORC_LAVAGAP = 3, ORC_DYNOBS = 4, ORC_EMPTY_RANDOM = 5,
+       ORC_LAVA_CROSSING = 6, ORC_SIMPLE_CROSSING = 7 };
+#define ORC_N_FAMILIES 8
 /* actions */
 enum { ORC_LEFT = 0, ORC_RIGHT = 1, ORC_FORWARD = 2, ORC_PICKUP = 3, ORC_DROP = 4, ORC_TOGGLE = 5, ORC_DONE = 6 };
 /* entity codes */
@@ -61,7 +63,7 @@ enum { ORC_OPEN = 0, ORC_CLOSED = 1, ORC_LOCKED = 2 };
 enum { ORC_REWARD_MARKOV = 0, ORC_REWARD_MINIGRID = 1 };
 
 typedef struct orc_env {
-    int32_t family, height, width, max_steps, n_balls, reward_mode;
+    int32_t family, height, width, max_steps, n_balls, reward_mode, variant;
     float lava_reward;
     uint64_t seed;
     uint32_t env_index;
@@ -83,7 +85,8 @@ uint32_t orc_draw(uint64_t seed, uint32_t env_index, uint32_t episode, uint32_t 
 
 int32_t orc_default_max_steps(int32_t family, int32_t size);
 int32_t orc_env_init(orc_env* e, int32_t family, int32_t size, int32_t max_steps, int32_t n_balls, uint64_t seed,
-                     uint32_t env_index, int32_t reward_mode, float lava_reward);
+                     uint32_t env_index, int32_t reward_mode, float lava_reward, int32_t variant);
+int32_t orc_max_variant(int32_t family, int32_t size);
 void orc_reset(orc_env* e, uint32_t episode);
 int32_t orc_random_action(const orc_env* e, uint32_t gstep);
 void orc_step(orc_env* e, int32_t action, float* reward, uint8_t* terminated, uint8_t* truncated);
@@ -100,12 +103,12 @@ void orc_set_agent(orc_env* e, int32_t x, int32_t y, int32_t dir, int32_t carry_
  * global env indices 0..n-1.  Output arrays are [n, ...]; any may be NULL. */
 typedef struct orc_batch orc_batch;
 orc_batch* orc_batch_create(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
-                            int32_t n_balls, uint64_t seed, uint32_t env_index_base, int32_t reward_mode,
-                            float lava_reward);
+                            const int32_t* variant, int32_t n_balls, uint64_t seed, uint32_t env_index_base,
+                            int32_t reward_mode, float lava_reward);
 /* as above, with an explicit global env index per env (a sample of a larger batch) */
 orc_batch* orc_batch_create_indexed(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
-                                    int32_t n_balls, uint64_t seed, const uint32_t* env_index, int32_t reward_mode,
-                                    float lava_reward);
+                                    const int32_t* variant, int32_t n_balls, uint64_t seed, const uint32_t* env_index,
+                                    int32_t reward_mode, float lava_reward);
 void orc_batch_destroy(orc_batch* b);
 orc_env* orc_batch_env(orc_batch* b, int32_t i);
 void orc_batch_reset(orc_batch* b, uint8_t* obs_sym, uint8_t* obs_rgb, const uint8_t* atlas, float* reward,
