@@ -58,8 +58,13 @@ enum {
     NX_E_STATE = -7          /* call out of order (e.g. step before reset) */
 };
 
-/* environment families of Table 8 */
-enum { NX_EMPTY = 0, NX_DOORKEY = 1, NX_FOURROOMS = 2, NX_LAVAGAP = 3, NX_DYNOBS = 4 };
+/* environment families of Table 8; the crossings take their number of
+ * rivers as the descriptor's variant (0..nx_max_variant) */
+enum {
+    NX_EMPTY = 0, NX_DOORKEY = 1, NX_FOURROOMS = 2, NX_LAVAGAP = 3, NX_DYNOBS = 4, NX_EMPTY_RANDOM = 5,
+    NX_LAVA_CROSSING = 6, NX_SIMPLE_CROSSING = 7
+};
+#define NX_N_FAMILIES 8
 /* observation bit flags (Table 4) */
 enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2 };
 /* action sources */
@@ -85,10 +90,11 @@ typedef struct nx_env nx_env;
 typedef struct nx_server nx_server;
 
 /* One environment's shape: family, square grid side (height == width,
- * 5..19), timeout T (<= 0: the family default: Empty/LavaGap/
- * Dynamic-Obstacles 4 S^2, DoorKey 10 S^2, FourRooms 100; at most 65535). */
+ * 5..19), timeout T (<= 0: the family default: DoorKey 10 S^2, FourRooms
+ * 100, the others 4 S^2; at most 65535), and the family's variant (the number
+ * of rivers of a crossing family, 0 otherwise). */
 typedef struct {
-    int32_t family, height, width, max_steps;
+    int32_t family, height, width, max_steps, variant;
 } nx_desc;
 
 /* Creation options; nx_options_default() fills the defaults. */
@@ -111,6 +117,7 @@ typedef struct {
      * contexts over disjoint index ranges reproduce one large batch exactly,
      * which is how a batch is split over GPUs */
     uint32_t env_index_base;
+    int32_t variant;          /* nx_create only: the variant of every env (rivers of a crossing family) */
 } nx_options;
 
 /* Per-step outputs, device pointers owned by the caller; any may be NULL (not
@@ -136,6 +143,10 @@ typedef struct {
 } nx_info;
 
 void nx_options_default(nx_options* opts);
+/* Largest valid variant of a family at a size (the number of candidate
+ * rivers of a crossing family: rows and columns 2, 4, .., size-3), 0 for
+ * the other families. */
+int32_t nx_max_variant(int32_t family, int32_t size);
 
 /* nx_create: one family and size for all n_envs environments (the paper's
  * make(id), Code 1, batched as in Code 3).  n_envs >= 1.  seed keys every
@@ -236,6 +247,8 @@ nx_status nx_get_info(const nx_env* env, nx_info* info);
  */
 typedef struct {
     int32_t family, size, n_envs, horizon;  /* size 5..19, n_envs >= 1, horizon >= 1 */
+    int32_t variant;                        /* the family's variant (rivers of a crossing family) */
+    int32_t reserved;
     uint64_t seed;
     /* optional host outputs, written when the request finishes:
      * returns [n_envs] float32 (sum of rewards over the horizon, in step

@@ -132,10 +132,21 @@ int nx_default_max_steps(int family, int size)
     }
 }
 
+int32_t nx_max_variant(int32_t family, int32_t size)
+{
+    if (family != NX_LAVA_CROSSING && family != NX_SIMPLE_CROSSING) return 0;
+    if (size < NX_MIN_SIZE || size > NX_MAX_SIZE) return 0;
+    return 2 * ((size - 3) / 2);  // rows and columns 2, 4, .., size - 3
+}
+
 static nx_status validate_desc(const nx_desc& d, int n_balls, std::string* why)
 {
-    if (d.family < NX_EMPTY || d.family > NX_DYNOBS) {
-        *why = "family must be 0..4";
+    if (d.family < NX_EMPTY || d.family >= NX_N_FAMILIES) {
+        *why = "family must be 0..7";
+        return NX_E_INVAL;
+    }
+    if (d.variant < 0 || d.variant > nx_max_variant(d.family, d.height)) {
+        *why = "variant out of range for this family and size (see nx_max_variant)";
         return NX_E_INVAL;
     }
     if (d.height != d.width) {
@@ -168,7 +179,7 @@ std::vector<nx_item> nx_build_items(const nx_env* env, int E)
         int j = i;
         const nx_desc& d = env->descs[i];
         while (j < n && env->descs[j].family == d.family && env->descs[j].height == d.height &&
-               env->descs[j].max_steps == d.max_steps)
+               env->descs[j].max_steps == d.max_steps && env->descs[j].variant == d.variant)
             ++j;
         for (int b = i; b < j; b += E) {
             nx_item it;
@@ -181,6 +192,7 @@ std::vector<nx_item> nx_build_items(const nx_env* env, int E)
             it.max_steps = (uint16_t)d.max_steps;
             it.family = (uint8_t)d.family;
             it.size = (uint8_t)d.height;
+            it.variant = (uint32_t)d.variant;
             items.push_back(it);
         }
         i = j;
@@ -238,7 +250,7 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
     // grid pool layout and families
     size_t off = 0;
     int max_cells = 0;
-    bool seen[5] = {false, false, false, false, false};
+    bool seen[NX_N_FAMILIES] = {};
     env->grid_offset.resize(env->n_envs);
     for (int i = 0; i < env->n_envs; ++i) {
         const int S = env->descs[i].height;
@@ -312,7 +324,7 @@ nx_status nx_create(nx_env** env, int32_t family, int32_t size, int32_t n_envs, 
                     void* cuda_stream)
 {
     if (n_envs < 1) return nx_fail(nullptr, NX_E_INVAL, "n_envs must be >= 1");
-    std::vector<nx_desc> d((size_t)n_envs, nx_desc{family, size, size, 0});
+    std::vector<nx_desc> d((size_t)n_envs, nx_desc{family, size, size, 0, opts ? opts->variant : 0});
     return create_common(env, std::move(d), seed, opts, cuda_stream);
 }
 
@@ -337,13 +349,13 @@ nx_status nx_apply_shape(nx_env* env, const nx_launch_shape& s)
     std::vector<nx_item> items = nx_build_items(env, s.envs_per_cta);
     // family-ordered copy for the per-family form
     std::vector<nx_item> fam;
-    std::vector<int> fam_begin(6, 0);
-    for (int f = 0; f < 5; ++f) {
+    std::vector<int> fam_begin(NX_N_FAMILIES + 1, 0);
+    for (int f = 0; f < NX_N_FAMILIES; ++f) {
         fam_begin[f] = (int)fam.size();
         for (auto& it : items)
             if (it.family == f) fam.push_back(it);
     }
-    fam_begin[5] = (int)fam.size();
+    fam_begin[NX_N_FAMILIES] = (int)fam.size();
     const size_t bytes = sizeof(nx_item) * items.size();
     if (bytes > env->items_capacity) {
         // the previous list stays allocated until the context goes away (small)
@@ -526,7 +538,7 @@ static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, co
     env->n_all_launches += 1;
     if (per_family) {
         for (int t = 0; t < n_steps; ++t) {
-            for (int f = 0; f < 5; ++f) {
+            for (int f = 0; f < NX_N_FAMILIES; ++f) {
                 const int b = env->fam_begin[f], e = env->fam_begin[f + 1];
                 if (e == b) continue;
                 nx_kparams p = nx_params(env, 1, 0);

@@ -247,6 +247,75 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
     reinterpret_cast<uint4*>(dst)[1] = w1;
 }
 
+// L7 crossings: N rivers of lava or wall (see reset_layout), kept out of line
+// so that its small local arrays do not weigh on the step kernel's registers.
+template <int G>
+__device__ __noinline__ void crossing_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int variant,
+                                             uint64_t seed, uint32_t key_env, uint32_t episode)
+{
+    const int HW = S * S;
+        // rivers: a partial Fisher-Yates choice among rows then columns 2, 4, ..
+        // S-3; kept as row/column bitmasks, so their sorted order is the bit order
+        int ck[2 * NX_MAX_SIZE];
+        int m = 0;
+        for (int y = 2; y <= S - 3; y += 2) ck[m++] = y;            // horizontal: the row
+        for (int x = 2; x <= S - 3; x += 2) ck[m++] = 0x100 | x;    // vertical: 0x100 | the column
+        uint32_t k = 0;
+        for (int i = 0; i < variant; ++i) {
+            const int j = i + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++), (uint32_t)(m - i));
+            const int t = ck[i];
+            ck[i] = ck[j];
+            ck[j] = t;
+        }
+        uint32_t hmask = 0, vmask = 0;
+        for (int i = 0; i < variant; ++i) {
+            if (ck[i] & 0x100)
+                vmask |= 1u << (ck[i] & 0xFF);
+            else
+                hmask |= 1u << ck[i];
+        }
+        const uint32_t obst = family == NX_LAVA_CROSSING ? (uint32_t)C_LAVA : (uint32_t)C_WALL;
+        grp.sync();
+        for (int c = grp.lane; c < HW; c += G) {
+            const int y = c / S, x = c - y * S;
+            if (x >= 1 && y >= 1 && x <= S - 2 && y <= S - 2 && (((hmask >> y) | (vmask >> x)) & 1u))
+                g[c] = (uint8_t)obst;
+        }
+        // order of crossings: east moves (vertical rivers) first, then south
+        // moves, shuffled by Fisher-Yates from the last position down
+        const int nv = __popc(vmask), nh = __popc(hmask), L = nv + nh;
+        int path[2 * NX_MAX_SIZE];
+        for (int i = 0; i < L; ++i) path[i] = i < nv ? 1 : 0;
+        for (int i = L - 1; i >= 1; --i) {
+            const int j = bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++), (uint32_t)(i + 1));
+            const int t = path[i];
+            path[i] = path[j];
+            path[j] = t;
+        }
+        // walk the rooms from the top-left one; each move opens one cell of
+        // the river it crosses, drawn within the current room's span
+        int x_lo = 0, y_lo = 0;              // the current room's west / north bounds
+        uint32_t vrest = vmask, hrest = hmask;  // rivers not yet crossed, east / south of the room
+        grp.sync();
+        for (int i = 0; i < L; ++i) {
+            const int x_hi = vrest ? __ffs(vrest) - 1 : S - 1;
+            const int y_hi = hrest ? __ffs(hrest) - 1 : S - 1;
+            if (path[i]) {
+                const int y = y_lo + 1 + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++),
+                                                 (uint32_t)(y_hi - y_lo - 1));
+                if (grp.lane == 0) g[y * S + x_hi] = (uint8_t)C_EMPTY;
+                x_lo = x_hi;
+                vrest &= vrest - 1u;
+            } else {
+                const int x = x_lo + 1 + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++),
+                                                 (uint32_t)(x_hi - x_lo - 1));
+                if (grp.lane == 0) g[y_hi * S + x] = (uint8_t)C_EMPTY;
+                y_lo = y_hi;
+                hrest &= hrest - 1u;
+            }
+        }
+}
+
 // ---------------------------------------------------------------------------
 // Layout generators of the Table 8 families.  Draw k of a reset is
 // draw(seed, env, episode, 0, PURPOSE_LAYOUT, k); the k-th free cell is
@@ -254,8 +323,8 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
 // Returns false (and leaves a partial layout) only if a free-cell choice found
 // no cell, which cannot happen for sizes 5..19; the caller raises a flag.
 template <int G>
-__device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int n_balls, uint64_t seed,
-                             uint32_t key_env, uint32_t episode, AgentReg& a)
+__device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int n_balls, int variant,
+                                             uint64_t seed, uint32_t key_env, uint32_t episode, AgentReg& a)
 {
     const int HW = S * S;
     for (int c = grp.lane; c < HW; c += G) {
@@ -278,7 +347,7 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
     }
     uint32_t d[8];
     const int n_draws = family == NX_DOORKEY ? 5 : family == NX_FOURROOMS ? 7 : family == NX_LAVAGAP ? 2
-                        : family == NX_DYNOBS ? n_balls : 0;
+                        : family == NX_DYNOBS ? n_balls : family == NX_EMPTY_RANDOM ? 2 : 0;
     group_draws(grp, n_draws, d,
                 [&](uint32_t k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k); });
     grp.sync();
@@ -331,6 +400,16 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         const int gap = 1 + bounded(d[1], (uint32_t)(S - 2));
         for (int y = 1 + grp.lane; y <= S - 2; y += G)
             if (y != gap) g[y * S + xl] = (uint8_t)C_LAVA;
+    } else if (family == NX_EMPTY_RANDOM) {
+        grp.sync();
+        const int n = count_free(grp, g, S, 1, S - 2, 1, S - 2, -1);
+        const int ac = kth_free(grp, g, S, 1, S - 2, 1, S - 2, -1, bounded(d[0], (uint32_t)n));
+        if (ac < 0) return false;
+        a.x = ac % S;
+        a.y = ac / S;
+        a.dir = bounded(d[1], 4u);
+    } else if (family == NX_LAVA_CROSSING || family == NX_SIMPLE_CROSSING) {
+        crossing_layout(grp, g, S, family, variant, seed, key_env, episode);
     } else if (family == NX_DYNOBS) {
         grp.sync();
         const int agent = 1 * S + 1;
@@ -353,10 +432,10 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
 // The same generator run by a whole warp for one env, kept out of line: it is
 // the rare path of narrow groups, and inlining it would raise the register
 // allocation of the whole step kernel.
-__device__ __noinline__ bool reset_layout_warp(uint8_t* g, int S, int family, int n_balls, uint64_t seed,
+__device__ __noinline__ bool reset_layout_warp(uint8_t* g, int S, int family, int n_balls, int variant, uint64_t seed,
                                                uint32_t key_env, uint32_t episode, AgentReg& a)
 {
-    return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, family, n_balls, seed, key_env, episode, a);
+    return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, family, n_balls, variant, seed, key_env, episode, a);
 }
 
 // ---------------------------------------------------------------------------

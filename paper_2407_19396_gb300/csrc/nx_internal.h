@@ -39,7 +39,8 @@ struct NX_ALIGN16 nx_item {
     uint32_t local_begin;  // index of env_begin within its request (keys, output rows)
     uint16_t max_steps;
     uint8_t family, size;
-    uint32_t pad[2];
+    uint32_t variant;      // rivers of a crossing family, 0 otherwise
+    uint32_t pad;
 };
 static_assert(sizeof(nx_item) == 32, "item is 32 bytes");
 

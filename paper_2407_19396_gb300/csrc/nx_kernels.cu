@@ -168,7 +168,7 @@ __device__ __forceinline__ void coop_rgb(uint8_t* dst, const uint16_t* tiles, co
 }
 
 template <int G, bool RGB>
-__global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p)
+__global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparams p)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t s_dec[256];  // cell code -> observation triple
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
         uint64_t* digest = rq->digest;
         uint32_t* episodes = rq->episodes;
 
-        const int n = (int)item.n_envs, S = item.size, HW = S * S, family = item.family;
+        const int n = (int)item.n_envs, S = item.size, HW = S * S, family = item.family, variant = (int)item.variant;
         const int max_steps = item.max_steps;
         const bool active = gi < n;
         const uint32_t local = item.local_begin + (uint32_t)gi;
@@ -265,7 +265,8 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
             if constexpr (G >= 8) {
                 if (starts) {
                     const int inv = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
-                    if (!reset_layout(grp, mygrid, S, family, n_balls, seed, key, p.reset_all ? 0u : a.episode + 1u, a))
+                    if (!reset_layout(grp, mygrid, S, family, n_balls, variant, seed, key,
+                                      p.reset_all ? 0u : a.episode + 1u, a))
                         if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
                     a.invalid = inv;
                 }
@@ -278,7 +279,8 @@ __global__ void __launch_bounds__(kMaxThreads) nx_step_kernel(const nx_kparams p
                     const uint32_t k = __shfl_sync(0xFFFFFFFFu, key, L);
                     const int owner = ((tid & ~31) + L) / G;  // group (env slot) of lane L
                     AgentReg na;
-                    const bool ok = reset_layout_warp(sgrid + owner * p.cell_stride, S, family, n_balls, seed, k, ep, na);
+                    const bool ok =
+                        reset_layout_warp(sgrid + owner * p.cell_stride, S, family, n_balls, variant, seed, k, ep, na);
                     if (!ok && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
                     if (gi == owner) {
                         na.invalid = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky

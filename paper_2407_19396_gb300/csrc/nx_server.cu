@@ -218,6 +218,7 @@ void items_of(const nx_server* s, const SReq& q, std::vector<nx_item>& out)
         it.max_steps = (uint16_t)q.max_steps;
         it.family = (uint8_t)q.r.family;
         it.size = (uint8_t)S;
+        it.variant = (uint32_t)q.r.variant;
         out.push_back(it);
     }
 }
@@ -500,9 +501,10 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
 nx_status nx_submit(nx_server* s, const nx_request* r, uint64_t* ticket)
 {
     if (!s || !r || !ticket) return nx_fail(nullptr, NX_E_INVAL, "NULL argument");
-    if (r->family < NX_EMPTY || r->family > NX_DYNOBS || r->size < NX_MIN_SIZE || r->size > NX_MAX_SIZE ||
-        r->n_envs < 1 || r->horizon < 1)
-        return nx_fail(nullptr, NX_E_INVAL, "request: family 0..4, size 5..19, n_envs >= 1, horizon >= 1");
+    if (r->family < NX_EMPTY || r->family >= NX_N_FAMILIES || r->size < NX_MIN_SIZE || r->size > NX_MAX_SIZE ||
+        r->n_envs < 1 || r->horizon < 1 || r->variant < 0 || r->variant > nx_max_variant(r->family, r->size))
+        return nx_fail(nullptr, NX_E_INVAL,
+                       "request: family 0..7, size 5..19, n_envs >= 1, horizon >= 1, variant <= nx_max_variant");
     SReq q;
     q.r = *r;
     q.max_steps = nx_default_max_steps(r->family, r->size);

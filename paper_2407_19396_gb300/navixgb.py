@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libnavixgb.so")
 
 NX_OK, NX_PENDING = 0, 1
 NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET, NX_E_STATE = -1, -2, -3, -4, -5, -6, -7
-NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS = range(5)
+NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS, NX_EMPTY_RANDOM, NX_LAVA_CROSSING, NX_SIMPLE_CROSSING = range(8)
 NX_OBS_SYM, NX_OBS_RGB = 1, 2
 NX_ACT_BUFFER, NX_ACT_RANDOM = 0, 1
 NX_REWARD_MARKOV, NX_REWARD_MINIGRID = 0, 1
@@ -29,7 +29,8 @@ OBS_SYM_BYTES, OBS_RGB_BYTES = 147, 150528
 ATLAS_BYTES = 397 * 3072
 AGENT_BYTES = 32
 FAMILIES = {"empty": NX_EMPTY, "doorkey": NX_DOORKEY, "fourrooms": NX_FOURROOMS, "lavagap": NX_LAVAGAP,
-            "dynobs": NX_DYNOBS}
+            "dynobs": NX_DYNOBS, "empty_random": NX_EMPTY_RANDOM, "lava_crossing": NX_LAVA_CROSSING,
+            "simple_crossing": NX_SIMPLE_CROSSING}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -37,7 +38,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 class nx_desc(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
-                ("max_steps", ctypes.c_int32)]
+                ("max_steps", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class nx_options(ctypes.Structure):
@@ -45,7 +46,7 @@ class nx_options(ctypes.Structure):
                 ("n_balls", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("group_lanes", ctypes.c_int32), ("envs_per_cta", ctypes.c_int32), ("staging", ctypes.c_int32),
                 ("atlas", ctypes.POINTER(ctypes.c_uint8)), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p), ("env_index_base", ctypes.c_uint32)]
+                ("alloc_user", ctypes.c_void_p), ("env_index_base", ctypes.c_uint32), ("variant", ctypes.c_int32)]
 
 
 class nx_out(ctypes.Structure):
@@ -62,8 +63,8 @@ class nx_info(ctypes.Structure):
 
 class nx_request(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("size", ctypes.c_int32), ("n_envs", ctypes.c_int32),
-                ("horizon", ctypes.c_int32), ("seed", ctypes.c_uint64), ("returns", ctypes.c_void_p),
-                ("final_obs", ctypes.c_void_p)]
+                ("horizon", ctypes.c_int32), ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("returns", ctypes.c_void_p), ("final_obs", ctypes.c_void_p)]
 
 
 class nx_result(ctypes.Structure):
@@ -84,6 +85,7 @@ _P = ctypes.POINTER
 _vp, _i32, _u32, _u64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
 SIGNATURES = {
     "nx_options_default": (None, [_P(nx_options)]),
+    "nx_max_variant": (_i32, [_i32, _i32]),
     "nx_create": (_i32, [_P(_vp), _i32, _i32, _i32, _u64, _P(nx_options), _vp]),
     "nx_create_mixed": (_i32, [_P(_vp), _P(nx_desc), _i32, _u64, _P(nx_options), _vp]),
     "nx_reset": (_i32, [_vp, _P(nx_out)]),
@@ -163,8 +165,13 @@ def nx_create(family, size, n_envs, seed, opts=None, stream=0):
     return h
 
 
+def nx_max_variant(family, size):
+    return int(lib().nx_max_variant(family, size))
+
+
 def nx_create_mixed(descs, seed, opts=None, stream=0):
-    arr = (nx_desc * len(descs))(*[nx_desc(int(f), int(s), int(s), int(m)) for f, s, m in descs])
+    """descs: (family, size, max_steps, variant) per env."""
+    arr = (nx_desc * len(descs))(*[nx_desc(int(f), int(s), int(s), int(m), int(v)) for f, s, m, v in descs])
     h = ctypes.c_void_p()
     st = lib().nx_create_mixed(ctypes.byref(h), arr, len(descs), seed, ctypes.byref(opts) if opts else None,
                                ctypes.c_void_p(stream))
@@ -298,7 +305,8 @@ class Env:
 
     def __init__(self, family=NX_EMPTY, size=5, n_envs=1, seed=0, *, descs=None, obs_sym=True, obs_rgb=False,
                  atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
-                 autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, torch_allocator=True):
+                 autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, variant=0,
+                 torch_allocator=True):
         import torch
 
         self.torch = torch
@@ -317,6 +325,7 @@ class Env:
         o.envs_per_cta = envs_per_cta
         o.staging = staging
         o.env_index_base = env_index_base
+        o.variant = variant
         self._atlas = None
         if obs_rgb:
             if atlas is None:
@@ -343,7 +352,8 @@ class Env:
             self.n = int(n_envs)
             self.h = nx_create(int(family), int(size), self.n, int(seed), o, self.stream.cuda_stream)
         else:
-            d = [(f, s, (m[0] if m else 0)) for f, s, *m in descs]
+            # each desc: (family, size[, max_steps[, variant]])
+            d = [(f, s, (m[0] if len(m) > 0 else 0), (m[1] if len(m) > 1 else 0)) for f, s, *m in descs]
             self.n = len(d)
             self.h = nx_create_mixed(d, int(seed), o, self.stream.cuda_stream)
 
@@ -530,10 +540,11 @@ class Server:
         self.h = nx_server_create(budget_bytes, o, stream)
         self._bufs = {}
 
-    def submit(self, family, size, n_envs, horizon, seed):
+    def submit(self, family, size, n_envs, horizon, seed, variant=0):
         ret = np.zeros(n_envs, np.float32)
         obs = np.zeros((n_envs, 7, 7, 3), np.uint8)
-        r = nx_request(int(family), int(size), int(n_envs), int(horizon), int(seed), ret.ctypes.data, obs.ctypes.data)
+        r = nx_request(int(family), int(size), int(n_envs), int(horizon), int(variant), 0, int(seed), ret.ctypes.data,
+                       obs.ctypes.data)
         t = nx_submit(self.h, r)
         self._bufs[t] = (ret, obs)
         return t

@@ -7,7 +7,7 @@ import numpy as np
 import oracle as O
 
 STATE_KEYS = ("x", "y", "dir", "carry_ent", "carry_col", "done", "t", "episode", "ent", "col", "st", "ball_x",
-              "ball_y", "invalid", "max_steps", "height")
+              "ball_y", "invalid", "max_steps", "height", "family")
 
 
 def to_np(t):
@@ -44,14 +44,17 @@ def assert_states_equal(gpu_envs: list, orc_batch: O.Batch, indices=None, what="
 
 
 def oracle_batch_for(descs, seed, indices=None, **kw):
+    """descs: (family, size[, max_steps[, variant]]) per env, as given to navixgb.Env."""
     fam = [d[0] for d in descs]
     siz = [d[1] for d in descs]
     ms = [(d[2] if len(d) > 2 and d[2] else O.default_max_steps(d[0], d[1])) for d in descs]
+    var = [(d[3] if len(d) > 3 else 0) for d in descs]
     if indices is not None:
         fam = [fam[i] for i in indices]
         siz = [siz[i] for i in indices]
         ms = [ms[i] for i in indices]
-    return O.Batch(fam, siz, seed, max_steps=ms, env_indices=indices, **kw)
+        var = [var[i] for i in indices]
+    return O.Batch(fam, siz, seed, max_steps=ms, env_indices=indices, variants=var, **kw)
 
 
 def mixed_descs(n_total, parts):
@@ -79,11 +82,11 @@ def record_words(obs, reward, term, trunc):
     return np.concatenate([cells, rbits[:, None], flags[:, None]], axis=1)
 
 
-def oracle_request(family, size, n_envs, horizon, seed, **kw):
+def oracle_request(family, size, n_envs, horizon, seed, variant=0, **kw):
     """What a serving request must return, computed by the oracle: per-env
     returns (float32, summed in step order), the final view, the number of
     ended episodes and the digest of the reset record plus every step record."""
-    b = O.Batch([family] * n_envs, [size] * n_envs, seed, **kw)
+    b = O.Batch([family] * n_envs, [size] * n_envs, seed, variants=[variant] * n_envs, **kw)
     r0 = b.reset()
     h = np.zeros(n_envs, np.uint64)
     with np.errstate(over="ignore"):

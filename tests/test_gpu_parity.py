@@ -34,18 +34,21 @@ def nxmod():
     return nx
 
 
-ALL_FAMILIES = [(O.EMPTY, 5), (O.EMPTY, 8), (O.EMPTY, 16), (O.DOORKEY, 5), (O.DOORKEY, 8), (O.DOORKEY, 16),
-                (O.FOURROOMS, 19), (O.FOURROOMS, 9), (O.LAVAGAP, 5), (O.LAVAGAP, 7), (O.DYNOBS, 5), (O.DYNOBS, 16),
-                (O.DOORKEY, 19), (O.EMPTY, 19), (O.LAVAGAP, 13)]
+ALL_FAMILIES = [(O.EMPTY, 5, 0), (O.EMPTY, 8, 0), (O.EMPTY, 16, 0), (O.DOORKEY, 5, 0), (O.DOORKEY, 8, 0),
+                (O.DOORKEY, 16, 0), (O.FOURROOMS, 19, 0), (O.FOURROOMS, 9, 0), (O.LAVAGAP, 5, 0), (O.LAVAGAP, 7, 0),
+                (O.DYNOBS, 5, 0), (O.DYNOBS, 16, 0), (O.DOORKEY, 19, 0), (O.EMPTY, 19, 0), (O.LAVAGAP, 13, 0),
+                (O.EMPTY_RANDOM, 5, 0), (O.EMPTY_RANDOM, 16, 0), (O.LAVA_CROSSING, 9, 1), (O.LAVA_CROSSING, 9, 3),
+                (O.LAVA_CROSSING, 11, 5), (O.SIMPLE_CROSSING, 9, 2), (O.SIMPLE_CROSSING, 19, 16),
+                (O.SIMPLE_CROSSING, 5, 2), (O.LAVA_CROSSING, 13, 0)]
 
 
-@pytest.mark.parametrize("family,size", ALL_FAMILIES)
-def test_reset_matches_oracle(family, size):
+@pytest.mark.parametrize("family,size,variant", ALL_FAMILIES)
+def test_reset_matches_oracle(family, size, variant):
     nx = nxmod()
     n = 37  # ragged against every envs-per-CTA choice
-    env = nx.Env(family, size, n, seed=11, autotune=False)
+    env = nx.Env(family, size, n, seed=11, autotune=False, variant=variant)
     out = env.reset()
-    ob = O.Batch([family] * n, [size] * n, seed=11)
+    ob = O.Batch([family] * n, [size] * n, seed=11, variants=[variant] * n)
     oo = ob.reset()
     assert_outputs_equal(out, oo, what="reset")
     assert_states_equal(env.state()["envs"], ob, what="reset")
@@ -321,6 +324,37 @@ def test_reward_variants(reward_mode, lava):
     r = to_np(out["reward"])
     assert (r[(r != 0)] != 1.0).any() or reward_mode == 0
     env.close()
+
+
+NEW_FAMILIES = [(O.EMPTY_RANDOM, 6, 0, 0), (O.LAVA_CROSSING, 9, 0, 1), (O.LAVA_CROSSING, 9, 0, 3),
+                (O.LAVA_CROSSING, 11, 0, 5), (O.SIMPLE_CROSSING, 9, 0, 2), (O.SIMPLE_CROSSING, 11, 0, 5),
+                (O.EMPTY_RANDOM, 16, 0, 0), (O.SIMPLE_CROSSING, 19, 0, 9)]
+
+
+@pytest.mark.parametrize("lanes,envs,staging", [(1, 64, 2), (8, 16, 1), (32, 4, 1)])
+def test_new_families_every_step(lanes, envs, staging):
+    nx = nxmod()
+    descs = mixed_descs(200, NEW_FAMILIES)
+    for lava in (0.0, -1.0):
+        env = nx.Env(descs=descs, seed=41, group_lanes=lanes, envs_per_cta=envs, staging=staging, autotune=False,
+                     steps_per_launch=50, lava_reward=lava)
+        r = env.reset()
+        out = env.rollout(400)
+        ob = oracle_batch_for(descs, 41, lava_reward=lava)
+        assert_outputs_equal(r, ob.reset(), what="reset")
+        assert_outputs_equal(out, ob.rollout(400), what=f"new families G={lanes} lava={lava}")
+        assert_states_equal(env.state()["envs"], ob, what="new families")
+        env.close()
+
+
+def test_variant_validation():
+    nx = nxmod()
+    assert nx.nx_max_variant(O.LAVA_CROSSING, 9) == O.max_variant(O.LAVA_CROSSING, 9) == 6
+    assert nx.nx_max_variant(O.SIMPLE_CROSSING, 19) == 16 and nx.nx_max_variant(O.DOORKEY, 9) == 0
+    with pytest.raises(nx.NavixError):
+        nx.Env(O.LAVA_CROSSING, 9, 4, seed=0, variant=7)
+    with pytest.raises(nx.NavixError):
+        nx.Env(O.DOORKEY, 9, 4, seed=0, variant=1)
 
 
 def test_nballs_option_and_small_dynobs():
