@@ -47,6 +47,9 @@ WORKLOADS = {
     "rgb": dict(desc="Dynamic-Obstacles-16x16, 4 balls, 8192 envs x 512 steps, seed 3, 3 random actions, "
                      "RGB 224x224x3 + symbolic obs (8-slot output ring)",
                 parts=[(4, 16)], n=8192, T=512, seed=3, rgb=True, depth=8),
+    "doorkey8_full": dict(desc="DoorKey-8x8, 4096 envs x 1000 steps, seed 1, symbolic + fully observable views "
+                               "(symbolic 8x8x3, categorical 8x8, categorical first person 7x7)",
+                          parts=[(1, 8)], n=4096, T=1000, seed=1, rgb=False, depth=1000, full=True),
     # a reduced RGB case sized for ncu captures only (about 2.5 GB written per launch)
     "rgb_small": dict(desc="Dynamic-Obstacles-16x16, 4 balls, 1024 envs x 16 steps, seed 3, RGB + symbolic, 2-slot ring",
                       parts=[(4, 16)], n=1024, T=16, seed=3, rgb=True, depth=2, steps_per_launch=16),
@@ -71,7 +74,8 @@ def alg_bytes(w, descs, steps_per_launch):
     S*S bytes plus a 32-byte agent block)."""
     T = w["T"]
     n = len(descs)
-    per_step = OUT_BYTES_SYM + (OUT_BYTES_RGB if w["rgb"] else 0)
+    side = max(s for _, s in descs)
+    per_step = OUT_BYTES_SYM + (OUT_BYTES_RGB if w["rgb"] else 0) + (side * side * 4 + 49 if w.get("full") else 0)
     state = sum(3 * s * s + 32 for _, s in descs)
     launches = -(-T // steps_per_launch)
     return n * T * per_step + 2 * state * launches
@@ -361,7 +365,9 @@ def main():
                      autotune=False)
     if "steps_per_launch" in w:
         shape["steps_per_launch"] = w["steps_per_launch"]
-    env = nx.Env(descs=descs, seed=w["seed"], obs_rgb=w["rgb"], atlas=atlas, env_index_base=rank * n, **shape)
+    fv = bool(w.get("full"))
+    env = nx.Env(descs=descs, seed=w["seed"], obs_rgb=w["rgb"], atlas=atlas, env_index_base=rank * n,
+                 obs_full=fv, obs_cat=fv, obs_cat_fp=fv, **shape)
     env.reset()
     out = env.alloc_out(w["depth"])
     if args.ncu_case:
@@ -451,12 +457,14 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {}
-        for name in ("mixed", "rgb", "empty5"):
+        for name in ("mixed", "rgb", "empty5", "doorkey8_full"):
             if name == args.workload:
                 continue
             wx = WORKLOADS[name]
             dx = descs_of(wx)
-            ex = nx.Env(descs=dx, seed=wx["seed"], obs_rgb=wx["rgb"], atlas=inputs.atlas() if wx["rgb"] else None)
+            fv = bool(wx.get("full"))
+            ex = nx.Env(descs=dx, seed=wx["seed"], obs_rgb=wx["rgb"], atlas=inputs.atlas() if wx["rgb"] else None,
+                        obs_full=fv, obs_cat=fv, obs_cat_fp=fv)
             ex.reset()
             ox = ex.alloc_out(wx["depth"])
             ms, kms, kl, _ = time_rollouts(ex, wx, ox, 2, 1, flush)

@@ -123,9 +123,17 @@ typedef struct {
 /* Per-step outputs, device pointers owned by the caller; any may be NULL (not
  * written).  Shapes are [depth, n_envs, ...] row-major: obs_sym [.., 7, 7, 3]
  * uint8 laid out [view row vy][view column vx][entity, colour, state] with
- * the agent at (vx 3, vy 6) facing vy = 0; obs_rgb [.., 224, 224, 3] uint8;
- * reward [..] float32; terminated / truncated [..] uint8 (0/1).  Step i of a
- * call writes time slot i % depth (depth <= 0 means 1). */
+ * the agent at (vx 3, vy 6) facing vy = 0 (symbolic_first_person, Table 4);
+ * obs_rgb [.., 224, 224, 3] uint8 (rgb_first_person); reward [..] float32;
+ * terminated / truncated [..] uint8 (0/1).  Step i of a call writes time
+ * slot i % depth (depth <= 0 means 1).
+ * The fully observable views of Table 4 (device rollouts only):
+ * obs_full [.., full_side, full_side, 3] (symbolic: every cell's triple, row
+ * y then column x, the agent's cell holding (10, 0, direction)), obs_cat
+ * [.., full_side, full_side] (categorical: entity codes, the agent 10), both
+ * zero beyond an env's grid; obs_cat_fp [.., 7, 7] (categorical_first_person:
+ * the entity bytes of obs_sym).  full_side must be at least the largest grid
+ * size (0: the largest grid size). */
 typedef struct {
     uint8_t* obs_sym;
     uint8_t* obs_rgb;
@@ -133,6 +141,10 @@ typedef struct {
     uint8_t* terminated;
     uint8_t* truncated;
     int32_t depth;
+    int32_t full_side;
+    uint8_t* obs_full;
+    uint8_t* obs_cat;
+    uint8_t* obs_cat_fp;
 } nx_out;
 
 /* Launch shape in use (after autotuning). */
@@ -196,7 +208,8 @@ nx_status nx_rollout_per_family(nx_env* env, int32_t n_steps, int32_t act_mode, 
  * overlap): actions are copied in and outputs copied back chunk by chunk on
  * the context stream; returns when the copies have finished.  host_actions_TN
  * is int8 [n_steps, n_envs] (ignored for NX_ACT_RANDOM); the host outputs are
- * [n_steps, n_envs, ...] (depth is ignored).  Any output may be NULL. */
+ * [n_steps, n_envs, ...] (depth is ignored).  Any output may be NULL; the
+ * fully observable views are not available here (NX_E_INVAL). */
 nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* host_actions_TN,
                           const nx_out* host_traj);
 

@@ -101,6 +101,10 @@ def lib():
             L.orc_batch_reset.argtypes = [ctypes.c_void_p, u8p, u8p, u8p, f32p, u8p, u8p]
             L.orc_batch_step.argtypes = [ctypes.c_void_p, i8p, u8p, u8p, u8p, f32p, u8p, u8p]
             L.orc_batch_rollout.argtypes = [ctypes.c_void_p, ctypes.c_int32, i8p, u8p, u8p, u8p, f32p, u8p, u8p]
+            L.orc_obs_full.argtypes = [P(OrcEnv), u8p, ctypes.c_int32]
+            L.orc_obs_cat.argtypes = [P(OrcEnv), u8p, ctypes.c_int32]
+            L.orc_obs_cat_fp.argtypes = [P(OrcEnv), u8p]
+            L.orc_batch_obs_full.argtypes = [ctypes.c_void_p, u8p, u8p, u8p, ctypes.c_int32]
             L.orc_batch_gstep.argtypes = [ctypes.c_void_p]
             L.orc_batch_gstep.restype = ctypes.c_uint32
             _lib = L
@@ -176,6 +180,23 @@ class Env:
         lib().orc_obs_rgb(ctypes.byref(self.s), _ptr(np.ascontiguousarray(atlas, np.uint8).reshape(-1), ctypes.c_uint8),
                           _ptr(img, ctypes.c_uint8))
         return img.reshape(224, 224, 3)
+
+    def full(self, side=None):
+        side = side or self.s.width
+        o = np.zeros(side * side * 3, np.uint8)
+        lib().orc_obs_full(ctypes.byref(self.s), _ptr(o, ctypes.c_uint8), side)
+        return o.reshape(side, side, 3)
+
+    def cat(self, side=None):
+        side = side or self.s.width
+        o = np.zeros(side * side, np.uint8)
+        lib().orc_obs_cat(ctypes.byref(self.s), _ptr(o, ctypes.c_uint8), side)
+        return o.reshape(side, side)
+
+    def cat_fp(self):
+        o = np.zeros(49, np.uint8)
+        lib().orc_obs_cat_fp(ctypes.byref(self.s), _ptr(o, ctypes.c_uint8))
+        return o.reshape(7, 7)
 
     def set_cell(self, x, y, ent, col, st):
         lib().orc_set_cell(ctypes.byref(self.s), x, y, ent, col, st)
@@ -269,6 +290,24 @@ class Batch:
         a = None if actions is None else np.ascontiguousarray(actions, np.int8)
         self._call(lib().orc_batch_rollout, (ctypes.c_int32(T), _ptr(a, ctypes.c_int8)), o, atlas)
         return o
+
+    def full_views(self, side):
+        """Current fully observable views: (symbolic [n,side,side,3], categorical [n,side,side], cat_fp [n,7,7])."""
+        full = np.zeros((self.n, side, side, 3), np.uint8)
+        cat = np.zeros((self.n, side, side), np.uint8)
+        cfp = np.zeros((self.n, 7, 7), np.uint8)
+        lib().orc_batch_obs_full(self.h, _ptr(full, ctypes.c_uint8), _ptr(cat, ctypes.c_uint8),
+                                 _ptr(cfp, ctypes.c_uint8), side)
+        return full, cat, cfp
+
+    def rollout_full(self, T, side, actions=None):
+        """T steps with every output, including the fully observable views."""
+        outs = []
+        for t in range(T):
+            o = self.step(None if actions is None else actions[t])
+            o["obs_full"], o["obs_cat"], o["obs_cat_fp"] = self.full_views(side)
+            outs.append(o)
+        return {k: np.stack([o[k] for o in outs]) for k in outs[0] if outs[0][k] is not None}
 
     def env(self, i) -> OrcEnv:
         return lib().orc_batch_env(self.h, i).contents

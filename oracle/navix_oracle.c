@@ -707,6 +707,49 @@ void orc_obs_rgb(const orc_env* e, const uint8_t* atlas, uint8_t* img)
         }
 }
 
+/* symbolic (Table 4): the canonical grid encoding of the whole grid; the
+ * agent's cell holds (agent, red, direction) in place of what lies under it
+ * (reading R19).  categorical (Table 4): the entity code of every cell, the
+ * agent's cell holding the agent code (reading R20).  Cells beyond the grid
+ * (up to `side`) are 0. */
+void orc_obs_full(const orc_env* e, uint8_t* full, int32_t side)
+{
+    for (int y = 0; y < side; y++)
+        for (int x = 0; x < side; x++) {
+            uint8_t* o = full + ((size_t)y * side + x) * 3;
+            if (x >= e->width || y >= e->height) {
+                o[0] = o[1] = o[2] = 0;
+            } else if (x == e->ax && y == e->ay) {
+                o[0] = ORC_AGENT;
+                o[1] = ORC_RED;
+                o[2] = (uint8_t)e->dir;
+            } else {
+                int i = idx(e, x, y);
+                o[0] = e->ent[i];
+                o[1] = e->col[i];
+                o[2] = e->st[i];
+            }
+        }
+}
+
+void orc_obs_cat(const orc_env* e, uint8_t* cat, int32_t side)
+{
+    for (int y = 0; y < side; y++)
+        for (int x = 0; x < side; x++) {
+            uint8_t v = 0;
+            if (x < e->width && y < e->height) v = (x == e->ax && y == e->ay) ? ORC_AGENT : e->ent[idx(e, x, y)];
+            cat[(size_t)y * side + x] = v;
+        }
+}
+
+/* categorical_first_person (Table 4): the entity codes of the egocentric view */
+void orc_obs_cat_fp(const orc_env* e, uint8_t cat[ORC_VIEW * ORC_VIEW])
+{
+    uint8_t obs[ORC_OBS_BYTES];
+    orc_obs_sym(e, obs);
+    for (int c = 0; c < ORC_VIEW * ORC_VIEW; c++) cat[c] = obs[3 * c];
+}
+
 /* ------------------------------------------------------------------------ */
 /* Batch convenience (vmap over environments, Code 3), stepped sequentially. */
 struct orc_batch {
@@ -811,5 +854,15 @@ void orc_batch_rollout(orc_batch* b, int32_t T, const int8_t* actions_TN, uint8_
                        obs_rgb ? obs_rgb + (size_t)t * n * ORC_RGB_BYTES : NULL, atlas,
                        reward ? reward + (size_t)t * n : NULL, terminated ? terminated + (size_t)t * n : NULL,
                        truncated ? truncated + (size_t)t * n : NULL);
+    }
+}
+
+void orc_batch_obs_full(orc_batch* b, uint8_t* full, uint8_t* cat, uint8_t* cat_fp, int32_t side)
+{
+    for (int32_t i = 0; i < b->n; i++) {
+        const orc_env* e = &b->envs[i];
+        if (full) orc_obs_full(e, full + (size_t)i * side * side * 3, side);
+        if (cat) orc_obs_cat(e, cat + (size_t)i * side * side, side);
+        if (cat_fp) orc_obs_cat_fp(e, cat_fp + (size_t)i * ORC_VIEW * ORC_VIEW);
     }
 }

@@ -92,6 +92,12 @@ int32_t orc_random_action(const orc_env* e, uint32_t gstep);
 void orc_step(orc_env* e, int32_t action, float* reward, uint8_t* terminated, uint8_t* truncated);
 void orc_obs_sym(const orc_env* e, uint8_t obs[ORC_OBS_BYTES]);
 int32_t orc_tile_index(int32_t visible, int32_t agent_cell, int32_t ent, int32_t col, int32_t st);
+/* Fully observable views (Table 4): symbolic [side][side][3] and categorical
+ * [side][side], row-major over y then x, padded with zeros up to `side`
+ * (>= the grid size); and categorical_first_person [7][7]. */
+void orc_obs_full(const orc_env* e, uint8_t* full, int32_t side);
+void orc_obs_cat(const orc_env* e, uint8_t* cat, int32_t side);
+void orc_obs_cat_fp(const orc_env* e, uint8_t cat[ORC_VIEW * ORC_VIEW]);
 void orc_obs_rgb(const orc_env* e, const uint8_t* atlas, uint8_t* img);
 
 /* hand-built states for the worked sequences */
@@ -121,6 +127,9 @@ void orc_batch_step(orc_batch* b, const int8_t* actions, uint8_t* obs_sym, uint8
 void orc_batch_rollout(orc_batch* b, int32_t T, const int8_t* actions_TN, uint8_t* obs_sym, uint8_t* obs_rgb,
                        const uint8_t* atlas, float* reward, uint8_t* terminated, uint8_t* truncated);
 uint32_t orc_batch_gstep(const orc_batch* b);
+/* the current fully observable views of every env ([n, side, side, 3],
+ * [n, side, side], [n, 7, 7]; any may be NULL) */
+void orc_batch_obs_full(orc_batch* b, uint8_t* full, uint8_t* cat, uint8_t* cat_fp, int32_t side);
 
 #ifdef __cplusplus
 }

@@ -257,6 +257,7 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
         env->grid_offset[i] = (uint32_t)off;
         off += (size_t)3 * S * S;
         max_cells = std::max(max_cells, S * S);
+        env->max_side = std::max(env->max_side, S);
         seen[env->descs[i].family] = true;
     }
     if (off > 0xFFFFFFFFull) {
@@ -494,12 +495,19 @@ static nx_req call_req(const nx_env* env, int steps, int act_mode, const int8_t*
     r.returns = nullptr;
     r.digest = nullptr;
     r.episodes = nullptr;
+    r.obs_full = out ? out->obs_full : nullptr;
+    r.obs_cat = out ? out->obs_cat : nullptr;
+    r.obs_cat_fp = out ? out->obs_cat_fp : nullptr;
+    r.full_side = (out && out->full_side > 0) ? out->full_side : env->max_side;
     return r;
 }
 
 static nx_status check_out(nx_env* env, const nx_out* out)
 {
     if (out && out->obs_rgb && !env->rgb) return nx_fail(env, NX_E_INVAL, "obs_rgb given but NX_OBS_RGB was not enabled");
+    if (out && (out->obs_full || out->obs_cat) && out->full_side > 0 && out->full_side < env->max_side)
+        return nx_fail(env, NX_E_INVAL, "full_side is smaller than the largest grid");
+    if (out && (out->full_side < 0 || out->full_side > 255)) return nx_fail(env, NX_E_INVAL, "full_side must be 0..255");
     return NX_OK;
 }
 
@@ -601,6 +609,8 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
     if (act_mode == NX_ACT_BUFFER && !h_actions) return nx_fail(env, NX_E_INVAL, "NX_ACT_BUFFER needs actions");
     nx_status st = check_out(env, h);
     if (st != NX_OK) return st;
+    if (h && (h->obs_full || h->obs_cat || h->obs_cat_fp))
+        return nx_fail(env, NX_E_INVAL, "the fully observable views are device outputs only");
     if (n_steps == 0) return NX_OK;
     if (!env->tuned) {
         st = nx_autotune(env);

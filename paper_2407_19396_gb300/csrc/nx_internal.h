@@ -68,6 +68,11 @@ struct NX_ALIGN16 nx_req {
     float lava_reward;
     int32_t n_balls;      // Dynamic-Obstacles balls placed at every reset
     uint32_t key_base;    // draw-counter env index of the request's env 0
+    uint8_t* obs_full;    // [depth, n_envs, full_side, full_side, 3] (may be NULL)
+    uint8_t* obs_cat;     // [depth, n_envs, full_side, full_side]
+    uint8_t* obs_cat_fp;  // [depth, n_envs, 7, 7]
+    int32_t full_side;
+    int32_t pad2;
 };
 
 struct NX_ALIGN16 nx_ctl {

@@ -208,6 +208,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         float* returns = rq->returns;
         uint64_t* digest = rq->digest;
         uint32_t* episodes = rq->episodes;
+        uint8_t* obs_full = rq->obs_full;
+        uint8_t* obs_cat = rq->obs_cat;
+        uint8_t* obs_cat_fp = rq->obs_cat_fp;
+        const int F = rq->full_side;
 
         const int n = (int)item.n_envs, S = item.size, HW = S * S, family = item.family, variant = (int)item.variant;
         const int max_steps = item.max_steps;
@@ -313,6 +317,25 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 }
                 grp.sync();
                 render_view(grp, mygrid, S, a, s_dec, vo, RGB && obs_rgb ? stiles + gi * 49 : nullptr);
+                if (obs_full || obs_cat) {
+                    // fully observable views: every cell's triple, the agent's
+                    // cell holding (agent, red, direction), zero beyond the grid
+                    const size_t row = (size_t)slot * nreq + local;
+                    uint8_t* fo = obs_full ? obs_full + row * (size_t)(F * F * 3) : nullptr;
+                    uint8_t* co = obs_cat ? obs_cat + row * (size_t)(F * F) : nullptr;
+                    for (int c = grp.lane; c < F * F; c += G) {
+                        const int y = c / F, x = c - y * F;
+                        uint32_t tri = 0;
+                        if (x < S && y < S)
+                            tri = (x == a.x && y == a.y) ? (10u | ((uint32_t)a.dir << 16)) : s_dec[mygrid[y * S + x]];
+                        if (fo) {
+                            fo[3 * c] = (uint8_t)tri;
+                            fo[3 * c + 1] = (uint8_t)(tri >> 8);
+                            fo[3 * c + 2] = (uint8_t)(tri >> 16);
+                        }
+                        if (co) co[c] = (uint8_t)tri;
+                    }
+                }
                 if (grp.lane == 0) {
                     const size_t o = (size_t)slot * nreq + local;
                     if (out_reward) out_reward[o] = reward;
@@ -333,6 +356,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 if (active && gi >= lo && gi < hi) {
                     uint8_t* my_sym = stage + (gi - lo) * NX_OBS_SYM_BYTES;
                     write_view(grp, vo, my_sym);
+                    if (obs_cat_fp) {
+                        // categorical_first_person: the entity bytes of the staged view
+                        grp.sync();
+                        uint8_t* cf = obs_cat_fp + ((size_t)slot * nreq + local) * 49;
+                        for (int c = grp.lane; c < 49; c += G) cf[c] = my_sym[3 * c];
+                    }
                     if (digest) {
                         grp.sync();
                         if (grp.lane == 0) {

@@ -29,6 +29,7 @@ struct nx_env {
     std::vector<uint32_t> grid_offset;
     size_t grid_pool = 0;
     int cell_stride = 0;
+    int max_side = 0;
     int device = 0;
     int sm_count = 0;
     cudaStream_t stream = nullptr;

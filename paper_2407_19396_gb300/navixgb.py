@@ -51,7 +51,11 @@ class nx_options(ctypes.Structure):
 
 class nx_out(ctypes.Structure):
     _fields_ = [("obs_sym", ctypes.c_void_p), ("obs_rgb", ctypes.c_void_p), ("reward", ctypes.c_void_p),
-                ("terminated", ctypes.c_void_p), ("truncated", ctypes.c_void_p), ("depth", ctypes.c_int32)]
+                ("terminated", ctypes.c_void_p), ("truncated", ctypes.c_void_p), ("depth", ctypes.c_int32),
+                ("full_side", ctypes.c_int32), ("obs_full", ctypes.c_void_p), ("obs_cat", ctypes.c_void_p),
+                ("obs_cat_fp", ctypes.c_void_p)]
+
+OUT_KEYS = ("obs_sym", "obs_rgb", "reward", "terminated", "truncated", "obs_full", "obs_cat", "obs_cat_fp")
 
 
 class nx_info(ctypes.Structure):
@@ -306,7 +310,7 @@ class Env:
     def __init__(self, family=NX_EMPTY, size=5, n_envs=1, seed=0, *, descs=None, obs_sym=True, obs_rgb=False,
                  atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
                  autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, variant=0,
-                 torch_allocator=True):
+                 obs_full=False, obs_cat=False, obs_cat_fp=False, torch_allocator=True):
         import torch
 
         self.torch = torch
@@ -348,13 +352,16 @@ class Env:
             o.alloc, o.free = self._cbs
         self.opts = o
         self.obs_sym, self.obs_rgb = obs_sym, obs_rgb
+        self.want_full, self.want_cat, self.want_cat_fp = obs_full, obs_cat, obs_cat_fp
         if descs is None:
             self.n = int(n_envs)
+            self.side = int(size)
             self.h = nx_create(int(family), int(size), self.n, int(seed), o, self.stream.cuda_stream)
         else:
             # each desc: (family, size[, max_steps[, variant]])
             d = [(f, s, (m[0] if len(m) > 0 else 0), (m[1] if len(m) > 1 else 0)) for f, s, *m in descs]
             self.n = len(d)
+            self.side = max(x[1] for x in d)
             self.h = nx_create_mixed(d, int(seed), o, self.stream.cuda_stream)
 
     def close(self):
@@ -379,15 +386,19 @@ class Env:
             "terminated": torch.empty(lead + (n,), dtype=torch.uint8, device=self.device),
             "truncated": torch.empty(lead + (n,), dtype=torch.uint8, device=self.device),
         }
+        F = self.side
+        o["obs_full"] = torch.empty(lead + (n, F, F, 3), dtype=torch.uint8, device=self.device) if self.want_full else None
+        o["obs_cat"] = torch.empty(lead + (n, F, F), dtype=torch.uint8, device=self.device) if self.want_cat else None
+        o["obs_cat_fp"] = torch.empty(lead + (n, 7, 7), dtype=torch.uint8, device=self.device) if self.want_cat_fp else None
         return o
 
-    @staticmethod
-    def out_struct(o, depth=1):
+    def out_struct(self, o, depth=1):
         s = nx_out()
-        for k in ("obs_sym", "obs_rgb", "reward", "terminated", "truncated"):
+        for k in OUT_KEYS:
             t = o.get(k)
             setattr(s, k, t.data_ptr() if t is not None else None)
         s.depth = depth
+        s.full_side = self.side
         return s
 
     def reset(self, out=None):

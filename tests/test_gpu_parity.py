@@ -347,6 +347,28 @@ def test_new_families_every_step(lanes, envs, staging):
         env.close()
 
 
+@pytest.mark.parametrize("lanes,envs,staging", [(1, 64, 2), (8, 16, 1), (32, 4, 1)])
+def test_fully_observable_views(lanes, envs, staging):
+    """symbolic / categorical / categorical_first_person (Table 4) of a mixed-size
+    batch, padded to the largest grid, every step."""
+    nx = nxmod()
+    descs = mixed_descs(90, [(O.DOORKEY, 8), (O.FOURROOMS, 11), (O.SIMPLE_CROSSING, 9, 0, 3), (O.DYNOBS, 6)])
+    env = nx.Env(descs=descs, seed=51, group_lanes=lanes, envs_per_cta=envs, staging=staging, autotune=False,
+                 steps_per_launch=40, obs_full=True, obs_cat=True, obs_cat_fp=True)
+    r = env.reset()
+    out = env.rollout(120)
+    ob = oracle_batch_for(descs, 51)
+    ob.reset()
+    f0, c0, p0 = ob.full_views(11)
+    np.testing.assert_array_equal(to_np(r["obs_full"]), f0)
+    np.testing.assert_array_equal(to_np(r["obs_cat"]), c0)
+    np.testing.assert_array_equal(to_np(r["obs_cat_fp"]), p0)
+    oo = ob.rollout_full(120, 11)
+    assert_outputs_equal(out, oo, keys=("obs_sym", "reward", "terminated", "truncated", "obs_full", "obs_cat",
+                                        "obs_cat_fp"), what=f"full views G={lanes}")
+    env.close()
+
+
 def test_variant_validation():
     nx = nxmod()
     assert nx.nx_max_variant(O.LAVA_CROSSING, 9) == O.max_variant(O.LAVA_CROSSING, 9) == 6

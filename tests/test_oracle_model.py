@@ -280,3 +280,43 @@ def test_ball_moves_stay_on_free_neighbours():
             assert max(abs(a - c), abs(b - d)) <= 1
             assert (c, d) != (env.s.ax, env.s.ay)
         assert len(set(after)) == 4
+
+
+@pytest.mark.parametrize("family,size,seed", [(O.DOORKEY, 8, 1), (O.FOURROOMS, 19, 2), (O.DYNOBS, 8, 3),
+                                              (O.SIMPLE_CROSSING, 11, 4)])
+def test_full_views_agree_with_the_grid_and_the_egocentric_view(family, size, seed):
+    """symbolic / categorical (Table 4) against the grid planes, and every
+    visible egocentric cell against the full view at its world position."""
+    variant = 3 if family == O.SIMPLE_CROSSING else 0
+    b = O.Batch([family] * 6, [size] * 6, seed=seed, variants=[variant] * 6)
+    b.reset()
+    for t in range(150):
+        o = b.step()
+        full, cat, cfp = b.full_views(size + 2)
+        for i in range(6):
+            s = b.state(i)
+            ent = np.frombuffer(s["ent"], np.uint8).reshape(size, size)
+            col = np.frombuffer(s["col"], np.uint8).reshape(size, size)
+            st = np.frombuffer(s["st"], np.uint8).reshape(size, size)
+            f = full[i]
+            assert (f[size:, :, :] == 0).all() and (f[:, size:, :] == 0).all()
+            x, y, d = s["x"], s["y"], s["dir"]
+            assert tuple(f[y, x]) == (10, 0, d) and cat[i, y, x] == 10
+            mask = np.ones((size, size), bool)
+            mask[y, x] = False
+            assert (f[:size, :size, 0][mask] == ent[mask]).all() and (f[:size, :size, 1][mask] == col[mask]).all()
+            assert (f[:size, :size, 2][mask] == st[mask]).all() and (cat[i, :size, :size][mask] == ent[mask]).all()
+            np.testing.assert_array_equal(cfp[i], o["obs_sym"][i][:, :, 0])
+            F = [(1, 0), (0, 1), (-1, 0), (0, -1)][d]
+            R = [(1, 0), (0, 1), (-1, 0), (0, -1)][(d + 1) % 4]
+            for vy in range(7):
+                for vx in range(7):
+                    v = o["obs_sym"][i][vy, vx]
+                    if (vx, vy) == (3, 6) or v[0] == 0:
+                        continue
+                    wx = x + (6 - vy) * F[0] + (vx - 3) * R[0]
+                    wy = y + (6 - vy) * F[1] + (vx - 3) * R[1]
+                    if 0 <= wx < size and 0 <= wy < size:
+                        assert tuple(v) == tuple(f[wy, wx])
+                    else:
+                        assert tuple(v) == (2, 5, 0)
