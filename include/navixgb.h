@@ -292,8 +292,9 @@ typedef struct {
 /* nx_server_create: hbm_budget_bytes (at most 4 GiB) is allocated once, up
  * front, and every admitted request's state and outputs are carved from it.
  * opts: steps_per_launch is the chunk length (latency vs launch overhead),
- * group_lanes / envs_per_cta fix the launch shape (0: 4 x 32), reward options
- * apply to every request; obs_flags must be NX_OBS_SYM. */
+ * group_lanes / envs_per_cta / staging fix the launch shape (0: 1 lane per
+ * env, 128 envs per block, half staging), reward options apply to every
+ * request; obs_flags must be NX_OBS_SYM. */
 nx_status nx_server_create(nx_server** server, size_t hbm_budget_bytes, const nx_options* opts, void* cuda_stream);
 /* nx_submit: queue a request; NX_E_BUDGET if it can never fit the budget,
  * NX_E_INVAL on bad arguments.  The host output buffers must stay valid until

@@ -130,7 +130,7 @@ struct nx_server {
     size_t budget = 0;
     int device = 0;
     int sm_count = 0;
-    nx_launch_shape shape{4, 32, 0};
+    nx_launch_shape shape{1, 128, 0, 2};  // measured best for the serving mix
     int cell_stride = 0, per_sm = 0, chunk = 128;
     int max_slots = 4096;
     size_t max_items = 0;
@@ -362,6 +362,7 @@ bool iterate(nx_server* s, int& cur, bool* idle)
     p.ctl = s->d_ctl;
     p.cell_stride = s->cell_stride;
     p.envs_per_cta = s->shape.envs_per_cta;
+    p.phases = s->shape.phases;
     const int max_grid = s->per_sm * s->sm_count;
     if (nr) {
         for (const SReq* qp : fresh_q) {
@@ -449,7 +450,7 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
     s->stream = (cudaStream_t)cuda_stream;
     s->budget = budget;
     s->chunk = o.steps_per_launch;
-    if (o.group_lanes) s->shape = nx_launch_shape{o.group_lanes, o.envs_per_cta, 0};
+    if (o.group_lanes) s->shape = nx_launch_shape{o.group_lanes, o.envs_per_cta, 0, o.staging == NX_STAGE_FULL ? 1 : 2};
     if (!nx_shape_supported(s->shape)) {
         delete s;
         return nx_fail(nullptr, NX_E_INVAL, "unsupported launch shape");

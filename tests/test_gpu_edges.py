@@ -1,0 +1,162 @@
+"""Edge cases and error paths of the C ABI on the GPU (exact comparisons with
+the oracle where outputs are produced)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from tests.gpu_util import assert_outputs_equal, assert_states_equal, mixed_descs, oracle_batch_for, to_np  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2407_19396_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def nxmod():
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    return nx
+
+
+def test_single_env_every_family():
+    nx = nxmod()
+    for fam, size, var in [(O.EMPTY, 5, 0), (O.DOORKEY, 19, 0), (O.FOURROOMS, 5, 0), (O.DYNOBS, 19, 0),
+                           (O.LAVA_CROSSING, 19, 16), (O.EMPTY_RANDOM, 19, 0)]:
+        env = nx.Env(fam, size, 1, seed=77, variant=var)
+        env.reset()
+        out = env.rollout(300)
+        ob = O.Batch([fam], [size], seed=77, variants=[var])
+        ob.reset()
+        assert_outputs_equal(out, ob.rollout(300), what=f"single env family {fam}")
+        env.close()
+
+
+@pytest.mark.parametrize("spl", [1, 7, 1024])
+def test_steps_per_launch_extremes_and_ring_wrap(spl):
+    nx = nxmod()
+    descs = mixed_descs(70, [(O.DOORKEY, 6), (O.LAVAGAP, 5)])
+    env = nx.Env(descs=descs, seed=8, steps_per_launch=spl, autotune=False)
+    env.reset()
+    T, D = 1100, 3
+    out = env.rollout(T, depth=D)
+    ob = oracle_batch_for(descs, 8)
+    ob.reset()
+    oo = ob.rollout(T)
+    # slot i % D holds step i: the ring keeps the last D steps
+    slots = [(T - D + i) % D for i in range(D)]
+    got = {k: to_np(out[k])[slots] for k in ("obs_sym", "reward", "terminated", "truncated")}
+    want = {k: oo[k][T - D:] for k in ("obs_sym", "reward", "terminated", "truncated")}
+    assert_outputs_equal(got, want, what=f"steps_per_launch={spl}")
+    assert_states_equal(env.state()["envs"], ob, what=f"steps_per_launch={spl}")
+    env.close()
+
+
+def test_many_more_envs_than_resident_ctas():
+    nx = nxmod()
+    n = 200_000
+    env = nx.Env(O.EMPTY, 5, n, seed=12, group_lanes=32, envs_per_cta=8, autotune=False)
+    env.reset()
+    out = env.rollout(12)
+    sample = sorted(set([0, 1, 2, n // 3, n // 2, n - 2, n - 1] + list(range(1000, n, 9973))))
+    ob = O.Batch([O.EMPTY] * len(sample), [5] * len(sample), seed=12, env_indices=sample)
+    ob.reset()
+    oo = ob.rollout(12)
+    got = {k: to_np(out[k])[:, sample] for k in ("obs_sym", "reward", "terminated", "truncated")}
+    assert_outputs_equal(got, oo, what="200k envs")
+    env.close()
+
+
+def test_reset_twice_restarts_everything():
+    nx = nxmod()
+    env = nx.Env(O.FOURROOMS, 11, 50, seed=3, autotune=False)
+    r1 = env.reset()
+    a = env.rollout(90)
+    r1 = {k: v.clone() if v is not None else None for k, v in r1.items()}
+    a = {k: v.clone() if v is not None else None for k, v in a.items()}
+    r2 = env.reset()
+    b = env.rollout(90)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        assert torch.equal(r1[k], r2[k]) and torch.equal(a[k], b[k]), k
+    env.close()
+
+
+def test_calls_out_of_order_and_bad_arguments():
+    nx = nxmod()
+    env = nx.Env(O.EMPTY, 5, 4, seed=0, autotune=False)
+    with pytest.raises(nx.NavixError) as ei:
+        env.rollout(3)  # before nx_reset
+    assert ei.value.status == nx.NX_E_STATE
+    env.reset()
+    out = env.alloc_out(3)
+    s = env.out_struct(out, 3)
+    with pytest.raises(nx.NavixError) as ei:
+        nx.nx_rollout(env.h, 3, 7, None, s)  # unknown action source
+    assert ei.value.status == nx.NX_E_INVAL
+    with pytest.raises(nx.NavixError) as ei:
+        nx.nx_rollout(env.h, 3, nx.NX_ACT_BUFFER, None, s)  # buffered actions without a buffer
+    assert ei.value.status == nx.NX_E_INVAL
+    with pytest.raises(nx.NavixError) as ei:
+        nx.nx_rollout(env.h, -1, nx.NX_ACT_RANDOM, None, s)
+    assert ei.value.status == nx.NX_E_INVAL
+    fake_rgb = torch.empty(16, dtype=torch.uint8, device="cuda")
+    s.obs_rgb = fake_rgb.data_ptr()
+    with pytest.raises(nx.NavixError) as ei:
+        nx.nx_rollout(env.h, 3, nx.NX_ACT_RANDOM, None, s)  # RGB was not enabled at creation
+    assert ei.value.status == nx.NX_E_INVAL
+    s.obs_rgb = None
+    s.obs_full = fake_rgb.data_ptr()
+    s.full_side = 3
+    with pytest.raises(nx.NavixError) as ei:
+        nx.nx_rollout(env.h, 3, nx.NX_ACT_RANDOM, None, s)  # full views narrower than the grid
+    assert ei.value.status == nx.NX_E_INVAL
+    assert nx.nx_rollout(env.h, 0, nx.NX_ACT_RANDOM, None, None) == 0  # zero steps is a no-op
+    assert env.sync(timeout_s=10.0) == 0
+    env.close()
+
+
+def test_corrupt_snapshots_are_rejected():
+    nx = nxmod()
+    env = nx.Env(O.DOORKEY, 6, 5, seed=1, autotune=False)
+    env.reset()
+    env.rollout(20)
+    good = env.state_bytes()
+    before = env.state_bytes()
+
+    def corrupt(fn):
+        b = bytearray(good)
+        fn(b)
+        with pytest.raises(nx.NavixError) as ei:
+            env.set_state(bytes(b))
+        assert ei.value.status == nx.NX_E_INVAL
+
+    corrupt(lambda b: b.__setitem__(0, ord("X")))               # magic
+    corrupt(lambda b: b.__setitem__(8, 9))                      # env count
+    corrupt(lambda b: b.__setitem__(64 + 0, 200))               # agent x outside the grid
+    corrupt(lambda b: b.__setitem__(64 + 2, 7))                 # direction
+    corrupt(lambda b: b.__setitem__(64 + 5 * 32 + 3 * 36, 77))  # a grid cell's entity code
+    with pytest.raises(nx.NavixError):
+        env.set_state(good[:100])                                # too short
+    assert env.state_bytes() == before                           # nothing was applied
+    env.set_state(good)
+    env.close()
+
+
+def test_snapshot_of_one_context_rejected_by_another_shape():
+    nx = nxmod()
+    a = nx.Env(O.DOORKEY, 6, 5, seed=1, autotune=False)
+    b = nx.Env(O.DOORKEY, 7, 5, seed=1, autotune=False)
+    a.reset()
+    b.reset()
+    with pytest.raises(nx.NavixError):
+        b.set_state(a.state_bytes())
+    a.close()
+    b.close()
