@@ -65,8 +65,8 @@ enum {
     NX_LAVA_CROSSING = 6, NX_SIMPLE_CROSSING = 7
 };
 #define NX_N_FAMILIES 8
-/* observation bit flags (Table 4) */
-enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2 };
+/* observation bit flags (Table 4): RGB and RGB_FULL need the sprite atlas */
+enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2, NX_OBS_RGB_FULL = 4 };
 /* action sources */
 enum { NX_ACT_BUFFER = 0, NX_ACT_RANDOM = 1 };
 /* reward functions: Markovian (Section 3.2.1, Table 5) or MiniGrid's Eq. 1 */
@@ -81,8 +81,8 @@ enum { NX_STAGE_AUTO = 0, NX_STAGE_FULL = 1, NX_STAGE_HALF = 2 };
 #define NX_VIEW 7
 #define NX_OBS_SYM_BYTES 147        /* 7 x 7 x 3 */
 #define NX_OBS_RGB_BYTES 150528     /* 224 x 224 x 3 */
-#define NX_ATLAS_TILES 397
-#define NX_ATLAS_BYTES (397 * 3072) /* 397 tiles of 32 x 32 x 3 */
+#define NX_ATLAS_TILES 401
+#define NX_ATLAS_BYTES (401 * 3072) /* 401 tiles of 32 x 32 x 3 */
 #define NX_AGENT_BYTES 32
 #define NX_MAX_BALLS 4
 
@@ -108,7 +108,7 @@ typedef struct {
     int32_t group_lanes;      /* lanes per env, 1/2/4/8/16/32; 0 = chosen by the library */
     int32_t envs_per_cta;     /* envs per thread block; 0 = chosen by the library */
     int32_t staging;          /* NX_STAGE_*; 0 = chosen by the library (used with group_lanes) */
-    const uint8_t* atlas;     /* host sprite atlas, NX_ATLAS_BYTES (required with NX_OBS_RGB) */
+    const uint8_t* atlas;     /* host sprite atlas, NX_ATLAS_BYTES (required with NX_OBS_RGB / _RGB_FULL) */
     /* optional device allocator (e.g. a framework's caching allocator); NULL: cudaMallocAsync */
     void* (*alloc)(size_t bytes, void* user);
     void (*free)(void* ptr, void* user);
@@ -133,7 +133,10 @@ typedef struct {
  * [.., full_side, full_side] (categorical: entity codes, the agent 10), both
  * zero beyond an env's grid; obs_cat_fp [.., 7, 7] (categorical_first_person:
  * the entity bytes of obs_sym).  full_side must be at least the largest grid
- * size (0: the largest grid size). */
+ * size (0: the largest grid size).  obs_rgb_full [.., 32 full_side,
+ * 32 full_side, 3] (rgb: every cell's sprite, the agent drawn facing its
+ * direction; needs NX_OBS_RGB_FULL at creation and full_side equal to the
+ * largest grid size). */
 typedef struct {
     uint8_t* obs_sym;
     uint8_t* obs_rgb;
@@ -145,6 +148,7 @@ typedef struct {
     uint8_t* obs_full;
     uint8_t* obs_cat;
     uint8_t* obs_cat_fp;
+    uint8_t* obs_rgb_full;
 } nx_out;
 
 /* Launch shape in use (after autotuning). */

@@ -105,6 +105,8 @@ def lib():
             L.orc_obs_cat.argtypes = [P(OrcEnv), u8p, ctypes.c_int32]
             L.orc_obs_cat_fp.argtypes = [P(OrcEnv), u8p]
             L.orc_batch_obs_full.argtypes = [ctypes.c_void_p, u8p, u8p, u8p, ctypes.c_int32]
+            L.orc_obs_rgb_full.argtypes = [P(OrcEnv), u8p, u8p, ctypes.c_int32]
+            L.orc_batch_obs_rgb_full.argtypes = [ctypes.c_void_p, u8p, u8p, ctypes.c_int32]
             L.orc_batch_gstep.argtypes = [ctypes.c_void_p]
             L.orc_batch_gstep.restype = ctypes.c_uint32
             _lib = L
@@ -300,12 +302,21 @@ class Batch:
                                  _ptr(cfp, ctypes.c_uint8), side)
         return full, cat, cfp
 
-    def rollout_full(self, T, side, actions=None):
-        """T steps with every output, including the fully observable views."""
+    def rgb_full(self, atlas, side):
+        img = np.zeros((self.n, 32 * side, 32 * side, 3), np.uint8)
+        at = np.ascontiguousarray(atlas, np.uint8).reshape(-1)
+        lib().orc_batch_obs_rgb_full(self.h, _ptr(at, ctypes.c_uint8), _ptr(img, ctypes.c_uint8), side)
+        return img
+
+    def rollout_full(self, T, side, actions=None, atlas=None):
+        """T steps with every output, including the fully observable views
+        (and the full RGB view when an atlas is given)."""
         outs = []
         for t in range(T):
             o = self.step(None if actions is None else actions[t])
             o["obs_full"], o["obs_cat"], o["obs_cat_fp"] = self.full_views(side)
+            if atlas is not None:
+                o["obs_rgb_full"] = self.rgb_full(atlas, side)
             outs.append(o)
         return {k: np.stack([o[k] for o in outs]) for k in outs[0] if outs[0][k] is not None}
 

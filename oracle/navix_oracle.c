@@ -742,6 +742,32 @@ void orc_obs_cat(const orc_env* e, uint8_t* cat, int32_t side)
         }
 }
 
+void orc_obs_rgb_full(const orc_env* e, const uint8_t* atlas, uint8_t* img, int32_t side)
+{
+    uint8_t* full = (uint8_t*)malloc((size_t)side * side * 3);
+    if (!full) return;
+    orc_obs_full(e, full, side);
+    const size_t row_bytes = (size_t)side * ORC_TILE * 3;
+    for (int y = 0; y < side; y++)
+        for (int x = 0; x < side; x++) {
+            const uint8_t* f = full + ((size_t)y * side + x) * 3;
+            int tile;
+            if (x >= e->width || y >= e->height)
+                tile = 0;
+            else if (f[0] == ORC_AGENT)
+                tile = 397 + f[2];
+            else
+                tile = 1 + 18 * f[0] + 3 * f[1] + f[2];
+            const uint8_t* src = atlas + (size_t)tile * ORC_TILE_BYTES;
+            for (int ty = 0; ty < ORC_TILE; ty++)
+                for (int tx = 0; tx < ORC_TILE; tx++)
+                    for (int c = 0; c < 3; c++)
+                        img[(size_t)(y * ORC_TILE + ty) * row_bytes + (size_t)(x * ORC_TILE + tx) * 3 + c] =
+                            src[(ty * ORC_TILE + tx) * 3 + c];
+        }
+    free(full);
+}
+
 /* categorical_first_person (Table 4): the entity codes of the egocentric view */
 void orc_obs_cat_fp(const orc_env* e, uint8_t cat[ORC_VIEW * ORC_VIEW])
 {
@@ -865,4 +891,10 @@ void orc_batch_obs_full(orc_batch* b, uint8_t* full, uint8_t* cat, uint8_t* cat_
         if (cat) orc_obs_cat(e, cat + (size_t)i * side * side, side);
         if (cat_fp) orc_obs_cat_fp(e, cat_fp + (size_t)i * ORC_VIEW * ORC_VIEW);
     }
+}
+
+void orc_batch_obs_rgb_full(orc_batch* b, const uint8_t* atlas, uint8_t* img, int32_t side)
+{
+    const size_t per = (size_t)side * ORC_TILE * side * ORC_TILE * 3;
+    for (int32_t i = 0; i < b->n; i++) orc_obs_rgb_full(&b->envs[i], atlas, img + (size_t)i * per, side);
 }

@@ -98,6 +98,10 @@ int32_t orc_tile_index(int32_t visible, int32_t agent_cell, int32_t ent, int32_t
 void orc_obs_full(const orc_env* e, uint8_t* full, int32_t side);
 void orc_obs_cat(const orc_env* e, uint8_t* cat, int32_t side);
 void orc_obs_cat_fp(const orc_env* e, uint8_t cat[ORC_VIEW * ORC_VIEW]);
+/* rgb (Table 4): the whole grid as 32-px sprites, [32 side][32 side][3]; a
+ * cell (e, c, s) uses tile 1 + 18 e + 3 c + s, the agent's cell tile
+ * 397 + direction, cells beyond the grid tile 0. */
+void orc_obs_rgb_full(const orc_env* e, const uint8_t* atlas, uint8_t* img, int32_t side);
 void orc_obs_rgb(const orc_env* e, const uint8_t* atlas, uint8_t* img);
 
 /* hand-built states for the worked sequences */
@@ -130,6 +134,7 @@ uint32_t orc_batch_gstep(const orc_batch* b);
 /* the current fully observable views of every env ([n, side, side, 3],
  * [n, side, side], [n, 7, 7]; any may be NULL) */
 void orc_batch_obs_full(orc_batch* b, uint8_t* full, uint8_t* cat, uint8_t* cat_fp, int32_t side);
+void orc_batch_obs_rgb_full(orc_batch* b, const uint8_t* atlas, uint8_t* img, int32_t side);
 
 #ifdef __cplusplus
 }

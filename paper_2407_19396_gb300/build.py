@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnavixgb.so")
-SOURCES = ["nx_kernels.cu", "nx_capi.cu", "nx_static.cu", "nx_server.cu"]
+SOURCES = ["nx_kernels.cu", "nx_kernels_full.cu", "nx_capi.cu", "nx_static.cu", "nx_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

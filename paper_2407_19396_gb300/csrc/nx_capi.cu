@@ -210,8 +210,10 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
         o = *opts;
     else
         nx_options_default(&o);
-    if (o.obs_flags & ~(uint32_t)(NX_OBS_SYM | NX_OBS_RGB)) return nx_fail(nullptr, NX_E_INVAL, "unknown obs flag");
-    if ((o.obs_flags & NX_OBS_RGB) && !o.atlas) return nx_fail(nullptr, NX_E_INVAL, "NX_OBS_RGB needs opts.atlas");
+    if (o.obs_flags & ~(uint32_t)(NX_OBS_SYM | NX_OBS_RGB | NX_OBS_RGB_FULL))
+        return nx_fail(nullptr, NX_E_INVAL, "unknown obs flag");
+    if ((o.obs_flags & (NX_OBS_RGB | NX_OBS_RGB_FULL)) && !o.atlas)
+        return nx_fail(nullptr, NX_E_INVAL, "NX_OBS_RGB / NX_OBS_RGB_FULL need opts.atlas");
     if (o.steps_per_launch <= 0) o.steps_per_launch = 128;
     if (o.steps_per_launch > 1024) return nx_fail(nullptr, NX_E_INVAL, "steps_per_launch must be <= 1024");
     if (o.reward_mode != NX_REWARD_MARKOV && o.reward_mode != NX_REWARD_MINIGRID)
@@ -236,7 +238,8 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
     env->stream = (cudaStream_t)stream;
     env->n_envs = (int)descs.size();
     env->descs = std::move(descs);
-    env->rgb = (o.obs_flags & NX_OBS_RGB) != 0;
+    env->rgb = (o.obs_flags & (NX_OBS_RGB | NX_OBS_RGB_FULL)) != 0;
+    env->rgb_full = (o.obs_flags & NX_OBS_RGB_FULL) != 0;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&env->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -307,9 +310,10 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
     env->req_host.key_base = o.env_index_base;
 
     // default launch shape (replaced by the autotuner when enabled)
-    nx_launch_shape s{8, 32, env->rgb ? 1 : 0, 1};
+    nx_launch_shape s{8, 32, env->rgb ? 1 : 0, 1, env->rgb_full ? env->max_side : 0};
     if (o.group_lanes)
-        s = nx_launch_shape{o.group_lanes, o.envs_per_cta, env->rgb ? 1 : 0, o.staging == NX_STAGE_HALF ? 2 : 1};
+        s = nx_launch_shape{o.group_lanes, o.envs_per_cta, env->rgb ? 1 : 0, o.staging == NX_STAGE_HALF ? 2 : 1,
+                            env->rgb_full ? env->max_side : 0};
     nx_status st = nx_apply_shape(env, s);
     if (st != NX_OK) {
         std::string m = env->last_error;
@@ -371,6 +375,7 @@ nx_status nx_apply_shape(nx_env* env, const nx_launch_shape& s)
     // the host vectors must outlive the asynchronous copies from pageable memory
     NX_CK(env, cudaStreamSynchronize(env->stream), "work list upload");
     env->shape = s;
+    env->per_sm_full = 0;  // recomputed for the new shape on first use
     env->n_items = (int)items.size();
     env->fam_begin = fam_begin;
     env->grid_ctas = std::min(env->n_items, per_sm * env->sm_count);
@@ -402,6 +407,7 @@ nx_kparams nx_params(const nx_env* env, int launch_steps, int reset_all)
     p.envs_per_cta = env->shape.envs_per_cta;
     p.reset_all = reset_all;
     p.phases = env->shape.phases;
+    p.rgb_full_side = env->shape.rgb_full_side;
     return p;
 }
 
@@ -422,19 +428,41 @@ static nx_status prof_mark(nx_env* env, bool begin)
     return NX_OK;
 }
 
-static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st)
+// Launch shape and grid of a call: the plain instantiation, or (full) the
+// one that also writes the fully observable views.
+static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid)
 {
+    *s = env->shape;
+    *grid = env->grid_ctas;
+    if (!full) return NX_OK;
+    s->full = true;
+    if (env->per_sm_full <= 0) {
+        int err = 0;
+        env->per_sm_full = nx_kernel_max_ctas(*s, env->cell_stride, &err);
+        if (err) return nx_cuda_fail(env, err, "occupancy query");
+        if (env->per_sm_full < 1) return nx_fail(env, NX_E_INVAL, "launch shape does not fit on an SM");
+    }
+    *grid = std::min(env->n_items, env->per_sm_full * env->sm_count);
+    return NX_OK;
+}
+
+static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full)
+{
+    nx_launch_shape s;
+    int grid = 0;
+    nx_status ss = shape_for(env, full, &s, &grid);
+    if (ss != NX_OK) return ss;
     nx_kparams p = nx_params(env, steps, 0);
-    NX_CK(env, nx_launch_step_kernel(env->shape, p, env->grid_ctas, st), "step kernel launch");
+    NX_CK(env, nx_launch_step_kernel(s, p, grid, st), "step kernel launch");
     NX_CK(env, nx_launch_advance(env->d_req, 1, st), "advance launch");
     return NX_OK;
 }
 
 // A direct (uncaptured) chunk launch on the context stream, counted and timed.
-static nx_status launch_chunk_direct(nx_env* env, int steps)
+static nx_status launch_chunk_direct(nx_env* env, int steps, bool full)
 {
     nx_status st = prof_mark(env, true);
-    if (st == NX_OK) st = launch_chunk(env, steps, env->stream);
+    if (st == NX_OK) st = launch_chunk(env, steps, env->stream, full);
     if (st == NX_OK) st = prof_mark(env, false);
     env->n_step_launches += 1;
     env->n_all_launches += 2;
@@ -444,17 +472,24 @@ static nx_status launch_chunk_direct(nx_env* env, int steps)
 // Replays (capturing on first use) the graph {step kernel of `steps` steps;
 // counter advance}.  The graph reads every per-call argument from the
 // device-side request record, so one graph serves every call.
-static nx_status launch_chunk_graph(nx_env* env, int steps)
+static nx_status launch_chunk_graph(nx_env* env, int steps, bool full)
 {
     nx_graph* g = nullptr;
     for (auto& c : env->graphs)
-        if (c.steps == steps) g = &c;
+        if (c.steps == steps && c.full == full) g = &c;
     if (!g) {
         nx_graph ng;
         ng.steps = steps;
+        ng.full = full;
+        if (full) {  // the occupancy query sets a kernel attribute: keep it out of the capture
+            nx_launch_shape s;
+            int grid = 0;
+            nx_status ss = shape_for(env, true, &s, &grid);
+            if (ss != NX_OK) return ss;
+        }
         cudaGraph_t graph = nullptr;
         NX_CK(env, cudaStreamBeginCapture(env->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        nx_status st = launch_chunk(env, steps, env->capture_stream);
+        nx_status st = launch_chunk(env, steps, env->capture_stream, full);
         cudaError_t e = cudaStreamEndCapture(env->capture_stream, &graph);
         if (st != NX_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -498,8 +533,14 @@ static nx_req call_req(const nx_env* env, int steps, int act_mode, const int8_t*
     r.obs_full = out ? out->obs_full : nullptr;
     r.obs_cat = out ? out->obs_cat : nullptr;
     r.obs_cat_fp = out ? out->obs_cat_fp : nullptr;
+    r.obs_rgb_full = (out && env->rgb_full) ? out->obs_rgb_full : nullptr;
     r.full_side = (out && out->full_side > 0) ? out->full_side : env->max_side;
     return r;
+}
+
+static bool wants_full(const nx_out* out)
+{
+    return out && (out->obs_full || out->obs_cat || out->obs_cat_fp || out->obs_rgb_full);
 }
 
 static nx_status check_out(nx_env* env, const nx_out* out)
@@ -508,6 +549,10 @@ static nx_status check_out(nx_env* env, const nx_out* out)
     if (out && (out->obs_full || out->obs_cat) && out->full_side > 0 && out->full_side < env->max_side)
         return nx_fail(env, NX_E_INVAL, "full_side is smaller than the largest grid");
     if (out && (out->full_side < 0 || out->full_side > 255)) return nx_fail(env, NX_E_INVAL, "full_side must be 0..255");
+    if (out && out->obs_rgb_full && !env->rgb_full)
+        return nx_fail(env, NX_E_INVAL, "obs_rgb_full given but NX_OBS_RGB_FULL was not enabled");
+    if (out && out->obs_rgb_full && out->full_side != 0 && out->full_side != env->max_side)
+        return nx_fail(env, NX_E_INVAL, "obs_rgb_full needs full_side equal to the largest grid size");
     return NX_OK;
 }
 
@@ -519,7 +564,11 @@ nx_status nx_reset(nx_env* env, const nx_out* out)
     nx_req r = call_req(env, 0, NX_ACT_RANDOM, nullptr, out);
     NX_CK(env, nx_launch_configure(env->d_req, r, 1, env->stream), "configure");
     nx_kparams p = nx_params(env, 0, 1);
-    NX_CK(env, nx_launch_step_kernel(env->shape, p, env->grid_ctas, env->stream), "reset kernel launch");
+    nx_launch_shape sh;
+    int grid = 0;
+    st = shape_for(env, wants_full(out), &sh, &grid);
+    if (st != NX_OK) return st;
+    NX_CK(env, nx_launch_step_kernel(sh, p, grid, env->stream), "reset kernel launch");
     env->n_all_launches += 2;
     env->was_reset = true;
     return NX_OK;
@@ -541,6 +590,11 @@ static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, co
         if (st != NX_OK) return st;
     }
     const int C = per_family ? 1 : env->opt.steps_per_launch;
+    const bool full = wants_full(traj);
+    nx_launch_shape fsh;
+    int fgrid = 0;
+    st = shape_for(env, full, &fsh, &fgrid);
+    if (st != NX_OK) return st;
     nx_req r = call_req(env, C, act_mode, d_actions, traj);
     NX_CK(env, nx_launch_configure(env->d_req, r, 0, env->stream), "configure");
     env->n_all_launches += 1;
@@ -552,10 +606,10 @@ static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, co
                 nx_kparams p = nx_params(env, 1, 0);
                 p.items = env->d_items_fam + b;
                 p.n_items = e - b;
-                const int grid = std::min(e - b, env->per_sm * env->sm_count);
+                const int grid = std::min(e - b, (full ? env->per_sm_full : env->per_sm) * env->sm_count);
                 st = prof_mark(env, true);
                 if (st != NX_OK) return st;
-                NX_CK(env, nx_launch_step_kernel(env->shape, p, grid, env->stream), "per-family launch");
+                NX_CK(env, nx_launch_step_kernel(fsh, p, grid, env->stream), "per-family launch");
                 st = prof_mark(env, false);
                 if (st != NX_OK) return st;
                 env->n_step_launches += 1;
@@ -566,15 +620,15 @@ static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, co
         }
         return NX_OK;
     }
-    const int full = n_steps / C, rem = n_steps % C;
-    for (int k = 0; k < full; ++k) {
-        st = launch_chunk_graph(env, C);
+    const int nfull = n_steps / C, rem = n_steps % C;
+    for (int k = 0; k < nfull; ++k) {
+        st = launch_chunk_graph(env, C, full);
         if (st != NX_OK) return st;
     }
     if (rem) {
         NX_CK(env, nx_launch_set_steps(env->d_req, rem, env->stream), "set steps");
         env->n_all_launches += 1;
-        st = launch_chunk_direct(env, rem);
+        st = launch_chunk_direct(env, rem, full);
         if (st != NX_OK) return st;
     }
     return NX_OK;
@@ -609,7 +663,7 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
     if (act_mode == NX_ACT_BUFFER && !h_actions) return nx_fail(env, NX_E_INVAL, "NX_ACT_BUFFER needs actions");
     nx_status st = check_out(env, h);
     if (st != NX_OK) return st;
-    if (h && (h->obs_full || h->obs_cat || h->obs_cat_fp))
+    if (h && (h->obs_full || h->obs_cat || h->obs_cat_fp || h->obs_rgb_full))
         return nx_fail(env, NX_E_INVAL, "the fully observable views are device outputs only");
     if (n_steps == 0) return NX_OK;
     if (!env->tuned) {
@@ -669,7 +723,7 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
         nx_req r = call_req(env, Ck, act_mode, dact, &d);
         NX_CK(env, nx_launch_configure(env->d_req, r, 0, env->stream), "configure");
         env->n_all_launches += 1;
-        st = launch_chunk_direct(env, Ck);
+        st = launch_chunk_direct(env, Ck, false);
         if (st != NX_OK) return st;
         NX_CK(env, cudaEventRecord(env->ev_done[b], env->stream), "record");
         NX_CK(env, cudaStreamWaitEvent(env->copy_stream, env->ev_done[b], 0), "wait compute");
@@ -737,7 +791,7 @@ nx_status nx_autotune(nx_env* env)
     for (int G : lanes)
         for (int th : threads)
             for (int ph = 1; ph <= 2; ++ph) {
-            nx_launch_shape s{G, th / G, env->rgb ? 1 : 0, ph};
+            nx_launch_shape s{G, th / G, env->rgb ? 1 : 0, ph, env->rgb_full ? env->max_side : 0};
             if (!nx_shape_supported(s)) continue;
             if (nx_apply_shape(env, s) != NX_OK) {
                 cudaGetLastError();

@@ -432,7 +432,7 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
 // The same generator run by a whole warp for one env, kept out of line: it is
 // the rare path of narrow groups, and inlining it would raise the register
 // allocation of the whole step kernel.
-__device__ __noinline__ bool reset_layout_warp(uint8_t* g, int S, int family, int n_balls, int variant, uint64_t seed,
+static __device__ __noinline__ bool reset_layout_warp(uint8_t* g, int S, int family, int n_balls, int variant, uint64_t seed,
                                                uint32_t key_env, uint32_t episode, AgentReg& a)
 {
     return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, family, n_balls, variant, seed, key_env, episode, a);
@@ -482,6 +482,7 @@ __device__ __forceinline__ uint64_t occlusion(uint64_t tmask)
 {
     uint64_t vis = 0;
     uint32_t seed = 1u << 3;
+    // once a row lights nothing ahead, every farther row stays unseen
 #pragma unroll 1
     for (int j = 6; j >= 0 && seed != 0u; --j) {
         const uint32_t t = (uint32_t)(tmask >> (7 * j)) & 0x7Fu;
@@ -609,8 +610,9 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int c = k * G + grp.lane;
+            const int vy = (c * 37) >> 8, vx = c - 7 * vy;  // c / 7 and c % 7 for c < 56
             uint32_t cd = C_WALL;
-            if (c < 49) cd = view_code(g, v, a, c % 7, c / 7);
+            if (c < 49) cd = view_code(g, v, a, vx, vy);
             code[k] = cd;
             const uint32_t bits = grp.ballot(c < 49 && !(cd & OPAQUE));
             tmask |= (uint64_t)bits << (k * G);

@@ -71,6 +71,7 @@ struct NX_ALIGN16 nx_req {
     uint8_t* obs_full;    // [depth, n_envs, full_side, full_side, 3] (may be NULL)
     uint8_t* obs_cat;     // [depth, n_envs, full_side, full_side]
     uint8_t* obs_cat_fp;  // [depth, n_envs, 7, 7]
+    uint8_t* obs_rgb_full;  // [depth, n_envs, 32 full_side, 32 full_side, 3]
     int32_t full_side;
     int32_t pad2;
 };
@@ -96,6 +97,8 @@ struct nx_kparams {
     int32_t envs_per_cta;
     int32_t reset_all;     // 1: start every env at episode 0 and emit its observation (no steps)
     int32_t phases;        // symbolic staging parts per step (1 or 2)
+    int32_t rgb_full_side; // side of the smem full-view tile buffer (0: none)
+    int32_t pad;
 };
 
 // Host-side launch helpers implemented in nx_kernels.cu.
@@ -104,6 +107,8 @@ struct nx_launch_shape {
     int envs_per_cta;
     int rgb;
     int phases = 1;  // the symbolic outputs of a CTA are staged and stored in this many parts (1 or 2)
+    int rgb_full_side = 0;  // reserve smem for full-view RGB tile ids of this grid side
+    bool full = false;      // the instantiation that writes the fully observable views
 };
 int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride);
 int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err);  // resident CTAs on the device
@@ -112,3 +117,7 @@ int nx_launch_advance(nx_req* reqs, int n_reqs, void* stream);
 int nx_launch_configure(nx_req* r, const nx_req& v, int gstep_mode, void* stream);
 int nx_launch_set_steps(nx_req* r, int steps, void* stream);
 int nx_shape_supported(const nx_launch_shape& s);
+#ifdef __CUDACC__
+int nx_kernel_max_ctas_full(const nx_launch_shape& s, int threads, int smem, int* err);
+int nx_launch_step_kernel_full(const nx_launch_shape& s, const nx_kparams& p, int grid, int smem, cudaStream_t st);
+#endif

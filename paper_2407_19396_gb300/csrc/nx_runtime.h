@@ -10,6 +10,7 @@
 
 struct nx_graph {
     int steps = 0;
+    bool full = false;
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -25,6 +26,7 @@ struct nx_env {
     int n_envs = 0;
     int n_families = 0;
     bool rgb = false;
+    bool rgb_full = false;
     std::vector<nx_desc> descs;
     std::vector<uint32_t> grid_offset;
     size_t grid_pool = 0;
@@ -53,6 +55,7 @@ struct nx_env {
     int n_items = 0;
     int grid_ctas = 0;
     int per_sm = 0;
+    int per_sm_full = 0;  // resident CTAs of the instantiation with the fully observable views
     std::vector<int> fam_begin;
     bool tuned = false;
     std::vector<nx_tune_entry> tune_log;

@@ -1,0 +1,498 @@
+// nx_step.cuh -- the fused, persistent MiniGrid step kernel of libnavixgb
+// (template; instantiated by nx_kernels.cu without and by nx_kernels_full.cu
+// with the fully observable views, so the hot path carries none of their code).
+//
+// One CTA processes one work item at a time (a run of <= envs_per_cta
+// consecutive envs that share a descriptor); a group of G lanes owns one env.
+// Per item: the envs' three int8 planes are packed into one byte per cell in
+// shared memory, then `steps` steps run back to back with the grid and the
+// agent state on chip, and the state is written back at the end.  Per step:
+//   draws (Philox, lanes in parallel) -> autoreset or transition + rules +
+//   reward/termination/truncation -> egocentric view + occlusion (ballots
+//   build the 49-bit transparency mask, a 32 KB table gives each row) ->
+//   147 symbolic bytes staged per warp in smem (co-aligned with the
+//   destination) and stored with 16-byte vectors -> with RGB, one CTA barrier
+//   and 16-byte streaming stores of the atlas tiles (L2-resident atlas).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "navixgb.h"
+#include "nx_device.cuh"
+#include "nx_internal.h"
+
+namespace nxk {
+
+using namespace nxd;
+
+constexpr int kMaxThreads = 256;
+
+__host__ __device__ __forceinline__ int align16(int v) { return (v + 15) & ~15; }
+
+// 64-bit FNV-style running digest over 32-bit words
+__device__ __forceinline__ uint64_t digest_word(uint64_t h, uint32_t w) { return (h ^ (uint64_t)w) * 0x100000001B3ull; }
+
+// Intervention (rotate / forward / pickup / drop / toggle / done), the
+// Dynamic-Obstacles transition, then time, truncation, reward and termination.
+template <int G>
+__device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int family, int max_steps, AgentReg& a,
+                                         int action, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
+                                         float& reward, int& term, int& trunc, nx_ctl* ctl)
+{
+    // transition system: each ball, in index order, moves to a uniformly drawn
+    // empty cell of its 8-neighbourhood that is not the agent's cell
+    if (family == NX_DYNOBS) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (b >= a.nb) break;
+            uint32_t cand = 0;
+            int j = 0;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (dx == 0 && dy == 0) continue;
+                    const int x = a.bx[b] + dx, y = a.by[b] + dy;
+                    const bool f = (unsigned)x < (unsigned)S && (unsigned)y < (unsigned)S && g[y * S + x] == C_EMPTY &&
+                                   !(x == a.x && y == a.y);
+                    cand |= (f ? 1u : 0u) << j;
+                    ++j;
+                }
+            const int cnt = __popc(cand);
+            if (cnt > 0) {
+                int k = bounded(d[b], (uint32_t)cnt);
+                uint32_t c = cand;
+                for (int i = 0; i < k; ++i) c &= c - 1u;
+                const int jj = __ffs(c) - 1;          // 0..7 over the 8 neighbours, row-major
+                const int o = jj < 4 ? jj : jj + 1;   // position in the 3x3 block, skipping the centre
+                const int nx = a.bx[b] + (o % 3) - 1, ny = a.by[b] + (o / 3) - 1;
+                grp.sync();
+                if (grp.lane == 0) {
+                    g[a.by[b] * S + a.bx[b]] = (uint8_t)C_EMPTY;
+                    g[ny * S + nx] = (uint8_t)C_BALL_BLUE;
+                }
+                grp.sync();
+                a.bx[b] = nx;
+                a.by[b] = ny;
+            }
+        }
+    }
+    // intervention system, written as selects so that envs of one warp taking
+    // different actions do not serialise on branches
+    const int n_act = family == NX_DYNOBS ? 3 : 7;
+    if ((unsigned)action > 6u) {
+        if (!a.invalid && grp.lane == 0) atomicOr(&ctl->flags, (unsigned)NX_FLAG_INVALID_ACTION);
+        a.invalid = 1;
+    }
+    const bool acts = (unsigned)action < (unsigned)n_act;  // out-of-range and restricted actions are no-ops
+    const int fxd = (a.dir == 0) - (a.dir == 2), fyd = (a.dir == 1) - (a.dir == 3);
+    const int fx = a.x + fxd, fy = a.y + fyd;
+    const bool in = (unsigned)fx < (unsigned)S && (unsigned)fy < (unsigned)S;
+    const int fi = fy * S + fx;
+    const uint32_t fc = in ? (uint32_t)g[fi] : (uint32_t)C_WALL;
+    const uint32_t fk = cell_kind(fc), fcol = cell_col(fc);
+    const bool is_fwd = acts && action == 2;
+    const bool hit = is_fwd && family == NX_DYNOBS && fk == K_BALL;
+    const bool move = is_fwd && !hit && walkable(fc);
+    const bool pick = acts && action == 3 && a.carry == 0u && (fk == K_KEY || fk == K_BALL);
+    const bool drop = acts && action == 4 && a.carry != 0u && in && fc == C_EMPTY;
+    const bool tog = acts && action == 5;
+    const bool unlock = tog && fk == K_DOOR_LOCKED && a.carry != 0u && cell_kind(a.carry) == K_KEY &&
+                        cell_col(a.carry) == fcol;
+    const bool open_ = tog && fk == K_DOOR_CLOSED;
+    const bool close_ = tog && fk == K_DOOR_OPEN;
+    const int goal = move && fk == K_GOAL, lava = move && fk == K_LAVA;
+    a.dir = (a.dir + ((acts && action == 1) ? 1 : 0) + ((acts && action == 0) ? 3 : 0)) & 3;
+    a.x = move ? fx : a.x;
+    a.y = move ? fy : a.y;
+    const bool write = pick || drop || unlock || open_ || close_;
+    const uint32_t wcode = pick ? (uint32_t)C_EMPTY
+                                : drop ? a.carry : (close_ ? make_code(K_DOOR_CLOSED, fcol) : make_code(K_DOOR_OPEN, fcol));
+    a.carry = pick ? fc : (drop ? 0u : a.carry);
+    if (write) {
+        grp.sync();
+        if (grp.lane == 0) g[fi] = (uint8_t)wcode;
+        grp.sync();
+    }
+    // time and truncation; reward and termination on the goal / lava / hit events
+    a.t += 1;
+    trunc = a.t >= max_steps;
+    reward = 0.0f;
+    term = 0;
+    if (goal) {
+        reward = reward_mode == NX_REWARD_MINIGRID
+                     ? __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(0.9f, (float)a.t), (float)max_steps))
+                     : 1.0f;
+        term = 1;
+    } else if (lava) {
+        reward = lava_reward;
+        term = 1;
+    } else if (hit) {
+        reward = -1.0f;
+        term = 1;
+    }
+    a.done = term || trunc;
+}
+
+// CTA-wide copy from shared to global memory; src and dst are congruent
+// modulo 16, the body moves in 16-byte vectors.
+__device__ __forceinline__ void coop_copy(uint8_t* dst, const uint8_t* src, int nbytes, int tid, int nthreads)
+{
+    const int head = min(nbytes, (int)((16u - ((uint32_t)(uintptr_t)dst & 15u)) & 15u));
+    const int body = (nbytes - head) & ~15;
+    const int tail = nbytes - head - body;
+    for (int i = tid; i < head; i += nthreads) dst[i] = src[i];
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + head);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + head);
+    for (int i = tid; i < body / 16; i += nthreads) d4[i] = s4[i];
+    for (int i = tid; i < tail; i += nthreads) dst[head + body + i] = src[head + body + i];
+}
+
+// Writes n envs' 224x224x3 images: 16-byte chunk r of an image is pixel row
+// r / 42, bytes 16 (r % 42) .. of it, i.e. view column (r % 42) / 6, part
+// (r % 42) % 6 of that tile's 96-byte row.
+__device__ __forceinline__ void coop_rgb(uint8_t* dst, const uint16_t* tiles, const uint8_t* atlas, int n, int tid,
+                                         int nthreads)
+{
+    constexpr int kChunks = NX_OBS_RGB_BYTES / 16;  // 9408
+    for (int e = 0; e < n; ++e) {
+        uint4* d4 = reinterpret_cast<uint4*>(dst + (size_t)e * NX_OBS_RGB_BYTES);
+        const uint16_t* te = tiles + e * 49;
+#pragma unroll 4
+        for (int r = tid; r < kChunks; r += nthreads) {
+            const int row = r / 42, c16 = r - row * 42;
+            const int vx = c16 / 6, part = c16 - vx * 6;
+            const int vy = row >> 5, ty = row & 31;
+            const uint32_t tile = te[vy * 7 + vx];
+            const uint4* src = reinterpret_cast<const uint4*>(atlas + (size_t)tile * 3072u + ty * 96 + part * 16);
+            __stcs(d4 + r, __ldg(src));
+        }
+    }
+}
+
+// The same for the fully observable RGB view: F x F tiles per env.
+__device__ __forceinline__ void coop_rgb_full(uint8_t* dst, const uint16_t* tiles, const uint8_t* atlas, int n, int F,
+                                              int tid, int nthreads)
+{
+    const int per_row = 6 * F;  // 16-byte chunks per pixel row
+    const int chunks = 32 * F * per_row;
+    for (int e = 0; e < n; ++e) {
+        uint4* d4 = reinterpret_cast<uint4*>(dst + (size_t)e * chunks * 16);
+        const uint16_t* te = tiles + e * F * F;
+#pragma unroll 4
+        for (int r = tid; r < chunks; r += nthreads) {
+            const int row = r / per_row, c16 = r - row * per_row;
+            const int tx = c16 / 6, part = c16 - tx * 6;
+            const int ty = row >> 5, py = row & 31;
+            const uint32_t tile = te[ty * F + tx];
+            const uint4* src = reinterpret_cast<const uint4*>(atlas + (size_t)tile * 3072u + py * 96 + part * 16);
+            __stcs(d4 + r, __ldg(src));
+        }
+    }
+}
+
+template <int G, bool RGB, bool FULL>
+__global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparams p)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t s_dec[256];  // cell code -> observation triple
+    const int E = p.envs_per_cta;
+    const int phases = p.phases > 1 ? 2 : 1;
+    const int tid = threadIdx.x, nthreads = blockDim.x, lane32 = tid & 31, warp = tid >> 5;
+    constexpr int epw = 32 / G;                         // envs per warp
+    const int whalf = (epw + phases - 1) / phases;      // envs staged per part
+    const int wbytes = align16(whalf * NX_OBS_SYM_BYTES + 16);
+    const int wenv0 = warp * epw;                       // the warp's first env slot
+    uint8_t* sgrid = smem;
+    uint8_t* wstage = smem + E * p.cell_stride + warp * wbytes;
+    uint16_t* stiles = reinterpret_cast<uint16_t*>(smem + E * p.cell_stride + (nthreads >> 5) * wbytes);
+    const int FR = p.rgb_full_side;  // full-view RGB tile buffer: E x FR x FR ids after the egocentric ones
+    uint16_t* sfull = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(stiles) + align16(E * 49 * 2));
+    const int gi = tid / G;
+    const Grp<G> grp(tid);
+    uint8_t* mygrid = sgrid + gi * p.cell_stride;
+    for (int i = tid; i < 256; i += nthreads) s_dec[i] = cell_triple((uint32_t)i);
+
+    for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
+        const nx_item item = p.items[it];
+        const nx_req* rq = p.reqs + item.req;
+        const uint64_t seed = rq->seed;
+        const uint32_t gstep0 = rq->gstep, call0 = rq->call_step;
+        const int steps = p.reset_all ? 0 : min(rq->steps, p.launch_steps);
+        const int depth = rq->depth > 0 ? rq->depth : 1;
+        const uint32_t nreq = rq->n_envs;
+        const int act_mode = rq->act_mode;
+        const int8_t* actions = rq->actions;
+        uint8_t* obs_sym = rq->obs_sym;
+        uint8_t* obs_rgb = RGB ? rq->obs_rgb : nullptr;
+        float* out_reward = rq->reward;
+        uint8_t* out_term = rq->terminated;
+        uint8_t* out_trunc = rq->truncated;
+        const uint32_t reward_mode = rq->reward_mode;
+        const float lava_reward = rq->lava_reward;
+        const int n_balls = rq->n_balls;
+        float* returns = rq->returns;
+        uint64_t* digest = rq->digest;
+        uint32_t* episodes = rq->episodes;
+        // the fully observable views exist only in the FULL instantiations
+        uint8_t* obs_full = FULL ? rq->obs_full : nullptr;
+        uint8_t* obs_cat = FULL ? rq->obs_cat : nullptr;
+        uint8_t* obs_cat_fp = FULL ? rq->obs_cat_fp : nullptr;
+        uint8_t* obs_rgb_full = (FULL && RGB && FR > 0) ? rq->obs_rgb_full : nullptr;
+        const int F = FULL ? rq->full_side : 0;
+
+        const int n = (int)item.n_envs, S = item.size, HW = S * S, family = item.family, variant = (int)item.variant;
+        const int max_steps = item.max_steps;
+        const bool active = gi < n;
+        const uint32_t local = item.local_begin + (uint32_t)gi;
+        const uint32_t key = rq->key_base + local;  // env index in the draw counters
+        const uint32_t env = item.env_begin + (uint32_t)gi;
+        AgentReg a;
+        float ret = 0.0f;
+        uint64_t dig = 0;
+        uint32_t eps = 0;
+
+        if (!p.reset_all) {
+            const uint8_t* src = p.grids + item.grid_offset;
+            for (int i = tid; i < n * HW; i += nthreads) {
+                const int e = i / HW, c = i - e * HW;
+                const uint8_t* b = src + (size_t)e * 3 * HW;
+                sgrid[e * p.cell_stride + c] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
+            }
+            if (active) load_agent(p.agents + env, a);
+        }
+        if (active) {
+            if (returns) ret = returns[local];
+            if (digest) dig = digest[local];
+            if (episodes) eps = episodes[local];
+        }
+        __syncthreads();
+
+        // steps == 0 with reset_all: one emission of the episode-0 start state
+        const int emissions = p.reset_all ? 1 : steps;
+        const bool rnd = act_mode == NX_ACT_RANDOM;
+        const uint32_t n_act = family == NX_DYNOBS ? 3u : 7u;
+        uint32_t slot = call0 % (uint32_t)depth;
+        uint32_t my_draw = 0;  // G > 1: this lane's random-action draw for step s0 + lane
+        for (int s = 0; s < emissions; ++s) {
+            const size_t row0 = (size_t)slot * nreq + item.local_begin;
+            uint8_t* sym_dst = obs_sym ? obs_sym + row0 * NX_OBS_SYM_BYTES : nullptr;
+            ViewOut<G> vo;
+            float reward = 0.0f;
+            int term = 0, trunc = 0;
+            if (G > 1 && rnd && (s % G) == 0) {
+                // the random actions of the next G steps depend only on the step
+                // counter, so the group's lanes draw them in parallel
+                my_draw = (s + grp.lane < steps) ? draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)(s + grp.lane),
+                                                        PURPOSE_ACTION, 0u)
+                                                 : 0u;
+            }
+            // Episode starts (every env on a reset launch; autoreset after a
+            // terminal or truncated step).  Groups of 8 or more lanes lay out
+            // their own env; narrower groups hand every starting env of the
+            // warp to all 32 lanes, one env after another, so one resetting env
+            // never runs its layout generation serially while the rest of its
+            // warp waits.
+            const bool starts = active && (p.reset_all || a.done);
+            if constexpr (G >= 8) {
+                if (starts) {
+                    const int inv = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
+                    if (!reset_layout(grp, mygrid, S, family, n_balls, variant, seed, key,
+                                      p.reset_all ? 0u : a.episode + 1u, a))
+                        if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    a.invalid = inv;
+                }
+            } else {
+                unsigned lead = __ballot_sync(0xFFFFFFFFu, starts && grp.lane == 0);
+                while (lead) {
+                    const int L = __ffs(lead) - 1;
+                    lead &= lead - 1u;
+                    const uint32_t ep = __shfl_sync(0xFFFFFFFFu, p.reset_all ? 0u : a.episode + 1u, L);
+                    const uint32_t k = __shfl_sync(0xFFFFFFFFu, key, L);
+                    const int owner = ((tid & ~31) + L) / G;  // group (env slot) of lane L
+                    AgentReg na;
+                    const bool ok =
+                        reset_layout_warp(sgrid + owner * p.cell_stride, S, family, n_balls, variant, seed, k, ep, na);
+                    if (!ok && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    if (gi == owner) {
+                        na.invalid = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
+                        a = na;
+                    }
+                }
+                __syncwarp();
+            }
+            if (active) {
+                if (starts) {
+                    // the new episode's start: reward padding 0, the action is ignored
+                } else {
+                    uint32_t d[8];
+                    if (family == NX_DYNOBS) {
+                        const uint32_t episode = a.episode, t = (uint32_t)a.t;
+                        group_draws(grp, a.nb, d, [&](uint32_t k) -> uint32_t {
+                            return draw(seed, key, episode, t, PURPOSE_BALL, k);
+                        });
+                    }
+                    int action;
+                    if (rnd) {
+                        const uint32_t x = G > 1 ? grp.shfl(my_draw, s % G)
+                                                 : draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)s, PURPOSE_ACTION, 0u);
+                        action = bounded(x, n_act);
+                    } else {
+                        action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
+                    }
+                    env_step(grp, mygrid, S, family, max_steps, a, action, d, reward_mode, lava_reward, reward, term,
+                             trunc, p.ctl);
+                }
+                grp.sync();
+                render_view(grp, mygrid, S, a, s_dec, vo, RGB && obs_rgb ? stiles + gi * 49 : nullptr);
+                if (FULL && (obs_full || obs_cat || obs_rgb_full)) {
+                    // fully observable views: every cell's triple, the agent's
+                    // cell holding (agent, red, direction), zero beyond the grid;
+                    // for the RGB view, the cell's tile (the agent facing its
+                    // direction) goes to shared memory for the gather below
+                    const size_t row = (size_t)slot * nreq + local;
+                    uint8_t* fo = obs_full ? obs_full + row * (size_t)(F * F * 3) : nullptr;
+                    uint8_t* co = obs_cat ? obs_cat + row * (size_t)(F * F) : nullptr;
+                    for (int c = grp.lane; c < F * F; c += G) {
+                        const int y = c / F, x = c - y * F;
+                        uint32_t tri = 0;
+                        const bool agent_cell = x == a.x && y == a.y;
+                        if (x < S && y < S) tri = agent_cell ? (10u | ((uint32_t)a.dir << 16)) : s_dec[mygrid[y * S + x]];
+                        if (fo) {
+                            fo[3 * c] = (uint8_t)tri;
+                            fo[3 * c + 1] = (uint8_t)(tri >> 8);
+                            fo[3 * c + 2] = (uint8_t)(tri >> 16);
+                        }
+                        if (co) co[c] = (uint8_t)tri;
+                        if (RGB && obs_rgb_full && c < FR * FR) {
+                            uint32_t tile = 0;
+                            if (x < S && y < S)
+                                tile = agent_cell ? 397u + (uint32_t)a.dir
+                                                  : 1u + 18u * (tri & 0xFFu) + 3u * ((tri >> 8) & 0xFFu) + (tri >> 16);
+                            sfull[gi * FR * FR + c] = (uint16_t)(tile < (uint32_t)NX_ATLAS_TILES ? tile : 0u);
+                        }
+                    }
+                }
+                if (grp.lane == 0) {
+                    const size_t o = (size_t)slot * nreq + local;
+                    if (out_reward) out_reward[o] = reward;
+                    if (out_term) out_term[o] = (uint8_t)term;
+                    if (out_trunc) out_trunc[o] = (uint8_t)trunc;
+                    ret += reward;
+                    eps += (uint32_t)(term || trunc);
+                }
+            }
+            // Each warp stages the symbolic outputs of its own envs (placed at
+            // the same address modulo 16 as their destination) and stores them
+            // with 16-byte vectors, in `phases` parts; warps never wait for
+            // each other here.
+            for (int ph = 0; ph < phases; ++ph) {
+                const int lo = wenv0 + ph * whalf, hi = min(n, min(wenv0 + epw, lo + whalf));
+                uint8_t* dst = sym_dst ? sym_dst + (size_t)lo * NX_OBS_SYM_BYTES : nullptr;
+                uint8_t* stage = wstage + ((uint32_t)(uintptr_t)dst & 15u);
+                if (active && gi >= lo && gi < hi) {
+                    uint8_t* my_sym = stage + (gi - lo) * NX_OBS_SYM_BYTES;
+                    write_view(grp, vo, my_sym);
+                    if (FULL && obs_cat_fp) {
+                        // categorical_first_person: the entity bytes of the staged view
+                        grp.sync();
+                        uint8_t* cf = obs_cat_fp + ((size_t)slot * nreq + local) * 49;
+                        for (int c = grp.lane; c < 49; c += G) cf[c] = my_sym[3 * c];
+                    }
+                    if (digest) {
+                        grp.sync();
+                        if (grp.lane == 0) {
+#pragma unroll 7
+                            for (int c = 0; c < 49; ++c)
+                                dig = digest_word(dig, (uint32_t)my_sym[3 * c] | ((uint32_t)my_sym[3 * c + 1] << 8) |
+                                                           ((uint32_t)my_sym[3 * c + 2] << 16));
+                            dig = digest_word(dig, __float_as_uint(reward));
+                            dig = digest_word(dig, (uint32_t)term | ((uint32_t)trunc << 8));
+                        }
+                    }
+                }
+                __syncwarp();
+                if (dst && hi > lo) coop_copy(dst, stage, (hi - lo) * NX_OBS_SYM_BYTES, lane32, 32);
+                __syncwarp();
+            }
+            if (RGB && (obs_rgb || obs_rgb_full)) {
+                __syncthreads();
+                if (obs_rgb) coop_rgb(obs_rgb + row0 * NX_OBS_RGB_BYTES, stiles, p.atlas, n, tid, nthreads);
+                if (FULL && obs_rgb_full)
+                    coop_rgb_full(obs_rgb_full + row0 * (size_t)(3072 * FR * FR), sfull, p.atlas, n, FR, tid, nthreads);
+                __syncthreads();
+            }
+            slot = slot + 1u == (uint32_t)depth ? 0u : slot + 1u;
+        }
+
+        // write the state back (the grids are written back by every thread of
+        // the CTA, so all groups' last smem writes must be visible first)
+        __syncthreads();
+        if (active && grp.lane == 0) {
+            store_agent(p.agents + env, a, item, item.grid_offset + (uint32_t)(gi * 3 * HW));
+            if (returns) returns[local] = ret;
+            if (digest) digest[local] = dig;
+            if (episodes) episodes[local] = eps;
+        }
+        {
+            uint8_t* dst = p.grids + item.grid_offset;
+            for (int i = tid; i < n * HW; i += nthreads) {
+                const int e = i / HW, c = i - e * HW;
+                const uint32_t code = sgrid[e * p.cell_stride + c];
+                uint8_t* b = dst + (size_t)e * 3 * HW;
+                b[c] = (uint8_t)cell_ent(code);
+                b[HW + c] = (uint8_t)cell_col(code);
+                b[2 * HW + c] = (uint8_t)cell_st(code);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+
+// The dynamic shared-memory limit is raised once per shape by
+// nx_kernel_max_ctas (outside any stream capture); launches only launch.
+template <int G, bool RGB, bool FULL>
+int launch_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
+{
+    nx_step_kernel<G, RGB, FULL><<<grid, p.envs_per_cta * G, smem, st>>>(p);
+    return (int)cudaGetLastError();
+}
+
+// The dynamic shared-memory limit is a per-kernel attribute shared by every
+// context in the process, so it is always raised to the most the device
+// allows next to the kernel's static shared memory (never lowered to one
+// context's need).
+template <int G, bool RGB, bool FULL>
+int occupancy_t(int threads, int smem, int* err)
+{
+    auto k = nx_step_kernel<G, RGB, FULL>;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+    const int dyn_max = e == cudaSuccess ? optin - (int)fa.sharedSizeBytes : 0;  // static + dynamic <= opt-in limit
+    if (e == cudaSuccess && smem > dyn_max) {
+        *err = 0;
+        return 0;
+    }
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    int blocks = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, threads, smem);
+    *err = (int)e;
+    return blocks;
+}
+
+#define NX_DISPATCH_G(G_, RGB_, FULL_, FN, ...)                                                   \
+    switch (G_) {                                                                                 \
+    case 1: return RGB_ ? FN<1, true, FULL_>(__VA_ARGS__) : FN<1, false, FULL_>(__VA_ARGS__);    \
+    case 2: return RGB_ ? FN<2, true, FULL_>(__VA_ARGS__) : FN<2, false, FULL_>(__VA_ARGS__);    \
+    case 4: return RGB_ ? FN<4, true, FULL_>(__VA_ARGS__) : FN<4, false, FULL_>(__VA_ARGS__);    \
+    case 8: return RGB_ ? FN<8, true, FULL_>(__VA_ARGS__) : FN<8, false, FULL_>(__VA_ARGS__);    \
+    case 16: return RGB_ ? FN<16, true, FULL_>(__VA_ARGS__) : FN<16, false, FULL_>(__VA_ARGS__); \
+    case 32: return RGB_ ? FN<32, true, FULL_>(__VA_ARGS__) : FN<32, false, FULL_>(__VA_ARGS__); \
+    default: return -1;                                                                           \
+    }
+
+}  // namespace nxk

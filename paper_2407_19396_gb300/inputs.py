@@ -14,7 +14,9 @@ Sprite atlas convention (an interface between the atlas and the renderers):
   (ent, col, st), ent in 0..10, col in 0..5, st in 0..2, highlighted;
 * tile ``199 + 18*ent + 3*col + st``: the agent's own cell, i.e. the agent
   (a red triangle pointing up, since the view is egocentric) drawn over what
-  it carries, highlighted.
+  it carries, highlighted;
+* tile ``397 + dir``: the agent facing east, south, west or north on an empty
+  cell, highlighted (the fully observable RGB view).
 
 Every tile carries its own index in its bottom-right pixel, so no two tiles
 are equal.
@@ -30,7 +32,8 @@ import numpy as np
 TILE = 32
 TILE_BYTES = TILE * TILE * 3
 N_ENT, N_COL, N_ST = 11, 6, 3
-ATLAS_TILES = 1 + 2 * N_ENT * N_COL * N_ST  # 397
+EGO_TILES = 1 + 2 * N_ENT * N_COL * N_ST  # 397
+ATLAS_TILES = EGO_TILES + 4  # 401
 
 # colour palette (index -> RGB); codes follow the colour table of the cell encoding
 COLOURS = np.array(
@@ -138,8 +141,11 @@ def _draw_object(img: np.ndarray, ent: int, col: int, st: int) -> None:
     # ent 0 (unseen) and 1 (empty): nothing drawn
 
 
-def _draw_agent(img: np.ndarray) -> None:
-    _blend(img, _coverage(_triangle((0.5, 0.12), (0.85, 0.88), (0.15, 0.88))), [255, 0, 0])
+def _draw_agent(img: np.ndarray, direction: int = 3) -> None:
+    """A red triangle pointing east (0), south (1), west (2) or north (3)."""
+    tri = {3: ((0.5, 0.12), (0.85, 0.88), (0.15, 0.88)), 1: ((0.5, 0.88), (0.15, 0.12), (0.85, 0.12)),
+           0: ((0.88, 0.5), (0.12, 0.15), (0.12, 0.85)), 2: ((0.12, 0.5), (0.88, 0.85), (0.88, 0.15))}[direction]
+    _blend(img, _coverage(_triangle(*tri)), [255, 0, 0])
 
 
 def _highlight(img: np.ndarray) -> np.ndarray:
@@ -147,9 +153,12 @@ def _highlight(img: np.ndarray) -> np.ndarray:
 
 
 def tile_params(t: int):
-    """Inverse of the atlas convention: tile index -> (visible, agent_cell, ent, col, st)."""
+    """Inverse of the atlas convention: tile index -> (visible, agent_cell, ent, col, st);
+    for the directional agent tiles, agent_cell is 2 and st holds the direction."""
     if t == 0:
         return 0, 0, 0, 0, 0
+    if t >= EGO_TILES:
+        return 1, 2, 10, 0, t - EGO_TILES
     agent = 1 if t >= 199 else 0
     r = t - (199 if agent else 1)
     return 1, agent, r // 18, (r % 18) // 3, r % 3
@@ -161,7 +170,10 @@ def make_atlas() -> np.ndarray:
     for t in range(ATLAS_TILES):
         visible, agent, ent, col, st = tile_params(t)
         img = _base_tile()
-        if visible:
+        if visible and agent == 2:
+            _draw_agent(img, st)
+            img = _highlight(img)
+        elif visible:
             _draw_object(img, ent, col, st)
             if agent:
                 _draw_agent(img)

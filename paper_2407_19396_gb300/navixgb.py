@@ -21,12 +21,12 @@ LIB_PATH = os.path.join(HERE, "_build", "libnavixgb.so")
 NX_OK, NX_PENDING = 0, 1
 NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET, NX_E_STATE = -1, -2, -3, -4, -5, -6, -7
 NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS, NX_EMPTY_RANDOM, NX_LAVA_CROSSING, NX_SIMPLE_CROSSING = range(8)
-NX_OBS_SYM, NX_OBS_RGB = 1, 2
+NX_OBS_SYM, NX_OBS_RGB, NX_OBS_RGB_FULL = 1, 2, 4
 NX_ACT_BUFFER, NX_ACT_RANDOM = 0, 1
 NX_REWARD_MARKOV, NX_REWARD_MINIGRID = 0, 1
 NX_STAGE_AUTO, NX_STAGE_FULL, NX_STAGE_HALF = 0, 1, 2
 OBS_SYM_BYTES, OBS_RGB_BYTES = 147, 150528
-ATLAS_BYTES = 397 * 3072
+ATLAS_BYTES = 401 * 3072
 AGENT_BYTES = 32
 FAMILIES = {"empty": NX_EMPTY, "doorkey": NX_DOORKEY, "fourrooms": NX_FOURROOMS, "lavagap": NX_LAVAGAP,
             "dynobs": NX_DYNOBS, "empty_random": NX_EMPTY_RANDOM, "lava_crossing": NX_LAVA_CROSSING,
@@ -53,9 +53,10 @@ class nx_out(ctypes.Structure):
     _fields_ = [("obs_sym", ctypes.c_void_p), ("obs_rgb", ctypes.c_void_p), ("reward", ctypes.c_void_p),
                 ("terminated", ctypes.c_void_p), ("truncated", ctypes.c_void_p), ("depth", ctypes.c_int32),
                 ("full_side", ctypes.c_int32), ("obs_full", ctypes.c_void_p), ("obs_cat", ctypes.c_void_p),
-                ("obs_cat_fp", ctypes.c_void_p)]
+                ("obs_cat_fp", ctypes.c_void_p), ("obs_rgb_full", ctypes.c_void_p)]
 
-OUT_KEYS = ("obs_sym", "obs_rgb", "reward", "terminated", "truncated", "obs_full", "obs_cat", "obs_cat_fp")
+OUT_KEYS = ("obs_sym", "obs_rgb", "reward", "terminated", "truncated", "obs_full", "obs_cat", "obs_cat_fp",
+            "obs_rgb_full")
 
 
 class nx_info(ctypes.Structure):
@@ -310,7 +311,7 @@ class Env:
     def __init__(self, family=NX_EMPTY, size=5, n_envs=1, seed=0, *, descs=None, obs_sym=True, obs_rgb=False,
                  atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
                  autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, variant=0,
-                 obs_full=False, obs_cat=False, obs_cat_fp=False, torch_allocator=True):
+                 obs_full=False, obs_cat=False, obs_cat_fp=False, obs_rgb_full=False, torch_allocator=True):
         import torch
 
         self.torch = torch
@@ -319,7 +320,8 @@ class Env:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = torch.cuda.current_stream(self.device)
         o = nx_options_default()
-        o.obs_flags = (NX_OBS_SYM if obs_sym else 0) | (NX_OBS_RGB if obs_rgb else 0)
+        o.obs_flags = (NX_OBS_SYM if obs_sym else 0) | (NX_OBS_RGB if obs_rgb else 0) | \
+            (NX_OBS_RGB_FULL if obs_rgb_full else 0)
         o.reward_mode = reward_mode
         o.lava_reward = lava_reward
         o.n_balls = n_balls
@@ -331,7 +333,7 @@ class Env:
         o.env_index_base = env_index_base
         o.variant = variant
         self._atlas = None
-        if obs_rgb:
+        if obs_rgb or obs_rgb_full:
             if atlas is None:
                 from . import inputs
                 atlas = inputs.atlas()
@@ -353,6 +355,7 @@ class Env:
         self.opts = o
         self.obs_sym, self.obs_rgb = obs_sym, obs_rgb
         self.want_full, self.want_cat, self.want_cat_fp = obs_full, obs_cat, obs_cat_fp
+        self.want_rgb_full = obs_rgb_full
         if descs is None:
             self.n = int(n_envs)
             self.side = int(size)
@@ -390,6 +393,8 @@ class Env:
         o["obs_full"] = torch.empty(lead + (n, F, F, 3), dtype=torch.uint8, device=self.device) if self.want_full else None
         o["obs_cat"] = torch.empty(lead + (n, F, F), dtype=torch.uint8, device=self.device) if self.want_cat else None
         o["obs_cat_fp"] = torch.empty(lead + (n, 7, 7), dtype=torch.uint8, device=self.device) if self.want_cat_fp else None
+        o["obs_rgb_full"] = (torch.empty(lead + (n, 32 * F, 32 * F, 3), dtype=torch.uint8, device=self.device)
+                             if self.want_rgb_full else None)
         return o
 
     def out_struct(self, o, depth=1):

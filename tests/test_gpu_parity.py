@@ -369,6 +369,23 @@ def test_fully_observable_views(lanes, envs, staging):
     env.close()
 
 
+@pytest.mark.parametrize("lanes,envs", [(1, 64), (16, 8), (32, 4)])
+def test_full_rgb_view(lanes, envs):
+    nx = nxmod()
+    atlas = inputs.atlas()
+    descs = mixed_descs(20, [(O.DOORKEY, 8), (O.FOURROOMS, 11), (O.LAVA_CROSSING, 9, 0, 2)])
+    env = nx.Env(descs=descs, seed=61, group_lanes=lanes, envs_per_cta=envs, autotune=False, steps_per_launch=16,
+                 obs_rgb=True, obs_rgb_full=True, atlas=atlas)
+    r = env.reset()
+    out = env.rollout(30)
+    ob = oracle_batch_for(descs, 61)
+    ob.reset()
+    np.testing.assert_array_equal(to_np(r["obs_rgb_full"]), ob.rgb_full(atlas, 11))
+    oo = ob.rollout_full(30, 11, atlas=atlas)
+    assert_outputs_equal(out, oo, keys=("obs_sym", "reward", "obs_rgb_full"), what=f"full rgb G={lanes}")
+    env.close()
+
+
 def test_variant_validation():
     nx = nxmod()
     assert nx.nx_max_variant(O.LAVA_CROSSING, 9) == O.max_variant(O.LAVA_CROSSING, 9) == 6

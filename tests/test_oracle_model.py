@@ -320,3 +320,31 @@ def test_full_views_agree_with_the_grid_and_the_egocentric_view(family, size, se
                         assert tuple(v) == tuple(f[wy, wx])
                     else:
                         assert tuple(v) == (2, 5, 0)
+
+
+def test_full_rgb_view_assembles_the_atlas_tiles_of_the_full_symbolic_view(atlas):
+    """rgb (Table 4): each 32x32 block of the oracle's full RGB view is the atlas
+    tile the atlas module assigns to that cell's triple (the agent's cell: the
+    agent facing its direction; beyond the grid: the unseen tile)."""
+    from paper_2407_19396_gb300 import inputs
+
+    index = {atlas[k].tobytes(): k for k in range(atlas.shape[0])}
+    b = O.Batch([O.DOORKEY, O.SIMPLE_CROSSING, O.DYNOBS], [8, 9, 6], seed=5, variants=[0, 2, 0])
+    b.reset()
+    for t in range(40):
+        b.step()
+        full, _, _ = b.full_views(10)
+        img = b.rgb_full(atlas, 10)
+        for i in range(3):
+            for y in range(10):
+                for x in range(10):
+                    blk = img[i, 32 * y:32 * y + 32, 32 * x:32 * x + 32]
+                    tile = index[np.ascontiguousarray(blk).tobytes()]
+                    vis, agent, e, c, s = inputs.tile_params(tile)
+                    f = tuple(int(v) for v in full[i, y, x])
+                    if f == (0, 0, 0):
+                        assert tile == 0
+                    elif f[0] == 10:
+                        assert agent == 2 and s == f[2]
+                    else:
+                        assert vis == 1 and agent == 0 and (e, c, s) == f
