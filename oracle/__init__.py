@@ -27,9 +27,11 @@ RGB_BYTES = 224 * 224 * 3
 TILE_BYTES = 32 * 32 * 3
 MAX_CELLS = 19 * 19
 
-EMPTY, DOORKEY, FOURROOMS, LAVAGAP, DYNOBS, EMPTY_RANDOM, LAVA_CROSSING, SIMPLE_CROSSING = range(8)
+EMPTY, DOORKEY, FOURROOMS, LAVAGAP, DYNOBS, EMPTY_RANDOM, LAVA_CROSSING, SIMPLE_CROSSING, GOTODOOR = range(9)
+NO_MISSION = 255
 FAMILY_NAMES = {"empty": EMPTY, "doorkey": DOORKEY, "fourrooms": FOURROOMS, "lavagap": LAVAGAP, "dynobs": DYNOBS,
-                "empty_random": EMPTY_RANDOM, "lava_crossing": LAVA_CROSSING, "simple_crossing": SIMPLE_CROSSING}
+                "empty_random": EMPTY_RANDOM, "lava_crossing": LAVA_CROSSING, "simple_crossing": SIMPLE_CROSSING,
+                "gotodoor": GOTODOOR}
 
 
 def build(force: bool = False) -> str:
@@ -53,7 +55,7 @@ class OrcEnv(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("env_index", ctypes.c_uint32), ("episode", ctypes.c_uint32),
         ("t", ctypes.c_int32), ("ax", ctypes.c_int32), ("ay", ctypes.c_int32), ("dir", ctypes.c_int32),
         ("carry_ent", ctypes.c_int32), ("carry_col", ctypes.c_int32), ("done", ctypes.c_int32),
-        ("invalid_action", ctypes.c_int32),
+        ("mission", ctypes.c_int32), ("invalid_action", ctypes.c_int32),
         ("ball_x", ctypes.c_int32 * 4), ("ball_y", ctypes.c_int32 * 4),
         ("ent", ctypes.c_uint8 * MAX_CELLS), ("col", ctypes.c_uint8 * MAX_CELLS), ("st", ctypes.c_uint8 * MAX_CELLS),
     ]
@@ -224,6 +226,7 @@ def env_state(s: OrcEnv) -> dict:
         "family": s.family, "height": H, "width": W, "max_steps": s.max_steps,
         "x": s.ax, "y": s.ay, "dir": s.dir, "carry_ent": s.carry_ent, "carry_col": s.carry_col,
         "done": s.done, "t": s.t, "episode": s.episode, "n_balls": s.n_balls, "variant": s.variant,
+        "mission": s.mission,
         "ball_x": list(s.ball_x)[: s.n_balls], "ball_y": list(s.ball_y)[: s.n_balls],
         "invalid": s.invalid_action,
         "ent": bytes(s.ent)[:n], "col": bytes(s.col)[:n], "st": bytes(s.st)[:n],
@@ -308,6 +311,9 @@ class Batch:
         lib().orc_batch_obs_rgb_full(self.h, _ptr(at, ctypes.c_uint8), _ptr(img, ctypes.c_uint8), side)
         return img
 
+    def missions(self):
+        return np.array([self.env(i).mission for i in range(self.n)], np.uint8)
+
     def rollout_full(self, T, side, actions=None, atlas=None):
         """T steps with every output, including the fully observable views
         (and the full RGB view when an atlas is given)."""
@@ -315,6 +321,7 @@ class Batch:
         for t in range(T):
             o = self.step(None if actions is None else actions[t])
             o["obs_full"], o["obs_cat"], o["obs_cat_fp"] = self.full_views(side)
+            o["mission"] = self.missions()
             if atlas is not None:
                 o["obs_rgb_full"] = self.rgb_full(atlas, side)
             outs.append(o)

@@ -142,9 +142,10 @@ int32_t orc_default_max_steps(int32_t family, int32_t size)
 {
     /* reading R17: Empty 4S^2 (100 at S = 5), DoorKey 10S^2 (640 at S = 8),
      * FourRooms 100, LavaGap 4S^2, Dynamic-Obstacles 4S^2; Empty-Random and the
-     * crossings 4S^2 */
+     * crossings 4S^2; GoToDoor 5S^2 */
     switch (family) {
     case ORC_DOORKEY: return 10 * size * size;
+    case ORC_GOTODOOR: return 5 * size * size;
     case ORC_FOURROOMS: return 100;
     default: return 4 * size * size;
     }
@@ -408,12 +409,52 @@ static void layout_crossing(orc_env* e)
     orc_set_agent(e, 1, 1, 0, 0, 0);
 }
 
+/* L8 GoToDoor-S: four closed doors, one on each side of the border (never a
+ * corner), in four distinct colours; the mission is one of them; the agent
+ * on a drawn empty interior cell facing a drawn direction.  Draws, in order:
+ * the door positions along the top, bottom, left and right walls (each in
+ * 1..S-2), the colours by a partial Fisher-Yates shuffle of the six (step i
+ * swaps colour i with colour i + k(d, 6 - i)), the target door k(d, 4), the
+ * agent cell k(d, n) and its direction k(d, 4). */
+static void layout_gotodoor(orc_env* e)
+{
+    int S = e->width;
+    uint32_t k = 0;
+    int px[4], py[4];
+    int p0 = 1 + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(S - 2));
+    px[0] = p0;
+    py[0] = 0;
+    int p1 = 1 + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(S - 2));
+    px[1] = p1;
+    py[1] = S - 1;
+    int p2 = 1 + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(S - 2));
+    px[2] = 0;
+    py[2] = p2;
+    int p3 = 1 + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(S - 2));
+    px[3] = S - 1;
+    py[3] = p3;
+    int colours[6] = {0, 1, 2, 3, 4, 5};
+    for (int i = 0; i < 4; i++) {
+        int j = i + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(6 - i));
+        int t = colours[i];
+        colours[i] = colours[j];
+        colours[j] = t;
+    }
+    for (int i = 0; i < 4; i++) orc_set_cell(e, px[i], py[i], ORC_DOOR, colours[i], ORC_CLOSED);
+    e->mission = colours[(int)orc_bounded(layout_draw(e, k++), 4u)];
+    int n = count_free(e, 1, S - 2, 1, S - 2, -1, -1);
+    int ax, ay;
+    kth_free(e, (int)orc_bounded(layout_draw(e, k++), (uint32_t)n), 1, S - 2, 1, S - 2, -1, -1, &ax, &ay);
+    orc_set_agent(e, ax, ay, (int)orc_bounded(layout_draw(e, k++), 4u), 0, 0);
+}
+
 /* reset(key) of Section 3.2.2: sample a start state for the given episode. */
 void orc_reset(orc_env* e, uint32_t episode)
 {
     e->episode = episode;
     e->t = 0;
     e->done = 0;
+    e->mission = ORC_NO_MISSION;
     e->carry_ent = 0;
     e->carry_col = 0;
     for (int b = 0; b < ORC_MAX_BALLS; b++) {
@@ -434,6 +475,7 @@ void orc_reset(orc_env* e, uint32_t episode)
     case ORC_EMPTY_RANDOM: layout_empty_random(e); break;
     case ORC_LAVA_CROSSING:
     case ORC_SIMPLE_CROSSING: layout_crossing(e); break;
+    case ORC_GOTODOOR: layout_gotodoor(e); break;
     default: break;
     }
 }
@@ -571,7 +613,12 @@ void orc_step(orc_env* e, int32_t action, float* reward, uint8_t* terminated, ui
                 }
             }
         }
-        /* ORC_DONE: no effect */
+        else if (action == ORC_DONE) {
+            /* on_door_done (Tables 5 and 6): in GoToDoor, done while facing a
+             * door of the mission's colour completes the task; elsewhere done
+             * has no effect (reading R21) */
+            if (e->family == ORC_GOTODOOR && fent == ORC_DOOR && fcol == e->mission) goal = 1;
+        }
     }
 
     /* 4. time and truncation (R17) */

@@ -48,8 +48,9 @@ extern "C" {
 
 /* families (variant: the number of rivers for the two crossing families) */
 enum { ORC_EMPTY = 0, ORC_DOORKEY = 1, ORC_FOURROOMS = 2, ORC_LAVAGAP = 3, ORC_DYNOBS = 4, ORC_EMPTY_RANDOM = 5,
-       ORC_LAVA_CROSSING = 6, ORC_SIMPLE_CROSSING = 7 };
-#define ORC_N_FAMILIES 8
+       ORC_LAVA_CROSSING = 6, ORC_SIMPLE_CROSSING = 7, ORC_GOTODOOR = 8 };
+#define ORC_N_FAMILIES 9
+#define ORC_NO_MISSION 255
 /* actions */
 enum { ORC_LEFT = 0, ORC_RIGHT = 1, ORC_FORWARD = 2, ORC_PICKUP = 3, ORC_DROP = 4, ORC_TOGGLE = 5, ORC_DONE = 6 };
 /* entity codes */
@@ -72,6 +73,7 @@ typedef struct orc_env {
     int32_t ax, ay, dir;          /* agent position (x = column, y = row) and direction */
     int32_t carry_ent, carry_col; /* carry_ent == 0: nothing carried */
     int32_t done;                 /* previous call ended the episode: next call resets */
+    int32_t mission;              /* GoToDoor: the colour of the target door; ORC_NO_MISSION otherwise */
     int32_t invalid_action;       /* sticky: an out-of-range action was seen */
     int32_t ball_x[ORC_MAX_BALLS], ball_y[ORC_MAX_BALLS];
     uint8_t ent[ORC_MAX_CELLS], col[ORC_MAX_CELLS], st[ORC_MAX_CELLS]; /* row-major y*W+x */

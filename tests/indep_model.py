@@ -89,8 +89,11 @@ def observe(ent, col, st, ax, ay, d, carry=None):
 STEP = {0: (1, 0), 1: (0, 1), 2: (-1, 0), 3: (0, -1)}
 
 
-def successors(state, W, H, n_actions=6):
-    """Yield (action, next_state, event) with event in {None, 'goal', 'lava'}."""
+def successors(state, W, H, n_actions=6, mission=None):
+    """Yield (action, next_state, event) with event in {None, 'goal', 'lava'}.
+
+    With a mission colour, action 6 (done) facing a door of that colour is
+    the goal event (GoToDoor's on_door_done)."""
     x, y, d, carry, cells = state
     dx, dy = STEP[d]
     fx, fy = x + dx, y + dy
@@ -126,10 +129,13 @@ def successors(state, W, H, n_actions=6):
             c = list(cells)
             c[fy * W + fx] = (4, f[1], new)
             yield 5, (x, y, d, carry, tuple(c)), None
+    # 6: done, facing the mission's door
+    if mission is not None and f[0] == 4 and f[1] == mission:
+        yield 6, state, "goal"
 
 
-def bfs_goal(start, W, H, max_depth=64):
-    """Shortest action sequence to step onto a goal cell (lava ends a path)."""
+def bfs_goal(start, W, H, max_depth=64, mission=None):
+    """Shortest action sequence to a goal event (lava ends a path)."""
     q = deque([start])
     parent = {start: None}
     while q:
@@ -141,7 +147,7 @@ def bfs_goal(start, W, H, max_depth=64):
             p = parent[p][0]
         if depth >= max_depth:
             continue
-        for a, n, ev in successors(s, W, H):
+        for a, n, ev in successors(s, W, H, mission=mission):
             if ev == "goal":
                 plan = [a]
                 p = s

@@ -142,3 +142,116 @@ def test_invalid_variants_rejected():
     with pytest.raises(ValueError):
         O.Env(O.EMPTY, 9, variant=1)
     assert O.max_variant(O.SIMPLE_CROSSING, 11) == 8 and O.max_variant(O.LAVA_CROSSING, 5) == 2
+
+
+# --- GoToDoor-S (Table 8; on_door_done of Tables 5 and 6) ---------------------
+
+def _doors(ent, col, st):
+    S = ent.shape[0]
+    ys, xs = np.nonzero(ent == 4)
+    return [(int(x), int(y), int(col[y, x]), int(st[y, x])) for x, y in zip(xs, ys)]
+
+
+def test_gotodoor_layouts_are_valid():
+    for S in (5, 6, 8, 11, 19):
+        for seed in range(25):
+            e = O.Env(O.GOTODOOR, S, seed=seed, env_index=seed)
+            ent, col, st = e.grid()
+            doors = _doors(ent, col, st)
+            assert len(doors) == 4
+            sides = set()
+            for x, y, c, s in doors:
+                assert s == 1  # closed
+                assert (x in (0, S - 1)) != (y in (0, S - 1))  # on a wall, never a corner
+                sides.add("top" if y == 0 else "bottom" if y == S - 1 else "left" if x == 0 else "right")
+            assert sides == {"top", "bottom", "left", "right"}
+            colours = [c for *_, c, _ in doors]
+            assert len(set(colours)) == 4 and all(0 <= c <= 5 for c in colours)
+            assert e.s.mission in colours
+            # no goal, an empty interior, walls elsewhere on the border
+            assert (ent != 8).all() and (ent[1:S - 1, 1:S - 1] == 1).all()
+            border = np.ones((S, S), bool)
+            border[1:S - 1, 1:S - 1] = False
+            assert ((ent == 2) | (ent == 4))[border].all() and (ent == 2)[border].sum() == 4 * (S - 1) - 4
+            assert 1 <= e.s.ax <= S - 2 and 1 <= e.s.ay <= S - 2 and 0 <= e.s.dir < 4
+            assert e.s.max_steps == 5 * S * S
+
+
+def test_gotodoor_draws_cover_their_ranges():
+    S = 6
+    pos = {k: set() for k in ("top", "bottom", "left", "right")}
+    col_side = set()
+    target_sides, agents, dirs, missions = set(), set(), set(), set()
+    for ep in range(1500):
+        e = O.Env(O.GOTODOOR, S, seed=11)
+        e.reset(ep)
+        ent, col, st = e.grid()
+        for x, y, c, _ in _doors(ent, col, st):
+            side = "top" if y == 0 else "bottom" if y == S - 1 else "left" if x == 0 else "right"
+            pos[side].add(x if side in ("top", "bottom") else y)
+            col_side.add((side, c))
+            if c == e.s.mission:
+                target_sides.add(side)
+        agents.add((e.s.ax, e.s.ay))
+        dirs.add(e.s.dir)
+        missions.add(e.s.mission)
+    assert all(v == set(range(1, S - 1)) for v in pos.values())
+    assert len(col_side) == 24  # every colour on every side
+    assert target_sides == {"top", "bottom", "left", "right"}
+    assert missions == set(range(6)) and dirs == {0, 1, 2, 3} and len(agents) == (S - 2) ** 2
+
+
+def _plan_to_door(env, S):
+    ent, col, st = env.grid()
+    cells = tuple((int(ent[y, x]), int(col[y, x]), int(st[y, x])) for y in range(S) for x in range(S))
+    return M.bfs_goal((env.s.ax, env.s.ay, env.s.dir, None, cells), S, S, max_depth=40, mission=env.s.mission)
+
+
+@pytest.mark.parametrize("S,seed,mode", [(5, 0, 0), (6, 1, 0), (8, 2, 1), (8, 3, 0), (11, 4, 1)])
+def test_gotodoor_done_at_the_mission_door_ends_with_reward(S, seed, mode):
+    env = O.Env(O.GOTODOOR, S, seed=seed, reward_mode=mode)
+    plan = _plan_to_door(env, S)
+    assert plan is not None and plan[-1] == 6
+    T = env.s.max_steps
+    for i, a in enumerate(plan):
+        r, te, tr = env.step(a)
+        if i < len(plan) - 1:
+            assert (r, te) == (0.0, 0)
+    want = 1.0 if mode == 0 else float(np.float32(1.0) - np.float32(np.float32(0.9) * np.float32(len(plan))) / np.float32(T))
+    assert (te, tr) == (1, 0) and r == pytest.approx(want, abs=0) and env.s.t == len(plan)
+    # the next call starts a new episode with reward padding 0
+    assert env.step(2) == (0.0, 0, 0) and env.s.t == 0 and env.s.episode == 1
+
+
+def test_gotodoor_done_elsewhere_does_nothing():
+    S = 7
+    for seed in range(30):
+        env = O.Env(O.GOTODOOR, S, seed=seed)
+        ent, col, st = env.grid()
+        doors = {(x, y): c for x, y, c, _ in _doors(ent, col, st)}
+        # walk straight ahead, saying done at every cell on the way
+        for _ in range(S):
+            fx = env.s.ax + (1, 0, -1, 0)[env.s.dir]
+            fy = env.s.ay + (0, 1, 0, -1)[env.s.dir]
+            facing = doors.get((fx, fy))
+            before = (env.s.ax, env.s.ay, env.s.dir, bytes(env.s.ent))
+            r, te, tr = env.step(6)
+            if facing == env.s.mission:
+                assert (r, te) == (1.0, 1)
+                break
+            assert (r, te, tr) == (0.0, 0, 0)
+            assert (env.s.ax, env.s.ay, env.s.dir, bytes(env.s.ent)) == before
+            env.step(2)
+    # done never rewards in a family without a mission, even facing a door
+    e = O.Env(O.DOORKEY, 5, seed=0)
+    e.set_cell(2, 1, 4, 4, 1)
+    e.set_agent(1, 1, 0)
+    assert e.step(6) == (0.0, 0, 0) and e.s.mission == O.NO_MISSION
+
+
+def test_gotodoor_truncates_at_5_s_squared():
+    S = 5
+    env = O.Env(O.GOTODOOR, S, seed=3)
+    for t in range(1, 5 * S * S + 1):
+        r, te, tr = env.step(0)  # turning never ends the episode
+        assert (r, te) == (0.0, 0) and tr == (t == 5 * S * S)
