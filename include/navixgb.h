@@ -59,12 +59,16 @@ enum {
 };
 
 /* environment families of Table 8; the crossings take their number of
- * rivers as the descriptor's variant (0..nx_max_variant) */
+ * rivers as the descriptor's variant (0..nx_max_variant).  GoToDoor has a
+ * mission (the colour of one of its four doors, nx_out.mission) and ends
+ * with reward 1 when the done action is taken facing that door
+ * (on_door_done, Tables 5 and 6). */
 enum {
     NX_EMPTY = 0, NX_DOORKEY = 1, NX_FOURROOMS = 2, NX_LAVAGAP = 3, NX_DYNOBS = 4, NX_EMPTY_RANDOM = 5,
-    NX_LAVA_CROSSING = 6, NX_SIMPLE_CROSSING = 7
+    NX_LAVA_CROSSING = 6, NX_SIMPLE_CROSSING = 7, NX_GOTODOOR = 8
 };
-#define NX_N_FAMILIES 8
+#define NX_N_FAMILIES 9
+#define NX_NO_MISSION 255  /* the mission byte of a family without one */
 /* observation bit flags (Table 4): RGB and RGB_FULL need the sprite atlas */
 enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2, NX_OBS_RGB_FULL = 4 };
 /* action sources */
@@ -91,7 +95,7 @@ typedef struct nx_server nx_server;
 
 /* One environment's shape: family, square grid side (height == width,
  * 5..19), timeout T (<= 0: the family default: DoorKey 10 S^2, FourRooms
- * 100, the others 4 S^2; at most 65535), and the family's variant (the number
+ * 100, GoToDoor 5 S^2, the others 4 S^2; at most 65535), and the family's variant (the number
  * of rivers of a crossing family, 0 otherwise). */
 typedef struct {
     int32_t family, height, width, max_steps, variant;
@@ -136,7 +140,10 @@ typedef struct {
  * size (0: the largest grid size).  obs_rgb_full [.., 32 full_side,
  * 32 full_side, 3] (rgb: every cell's sprite, the agent drawn facing its
  * direction; needs NX_OBS_RGB_FULL at creation and full_side equal to the
- * largest grid size). */
+ * largest grid size).
+ * mission [..] uint8: the mission of the episode the slot's observation
+ * belongs to (GoToDoor: the target door's colour index; NX_NO_MISSION for
+ * the other families). */
 typedef struct {
     uint8_t* obs_sym;
     uint8_t* obs_rgb;
@@ -149,6 +156,7 @@ typedef struct {
     uint8_t* obs_cat;
     uint8_t* obs_cat_fp;
     uint8_t* obs_rgb_full;
+    uint8_t* mission;
 } nx_out;
 
 /* Launch shape in use (after autotuning). */
@@ -223,7 +231,8 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
  *   [64, 64 + 32 n)        per-env agent blocks, NX_AGENT_BYTES each:
  *       u8 x, y, dir, carry_ent, carry_col, done, invalid, n_balls;
  *       u16 t, max_steps; u32 episode; u8 ball_x[4], ball_y[4];
- *       u8 family, size; u16 reserved; u32 grid_offset
+ *       u8 family, size, mission (NX_NO_MISSION without one), reserved;
+ *       u32 grid_offset
  *   [64 + 32 n, end)       grid pool: for each env at grid_offset, three
  *                          planes of size*size bytes (entity, colour, state),
  *                          row-major y * size + x.

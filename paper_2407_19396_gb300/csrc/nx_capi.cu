@@ -128,6 +128,7 @@ int nx_default_max_steps(int family, int size)
     switch (family) {
     case NX_DOORKEY: return 10 * size * size;
     case NX_FOURROOMS: return 100;
+    case NX_GOTODOOR: return 5 * size * size;
     default: return 4 * size * size;
     }
 }
@@ -142,7 +143,7 @@ int32_t nx_max_variant(int32_t family, int32_t size)
 static nx_status validate_desc(const nx_desc& d, int n_balls, std::string* why)
 {
     if (d.family < NX_EMPTY || d.family >= NX_N_FAMILIES) {
-        *why = "family must be 0..7";
+        *why = "unknown family";
         return NX_E_INVAL;
     }
     if (d.variant < 0 || d.variant > nx_max_variant(d.family, d.height)) {
@@ -534,6 +535,7 @@ static nx_req call_req(const nx_env* env, int steps, int act_mode, const int8_t*
     r.obs_cat = out ? out->obs_cat : nullptr;
     r.obs_cat_fp = out ? out->obs_cat_fp : nullptr;
     r.obs_rgb_full = (out && env->rgb_full) ? out->obs_rgb_full : nullptr;
+    r.mission = out ? out->mission : nullptr;
     r.full_side = (out && out->full_side > 0) ? out->full_side : env->max_side;
     return r;
 }
@@ -673,10 +675,10 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
     const int C = env->opt.steps_per_launch;
     const size_t N = (size_t)env->n_envs;
     const bool want_sym = h && h->obs_sym, want_rgb = h && h->obs_rgb, want_r = h && h->reward,
-               want_te = h && h->terminated, want_tr = h && h->truncated;
+               want_te = h && h->terminated, want_tr = h && h->truncated, want_m = h && h->mission;
     const size_t per_step = N * ((want_sym ? NX_OBS_SYM_BYTES : 0) + (want_rgb ? NX_OBS_RGB_BYTES : 0) +
-                                 (want_r ? 4 : 0) + (want_te ? 1 : 0) + (want_tr ? 1 : 0)) +
-                            (act_mode == NX_ACT_BUFFER ? N : 0) + 256 * 6;
+                                 (want_r ? 4 : 0) + (want_te ? 1 : 0) + (want_tr ? 1 : 0) + (want_m ? 1 : 0)) +
+                            (act_mode == NX_ACT_BUFFER ? N : 0) + 256 * 7;
     const size_t need = per_step * (size_t)C;
     if (need > env->host_chunk_bytes) {
         for (int b = 0; b < 2; ++b) {
@@ -714,6 +716,7 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
         if (want_r) d.reward = (float*)take((size_t)Ck * N * 4);
         if (want_te) d.terminated = take((size_t)Ck * N);
         if (want_tr) d.truncated = take((size_t)Ck * N);
+        if (want_m) d.mission = take((size_t)Ck * N);
         int8_t* dact = nullptr;
         if (act_mode == NX_ACT_BUFFER) {
             dact = (int8_t*)take((size_t)Ck * N);
@@ -742,6 +745,9 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
                                        env->copy_stream), "copy back");
         if (want_tr)
             NX_CK(env, cudaMemcpyAsync(h->truncated + T0 * N, d.truncated, (size_t)Ck * N, cudaMemcpyDeviceToHost,
+                                       env->copy_stream), "copy back");
+        if (want_m)
+            NX_CK(env, cudaMemcpyAsync(h->mission + T0 * N, d.mission, (size_t)Ck * N, cudaMemcpyDeviceToHost,
                                        env->copy_stream), "copy back");
         NX_CK(env, cudaEventRecord(env->ev_copied[b], env->copy_stream), "record");
         used[b] = true;
@@ -885,7 +891,8 @@ nx_status nx_set_state(nx_env* env, const void* host_buf, size_t bytes)
             return nx_fail(env, NX_E_INVAL, "snapshot descriptors differ from this context");
         // every index the kernels derive from the snapshot must stay inside the grid
         bool ok = a.x < S && a.y < S && a.dir < 4 && a.done <= 1 && a.invalid <= 1 && a.n_balls <= NX_MAX_BALLS &&
-                  a.carry_ent <= 10 && a.carry_col <= 5 && (d.family == NX_DYNOBS || a.n_balls == 0);
+                  a.carry_ent <= 10 && a.carry_col <= 5 && (d.family == NX_DYNOBS || a.n_balls == 0) &&
+                  (d.family == NX_GOTODOOR ? a.mission <= 5 : a.mission == NX_NO_MISSION);
         for (int k = 0; ok && k < a.n_balls; ++k) ok = a.ball_x[k] < S && a.ball_y[k] < S;
         const uint8_t* g = pool_b + a.grid_offset;
         for (int c = 0; ok && c < S * S; ++c) ok = g[c] <= 10 && g[S * S + c] <= 5 && g[2 * S * S + c] <= 2;

@@ -199,6 +199,7 @@ struct AgentReg {
     uint32_t carry;  // packed code of the carried object, 0 = nothing
     int done, invalid, t;
     uint32_t episode;
+    uint32_t mission;  // GoToDoor target colour, NX_NO_MISSION otherwise
     int nb;
     int bx[4], by[4];
 };
@@ -217,6 +218,7 @@ __device__ __forceinline__ void load_agent(const nx_agent* src, AgentReg& a)
     a.nb = (w0.y >> 24) & 0xFF;
     a.t = w0.z & 0xFFFF;
     a.episode = w0.w;
+    a.mission = (w1.z >> 16) & 0xFF;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         a.bx[b] = (w1.x >> (8 * b)) & 0xFF;
@@ -241,7 +243,7 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
         w1.x |= (uint32_t)a.bx[b] << (8 * b);
         w1.y |= (uint32_t)a.by[b] << (8 * b);
     }
-    w1.z = (uint32_t)it.family | ((uint32_t)it.size << 8);
+    w1.z = (uint32_t)it.family | ((uint32_t)it.size << 8) | (a.mission << 16);
     w1.w = grid_offset;
     reinterpret_cast<uint4*>(dst)[0] = w0;
     reinterpret_cast<uint4*>(dst)[1] = w1;
@@ -339,6 +341,7 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
     a.done = 0;
     a.t = 0;
     a.episode = episode;
+    a.mission = NX_NO_MISSION;
     a.nb = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
@@ -347,12 +350,13 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
     }
     uint32_t d[8];
     const int n_draws = family == NX_DOORKEY ? 5 : family == NX_FOURROOMS ? 7 : family == NX_LAVAGAP ? 2
-                        : family == NX_DYNOBS ? n_balls : family == NX_EMPTY_RANDOM ? 2 : 0;
+                        : family == NX_DYNOBS ? n_balls : family == NX_EMPTY_RANDOM ? 2
+                        : family == NX_GOTODOOR ? 8 : 0;
     group_draws(grp, n_draws, d,
                 [&](uint32_t k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k); });
     grp.sync();
     const int goal = (S - 2) * S + (S - 2);
-    if (family != NX_FOURROOMS) {
+    if (family != NX_FOURROOMS && family != NX_GOTODOOR) {
         if (grp.lane == 0) g[goal] = (uint8_t)C_GOAL;
     }
     if (family == NX_DOORKEY) {
@@ -408,6 +412,33 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         a.x = ac % S;
         a.y = ac / S;
         a.dir = bounded(d[1], 4u);
+    } else if (family == NX_GOTODOOR) {
+        // L8: one closed door on each wall (top, bottom, left, right) at drawn
+        // positions 1..S-2; their colours are the first four of a partial
+        // Fisher-Yates shuffle of the six colours (nibble i of perm holds the
+        // colour at position i); draws 8..10 pick the target door, the agent's
+        // interior cell (row-major; the interior is all empty) and direction
+        uint32_t perm = 0x543210u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = i + bounded(d[4 + i], (uint32_t)(6 - i));
+            const uint32_t ci = (perm >> (4 * i)) & 15u, cj = (perm >> (4 * j)) & 15u;
+            perm = (perm & ~((15u << (4 * i)) | (15u << (4 * j)))) | (cj << (4 * i)) | (ci << (4 * j));
+        }
+        if (grp.lane == 0) {
+            g[1 + bounded(d[0], (uint32_t)(S - 2))] = (uint8_t)make_code(K_DOOR_CLOSED, perm & 15u);
+            g[(S - 1) * S + 1 + bounded(d[1], (uint32_t)(S - 2))] = (uint8_t)make_code(K_DOOR_CLOSED, (perm >> 4) & 15u);
+            g[(1 + bounded(d[2], (uint32_t)(S - 2))) * S] = (uint8_t)make_code(K_DOOR_CLOSED, (perm >> 8) & 15u);
+            g[(1 + bounded(d[3], (uint32_t)(S - 2))) * S + S - 1] =
+                (uint8_t)make_code(K_DOOR_CLOSED, (perm >> 12) & 15u);
+        }
+        group_draws(grp, 3, d,
+                    [&](uint32_t k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, 8u + k); });
+        a.mission = (perm >> (4 * bounded(d[0], 4u))) & 15u;
+        const int w = S - 2, ac = bounded(d[1], (uint32_t)(w * w));
+        a.y = 1 + ac / w;
+        a.x = 1 + (ac - (a.y - 1) * w);
+        a.dir = bounded(d[2], 4u);
     } else if (family == NX_LAVA_CROSSING || family == NX_SIMPLE_CROSSING) {
         crossing_layout(grp, g, S, family, variant, seed, key_env, episode);
     } else if (family == NX_DYNOBS) {

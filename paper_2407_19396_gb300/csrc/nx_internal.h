@@ -25,7 +25,8 @@ struct NX_ALIGN16 nx_agent {
     uint8_t ball_x[4];
     uint8_t ball_y[4];
     uint8_t family, size;
-    uint16_t reserved;
+    uint8_t mission;       // GoToDoor: colour of the target door; 255 otherwise
+    uint8_t reserved;
     uint32_t grid_offset;
 };
 static_assert(sizeof(nx_agent) == 32, "agent block is 32 bytes");
@@ -72,6 +73,7 @@ struct NX_ALIGN16 nx_req {
     uint8_t* obs_cat;     // [depth, n_envs, full_side, full_side]
     uint8_t* obs_cat_fp;  // [depth, n_envs, 7, 7]
     uint8_t* obs_rgb_full;  // [depth, n_envs, 32 full_side, 32 full_side, 3]
+    uint8_t* mission;     // [depth, n_envs] (may be NULL)
     int32_t full_side;
     int32_t pad2;
 };

@@ -505,7 +505,7 @@ nx_status nx_submit(nx_server* s, const nx_request* r, uint64_t* ticket)
     if (r->family < NX_EMPTY || r->family >= NX_N_FAMILIES || r->size < NX_MIN_SIZE || r->size > NX_MAX_SIZE ||
         r->n_envs < 1 || r->horizon < 1 || r->variant < 0 || r->variant > nx_max_variant(r->family, r->size))
         return nx_fail(nullptr, NX_E_INVAL,
-                       "request: family 0..7, size 5..19, n_envs >= 1, horizon >= 1, variant <= nx_max_variant");
+                       "request: known family, size 5..19, n_envs >= 1, horizon >= 1, variant <= nx_max_variant");
     SReq q;
     q.r = *r;
     q.max_steps = nx_default_max_steps(r->family, r->size);

@@ -94,7 +94,7 @@ size_t scratch_needed(int32_t size, int32_t n_envs)
 nx_status nx_rollout_noalloc(int32_t family, int32_t size, int32_t n_envs, uint64_t seed, int32_t n_steps,
                              int32_t act_mode, const int8_t* d_actions_TN, const nx_out* traj, void* cuda_stream)
 {
-    if (family < NX_EMPTY || family >= NX_N_FAMILIES) return nx_fail(nullptr, NX_E_INVAL, "family must be 0..7");
+    if (family < NX_EMPTY || family >= NX_N_FAMILIES) return nx_fail(nullptr, NX_E_INVAL, "unknown family");
     if (size < NX_MIN_SIZE || size > NX_MAX_SIZE) return nx_fail(nullptr, NX_E_INVAL, "grid size must be in 5..19");
     if (n_envs < 1) return nx_fail(nullptr, NX_E_INVAL, "n_envs must be >= 1");
     if (n_steps < 0) return nx_fail(nullptr, NX_E_INVAL, "n_steps must be >= 0");

@@ -101,7 +101,11 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
                         cell_col(a.carry) == fcol;
     const bool open_ = tog && fk == K_DOOR_CLOSED;
     const bool close_ = tog && fk == K_DOOR_OPEN;
-    const int goal = move && fk == K_GOAL, lava = move && fk == K_LAVA;
+    // on_door_done (Tables 5, 6): GoToDoor's done action facing a door of the
+    // mission's colour completes the task; done does nothing elsewhere
+    const bool door_done = acts && action == 6 && family == NX_GOTODOOR &&
+                           (fk == K_DOOR_OPEN || fk >= K_DOOR_CLOSED) && fcol == a.mission;
+    const int goal = (move && fk == K_GOAL) || door_done, lava = move && fk == K_LAVA;
     a.dir = (a.dir + ((acts && action == 1) ? 1 : 0) + ((acts && action == 0) ? 3 : 0)) & 3;
     a.x = move ? fx : a.x;
     a.y = move ? fy : a.y;
@@ -228,6 +232,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         float* out_reward = rq->reward;
         uint8_t* out_term = rq->terminated;
         uint8_t* out_trunc = rq->truncated;
+        uint8_t* out_mission = rq->mission;
         const uint32_t reward_mode = rq->reward_mode;
         const float lava_reward = rq->lava_reward;
         const int n_balls = rq->n_balls;
@@ -378,6 +383,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     if (out_reward) out_reward[o] = reward;
                     if (out_term) out_term[o] = (uint8_t)term;
                     if (out_trunc) out_trunc[o] = (uint8_t)trunc;
+                    if (out_mission) out_mission[o] = (uint8_t)a.mission;
                     ret += reward;
                     eps += (uint32_t)(term || trunc);
                 }

@@ -20,7 +20,10 @@ LIB_PATH = os.path.join(HERE, "_build", "libnavixgb.so")
 
 NX_OK, NX_PENDING = 0, 1
 NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET, NX_E_STATE = -1, -2, -3, -4, -5, -6, -7
-NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS, NX_EMPTY_RANDOM, NX_LAVA_CROSSING, NX_SIMPLE_CROSSING = range(8)
+(NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS, NX_EMPTY_RANDOM, NX_LAVA_CROSSING, NX_SIMPLE_CROSSING,
+ NX_GOTODOOR) = range(9)
+NX_N_FAMILIES = 9
+NX_NO_MISSION = 255
 NX_OBS_SYM, NX_OBS_RGB, NX_OBS_RGB_FULL = 1, 2, 4
 NX_ACT_BUFFER, NX_ACT_RANDOM = 0, 1
 NX_REWARD_MARKOV, NX_REWARD_MINIGRID = 0, 1
@@ -53,10 +56,10 @@ class nx_out(ctypes.Structure):
     _fields_ = [("obs_sym", ctypes.c_void_p), ("obs_rgb", ctypes.c_void_p), ("reward", ctypes.c_void_p),
                 ("terminated", ctypes.c_void_p), ("truncated", ctypes.c_void_p), ("depth", ctypes.c_int32),
                 ("full_side", ctypes.c_int32), ("obs_full", ctypes.c_void_p), ("obs_cat", ctypes.c_void_p),
-                ("obs_cat_fp", ctypes.c_void_p), ("obs_rgb_full", ctypes.c_void_p)]
+                ("obs_cat_fp", ctypes.c_void_p), ("obs_rgb_full", ctypes.c_void_p), ("mission", ctypes.c_void_p)]
 
 OUT_KEYS = ("obs_sym", "obs_rgb", "reward", "terminated", "truncated", "obs_full", "obs_cat", "obs_cat_fp",
-            "obs_rgb_full")
+            "obs_rgb_full", "mission")
 
 
 class nx_info(ctypes.Structure):
@@ -290,7 +293,7 @@ def parse_state(data: bytes) -> dict:
             "t": int(a[8:10].view(np.uint16)[0]), "max_steps": int(a[10:12].view(np.uint16)[0]),
             "episode": int(a[12:16].view(np.uint32)[0]),
             "ball_x": [int(v) for v in a[16:16 + nb]], "ball_y": [int(v) for v in a[20:20 + nb]],
-            "family": int(a[24]), "height": size, "width": size,
+            "family": int(a[24]), "height": size, "width": size, "mission": int(a[26]),
             "ent": grids[off:off + hw].tobytes(), "col": grids[off + hw:off + 2 * hw].tobytes(),
             "st": grids[off + 2 * hw:off + 3 * hw].tobytes(),
         })
@@ -311,7 +314,8 @@ class Env:
     def __init__(self, family=NX_EMPTY, size=5, n_envs=1, seed=0, *, descs=None, obs_sym=True, obs_rgb=False,
                  atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
                  autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, variant=0,
-                 obs_full=False, obs_cat=False, obs_cat_fp=False, obs_rgb_full=False, torch_allocator=True):
+                 obs_full=False, obs_cat=False, obs_cat_fp=False, obs_rgb_full=False, mission=None,
+                 torch_allocator=True):
         import torch
 
         self.torch = torch
@@ -360,12 +364,16 @@ class Env:
             self.n = int(n_envs)
             self.side = int(size)
             self.h = nx_create(int(family), int(size), self.n, int(seed), o, self.stream.cuda_stream)
+            fams = {int(family)}
         else:
             # each desc: (family, size[, max_steps[, variant]])
             d = [(f, s, (m[0] if len(m) > 0 else 0), (m[1] if len(m) > 1 else 0)) for f, s, *m in descs]
             self.n = len(d)
             self.side = max(x[1] for x in d)
             self.h = nx_create_mixed(d, int(seed), o, self.stream.cuda_stream)
+            fams = {int(x[0]) for x in d}
+        # the per-step mission output, by default only where a family has one
+        self.want_mission = (NX_GOTODOOR in fams) if mission is None else bool(mission)
 
     def close(self):
         if getattr(self, "h", None):
@@ -395,6 +403,7 @@ class Env:
         o["obs_cat_fp"] = torch.empty(lead + (n, 7, 7), dtype=torch.uint8, device=self.device) if self.want_cat_fp else None
         o["obs_rgb_full"] = (torch.empty(lead + (n, 32 * F, 32 * F, 3), dtype=torch.uint8, device=self.device)
                              if self.want_rgb_full else None)
+        o["mission"] = torch.empty(lead + (n,), dtype=torch.uint8, device=self.device) if self.want_mission else None
         return o
 
     def out_struct(self, o, depth=1):
@@ -441,9 +450,10 @@ class Env:
                 "reward": np.empty((n_steps, n), np.float32),
                 "terminated": np.empty((n_steps, n), np.uint8),
                 "truncated": np.empty((n_steps, n), np.uint8),
+                "mission": np.empty((n_steps, n), np.uint8) if self.want_mission else None,
             }
         s = nx_out()
-        for k in ("obs_sym", "obs_rgb", "reward", "terminated", "truncated"):
+        for k in ("obs_sym", "obs_rgb", "reward", "terminated", "truncated", "mission"):
             a = out.get(k)
             if a is None:
                 setattr(s, k, None)

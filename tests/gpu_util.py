@@ -7,7 +7,7 @@ import numpy as np
 import oracle as O
 
 STATE_KEYS = ("x", "y", "dir", "carry_ent", "carry_col", "done", "t", "episode", "ent", "col", "st", "ball_x",
-              "ball_y", "invalid", "max_steps", "height", "family")
+              "ball_y", "invalid", "max_steps", "height", "family", "mission")
 
 
 def to_np(t):

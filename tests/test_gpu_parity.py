@@ -39,7 +39,8 @@ ALL_FAMILIES = [(O.EMPTY, 5, 0), (O.EMPTY, 8, 0), (O.EMPTY, 16, 0), (O.DOORKEY, 
                 (O.DYNOBS, 5, 0), (O.DYNOBS, 16, 0), (O.DOORKEY, 19, 0), (O.EMPTY, 19, 0), (O.LAVAGAP, 13, 0),
                 (O.EMPTY_RANDOM, 5, 0), (O.EMPTY_RANDOM, 16, 0), (O.LAVA_CROSSING, 9, 1), (O.LAVA_CROSSING, 9, 3),
                 (O.LAVA_CROSSING, 11, 5), (O.SIMPLE_CROSSING, 9, 2), (O.SIMPLE_CROSSING, 19, 16),
-                (O.SIMPLE_CROSSING, 5, 2), (O.LAVA_CROSSING, 13, 0)]
+                (O.SIMPLE_CROSSING, 5, 2), (O.LAVA_CROSSING, 13, 0), (O.GOTODOOR, 5, 0), (O.GOTODOOR, 8, 0),
+                (O.GOTODOOR, 19, 0)]
 
 
 @pytest.mark.parametrize("family,size,variant", ALL_FAMILIES)
@@ -328,7 +329,7 @@ def test_reward_variants(reward_mode, lava):
 
 NEW_FAMILIES = [(O.EMPTY_RANDOM, 6, 0, 0), (O.LAVA_CROSSING, 9, 0, 1), (O.LAVA_CROSSING, 9, 0, 3),
                 (O.LAVA_CROSSING, 11, 0, 5), (O.SIMPLE_CROSSING, 9, 0, 2), (O.SIMPLE_CROSSING, 11, 0, 5),
-                (O.EMPTY_RANDOM, 16, 0, 0), (O.SIMPLE_CROSSING, 19, 0, 9)]
+                (O.EMPTY_RANDOM, 16, 0, 0), (O.SIMPLE_CROSSING, 19, 0, 9), (O.GOTODOOR, 6, 0, 0)]
 
 
 @pytest.mark.parametrize("lanes,envs,staging", [(1, 64, 2), (8, 16, 1), (32, 4, 1)])
@@ -384,6 +385,74 @@ def test_full_rgb_view(lanes, envs):
     oo = ob.rollout_full(30, 11, atlas=atlas)
     assert_outputs_equal(out, oo, keys=("obs_sym", "reward", "obs_rgb_full"), what=f"full rgb G={lanes}")
     env.close()
+
+
+def _oracle_missions(ob, T):
+    """Per-step outputs of the oracle with the mission of each slot's episode."""
+    outs = {k: [] for k in ("obs_sym", "reward", "terminated", "truncated", "mission")}
+    for _ in range(T):
+        o = ob.step()
+        for k in ("obs_sym", "reward", "terminated", "truncated"):
+            outs[k].append(o[k])
+        outs["mission"].append(ob.missions())
+    return {k: np.stack(v) for k, v in outs.items()}
+
+
+@pytest.mark.parametrize("lanes,envs,staging", [(1, 64, 2), (2, 64, 1), (8, 16, 1), (32, 4, 1)])
+@pytest.mark.parametrize("reward_mode", [0, 1])
+def test_gotodoor_missions_and_door_done(lanes, envs, staging, reward_mode):
+    """GoToDoor-5/6/8 beside DoorKey: layouts, missions of every step, and the
+    on_door_done reward/termination under random actions (done is one of the
+    seven), against the oracle step by step."""
+    nx = nxmod()
+    descs = mixed_descs(150, [(O.GOTODOOR, 5), (O.GOTODOOR, 6), (O.DOORKEY, 6), (O.GOTODOOR, 8)])
+    env = nx.Env(descs=descs, seed=71, group_lanes=lanes, envs_per_cta=envs, staging=staging, autotune=False,
+                 steps_per_launch=64, reward_mode=reward_mode)
+    r = env.reset()
+    out = env.rollout(500)
+    ob = oracle_batch_for(descs, 71, reward_mode=reward_mode)
+    o0 = ob.reset()
+    o0["mission"] = ob.missions()
+    keys = ("obs_sym", "reward", "terminated", "truncated", "mission")
+    assert_outputs_equal(r, o0, keys=keys, what="gotodoor reset")
+    oo = _oracle_missions(ob, 500)
+    assert_outputs_equal(out, oo, keys=keys, what=f"gotodoor G={lanes} mode={reward_mode}")
+    assert_states_equal(env.state()["envs"], ob, what="gotodoor")
+    m = oo["mission"]
+    dk = np.array([d[0] == O.DOORKEY for d in descs])
+    assert (m[:, dk] == O.NO_MISSION).all() and (m[:, ~dk] <= 5).all()
+    wins = (oo["terminated"] == 1) & (oo["reward"] > 0)
+    assert wins[:, ~dk].sum() > 20  # done facing the right door happens under random play
+    env.close()
+
+
+def test_gotodoor_host_rollout_and_snapshot():
+    nx = nxmod()
+    env = nx.Env(O.GOTODOOR, 7, 300, seed=5, autotune=False)
+    env.reset()
+    dev = env.rollout(150)
+    snap = env.state_bytes()
+    host = env.rollout_host(100)
+    env.set_state(snap)
+    again = env.rollout(100)
+    for k in ("obs_sym", "reward", "terminated", "truncated", "mission"):
+        np.testing.assert_array_equal(host[k], to_np(again[k]), err_msg=k)
+    assert (to_np(dev["mission"]) <= 5).all()
+    # the mission byte of a snapshot is validated per family
+    b = bytearray(snap)
+    b[64 + 26] = 6
+    with pytest.raises(nx.NavixError) as ei:
+        env.set_state(bytes(b))
+    assert ei.value.status == nx.NX_E_INVAL
+    env.close()
+    e2 = nx.Env(O.EMPTY, 5, 3, seed=5, autotune=False)
+    e2.reset()
+    b = bytearray(e2.state_bytes())
+    assert b[64 + 26] == nx.NX_NO_MISSION
+    b[64 + 26] = 0
+    with pytest.raises(nx.NavixError):
+        e2.set_state(bytes(b))
+    e2.close()
 
 
 def test_variant_validation():
