@@ -27,11 +27,11 @@ RGB_BYTES = 224 * 224 * 3
 TILE_BYTES = 32 * 32 * 3
 MAX_CELLS = 19 * 19
 
-EMPTY, DOORKEY, FOURROOMS, LAVAGAP, DYNOBS, EMPTY_RANDOM, LAVA_CROSSING, SIMPLE_CROSSING, GOTODOOR = range(9)
+EMPTY, DOORKEY, FOURROOMS, LAVAGAP, DYNOBS, EMPTY_RANDOM, LAVA_CROSSING, SIMPLE_CROSSING, GOTODOOR, DISTSHIFT = range(10)
 NO_MISSION = 255
 FAMILY_NAMES = {"empty": EMPTY, "doorkey": DOORKEY, "fourrooms": FOURROOMS, "lavagap": LAVAGAP, "dynobs": DYNOBS,
                 "empty_random": EMPTY_RANDOM, "lava_crossing": LAVA_CROSSING, "simple_crossing": SIMPLE_CROSSING,
-                "gotodoor": GOTODOOR}
+                "gotodoor": GOTODOOR, "distshift": DISTSHIFT}
 
 
 def build(force: bool = False) -> str:
@@ -51,7 +51,8 @@ class OrcEnv(ctypes.Structure):
     _fields_ = [
         ("family", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
         ("max_steps", ctypes.c_int32), ("n_balls", ctypes.c_int32), ("reward_mode", ctypes.c_int32),
-        ("variant", ctypes.c_int32), ("lava_reward", ctypes.c_float),
+        ("variant", ctypes.c_int32), ("lava_reward", ctypes.c_float), ("action_cost", ctypes.c_float),
+        ("time_cost", ctypes.c_float),
         ("seed", ctypes.c_uint64), ("env_index", ctypes.c_uint32), ("episode", ctypes.c_uint32),
         ("t", ctypes.c_int32), ("ax", ctypes.c_int32), ("ay", ctypes.c_int32), ("dir", ctypes.c_int32),
         ("carry_ent", ctypes.c_int32), ("carry_col", ctypes.c_int32), ("done", ctypes.c_int32),
@@ -98,6 +99,8 @@ def lib():
                                                    ctypes.c_uint64, P(ctypes.c_uint32), ctypes.c_int32, ctypes.c_float]
             L.orc_batch_create_indexed.restype = ctypes.c_void_p
             L.orc_batch_destroy.argtypes = [ctypes.c_void_p]
+            L.orc_set_costs.argtypes = [P(OrcEnv), ctypes.c_float, ctypes.c_float]
+            L.orc_batch_set_costs.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_float]
             L.orc_batch_env.argtypes = [ctypes.c_void_p, ctypes.c_int32]
             L.orc_batch_env.restype = P(OrcEnv)
             L.orc_batch_reset.argtypes = [ctypes.c_void_p, u8p, u8p, u8p, f32p, u8p, u8p]
@@ -154,12 +157,13 @@ class Env:
     """One oracle environment (for hand-built states and worked examples)."""
 
     def __init__(self, family, size, seed=0, env_index=0, max_steps=0, n_balls=4, reward_mode=0, lava_reward=0.0,
-                 variant=0):
+                 variant=0, action_cost=0.0, time_cost=0.0):
         self.s = OrcEnv()
         rc = lib().orc_env_init(ctypes.byref(self.s), family, size, max_steps, n_balls, seed, env_index,
                                 reward_mode, lava_reward, variant)
         if rc != 0:
             raise ValueError("invalid oracle env arguments")
+        lib().orc_set_costs(ctypes.byref(self.s), action_cost, time_cost)
 
     def reset(self, episode=0):
         lib().orc_reset(ctypes.byref(self.s), episode)
@@ -237,7 +241,7 @@ class Batch:
     """n oracle environments with global indices base..base+n-1 (Code 3's vmap)."""
 
     def __init__(self, families, sizes, seed, max_steps=None, n_balls=4, env_index_base=0, reward_mode=0,
-                 lava_reward=0.0, env_indices=None, variants=None):
+                 lava_reward=0.0, env_indices=None, variants=None, action_cost=0.0, time_cost=0.0):
         fam = np.ascontiguousarray(families, np.int32)
         siz = np.ascontiguousarray(sizes, np.int32)
         self.n = int(fam.shape[0])
@@ -256,6 +260,7 @@ class Batch:
         if not h:
             raise ValueError("invalid oracle batch arguments")
         self.h = h
+        lib().orc_batch_set_costs(h, action_cost, time_cost)
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -300,6 +300,22 @@ static void layout_empty_random(orc_env* e)
     orc_set_agent(e, ax, ay, (int)orc_bounded(layout_draw(e, 1), 4u), 0, 0);
 }
 
+/* L9 DistShift-S, variant v (0: DistShift1, 1: DistShift2): agent (1,1)
+ * east, goal (S-2, 1); lava on row 1 and on row 3 (v = 0) or row S-2 (v = 1),
+ * each over the columns 2..S-3.  No draws: the two variants are the fixed
+ * train / test layouts of a distribution shift. */
+static void layout_distshift(orc_env* e)
+{
+    int S = e->width;
+    orc_set_cell(e, S - 2, 1, ORC_GOAL, ORC_GREEN, 0);
+    orc_set_agent(e, 1, 1, 0, 0, 0);
+    int r2 = e->variant == 0 ? 3 : S - 2;
+    for (int x = 2; x <= S - 3; x++) {
+        orc_set_cell(e, x, 1, ORC_LAVA, 0, 0);
+        orc_set_cell(e, x, r2, ORC_LAVA, 0, 0);
+    }
+}
+
 /* Candidate rivers of an S x S crossing layout: rows 2, 4, .., S-3 (kind 0,
  * horizontal), then columns 2, 4, .., S-3 (kind 1, vertical). */
 static int crossing_candidates(int S, int* kind, int* pos)
@@ -320,6 +336,7 @@ static int crossing_candidates(int S, int* kind, int* pos)
 
 int32_t orc_max_variant(int32_t family, int32_t size)
 {
+    if (family == ORC_DISTSHIFT) return 1;
     if (family != ORC_LAVA_CROSSING && family != ORC_SIMPLE_CROSSING) return 0;
     int kind[ORC_MAX_SIZE * 2], pos[ORC_MAX_SIZE * 2];
     return crossing_candidates(size, kind, pos);
@@ -448,6 +465,12 @@ static void layout_gotodoor(orc_env* e)
     orc_set_agent(e, ax, ay, (int)orc_bounded(layout_draw(e, k++), 4u), 0, 0);
 }
 
+void orc_set_costs(orc_env* e, float action_cost, float time_cost)
+{
+    e->action_cost = action_cost;
+    e->time_cost = time_cost;
+}
+
 /* reset(key) of Section 3.2.2: sample a start state for the given episode. */
 void orc_reset(orc_env* e, uint32_t episode)
 {
@@ -476,6 +499,7 @@ void orc_reset(orc_env* e, uint32_t episode)
     case ORC_LAVA_CROSSING:
     case ORC_SIMPLE_CROSSING: layout_crossing(e); break;
     case ORC_GOTODOOR: layout_gotodoor(e); break;
+    case ORC_DISTSHIFT: layout_distshift(e); break;
     default: break;
     }
 }
@@ -495,6 +519,8 @@ int32_t orc_env_init(orc_env* e, int32_t family, int32_t size, int32_t max_steps
     e->n_balls = family == ORC_DYNOBS ? n_balls : 0;
     e->reward_mode = reward_mode;
     e->lava_reward = lava_reward;
+    e->action_cost = 0.0f;
+    e->time_cost = 0.0f;
     e->seed = seed;
     e->env_index = env_index;
     e->variant = variant;
@@ -639,6 +665,11 @@ void orc_step(orc_env* e, int32_t action, float* reward, uint8_t* terminated, ui
         r = -1.0f;
         term = 1;
     }
+    /* the shaping terms of Table 5 (reading R22): action_cost for every
+     * action but done (an action in 0..5, whether or not it changes the
+     * state), then time_cost, each subtracted in single precision */
+    if (action >= 0 && action < ORC_DONE) r = r - e->action_cost;
+    r = r - e->time_cost;
     *reward = r;
     *terminated = (uint8_t)term;
     *truncated = (uint8_t)trunc;
@@ -873,6 +904,11 @@ void orc_batch_destroy(orc_batch* b)
     if (!b) return;
     free(b->envs);
     free(b);
+}
+
+void orc_batch_set_costs(orc_batch* b, float action_cost, float time_cost)
+{
+    for (int32_t i = 0; i < b->n; i++) orc_set_costs(&b->envs[i], action_cost, time_cost);
 }
 
 orc_env* orc_batch_env(orc_batch* b, int32_t i) { return (i >= 0 && i < b->n) ? &b->envs[i] : NULL; }

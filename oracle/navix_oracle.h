@@ -48,8 +48,8 @@ extern "C" {
 
 /* families (variant: the number of rivers for the two crossing families) */
 enum { ORC_EMPTY = 0, ORC_DOORKEY = 1, ORC_FOURROOMS = 2, ORC_LAVAGAP = 3, ORC_DYNOBS = 4, ORC_EMPTY_RANDOM = 5,
-       ORC_LAVA_CROSSING = 6, ORC_SIMPLE_CROSSING = 7, ORC_GOTODOOR = 8 };
-#define ORC_N_FAMILIES 9
+       ORC_LAVA_CROSSING = 6, ORC_SIMPLE_CROSSING = 7, ORC_GOTODOOR = 8, ORC_DISTSHIFT = 9 };
+#define ORC_N_FAMILIES 10
 #define ORC_NO_MISSION 255
 /* actions */
 enum { ORC_LEFT = 0, ORC_RIGHT = 1, ORC_FORWARD = 2, ORC_PICKUP = 3, ORC_DROP = 4, ORC_TOGGLE = 5, ORC_DONE = 6 };
@@ -66,6 +66,7 @@ enum { ORC_REWARD_MARKOV = 0, ORC_REWARD_MINIGRID = 1 };
 typedef struct orc_env {
     int32_t family, height, width, max_steps, n_balls, reward_mode, variant;
     float lava_reward;
+    float action_cost, time_cost; /* Table 5's shaping terms (0 by default) */
     uint64_t seed;
     uint32_t env_index;
     uint32_t episode;
@@ -89,6 +90,8 @@ int32_t orc_default_max_steps(int32_t family, int32_t size);
 int32_t orc_env_init(orc_env* e, int32_t family, int32_t size, int32_t max_steps, int32_t n_balls, uint64_t seed,
                      uint32_t env_index, int32_t reward_mode, float lava_reward, int32_t variant);
 int32_t orc_max_variant(int32_t family, int32_t size);
+/* action_cost / time_cost of Table 5 (both 0 after orc_env_init) */
+void orc_set_costs(orc_env* e, float action_cost, float time_cost);
 void orc_reset(orc_env* e, uint32_t episode);
 int32_t orc_random_action(const orc_env* e, uint32_t gstep);
 void orc_step(orc_env* e, int32_t action, float* reward, uint8_t* terminated, uint8_t* truncated);
@@ -122,6 +125,7 @@ orc_batch* orc_batch_create_indexed(int32_t n, const int32_t* family, const int3
                                     const int32_t* variant, int32_t n_balls, uint64_t seed, const uint32_t* env_index,
                                     int32_t reward_mode, float lava_reward);
 void orc_batch_destroy(orc_batch* b);
+void orc_batch_set_costs(orc_batch* b, float action_cost, float time_cost);
 orc_env* orc_batch_env(orc_batch* b, int32_t i);
 void orc_batch_reset(orc_batch* b, uint8_t* obs_sym, uint8_t* obs_rgb, const uint8_t* atlas, float* reward,
                      uint8_t* terminated, uint8_t* truncated);

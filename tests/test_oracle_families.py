@@ -255,3 +255,73 @@ def test_gotodoor_truncates_at_5_s_squared():
     for t in range(1, 5 * S * S + 1):
         r, te, tr = env.step(0)  # turning never ends the episode
         assert (r, te) == (0.0, 0) and tr == (t == 5 * S * S)
+
+
+# --- DistShift1/2 (Table 8, R2) -----------------------------------------------
+
+@pytest.mark.parametrize("S", [5, 6, 8, 11, 19])
+def test_distshift_layouts(S):
+    assert O.max_variant(O.DISTSHIFT, S) == 1
+    grids = []
+    for v in (0, 1):
+        e = O.Env(O.DISTSHIFT, S, seed=v, variant=v, env_index=3)
+        ent, col, st = e.grid()
+        r2 = 3 if v == 0 else S - 2
+        want = np.full((S, S), 1, np.uint8)
+        want[0, :] = want[-1, :] = want[:, 0] = want[:, -1] = 2
+        want[1, 2:S - 2] = 9
+        want[r2, 2:S - 2] = 9
+        want[1, S - 2] = 8
+        np.testing.assert_array_equal(ent, want)
+        assert (e.s.ax, e.s.ay, e.s.dir) == (1, 1, 0)
+        # no draws: every episode and seed gives the same layout
+        e2 = O.Env(O.DISTSHIFT, S, seed=99, variant=v)
+        e2.reset(17)
+        assert bytes(e2.s.ent) == bytes(e.s.ent)
+        grids.append(ent)
+        # a BFS plan (independent rules; lava ends a path) reaches the goal
+        cells = tuple((int(ent[y, x]), int(col[y, x]), int(st[y, x])) for y in range(S) for x in range(S))
+        plan = M.bfs_goal((1, 1, 0, None, cells), S, S, max_depth=60)
+        assert plan is not None
+        for a in plan:
+            r, te, tr = e.step(a)
+        assert (r, te) == (1.0, 1) and e.s.t == len(plan)
+    assert S == 5 or (grids[0] != grids[1]).any()
+
+
+def test_distshift_lava_ends_with_the_lava_reward():
+    e = O.Env(O.DISTSHIFT, 8, lava_reward=-1.0)
+    assert e.step(2) == (-1.0, 1, 0)  # the lava cell right of the start
+    e = O.Env(O.DISTSHIFT, 8)
+    assert e.step(2) == (0.0, 1, 0)
+
+
+# --- action_cost / time_cost (Table 5) ----------------------------------------
+
+def test_shaping_costs_follow_table5():
+    f = np.float32
+    ac, tc = f(0.01), f(0.003)
+    e = O.Env(O.EMPTY, 5, action_cost=float(ac), time_cost=float(tc))
+    # a plain move: both costs, subtracted in order
+    r, te, tr = e.step(2)
+    assert np.float32(r) == (f(0.0) - ac) - tc and te == 0
+    # done: only the time cost
+    r, te, tr = e.step(6)
+    assert np.float32(r) == f(0.0) - tc
+    # out-of-range action: a no-op that is no action, only the time cost
+    r, te, tr = e.step(9)
+    assert np.float32(r) == f(0.0) - tc
+    # reaching the goal: 1 - action_cost - time_cost
+    e.step(2)
+    e.step(1)
+    e.step(2)
+    r, te, tr = e.step(2)
+    assert (e.s.ax, e.s.ay) == (3, 3) and te == 1 and np.float32(r) == (f(1.0) - ac) - tc
+    # the autoreset step carries no cost (reward padding)
+    assert e.step(2) == (0.0, 0, 0)
+    # with zero costs nothing changes, bit for bit
+    b1 = O.Batch([O.DOORKEY] * 16, [6] * 16, seed=3)
+    b2 = O.Batch([O.DOORKEY] * 16, [6] * 16, seed=3, action_cost=0.0, time_cost=0.0)
+    b1.reset(), b2.reset()
+    o1, o2 = b1.rollout(300), b2.rollout(300)
+    assert o1["reward"].tobytes() == o2["reward"].tobytes()
