@@ -59,15 +59,16 @@ enum {
 };
 
 /* environment families of Table 8; the crossings take their number of
- * rivers as the descriptor's variant (0..nx_max_variant).  GoToDoor has a
+ * rivers as the descriptor's variant (0..nx_max_variant), DistShift its
+ * layout (variant 0: DistShift1, 1: DistShift2).  GoToDoor has a
  * mission (the colour of one of its four doors, nx_out.mission) and ends
  * with reward 1 when the done action is taken facing that door
  * (on_door_done, Tables 5 and 6). */
 enum {
     NX_EMPTY = 0, NX_DOORKEY = 1, NX_FOURROOMS = 2, NX_LAVAGAP = 3, NX_DYNOBS = 4, NX_EMPTY_RANDOM = 5,
-    NX_LAVA_CROSSING = 6, NX_SIMPLE_CROSSING = 7, NX_GOTODOOR = 8
+    NX_LAVA_CROSSING = 6, NX_SIMPLE_CROSSING = 7, NX_GOTODOOR = 8, NX_DISTSHIFT = 9
 };
-#define NX_N_FAMILIES 9
+#define NX_N_FAMILIES 10
 #define NX_NO_MISSION 255  /* the mission byte of a family without one */
 /* observation bit flags (Table 4): RGB and RGB_FULL need the sprite atlas */
 enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2, NX_OBS_RGB_FULL = 4 };
@@ -122,6 +123,11 @@ typedef struct {
      * which is how a batch is split over GPUs */
     uint32_t env_index_base;
     int32_t variant;          /* nx_create only: the variant of every env (rivers of a crossing family) */
+    /* Table 5's shaping terms, subtracted from every step's reward in this
+     * order: action_cost for each action 0..5 (every action but done), then
+     * time_cost (default 0 and 0; not applied to autoreset steps) */
+    float action_cost;
+    float time_cost;
 } nx_options;
 
 /* Per-step outputs, device pointers owned by the caller; any may be NULL (not
@@ -168,8 +174,8 @@ typedef struct {
 
 void nx_options_default(nx_options* opts);
 /* Largest valid variant of a family at a size (the number of candidate
- * rivers of a crossing family: rows and columns 2, 4, .., size-3), 0 for
- * the other families. */
+ * rivers of a crossing family: rows and columns 2, 4, .., size-3; 1 for
+ * DistShift), 0 for the other families. */
 int32_t nx_max_variant(int32_t family, int32_t size);
 
 /* nx_create: one family and size for all n_envs environments (the paper's

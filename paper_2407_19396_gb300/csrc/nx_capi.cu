@@ -135,8 +135,9 @@ int nx_default_max_steps(int family, int size)
 
 int32_t nx_max_variant(int32_t family, int32_t size)
 {
-    if (family != NX_LAVA_CROSSING && family != NX_SIMPLE_CROSSING) return 0;
     if (size < NX_MIN_SIZE || size > NX_MAX_SIZE) return 0;
+    if (family == NX_DISTSHIFT) return 1;
+    if (family != NX_LAVA_CROSSING && family != NX_SIMPLE_CROSSING) return 0;
     return 2 * ((size - 3) / 2);  // rows and columns 2, 4, .., size - 3
 }
 
@@ -307,6 +308,8 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
     env->req_host.n_envs = (uint32_t)env->n_envs;
     env->req_host.reward_mode = (uint32_t)o.reward_mode;
     env->req_host.lava_reward = o.lava_reward;
+    env->req_host.action_cost = o.action_cost;
+    env->req_host.time_cost = o.time_cost;
     env->req_host.n_balls = o.n_balls;
     env->req_host.key_base = o.env_index_base;
 

@@ -355,7 +355,7 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
     group_draws(grp, n_draws, d,
                 [&](uint32_t k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k); });
     grp.sync();
-    const int goal = (S - 2) * S + (S - 2);
+    const int goal = family == NX_DISTSHIFT ? S + (S - 2) : (S - 2) * S + (S - 2);
     if (family != NX_FOURROOMS && family != NX_GOTODOOR) {
         if (grp.lane == 0) g[goal] = (uint8_t)C_GOAL;
     }
@@ -439,6 +439,14 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         a.y = 1 + ac / w;
         a.x = 1 + (ac - (a.y - 1) * w);
         a.dir = bounded(d[2], 4u);
+    } else if (family == NX_DISTSHIFT) {
+        // L9: lava over columns 2..S-3 of row 1 and of row 3 (variant 0) or
+        // S-2 (variant 1); the goal is at (S-2, 1); no draws
+        const int r2 = variant == 0 ? 3 : S - 2;
+        for (int x = 2 + grp.lane; x <= S - 3; x += G) {
+            g[S + x] = (uint8_t)C_LAVA;
+            g[r2 * S + x] = (uint8_t)C_LAVA;
+        }
     } else if (family == NX_LAVA_CROSSING || family == NX_SIMPLE_CROSSING) {
         crossing_layout(grp, g, S, family, variant, seed, key_env, episode);
     } else if (family == NX_DYNOBS) {

@@ -75,7 +75,8 @@ struct NX_ALIGN16 nx_req {
     uint8_t* obs_rgb_full;  // [depth, n_envs, 32 full_side, 32 full_side, 3]
     uint8_t* mission;     // [depth, n_envs] (may be NULL)
     int32_t full_side;
-    int32_t pad2;
+    float action_cost;    // Table 5 shaping terms
+    float time_cost;
 };
 
 struct NX_ALIGN16 nx_ctl {

@@ -198,6 +198,8 @@ nx_req record_of(const nx_server* s, const SReq& q, int steps)
     r.episodes = (uint32_t*)(base + q.lay.episodes);
     r.reward_mode = (uint32_t)s->opt.reward_mode;
     r.lava_reward = s->opt.lava_reward;
+    r.action_cost = s->opt.action_cost;
+    r.time_cost = s->opt.time_cost;
     r.n_balls = s->opt.n_balls;
     r.key_base = 0;
     return r;

@@ -37,7 +37,8 @@ __device__ __forceinline__ uint64_t digest_word(uint64_t h, uint32_t w) { return
 template <int G>
 __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int family, int max_steps, AgentReg& a,
                                          int action, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
-                                         float& reward, int& term, int& trunc, nx_ctl* ctl)
+                                         float action_cost, float time_cost, float& reward, int& term, int& trunc,
+                                         nx_ctl* ctl)
 {
     // transition system: each ball, in index order, moves to a uniformly drawn
     // empty cell of its 8-neighbourhood that is not the agent's cell
@@ -135,6 +136,10 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
         reward = -1.0f;
         term = 1;
     }
+    // the shaping terms of Table 5: action_cost for every action but done
+    // (0..5), then time_cost (subtracting 0 leaves a reward unchanged)
+    reward = __fsub_rn(reward, (unsigned)action < 6u ? action_cost : 0.0f);
+    reward = __fsub_rn(reward, time_cost);
     a.done = term || trunc;
 }
 
@@ -235,6 +240,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         uint8_t* out_mission = rq->mission;
         const uint32_t reward_mode = rq->reward_mode;
         const float lava_reward = rq->lava_reward;
+        const float action_cost = rq->action_cost, time_cost = rq->time_cost;
         const int n_balls = rq->n_balls;
         float* returns = rq->returns;
         uint64_t* digest = rq->digest;
@@ -345,8 +351,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     } else {
                         action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
                     }
-                    env_step(grp, mygrid, S, family, max_steps, a, action, d, reward_mode, lava_reward, reward, term,
-                             trunc, p.ctl);
+                    env_step(grp, mygrid, S, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
+                             time_cost, reward, term, trunc, p.ctl);
                 }
                 grp.sync();
                 render_view(grp, mygrid, S, a, s_dec, vo, RGB && obs_rgb ? stiles + gi * 49 : nullptr);

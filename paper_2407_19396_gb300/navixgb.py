@@ -21,8 +21,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libnavixgb.so")
 NX_OK, NX_PENDING = 0, 1
 NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET, NX_E_STATE = -1, -2, -3, -4, -5, -6, -7
 (NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS, NX_EMPTY_RANDOM, NX_LAVA_CROSSING, NX_SIMPLE_CROSSING,
- NX_GOTODOOR) = range(9)
-NX_N_FAMILIES = 9
+ NX_GOTODOOR, NX_DISTSHIFT) = range(10)
+NX_N_FAMILIES = 10
 NX_NO_MISSION = 255
 NX_OBS_SYM, NX_OBS_RGB, NX_OBS_RGB_FULL = 1, 2, 4
 NX_ACT_BUFFER, NX_ACT_RANDOM = 0, 1
@@ -49,7 +49,8 @@ class nx_options(ctypes.Structure):
                 ("n_balls", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("group_lanes", ctypes.c_int32), ("envs_per_cta", ctypes.c_int32), ("staging", ctypes.c_int32),
                 ("atlas", ctypes.POINTER(ctypes.c_uint8)), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p), ("env_index_base", ctypes.c_uint32), ("variant", ctypes.c_int32)]
+                ("alloc_user", ctypes.c_void_p), ("env_index_base", ctypes.c_uint32), ("variant", ctypes.c_int32),
+                ("action_cost", ctypes.c_float), ("time_cost", ctypes.c_float)]
 
 
 class nx_out(ctypes.Structure):
@@ -315,7 +316,7 @@ class Env:
                  atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
                  autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, variant=0,
                  obs_full=False, obs_cat=False, obs_cat_fp=False, obs_rgb_full=False, mission=None,
-                 torch_allocator=True):
+                 action_cost=0.0, time_cost=0.0, torch_allocator=True):
         import torch
 
         self.torch = torch
@@ -328,6 +329,8 @@ class Env:
             (NX_OBS_RGB_FULL if obs_rgb_full else 0)
         o.reward_mode = reward_mode
         o.lava_reward = lava_reward
+        o.action_cost = action_cost
+        o.time_cost = time_cost
         o.n_balls = n_balls
         o.steps_per_launch = steps_per_launch
         o.autotune = 1 if autotune else 0
@@ -548,13 +551,16 @@ class Server:
     """Continuous-batching rollout server; results land in numpy arrays."""
 
     def __init__(self, budget_bytes=1 << 30, steps_per_launch=128, group_lanes=0, envs_per_cta=0,
-                 reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, stream=None):
+                 reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, action_cost=0.0, time_cost=0.0,
+                 stream=None):
         o = nx_options_default()
         o.steps_per_launch = steps_per_launch
         o.group_lanes = group_lanes
         o.envs_per_cta = envs_per_cta
         o.reward_mode = reward_mode
         o.lava_reward = lava_reward
+        o.action_cost = action_cost
+        o.time_cost = time_cost
         o.n_balls = n_balls
         if stream is None:
             try:

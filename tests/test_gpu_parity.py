@@ -40,7 +40,7 @@ ALL_FAMILIES = [(O.EMPTY, 5, 0), (O.EMPTY, 8, 0), (O.EMPTY, 16, 0), (O.DOORKEY, 
                 (O.EMPTY_RANDOM, 5, 0), (O.EMPTY_RANDOM, 16, 0), (O.LAVA_CROSSING, 9, 1), (O.LAVA_CROSSING, 9, 3),
                 (O.LAVA_CROSSING, 11, 5), (O.SIMPLE_CROSSING, 9, 2), (O.SIMPLE_CROSSING, 19, 16),
                 (O.SIMPLE_CROSSING, 5, 2), (O.LAVA_CROSSING, 13, 0), (O.GOTODOOR, 5, 0), (O.GOTODOOR, 8, 0),
-                (O.GOTODOOR, 19, 0)]
+                (O.GOTODOOR, 19, 0), (O.DISTSHIFT, 6, 0), (O.DISTSHIFT, 8, 1), (O.DISTSHIFT, 5, 1)]
 
 
 @pytest.mark.parametrize("family,size,variant", ALL_FAMILIES)
@@ -327,9 +327,32 @@ def test_reward_variants(reward_mode, lava):
     env.close()
 
 
+@pytest.mark.parametrize("lanes,envs", [(1, 64), (8, 16), (32, 4)])
+@pytest.mark.parametrize("reward_mode", [0, 1])
+def test_shaping_costs(lanes, envs, reward_mode):
+    """action_cost / time_cost of Table 5 with buffered actions that include
+    done and out-of-range entries, across families with every reward event."""
+    nx = nxmod()
+    descs = mixed_descs(130, [(O.DOORKEY, 5), (O.LAVAGAP, 5), (O.DYNOBS, 5), (O.GOTODOOR, 5), (O.DISTSHIFT, 6, 0, 1)])
+    T = 300
+    acts = inputs.random_actions(37, (T, 130), n_actions=7, invalid_fraction=0.03)
+    kw = dict(action_cost=0.0125, time_cost=0.004, lava_reward=-1.0)
+    env = nx.Env(descs=descs, seed=37, group_lanes=lanes, envs_per_cta=envs, autotune=False, reward_mode=reward_mode,
+                 **kw)
+    env.reset()
+    out = env.rollout(T, actions=torch.from_numpy(acts).cuda())
+    ob = oracle_batch_for(descs, 37, reward_mode=reward_mode, **kw)
+    ob.reset()
+    assert_outputs_equal(out, ob.rollout(T, actions=acts), what=f"costs G={lanes} mode={reward_mode}")
+    r = to_np(out["reward"])
+    assert (r < 0).mean() > 0.5 and (r > 0.9).any() and (r < -1.0).any()
+    env.close()
+
+
 NEW_FAMILIES = [(O.EMPTY_RANDOM, 6, 0, 0), (O.LAVA_CROSSING, 9, 0, 1), (O.LAVA_CROSSING, 9, 0, 3),
                 (O.LAVA_CROSSING, 11, 0, 5), (O.SIMPLE_CROSSING, 9, 0, 2), (O.SIMPLE_CROSSING, 11, 0, 5),
-                (O.EMPTY_RANDOM, 16, 0, 0), (O.SIMPLE_CROSSING, 19, 0, 9), (O.GOTODOOR, 6, 0, 0)]
+                (O.EMPTY_RANDOM, 16, 0, 0), (O.SIMPLE_CROSSING, 19, 0, 9), (O.GOTODOOR, 6, 0, 0),
+                (O.DISTSHIFT, 6, 0, 0), (O.DISTSHIFT, 8, 0, 1)]
 
 
 @pytest.mark.parametrize("lanes,envs,staging", [(1, 64, 2), (8, 16, 1), (32, 4, 1)])

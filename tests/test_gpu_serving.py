@@ -111,13 +111,26 @@ def test_new_families_served_like_the_oracle():
     from paper_2407_19396_gb300 import navixgb as nx
 
     reqs = [(O.LAVA_CROSSING, 11, 40, 120, 1, 5), (O.SIMPLE_CROSSING, 9, 17, 90, 2, 3), (O.EMPTY_RANDOM, 8, 33, 70, 3, 0),
-            (O.GOTODOOR, 6, 29, 150, 4, 0)]
+            (O.GOTODOOR, 6, 29, 150, 4, 0), (O.DISTSHIFT, 8, 21, 100, 5, 1)]
     srv = nx.Server(budget_bytes=64 << 20, steps_per_launch=32)
     tickets = [srv.submit(f, s_, n, h, seed, variant=v) for f, s_, n, h, seed, v in reqs]
     res = [srv.wait(t, timeout_s=120.0) for t in tickets]
     srv.close()
     for (f, s_, n, h, seed, v), m in zip(reqs, res):
         _same(m, oracle_request(f, s_, n, h, seed, variant=v))
+
+
+def test_served_rewards_with_shaping_costs():
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    kw = dict(action_cost=0.02, time_cost=0.001, lava_reward=-1.0)
+    reqs = [(O.DISTSHIFT, 6, 25, 80, 7, 0), (O.GOTODOOR, 5, 31, 120, 8, 0), (O.LAVAGAP, 6, 12, 60, 9, 0)]
+    srv = nx.Server(budget_bytes=64 << 20, steps_per_launch=32, **kw)
+    tickets = [srv.submit(f, s_, n, h, seed, variant=v) for f, s_, n, h, seed, v in reqs]
+    res = [srv.wait(t, timeout_s=120.0) for t in tickets]
+    srv.close()
+    for (f, s_, n, h, seed, v), m in zip(reqs, res):
+        _same(m, oracle_request(f, s_, n, h, seed, variant=v, **kw))
 
 
 def test_wait_timeout_is_bounded():
