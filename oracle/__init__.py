@@ -27,11 +27,12 @@ RGB_BYTES = 224 * 224 * 3
 TILE_BYTES = 32 * 32 * 3
 MAX_CELLS = 19 * 19
 
-EMPTY, DOORKEY, FOURROOMS, LAVAGAP, DYNOBS, EMPTY_RANDOM, LAVA_CROSSING, SIMPLE_CROSSING, GOTODOOR, DISTSHIFT = range(10)
+(EMPTY, DOORKEY, FOURROOMS, LAVAGAP, DYNOBS, EMPTY_RANDOM, LAVA_CROSSING, SIMPLE_CROSSING, GOTODOOR, DISTSHIFT,
+ KEYCORRIDOR) = range(11)
 NO_MISSION = 255
 FAMILY_NAMES = {"empty": EMPTY, "doorkey": DOORKEY, "fourrooms": FOURROOMS, "lavagap": LAVAGAP, "dynobs": DYNOBS,
                 "empty_random": EMPTY_RANDOM, "lava_crossing": LAVA_CROSSING, "simple_crossing": SIMPLE_CROSSING,
-                "gotodoor": GOTODOOR, "distshift": DISTSHIFT}
+                "gotodoor": GOTODOOR, "distshift": DISTSHIFT, "keycorridor": KEYCORRIDOR}
 
 
 def build(force: bool = False) -> str:

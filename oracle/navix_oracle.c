@@ -142,10 +142,14 @@ int32_t orc_default_max_steps(int32_t family, int32_t size)
 {
     /* reading R17: Empty 4S^2 (100 at S = 5), DoorKey 10S^2 (640 at S = 8),
      * FourRooms 100, LavaGap 4S^2, Dynamic-Obstacles 4S^2; Empty-Random and the
-     * crossings 4S^2; GoToDoor 5S^2 */
+     * crossings 4S^2; GoToDoor 5S^2; KeyCorridor 30 s^2 for room side s */
     switch (family) {
     case ORC_DOORKEY: return 10 * size * size;
     case ORC_GOTODOOR: return 5 * size * size;
+    case ORC_KEYCORRIDOR: {
+        int s = (size - 1) / 3 + 1; /* the room side */
+        return 30 * s * s;
+    }
     case ORC_FOURROOMS: return 100;
     default: return 4 * size * size;
     }
@@ -316,6 +320,58 @@ static void layout_distshift(orc_env* e)
     }
 }
 
+/* L10 KeyCorridor S{s}R{R} (Table 8; variant R - 1): a 3 x R block of rooms
+ * of side s sharing their walls, held in the S x S grid with S = 3(s-1)+1.
+ * The rooms span rows 0..H-1 with H = (s-1)R+1; every row below is wall
+ * (the views treat cells outside a grid as wall, so views and rules are those
+ * of the H x S grid).  The middle column of rooms is one corridor: the walls
+ * between its rooms are open.  Every side room has a door in the wall it
+ * shares with the corridor; the room holding the goal has a locked door and
+ * the key of that door's colour lies in a side room on the other side; the
+ * other doors are closed.  Draws, in order: the door rows (left rooms top to
+ * bottom, then right rooms), the door colours in the same order, the goal's
+ * side and room row, the key's room row, the goal cell, the key cell (free
+ * interior cells of their rooms), the agent's corridor cell and direction. */
+static void layout_keycorridor(orc_env* e)
+{
+    int S = e->width, s = (S - 1) / 3 + 1, R = e->variant + 1, H = (s - 1) * R + 1;
+    int xl = s - 1, xr = 2 * (s - 1); /* the corridor's walls */
+    for (int y = 0; y < S; y++)
+        for (int x = 0; x < S; x++) {
+            int wall = y >= H - 1 || y == 0 || x == 0 || x == S - 1 || x == xl || x == xr;
+            if (y % (s - 1) == 0 && !(x > xl && x < xr)) wall = 1;
+            if (wall) orc_set_cell(e, x, y, ORC_WALL, ORC_GREY, 0);
+        }
+    uint32_t k = 0;
+    int door_y[2][3], door_c[2][3];
+    for (int side = 0; side < 2; side++)
+        for (int j = 0; j < R; j++) door_y[side][j] = j * (s - 1) + 1 + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(s - 2));
+    for (int side = 0; side < 2; side++)
+        for (int j = 0; j < R; j++) door_c[side][j] = (int)orc_bounded(layout_draw(e, k++), 6u);
+    int gside = (int)orc_bounded(layout_draw(e, k++), 2u);
+    int grow = (int)orc_bounded(layout_draw(e, k++), (uint32_t)R);
+    int krow = (int)orc_bounded(layout_draw(e, k++), (uint32_t)R);
+    for (int side = 0; side < 2; side++)
+        for (int j = 0; j < R; j++)
+            orc_set_cell(e, side == 0 ? xl : xr, door_y[side][j], ORC_DOOR, door_c[side][j],
+                         (side == gside && j == grow) ? ORC_LOCKED : ORC_CLOSED);
+    /* the goal in room (gside, grow), the key in room (1 - gside, krow) */
+    int gx0 = gside == 0 ? 1 : xr + 1, gy0 = grow * (s - 1) + 1;
+    int n = count_free(e, gx0, gx0 + s - 3, gy0, gy0 + s - 3, -1, -1);
+    int gx, gy;
+    kth_free(e, (int)orc_bounded(layout_draw(e, k++), (uint32_t)n), gx0, gx0 + s - 3, gy0, gy0 + s - 3, -1, -1, &gx, &gy);
+    orc_set_cell(e, gx, gy, ORC_GOAL, ORC_GREEN, 0);
+    int kx0 = gside == 0 ? xr + 1 : 1, ky0 = krow * (s - 1) + 1;
+    n = count_free(e, kx0, kx0 + s - 3, ky0, ky0 + s - 3, -1, -1);
+    int kx, ky;
+    kth_free(e, (int)orc_bounded(layout_draw(e, k++), (uint32_t)n), kx0, kx0 + s - 3, ky0, ky0 + s - 3, -1, -1, &kx, &ky);
+    orc_set_cell(e, kx, ky, ORC_KEY, door_c[gside][grow], 0);
+    n = count_free(e, xl + 1, xr - 1, 1, H - 2, -1, -1);
+    int ax, ay;
+    kth_free(e, (int)orc_bounded(layout_draw(e, k++), (uint32_t)n), xl + 1, xr - 1, 1, H - 2, -1, -1, &ax, &ay);
+    orc_set_agent(e, ax, ay, (int)orc_bounded(layout_draw(e, k++), 4u), 0, 0);
+}
+
 /* Candidate rivers of an S x S crossing layout: rows 2, 4, .., S-3 (kind 0,
  * horizontal), then columns 2, 4, .., S-3 (kind 1, vertical). */
 static int crossing_candidates(int S, int* kind, int* pos)
@@ -337,6 +393,9 @@ static int crossing_candidates(int S, int* kind, int* pos)
 int32_t orc_max_variant(int32_t family, int32_t size)
 {
     if (family == ORC_DISTSHIFT) return 1;
+    /* KeyCorridor exists at S = 3(s-1)+1 for room sides s = 3..7, with 1..3
+     * rows of rooms; -1 marks a size the family does not have */
+    if (family == ORC_KEYCORRIDOR) return (size >= 7 && size % 3 == 1) ? 2 : -1;
     if (family != ORC_LAVA_CROSSING && family != ORC_SIMPLE_CROSSING) return 0;
     int kind[ORC_MAX_SIZE * 2], pos[ORC_MAX_SIZE * 2];
     return crossing_candidates(size, kind, pos);
@@ -500,6 +559,7 @@ void orc_reset(orc_env* e, uint32_t episode)
     case ORC_SIMPLE_CROSSING: layout_crossing(e); break;
     case ORC_GOTODOOR: layout_gotodoor(e); break;
     case ORC_DISTSHIFT: layout_distshift(e); break;
+    case ORC_KEYCORRIDOR: layout_keycorridor(e); break;
     default: break;
     }
 }

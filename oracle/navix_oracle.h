@@ -48,8 +48,9 @@ extern "C" {
 
 /* families (variant: the number of rivers for the two crossing families) */
 enum { ORC_EMPTY = 0, ORC_DOORKEY = 1, ORC_FOURROOMS = 2, ORC_LAVAGAP = 3, ORC_DYNOBS = 4, ORC_EMPTY_RANDOM = 5,
-       ORC_LAVA_CROSSING = 6, ORC_SIMPLE_CROSSING = 7, ORC_GOTODOOR = 8, ORC_DISTSHIFT = 9 };
-#define ORC_N_FAMILIES 10
+       ORC_LAVA_CROSSING = 6, ORC_SIMPLE_CROSSING = 7, ORC_GOTODOOR = 8, ORC_DISTSHIFT = 9,
+       ORC_KEYCORRIDOR = 10 };
+#define ORC_N_FAMILIES 11
 #define ORC_NO_MISSION 255
 /* actions */
 enum { ORC_LEFT = 0, ORC_RIGHT = 1, ORC_FORWARD = 2, ORC_PICKUP = 3, ORC_DROP = 4, ORC_TOGGLE = 5, ORC_DONE = 6 };

@@ -325,3 +325,115 @@ def test_shaping_costs_follow_table5():
     b1.reset(), b2.reset()
     o1, o2 = b1.rollout(300), b2.rollout(300)
     assert o1["reward"].tobytes() == o2["reward"].tobytes()
+
+
+# --- KeyCorridor S{s}R{R} (Table 8) --------------------------------------------
+
+KC_IDS = [(7, 0), (7, 1), (7, 2), (10, 2), (13, 2), (16, 2), (19, 0), (10, 1)]  # S3R1..S3R3, S4R3, S5R3, S6R3, ...
+
+
+def _kc_geometry(S, variant):
+    s = (S - 1) // 3 + 1
+    R = variant + 1
+    return s, R, (s - 1) * R + 1
+
+
+@pytest.mark.parametrize("S,variant", KC_IDS)
+def test_keycorridor_layouts(S, variant):
+    s, R, H = _kc_geometry(S, variant)
+    xl, xr = s - 1, 2 * (s - 1)
+    for seed in range(12):
+        e = O.Env(O.KEYCORRIDOR, S, seed=seed, variant=variant, env_index=seed)
+        ent, col, st = e.grid()
+        assert e.s.max_steps == 30 * s * s
+        assert (ent[H - 1:, :] == 2).all()  # the rows below the rooms are wall
+        assert (ent[:, 0] == 2).all() and (ent[:, S - 1] == 2).all() and (ent[0, :] == 2).all()
+        # horizontal room walls, open inside the corridor
+        for j in range(1, R):
+            y = j * (s - 1)
+            assert (ent[y, :xl + 1] == 2).all() and (ent[y, xr:] == 2).all() and (ent[y, xl + 1:xr] == 1).all()
+        doors = _doors(ent, col, st)
+        assert len(doors) == 2 * R
+        locked = [d for d in doors if d[3] == 2]
+        assert len(locked) == 1 and all(d[3] in (1, 2) for d in doors)
+        for side_x in (xl, xr):
+            for j in range(R):
+                rows = [y for x, y, _, _ in doors if x == side_x and j * (s - 1) < y < (j + 1) * (s - 1)]
+                assert len(rows) == 1
+        # walls of the corridor hold only the doors
+        for x in (xl, xr):
+            for y in range(H):
+                assert ent[y, x] in (2, 4)
+        lx, ly, lc, _ = locked[0]
+        (gy, gx), = np.argwhere(ent == 8)
+        (ky, kx), = np.argwhere(ent == 5)
+        assert col[ky, kx] == lc
+        # the goal is in the locked door's room, the key on the other side
+        assert (gx < xl) == (lx == xl) and (gy - 1) // (s - 1) == (ly - 1) // (s - 1)
+        assert (kx < xl) != (gx < xl) and 0 < ky < H - 1
+        # side room interiors are empty but for the goal and key
+        assert xl < e.s.ax < xr and 0 < e.s.ay < H - 1 and ent[e.s.ay, e.s.ax] == 1
+
+
+def test_keycorridor_draws_cover_their_ranges():
+    S, variant = 10, 2
+    s, R, H = _kc_geometry(S, variant)
+    seen = {"door_rows": set(), "colours": set(), "goal_room": set(), "key_room": set(), "agent": set(), "dir": set()}
+    for ep in range(2000):
+        e = O.Env(O.KEYCORRIDOR, S, seed=4, variant=variant)
+        e.reset(ep)
+        ent, col, st = e.grid()
+        for x, y, c, _ in _doors(ent, col, st):
+            seen["door_rows"].add((x, y))
+            seen["colours"].add(c)
+        (gy, gx), = np.argwhere(ent == 8)
+        (ky, kx), = np.argwhere(ent == 5)
+        seen["goal_room"].add((gx > s, (gy - 1) // (s - 1), gx, gy))
+        seen["key_room"].add((kx > s, (ky - 1) // (s - 1)))
+        seen["agent"].add((e.s.ax, e.s.ay))
+        seen["dir"].add(e.s.dir)
+    assert len(seen["door_rows"]) == 2 * R * (s - 2)
+    assert seen["colours"] == set(range(6)) and seen["dir"] == {0, 1, 2, 3}
+    assert len({g[:2] for g in seen["goal_room"]}) == 2 * R and len(seen["goal_room"]) == 2 * R * (s - 2) ** 2
+    assert len(seen["key_room"]) == 2 * R
+    assert len(seen["agent"]) == (s - 2) * (H - 2)
+
+
+@pytest.mark.parametrize("S,variant", [(7, 0), (7, 1), (10, 2)])
+def test_keycorridor_views_equal_those_of_the_unpadded_grid(S, variant):
+    """The square holding a non-square KeyCorridor gives the views of the
+    H x S grid itself (independent window model, outside = wall), for every
+    pose of the agent in the corridor."""
+    s, R, H = _kc_geometry(S, variant)
+    e = O.Env(O.KEYCORRIDOR, S, seed=9, variant=variant)
+    ent, col, st = e.grid()
+    for y in range(1, H - 1):
+        for x in range(s, 2 * s - 2):
+            for d in range(4):
+                e.set_agent(x, y, d)
+                want = M.observe(ent[:H], col[:H], st[:H], x, y, d)
+                np.testing.assert_array_equal(e.obs(), want)
+
+
+@pytest.mark.parametrize("S,variant,seed", [(7, 0, 0), (7, 1, 1), (7, 2, 2), (10, 1, 3)])
+def test_keycorridor_bfs_plans_fetch_the_key_and_reach_the_goal(S, variant, seed):
+    e = O.Env(O.KEYCORRIDOR, S, seed=seed, variant=variant)
+    ent, col, st = e.grid()
+    cells = tuple((int(ent[y, x]), int(col[y, x]), int(st[y, x])) for y in range(S) for x in range(S))
+    plan = M.bfs_goal((e.s.ax, e.s.ay, e.s.dir, None, cells), S, S, max_depth=60)
+    assert plan is not None and 3 in plan and 5 in plan  # a pickup and a toggle on the way
+    for i, a in enumerate(plan):
+        r, te, tr = e.step(a)
+        if i < len(plan) - 1:
+            assert (r, te) == (0.0, 0)
+    assert (r, te) == (1.0, 1) and e.s.t == len(plan)
+
+
+def test_keycorridor_sizes():
+    for S in (7, 10, 13, 16, 19):
+        assert O.max_variant(O.KEYCORRIDOR, S) == 2
+    for S in (5, 6, 8, 9, 11, 12, 18):
+        with pytest.raises(ValueError):
+            O.Env(O.KEYCORRIDOR, S)
+    with pytest.raises(ValueError):
+        O.Env(O.KEYCORRIDOR, 7, variant=3)
