@@ -60,15 +60,19 @@ enum {
 
 /* environment families of Table 8; the crossings take their number of
  * rivers as the descriptor's variant (0..nx_max_variant), DistShift its
- * layout (variant 0: DistShift1, 1: DistShift2).  GoToDoor has a
+ * layout (variant 0: DistShift1, 1: DistShift2).  KeyCorridor S{s}R{R} has
+ * size 3(s-1)+1 (7, 10, 13, 16, 19 for s = 3..7) and variant R - 1 (0..2);
+ * its grid of (s-1)R+1 rows is held in the square with wall rows below,
+ * which leaves the first-person views and the rules those of the smaller
+ * grid (the fully observable views show the wall rows).  GoToDoor has a
  * mission (the colour of one of its four doors, nx_out.mission) and ends
  * with reward 1 when the done action is taken facing that door
  * (on_door_done, Tables 5 and 6). */
 enum {
     NX_EMPTY = 0, NX_DOORKEY = 1, NX_FOURROOMS = 2, NX_LAVAGAP = 3, NX_DYNOBS = 4, NX_EMPTY_RANDOM = 5,
-    NX_LAVA_CROSSING = 6, NX_SIMPLE_CROSSING = 7, NX_GOTODOOR = 8, NX_DISTSHIFT = 9
+    NX_LAVA_CROSSING = 6, NX_SIMPLE_CROSSING = 7, NX_GOTODOOR = 8, NX_DISTSHIFT = 9, NX_KEYCORRIDOR = 10
 };
-#define NX_N_FAMILIES 10
+#define NX_N_FAMILIES 11
 #define NX_NO_MISSION 255  /* the mission byte of a family without one */
 /* observation bit flags (Table 4): RGB and RGB_FULL need the sprite atlas */
 enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2, NX_OBS_RGB_FULL = 4 };
@@ -96,7 +100,8 @@ typedef struct nx_server nx_server;
 
 /* One environment's shape: family, square grid side (height == width,
  * 5..19), timeout T (<= 0: the family default: DoorKey 10 S^2, FourRooms
- * 100, GoToDoor 5 S^2, the others 4 S^2; at most 65535), and the family's variant (the number
+ * 100, GoToDoor 5 S^2, KeyCorridor 30 s^2 for room side s, the others 4 S^2;
+ * at most 65535), and the family's variant (the number
  * of rivers of a crossing family, 0 otherwise). */
 typedef struct {
     int32_t family, height, width, max_steps, variant;
@@ -175,7 +180,8 @@ typedef struct {
 void nx_options_default(nx_options* opts);
 /* Largest valid variant of a family at a size (the number of candidate
  * rivers of a crossing family: rows and columns 2, 4, .., size-3; 1 for
- * DistShift), 0 for the other families. */
+ * DistShift; 2 for KeyCorridor), 0 for the other families, -1 where the
+ * family has no grid of that size (KeyCorridor off 7, 10, 13, 16, 19). */
 int32_t nx_max_variant(int32_t family, int32_t size);
 
 /* nx_create: one family and size for all n_envs environments (the paper's

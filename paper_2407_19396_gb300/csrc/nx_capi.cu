@@ -129,6 +129,10 @@ int nx_default_max_steps(int family, int size)
     case NX_DOORKEY: return 10 * size * size;
     case NX_FOURROOMS: return 100;
     case NX_GOTODOOR: return 5 * size * size;
+    case NX_KEYCORRIDOR: {
+        const int s = (size - 1) / 3 + 1;  // room side
+        return 30 * s * s;
+    }
     default: return 4 * size * size;
     }
 }
@@ -137,6 +141,7 @@ int32_t nx_max_variant(int32_t family, int32_t size)
 {
     if (size < NX_MIN_SIZE || size > NX_MAX_SIZE) return 0;
     if (family == NX_DISTSHIFT) return 1;
+    if (family == NX_KEYCORRIDOR) return (size >= 7 && size % 3 == 1) ? 2 : -1;
     if (family != NX_LAVA_CROSSING && family != NX_SIMPLE_CROSSING) return 0;
     return 2 * ((size - 3) / 2);  // rows and columns 2, 4, .., size - 3
 }

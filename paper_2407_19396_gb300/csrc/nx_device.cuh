@@ -318,6 +318,51 @@ __device__ __noinline__ void crossing_layout(const Grp<G>& grp, uint8_t* g, int 
         }
 }
 
+// L10 KeyCorridor S{s}R{R} (variant R - 1): a 3 x R block of rooms of side s
+// sharing walls in the S x S grid, S = 3(s-1)+1; rows from H - 1 = (s-1)R on
+// are wall (cells outside a grid read as wall, so views and rules are those
+// of the H x S grid).  The middle column of rooms is one open corridor; each
+// side room has a door in its corridor wall; the goal's room is locked and the
+// key of its colour lies in a room on the other side.  Draw k: 0..2R-1 the
+// door rows (left rooms top to bottom, then right), 2R..4R-1 their colours,
+// then the goal's side and room row, the key's room row, the goal cell, the
+// key cell and the agent's corridor cell and direction; the rooms and the
+// corridor are empty when their cells are drawn, so the k-th free cell is a
+// closed form (row-major).  Out of line like the crossings; returns the
+// agent as x | y << 8 | dir << 16.
+template <int G>
+__device__ __noinline__ uint32_t keycorridor_layout(const Grp<G>& grp, uint8_t* g, int S, int variant, uint64_t seed,
+                                                    uint32_t key_env, uint32_t episode)
+{
+    const int s = (S - 1) / 3 + 1, R = variant + 1, H = (s - 1) * R + 1, xl = s - 1, xr = 2 * (s - 1), w = s - 2;
+    auto dr = [&](int k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, (uint32_t)k); };
+    for (int c = grp.lane; c < S * S; c += G) {
+        const int y = c / S, x = c - y * S;
+        bool wall = y >= H - 1 || y == 0 || x == 0 || x == S - 1 || x == xl || x == xr;
+        if (y % (s - 1) == 0 && !(x > xl && x < xr)) wall = true;
+        g[c] = (uint8_t)(wall ? C_WALL : C_EMPTY);
+    }
+    const int gside = bounded(dr(4 * R), 2u), grow = bounded(dr(4 * R + 1), (uint32_t)R);
+    const int krow = bounded(dr(4 * R + 2), (uint32_t)R);
+    grp.sync();
+    for (int j = grp.lane; j < 2 * R; j += G) {  // door j: side j / R, room row j % R
+        const int side = j >= R, row = j - side * R;
+        const int y = row * (s - 1) + 1 + bounded(dr(j), (uint32_t)w);
+        const uint32_t c = bounded(dr(2 * R + j), 6u);
+        g[y * S + (side ? xr : xl)] = (uint8_t)make_code((side == gside && row == grow) ? K_DOOR_LOCKED : K_DOOR_CLOSED, c);
+    }
+    if (grp.lane == 0) {
+        const uint32_t lock_col = bounded(dr(2 * R + gside * R + grow), 6u);
+        const int gi = bounded(dr(4 * R + 3), (uint32_t)(w * w)), ki = bounded(dr(4 * R + 4), (uint32_t)(w * w));
+        const int gx0 = gside == 0 ? 1 : xr + 1, kx0 = gside == 0 ? xr + 1 : 1;
+        g[(grow * (s - 1) + 1 + gi / w) * S + gx0 + gi % w] = (uint8_t)C_GOAL;
+        g[(krow * (s - 1) + 1 + ki / w) * S + kx0 + ki % w] = (uint8_t)make_code(K_KEY, lock_col);
+    }
+    const int ai = bounded(dr(4 * R + 5), (uint32_t)(w * (H - 2)));
+    const int ax = xl + 1 + ai % w, ay = 1 + ai / w;
+    return (uint32_t)ax | ((uint32_t)ay << 8) | ((uint32_t)bounded(dr(4 * R + 6), 4u) << 16);
+}
+
 // ---------------------------------------------------------------------------
 // Layout generators of the Table 8 families.  Draw k of a reset is
 // draw(seed, env, episode, 0, PURPOSE_LAYOUT, k); the k-th free cell is
@@ -356,7 +401,7 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
                 [&](uint32_t k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k); });
     grp.sync();
     const int goal = family == NX_DISTSHIFT ? S + (S - 2) : (S - 2) * S + (S - 2);
-    if (family != NX_FOURROOMS && family != NX_GOTODOOR) {
+    if (family != NX_FOURROOMS && family != NX_GOTODOOR && family != NX_KEYCORRIDOR) {
         if (grp.lane == 0) g[goal] = (uint8_t)C_GOAL;
     }
     if (family == NX_DOORKEY) {
@@ -447,6 +492,11 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
             g[S + x] = (uint8_t)C_LAVA;
             g[r2 * S + x] = (uint8_t)C_LAVA;
         }
+    } else if (family == NX_KEYCORRIDOR) {
+        const uint32_t ag = keycorridor_layout(grp, g, S, variant, seed, key_env, episode);
+        a.x = ag & 0xFF;
+        a.y = (ag >> 8) & 0xFF;
+        a.dir = ag >> 16;
     } else if (family == NX_LAVA_CROSSING || family == NX_SIMPLE_CROSSING) {
         crossing_layout(grp, g, S, family, variant, seed, key_env, episode);
     } else if (family == NX_DYNOBS) {

@@ -96,6 +96,7 @@ nx_status nx_rollout_noalloc(int32_t family, int32_t size, int32_t n_envs, uint6
 {
     if (family < NX_EMPTY || family >= NX_N_FAMILIES) return nx_fail(nullptr, NX_E_INVAL, "unknown family");
     if (size < NX_MIN_SIZE || size > NX_MAX_SIZE) return nx_fail(nullptr, NX_E_INVAL, "grid size must be in 5..19");
+    if (nx_max_variant(family, size) < 0) return nx_fail(nullptr, NX_E_INVAL, "the family has no grid of this size");
     if (n_envs < 1) return nx_fail(nullptr, NX_E_INVAL, "n_envs must be >= 1");
     if (n_steps < 0) return nx_fail(nullptr, NX_E_INVAL, "n_steps must be >= 0");
     if (act_mode != NX_ACT_RANDOM && act_mode != NX_ACT_BUFFER) return nx_fail(nullptr, NX_E_INVAL, "unknown act_mode");

@@ -21,8 +21,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libnavixgb.so")
 NX_OK, NX_PENDING = 0, 1
 NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET, NX_E_STATE = -1, -2, -3, -4, -5, -6, -7
 (NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS, NX_EMPTY_RANDOM, NX_LAVA_CROSSING, NX_SIMPLE_CROSSING,
- NX_GOTODOOR, NX_DISTSHIFT) = range(10)
-NX_N_FAMILIES = 10
+ NX_GOTODOOR, NX_DISTSHIFT, NX_KEYCORRIDOR) = range(11)
+NX_N_FAMILIES = 11
 NX_NO_MISSION = 255
 NX_OBS_SYM, NX_OBS_RGB, NX_OBS_RGB_FULL = 1, 2, 4
 NX_ACT_BUFFER, NX_ACT_RANDOM = 0, 1

@@ -46,7 +46,8 @@ def test_status_strings_and_creation_errors_without_gpu(built):
     L = nx.lib()
     assert L.nx_status_str(nx.NX_E_BUDGET).decode() == "request exceeds the HBM budget"
     # argument validation happens before any device call
-    for fam, size, n in [(nx.NX_N_FAMILIES, 5, 4), (-1, 5, 4), (0, 4, 4), (0, 20, 4), (0, 5, 0)]:
+    for fam, size, n in [(nx.NX_N_FAMILIES, 5, 4), (-1, 5, 4), (0, 4, 4), (0, 20, 4), (0, 5, 0), (nx.NX_KEYCORRIDOR, 8, 4),
+                          (nx.NX_KEYCORRIDOR, 5, 4)]:
         with pytest.raises(nx.NavixError) as ei:
             nx.nx_create(fam, size, n, 0)
         assert ei.value.status == nx.NX_E_INVAL

@@ -40,7 +40,9 @@ ALL_FAMILIES = [(O.EMPTY, 5, 0), (O.EMPTY, 8, 0), (O.EMPTY, 16, 0), (O.DOORKEY, 
                 (O.EMPTY_RANDOM, 5, 0), (O.EMPTY_RANDOM, 16, 0), (O.LAVA_CROSSING, 9, 1), (O.LAVA_CROSSING, 9, 3),
                 (O.LAVA_CROSSING, 11, 5), (O.SIMPLE_CROSSING, 9, 2), (O.SIMPLE_CROSSING, 19, 16),
                 (O.SIMPLE_CROSSING, 5, 2), (O.LAVA_CROSSING, 13, 0), (O.GOTODOOR, 5, 0), (O.GOTODOOR, 8, 0),
-                (O.GOTODOOR, 19, 0), (O.DISTSHIFT, 6, 0), (O.DISTSHIFT, 8, 1), (O.DISTSHIFT, 5, 1)]
+                (O.GOTODOOR, 19, 0), (O.DISTSHIFT, 6, 0), (O.DISTSHIFT, 8, 1), (O.DISTSHIFT, 5, 1),
+                (O.KEYCORRIDOR, 7, 0), (O.KEYCORRIDOR, 7, 1), (O.KEYCORRIDOR, 7, 2), (O.KEYCORRIDOR, 10, 2),
+                (O.KEYCORRIDOR, 16, 2), (O.KEYCORRIDOR, 19, 1)]
 
 
 @pytest.mark.parametrize("family,size,variant", ALL_FAMILIES)
@@ -352,7 +354,8 @@ def test_shaping_costs(lanes, envs, reward_mode):
 NEW_FAMILIES = [(O.EMPTY_RANDOM, 6, 0, 0), (O.LAVA_CROSSING, 9, 0, 1), (O.LAVA_CROSSING, 9, 0, 3),
                 (O.LAVA_CROSSING, 11, 0, 5), (O.SIMPLE_CROSSING, 9, 0, 2), (O.SIMPLE_CROSSING, 11, 0, 5),
                 (O.EMPTY_RANDOM, 16, 0, 0), (O.SIMPLE_CROSSING, 19, 0, 9), (O.GOTODOOR, 6, 0, 0),
-                (O.DISTSHIFT, 6, 0, 0), (O.DISTSHIFT, 8, 0, 1)]
+                (O.DISTSHIFT, 6, 0, 0), (O.DISTSHIFT, 8, 0, 1), (O.KEYCORRIDOR, 7, 0, 0), (O.KEYCORRIDOR, 7, 0, 1),
+                (O.KEYCORRIDOR, 13, 0, 2)]
 
 
 @pytest.mark.parametrize("lanes,envs,staging", [(1, 64, 2), (8, 16, 1), (32, 4, 1)])
@@ -376,7 +379,8 @@ def test_fully_observable_views(lanes, envs, staging):
     """symbolic / categorical / categorical_first_person (Table 4) of a mixed-size
     batch, padded to the largest grid, every step."""
     nx = nxmod()
-    descs = mixed_descs(90, [(O.DOORKEY, 8), (O.FOURROOMS, 11), (O.SIMPLE_CROSSING, 9, 0, 3), (O.DYNOBS, 6)])
+    descs = mixed_descs(90, [(O.DOORKEY, 8), (O.FOURROOMS, 11), (O.SIMPLE_CROSSING, 9, 0, 3), (O.DYNOBS, 6),
+                             (O.KEYCORRIDOR, 10, 0, 1), (O.GOTODOOR, 6)])
     env = nx.Env(descs=descs, seed=51, group_lanes=lanes, envs_per_cta=envs, staging=staging, autotune=False,
                  steps_per_launch=40, obs_full=True, obs_cat=True, obs_cat_fp=True)
     r = env.reset()

@@ -111,7 +111,8 @@ def test_new_families_served_like_the_oracle():
     from paper_2407_19396_gb300 import navixgb as nx
 
     reqs = [(O.LAVA_CROSSING, 11, 40, 120, 1, 5), (O.SIMPLE_CROSSING, 9, 17, 90, 2, 3), (O.EMPTY_RANDOM, 8, 33, 70, 3, 0),
-            (O.GOTODOOR, 6, 29, 150, 4, 0), (O.DISTSHIFT, 8, 21, 100, 5, 1)]
+            (O.GOTODOOR, 6, 29, 150, 4, 0), (O.DISTSHIFT, 8, 21, 100, 5, 1),
+            (O.KEYCORRIDOR, 10, 19, 130, 6, 2)]
     srv = nx.Server(budget_bytes=64 << 20, steps_per_launch=32)
     tickets = [srv.submit(f, s_, n, h, seed, variant=v) for f, s_, n, h, seed, v in reqs]
     res = [srv.wait(t, timeout_s=120.0) for t in tickets]
