@@ -567,7 +567,12 @@ constexpr OccTable make_occ_table()
 }
 __device__ const OccTable occ_table = make_occ_table();
 
-__device__ __forceinline__ uint64_t occlusion(uint64_t tmask)
+// Rows are looked up in `tab` (the table staged in shared memory by groups of
+// eight or more lanes), or in the global table (L1-cached) when tab is null;
+// G = 1 evaluates occ_row directly, which measures faster there than either
+// table (its single thread per env is bound by the latency of the chain).
+template <int G>
+__device__ __forceinline__ uint64_t occlusion(uint64_t tmask, const uint16_t* tab)
 {
     uint64_t vis = 0;
     uint32_t seed = 1u << 3;
@@ -575,7 +580,11 @@ __device__ __forceinline__ uint64_t occlusion(uint64_t tmask)
 #pragma unroll 1
     for (int j = 6; j >= 0 && seed != 0u; --j) {
         const uint32_t t = (uint32_t)(tmask >> (7 * j)) & 0x7Fu;
-        const uint32_t e = __ldg(&occ_table.v[(seed << 7) | t]);
+        uint32_t e;
+        if constexpr (G == 1)
+            e = occ_row(seed, t);
+        else
+            e = tab ? (uint32_t)tab[(seed << 7) | t] : (uint32_t)__ldg(&occ_table.v[(seed << 7) | t]);
         vis |= (uint64_t)(e & 0x7Fu) << (7 * j);
         seed = e >> 7;
     }
@@ -654,12 +663,25 @@ struct ViewOut<1> {
     uint32_t sw[37];  // stream words of the 147-byte record
 };
 
+// Byte mask of the four low bits of m (bit i set -> byte i = 0xFF).
+__device__ __forceinline__ uint32_t byte_mask4(uint32_t m) { return ((m * 0x00204081u) & 0x01010101u) * 0xFFu; }
+
 template <int G>
 __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g, int S, const AgentReg& a,
-                                            const uint32_t* dec, ViewOut<G>& out, uint16_t* tiles)
+                                            const uint32_t* dec, const uint16_t* occ, ViewOut<G>& out, uint16_t* tiles)
 {
     const ViewGeom v = view_geom(a, S);
     if constexpr (G == 1) {
+        // Strided gather: cell (vx, vy) is read at g[idx0 + vx dR - vy dF]
+        // without a bounds test (guard bytes around the grid region keep every
+        // read inside shared memory); cells outside the grid are replaced by
+        // grey walls four at a time with byte masks of the in-grid bits.
+        constexpr uint32_t kWall4 = C_WALL * 0x01010101u;
+        const uint8_t* p0 = g + v.idx0;
+        uint64_t inmask = 0;
+#pragma unroll
+        for (int vy = 0; vy < 7; ++vy)
+            inmask |= (uint64_t)(((v.rowmask >> vy) & 1u) ? v.colmask : 0u) << (7 * vy);
         uint32_t packed[13];
         uint64_t tmask = 0;
 #pragma unroll
@@ -668,15 +690,19 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int c = 4 * w + b;
-                if (c < 49) word |= view_code(g, v, a, c % 7, c / 7) << (8 * b);
+                if (c < 49 && c != 45) word |= (uint32_t)p0[(c % 7) * v.dR - (c / 7) * v.dF] << (8 * b);
             }
+            const uint32_t m = byte_mask4((uint32_t)(inmask >> (4 * w)) & 15u);
+            word = (word & m) | (kWall4 & ~m);
+            if (w == 11)  // the agent's cell, c = 45: what it carries, else empty
+                word = (word & 0xFFFF00FFu) | ((a.carry ? a.carry : (uint32_t)C_EMPTY) << 8);
+            if (w == 12) word &= 0xFFu;  // c = 48 only
             packed[w] = word;
-            // transparency bits of these four cells: the complement of their opaque bits
             const uint32_t opq = (uint32_t)(((word & 0x80808080u) * 0x00204081u) >> 28);
             tmask |= (uint64_t)(~opq & 0xFu) << (4 * w);
         }
         tmask &= (1ull << 49) - 1ull;
-        const uint64_t vis = occlusion(tmask);
+        const uint64_t vis = occlusion<G>(tmask, occ);
         uint32_t tri[49];
 #pragma unroll
         for (int c = 0; c < 49; ++c) {
@@ -706,7 +732,7 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
             const uint32_t bits = grp.ballot(c < 49 && !(cd & OPAQUE));
             tmask |= (uint64_t)bits << (k * G);
         }
-        const uint64_t vis = occlusion(tmask);
+        const uint64_t vis = occlusion<G>(tmask, occ);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int c = k * G + grp.lane;

@@ -25,6 +25,12 @@ namespace nxk {
 
 using namespace nxd;
 
+// Guard bytes before and after the grid region of one-lane-per-env blocks:
+// their view gather reads every view cell without a bounds test, up to six
+// rows and six columns beyond a grid (at most 6 * 19 + 6 bytes before or
+// after it); reads that land in a neighbour's grid or a guard are replaced by
+// walls.
+constexpr int kGridGuard = 128;
 constexpr int kMaxThreads = 256;
 
 __host__ __device__ __forceinline__ int align16(int v) { return (v + 15) & ~15; }
@@ -205,6 +211,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t s_dec[256];  // cell code -> observation triple
+    // the occlusion table in shared memory for groups of 8 or more lanes (the
+    // narrow groups run many more envs per block, whose grids need the space)
+    constexpr bool kSmemOcc = G >= 8;
+    __shared__ __align__(16) uint16_t s_occ[kSmemOcc ? (1 << 14) : 8];
     const int E = p.envs_per_cta;
     const int phases = p.phases > 1 ? 2 : 1;
     const int tid = threadIdx.x, nthreads = blockDim.x, lane32 = tid & 31, warp = tid >> 5;
@@ -212,15 +222,23 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     const int whalf = (epw + phases - 1) / phases;      // envs staged per part
     const int wbytes = align16(whalf * NX_OBS_SYM_BYTES + 16);
     const int wenv0 = warp * epw;                       // the warp's first env slot
-    uint8_t* sgrid = smem;
-    uint8_t* wstage = smem + E * p.cell_stride + warp * wbytes;
-    uint16_t* stiles = reinterpret_cast<uint16_t*>(smem + E * p.cell_stride + (nthreads >> 5) * wbytes);
+    // One lane per env reads its view cells without bounds tests
+    // (render_view), so guards pad its grid region on both sides.
+    constexpr bool kGuard = G == 1;
+    const int cs = p.cell_stride;  // bytes per env slot
+    const int grid_bytes = kGuard ? E * cs + 2 * kGridGuard : E * cs;
+    uint8_t* sgrid = smem + (kGuard ? kGridGuard : 0);
+    uint8_t* wstage = smem + grid_bytes + warp * wbytes;
+    uint16_t* stiles = reinterpret_cast<uint16_t*>(smem + grid_bytes + (nthreads >> 5) * wbytes);
     const int FR = p.rgb_full_side;  // full-view RGB tile buffer: E x FR x FR ids after the egocentric ones
     uint16_t* sfull = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(stiles) + align16(E * 49 * 2));
     const int gi = tid / G;
     const Grp<G> grp(tid);
-    uint8_t* mygrid = sgrid + gi * p.cell_stride;
+    uint8_t* mygrid = sgrid + gi * cs;
     for (int i = tid; i < 256; i += nthreads) s_dec[i] = cell_triple((uint32_t)i);
+    if constexpr (kSmemOcc)
+        for (int i = tid; i < (1 << 14) / 8; i += nthreads)
+            reinterpret_cast<uint4*>(s_occ)[i] = __ldg(reinterpret_cast<const uint4*>(occ_table.v) + i);
 
     for (int it = blockIdx.x; it < p.n_items; it += gridDim.x) {
         const nx_item item = p.items[it];
@@ -268,7 +286,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             for (int i = tid; i < n * HW; i += nthreads) {
                 const int e = i / HW, c = i - e * HW;
                 const uint8_t* b = src + (size_t)e * 3 * HW;
-                sgrid[e * p.cell_stride + c] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
+                sgrid[e * cs + c] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
+
             }
             if (active) load_agent(p.agents + env, a);
         }
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     const int owner = ((tid & ~31) + L) / G;  // group (env slot) of lane L
                     AgentReg na;
                     const bool ok =
-                        reset_layout_warp(sgrid + owner * p.cell_stride, S, family, n_balls, variant, seed, k, ep, na);
+                        reset_layout_warp(sgrid + owner * cs, S, family, n_balls, variant, seed, k, ep, na);
                     if (!ok && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
                     if (gi == owner) {
                         na.invalid = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
@@ -355,7 +374,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                              time_cost, reward, term, trunc, p.ctl);
                 }
                 grp.sync();
-                render_view(grp, mygrid, S, a, s_dec, vo, RGB && obs_rgb ? stiles + gi * 49 : nullptr);
+                render_view(grp, mygrid, S, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
+                            RGB && obs_rgb ? stiles + gi * 49 : nullptr);
                 if (FULL && (obs_full || obs_cat || obs_rgb_full)) {
                     // fully observable views: every cell's triple, the agent's
                     // cell holding (agent, red, direction), zero beyond the grid;
@@ -450,7 +470,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             uint8_t* dst = p.grids + item.grid_offset;
             for (int i = tid; i < n * HW; i += nthreads) {
                 const int e = i / HW, c = i - e * HW;
-                const uint32_t code = sgrid[e * p.cell_stride + c];
+                const uint32_t code = sgrid[e * cs + c];
                 uint8_t* b = dst + (size_t)e * 3 * HW;
                 b[c] = (uint8_t)cell_ent(code);
                 b[HW + c] = (uint8_t)cell_col(code);
