@@ -275,7 +275,7 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
         return nx_fail(nullptr, NX_E_INVAL, "state pool larger than 4 GiB");
     }
     env->grid_pool = off;
-    env->cell_stride = (max_cells + 15) & ~15;
+    env->cell_stride = nx_cell_stride(max_cells);
     env->n_families = 0;
     for (bool b : seen) env->n_families += b ? 1 : 0;
 

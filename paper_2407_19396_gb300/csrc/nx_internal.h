@@ -96,7 +96,7 @@ struct nx_kparams {
     nx_req* reqs;
     nx_ctl* ctl;
     const uint8_t* atlas;
-    int32_t cell_stride;   // smem bytes per env grid (>= max size^2, multiple of 16)
+    int32_t cell_stride;   // smem bytes per env grid (nx_cell_stride: >= max size^2, an odd number of words)
     int32_t envs_per_cta;
     int32_t reset_all;     // 1: start every env at episode 0 and emit its observation (no steps)
     int32_t phases;        // symbolic staging parts per step (1 or 2)
@@ -113,6 +113,14 @@ struct nx_launch_shape {
     int rgb_full_side = 0;  // reserve smem for full-view RGB tile ids of this grid side
     bool full = false;      // the instantiation that writes the fully observable views
 };
+// Shared-memory bytes per env grid for grids of up to max_cells cells: a
+// whole number of 4-byte words, and an odd one, so that the grids of the 32
+// envs a warp steps one lane each start in 32 different banks.
+inline int nx_cell_stride(int max_cells)
+{
+    const int s = (max_cells + 3) & ~3;
+    return ((s >> 2) & 1) ? s : s + 4;
+}
 int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride);
 int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err);  // resident CTAs on the device
 int nx_launch_step_kernel(const nx_launch_shape& s, const nx_kparams& p, int grid, void* stream);

@@ -53,7 +53,7 @@ int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride)
     const int epw = 32 / s.group_lanes, warps = E * s.group_lanes / 32;
     const int whalf = s.phases > 1 ? (epw + 1) / 2 : epw;
     // one lane per env pads its grid region with guard bytes (see nx_step_kernel)
-    const int grid_bytes = s.group_lanes == 1 ? E * cell_stride + 2 * kGridGuard : E * cell_stride;
+    const int grid_bytes = align16(s.group_lanes == 1 ? E * cell_stride + 2 * kGridGuard : E * cell_stride);
     int b = grid_bytes + warps * align16(whalf * NX_OBS_SYM_BYTES + 16);
     if (s.rgb) b += align16(E * 49 * 2) + align16(E * s.rgb_full_side * s.rgb_full_side * 2);
     return b;

@@ -457,7 +457,7 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
         delete s;
         return nx_fail(nullptr, NX_E_INVAL, "unsupported launch shape");
     }
-    s->cell_stride = (NX_MAX_SIZE * NX_MAX_SIZE + 15) & ~15;
+    s->cell_stride = nx_cell_stride(NX_MAX_SIZE * NX_MAX_SIZE);
     int dev = 0, err = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     // (render_view), so guards pad its grid region on both sides.
     constexpr bool kGuard = G == 1;
     const int cs = p.cell_stride;  // bytes per env slot
-    const int grid_bytes = kGuard ? E * cs + 2 * kGridGuard : E * cs;
+    const int grid_bytes = align16(kGuard ? E * cs + 2 * kGridGuard : E * cs);  // the staging after it is 16-aligned
     uint8_t* sgrid = smem + (kGuard ? kGridGuard : 0);
     uint8_t* wstage = smem + grid_bytes + warp * wbytes;
     uint16_t* stiles = reinterpret_cast<uint16_t*>(smem + grid_bytes + (nthreads >> 5) * wbytes);
