@@ -163,6 +163,22 @@ __device__ __forceinline__ void coop_copy(uint8_t* dst, const uint8_t* src, int 
     for (int i = tid; i < tail; i += nthreads) dst[head + body + i] = src[head + body + i];
 }
 
+// Bulk (TMA) copy of a staged block from shared to global memory: the
+// writing lanes fence their generic-proxy stores (bulk_fence_smem) and meet
+// at a warp barrier, one lane issues the copy; before the buffer is written
+// again that lane waits until the copy has read it, and before the block's
+// work item ends until every copy has completed.
+__device__ __forceinline__ void bulk_fence_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_copy_s2g(void* gdst, const void* ssrc, uint32_t bytes)
+{
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(ssrc));
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Writes n envs' 224x224x3 images: 16-byte chunk r of an image is pixel row
 // r / 42, bytes 16 (r % 42) .. of it, i.e. view column (r % 42) / 6, part
 // (r % 42) % 6 of that tile's 96-byte row.
@@ -214,6 +230,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     // the occlusion table in shared memory for groups of 8 or more lanes (the
     // narrow groups run many more envs per block, whose grids need the space)
     constexpr bool kSmemOcc = G >= 8;
+    // narrow groups (at least 8 envs per warp) store their staged symbolic
+    // records with bulk copies; wider ones with the warp's vector copy
+    constexpr bool kBulk = G <= 4;
     __shared__ __align__(16) uint16_t s_occ[kSmemOcc ? (1 << 14) : 8];
     const int E = p.envs_per_cta;
     const int phases = p.phases > 1 ? 2 : 1;
@@ -422,6 +441,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 const int lo = wenv0 + ph * whalf, hi = min(n, min(wenv0 + epw, lo + whalf));
                 uint8_t* dst = sym_dst ? sym_dst + (size_t)lo * NX_OBS_SYM_BYTES : nullptr;
                 uint8_t* stage = wstage + ((uint32_t)(uintptr_t)dst & 15u);
+                if constexpr (kBulk) {
+                    // the previous bulk copy out of this buffer must have read it
+                    if (lane32 == 0) bulk_wait_read();
+                    __syncwarp();
+                }
                 if (active && gi >= lo && gi < hi) {
                     uint8_t* my_sym = stage + (gi - lo) * NX_OBS_SYM_BYTES;
                     write_view(grp, vo, my_sym);
@@ -443,9 +467,25 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                         }
                     }
                 }
-                __syncwarp();
-                if (dst && hi > lo) coop_copy(dst, stage, (hi - lo) * NX_OBS_SYM_BYTES, lane32, 32);
-                __syncwarp();
+                if constexpr (kBulk) {
+                    // the 16-byte-aligned body goes by one bulk copy, the
+                    // ragged head and tail by plain stores
+                    bulk_fence_smem();
+                    __syncwarp();
+                    if (dst && hi > lo) {
+                        const int nbytes = (hi - lo) * NX_OBS_SYM_BYTES;
+                        const int head = min(nbytes, (int)((16u - ((uint32_t)(uintptr_t)dst & 15u)) & 15u));
+                        const int body = (nbytes - head) & ~15;
+                        const int tail = nbytes - head - body;
+                        if (lane32 < head) dst[lane32] = stage[lane32];
+                        if (lane32 < tail) dst[head + body + lane32] = stage[head + body + lane32];
+                        if (lane32 == 0 && body > 0) bulk_copy_s2g(dst + head, stage + head, (uint32_t)body);
+                    }
+                } else {
+                    __syncwarp();
+                    if (dst && hi > lo) coop_copy(dst, stage, (hi - lo) * NX_OBS_SYM_BYTES, lane32, 32);
+                    __syncwarp();
+                }
             }
             if (RGB && (obs_rgb || obs_rgb_full)) {
                 __syncthreads();
@@ -457,6 +497,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             slot = slot + 1u == (uint32_t)depth ? 0u : slot + 1u;
         }
 
+        if (kBulk && lane32 == 0) bulk_wait_all();  // every record of this item is in global memory
         // write the state back (the grids are written back by every thread of
         // the CTA, so all groups' last smem writes must be visible first)
         __syncthreads();
