@@ -576,15 +576,24 @@ __device__ __forceinline__ uint64_t occlusion(uint64_t tmask, const uint16_t* ta
 {
     uint64_t vis = 0;
     uint32_t seed = 1u << 3;
-    // once a row lights nothing ahead, every farther row stays unseen
+    if constexpr (G > 1) {
+        // table rows: all seven in a row without a branch (a zero seed gives a
+        // zero row and a zero seed)
+#pragma unroll
+        for (int j = 6; j >= 0; --j) {
+            const uint32_t t = (uint32_t)(tmask >> (7 * j)) & 0x7Fu;
+            const uint32_t e = tab ? (uint32_t)tab[(seed << 7) | t] : (uint32_t)__ldg(&occ_table.v[(seed << 7) | t]);
+            vis |= (uint64_t)(e & 0x7Fu) << (7 * j);
+            seed = e >> 7;
+        }
+        return vis;
+    }
+    // one lane per env: once a row lights nothing ahead, every farther row
+    // stays unseen
 #pragma unroll 1
     for (int j = 6; j >= 0 && seed != 0u; --j) {
         const uint32_t t = (uint32_t)(tmask >> (7 * j)) & 0x7Fu;
-        uint32_t e;
-        if constexpr (G == 1)
-            e = occ_row(seed, t);
-        else
-            e = tab ? (uint32_t)tab[(seed << 7) | t] : (uint32_t)__ldg(&occ_table.v[(seed << 7) | t]);
+        const uint32_t e = occ_row(seed, t);
         vis |= (uint64_t)(e & 0x7Fu) << (7 * j);
         seed = e >> 7;
     }
@@ -624,15 +633,6 @@ __device__ __forceinline__ ViewGeom view_geom(const AgentReg& a, int S)
     const int dmax = sf > 0 ? S - 1 - af : af;
     g.rowmask = bit_range(6 - dmax, 6);
     return g;
-}
-
-// Code of view cell (vx, vy): the agent's cell shows what it carries (or
-// empty), cells outside the grid read as a grey wall.
-__device__ __forceinline__ uint32_t view_code(const uint8_t* g, const ViewGeom& v, const AgentReg& a, int vx, int vy)
-{
-    if (vx == 3 && vy == 6) return a.carry ? a.carry : (uint32_t)C_EMPTY;
-    const bool in = (v.colmask >> vx) & (v.rowmask >> vy) & 1u;
-    return in ? (uint32_t)g[v.idx0 + vx * v.dR - vy * v.dF] : (uint32_t)C_WALL;
 }
 
 // Atlas tile of a view cell from its triple: 0 unseen; 1 + 18 ent + 3 col +
@@ -726,8 +726,10 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
         for (int k = 0; k < K; ++k) {
             const int c = k * G + grp.lane;
             const int vy = (c * 37) >> 8, vx = c - 7 * vy;  // c / 7 and c % 7 for c < 56
-            uint32_t cd = C_WALL;
-            if (c < 49) cd = view_code(g, v, a, vx, vy);
+            // the in-grid test and the agent's cell (c = 45) as selects
+            const bool in = c < 49 && ((v.colmask >> vx) & (v.rowmask >> vy) & 1u);
+            const uint32_t ld = in ? (uint32_t)g[v.idx0 + vx * v.dR - vy * v.dF] : (uint32_t)C_WALL;
+            const uint32_t cd = c == 45 ? (a.carry ? a.carry : (uint32_t)C_EMPTY) : ld;
             code[k] = cd;
             const uint32_t bits = grp.ballot(c < 49 && !(cd & OPAQUE));
             tmask |= (uint64_t)bits << (k * G);

@@ -128,20 +128,12 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
     // time and truncation; reward and termination on the goal / lava / hit events
     a.t += 1;
     trunc = a.t >= max_steps;
-    reward = 0.0f;
-    term = 0;
-    if (goal) {
-        reward = reward_mode == NX_REWARD_MINIGRID
-                     ? __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(0.9f, (float)a.t), (float)max_steps))
-                     : 1.0f;
-        term = 1;
-    } else if (lava) {
-        reward = lava_reward;
-        term = 1;
-    } else if (hit) {
-        reward = -1.0f;
-        term = 1;
-    }
+    // (selects; only MiniGrid's success reward, a rare event, takes a branch)
+    float rgoal = 1.0f;
+    if (goal && reward_mode == NX_REWARD_MINIGRID)
+        rgoal = __fsub_rn(1.0f, __fdiv_rn(__fmul_rn(0.9f, (float)a.t), (float)max_steps));
+    reward = goal ? rgoal : (lava ? lava_reward : (hit ? -1.0f : 0.0f));
+    term = (goal || lava || hit) ? 1 : 0;
     // the shaping terms of Table 5: action_cost for every action but done
     // (0..5), then time_cost (subtracting 0 leaves a reward unchanged)
     reward = __fsub_rn(reward, (unsigned)action < 6u ? action_cost : 0.0f);
@@ -481,6 +473,20 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                         if (lane32 < tail) dst[head + body + lane32] = stage[head + body + lane32];
                         if (lane32 == 0 && body > 0) bulk_copy_s2g(dst + head, stage + head, (uint32_t)body);
                     }
+                } else if constexpr (G >= 16) {
+                    // at most two records (294 bytes): one pass of the warp, no loops
+                    __syncwarp();
+                    if (dst && hi > lo) {
+                        const int nbytes = (hi - lo) * NX_OBS_SYM_BYTES;
+                        const int head = min(nbytes, (int)((16u - ((uint32_t)(uintptr_t)dst & 15u)) & 15u));
+                        const int body = (nbytes - head) & ~15;
+                        const int tail = nbytes - head - body;
+                        if (lane32 < head) dst[lane32] = stage[lane32];
+                        if (lane32 < (body >> 4))
+                            reinterpret_cast<uint4*>(dst + head)[lane32] = reinterpret_cast<const uint4*>(stage + head)[lane32];
+                        if (lane32 < tail) dst[head + body + lane32] = stage[head + body + lane32];
+                    }
+                    __syncwarp();
                 } else {
                     __syncwarp();
                     if (dst && hi > lo) coop_copy(dst, stage, (hi - lo) * NX_OBS_SYM_BYTES, lane32, 32);
