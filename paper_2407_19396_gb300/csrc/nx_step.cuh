@@ -43,8 +43,7 @@ __device__ __forceinline__ uint64_t digest_word(uint64_t h, uint32_t w) { return
 template <int G>
 __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int family, int max_steps, AgentReg& a,
                                          int action, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
-                                         float action_cost, float time_cost, float& reward, int& term, int& trunc,
-                                         nx_ctl* ctl)
+                                         float action_cost, float time_cost, float& reward, int& term, int& trunc)
 {
     // transition system: each ball, in index order, moves to a uniformly drawn
     // empty cell of its 8-neighbourhood that is not the agent's cell
@@ -85,35 +84,33 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
         }
     }
     // intervention system, written as selects so that envs of one warp taking
-    // different actions do not serialise on branches
+    // different actions do not serialise on branches; the forward cell's kind
+    // is tested as one bit against constant kind masks.  An out-of-range
+    // action is a no-op that sets the sticky invalid flag (published to the
+    // device flags when the work item ends).
     const int n_act = family == NX_DYNOBS ? 3 : 7;
-    if ((unsigned)action > 6u) {
-        if (!a.invalid && grp.lane == 0) atomicOr(&ctl->flags, (unsigned)NX_FLAG_INVALID_ACTION);
-        a.invalid = 1;
-    }
-    const bool acts = (unsigned)action < (unsigned)n_act;  // out-of-range and restricted actions are no-ops
+    a.invalid |= (unsigned)action > 6u ? 1 : 0;
+    const int act = (unsigned)action < (unsigned)n_act ? action : 7;  // 7: no-op
     const int fxd = (a.dir == 0) - (a.dir == 2), fyd = (a.dir == 1) - (a.dir == 3);
     const int fx = a.x + fxd, fy = a.y + fyd;
     const bool in = (unsigned)fx < (unsigned)S && (unsigned)fy < (unsigned)S;
     const int fi = fy * S + fx;
     const uint32_t fc = in ? (uint32_t)g[fi] : (uint32_t)C_WALL;
-    const uint32_t fk = cell_kind(fc), fcol = cell_col(fc);
-    const bool is_fwd = acts && action == 2;
-    const bool hit = is_fwd && family == NX_DYNOBS && fk == K_BALL;
-    const bool move = is_fwd && !hit && walkable(fc);
-    const bool pick = acts && action == 3 && a.carry == 0u && (fk == K_KEY || fk == K_BALL);
-    const bool drop = acts && action == 4 && a.carry != 0u && in && fc == C_EMPTY;
-    const bool tog = acts && action == 5;
-    const bool unlock = tog && fk == K_DOOR_LOCKED && a.carry != 0u && cell_kind(a.carry) == K_KEY &&
-                        cell_col(a.carry) == fcol;
-    const bool open_ = tog && fk == K_DOOR_CLOSED;
-    const bool close_ = tog && fk == K_DOOR_OPEN;
+    const uint32_t fcol = cell_col(fc), kb = 1u << cell_kind(fc);
+    constexpr uint32_t kDoors = (1u << K_DOOR_OPEN) | (1u << K_DOOR_CLOSED) | (1u << K_DOOR_LOCKED);
+    // a ball is not walkable, so moving and being hit exclude each other
+    const bool move = act == 2 && (kb & NX_WALKABLE_KINDS);
+    const bool hit = act == 2 && family == NX_DYNOBS && (kb & (1u << K_BALL));
+    const bool pick = act == 3 && a.carry == 0u && (kb & ((1u << K_KEY) | (1u << K_BALL)));
+    const bool drop = act == 4 && a.carry != 0u && fc == C_EMPTY;  // a cell outside the grid reads as wall
+    const bool unlock = act == 5 && (kb & (1u << K_DOOR_LOCKED)) && a.carry == make_code(K_KEY, fcol);
+    const bool open_ = act == 5 && (kb & (1u << K_DOOR_CLOSED));
+    const bool close_ = act == 5 && (kb & (1u << K_DOOR_OPEN));
     // on_door_done (Tables 5, 6): GoToDoor's done action facing a door of the
     // mission's colour completes the task; done does nothing elsewhere
-    const bool door_done = acts && action == 6 && family == NX_GOTODOOR &&
-                           (fk == K_DOOR_OPEN || fk >= K_DOOR_CLOSED) && fcol == a.mission;
-    const int goal = (move && fk == K_GOAL) || door_done, lava = move && fk == K_LAVA;
-    a.dir = (a.dir + ((acts && action == 1) ? 1 : 0) + ((acts && action == 0) ? 3 : 0)) & 3;
+    const bool door_done = act == 6 && family == NX_GOTODOOR && (kb & kDoors) && fcol == a.mission;
+    const bool goal = (move && (kb & (1u << K_GOAL))) || door_done, lava = move && (kb & (1u << K_LAVA));
+    a.dir = (a.dir + (act == 1 ? 1 : 0) + (act == 0 ? 3 : 0)) & 3;
     a.x = move ? fx : a.x;
     a.y = move ? fy : a.y;
     const bool write = pick || drop || unlock || open_ || close_;
@@ -382,7 +379,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                         action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
                     }
                     env_step(grp, mygrid, S, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
-                             time_cost, reward, term, trunc, p.ctl);
+                             time_cost, reward, term, trunc);
                 }
                 grp.sync();
                 render_view(grp, mygrid, S, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
@@ -508,6 +505,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         // the CTA, so all groups' last smem writes must be visible first)
         __syncthreads();
         if (active && grp.lane == 0) {
+            if (a.invalid) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_INVALID_ACTION);
             store_agent(p.agents + env, a, item, item.grid_offset + (uint32_t)(gi * 3 * HW));
             if (returns) returns[local] = ret;
             if (digest) digest[local] = dig;
