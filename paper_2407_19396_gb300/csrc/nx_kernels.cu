@@ -51,7 +51,7 @@ int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride)
 {
     const int E = s.envs_per_cta;
     const int epw = 32 / s.group_lanes, warps = E * s.group_lanes / 32;
-    const int whalf = s.phases > 1 ? (epw + 1) / 2 : epw;
+    const int whalf = (s.phases > 1 && s.group_lanes < 16) ? (epw + 1) / 2 : epw;  // as nx_step_kernel
     // one lane per env pads its grid region with guard bytes (see nx_step_kernel)
     const int grid_bytes = align16(s.group_lanes == 1 ? E * cell_stride + 2 * kGridGuard : E * cell_stride);
     int b = grid_bytes + warps * align16(whalf * NX_OBS_SYM_BYTES + 16);

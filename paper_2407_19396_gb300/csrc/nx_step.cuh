@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t s_dec[256];  // cell code -> observation triple
+    __shared__ uint32_t s_sink[4];   // target of the stores of absent outputs
     // the occlusion table in shared memory for groups of 8 or more lanes (the
     // narrow groups run many more envs per block, whose grids need the space)
     constexpr bool kSmemOcc = G >= 8;
@@ -224,7 +225,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     constexpr bool kBulk = G <= 4;
     __shared__ __align__(16) uint16_t s_occ[kSmemOcc ? (1 << 14) : 8];
     const int E = p.envs_per_cta;
-    const int phases = p.phases > 1 ? 2 : 1;
+    // groups of 16 or more lanes stage at most two records per warp: always
+    // in one part (the host sizes the staging the same way)
+    const int phases = (G < 16 && p.phases > 1) ? 2 : 1;
     const int tid = threadIdx.x, nthreads = blockDim.x, lane32 = tid & 31, warp = tid >> 5;
     constexpr int epw = 32 / G;                         // envs per warp
     const int whalf = (epw + phases - 1) / phases;      // envs staged per part
@@ -412,12 +415,14 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                         }
                     }
                 }
-                if (grp.lane == 0) {
+                {
+                    // every lane of the group stores the same values (one
+                    // transaction); an absent output goes to a shared sink
                     const size_t o = (size_t)slot * nreq + local;
-                    if (out_reward) out_reward[o] = reward;
-                    if (out_term) out_term[o] = (uint8_t)term;
-                    if (out_trunc) out_trunc[o] = (uint8_t)trunc;
-                    if (out_mission) out_mission[o] = (uint8_t)a.mission;
+                    *(out_reward ? out_reward + o : reinterpret_cast<float*>(s_sink)) = reward;
+                    *(out_term ? out_term + o : reinterpret_cast<uint8_t*>(s_sink + 1)) = (uint8_t)term;
+                    *(out_trunc ? out_trunc + o : reinterpret_cast<uint8_t*>(s_sink + 2)) = (uint8_t)trunc;
+                    *(out_mission ? out_mission + o : reinterpret_cast<uint8_t*>(s_sink + 3)) = (uint8_t)a.mission;
                     ret += reward;
                     eps += (uint32_t)(term || trunc);
                 }
