@@ -100,6 +100,12 @@ def lib():
                                                    ctypes.c_uint64, P(ctypes.c_uint32), ctypes.c_int32, ctypes.c_float]
             L.orc_batch_create_indexed.restype = ctypes.c_void_p
             L.orc_batch_destroy.argtypes = [ctypes.c_void_p]
+            L.orc_policy_greedy.argtypes = [P(OrcPolicy), ctypes.c_int32, u8p, ctypes.c_int32]
+            L.orc_policy_greedy.restype = ctypes.c_int32
+            L.orc_policy_action.argtypes = [P(OrcPolicy), P(OrcEnv), ctypes.c_uint32]
+            L.orc_policy_action.restype = ctypes.c_int32
+            L.orc_batch_rollout_policy.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(OrcPolicy), i8p, u8p, f32p, u8p,
+                                                   u8p]
             L.orc_set_costs.argtypes = [P(OrcEnv), ctypes.c_float, ctypes.c_float]
             L.orc_batch_set_costs.argtypes = [ctypes.c_void_p, ctypes.c_float, ctypes.c_float]
             L.orc_batch_env.argtypes = [ctypes.c_void_p, ctypes.c_int32]
@@ -152,6 +158,48 @@ def max_variant(family, size):
 
 def tile_index(visible, agent_cell, ent, col, st):
     return int(lib().orc_tile_index(visible, agent_cell, ent, col, st))
+
+
+class OrcPolicy(ctypes.Structure):
+    _fields_ = [("n_agents", ctypes.c_int32), ("envs_per_agent", ctypes.c_int32),
+                ("w1", ctypes.POINTER(ctypes.c_int8)), ("b1", ctypes.POINTER(ctypes.c_int32)),
+                ("w2", ctypes.POINTER(ctypes.c_int8)), ("b2", ctypes.POINTER(ctypes.c_int32)),
+                ("w3", ctypes.POINTER(ctypes.c_int8)), ("b3", ctypes.POINTER(ctypes.c_int32)),
+                ("shift1", ctypes.c_int32), ("shift2", ctypes.c_int32), ("epsilon", ctypes.c_uint32)]
+
+
+class Policy:
+    """The fused rollout's integer MLP policy (numpy arrays kept alive here).
+
+    w1 [A, 64, 49] int8, b1 [A, 64] int32, w2 [A, 64, 64] int8, b2 [A, 64]
+    int32, w3 [A, 7, 64] int8, b3 [A, 7] int32."""
+
+    def __init__(self, w1, b1, w2, b2, w3, b3, shift1, shift2, epsilon=0, envs_per_agent=128):
+        self.w1 = np.ascontiguousarray(w1, np.int8)
+        self.b1 = np.ascontiguousarray(b1, np.int32)
+        self.w2 = np.ascontiguousarray(w2, np.int8)
+        self.b2 = np.ascontiguousarray(b2, np.int32)
+        self.w3 = np.ascontiguousarray(w3, np.int8)
+        self.b3 = np.ascontiguousarray(b3, np.int32)
+        A = self.w1.shape[0]
+        assert self.w1.shape == (A, 64, 49) and self.w2.shape == (A, 64, 64) and self.w3.shape == (A, 7, 64)
+        assert self.b1.shape == (A, 64) and self.b2.shape == (A, 64) and self.b3.shape == (A, 7)
+        self.shift1, self.shift2, self.epsilon, self.envs_per_agent = int(shift1), int(shift2), int(epsilon), int(envs_per_agent)
+        self.s = OrcPolicy(A, self.envs_per_agent, _ptr(self.w1, ctypes.c_int8), _ptr(self.b1, ctypes.c_int32),
+                           _ptr(self.w2, ctypes.c_int8), _ptr(self.b2, ctypes.c_int32),
+                           _ptr(self.w3, ctypes.c_int8), _ptr(self.b3, ctypes.c_int32),
+                           self.shift1, self.shift2, self.epsilon)
+
+    @property
+    def n_agents(self):
+        return self.w1.shape[0]
+
+    def greedy(self, agent, cat_fp, n_act=7):
+        c = np.ascontiguousarray(cat_fp, np.uint8).reshape(-1)
+        return int(lib().orc_policy_greedy(ctypes.byref(self.s), agent, _ptr(c, ctypes.c_uint8), n_act))
+
+    def action(self, env, gstep):
+        return int(lib().orc_policy_action(ctypes.byref(self.s), ctypes.byref(env.s), gstep))
 
 
 class Env:
@@ -316,6 +364,16 @@ class Batch:
         at = np.ascontiguousarray(atlas, np.uint8).reshape(-1)
         lib().orc_batch_obs_rgb_full(self.h, _ptr(at, ctypes.c_uint8), _ptr(img, ctypes.c_uint8), side)
         return img
+
+    def rollout_policy(self, T, policy):
+        """T steps with the policy choosing each env's action from its current view."""
+        o = {"actions": np.zeros((T, self.n), np.int8), "obs_sym": np.zeros((T, self.n, 7, 7, 3), np.uint8),
+             "reward": np.zeros((T, self.n), np.float32), "terminated": np.zeros((T, self.n), np.uint8),
+             "truncated": np.zeros((T, self.n), np.uint8)}
+        lib().orc_batch_rollout_policy(self.h, T, ctypes.byref(policy.s), _ptr(o["actions"], ctypes.c_int8),
+                                       _ptr(o["obs_sym"], ctypes.c_uint8), _ptr(o["reward"], ctypes.c_float),
+                                       _ptr(o["terminated"], ctypes.c_uint8), _ptr(o["truncated"], ctypes.c_uint8))
+        return o
 
     def missions(self):
         return np.array([self.env(i).mission for i in range(self.n)], np.uint8)

@@ -66,7 +66,7 @@ uint32_t orc_draw(uint64_t seed, uint32_t env_index, uint32_t episode, uint32_t 
     return out[0];
 }
 
-enum { PURPOSE_LAYOUT = 1, PURPOSE_BALL = 2, PURPOSE_ACTION = 3 };
+enum { PURPOSE_LAYOUT = 1, PURPOSE_BALL = 2, PURPOSE_ACTION = 3, PURPOSE_EXPLORE = 4 };
 
 /* ------------------------------------------------------------------------ */
 /* Cells (reading R5): the grid stores (entity, colour, state) per cell. */
@@ -1040,4 +1040,84 @@ void orc_batch_obs_rgb_full(orc_batch* b, const uint8_t* atlas, uint8_t* img, in
 {
     const size_t per = (size_t)side * ORC_TILE * side * ORC_TILE * 3;
     for (int32_t i = 0; i < b->n; i++) orc_obs_rgb_full(&b->envs[i], atlas, img + (size_t)i * per, side);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The fused rollout's policy (reading P1): the integer MLP of orc_policy,
+ * evaluated literally in 64-bit integers. */
+static int64_t floor_shift(int64_t v, int32_t s)
+{
+    /* floor(v / 2^s) for negative v as well */
+    int64_t d = (int64_t)1 << s;
+    int64_t q = v / d;
+    if (v % d != 0 && v < 0) q -= 1;
+    return q;
+}
+
+static int64_t clamp255(int64_t v) { return v < 0 ? 0 : (v > 255 ? 255 : v); }
+
+int32_t orc_policy_greedy(const orc_policy* p, int32_t agent, const uint8_t* cat_fp, int32_t n_act)
+{
+    const int8_t* w1 = p->w1 + (size_t)agent * ORC_HIDDEN * ORC_POLICY_IN;
+    const int32_t* b1 = p->b1 + (size_t)agent * ORC_HIDDEN;
+    const int8_t* w2 = p->w2 + (size_t)agent * ORC_HIDDEN * ORC_HIDDEN;
+    const int32_t* b2 = p->b2 + (size_t)agent * ORC_HIDDEN;
+    const int8_t* w3 = p->w3 + (size_t)agent * 7 * ORC_HIDDEN;
+    const int32_t* b3 = p->b3 + (size_t)agent * 7;
+    int64_t h1[ORC_HIDDEN], h2[ORC_HIDDEN];
+    for (int j = 0; j < ORC_HIDDEN; j++) {
+        int64_t acc = b1[j];
+        for (int k = 0; k < ORC_POLICY_IN; k++) acc += (int64_t)w1[j * ORC_POLICY_IN + k] * cat_fp[k];
+        h1[j] = clamp255(floor_shift(acc, p->shift1));
+    }
+    for (int j = 0; j < ORC_HIDDEN; j++) {
+        int64_t acc = b2[j];
+        for (int i = 0; i < ORC_HIDDEN; i++) acc += (int64_t)w2[j * ORC_HIDDEN + i] * h1[i];
+        h2[j] = clamp255(floor_shift(acc, p->shift2));
+    }
+    int32_t best = 0;
+    int64_t best_z = 0;
+    for (int a = 0; a < n_act; a++) {
+        int64_t z = b3[a];
+        for (int i = 0; i < ORC_HIDDEN; i++) z += (int64_t)w3[a * ORC_HIDDEN + i] * h2[i];
+        if (a == 0 || z > best_z) {
+            best = a;
+            best_z = z;
+        }
+    }
+    return best;
+}
+
+int32_t orc_policy_action(const orc_policy* p, const orc_env* e, uint32_t gstep)
+{
+    int32_t n_act = e->family == ORC_DYNOBS ? 3 : 7;
+    uint32_t coin = orc_draw(e->seed, e->env_index, 0xFFFFFFFEu, gstep, PURPOSE_EXPLORE, 0);
+    if (coin < p->epsilon) return orc_random_action(e, gstep);
+    uint8_t cat[ORC_VIEW * ORC_VIEW];
+    orc_obs_cat_fp(e, cat);
+    return orc_policy_greedy(p, (int32_t)(e->env_index / (uint32_t)p->envs_per_agent), cat, n_act);
+}
+
+void orc_batch_rollout_policy(orc_batch* b, int32_t T, const orc_policy* p, int8_t* actions_out, uint8_t* obs_sym,
+                              float* reward, uint8_t* terminated, uint8_t* truncated)
+{
+    size_t n = (size_t)b->n;
+    for (int32_t t = 0; t < T; t++) {
+        for (int32_t i = 0; i < b->n; i++) {
+            orc_env* e = &b->envs[i];
+            /* the action is chosen from the current state's view (an env
+             * about to autoreset ignores it) */
+            int32_t a = orc_policy_action(p, e, b->gstep);
+            float r;
+            uint8_t te, tr;
+            orc_step(e, a, &r, &te, &tr);
+            size_t o = (size_t)t * n + (size_t)i;
+            if (actions_out) actions_out[o] = (int8_t)a;
+            if (obs_sym) orc_obs_sym(e, obs_sym + o * ORC_OBS_BYTES);
+            if (reward) reward[o] = r;
+            if (terminated) terminated[o] = te;
+            if (truncated) truncated[o] = tr;
+        }
+        b->gstep += 1;
+    }
 }

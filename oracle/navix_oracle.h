@@ -117,6 +117,35 @@ void orc_set_agent(orc_env* e, int32_t x, int32_t y, int32_t dir, int32_t carry_
 /* Batch convenience used by the tests and the CPU baseline: n environments,
  * stepped one after another in index order, all with the same seed and
  * global env indices 0..n-1.  Output arrays are [n, ...]; any may be NULL. */
+/* A policy for the fused policy + environment rollout (the PPO rollout
+ * pattern of Section 4's batch-mode experiment, reading P1): an integer MLP
+ * from the categorical first-person view (49 entity codes) to one logit per
+ * action.  For each hidden unit j:
+ *   h1[j] = clamp((sum_k w1[j][k] x[k] + b1[j]) >> shift1, 0, 255)
+ *   h2[j] = clamp((sum_i w2[j][i] h1[i] + b2[j]) >> shift2, 0, 255)
+ *   z[a]  = sum_i w3[a][i] h2[i] + b3[a]
+ * (>> is the floor of division by 2^shift), the greedy action is the first
+ * index of the largest z[a] over the family's actions, and with probability
+ * epsilon / 2^32 (an exploration draw below epsilon) the action is the
+ * uniform random action instead.  Env e uses weight set e / envs_per_agent. */
+#define ORC_HIDDEN 64
+#define ORC_POLICY_IN 49
+typedef struct {
+    int32_t n_agents, envs_per_agent;
+    const int8_t* w1;  /* [n_agents][64][49] */
+    const int32_t* b1; /* [n_agents][64] */
+    const int8_t* w2;  /* [n_agents][64][64] */
+    const int32_t* b2; /* [n_agents][64] */
+    const int8_t* w3;  /* [n_agents][7][64] */
+    const int32_t* b3; /* [n_agents][7] */
+    int32_t shift1, shift2;
+    uint32_t epsilon;
+} orc_policy;
+/* the greedy action of weight set `agent` for a categorical view (first max) */
+int32_t orc_policy_greedy(const orc_policy* p, int32_t agent, const uint8_t* cat_fp, int32_t n_act);
+/* the action the policy takes in env e at global step gstep */
+int32_t orc_policy_action(const orc_policy* p, const orc_env* e, uint32_t gstep);
+
 typedef struct orc_batch orc_batch;
 orc_batch* orc_batch_create(int32_t n, const int32_t* family, const int32_t* size, const int32_t* max_steps,
                             const int32_t* variant, int32_t n_balls, uint64_t seed, uint32_t env_index_base,
@@ -138,6 +167,10 @@ void orc_batch_step(orc_batch* b, const int8_t* actions, uint8_t* obs_sym, uint8
 void orc_batch_rollout(orc_batch* b, int32_t T, const int8_t* actions_TN, uint8_t* obs_sym, uint8_t* obs_rgb,
                        const uint8_t* atlas, float* reward, uint8_t* terminated, uint8_t* truncated);
 uint32_t orc_batch_gstep(const orc_batch* b);
+/* T steps with the policy choosing every env's action from its current
+ * categorical view; actions_out [T, n] (may be NULL) receives the actions. */
+void orc_batch_rollout_policy(orc_batch* b, int32_t T, const orc_policy* p, int8_t* actions_out, uint8_t* obs_sym,
+                              float* reward, uint8_t* terminated, uint8_t* truncated);
 /* the current fully observable views of every env ([n, side, side, 3],
  * [n, side, side], [n, 7, 7]; any may be NULL) */
 void orc_batch_obs_full(orc_batch* b, uint8_t* full, uint8_t* cat, uint8_t* cat_fp, int32_t side);
