@@ -76,8 +76,9 @@ enum {
 #define NX_NO_MISSION 255  /* the mission byte of a family without one */
 /* observation bit flags (Table 4): RGB and RGB_FULL need the sprite atlas */
 enum { NX_OBS_SYM = 1, NX_OBS_RGB = 2, NX_OBS_RGB_FULL = 4 };
-/* action sources */
-enum { NX_ACT_BUFFER = 0, NX_ACT_RANDOM = 1 };
+/* action sources: a device buffer, the counter hash's uniform draw, or the
+ * context's fused policy (nx_set_policy) */
+enum { NX_ACT_BUFFER = 0, NX_ACT_RANDOM = 1, NX_ACT_POLICY = 2 };
 /* reward functions: Markovian (Section 3.2.1, Table 5) or MiniGrid's Eq. 1 */
 enum { NX_REWARD_MARKOV = 0, NX_REWARD_MINIGRID = 1 };
 /* staging of the symbolic outputs in shared memory (tunable; never changes
@@ -154,7 +155,9 @@ typedef struct {
  * largest grid size).
  * mission [..] uint8: the mission of the episode the slot's observation
  * belongs to (GoToDoor: the target door's colour index; NX_NO_MISSION for
- * the other families). */
+ * the other families).  action [..] int8: the action of the step (drawn,
+ * read from the buffer or chosen by the policy; an env that starts an
+ * episode on that step ignores it). */
 typedef struct {
     uint8_t* obs_sym;
     uint8_t* obs_rgb;
@@ -168,6 +171,7 @@ typedef struct {
     uint8_t* obs_cat_fp;
     uint8_t* obs_rgb_full;
     uint8_t* mission;
+    int8_t* action;  /* [.., n] the action each step took (device rollouts only) */
 } nx_out;
 
 /* Launch shape in use (after autotuning). */
@@ -218,7 +222,9 @@ nx_status nx_step(nx_env* env, const int8_t* d_actions, const nx_out* out);
 /* nx_rollout: n_steps consecutive nx_step calls fused into persistent,
  * CUDA-graph-captured chunks of steps_per_launch steps (the jitted scan of
  * Code 2).  act_mode NX_ACT_RANDOM ignores d_actions_TN; NX_ACT_BUFFER reads
- * device int8 [n_steps, n_envs].  Step i writes slot i % traj->depth. */
+ * device int8 [n_steps, n_envs]; NX_ACT_POLICY chooses every action with the
+ * context's policy from the env's current view (no RGB or fully observable
+ * outputs then).  Step i writes slot i % traj->depth. */
 nx_status nx_rollout(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* d_actions_TN,
                      const nx_out* traj);
 
@@ -236,6 +242,36 @@ nx_status nx_rollout_per_family(nx_env* env, int32_t n_steps, int32_t act_mode, 
  * fully observable views are not available here (NX_E_INVAL). */
 nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* host_actions_TN,
                           const nx_out* host_traj);
+
+/* The fused policy + environment rollout (the PPO rollout pattern of
+ * Section 4's batch-mode experiment, many agents each stepping its own
+ * envs): an integer MLP evaluated on the tensor cores inside the step
+ * kernel.  It maps each env's categorical first-person view x (49 entity
+ * codes, Table 4) to one logit per action:
+ *   h1[j] = clamp((sum_k w1[j][k] x[k] + b1[j]) >> shift1, 0, 255)
+ *   h2[j] = clamp((sum_i w2[j][i] h1[i] + b2[j]) >> shift2, 0, 255)
+ *   z[a]  = sum_i w3[a][i] h2[i] + b3[a]
+ * (>> floors), takes the first largest z[a] over the family's actions, and
+ * with an exploration draw below epsilon (of 2^32) the uniform random
+ * action instead.  Env e (its global draw index) uses weight set
+ * e / envs_per_agent.  Host arrays: w1 [n_agents][64][49], b1 [n_agents][64],
+ * w2 [n_agents][64][64], b2 [n_agents][64], w3 [n_agents][7][64],
+ * b3 [n_agents][7]; |bias| <= 2^22, shifts 0..24.  The policy runs 128 envs
+ * per thread block, so a weight set must cover whole aligned blocks of 128
+ * envs of the context's work list (NX_E_INVAL otherwise); it copies the
+ * weights to the device (the host arrays may be freed on return). */
+typedef struct {
+    int32_t n_agents, envs_per_agent;
+    const int8_t* w1;
+    const int32_t* b1;
+    const int8_t* w2;
+    const int32_t* b2;
+    const int8_t* w3;
+    const int32_t* b3;
+    int32_t shift1, shift2;
+    uint32_t epsilon;
+} nx_policy;
+nx_status nx_set_policy(nx_env* env, const nx_policy* policy);
 
 /* State snapshot (checkpoint/resume).  Blocking.  Layout of the buffer:
  *   [0, 64)                header: "NXST", version 1, n_envs, gstep (u32 at 12),

@@ -15,6 +15,7 @@
 #include "navixgb.h"
 #include "nx_internal.h"
 #include "nx_runtime.h"
+#include "nx_policy.cuh"
 
 // ---------------------------------------------------------------------------
 // errors
@@ -439,8 +440,13 @@ static nx_status prof_mark(nx_env* env, bool begin)
 
 // Launch shape and grid of a call: the plain instantiation, or (full) the
 // one that also writes the fully observable views.
-static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid)
+static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid, bool policy = false)
 {
+    if (policy) {
+        *s = nx_launch_shape{1, nxp::kRows, 0, 1, 0, false, true};
+        *grid = std::min(env->n_items_pol, env->per_sm_pol * env->sm_count);
+        return NX_OK;
+    }
     *s = env->shape;
     *grid = env->grid_ctas;
     if (!full) return NX_OK;
@@ -455,23 +461,30 @@ static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid
     return NX_OK;
 }
 
-static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full)
+static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full, bool policy = false)
 {
     nx_launch_shape s;
     int grid = 0;
-    nx_status ss = shape_for(env, full, &s, &grid);
+    nx_status ss = shape_for(env, full, &s, &grid, policy);
     if (ss != NX_OK) return ss;
     nx_kparams p = nx_params(env, steps, 0);
+    if (policy) {
+        p.items = env->d_items_pol;
+        p.n_items = env->n_items_pol;
+        p.envs_per_cta = nxp::kRows;
+        p.phases = 1;
+        p.rgb_full_side = 0;
+    }
     NX_CK(env, nx_launch_step_kernel(s, p, grid, st), "step kernel launch");
     NX_CK(env, nx_launch_advance(env->d_req, 1, st), "advance launch");
     return NX_OK;
 }
 
 // A direct (uncaptured) chunk launch on the context stream, counted and timed.
-static nx_status launch_chunk_direct(nx_env* env, int steps, bool full)
+static nx_status launch_chunk_direct(nx_env* env, int steps, bool full, bool policy = false)
 {
     nx_status st = prof_mark(env, true);
-    if (st == NX_OK) st = launch_chunk(env, steps, env->stream, full);
+    if (st == NX_OK) st = launch_chunk(env, steps, env->stream, full, policy);
     if (st == NX_OK) st = prof_mark(env, false);
     env->n_step_launches += 1;
     env->n_all_launches += 2;
@@ -481,15 +494,16 @@ static nx_status launch_chunk_direct(nx_env* env, int steps, bool full)
 // Replays (capturing on first use) the graph {step kernel of `steps` steps;
 // counter advance}.  The graph reads every per-call argument from the
 // device-side request record, so one graph serves every call.
-static nx_status launch_chunk_graph(nx_env* env, int steps, bool full)
+static nx_status launch_chunk_graph(nx_env* env, int steps, bool full, bool policy = false)
 {
     nx_graph* g = nullptr;
     for (auto& c : env->graphs)
-        if (c.steps == steps && c.full == full) g = &c;
+        if (c.steps == steps && c.full == full && c.policy == policy) g = &c;
     if (!g) {
         nx_graph ng;
         ng.steps = steps;
         ng.full = full;
+        ng.policy = policy;
         if (full) {  // the occupancy query sets a kernel attribute: keep it out of the capture
             nx_launch_shape s;
             int grid = 0;
@@ -498,7 +512,7 @@ static nx_status launch_chunk_graph(nx_env* env, int steps, bool full)
         }
         cudaGraph_t graph = nullptr;
         NX_CK(env, cudaStreamBeginCapture(env->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        nx_status st = launch_chunk(env, steps, env->capture_stream, full);
+        nx_status st = launch_chunk(env, steps, env->capture_stream, full, policy);
         cudaError_t e = cudaStreamEndCapture(env->capture_stream, &graph);
         if (st != NX_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -544,6 +558,14 @@ static nx_req call_req(const nx_env* env, int steps, int act_mode, const int8_t*
     r.obs_cat_fp = out ? out->obs_cat_fp : nullptr;
     r.obs_rgb_full = (out && env->rgb_full) ? out->obs_rgb_full : nullptr;
     r.mission = out ? out->mission : nullptr;
+    r.action_out = out ? out->action : nullptr;
+    if (act_mode == NX_ACT_POLICY) {
+        r.policy = env->d_policy;
+        r.policy_epa = env->policy_epa;
+        r.shift1 = env->policy_shift1;
+        r.shift2 = env->policy_shift2;
+        r.epsilon = env->policy_eps;
+    }
     r.full_side = (out && out->full_side > 0) ? out->full_side : env->max_side;
     return r;
 }
@@ -590,12 +612,20 @@ static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, co
     if (!env) return nx_fail(nullptr, NX_E_INVAL, "env is NULL");
     if (!env->was_reset) return nx_fail(env, NX_E_STATE, "nx_reset must come first");
     if (n_steps < 0) return nx_fail(env, NX_E_INVAL, "n_steps must be >= 0");
-    if (act_mode != NX_ACT_RANDOM && act_mode != NX_ACT_BUFFER) return nx_fail(env, NX_E_INVAL, "unknown act_mode");
+    if (act_mode != NX_ACT_RANDOM && act_mode != NX_ACT_BUFFER && act_mode != NX_ACT_POLICY)
+        return nx_fail(env, NX_E_INVAL, "unknown act_mode");
     if (act_mode == NX_ACT_BUFFER && !d_actions) return nx_fail(env, NX_E_INVAL, "NX_ACT_BUFFER needs actions");
+    const bool policy = act_mode == NX_ACT_POLICY;
+    if (policy) {
+        if (!env->d_policy) return nx_fail(env, NX_E_STATE, "NX_ACT_POLICY needs nx_set_policy first");
+        if (per_family) return nx_fail(env, NX_E_INVAL, "the per-family form has no fused policy");
+        if (traj && (traj->obs_rgb || traj->obs_rgb_full || wants_full(traj)))
+            return nx_fail(env, NX_E_INVAL, "policy rollouts write the symbolic outputs only");
+    }
     nx_status st = check_out(env, traj);
     if (st != NX_OK) return st;
     if (n_steps == 0) return NX_OK;
-    if (!env->tuned) {
+    if (!env->tuned && !policy) {
         st = nx_autotune(env);
         if (st != NX_OK) return st;
     }
@@ -632,15 +662,97 @@ static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, co
     }
     const int nfull = n_steps / C, rem = n_steps % C;
     for (int k = 0; k < nfull; ++k) {
-        st = launch_chunk_graph(env, C, full);
+        st = launch_chunk_graph(env, C, full, policy);
         if (st != NX_OK) return st;
     }
     if (rem) {
         NX_CK(env, nx_launch_set_steps(env->d_req, rem, env->stream), "set steps");
         env->n_all_launches += 1;
-        st = launch_chunk_direct(env, rem, full);
+        st = launch_chunk_direct(env, rem, full, policy);
         if (st != NX_OK) return st;
     }
+    return NX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fused policy: weight images in the tensor-core operand layout (bf16, see
+// nx_policy.cuh), a 128-env work list whose items never split a weight set.
+
+nx_status nx_set_policy(nx_env* env, const nx_policy* pol)
+{
+    if (!env || !pol) return nx_fail(env, NX_E_INVAL, "NULL argument");
+    if (pol->n_agents < 1 || pol->envs_per_agent < 1) return nx_fail(env, NX_E_INVAL, "n_agents and envs_per_agent >= 1");
+    if (!pol->w1 || !pol->b1 || !pol->w2 || !pol->b2 || !pol->w3 || !pol->b3)
+        return nx_fail(env, NX_E_INVAL, "policy weights missing");
+    if (pol->shift1 < 0 || pol->shift1 > 24 || pol->shift2 < 0 || pol->shift2 > 24)
+        return nx_fail(env, NX_E_INVAL, "shifts must be 0..24");
+    const uint64_t base = env->opt.env_index_base;
+    const uint64_t epa = (uint64_t)pol->envs_per_agent;
+    if ((base + (uint64_t)env->n_envs - 1) / epa >= (uint64_t)pol->n_agents)
+        return nx_fail(env, NX_E_INVAL, "the weight sets do not cover every env");
+    const int A = pol->n_agents;
+    auto bias_ok = [](const int32_t* b, size_t n) {
+        for (size_t i = 0; i < n; ++i)
+            if (b[i] > (1 << 22) || b[i] < -(1 << 22)) return false;
+        return true;
+    };
+    if (!bias_ok(pol->b1, (size_t)A * 64) || !bias_ok(pol->b2, (size_t)A * 64) || !bias_ok(pol->b3, (size_t)A * 7))
+        return nx_fail(env, NX_E_INVAL, "biases must lie in [-2^22, 2^22]");
+    std::vector<nx_item> items = nx_build_items(env, nxp::kRows);
+    for (const nx_item& it : items) {
+        const uint64_t first = base + it.local_begin, last = first + it.n_envs - 1;
+        if (first / epa != last / epa)
+            return nx_fail(env, NX_E_INVAL, "a weight set boundary splits a 128-env block of the work list");
+    }
+    nx_launch_shape ps{1, nxp::kRows, 0, 1, 0, false, true};
+    int err = 0;
+    const int per_sm = nx_kernel_max_ctas(ps, env->cell_stride, &err);
+    if (err) return nx_cuda_fail(env, err, "occupancy query");
+    if (per_sm < 1) return nx_fail(env, NX_E_INVAL, "the fused policy does not fit on an SM with these grids");
+    // weight images: bf16 bits of int8 values (exact), biases as int32
+    std::vector<uint8_t> img((size_t)A * nxp::kImageBytes, 0);
+    auto bf16 = [](int v) -> uint16_t {
+        float f = (float)v;
+        uint32_t u;
+        memcpy(&u, &f, 4);
+        return (uint16_t)(u >> 16);  // exact: |v| <= 128 has at most 8 significant bits
+    };
+    for (int a = 0; a < A; ++a) {
+        uint8_t* im = img.data() + (size_t)a * nxp::kImageBytes;
+        auto put = [&](int region, int n, int k, int v) {
+            const uint16_t b = bf16(v);
+            memcpy(im + region + nxp::tile_offset(n, k), &b, 2);
+        };
+        for (int n = 0; n < 64; ++n)
+            for (int k = 0; k < 64; ++k) {
+                put(nxp::kW1, n, k, k < nxp::kIn ? pol->w1[((size_t)a * 64 + n) * 49 + k] : 0);
+                put(nxp::kW2, n, k, pol->w2[((size_t)a * 64 + n) * 64 + k]);
+                if (n < 16) put(nxp::kW3, n, k, n < 7 ? pol->w3[((size_t)a * 7 + n) * 64 + k] : 0);
+            }
+        memcpy(im + nxp::kB1, pol->b1 + (size_t)a * 64, 64 * 4);
+        memcpy(im + nxp::kB2, pol->b2 + (size_t)a * 64, 64 * 4);
+        memcpy(im + nxp::kB3, pol->b3 + (size_t)a * 7, 7 * 4);
+    }
+    NX_CK(env, cudaStreamSynchronize(env->stream), "policy upload");  // the previous images are no longer read
+    if (env->d_policy) nx_dev_free(env, env->d_policy);
+    if (env->d_items_pol) nx_dev_free(env, env->d_items_pol);
+    env->d_policy = nullptr;
+    env->d_items_pol = nullptr;
+    env->d_policy = (uint8_t*)nx_dev_alloc(env, img.size());
+    env->d_items_pol = (nx_item*)nx_dev_alloc(env, items.size() * sizeof(nx_item));
+    if (!env->d_policy || !env->d_items_pol) return nx_fail(env, NX_E_NOMEM, "policy allocation failed");
+    env->policy_host = std::move(img);
+    env->items_pol = std::move(items);
+    NX_CK(env, cudaMemcpyAsync(env->d_policy, env->policy_host.data(), env->policy_host.size(), cudaMemcpyHostToDevice,
+                               env->stream), "policy upload");
+    NX_CK(env, cudaMemcpyAsync(env->d_items_pol, env->items_pol.data(), env->items_pol.size() * sizeof(nx_item),
+                               cudaMemcpyHostToDevice, env->stream), "policy work list upload");
+    env->n_items_pol = (int)env->items_pol.size();
+    env->per_sm_pol = per_sm;
+    env->policy_epa = (uint32_t)epa;
+    env->policy_shift1 = pol->shift1;
+    env->policy_shift2 = pol->shift2;
+    env->policy_eps = pol->epsilon;
     return NX_OK;
 }
 
@@ -673,8 +785,8 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
     if (act_mode == NX_ACT_BUFFER && !h_actions) return nx_fail(env, NX_E_INVAL, "NX_ACT_BUFFER needs actions");
     nx_status st = check_out(env, h);
     if (st != NX_OK) return st;
-    if (h && (h->obs_full || h->obs_cat || h->obs_cat_fp || h->obs_rgb_full))
-        return nx_fail(env, NX_E_INVAL, "the fully observable views are device outputs only");
+    if (h && (h->obs_full || h->obs_cat || h->obs_cat_fp || h->obs_rgb_full || h->action))
+        return nx_fail(env, NX_E_INVAL, "the fully observable views and the actions are device outputs only");
     if (n_steps == 0) return NX_OK;
     if (!env->tuned) {
         st = nx_autotune(env);

@@ -39,7 +39,7 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
     return c0;
 }
 
-enum { PURPOSE_LAYOUT = 1u, PURPOSE_BALL = 2u, PURPOSE_ACTION = 3u };
+enum { PURPOSE_LAYOUT = 1u, PURPOSE_BALL = 2u, PURPOSE_ACTION = 3u, PURPOSE_EXPLORE = 4u };
 
 __device__ __forceinline__ uint32_t draw(uint64_t seed, uint32_t env, uint32_t episode, uint32_t step,
                                          uint32_t purpose, uint32_t k)

@@ -77,6 +77,11 @@ struct NX_ALIGN16 nx_req {
     int32_t full_side;
     float action_cost;    // Table 5 shaping terms
     float time_cost;
+    int8_t* action_out;   // [depth, n_envs] the action of every step (may be NULL)
+    const uint8_t* policy;  // NX_ACT_POLICY: per-agent weight images (nxp::kImageBytes each)
+    uint32_t policy_epa;  // envs per agent
+    int32_t shift1, shift2;
+    uint32_t epsilon;     // exploration threshold on a 32-bit draw
 };
 
 struct NX_ALIGN16 nx_ctl {
@@ -84,7 +89,7 @@ struct NX_ALIGN16 nx_ctl {
     uint32_t pad[3];
 };
 
-enum { NX_FLAG_INVALID_ACTION = 1u, NX_FLAG_BOUNDS = 2u };
+enum { NX_FLAG_INVALID_ACTION = 1u, NX_FLAG_BOUNDS = 2u, NX_FLAG_WAIT_TIMEOUT = 4u };
 
 // Launch arguments of the step kernel.
 struct nx_kparams {
@@ -112,6 +117,7 @@ struct nx_launch_shape {
     int phases = 1;  // the symbolic outputs of a CTA are staged and stored in this many parts (1 or 2)
     int rgb_full_side = 0;  // reserve smem for full-view RGB tile ids of this grid side
     bool full = false;      // the instantiation that writes the fully observable views
+    bool policy = false;    // the fused-policy instantiation (1 lane, 128 envs per CTA)
 };
 // Shared-memory bytes per env grid for grids of up to max_cells cells: a
 // whole number of 4-byte words, and an odd one, so that the grids of the 32

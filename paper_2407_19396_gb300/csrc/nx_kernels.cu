@@ -40,6 +40,7 @@ __global__ void nx_advance_kernel(nx_req* reqs, int n_reqs)
 
 int nx_shape_supported(const nx_launch_shape& s)
 {
+    if (s.policy && (s.group_lanes != 1 || s.envs_per_cta != nxp::kRows || s.rgb || s.full)) return 0;
     const int G = s.group_lanes;
     if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return 0;
     if (s.envs_per_cta < 1 || s.envs_per_cta * G > kMaxThreads) return 0;
@@ -55,6 +56,8 @@ int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride)
     // one lane per env pads its grid region with guard bytes (see nx_step_kernel)
     const int grid_bytes = align16(s.group_lanes == 1 ? E * cell_stride + 2 * kGridGuard : E * cell_stride);
     int b = grid_bytes + warps * align16(whalf * NX_OBS_SYM_BYTES + 16);
+    if (s.policy) b = policy_smem_offset(grid_bytes, warps * align16(whalf * NX_OBS_SYM_BYTES + 16)) +
+                      nxp::kATileBytes + nxp::kImageBytes;
     if (s.rgb) b += align16(E * 49 * 2) + align16(E * s.rgb_full_side * s.rgb_full_side * 2);
     return b;
 }
@@ -64,6 +67,7 @@ int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err)
     const int smem = nx_kernel_smem_bytes(s, cell_stride);
     const int threads = s.envs_per_cta * s.group_lanes;
     if (s.full) return nx_kernel_max_ctas_full(s, threads, smem, err);
+    if (s.policy) return occupancy_t<1, false, false, true>(threads, smem, err);
     NX_DISPATCH_G(s.group_lanes, s.rgb, false, occupancy_t, threads, smem, err)
 }
 
@@ -72,6 +76,7 @@ int nx_launch_step_kernel(const nx_launch_shape& s, const nx_kparams& p, int gri
     const int smem = nx_kernel_smem_bytes(s, p.cell_stride);
     cudaStream_t st = (cudaStream_t)stream;
     if (s.full) return nx_launch_step_kernel_full(s, p, grid, smem, st);
+    if (s.policy) return launch_t<1, false, false, true>(p, grid, smem, st);
     NX_DISPATCH_G(s.group_lanes, s.rgb, false, launch_t, p, grid, smem, st)
 }
 

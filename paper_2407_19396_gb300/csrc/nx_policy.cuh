@@ -1,0 +1,215 @@
+// nx_policy.cuh -- the policy of the fused policy + environment rollout on
+// the fifth-generation tensor cores (tcgen05, tensor memory).
+//
+// The policy (reading P1) maps each env's categorical first-person view (49
+// entity codes, the input row x, padded to K = 64) through two hidden layers
+// of 64 units to one logit per action:
+//   h1 = clamp((W1 x + b1) >> shift1, 0, 255), h2 = clamp((W2 h1 + b2) >> shift2, 0, 255),
+//   z = W3 h2 + b3,   greedy action = the first largest z over the family's actions.
+// Weights are int8 and activations at most 255, so every product and every
+// partial sum is an integer below 2^24: bf16 operands with fp32 accumulation
+// give the exact integer result in any order of summation, and the tensor-core
+// result equals the integer arithmetic bit for bit.
+//
+// One block holds 128 envs, one per thread and one per row of the tensor-core
+// tile (M = 128) and of tensor memory (lane = row).  Per layer: every thread
+// writes its row of the A operand (bf16, shared memory), one thread issues
+// four tcgen05.mma (K = 16 each) against the layer's weights (the B operand,
+// N x K) with the accumulator in tensor memory and commits them to an
+// mbarrier; every thread waits (bounded), reads its row back with
+// tcgen05.ld, requantises and writes the next layer's A row.
+//
+// Shared-memory operand layout (no swizzle, K-major): 8 x 16-byte core
+// matrices; element (r, k) of a tile lives at
+//   (r / 8) * 1024 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// i.e. descriptor leading-dimension offset 128 bytes (the next core matrix
+// along K) and stride offset 1024 bytes (the next 8 rows).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nxp {
+
+constexpr int kRows = 128;     // envs per block = M of every MMA
+constexpr int kK = 64;         // inputs per layer (49 view cells + zero padding; 64 hidden units)
+constexpr int kIn = 49;
+constexpr int kATileBytes = kRows * kK * 2;  // 16 KB
+// one agent's image of weights and biases in shared memory
+constexpr int kW1 = 0, kW2 = 8192, kW3 = 16384;  // W1^T, W2^T: 64 x 64; W3^T: 16 x 64 (rows >= 7 zero)
+constexpr int kB1 = 18432, kB2 = 18688, kB3 = 18944;  // int32 biases: 64, 64, 16
+constexpr int kImageBytes = 19008;
+constexpr uint32_t kSbo = 1024, kLbo = 128;
+
+__host__ __device__ constexpr uint32_t tile_offset(int r, int k)
+{
+    return (uint32_t)((r / 8) * kSbo + (k / 8) * kLbo + (r % 8) * 16 + (k % 8) * 2);
+}
+
+// instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (16-byte units), the fixed version bits 0b001 at bit 46, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kLbo >> 4) << 16) | ((uint64_t)(kSbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// D[tmem] = A * B^T over K = 64 in four K = 16 steps (one thread)
+__device__ __forceinline__ void mma_k64(uint32_t tmem, const uint8_t* sA, const uint8_t* sB, uint32_t idesc)
+{
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+    for (int ks = 0; ks < kK / 16; ++ks) {
+        const uint64_t ad = smem_desc(a0 + ks * 2 * kLbo), bd = smem_desc(b0 + ks * 2 * kLbo);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                 : "memory");
+}
+
+// Waits for the mbarrier phase with the given parity; gives up after a bounded
+// number of polls and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 20) && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)), "r"(parity)
+            : "memory");
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// The threads' A rows (generic-proxy stores) and their tensor-memory reads
+// are complete before the next MMA is issued.
+__device__ __forceinline__ void sync_for_mma()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t bf16_bits(int v) { return (uint32_t)__bfloat16_as_ushort(__int2bfloat16_rn(v)); }
+
+// Writes 16 consecutive values of row r (k0 a multiple of 8) as bf16.
+__device__ __forceinline__ void store_row16(uint8_t* sA, int r, int k0, const int (&x)[16])
+{
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) w[j] = bf16_bits(x[2 * j]) | (bf16_bits(x[2 * j + 1]) << 16);
+    *reinterpret_cast<uint4*>(sA + tile_offset(r, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(sA + tile_offset(r, k0 + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// The input row: the categorical first-person view (the entity byte of each
+// of the 49 cells of the 147-byte symbolic record held as 37 stream words),
+// zero beyond.
+__device__ __forceinline__ void store_obs_row(uint8_t* sA, int r, const uint32_t (&sw)[37])
+{
+#pragma unroll
+    for (int k0 = 0; k0 < kK; k0 += 16) {
+        int x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int c = k0 + j;
+            x[j] = c < kIn ? (int)((sw[(3 * c) >> 2] >> (8 * ((3 * c) & 3))) & 0xFFu) : 0;
+        }
+        store_row16(sA, r, k0, x);
+    }
+}
+
+__device__ __forceinline__ void store_zero_row(uint8_t* sA, int r)
+{
+#pragma unroll
+    for (int k0 = 0; k0 < kK; k0 += 8) *reinterpret_cast<uint4*>(sA + tile_offset(r, k0)) = make_uint4(0, 0, 0, 0);
+}
+
+// All 128 threads of the block: the greedy action of this thread's row (rows
+// of inactive threads are computed and ignored).  `phase` tracks the
+// mbarrier's parity; `ok` turns false if a wait gave up.
+__device__ __forceinline__ int policy_greedy(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar,
+                                             uint32_t& phase, int n_act, int shift1, int shift2, bool& ok)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
+#pragma unroll 1
+    for (int layer = 0; layer < 2; ++layer) {
+        sync_for_mma();
+        if (tid == 0) {
+            mma_k64(tmem, sA, sW + (layer ? kW2 : kW1), idesc_bf16(kRows, kK));
+            mma_commit(mbar);
+        }
+        ok = mbar_wait(mbar, phase) && ok;
+        phase ^= 1u;
+        __syncwarp();  // tcgen05.ld is warp-collective: converge after the per-thread wait
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int32_t* b = reinterpret_cast<const int32_t*>(sW + (layer ? kB2 : kB1));
+        const int sh = layer ? shift2 : shift1;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kK; c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(trow + (uint32_t)c0, v);
+            int h[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int acc = __float2int_rn(__uint_as_float(v[j])) + b[c0 + j];
+                h[j] = min(max(acc >> sh, 0), 255);
+            }
+            store_row16(sA, tid, c0, h);
+        }
+    }
+    sync_for_mma();
+    if (tid == 0) {
+        mma_k64(tmem, sA, sW + kW3, idesc_bf16(kRows, 16));
+        mma_commit(mbar);
+    }
+    ok = mbar_wait(mbar, phase) && ok;
+    phase ^= 1u;
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t v[16];
+    tmem_ld16(trow, v);
+    const int32_t* b3 = reinterpret_cast<const int32_t*>(sW + kB3);
+    int best = 0, bz = __float2int_rn(__uint_as_float(v[0])) + b3[0];
+#pragma unroll
+    for (int a = 1; a < 7; ++a) {
+        const int z = __float2int_rn(__uint_as_float(v[a])) + b3[a];
+        if (a < n_act && z > bz) {
+            best = a;
+            bz = z;
+        }
+    }
+    return best;
+}
+
+}  // namespace nxp

@@ -11,6 +11,7 @@
 struct nx_graph {
     int steps = 0;
     bool full = false;
+    bool policy = false;
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -60,6 +61,17 @@ struct nx_env {
     bool tuned = false;
     std::vector<nx_tune_entry> tune_log;
     std::vector<nx_graph> graphs;
+
+    // fused policy (nx_set_policy): weight images, its own 128-env work list
+    uint8_t* d_policy = nullptr;
+    std::vector<uint8_t> policy_host;  // kept alive for the asynchronous upload
+    nx_item* d_items_pol = nullptr;
+    std::vector<nx_item> items_pol;
+    int n_items_pol = 0;
+    int per_sm_pol = 0;
+    uint32_t policy_epa = 0;
+    int32_t policy_shift1 = 0, policy_shift2 = 0;
+    uint32_t policy_eps = 0;
 
     // per-call request record (host image of the fixed fields)
     nx_req req_host{};

@@ -20,6 +20,7 @@
 #include "navixgb.h"
 #include "nx_device.cuh"
 #include "nx_internal.h"
+#include "nx_policy.cuh"
 
 namespace nxk {
 
@@ -211,10 +212,20 @@ __device__ __forceinline__ void coop_rgb_full(uint8_t* dst, const uint16_t* tile
     }
 }
 
-template <int G, bool RGB, bool FULL>
+// Byte offset of the fused policy's shared memory (the A tile, then the
+// agent's weight image) after the grids and the staging.
+__host__ __device__ __forceinline__ int policy_smem_offset(int grid_bytes, int staging_bytes)
+{
+    return (grid_bytes + staging_bytes + 127) & ~127;
+}
+
+template <int G, bool RGB, bool FULL, bool POL = false>
 __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparams p)
 {
+    static_assert(!POL || (G == 1 && !RGB && !FULL), "the fused policy runs one lane per env");
     extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_mbar;  // fused policy: MMA completion
+    __shared__ uint32_t s_tmem;               // fused policy: tensor-memory base address
     __shared__ uint32_t s_dec[256];  // cell code -> observation triple
     __shared__ uint32_t s_sink[4];   // target of the stores of absent outputs
     // the occlusion table in shared memory for groups of 8 or more lanes (the
@@ -246,6 +257,26 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     const int gi = tid / G;
     const Grp<G> grp(tid);
     uint8_t* mygrid = sgrid + gi * cs;
+    // fused policy: the A tile of the 128 envs' rows, then the agent's weights
+    uint8_t* sA = smem + policy_smem_offset(grid_bytes, (nthreads >> 5) * wbytes);
+    uint8_t* sW = sA + nxp::kATileBytes;
+    uint32_t tmem = 0, phase = 0;
+    bool pol_ok = true;
+    if constexpr (POL) {
+        // 64 tensor-memory columns: the 128 x 64 f32 accumulator of a layer
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(nxp::smem_u32(&s_tmem)));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(nxp::smem_u32(&s_mbar)));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem = s_tmem;
+    }
     for (int i = tid; i < 256; i += nthreads) s_dec[i] = cell_triple((uint32_t)i);
     if constexpr (kSmemOcc)
         for (int i = tid; i < (1 << 14) / 8; i += nthreads)
@@ -267,6 +298,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         uint8_t* out_term = rq->terminated;
         uint8_t* out_trunc = rq->truncated;
         uint8_t* out_mission = rq->mission;
+        int8_t* out_action = rq->action_out;
         const uint32_t reward_mode = rq->reward_mode;
         const float lava_reward = rq->lava_reward;
         const float action_cost = rq->action_cost, time_cost = rq->time_cost;
@@ -309,6 +341,20 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         }
         __syncthreads();
 
+        if constexpr (POL) {
+            // the item's weight set, and every env's current view as its input row
+            const uint32_t agent = (rq->key_base + item.local_begin) / rq->policy_epa;
+            const uint4* src = reinterpret_cast<const uint4*>(rq->policy + (size_t)agent * nxp::kImageBytes);
+            for (int i = tid; i < nxp::kImageBytes / 16; i += nthreads) reinterpret_cast<uint4*>(sW)[i] = src[i];
+            if (active) {
+                ViewOut<G> v0;
+                render_view(grp, mygrid, S, a, s_dec, nullptr, v0, nullptr);
+                nxp::store_obs_row(sA, tid, v0.sw);
+            } else {
+                nxp::store_zero_row(sA, tid);
+            }
+        }
+
         // steps == 0 with reset_all: one emission of the episode-0 start state
         const int emissions = p.reset_all ? 1 : steps;
         const bool rnd = act_mode == NX_ACT_RANDOM;
@@ -321,6 +367,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             ViewOut<G> vo;
             float reward = 0.0f;
             int term = 0, trunc = 0;
+            int pol_act = 0;  // fused policy: the greedy action of every env (all threads take part)
+            if constexpr (POL)
+                pol_act = nxp::policy_greedy(sA, sW, tmem, &s_mbar, phase, (int)n_act, rq->shift1, rq->shift2, pol_ok);
             if (G > 1 && rnd && (s % G) == 0) {
                 // the random actions of the next G steps depend only on the step
                 // counter, so the group's lanes draw them in parallel
@@ -363,6 +412,24 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 __syncwarp();
             }
             if (active) {
+                // the step's action (an env that starts an episode ignores it)
+                int action;
+                if (POL) {
+                    // exploration: with a draw below epsilon, the uniform random action
+                    const uint32_t eps_t = rq->epsilon;
+                    const uint32_t coin =
+                        eps_t ? draw(seed, key, 0xFFFFFFFEu, gstep0 + (uint32_t)s, PURPOSE_EXPLORE, 0u) : 0xFFFFFFFFu;
+                    action = coin < eps_t
+                                 ? bounded(draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)s, PURPOSE_ACTION, 0u), n_act)
+                                 : pol_act;
+                } else if (rnd) {
+                    const uint32_t x = G > 1 ? grp.shfl(my_draw, s % G)
+                                             : draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)s, PURPOSE_ACTION, 0u);
+                    action = bounded(x, n_act);
+                } else {
+                    action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
+                }
+                if (out_action) out_action[(size_t)slot * nreq + local] = (int8_t)action;
                 if (starts) {
                     // the new episode's start: reward padding 0, the action is ignored
                 } else {
@@ -373,20 +440,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                             return draw(seed, key, episode, t, PURPOSE_BALL, k);
                         });
                     }
-                    int action;
-                    if (rnd) {
-                        const uint32_t x = G > 1 ? grp.shfl(my_draw, s % G)
-                                                 : draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)s, PURPOSE_ACTION, 0u);
-                        action = bounded(x, n_act);
-                    } else {
-                        action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
-                    }
                     env_step(grp, mygrid, S, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
                              time_cost, reward, term, trunc);
                 }
                 grp.sync();
                 render_view(grp, mygrid, S, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
                             RGB && obs_rgb ? stiles + gi * 49 : nullptr);
+                if constexpr (POL) nxp::store_obs_row(sA, tid, vo.sw);  // the next step's policy input
                 if (FULL && (obs_full || obs_cat || obs_rgb_full)) {
                     // fully observable views: every cell's triple, the agent's
                     // cell holding (agent, red, direction), zero beyond the grid;
@@ -529,15 +589,23 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         }
         __syncthreads();
     }
+    if constexpr (POL) {
+        // every MMA has completed (each was waited for): free the tensor memory
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+        if (!pol_ok) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_WAIT_TIMEOUT);
+    }
 }
 
 
 // The dynamic shared-memory limit is raised once per shape by
 // nx_kernel_max_ctas (outside any stream capture); launches only launch.
-template <int G, bool RGB, bool FULL>
+template <int G, bool RGB, bool FULL, bool POL = false>
 int launch_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
 {
-    nx_step_kernel<G, RGB, FULL><<<grid, p.envs_per_cta * G, smem, st>>>(p);
+    nx_step_kernel<G, RGB, FULL, POL><<<grid, p.envs_per_cta * G, smem, st>>>(p);
     return (int)cudaGetLastError();
 }
 
@@ -545,10 +613,10 @@ int launch_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
 // context in the process, so it is always raised to the most the device
 // allows next to the kernel's static shared memory (never lowered to one
 // context's need).
-template <int G, bool RGB, bool FULL>
+template <int G, bool RGB, bool FULL, bool POL = false>
 int occupancy_t(int threads, int smem, int* err)
 {
-    auto k = nx_step_kernel<G, RGB, FULL>;
+    auto k = nx_step_kernel<G, RGB, FULL, POL>;
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -25,7 +25,7 @@ NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET,
 NX_N_FAMILIES = 11
 NX_NO_MISSION = 255
 NX_OBS_SYM, NX_OBS_RGB, NX_OBS_RGB_FULL = 1, 2, 4
-NX_ACT_BUFFER, NX_ACT_RANDOM = 0, 1
+NX_ACT_BUFFER, NX_ACT_RANDOM, NX_ACT_POLICY = 0, 1, 2
 NX_REWARD_MARKOV, NX_REWARD_MINIGRID = 0, 1
 NX_STAGE_AUTO, NX_STAGE_FULL, NX_STAGE_HALF = 0, 1, 2
 OBS_SYM_BYTES, OBS_RGB_BYTES = 147, 150528
@@ -57,10 +57,18 @@ class nx_out(ctypes.Structure):
     _fields_ = [("obs_sym", ctypes.c_void_p), ("obs_rgb", ctypes.c_void_p), ("reward", ctypes.c_void_p),
                 ("terminated", ctypes.c_void_p), ("truncated", ctypes.c_void_p), ("depth", ctypes.c_int32),
                 ("full_side", ctypes.c_int32), ("obs_full", ctypes.c_void_p), ("obs_cat", ctypes.c_void_p),
-                ("obs_cat_fp", ctypes.c_void_p), ("obs_rgb_full", ctypes.c_void_p), ("mission", ctypes.c_void_p)]
+                ("obs_cat_fp", ctypes.c_void_p), ("obs_rgb_full", ctypes.c_void_p), ("mission", ctypes.c_void_p),
+                ("action", ctypes.c_void_p)]
 
 OUT_KEYS = ("obs_sym", "obs_rgb", "reward", "terminated", "truncated", "obs_full", "obs_cat", "obs_cat_fp",
-            "obs_rgb_full", "mission")
+            "obs_rgb_full", "mission", "action")
+
+
+class nx_policy(ctypes.Structure):
+    _fields_ = [("n_agents", ctypes.c_int32), ("envs_per_agent", ctypes.c_int32),
+                ("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p),
+                ("w3", ctypes.c_void_p), ("b3", ctypes.c_void_p), ("shift1", ctypes.c_int32),
+                ("shift2", ctypes.c_int32), ("epsilon", ctypes.c_uint32)]
 
 
 class nx_info(ctypes.Structure):
@@ -105,6 +113,7 @@ SIGNATURES = {
     "nx_state_bytes": (_sz, [_vp]),
     "nx_get_state": (_i32, [_vp, _vp, _sz]),
     "nx_set_state": (_i32, [_vp, _vp, _sz]),
+    "nx_set_policy": (_i32, [_vp, _P(nx_policy)]),
     "nx_sync": (_i32, [_vp, ctypes.c_double]),
     "nx_device_flags": (_i32, [_vp, _P(_u32)]),
     "nx_get_info": (_i32, [_vp, _P(nx_info)]),
@@ -199,6 +208,18 @@ def nx_step(h, actions_ptr, out):
 def nx_rollout(h, n_steps, act_mode, actions_ptr, out):
     return check(lib().nx_rollout(h, n_steps, act_mode, ctypes.c_void_p(actions_ptr or None),
                                   ctypes.byref(out) if out is not None else None), h)
+
+
+def nx_set_policy(h, w1, b1, w2, b2, w3, b3, shift1, shift2, epsilon=0, envs_per_agent=128):
+    """Uploads the fused policy's weights (numpy int8 / int32 arrays: w1 [A, 64, 49],
+    b1 [A, 64], w2 [A, 64, 64], b2 [A, 64], w3 [A, 7, 64], b3 [A, 7])."""
+    arrs = [np.ascontiguousarray(w1, np.int8), np.ascontiguousarray(b1, np.int32), np.ascontiguousarray(w2, np.int8),
+            np.ascontiguousarray(b2, np.int32), np.ascontiguousarray(w3, np.int8), np.ascontiguousarray(b3, np.int32)]
+    A = arrs[0].shape[0]
+    assert arrs[0].shape == (A, 64, 49) and arrs[2].shape == (A, 64, 64) and arrs[4].shape == (A, 7, 64)
+    assert arrs[1].shape == (A, 64) and arrs[3].shape == (A, 64) and arrs[5].shape == (A, 7)
+    p = nx_policy(A, int(envs_per_agent), *[a.ctypes.data for a in arrs], int(shift1), int(shift2), int(epsilon))
+    return check(lib().nx_set_policy(h, ctypes.byref(p)), h)
 
 
 def nx_rollout_per_family(h, n_steps, act_mode, actions_ptr, out):
@@ -316,7 +337,7 @@ class Env:
                  atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
                  autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, variant=0,
                  obs_full=False, obs_cat=False, obs_cat_fp=False, obs_rgb_full=False, mission=None,
-                 action_cost=0.0, time_cost=0.0, torch_allocator=True):
+                 action_cost=0.0, time_cost=0.0, action=False, torch_allocator=True):
         import torch
 
         self.torch = torch
@@ -363,6 +384,7 @@ class Env:
         self.obs_sym, self.obs_rgb = obs_sym, obs_rgb
         self.want_full, self.want_cat, self.want_cat_fp = obs_full, obs_cat, obs_cat_fp
         self.want_rgb_full = obs_rgb_full
+        self.want_action = action
         if descs is None:
             self.n = int(n_envs)
             self.side = int(size)
@@ -407,6 +429,7 @@ class Env:
         o["obs_rgb_full"] = (torch.empty(lead + (n, 32 * F, 32 * F, 3), dtype=torch.uint8, device=self.device)
                              if self.want_rgb_full else None)
         o["mission"] = torch.empty(lead + (n,), dtype=torch.uint8, device=self.device) if self.want_mission else None
+        o["action"] = torch.empty(lead + (n,), dtype=torch.int8, device=self.device) if self.want_action else None
         return o
 
     def out_struct(self, o, depth=1):
@@ -432,10 +455,14 @@ class Env:
         nx_step(self.h, ptr, self.out_struct(out))
         return out
 
-    def rollout(self, n_steps, actions=None, depth=None, out=None, per_family=False):
+    def set_policy(self, w1, b1, w2, b2, w3, b3, shift1, shift2, epsilon=0, envs_per_agent=128):
+        """The fused policy used by rollout(..., policy=True) (see nx_set_policy)."""
+        nx_set_policy(self.h, w1, b1, w2, b2, w3, b3, shift1, shift2, epsilon, envs_per_agent)
+
+    def rollout(self, n_steps, actions=None, depth=None, out=None, per_family=False, policy=False):
         depth = depth or n_steps
         out = out or self.alloc_out(depth)
-        ptr, mode = None, NX_ACT_RANDOM
+        ptr, mode = None, (NX_ACT_POLICY if policy else NX_ACT_RANDOM)
         if actions is not None:
             assert actions.dtype == self.torch.int8 and actions.is_cuda and actions.shape == (n_steps, self.n)
             ptr, mode = actions.data_ptr(), NX_ACT_BUFFER

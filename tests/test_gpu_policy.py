@@ -1,0 +1,137 @@
+"""The fused policy + environment rollout (tensor-core policy inside the step
+kernel) against the oracle's integer MLP, every step, element by element."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from tests.gpu_util import assert_outputs_equal, assert_states_equal, mixed_descs, oracle_batch_for, to_np  # noqa: E402
+from tests.test_oracle_policy import wall_turner  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2407_19396_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def nxmod():
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    return nx
+
+
+def random_policy(A, seed, wmax=12, bmax=300, shift1=3, shift2=6, epsilon=0, epa=128):
+    rng = np.random.default_rng(seed)
+    w = dict(w1=rng.integers(-wmax, wmax + 1, (A, 64, 49)), b1=rng.integers(-bmax, bmax + 1, (A, 64)),
+             w2=rng.integers(-wmax, wmax + 1, (A, 64, 64)), b2=rng.integers(-bmax, bmax + 1, (A, 64)),
+             w3=rng.integers(-wmax, wmax + 1, (A, 7, 64)), b3=rng.integers(-bmax, bmax + 1, (A, 7)))
+    return O.Policy(**w, shift1=shift1, shift2=shift2, epsilon=epsilon, envs_per_agent=epa)
+
+
+def gpu_env_with(nx, descs, seed, pol, **kw):
+    env = nx.Env(descs=descs, seed=seed, autotune=False, action=True, **kw)
+    env.set_policy(pol.w1, pol.b1, pol.w2, pol.b2, pol.w3, pol.b3, pol.shift1, pol.shift2, pol.epsilon,
+                   pol.envs_per_agent)
+    return env
+
+
+KEYS = ("obs_sym", "reward", "terminated", "truncated", "action")
+
+
+@pytest.mark.parametrize("parts,A,epa,eps,T", [
+    ([(O.DOORKEY, 8)], 2, 128, 0, 300),
+    ([(O.DYNOBS, 6)], 1, 256, 2**30, 260),
+    ([(O.EMPTY, 5), (O.FOURROOMS, 11)], 4, 128, 2**28, 300),
+    ([(O.KEYCORRIDOR, 10, 0, 2), (O.LAVA_CROSSING, 9, 0, 2)], 2, 256, 0, 200),
+])
+def test_policy_rollout_matches_the_oracle(parts, A, epa, eps, T):
+    nx = nxmod()
+    descs = mixed_descs(A * epa, parts)
+    pol = random_policy(A, seed=len(parts) + A, epsilon=eps, epa=epa)
+    env = gpu_env_with(nx, descs, 23, pol)
+    env.reset()
+    out = env.rollout(T, policy=True)
+    ob = oracle_batch_for(descs, 23)
+    ob.reset()
+    oo = ob.rollout_policy(T, pol)
+    oo["action"] = oo.pop("actions")
+    assert_outputs_equal(out, oo, keys=KEYS, what="policy rollout")
+    assert_states_equal(env.state()["envs"], ob, what="policy rollout")
+    acts = oo["action"]
+    assert len(np.unique(acts)) >= 3  # the random weights do not collapse to one action
+    assert env.flags() & 4 == 0       # no bounded wait gave up
+    env.close()
+
+
+def test_hand_built_policy_on_the_gpu():
+    nx = nxmod()
+    pol = wall_turner()
+    descs = [(O.FOURROOMS, 13)] * 128
+    env = gpu_env_with(nx, descs, 4, pol)
+    env.reset()
+    out = env.rollout(150, policy=True)
+    ob = oracle_batch_for(descs, 4)
+    ob.reset()
+    oo = ob.rollout_policy(150, pol)
+    oo["action"] = oo.pop("actions")
+    assert_outputs_equal(out, oo, keys=KEYS, what="wall turner")
+    assert set(np.unique(to_np(out["action"]))) <= {1, 2}
+    env.close()
+
+
+def test_policy_then_random_then_policy_continue_one_trajectory():
+    nx = nxmod()
+    descs = [(O.DOORKEY, 6)] * 128
+    pol = random_policy(1, seed=8, epsilon=2**29)
+    env = gpu_env_with(nx, descs, 6, pol)
+    env.reset()
+    a = env.rollout(70, policy=True)
+    b = env.rollout(50)
+    c = env.rollout(90, policy=True)
+    ob = oracle_batch_for(descs, 6)
+    ob.reset()
+    oa = ob.rollout_policy(70, pol)
+    obb = ob.rollout(50)
+    oc = ob.rollout_policy(90, pol)
+    for got, want in ((a, oa), (b, obb), (c, oc)):
+        assert_outputs_equal(got, want, what="interleaved policy / random")
+    # the action output of the random-action rollout is the counter hash's draw
+    g0 = 70
+    ra = to_np(b["action"])
+    for i in (0, 17, 127):
+        e = O.Env(O.DOORKEY, 6, seed=6, env_index=i)
+        assert [e.random_action(g0 + t) for t in range(50)] == list(ra[:, i])
+    env.close()
+
+
+def test_policy_validation():
+    nx = nxmod()
+    pol = random_policy(2, seed=1, epa=128)
+    # a 128-env block of the work list straddling two weight sets
+    env = nx.Env(descs=[(O.DOORKEY, 6)] * 100 + [(O.EMPTY, 6)] * 156, seed=0, autotune=False)
+    with pytest.raises(nx.NavixError) as ei:
+        env.set_policy(pol.w1, pol.b1, pol.w2, pol.b2, pol.w3, pol.b3, 3, 6, 0, 128)
+    assert ei.value.status == nx.NX_E_INVAL
+    env.close()
+    env = nx.Env(O.DOORKEY, 6, 256, seed=0, autotune=False)
+    env.reset()
+    with pytest.raises(nx.NavixError) as ei:
+        env.rollout(3, policy=True)  # no policy yet
+    assert ei.value.status == nx.NX_E_STATE
+    big = pol.b1.copy()
+    big[0, 0] = 1 << 23
+    for args in ((pol.w1, big, pol.w2, pol.b2, pol.w3, pol.b3, 3, 6, 0, 128),   # bias out of range
+                 (pol.w1, pol.b1, pol.w2, pol.b2, pol.w3, pol.b3, 25, 6, 0, 128),  # shift out of range
+                 (pol.w1[:1], pol.b1[:1], pol.w2[:1], pol.b2[:1], pol.w3[:1], pol.b3[:1], 3, 6, 0, 128)):  # too few sets
+        with pytest.raises(nx.NavixError) as ei:
+            env.set_policy(*args)
+        assert ei.value.status == nx.NX_E_INVAL
+    env.close()
