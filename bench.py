@@ -50,6 +50,12 @@ WORKLOADS = {
     "doorkey8_full": dict(desc="DoorKey-8x8, 4096 envs x 1000 steps, seed 1, symbolic + fully observable views "
                                "(symbolic 8x8x3, categorical 8x8, categorical first person 7x7)",
                           parts=[(1, 8)], n=4096, T=1000, seed=1, rgb=False, depth=1000, full=True),
+    # the fused policy + environment rollout (the paper's PPO rollout pattern:
+    # many agents, each stepping its own envs with its own policy weights)
+    "policy": dict(desc="Empty-8x8, 32,768 envs = 256 agents x 128 envs x 1000 steps, seed 5, actions from each "
+                        "agent's integer MLP policy on the tensor cores (categorical first-person view -> 64 -> 64 "
+                        "-> 7, seeded int8 weights), exploration 1/16, symbolic obs",
+                   parts=[(0, 8)], n=32768, T=1000, seed=5, rgb=False, depth=128, policy=True, agents=256),
     # a reduced RGB case sized for ncu captures only (about 2.5 GB written per launch)
     "rgb_small": dict(desc="Dynamic-Obstacles-16x16, 4 balls, 1024 envs x 16 steps, seed 3, RGB + symbolic, 2-slot ring",
                       parts=[(4, 16)], n=1024, T=16, seed=3, rgb=True, depth=2, steps_per_launch=16),
@@ -88,6 +94,18 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def measured_tensor_peak():
+    """Dense bf16 TFLOP/s measured on the GB300s, sustained (the policy
+    kernel runs inside long rollouts), else the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("bf16_tflops_sustained"):
+            return float(d["bf16_tflops_sustained"]), "measured"
+    return 1700.0, "fallback"
 
 
 def kernel_source_hash():
@@ -300,7 +318,17 @@ def run_serving(n_req=2000, budget=2 << 30, load=0.7, seed=4, chunk=64):
             "steps_per_launch": chunk, "mix": "family U{5}, size U{5..19}, n_envs log-U[1, 4096], horizon U{1..512}, seed 4"}
 
 
-def time_rollouts(env, w, out, K, W, flush, per_family=False):
+POLICY_FLOPS = 2 * (64 * 64 + 64 * 64 + 16 * 64)  # per env-step on the tensor cores (K and N padded)
+
+
+def set_bench_policy(env, w):
+    from paper_2407_19396_gb300 import inputs
+
+    pw = inputs.policy_weights(w["seed"], w["agents"])
+    env.set_policy(pw["w1"], pw["b1"], pw["w2"], pw["b2"], pw["w3"], pw["b3"], 3, 6, 1 << 28, w["n"] // w["agents"])
+
+
+def time_rollouts(env, w, out, K, W, flush, per_family=False, policy=False):
     """W untimed rollouts, then K timed ones with CUDA events on the launching
     stream; L2 is flushed between timed rollouts, outside the event windows.
     Returns (per-step ms list, kernel ms, step launches, all launches)."""
@@ -308,7 +336,7 @@ def time_rollouts(env, w, out, K, W, flush, per_family=False):
 
     T, depth = w["T"], w["depth"]
     for _ in range(W):
-        env.rollout(T, depth=depth, out=out, per_family=per_family)
+        env.rollout(T, depth=depth, out=out, per_family=per_family, policy=policy)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -317,7 +345,7 @@ def time_rollouts(env, w, out, K, W, flush, per_family=False):
     for k in range(K):
         flush.fill_(k & 0xFF)
         evs[k][0].record(st)
-        env.rollout(T, depth=depth, out=out, per_family=per_family)
+        env.rollout(T, depth=depth, out=out, per_family=per_family, policy=policy)
         evs[k][1].record(st)
     torch.cuda.synchronize()
     kernel_ms, kl = env.profile_end()
@@ -371,7 +399,9 @@ def main():
     env.reset()
     out = env.alloc_out(w["depth"])
     if args.ncu_case:
-        env.rollout(w["T"], depth=w["depth"], out=out)
+        if w.get("policy"):
+            set_bench_policy(env, w)
+        env.rollout(w["T"], depth=w["depth"], out=out, policy=bool(w.get("policy")))
         torch.cuda.synchronize()
         print(json.dumps({"ncu_case": args.workload, "info": env.info()}), flush=True)
         return 0
@@ -480,6 +510,26 @@ def main():
             extras[name] = rec
             ex.close()
             del ox
+        # the fused policy rollout, beside the random-action rollout of the same envs
+        wx = WORKLOADS["policy"]
+        dx = descs_of(wx)
+        ex = nx.Env(descs=dx, seed=wx["seed"])
+        ex.reset()
+        set_bench_policy(ex, wx)
+        ox = ex.alloc_out(wx["depth"])
+        ms, kms, kl, _ = time_rollouts(ex, wx, ox, 2, 1, flush, policy=True)
+        ms_r, _, _, _ = time_rollouts(ex, wx, ox, 2, 1, flush)
+        rate = len(dx) * wx["T"] * len(ms) / (sum(ms) / 1000)
+        kern_rate = len(dx) * wx["T"] * len(ms) / (kms / 1000)
+        tf = kern_rate * POLICY_FLOPS / 1e12
+        tpeak, tsrc = measured_tensor_peak()
+        extras["policy"] = {"env_steps_per_s": rate, "random_action_env_steps_per_s":
+                            len(dx) * wx["T"] * len(ms_r) / (sum(ms_r) / 1000),
+                            "tensor_tflops": tf, "tensor_frac": tf / tpeak, "tensor_peak": tpeak,
+                            "tensor_peak_source": tsrc, "tensor_flops_per_env_step": POLICY_FLOPS,
+                            "workload": wx["desc"]}
+        ex.close()
+        del ox
         line["extras"] = extras
     if rank == 0 and world == 1 and not args.no_extras:
         line.setdefault("extras", {})["serving"] = run_serving()

@@ -174,11 +174,13 @@ typedef struct {
     int8_t* action;  /* [.., n] the action each step took (device rollouts only) */
 } nx_out;
 
-/* Launch shape in use (after autotuning). */
+/* Launch shape in use (after autotuning); policy_* describe the fused-policy
+ * launches (0 before nx_set_policy). */
 typedef struct {
     int32_t group_lanes, envs_per_cta, staging, n_items, grid_ctas, smem_bytes, steps_per_launch;
     int32_t n_envs, n_families;
     size_t state_bytes, device_bytes;
+    int32_t policy_items, policy_ctas_per_sm, policy_grid_ctas, policy_smem_bytes;
 } nx_info;
 
 void nx_options_default(nx_options* opts);

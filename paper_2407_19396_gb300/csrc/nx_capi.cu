@@ -1075,6 +1075,13 @@ nx_status nx_get_info(const nx_env* env, nx_info* info)
     info->n_families = env->n_families;
     info->state_bytes = nx_state_bytes(env);
     info->device_bytes = env->device_bytes;
+    if (env->d_policy) {
+        nx_launch_shape ps{1, nxp::kRows, 0, 1, 0, false, true};
+        info->policy_items = env->n_items_pol;
+        info->policy_ctas_per_sm = env->per_sm_pol;
+        info->policy_grid_ctas = std::min(env->n_items_pol, env->per_sm_pol * env->sm_count);
+        info->policy_smem_bytes = nx_kernel_smem_bytes(ps, env->cell_stride);
+    }
     return NX_OK;
 }
 

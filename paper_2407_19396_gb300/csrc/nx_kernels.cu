@@ -67,7 +67,7 @@ int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err)
     const int smem = nx_kernel_smem_bytes(s, cell_stride);
     const int threads = s.envs_per_cta * s.group_lanes;
     if (s.full) return nx_kernel_max_ctas_full(s, threads, smem, err);
-    if (s.policy) return occupancy_t<1, false, false, true>(threads, smem, err);
+    if (s.policy) return policy_occupancy(threads, smem, err);
     NX_DISPATCH_G(s.group_lanes, s.rgb, false, occupancy_t, threads, smem, err)
 }
 

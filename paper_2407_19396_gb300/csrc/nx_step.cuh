@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "navixgb.h"
 #include "nx_device.cuh"
 #include "nx_internal.h"
@@ -632,6 +634,39 @@ int occupancy_t(int threads, int smem, int* err)
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, threads, smem);
     *err = (int)e;
     return blocks;
+}
+
+// Resident blocks per SM of the fused-policy instantiation, from its shared
+// memory, registers and threads and the SM's 512 tensor-memory columns (64
+// per block).  The occupancy API reports one block for this kernel (it does
+// not size the tensor memory a kernel allocates at run time), while the
+// launch itself fits as many blocks as the resources allow; a block whose
+// allocation found the columns taken would wait for them, never fail.
+inline int policy_occupancy(int threads, int smem, int* err)
+{
+    auto k = nx_step_kernel<1, false, false, true>;
+    int dev = 0, optin = 0, smem_sm = 0, reserved = 0, regs_sm = 0, threads_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+    *err = (int)e;
+    if (e != cudaSuccess) return 0;
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if (smem > dyn_max) return 0;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    *err = (int)e;
+    if (e != cudaSuccess) return 0;
+    const int regs_block = ((fa.numRegs * 32 + 255) & ~255) * (threads / 32);  // per-warp allocation granule 256
+    int n = smem_sm / (smem + (int)fa.sharedSizeBytes + reserved);
+    n = std::min(n, regs_sm / std::max(regs_block, 1));
+    n = std::min(n, threads_sm / threads);
+    n = std::min(n, 512 / 64);
+    return std::max(n, 0);
 }
 
 #define NX_DISPATCH_G(G_, RGB_, FULL_, FN, ...)                                                   \

@@ -205,3 +205,18 @@ def random_actions(seed: int, shape, n_actions: int = 7, invalid_fraction: float
         bad = rng.random(size=shape) < invalid_fraction
         a = np.where(bad, rng.choice(np.array([-3, -1, 7, 9, 100, -128]), size=shape), a)
     return a.astype(np.int8)
+
+
+def policy_weights(seed: int, n_agents: int, wmax: int = 12, bmax: int = 300) -> dict:
+    """Seeded synthetic weights of the fused rollout's integer MLP policy:
+    w1 [A, 64, 49], w2 [A, 64, 64], w3 [A, 7, 64] int8 uniform in
+    [-wmax, wmax]; b1, b2 [A, 64], b3 [A, 7] int32 uniform in [-bmax, bmax].
+    (No trained weights exist here: these stand in for a policy's parameters.)"""
+    rng = np.random.default_rng(seed)
+    A = int(n_agents)
+    return dict(w1=rng.integers(-wmax, wmax + 1, (A, 64, 49)).astype(np.int8),
+                b1=rng.integers(-bmax, bmax + 1, (A, 64)).astype(np.int32),
+                w2=rng.integers(-wmax, wmax + 1, (A, 64, 64)).astype(np.int8),
+                b2=rng.integers(-bmax, bmax + 1, (A, 64)).astype(np.int32),
+                w3=rng.integers(-wmax, wmax + 1, (A, 7, 64)).astype(np.int8),
+                b3=rng.integers(-bmax, bmax + 1, (A, 7)).astype(np.int32))

@@ -75,7 +75,9 @@ class nx_info(ctypes.Structure):
     _fields_ = [("group_lanes", ctypes.c_int32), ("envs_per_cta", ctypes.c_int32), ("staging", ctypes.c_int32),
                 ("n_items", ctypes.c_int32), ("grid_ctas", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("steps_per_launch", ctypes.c_int32), ("n_envs", ctypes.c_int32), ("n_families", ctypes.c_int32),
-                ("state_bytes", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t)]
+                ("state_bytes", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
+                ("policy_items", ctypes.c_int32), ("policy_ctas_per_sm", ctypes.c_int32),
+                ("policy_grid_ctas", ctypes.c_int32), ("policy_smem_bytes", ctypes.c_int32)]
 
 
 class nx_request(ctypes.Structure):
