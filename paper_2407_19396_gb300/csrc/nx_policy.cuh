@@ -154,38 +154,68 @@ __device__ __forceinline__ void store_zero_row(uint8_t* sA, int r)
     for (int k0 = 0; k0 < kK; k0 += 8) *reinterpret_cast<uint4*>(sA + tile_offset(r, k0)) = make_uint4(0, 0, 0, 0);
 }
 
-// All 128 threads of the block: the greedy action of this thread's row (rows
-// of inactive threads are computed and ignored).  `phase` tracks the
-// mbarrier's parity; `ok` turns false if a wait gave up.
-__device__ __forceinline__ int policy_greedy(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar,
+// Requantises 16 accumulators of this thread's row into bf16 activations:
+// clamp(floor((acc + b) / 2^sh), 0, 255) in f32, exact since acc + b is an
+// integer below 2^24 and the scaling is by a power of two.
+__device__ __forceinline__ void requant_row16(uint8_t* sA, int r, int k0, const uint32_t (&v)[16], const int32_t* b,
+                                              float scale)
+{
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float h0 = floorf((__uint_as_float(v[2 * j]) + (float)b[2 * j]) * scale);
+        float h1 = floorf((__uint_as_float(v[2 * j + 1]) + (float)b[2 * j + 1]) * scale);
+        h0 = fminf(fmaxf(h0, 0.0f), 255.0f);
+        h1 = fminf(fmaxf(h1, 0.0f), 255.0f);
+        const __nv_bfloat162 p2 = __floats2bfloat162_rn(h0, h1);  // low half: h0
+        w[j] = *reinterpret_cast<const uint32_t*>(&p2);
+    }
+    *reinterpret_cast<uint4*>(sA + tile_offset(r, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(sA + tile_offset(r, k0 + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// 2^-sh as an f32 (sh in 0..24)
+__device__ __forceinline__ float pow2_neg(int sh) { return __int_as_float((127 - sh) << 23); }
+
+// All 128 threads of the block: after every thread wrote its input row, the
+// first layer's MMA is issued (it then runs while the block does other work).
+__device__ __forceinline__ void policy_issue_first(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar)
+{
+    sync_for_mma();
+    if (threadIdx.x == 0) {
+        mma_k64(tmem, sA, sW + kW1, idesc_bf16(kRows, kK));
+        mma_commit(mbar);
+    }
+}
+
+// All 128 threads of the block, after policy_issue_first: the greedy action
+// of this thread's row (rows of inactive threads are computed and ignored).
+// `phase` tracks the mbarrier's parity; `ok` turns false if a wait gave up.
+__device__ __forceinline__ int policy_finish(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar,
                                              uint32_t& phase, int n_act, int shift1, int shift2, bool& ok)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
 #pragma unroll 1
     for (int layer = 0; layer < 2; ++layer) {
-        sync_for_mma();
-        if (tid == 0) {
-            mma_k64(tmem, sA, sW + (layer ? kW2 : kW1), idesc_bf16(kRows, kK));
-            mma_commit(mbar);
+        if (layer == 1) {
+            sync_for_mma();
+            if (tid == 0) {
+                mma_k64(tmem, sA, sW + kW2, idesc_bf16(kRows, kK));
+                mma_commit(mbar);
+            }
         }
         ok = mbar_wait(mbar, phase) && ok;
         phase ^= 1u;
         __syncwarp();  // tcgen05.ld is warp-collective: converge after the per-thread wait
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int32_t* b = reinterpret_cast<const int32_t*>(sW + (layer ? kB2 : kB1));
-        const int sh = layer ? shift2 : shift1;
+        const float scale = pow2_neg(layer ? shift2 : shift1);
 #pragma unroll 1
         for (int c0 = 0; c0 < kK; c0 += 16) {
             uint32_t v[16];
             tmem_ld16(trow + (uint32_t)c0, v);
-            int h[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int acc = __float2int_rn(__uint_as_float(v[j])) + b[c0 + j];
-                h[j] = min(max(acc >> sh, 0), 255);
-            }
-            store_row16(sA, tid, c0, h);
+            requant_row16(sA, tid, c0, v, b + c0, scale);
         }
     }
     sync_for_mma();

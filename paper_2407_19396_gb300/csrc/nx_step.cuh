@@ -355,6 +355,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             } else {
                 nxp::store_zero_row(sA, tid);
             }
+            if (steps > 0) nxp::policy_issue_first(sA, sW, tmem, &s_mbar);
         }
 
         // steps == 0 with reset_all: one emission of the episode-0 start state
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             int term = 0, trunc = 0;
             int pol_act = 0;  // fused policy: the greedy action of every env (all threads take part)
             if constexpr (POL)
-                pol_act = nxp::policy_greedy(sA, sW, tmem, &s_mbar, phase, (int)n_act, rq->shift1, rq->shift2, pol_ok);
+                pol_act = nxp::policy_finish(sA, sW, tmem, &s_mbar, phase, (int)n_act, rq->shift1, rq->shift2, pol_ok);
             if (G > 1 && rnd && (s % G) == 0) {
                 // the random actions of the next G steps depend only on the step
                 // counter, so the group's lanes draw them in parallel
@@ -489,6 +490,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     eps += (uint32_t)(term || trunc);
                 }
             }
+            // fused policy: the next step's first layer runs during the stores
+            if constexpr (POL)
+                if (s + 1 < emissions) nxp::policy_issue_first(sA, sW, tmem, &s_mbar);
             // Each warp stages the symbolic outputs of its own envs (placed at
             // the same address modulo 16 as their destination) and stores them
             // with 16-byte vectors, in `phases` parts; warps never wait for
