@@ -147,21 +147,44 @@ __device__ __forceinline__ void group_draws(const Grp<G>& grp, int n, uint32_t (
     }
 }
 
+// Position of the (k+1)-th set bit of b (k < popc(b)): halving search on
+// the bit counts of the low halves.
+__device__ __forceinline__ int nth_set_bit(uint32_t b, int k)
+{
+    int pos = 0;
+#pragma unroll
+    for (int sh = 16; sh >= 1; sh >>= 1) {
+        const int c = __popc(b & ((1u << sh) - 1u));
+        const bool up = k >= c;
+        k -= up ? c : 0;
+        b = up ? (b >> sh) : b;
+        pos += up ? sh : 0;
+    }
+    return pos;
+}
+
 // Number of empty cells in the rectangle [x0,x1] x [y0,y1] not counting cell
 // index `skip` (-1 for none).
 template <int G>
 __device__ int count_free(const Grp<G>& grp, const uint8_t* g, int W, int x0, int x1, int y0, int y1, int skip)
 {
+    // lane l visits rectangle positions r = l, l + G, ..; its column and row
+    // advance by G mod w and G / w per round (one wrap at most), no division
     const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+    const int dy = G / w, dx = G - dy * w;
+    int ry = grp.lane / w, rx = grp.lane - ry * w;
     int total = 0;
     for (int r0 = 0; r0 < n; r0 += G) {
-        const int r = r0 + grp.lane;
-        bool f = false;
-        if (r < n) {
-            const int yy = y0 + r / w, xx = x0 + r % w, ci = yy * W + xx;
-            f = g[ci] == C_EMPTY && ci != skip;
-        }
+        const bool in = r0 + grp.lane < n;
+        const int ci = in ? (y0 + ry) * W + x0 + rx : 0;  // lanes past the end read cell 0
+        const bool f = in && g[ci] == C_EMPTY && ci != skip;
         total += __popc(grp.ballot(f));
+        rx += dx;
+        ry += dy;
+        if (rx >= w) {
+            rx -= w;
+            ry += 1;
+        }
     }
     return total;
 }
@@ -172,22 +195,22 @@ template <int G>
 __device__ int kth_free(const Grp<G>& grp, const uint8_t* g, int W, int x0, int x1, int y0, int y1, int skip, int k)
 {
     const int w = x1 - x0 + 1, n = w * (y1 - y0 + 1);
+    const int dy = G / w, dx = G - dy * w;
+    int ry = grp.lane / w, rx = grp.lane - ry * w;
     for (int r0 = 0; r0 < n; r0 += G) {
-        const int r = r0 + grp.lane;
-        bool f = false;
-        int ci = 0;
-        if (r < n) {
-            const int yy = y0 + r / w, xx = x0 + r % w;
-            ci = yy * W + xx;
-            f = g[ci] == C_EMPTY && ci != skip;
-        }
-        uint32_t b = grp.ballot(f);
+        const bool in = r0 + grp.lane < n;
+        const int ci = in ? (y0 + ry) * W + x0 + rx : 0;  // lanes past the end read cell 0
+        const bool f = in && g[ci] == C_EMPTY && ci != skip;
+        const uint32_t b = grp.ballot(f);
         const int cnt = __popc(b);
-        if (k < cnt) {
-            for (int i = 0; i < k; ++i) b &= b - 1u;
-            return grp.shfl(ci, __ffs(b) - 1);
-        }
+        if (k < cnt) return grp.shfl(ci, nth_set_bit(b, k));
         k -= cnt;
+        rx += dx;
+        ry += dy;
+        if (rx >= w) {
+            rx -= w;
+            ry += 1;
+        }
     }
     return -1;
 }
@@ -373,11 +396,17 @@ template <int G>
 __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int n_balls, int variant,
                                              uint64_t seed, uint32_t key_env, uint32_t episode, AgentReg& a)
 {
+    // empty cells four at a time (the env's slot is a whole number of words
+    // at least S * S bytes long), then the four border lines of walls
     const int HW = S * S;
-    for (int c = grp.lane; c < HW; c += G) {
-        const int y = c / S, x = c - y * S;
-        const bool border = x == 0 || y == 0 || x == S - 1 || y == S - 1;
-        g[c] = (uint8_t)(border ? C_WALL : C_EMPTY);
+    constexpr uint32_t kEmpty4 = C_EMPTY * 0x01010101u;
+    for (int c4 = grp.lane; c4 < (HW + 3) / 4; c4 += G) reinterpret_cast<uint32_t*>(g)[c4] = kEmpty4;
+    grp.sync();
+    for (int i = grp.lane; i < S; i += G) {
+        g[i] = (uint8_t)C_WALL;
+        g[(S - 1) * S + i] = (uint8_t)C_WALL;
+        g[i * S] = (uint8_t)C_WALL;
+        g[i * S + S - 1] = (uint8_t)C_WALL;
     }
     a.x = 1;
     a.y = 1;
