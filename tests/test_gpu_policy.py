@@ -135,3 +135,31 @@ def test_policy_validation():
             env.set_policy(*args)
         assert ei.value.status == nx.NX_E_INVAL
     env.close()
+
+
+def test_policy_snapshot_resume_and_shards():
+    nx = nxmod()
+    pol = random_policy(4, seed=12, epsilon=2**29, epa=128)
+    # one context of 512 envs ...
+    whole = gpu_env_with(nx, [(O.DOORKEY, 8)] * 512, 31, pol)
+    whole.reset()
+    a = whole.rollout(100, policy=True)
+    # ... equals two shards of 256 over disjoint global env ranges, each with the whole weight table
+    outs = []
+    for base in (0, 256):
+        sh = nx.Env(descs=[(O.DOORKEY, 8)] * 256, seed=31, autotune=False, action=True, env_index_base=base)
+        sh.set_policy(pol.w1, pol.b1, pol.w2, pol.b2, pol.w3, pol.b3, pol.shift1, pol.shift2, pol.epsilon, 128)
+        sh.reset()
+        outs.append(sh.rollout(100, policy=True))
+        sh.close()
+    for k in KEYS:
+        np.testing.assert_array_equal(to_np(a[k]), np.concatenate([to_np(o[k]) for o in outs], axis=1), err_msg=k)
+    # a snapshot taken mid-rollout resumes the same trajectory
+    snap = whole.state_bytes()
+    b1 = whole.rollout(60, policy=True)
+    b1 = {k: to_np(v) for k, v in b1.items() if v is not None}
+    whole.set_state(snap)
+    b2 = whole.rollout(60, policy=True)
+    for k in KEYS:
+        np.testing.assert_array_equal(b1[k], to_np(b2[k]), err_msg=k)
+    whole.close()
