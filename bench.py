@@ -56,6 +56,11 @@ WORKLOADS = {
                         "agent's integer MLP policy on the tensor cores (categorical first-person view -> 64 -> 64 "
                         "-> 7, seeded int8 weights), exploration 1/16, symbolic obs",
                    parts=[(0, 8)], n=32768, T=1000, seed=5, rgb=False, depth=128, policy=True, agents=256),
+    # the paper's own batch-mode scale: 2^21 envs of Empty-8x8 unrolled for
+    # 1000 steps (its reported wall time: almost always below 1 s on an A100)
+    "paper_scale": dict(desc="Empty-8x8, 2,097,152 envs x 1000 steps, seed 6, uniform random actions over 7, "
+                             "symbolic obs (1-slot output ring)",
+                        parts=[(0, 8)], n=1 << 21, T=1000, seed=6, rgb=False, depth=1),
     # a reduced RGB case sized for ncu captures only (about 2.5 GB written per launch)
     "rgb_small": dict(desc="Dynamic-Obstacles-16x16, 4 balls, 1024 envs x 16 steps, seed 3, RGB + symbolic, 2-slot ring",
                       parts=[(4, 16)], n=1024, T=16, seed=3, rgb=True, depth=2, steps_per_launch=16),
@@ -545,6 +550,20 @@ def main():
             extras[name] = rec
             ex.close()
             del ox
+        # the paper's batch-mode scale: wall time of one 1000-step rollout of 2^21 envs
+        wx = WORKLOADS["paper_scale"]
+        dx = descs_of(wx)
+        ex = nx.Env(descs=dx, seed=wx["seed"])
+        ex.reset()
+        ox = ex.alloc_out(wx["depth"])
+        ms, kms, kl, _ = time_rollouts(ex, wx, ox, 2, 1, flush)
+        bx = alg_bytes(wx, dx, ex.info()["steps_per_launch"])
+        extras["paper_scale"] = {"env_steps_per_s": len(dx) * wx["T"] * len(ms) / (sum(ms) / 1000),
+                                 "rollout_ms": min(ms), "hbm_frac": bx * len(ms) / (kms / 1000) / 1e9 / peak,
+                                 "launch_shape": {k: ex.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas")},
+                                 "workload": wx["desc"]}
+        ex.close()
+        del ox
         # the fused policy rollout, beside the random-action rollout of the same envs
         wx = WORKLOADS["policy"]
         dx = descs_of(wx)
