@@ -493,6 +493,14 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             // fused policy: the next step's first layer runs during the stores
             if constexpr (POL)
                 if (s + 1 < emissions) nxp::policy_issue_first(sA, sW, tmem, &s_mbar);
+            // Groups of 8 or more lanes (at most 4 envs per warp) write each
+            // cell's three bytes straight to global memory (measured faster
+            // than staging there); the staged path serves the narrow groups
+            // and the outputs that read the staged record (digest, the
+            // categorical first-person view).
+            if (G >= 8 && !digest && !(FULL && obs_cat_fp)) {
+                if (active && obs_sym) write_view(grp, vo, obs_sym + ((size_t)slot * nreq + local) * NX_OBS_SYM_BYTES);
+            } else {
             // Each warp stages the symbolic outputs of its own envs (placed at
             // the same address modulo 16 as their destination) and stores them
             // with 16-byte vectors, in `phases` parts; warps never wait for
@@ -560,6 +568,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     if (dst && hi > lo) coop_copy(dst, stage, (hi - lo) * NX_OBS_SYM_BYTES, lane32, 32);
                     __syncwarp();
                 }
+            }
             }
             if (RGB && (obs_rgb || obs_rgb_full)) {
                 __syncthreads();
