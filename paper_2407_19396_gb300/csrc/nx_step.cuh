@@ -446,7 +446,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     env_step(grp, mygrid, S, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
                              time_cost, reward, term, trunc);
                 }
-                grp.sync();
+                // (every grid write above -- a reset, a ball move, the action's
+                // write -- ends with a group barrier, so the view sees it)
                 render_view(grp, mygrid, S, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
                             RGB && obs_rgb ? stiles + gi * 49 : nullptr);
                 if constexpr (POL) nxp::store_obs_row(sA, tid, vo.sw);  // the next step's policy input
