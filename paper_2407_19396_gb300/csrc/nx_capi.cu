@@ -886,7 +886,7 @@ nx_status nx_autotune(nx_env* env)
 {
     env->tuned = true;
     const int lanes[6] = {1, 2, 4, 8, 16, 32};
-    const int threads[3] = {64, 128, 256};
+    const int threads[4] = {32, 64, 128, 256};
     const size_t N = (size_t)env->n_envs;
     // scratch: state copy + one output slot
     nx_agent* sa = (nx_agent*)nx_dev_alloc(env, sizeof(nx_agent) * N);
