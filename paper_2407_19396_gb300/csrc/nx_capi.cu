@@ -885,7 +885,9 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
 nx_status nx_autotune(nx_env* env)
 {
     env->tuned = true;
-    const int lanes[6] = {1, 2, 4, 8, 16, 32};
+    // (2 lanes per env, never the fastest in any measured workload and the
+    // slowest to try, stays available as an explicit shape only)
+    const int lanes[5] = {1, 4, 8, 16, 32};
     const int threads[4] = {32, 64, 128, 256};
     const size_t N = (size_t)env->n_envs;
     // scratch: state copy + one output slot
