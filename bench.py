@@ -113,9 +113,14 @@ def measured_tensor_peak():
     return 1700.0, "fallback"
 
 
+# the files that define the step kernels (host-side files do not change a
+# captured kernel)
+KERNEL_SOURCES = ("nx_device.cuh", "nx_internal.h", "nx_kernels.cu", "nx_kernels_full.cu", "nx_policy.cuh", "nx_step.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2407_19396_gb300", "csrc"))):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2407_19396_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
