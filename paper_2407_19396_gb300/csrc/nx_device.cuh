@@ -273,72 +273,88 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
 }
 
 // L7 crossings: N rivers of lava or wall (see reset_layout), kept out of line
-// so that its small local arrays do not weigh on the step kernel's registers.
+// to hold down the step kernel's registers.  Its shuffles run on registers:
+// an array indexed by a loop counter would sit in local memory and be charged
+// to the calling kernel's stack frame.
 template <int G>
 __device__ __noinline__ void crossing_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int variant,
                                              uint64_t seed, uint32_t key_env, uint32_t episode)
 {
     const int HW = S * S;
-        // rivers: a partial Fisher-Yates choice among rows then columns 2, 4, ..
-        // S-3; kept as row/column bitmasks, so their sorted order is the bit order
-        int ck[2 * NX_MAX_SIZE];
-        int m = 0;
-        for (int y = 2; y <= S - 3; y += 2) ck[m++] = y;            // horizontal: the row
-        for (int x = 2; x <= S - 3; x += 2) ck[m++] = 0x100 | x;    // vertical: 0x100 | the column
-        uint32_t k = 0;
-        for (int i = 0; i < variant; ++i) {
-            const int j = i + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++), (uint32_t)(m - i));
-            const int t = ck[i];
-            ck[i] = ck[j];
-            ck[j] = t;
+    // rivers: a partial Fisher-Yates choice among rows then columns 2, 4, ..
+    // S-3 (at most 16 candidates for S <= 19), one byte each in two 64-bit
+    // words: the row y for a horizontal river, 0x80 | x for a vertical one;
+    // the choice is kept as row/column bitmasks, so their sorted order is the
+    // bit order
+    uint64_t ck[2] = {0ull, 0ull};  // constant indexes only after unrolling
+    auto get = [&](int i) -> uint32_t {
+        const uint64_t w = i < 8 ? ck[0] : ck[1];
+        return (uint32_t)(w >> (8 * (i & 7))) & 0xFFu;
+    };
+    auto put = [&](int i, uint32_t v) {
+        const int sh = 8 * (i & 7);
+        const uint64_t cleared = ((i < 8 ? ck[0] : ck[1]) & ~(0xFFull << sh)) | ((uint64_t)v << sh);
+        if (i < 8)
+            ck[0] = cleared;
+        else
+            ck[1] = cleared;
+    };
+    int m = 0;
+    for (int y = 2; y <= S - 3; y += 2) put(m++, (uint32_t)y);           // horizontal: the row
+    for (int x = 2; x <= S - 3; x += 2) put(m++, 0x80u | (uint32_t)x);   // vertical: 0x80 | the column
+    uint32_t k = 0;
+    for (int i = 0; i < variant; ++i) {
+        const int j = i + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++), (uint32_t)(m - i));
+        const uint32_t ti = get(i), tj = get(j);
+        put(i, tj);
+        put(j, ti);
+    }
+    uint32_t hmask = 0, vmask = 0;
+    for (int i = 0; i < variant; ++i) {
+        const uint32_t c = get(i);
+        if (c & 0x80u)
+            vmask |= 1u << (c & 0x7Fu);
+        else
+            hmask |= 1u << c;
+    }
+    const uint32_t obst = family == NX_LAVA_CROSSING ? (uint32_t)C_LAVA : (uint32_t)C_WALL;
+    grp.sync();
+    for (int c = grp.lane; c < HW; c += G) {
+        const int y = c / S, x = c - y * S;
+        if (x >= 1 && y >= 1 && x <= S - 2 && y <= S - 2 && (((hmask >> y) | (vmask >> x)) & 1u))
+            g[c] = (uint8_t)obst;
+    }
+    // order of crossings: east moves (vertical rivers) first, then south
+    // moves, shuffled by Fisher-Yates from the last position down; bit i of
+    // `east` is set when move i goes east
+    const int nv = __popc(vmask), nh = __popc(hmask), L = nv + nh;
+    uint32_t east = (1u << nv) - 1u;
+    for (int i = L - 1; i >= 1; --i) {
+        const int j = bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++), (uint32_t)(i + 1));
+        if (((east >> i) ^ (east >> j)) & 1u) east ^= (1u << i) | (1u << j);
+    }
+    // walk the rooms from the top-left one; each move opens one cell of
+    // the river it crosses, drawn within the current room's span
+    int x_lo = 0, y_lo = 0;                 // the current room's west / north bounds
+    uint32_t vrest = vmask, hrest = hmask;  // rivers not yet crossed, east / south of the room
+    grp.sync();
+    for (int i = 0; i < L; ++i) {
+        const int x_hi = vrest ? __ffs(vrest) - 1 : S - 1;
+        const int y_hi = hrest ? __ffs(hrest) - 1 : S - 1;
+        if ((east >> i) & 1u) {
+            const int y = y_lo + 1 + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++),
+                                             (uint32_t)(y_hi - y_lo - 1));
+            if (grp.lane == 0) g[y * S + x_hi] = (uint8_t)C_EMPTY;
+            x_lo = x_hi;
+            vrest &= vrest - 1u;
+        } else {
+            const int x = x_lo + 1 + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++),
+                                             (uint32_t)(x_hi - x_lo - 1));
+            if (grp.lane == 0) g[y_hi * S + x] = (uint8_t)C_EMPTY;
+            y_lo = y_hi;
+            hrest &= hrest - 1u;
         }
-        uint32_t hmask = 0, vmask = 0;
-        for (int i = 0; i < variant; ++i) {
-            if (ck[i] & 0x100)
-                vmask |= 1u << (ck[i] & 0xFF);
-            else
-                hmask |= 1u << ck[i];
-        }
-        const uint32_t obst = family == NX_LAVA_CROSSING ? (uint32_t)C_LAVA : (uint32_t)C_WALL;
-        grp.sync();
-        for (int c = grp.lane; c < HW; c += G) {
-            const int y = c / S, x = c - y * S;
-            if (x >= 1 && y >= 1 && x <= S - 2 && y <= S - 2 && (((hmask >> y) | (vmask >> x)) & 1u))
-                g[c] = (uint8_t)obst;
-        }
-        // order of crossings: east moves (vertical rivers) first, then south
-        // moves, shuffled by Fisher-Yates from the last position down
-        const int nv = __popc(vmask), nh = __popc(hmask), L = nv + nh;
-        int path[2 * NX_MAX_SIZE];
-        for (int i = 0; i < L; ++i) path[i] = i < nv ? 1 : 0;
-        for (int i = L - 1; i >= 1; --i) {
-            const int j = bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++), (uint32_t)(i + 1));
-            const int t = path[i];
-            path[i] = path[j];
-            path[j] = t;
-        }
-        // walk the rooms from the top-left one; each move opens one cell of
-        // the river it crosses, drawn within the current room's span
-        int x_lo = 0, y_lo = 0;              // the current room's west / north bounds
-        uint32_t vrest = vmask, hrest = hmask;  // rivers not yet crossed, east / south of the room
-        grp.sync();
-        for (int i = 0; i < L; ++i) {
-            const int x_hi = vrest ? __ffs(vrest) - 1 : S - 1;
-            const int y_hi = hrest ? __ffs(hrest) - 1 : S - 1;
-            if (path[i]) {
-                const int y = y_lo + 1 + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++),
-                                                 (uint32_t)(y_hi - y_lo - 1));
-                if (grp.lane == 0) g[y * S + x_hi] = (uint8_t)C_EMPTY;
-                x_lo = x_hi;
-                vrest &= vrest - 1u;
-            } else {
-                const int x = x_lo + 1 + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++),
-                                                 (uint32_t)(x_hi - x_lo - 1));
-                if (grp.lane == 0) g[y_hi * S + x] = (uint8_t)C_EMPTY;
-                y_lo = y_hi;
-                hrest &= hrest - 1u;
-            }
-        }
+    }
 }
 
 // L10 KeyCorridor S{s}R{R} (variant R - 1): a 3 x R block of rooms of side s
@@ -424,7 +440,7 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
     }
     uint32_t d[8];
     const int n_draws = family == NX_DOORKEY ? 5 : family == NX_FOURROOMS ? 7 : family == NX_LAVAGAP ? 2
-                        : family == NX_DYNOBS ? n_balls : family == NX_EMPTY_RANDOM ? 2
+                        : family == NX_EMPTY_RANDOM ? 2
                         : family == NX_GOTODOOR ? 8 : 0;
     group_draws(grp, n_draws, d,
                 [&](uint32_t k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k); });
@@ -532,15 +548,26 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         grp.sync();
         const int agent = 1 * S + 1;
         a.nb = n_balls;
+        // ball b's column / row go to byte b of px / py and its draw k = b is
+        // taken in the loop, so that no array is indexed by the loop counter
+        // (that would move a.bx / a.by and the draws to local memory)
+        uint32_t px = 0, py = 0;
         for (int b = 0; b < n_balls; ++b) {
+            const uint32_t db = draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, (uint32_t)b);
             const int n = count_free(grp, g, S, 1, S - 2, 1, S - 2, agent);
-            const int bc = kth_free(grp, g, S, 1, S - 2, 1, S - 2, agent, bounded(d[b], (uint32_t)n));
+            const int bc = kth_free(grp, g, S, 1, S - 2, 1, S - 2, agent, bounded(db, (uint32_t)n));
             if (bc < 0) return false;
             grp.sync();
             if (grp.lane == 0) g[bc] = (uint8_t)C_BALL_BLUE;
             grp.sync();
-            a.bx[b] = bc % S;
-            a.by[b] = bc / S;
+            const int by = bc / S;
+            px |= (uint32_t)(bc - by * S) << (8 * b);
+            py |= (uint32_t)by << (8 * b);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            a.bx[b] = (px >> (8 * b)) & 0xFFu;
+            a.by[b] = (py >> (8 * b)) & 0xFFu;
         }
     }
     grp.sync();
