@@ -705,8 +705,12 @@ __device__ __forceinline__ uint32_t tile_of_triple(bool visible, bool agent_cell
 // stores the 147 symbolic bytes (row-major [vy][vx][ent, col, st], unseen
 // cells 0) at `sym`.  `dec` maps a cell code to its observation triple.
 //
-// G > 1: lane l owns cells c = l, l + G, ...; a ballot per round assembles the
-// transparency mask; each lane stores its cells' three bytes.
+// G >= 8: one view row per 8 lanes -- in round k, lane l holds cell
+// (vx, vy) = (l % 8, k G/8 + l / 8) (lanes with vx = 7 or vy > 6 idle), so a
+// round's ballot carries whole rows at byte offsets; the occlusion reads
+// and writes those bytes and a lane's visibility bit is bit l of its round.
+// G = 2, 4: lane l owns cells c = l, l + G, ...; a ballot per round assembles
+// the 49-bit transparency mask.  Each lane stores its cells' three bytes.
 // G = 1: the 49 codes are packed four per register, the transparency mask is
 // gathered four cells at a time from the opaque bits, and the byte stream is
 // stored as 36 funnel-shifted 32-bit words plus three single bytes.
@@ -774,6 +778,44 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
             out.sw[3 * m + 2] = (tri[4 * m + 2] >> 16) | (tri[4 * m + 3] << 8);
         }
         out.sw[36] = tri[48];
+    } else if constexpr (G >= 8) {
+        constexpr int RPK = G / 8, K = (7 + RPK - 1) / RPK;  // view rows per round, rounds
+        static_assert(K == (49 + G - 1) / G, "ViewOut holds one triple per round");
+        const int vx = grp.lane & 7, r0 = grp.lane >> 3;
+        const uint32_t carried = a.carry ? a.carry : (uint32_t)C_EMPTY;
+        uint32_t code[K], tw[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int vy = k * RPK + r0;
+            const bool cell = vx < 7 && vy < 7;
+            // the in-grid test and the agent's cell (3, 6) as selects
+            const bool in = cell && ((v.colmask >> vx) & (v.rowmask >> vy) & 1u);
+            const uint32_t ld = in ? (uint32_t)g[v.idx0 + vx * v.dR - vy * v.dF] : (uint32_t)C_WALL;
+            const uint32_t cd = (vy == 6 && vx == 3) ? carried : ld;
+            code[k] = cd;
+            tw[k] = grp.ballot(cell && !(cd & OPAQUE));  // row k RPK + r: bits 8 r .. 8 r + 6
+        }
+        // rows from the agent's (6) to the farthest (0), as in occlusion()
+        uint32_t vw[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) vw[k] = 0u;
+        uint32_t seed = 1u << 3;
+#pragma unroll
+        for (int j = 6; j >= 0; --j) {
+            const int k = j / RPK, sh = 8 * (j % RPK);
+            const uint32_t t = (tw[k] >> sh) & 0x7Fu;
+            const uint32_t e = occ ? (uint32_t)occ[(seed << 7) | t] : (uint32_t)__ldg(&occ_table.v[(seed << 7) | t]);
+            vw[k] |= (e & 0x7Fu) << sh;
+            seed = e >> 7;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int vy = k * RPK + r0;
+            const bool vb = (vw[k] >> grp.lane) & 1u;  // only cells have their bit set
+            out.tri[k] = vb ? dec[code[k]] : 0u;
+            if (tiles && vx < 7 && vy < 7)
+                tiles[vy * 7 + vx] = (uint16_t)tile_of_triple(vb, vy == 6 && vx == 3, out.tri[k]);
+        }
     } else {
         constexpr int K = (49 + G - 1) / G;
         uint32_t code[K];
@@ -811,6 +853,19 @@ __device__ __forceinline__ void write_view(const Grp<G>& grp, const ViewOut<G>& 
 #pragma unroll
         for (int i = 0; i < 36; ++i) wd[i] = __funnelshift_r(out.sw[i], out.sw[i + 1], 8 * head);
         for (uint32_t i = head; i < 3; ++i) sym[144 + i] = (uint8_t)(out.sw[36] >> (8 * i));
+    } else if constexpr (G >= 8) {
+        constexpr int RPK = G / 8, K = (7 + RPK - 1) / RPK;
+        const int vx = grp.lane & 7, r0 = grp.lane >> 3;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int vy = k * RPK + r0, c = vy * 7 + vx;
+            if (vx < 7 && vy < 7) {
+                const uint32_t tri = out.tri[k];
+                sym[3 * c + 0] = (uint8_t)tri;
+                sym[3 * c + 1] = (uint8_t)(tri >> 8);
+                sym[3 * c + 2] = (uint8_t)(tri >> 16);
+            }
+        }
     } else {
         constexpr int K = (49 + G - 1) / G;
 #pragma unroll

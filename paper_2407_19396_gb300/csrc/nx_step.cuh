@@ -229,7 +229,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     __shared__ __align__(8) uint64_t s_mbar;  // fused policy: MMA completion
     __shared__ uint32_t s_tmem;               // fused policy: tensor-memory base address
     __shared__ uint32_t s_dec[256];  // cell code -> observation triple
-    __shared__ uint32_t s_sink[4];   // target of the stores of absent outputs
     // the occlusion table in shared memory for groups of 8 or more lanes (the
     // narrow groups run many more envs per block, whose grids need the space)
     constexpr bool kSmemOcc = G >= 8;
@@ -363,9 +362,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         const bool rnd = act_mode == NX_ACT_RANDOM;
         const uint32_t n_act = family == NX_DYNOBS ? 3u : 7u;
         uint32_t slot = call0 % (uint32_t)depth;
+        // this env's row of the output ring (slot * n_envs + local), advanced
+        // by one add per step
+        size_t o = (size_t)slot * nreq + local;
         uint32_t my_draw = 0;  // G > 1: this lane's random-action draw for step s0 + lane
         for (int s = 0; s < emissions; ++s) {
-            const size_t row0 = (size_t)slot * nreq + item.local_begin;
+            const size_t row0 = o - (size_t)gi;  // the item's first env in this slot
             uint8_t* sym_dst = obs_sym ? obs_sym + row0 * NX_OBS_SYM_BYTES : nullptr;
             ViewOut<G> vo;
             float reward = 0.0f;
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 } else {
                     action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
                 }
-                if (out_action) out_action[(size_t)slot * nreq + local] = (int8_t)action;
+                if (out_action) out_action[o] = (int8_t)action;
                 if (starts) {
                     // the new episode's start: reward padding 0, the action is ignored
                 } else {
@@ -456,9 +458,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     // cell holding (agent, red, direction), zero beyond the grid;
                     // for the RGB view, the cell's tile (the agent facing its
                     // direction) goes to shared memory for the gather below
-                    const size_t row = (size_t)slot * nreq + local;
-                    uint8_t* fo = obs_full ? obs_full + row * (size_t)(F * F * 3) : nullptr;
-                    uint8_t* co = obs_cat ? obs_cat + row * (size_t)(F * F) : nullptr;
+                    uint8_t* fo = obs_full ? obs_full + o * (size_t)(F * F * 3) : nullptr;
+                    uint8_t* co = obs_cat ? obs_cat + o * (size_t)(F * F) : nullptr;
                     for (int c = grp.lane; c < F * F; c += G) {
                         const int y = c / F, x = c - y * F;
                         uint32_t tri = 0;
@@ -481,12 +482,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 }
                 {
                     // every lane of the group stores the same values (one
-                    // transaction); an absent output goes to a shared sink
-                    const size_t o = (size_t)slot * nreq + local;
-                    *(out_reward ? out_reward + o : reinterpret_cast<float*>(s_sink)) = reward;
-                    *(out_term ? out_term + o : reinterpret_cast<uint8_t*>(s_sink + 1)) = (uint8_t)term;
-                    *(out_trunc ? out_trunc + o : reinterpret_cast<uint8_t*>(s_sink + 2)) = (uint8_t)trunc;
-                    *(out_mission ? out_mission + o : reinterpret_cast<uint8_t*>(s_sink + 3)) = (uint8_t)a.mission;
+                    // transaction); absent outputs are skipped
+                    if (out_reward) out_reward[o] = reward;
+                    if (out_term) out_term[o] = (uint8_t)term;
+                    if (out_trunc) out_trunc[o] = (uint8_t)trunc;
+                    if (out_mission) out_mission[o] = (uint8_t)a.mission;
                     ret += reward;
                     eps += (uint32_t)(term || trunc);
                 }
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             // and the outputs that read the staged record (digest, the
             // categorical first-person view).
             if (G >= 8 && !digest && !(FULL && obs_cat_fp)) {
-                if (active && obs_sym) write_view(grp, vo, obs_sym + ((size_t)slot * nreq + local) * NX_OBS_SYM_BYTES);
+                if (active && obs_sym) write_view(grp, vo, obs_sym + o * NX_OBS_SYM_BYTES);
             } else {
             // Each warp stages the symbolic outputs of its own envs (placed at
             // the same address modulo 16 as their destination) and stores them
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     if (FULL && obs_cat_fp) {
                         // categorical_first_person: the entity bytes of the staged view
                         grp.sync();
-                        uint8_t* cf = obs_cat_fp + ((size_t)slot * nreq + local) * 49;
+                        uint8_t* cf = obs_cat_fp + o * 49;
                         for (int c = grp.lane; c < 49; c += G) cf[c] = my_sym[3 * c];
                     }
                     if (digest) {
@@ -578,7 +578,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     coop_rgb_full(obs_rgb_full + row0 * (size_t)(3072 * FR * FR), sfull, p.atlas, n, FR, tid, nthreads);
                 __syncthreads();
             }
-            slot = slot + 1u == (uint32_t)depth ? 0u : slot + 1u;
+            const bool wrap = slot + 1u == (uint32_t)depth;
+            slot = wrap ? 0u : slot + 1u;
+            o = wrap ? (size_t)local : o + nreq;
         }
 
         if (kBulk && lane32 == 0) bulk_wait_all();  // every record of this item is in global memory
