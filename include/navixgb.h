@@ -175,12 +175,16 @@ typedef struct {
 } nx_out;
 
 /* Launch shape in use (after autotuning); policy_* describe the fused-policy
- * launches (0 before nx_set_policy). */
+ * launches (0 before nx_set_policy).  lean_family >= 0: rollouts of this
+ * context with random actions, no action output and the Markov reward (and
+ * no RGB or fully observable views) launch the step kernel compiled for that
+ * one family, on lean_grid_ctas CTAs; -1: every call runs the general one. */
 typedef struct {
     int32_t group_lanes, envs_per_cta, staging, n_items, grid_ctas, smem_bytes, steps_per_launch;
     int32_t n_envs, n_families;
     size_t state_bytes, device_bytes;
     int32_t policy_items, policy_ctas_per_sm, policy_grid_ctas, policy_smem_bytes;
+    int32_t lean_family, lean_grid_ctas;
 } nx_info;
 
 void nx_options_default(nx_options* opts);

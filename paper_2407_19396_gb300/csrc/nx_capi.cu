@@ -279,6 +279,7 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
     env->cell_stride = nx_cell_stride(max_cells);
     env->n_families = 0;
     for (bool b : seen) env->n_families += b ? 1 : 0;
+    env->lean_family = env->n_families == 1 ? (int)env->descs[0].family : -1;
 
     env->d_agents = (nx_agent*)nx_dev_alloc(env, sizeof(nx_agent) * (size_t)env->n_envs);
     env->d_grids = (uint8_t*)nx_dev_alloc(env, env->grid_pool);
@@ -386,6 +387,7 @@ nx_status nx_apply_shape(nx_env* env, const nx_launch_shape& s)
     NX_CK(env, cudaStreamSynchronize(env->stream), "work list upload");
     env->shape = s;
     env->per_sm_full = 0;  // recomputed for the new shape on first use
+    env->per_sm_lean = 0;
     env->n_items = (int)items.size();
     env->fam_begin = fam_begin;
     env->grid_ctas = std::min(env->n_items, per_sm * env->sm_count);
@@ -438,9 +440,33 @@ static nx_status prof_mark(nx_env* env, bool begin)
     return NX_OK;
 }
 
-// Launch shape and grid of a call: the plain instantiation, or (full) the
+// The lean instantiation of the context's shape (one family, the Markov
+// reward; see nx_step_kernel), with its grid; false where there is none.  Its
+// occupancy query (which sets a kernel attribute) runs on first use, outside
+// any stream capture.
+static bool lean_shape(const nx_env* env, nx_launch_shape* s, int* grid)
+{
+    if (env->lean_family < 0 || env->req_host.reward_mode != NX_REWARD_MARKOV) return false;
+    nx_launch_shape ls = env->shape;
+    ls.lean_family = env->lean_family;
+    if (!nx_lean_supported(ls)) return false;
+    if (env->per_sm_lean == 0) {
+        int err = 0;
+        const int n = nx_kernel_max_ctas(ls, env->cell_stride, &err);
+        if (err) cudaGetLastError();
+        env->per_sm_lean = (!err && n >= 1) ? n : -1;  // the general kernel serves where it is unavailable
+    }
+    if (env->per_sm_lean < 1) return false;
+    *s = ls;
+    *grid = std::min(env->n_items, env->per_sm_lean * env->sm_count);
+    return true;
+}
+
+// Launch shape and grid of a call: the plain instantiation, its lean form
+// (lean: a call with random actions and no action output), or (full) the
 // one that also writes the fully observable views.
-static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid, bool policy = false)
+static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid, bool policy = false,
+                           bool lean = false)
 {
     if (policy) {
         *s = nx_launch_shape{1, nxp::kRows, 0, 1, 0, false, true};
@@ -449,6 +475,7 @@ static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid
     }
     *s = env->shape;
     *grid = env->grid_ctas;
+    if (!full && lean) lean_shape(env, s, grid);
     if (!full) return NX_OK;
     s->full = true;
     if (env->per_sm_full <= 0) {
@@ -461,11 +488,12 @@ static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid
     return NX_OK;
 }
 
-static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full, bool policy = false)
+static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full, bool policy = false,
+                              bool lean = false)
 {
     nx_launch_shape s;
     int grid = 0;
-    nx_status ss = shape_for(env, full, &s, &grid, policy);
+    nx_status ss = shape_for(env, full, &s, &grid, policy, lean);
     if (ss != NX_OK) return ss;
     nx_kparams p = nx_params(env, steps, 0);
     if (policy) {
@@ -481,10 +509,10 @@ static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full
 }
 
 // A direct (uncaptured) chunk launch on the context stream, counted and timed.
-static nx_status launch_chunk_direct(nx_env* env, int steps, bool full, bool policy = false)
+static nx_status launch_chunk_direct(nx_env* env, int steps, bool full, bool policy = false, bool lean = false)
 {
     nx_status st = prof_mark(env, true);
-    if (st == NX_OK) st = launch_chunk(env, steps, env->stream, full, policy);
+    if (st == NX_OK) st = launch_chunk(env, steps, env->stream, full, policy, lean);
     if (st == NX_OK) st = prof_mark(env, false);
     env->n_step_launches += 1;
     env->n_all_launches += 2;
@@ -494,25 +522,26 @@ static nx_status launch_chunk_direct(nx_env* env, int steps, bool full, bool pol
 // Replays (capturing on first use) the graph {step kernel of `steps` steps;
 // counter advance}.  The graph reads every per-call argument from the
 // device-side request record, so one graph serves every call.
-static nx_status launch_chunk_graph(nx_env* env, int steps, bool full, bool policy = false)
+static nx_status launch_chunk_graph(nx_env* env, int steps, bool full, bool policy = false, bool lean = false)
 {
     nx_graph* g = nullptr;
     for (auto& c : env->graphs)
-        if (c.steps == steps && c.full == full && c.policy == policy) g = &c;
+        if (c.steps == steps && c.full == full && c.policy == policy && c.lean == lean) g = &c;
     if (!g) {
         nx_graph ng;
         ng.steps = steps;
         ng.full = full;
         ng.policy = policy;
-        if (full) {  // the occupancy query sets a kernel attribute: keep it out of the capture
+        ng.lean = lean;
+        if (full || lean) {  // the occupancy query sets a kernel attribute: keep it out of the capture
             nx_launch_shape s;
             int grid = 0;
-            nx_status ss = shape_for(env, true, &s, &grid);
+            nx_status ss = shape_for(env, full, &s, &grid, false, lean);
             if (ss != NX_OK) return ss;
         }
         cudaGraph_t graph = nullptr;
         NX_CK(env, cudaStreamBeginCapture(env->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        nx_status st = launch_chunk(env, steps, env->capture_stream, full, policy);
+        nx_status st = launch_chunk(env, steps, env->capture_stream, full, policy, lean);
         cudaError_t e = cudaStreamEndCapture(env->capture_stream, &graph);
         if (st != NX_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -660,15 +689,18 @@ static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, co
         }
         return NX_OK;
     }
+    // random actions without an action output run the lean kernel where the
+    // context has one (a single family, the Markov reward)
+    const bool lean = act_mode == NX_ACT_RANDOM && !(traj && traj->action);
     const int nfull = n_steps / C, rem = n_steps % C;
     for (int k = 0; k < nfull; ++k) {
-        st = launch_chunk_graph(env, C, full, policy);
+        st = launch_chunk_graph(env, C, full, policy, lean);
         if (st != NX_OK) return st;
     }
     if (rem) {
         NX_CK(env, nx_launch_set_steps(env->d_req, rem, env->stream), "set steps");
         env->n_all_launches += 1;
-        st = launch_chunk_direct(env, rem, full, policy);
+        st = launch_chunk_direct(env, rem, full, policy, lean);
         if (st != NX_OK) return st;
     }
     return NX_OK;
@@ -846,7 +878,7 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
         nx_req r = call_req(env, Ck, act_mode, dact, &d);
         NX_CK(env, nx_launch_configure(env->d_req, r, 0, env->stream), "configure");
         env->n_all_launches += 1;
-        st = launch_chunk_direct(env, Ck, false);
+        st = launch_chunk_direct(env, Ck, false, false, act_mode == NX_ACT_RANDOM);
         if (st != NX_OK) return st;
         NX_CK(env, cudaEventRecord(env->ev_done[b], env->stream), "record");
         NX_CK(env, cudaStreamWaitEvent(env->copy_stream, env->ev_done[b], 0), "wait compute");
@@ -925,6 +957,11 @@ nx_status nx_autotune(nx_env* env)
                 cudaGetLastError();
                 continue;
             }
+            // time the kernel these calls will run: the lean one where the
+            // context has it (the timing request has random actions)
+            nx_launch_shape ls = s;
+            int lgrid = env->grid_ctas;
+            lean_shape(env, &ls, &lgrid);
             nx_kparams p = nx_params(env, T, 0);
             p.phases = s.phases;
             p.agents = sa;
@@ -936,7 +973,7 @@ nx_status nx_autotune(nx_env* env)
                 ok = cudaMemcpyAsync(sa, env->d_agents, sizeof(nx_agent) * N, cudaMemcpyDeviceToDevice, env->stream) == cudaSuccess &&
                      cudaMemcpyAsync(sg, env->d_grids, env->grid_pool, cudaMemcpyDeviceToDevice, env->stream) == cudaSuccess &&
                      nx_launch_configure(sr, r, 1, env->stream) == 0 && cudaEventRecord(e0, env->stream) == cudaSuccess &&
-                     nx_launch_step_kernel(s, p, env->grid_ctas, env->stream) == 0 &&
+                     nx_launch_step_kernel(ls, p, lgrid, env->stream) == 0 &&
                      cudaEventRecord(e1, env->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
                 float ms = 0;
                 if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && rep > 0) ms_min = std::min(ms_min, ms);
@@ -1083,6 +1120,13 @@ nx_status nx_get_info(const nx_env* env, nx_info* info)
         info->policy_ctas_per_sm = env->per_sm_pol;
         info->policy_grid_ctas = std::min(env->n_items_pol, env->per_sm_pol * env->sm_count);
         info->policy_smem_bytes = nx_kernel_smem_bytes(ps, env->cell_stride);
+    }
+    nx_launch_shape ls;
+    int lgrid = 0;
+    info->lean_family = -1;
+    if (lean_shape(env, &ls, &lgrid)) {
+        info->lean_family = ls.lean_family;
+        info->lean_grid_ctas = lgrid;
     }
     return NX_OK;
 }

@@ -118,6 +118,7 @@ struct nx_launch_shape {
     int rgb_full_side = 0;  // reserve smem for full-view RGB tile ids of this grid side
     bool full = false;      // the instantiation that writes the fully observable views
     bool policy = false;    // the fused-policy instantiation (1 lane, 128 envs per CTA)
+    int lean_family = -1;   // >= 0: the lean instantiation for this family (nx_lean_supported)
 };
 // Shared-memory bytes per env grid for grids of up to max_cells cells: a
 // whole number of 4-byte words, and an odd one, so that the grids of the 32
@@ -134,7 +135,20 @@ int nx_launch_advance(nx_req* reqs, int n_reqs, void* stream);
 int nx_launch_configure(nx_req* r, const nx_req& v, int gstep_mode, void* stream);
 int nx_launch_set_steps(nx_req* r, int steps, void* stream);
 int nx_shape_supported(const nx_launch_shape& s);
+// Whether a shape has lean instantiations (one family, random actions, no
+// action output or digest, Markov reward, symbolic outputs only).
+int nx_lean_supported(const nx_launch_shape& s);
 #ifdef __CUDACC__
 int nx_kernel_max_ctas_full(const nx_launch_shape& s, int threads, int smem, int* err);
 int nx_launch_step_kernel_full(const nx_launch_shape& s, const nx_kparams& p, int grid, int smem, cudaStream_t st);
+// the lean instantiations, one translation unit per lane count
+#define NX_LEAN_DECL(G_)                                                                                   \
+    int nx_lean_occupancy_g##G_(int family, int threads, int smem, int* err);                              \
+    int nx_lean_launch_g##G_(int family, const nx_kparams& p, int grid, int smem, cudaStream_t st);
+NX_LEAN_DECL(1)
+NX_LEAN_DECL(4)
+NX_LEAN_DECL(8)
+NX_LEAN_DECL(16)
+NX_LEAN_DECL(32)
+#undef NX_LEAN_DECL
 #endif

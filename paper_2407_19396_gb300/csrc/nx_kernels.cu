@@ -48,6 +48,12 @@ int nx_shape_supported(const nx_launch_shape& s)
     return 1;
 }
 
+int nx_lean_supported(const nx_launch_shape& s)
+{
+    const int G = s.group_lanes;
+    return (G == 1 || G == 4 || G == 8 || G == 16 || G == 32) && !s.rgb && !s.full && !s.policy;
+}
+
 int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride)
 {
     const int E = s.envs_per_cta;
@@ -68,6 +74,16 @@ int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err)
     const int threads = s.envs_per_cta * s.group_lanes;
     if (s.full) return nx_kernel_max_ctas_full(s, threads, smem, err);
     if (s.policy) return policy_occupancy(threads, smem, err);
+    if (s.lean_family >= 0) {
+        if (!nx_lean_supported(s)) return -1;
+        switch (s.group_lanes) {
+        case 1: return nx_lean_occupancy_g1(s.lean_family, threads, smem, err);
+        case 4: return nx_lean_occupancy_g4(s.lean_family, threads, smem, err);
+        case 8: return nx_lean_occupancy_g8(s.lean_family, threads, smem, err);
+        case 16: return nx_lean_occupancy_g16(s.lean_family, threads, smem, err);
+        default: return nx_lean_occupancy_g32(s.lean_family, threads, smem, err);
+        }
+    }
     NX_DISPATCH_G(s.group_lanes, s.rgb, false, occupancy_t, threads, smem, err)
 }
 
@@ -77,6 +93,16 @@ int nx_launch_step_kernel(const nx_launch_shape& s, const nx_kparams& p, int gri
     cudaStream_t st = (cudaStream_t)stream;
     if (s.full) return nx_launch_step_kernel_full(s, p, grid, smem, st);
     if (s.policy) return launch_t<1, false, false, true>(p, grid, smem, st);
+    if (s.lean_family >= 0) {
+        if (!nx_lean_supported(s)) return -1;
+        switch (s.group_lanes) {
+        case 1: return nx_lean_launch_g1(s.lean_family, p, grid, smem, st);
+        case 4: return nx_lean_launch_g4(s.lean_family, p, grid, smem, st);
+        case 8: return nx_lean_launch_g8(s.lean_family, p, grid, smem, st);
+        case 16: return nx_lean_launch_g16(s.lean_family, p, grid, smem, st);
+        default: return nx_lean_launch_g32(s.lean_family, p, grid, smem, st);
+        }
+    }
     NX_DISPATCH_G(s.group_lanes, s.rgb, false, launch_t, p, grid, smem, st)
 }
 

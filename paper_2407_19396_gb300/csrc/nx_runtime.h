@@ -12,6 +12,7 @@ struct nx_graph {
     int steps = 0;
     bool full = false;
     bool policy = false;
+    bool lean = false;
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -57,6 +58,8 @@ struct nx_env {
     int grid_ctas = 0;
     int per_sm = 0;
     int per_sm_full = 0;  // resident CTAs of the instantiation with the fully observable views
+    int lean_family = -1;  // the one family of every env (-1: several), for the lean step kernels
+    mutable int per_sm_lean = 0;  // resident CTAs of the lean instantiation (cache; 0: not queried, -1: none)
     std::vector<int> fam_begin;
     bool tuned = false;
     std::vector<nx_tune_entry> tune_log;

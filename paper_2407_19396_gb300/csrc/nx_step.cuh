@@ -221,10 +221,19 @@ __host__ __device__ __forceinline__ int policy_smem_offset(int grid_bytes, int s
     return (grid_bytes + staging_bytes + 127) & ~127;
 }
 
-template <int G, bool RGB, bool FULL, bool POL = false>
+// FAM >= 0 is the lean instantiation for launches whose every work item has
+// family FAM and whose request is of the common kind: random actions, no
+// action output, no digest, the Markov reward, symbolic outputs only.  The
+// compiler then drops the other families' generators and rules and the
+// per-call branches of the step loop (the paper's implementation likewise
+// compiles one program per environment); the host launches it only for such
+// calls.
+template <int G, bool RGB, bool FULL, bool POL = false, int FAM = -1>
 __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparams p)
 {
     static_assert(!POL || (G == 1 && !RGB && !FULL), "the fused policy runs one lane per env");
+    constexpr bool kLean = FAM >= 0;
+    static_assert(!kLean || (!RGB && !FULL && !POL && FAM < NX_N_FAMILIES), "lean: one family, symbolic outputs");
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar;  // fused policy: MMA completion
     __shared__ uint32_t s_tmem;               // fused policy: tensor-memory base address
@@ -299,13 +308,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         uint8_t* out_term = rq->terminated;
         uint8_t* out_trunc = rq->truncated;
         uint8_t* out_mission = rq->mission;
-        int8_t* out_action = rq->action_out;
-        const uint32_t reward_mode = rq->reward_mode;
+        int8_t* out_action = kLean ? nullptr : rq->action_out;
+        const uint32_t reward_mode = kLean ? (uint32_t)NX_REWARD_MARKOV : rq->reward_mode;
         const float lava_reward = rq->lava_reward;
         const float action_cost = rq->action_cost, time_cost = rq->time_cost;
         const int n_balls = rq->n_balls;
         float* returns = rq->returns;
-        uint64_t* digest = rq->digest;
+        uint64_t* digest = kLean ? nullptr : rq->digest;
         uint32_t* episodes = rq->episodes;
         // the fully observable views exist only in the FULL instantiations
         uint8_t* obs_full = FULL ? rq->obs_full : nullptr;
@@ -314,7 +323,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         uint8_t* obs_rgb_full = (FULL && RGB && FR > 0) ? rq->obs_rgb_full : nullptr;
         const int F = FULL ? rq->full_side : 0;
 
-        const int n = (int)item.n_envs, S = item.size, HW = S * S, family = item.family, variant = (int)item.variant;
+        const int n = (int)item.n_envs, S = item.size, HW = S * S, variant = (int)item.variant;
+        const int family = kLean ? FAM : (int)item.family;
         const int max_steps = item.max_steps;
         const bool active = gi < n;
         const uint32_t local = item.local_begin + (uint32_t)gi;
@@ -359,7 +369,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 
         // steps == 0 with reset_all: one emission of the episode-0 start state
         const int emissions = p.reset_all ? 1 : steps;
-        const bool rnd = act_mode == NX_ACT_RANDOM;
+        const bool rnd = kLean || act_mode == NX_ACT_RANDOM;
         const uint32_t n_act = family == NX_DYNOBS ? 3u : 7u;
         uint32_t slot = call0 % (uint32_t)depth;
         // this env's row of the output ring (slot * n_envs + local), advanced
@@ -407,7 +417,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     const int owner = ((tid & ~31) + L) / G;  // group (env slot) of lane L
                     AgentReg na;
                     const bool ok =
-                        reset_layout_warp(sgrid + owner * cs, S, family, n_balls, variant, seed, k, ep, na);
+                        reset_layout_warp<FAM>(sgrid + owner * cs, S, family, n_balls, variant, seed, k, ep, na);
                     if (!ok && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
                     if (gi == owner) {
                         na.invalid = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
@@ -453,7 +463,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 render_view(grp, mygrid, S, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
                             RGB && obs_rgb ? stiles + gi * 49 : nullptr);
                 if constexpr (POL) nxp::store_obs_row(sA, tid, vo.sw);  // the next step's policy input
-                if (FULL && (obs_full || obs_cat || obs_rgb_full)) {
+                if constexpr (FULL) if (obs_full || obs_cat || obs_rgb_full) {
                     // fully observable views: every cell's triple, the agent's
                     // cell holding (agent, red, direction), zero beyond the grid;
                     // for the RGB view, the cell's tile (the agent facing its
@@ -620,10 +630,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 
 // The dynamic shared-memory limit is raised once per shape by
 // nx_kernel_max_ctas (outside any stream capture); launches only launch.
-template <int G, bool RGB, bool FULL, bool POL = false>
+template <int G, bool RGB, bool FULL, bool POL = false, int FAM = -1>
 int launch_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
 {
-    nx_step_kernel<G, RGB, FULL, POL><<<grid, p.envs_per_cta * G, smem, st>>>(p);
+    nx_step_kernel<G, RGB, FULL, POL, FAM><<<grid, p.envs_per_cta * G, smem, st>>>(p);
     return (int)cudaGetLastError();
 }
 
@@ -631,10 +641,10 @@ int launch_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
 // context in the process, so it is always raised to the most the device
 // allows next to the kernel's static shared memory (never lowered to one
 // context's need).
-template <int G, bool RGB, bool FULL, bool POL = false>
+template <int G, bool RGB, bool FULL, bool POL = false, int FAM = -1>
 int occupancy_t(int threads, int smem, int* err)
 {
-    auto k = nx_step_kernel<G, RGB, FULL, POL>;
+    auto k = nx_step_kernel<G, RGB, FULL, POL, FAM>;
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -695,5 +705,23 @@ inline int policy_occupancy(int threads, int smem, int* err)
     case 32: return RGB_ ? FN<32, true, FULL_>(__VA_ARGS__) : FN<32, false, FULL_>(__VA_ARGS__); \
     default: return -1;                                                                           \
     }
+
+// The lean instantiations of one lane count, by family.
+#define NX_DISPATCH_FAM(G_, FAM_, FN, ...)                                   \
+    switch (FAM_) {                                                         \
+    case 0: return FN<G_, false, false, false, 0>(__VA_ARGS__);             \
+    case 1: return FN<G_, false, false, false, 1>(__VA_ARGS__);             \
+    case 2: return FN<G_, false, false, false, 2>(__VA_ARGS__);             \
+    case 3: return FN<G_, false, false, false, 3>(__VA_ARGS__);             \
+    case 4: return FN<G_, false, false, false, 4>(__VA_ARGS__);             \
+    case 5: return FN<G_, false, false, false, 5>(__VA_ARGS__);             \
+    case 6: return FN<G_, false, false, false, 6>(__VA_ARGS__);             \
+    case 7: return FN<G_, false, false, false, 7>(__VA_ARGS__);             \
+    case 8: return FN<G_, false, false, false, 8>(__VA_ARGS__);             \
+    case 9: return FN<G_, false, false, false, 9>(__VA_ARGS__);             \
+    case 10: return FN<G_, false, false, false, 10>(__VA_ARGS__);           \
+    default: return -1;                                                     \
+    }
+static_assert(NX_N_FAMILIES == 11, "NX_DISPATCH_FAM lists every family");
 
 }  // namespace nxk

@@ -77,7 +77,8 @@ class nx_info(ctypes.Structure):
                 ("steps_per_launch", ctypes.c_int32), ("n_envs", ctypes.c_int32), ("n_families", ctypes.c_int32),
                 ("state_bytes", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
                 ("policy_items", ctypes.c_int32), ("policy_ctas_per_sm", ctypes.c_int32),
-                ("policy_grid_ctas", ctypes.c_int32), ("policy_smem_bytes", ctypes.c_int32)]
+                ("policy_grid_ctas", ctypes.c_int32), ("policy_smem_bytes", ctypes.c_int32),
+                ("lean_family", ctypes.c_int32), ("lean_grid_ctas", ctypes.c_int32)]
 
 
 class nx_request(ctypes.Structure):

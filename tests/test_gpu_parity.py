@@ -482,6 +482,56 @@ def test_gotodoor_host_rollout_and_snapshot():
     e2.close()
 
 
+# one configuration per family (small grids, so episodes end and reset often)
+LEAN_FAMILIES = [(O.EMPTY, 5, 0), (O.DOORKEY, 6, 0), (O.FOURROOMS, 9, 0), (O.LAVAGAP, 5, 0), (O.DYNOBS, 6, 0),
+                 (O.EMPTY_RANDOM, 6, 0), (O.LAVA_CROSSING, 9, 1), (O.SIMPLE_CROSSING, 11, 3), (O.GOTODOOR, 6, 0),
+                 (O.DISTSHIFT, 7, 1), (O.KEYCORRIDOR, 7, 1)]
+
+
+@pytest.mark.parametrize("family,size,variant", LEAN_FAMILIES)
+def test_lean_kernels_every_family_every_lanes(family, size, variant):
+    """A single-family context's random-action rollouts run the step kernel
+    compiled for that family; each lane count against the oracle, every step
+    (graph chunks and a remainder launch), and against the general kernel
+    (selected by asking for the action output)."""
+    nx = nxmod()
+    n, T = 37, 200
+    ob = O.Batch([family] * n, [size] * n, seed=23, variants=[variant] * n)
+    oo_r = ob.reset()
+    oo = ob.rollout(T)
+    for lanes, envs in ((1, 64), (4, 16), (8, 8), (16, 4), (32, 2)):
+        env = nx.Env(family, size, n, seed=23, variant=variant, group_lanes=lanes, envs_per_cta=envs, autotune=False,
+                     steps_per_launch=64)
+        info = env.info()
+        assert info["lean_family"] == family and info["lean_grid_ctas"] >= 1, info
+        assert_outputs_equal(env.reset(), oo_r, what=f"lean reset G={lanes}")
+        out = env.rollout(T)
+        assert_outputs_equal(out, oo, what=f"lean G={lanes} family={family}")
+        assert_states_equal(env.state()["envs"], ob, what=f"lean G={lanes} family={family}")
+        env.close()
+        if lanes == 16:
+            genv = nx.Env(family, size, n, seed=23, variant=variant, group_lanes=lanes, envs_per_cta=envs,
+                          autotune=False, steps_per_launch=64, action=True)
+            genv.reset()
+            gout = genv.rollout(T)
+            for k in ("obs_sym", "reward", "terminated", "truncated"):
+                np.testing.assert_array_equal(to_np(gout[k]), to_np(out[k]), err_msg=f"general vs lean {k}")
+            genv.close()
+
+
+def test_lean_kernel_not_used_where_it_does_not_apply():
+    nx = nxmod()
+    mixed = nx.Env(descs=mixed_descs(40, [(O.EMPTY, 5), (O.DOORKEY, 8)]), seed=1, autotune=False)
+    assert mixed.info()["lean_family"] == -1  # several families
+    mixed.close()
+    mg = nx.Env(O.DOORKEY, 8, 40, seed=1, autotune=False, reward_mode=nx.NX_REWARD_MINIGRID)
+    assert mg.info()["lean_family"] == -1  # MiniGrid reward
+    mg.close()
+    g2 = nx.Env(O.DOORKEY, 8, 40, seed=1, autotune=False, group_lanes=2, envs_per_cta=16)
+    assert g2.info()["lean_family"] == -1  # no lean instantiation with 2 lanes per env
+    g2.close()
+
+
 def test_variant_validation():
     nx = nxmod()
     assert nx.nx_max_variant(O.LAVA_CROSSING, 9) == O.max_variant(O.LAVA_CROSSING, 9) == 6
