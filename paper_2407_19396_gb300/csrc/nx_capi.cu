@@ -260,14 +260,12 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
 
     // grid pool layout and families
     size_t off = 0;
-    int max_cells = 0;
     bool seen[NX_N_FAMILIES] = {};
     env->grid_offset.resize(env->n_envs);
     for (int i = 0; i < env->n_envs; ++i) {
         const int S = env->descs[i].height;
         env->grid_offset[i] = (uint32_t)off;
         off += (size_t)3 * S * S;
-        max_cells = std::max(max_cells, S * S);
         env->max_side = std::max(env->max_side, S);
         seen[env->descs[i].family] = true;
     }
@@ -276,7 +274,6 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
         return nx_fail(nullptr, NX_E_INVAL, "state pool larger than 4 GiB");
     }
     env->grid_pool = off;
-    env->cell_stride = nx_cell_stride(max_cells);
     env->n_families = 0;
     for (bool b : seen) env->n_families += b ? 1 : 0;
     env->lean_family = env->n_families == 1 ? (int)env->descs[0].family : -1;
@@ -359,7 +356,7 @@ nx_status nx_apply_shape(nx_env* env, const nx_launch_shape& s)
 {
     if (!nx_shape_supported(s)) return nx_fail(env, NX_E_INVAL, "unsupported launch shape");
     int err = 0;
-    const int per_sm = nx_kernel_max_ctas(s, env->cell_stride, &err);
+    const int per_sm = nx_kernel_max_ctas(s, env->max_side, &err);
     if (err) return nx_cuda_fail(env, err, "occupancy query");
     if (per_sm < 1) return nx_fail(env, NX_E_INVAL, "launch shape does not fit on an SM");
     std::vector<nx_item> items = nx_build_items(env, s.envs_per_cta);
@@ -415,7 +412,7 @@ nx_kparams nx_params(const nx_env* env, int launch_steps, int reset_all)
     p.reqs = env->d_req;
     p.ctl = env->d_ctl;
     p.atlas = env->d_atlas;
-    p.cell_stride = env->cell_stride;
+    p.cell_stride = nx_slot_stride(env->shape, env->max_side);
     p.envs_per_cta = env->shape.envs_per_cta;
     p.reset_all = reset_all;
     p.phases = env->shape.phases;
@@ -452,7 +449,7 @@ static bool lean_shape(const nx_env* env, nx_launch_shape* s, int* grid)
     if (!nx_lean_supported(ls)) return false;
     if (env->per_sm_lean == 0) {
         int err = 0;
-        const int n = nx_kernel_max_ctas(ls, env->cell_stride, &err);
+        const int n = nx_kernel_max_ctas(ls, env->max_side, &err);
         if (err) cudaGetLastError();
         env->per_sm_lean = (!err && n >= 1) ? n : -1;  // the general kernel serves where it is unavailable
     }
@@ -480,7 +477,7 @@ static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid
     s->full = true;
     if (env->per_sm_full <= 0) {
         int err = 0;
-        env->per_sm_full = nx_kernel_max_ctas(*s, env->cell_stride, &err);
+        env->per_sm_full = nx_kernel_max_ctas(*s, env->max_side, &err);
         if (err) return nx_cuda_fail(env, err, "occupancy query");
         if (env->per_sm_full < 1) return nx_fail(env, NX_E_INVAL, "launch shape does not fit on an SM");
     }
@@ -500,6 +497,7 @@ static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full
         p.items = env->d_items_pol;
         p.n_items = env->n_items_pol;
         p.envs_per_cta = nxp::kRows;
+        p.cell_stride = nx_slot_stride(s, env->max_side);
         p.phases = 1;
         p.rgb_full_side = 0;
     }
@@ -738,7 +736,7 @@ nx_status nx_set_policy(nx_env* env, const nx_policy* pol)
     }
     nx_launch_shape ps{1, nxp::kRows, 0, 1, 0, false, true};
     int err = 0;
-    const int per_sm = nx_kernel_max_ctas(ps, env->cell_stride, &err);
+    const int per_sm = nx_kernel_max_ctas(ps, env->max_side, &err);
     if (err) return nx_cuda_fail(env, err, "occupancy query");
     if (per_sm < 1) return nx_fail(env, NX_E_INVAL, "the fused policy does not fit on an SM with these grids");
     // weight images: bf16 bits of int8 values (exact), biases as int32
@@ -1108,7 +1106,7 @@ nx_status nx_get_info(const nx_env* env, nx_info* info)
     info->staging = env->shape.phases > 1 ? NX_STAGE_HALF : NX_STAGE_FULL;
     info->n_items = env->n_items;
     info->grid_ctas = env->grid_ctas;
-    info->smem_bytes = nx_kernel_smem_bytes(env->shape, env->cell_stride);
+    info->smem_bytes = nx_kernel_smem_bytes(env->shape, env->max_side);
     info->steps_per_launch = env->opt.steps_per_launch;
     info->n_envs = env->n_envs;
     info->n_families = env->n_families;
@@ -1119,7 +1117,7 @@ nx_status nx_get_info(const nx_env* env, nx_info* info)
         info->policy_items = env->n_items_pol;
         info->policy_ctas_per_sm = env->per_sm_pol;
         info->policy_grid_ctas = std::min(env->n_items_pol, env->per_sm_pol * env->sm_count);
-        info->policy_smem_bytes = nx_kernel_smem_bytes(ps, env->cell_stride);
+        info->policy_smem_bytes = nx_kernel_smem_bytes(ps, env->max_side);
     }
     nx_launch_shape ls;
     int lgrid = 0;

@@ -277,7 +277,7 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
 // an array indexed by a loop counter would sit in local memory and be charged
 // to the calling kernel's stack frame.
 template <int G>
-__device__ __noinline__ void crossing_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int variant,
+__device__ __noinline__ void crossing_layout(const Grp<G>& grp, uint8_t* g, int S, int W, int family, int variant,
                                              uint64_t seed, uint32_t key_env, uint32_t episode)
 {
     const int HW = S * S;
@@ -322,7 +322,7 @@ __device__ __noinline__ void crossing_layout(const Grp<G>& grp, uint8_t* g, int 
     for (int c = grp.lane; c < HW; c += G) {
         const int y = c / S, x = c - y * S;
         if (x >= 1 && y >= 1 && x <= S - 2 && y <= S - 2 && (((hmask >> y) | (vmask >> x)) & 1u))
-            g[c] = (uint8_t)obst;
+            g[y * W + x] = (uint8_t)obst;
     }
     // order of crossings: east moves (vertical rivers) first, then south
     // moves, shuffled by Fisher-Yates from the last position down; bit i of
@@ -344,13 +344,13 @@ __device__ __noinline__ void crossing_layout(const Grp<G>& grp, uint8_t* g, int 
         if ((east >> i) & 1u) {
             const int y = y_lo + 1 + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++),
                                              (uint32_t)(y_hi - y_lo - 1));
-            if (grp.lane == 0) g[y * S + x_hi] = (uint8_t)C_EMPTY;
+            if (grp.lane == 0) g[y * W + x_hi] = (uint8_t)C_EMPTY;
             x_lo = x_hi;
             vrest &= vrest - 1u;
         } else {
             const int x = x_lo + 1 + bounded(draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k++),
                                              (uint32_t)(x_hi - x_lo - 1));
-            if (grp.lane == 0) g[y_hi * S + x] = (uint8_t)C_EMPTY;
+            if (grp.lane == 0) g[y_hi * W + x] = (uint8_t)C_EMPTY;
             y_lo = y_hi;
             hrest &= hrest - 1u;
         }
@@ -370,8 +370,8 @@ __device__ __noinline__ void crossing_layout(const Grp<G>& grp, uint8_t* g, int 
 // closed form (row-major).  Out of line like the crossings; returns the
 // agent as x | y << 8 | dir << 16.
 template <int G>
-__device__ __noinline__ uint32_t keycorridor_layout(const Grp<G>& grp, uint8_t* g, int S, int variant, uint64_t seed,
-                                                    uint32_t key_env, uint32_t episode)
+__device__ __noinline__ uint32_t keycorridor_layout(const Grp<G>& grp, uint8_t* g, int S, int W, int variant,
+                                                    uint64_t seed, uint32_t key_env, uint32_t episode)
 {
     const int s = (S - 1) / 3 + 1, R = variant + 1, H = (s - 1) * R + 1, xl = s - 1, xr = 2 * (s - 1), w = s - 2;
     auto dr = [&](int k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, (uint32_t)k); };
@@ -379,7 +379,7 @@ __device__ __noinline__ uint32_t keycorridor_layout(const Grp<G>& grp, uint8_t* 
         const int y = c / S, x = c - y * S;
         bool wall = y >= H - 1 || y == 0 || x == 0 || x == S - 1 || x == xl || x == xr;
         if (y % (s - 1) == 0 && !(x > xl && x < xr)) wall = true;
-        g[c] = (uint8_t)(wall ? C_WALL : C_EMPTY);
+        g[y * W + x] = (uint8_t)(wall ? C_WALL : C_EMPTY);
     }
     const int gside = bounded(dr(4 * R), 2u), grow = bounded(dr(4 * R + 1), (uint32_t)R);
     const int krow = bounded(dr(4 * R + 2), (uint32_t)R);
@@ -388,14 +388,14 @@ __device__ __noinline__ uint32_t keycorridor_layout(const Grp<G>& grp, uint8_t* 
         const int side = j >= R, row = j - side * R;
         const int y = row * (s - 1) + 1 + bounded(dr(j), (uint32_t)w);
         const uint32_t c = bounded(dr(2 * R + j), 6u);
-        g[y * S + (side ? xr : xl)] = (uint8_t)make_code((side == gside && row == grow) ? K_DOOR_LOCKED : K_DOOR_CLOSED, c);
+        g[y * W + (side ? xr : xl)] = (uint8_t)make_code((side == gside && row == grow) ? K_DOOR_LOCKED : K_DOOR_CLOSED, c);
     }
     if (grp.lane == 0) {
         const uint32_t lock_col = bounded(dr(2 * R + gside * R + grow), 6u);
         const int gi = bounded(dr(4 * R + 3), (uint32_t)(w * w)), ki = bounded(dr(4 * R + 4), (uint32_t)(w * w));
         const int gx0 = gside == 0 ? 1 : xr + 1, kx0 = gside == 0 ? xr + 1 : 1;
-        g[(grow * (s - 1) + 1 + gi / w) * S + gx0 + gi % w] = (uint8_t)C_GOAL;
-        g[(krow * (s - 1) + 1 + ki / w) * S + kx0 + ki % w] = (uint8_t)make_code(K_KEY, lock_col);
+        g[(grow * (s - 1) + 1 + gi / w) * W + gx0 + gi % w] = (uint8_t)C_GOAL;
+        g[(krow * (s - 1) + 1 + ki / w) * W + kx0 + ki % w] = (uint8_t)make_code(K_KEY, lock_col);
     }
     const int ai = bounded(dr(4 * R + 5), (uint32_t)(w * (H - 2)));
     const int ax = xl + 1 + ai % w, ay = 1 + ai / w;
@@ -405,24 +405,31 @@ __device__ __noinline__ uint32_t keycorridor_layout(const Grp<G>& grp, uint8_t* 
 // ---------------------------------------------------------------------------
 // Layout generators of the Table 8 families.  Draw k of a reset is
 // draw(seed, env, episode, 0, PURPOSE_LAYOUT, k); the k-th free cell is
-// counted row-major; the agent is never stored in the grid.
+// counted row-major; the agent is never stored in the grid.  Cell (x, y) is
+// g[y W + x]: W = S for a packed grid, larger with a wall margin around it
+// (the margin is never written).
 // Returns false (and leaves a partial layout) only if a free-cell choice found
 // no cell, which cannot happen for sizes 5..19; the caller raises a flag.
 template <int G>
-__device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int S, int family, int n_balls, int variant,
-                                             uint64_t seed, uint32_t key_env, uint32_t episode, AgentReg& a)
+__device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int S, int W, int family, int n_balls,
+                                             int variant, uint64_t seed, uint32_t key_env, uint32_t episode, AgentReg& a)
 {
-    // empty cells four at a time (the env's slot is a whole number of words
-    // at least S * S bytes long), then the four border lines of walls
+    // empty cells (a packed grid four at a time: its slot is a whole number
+    // of words at least S * S bytes long), then the four border lines of walls
     const int HW = S * S;
     constexpr uint32_t kEmpty4 = C_EMPTY * 0x01010101u;
-    for (int c4 = grp.lane; c4 < (HW + 3) / 4; c4 += G) reinterpret_cast<uint32_t*>(g)[c4] = kEmpty4;
+    if (W == S) {
+        for (int c4 = grp.lane; c4 < (HW + 3) / 4; c4 += G) reinterpret_cast<uint32_t*>(g)[c4] = kEmpty4;
+    } else {
+        for (int y = 0; y < S; ++y)
+            for (int x = grp.lane; x < S; x += G) g[y * W + x] = (uint8_t)C_EMPTY;
+    }
     grp.sync();
     for (int i = grp.lane; i < S; i += G) {
         g[i] = (uint8_t)C_WALL;
-        g[(S - 1) * S + i] = (uint8_t)C_WALL;
-        g[i * S] = (uint8_t)C_WALL;
-        g[i * S + S - 1] = (uint8_t)C_WALL;
+        g[(S - 1) * W + i] = (uint8_t)C_WALL;
+        g[i * W] = (uint8_t)C_WALL;
+        g[i * W + S - 1] = (uint8_t)C_WALL;
     }
     a.x = 1;
     a.y = 1;
@@ -445,7 +452,7 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
     group_draws(grp, n_draws, d,
                 [&](uint32_t k) { return draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, k); });
     grp.sync();
-    const int goal = family == NX_DISTSHIFT ? S + (S - 2) : (S - 2) * S + (S - 2);
+    const int goal = family == NX_DISTSHIFT ? W + (S - 2) : (S - 2) * W + (S - 2);
     if (family != NX_FOURROOMS && family != NX_GOTODOOR && family != NX_KEYCORRIDOR) {
         if (grp.lane == 0) g[goal] = (uint8_t)C_GOAL;
     }
@@ -453,54 +460,54 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         const int xw = 2 + bounded(d[0], (uint32_t)(S - 4));
         const int door_y = 1 + bounded(d[1], (uint32_t)(S - 3));
         for (int y = 1 + grp.lane; y <= S - 2; y += G)
-            g[y * S + xw] = (uint8_t)(y == door_y ? C_DOOR_LOCKED_YELLOW : C_WALL);
+            g[y * W + xw] = (uint8_t)(y == door_y ? C_DOOR_LOCKED_YELLOW : C_WALL);
         grp.sync();
-        const int n = count_free(grp, g, S, 1, xw - 1, 1, S - 2, -1);
-        const int ac = kth_free(grp, g, S, 1, xw - 1, 1, S - 2, -1, bounded(d[2], (uint32_t)n));
-        const int kc = kth_free(grp, g, S, 1, xw - 1, 1, S - 2, ac, bounded(d[4], (uint32_t)(n - 1)));
+        const int n = count_free(grp, g, W, 1, xw - 1, 1, S - 2, -1);
+        const int ac = kth_free(grp, g, W, 1, xw - 1, 1, S - 2, -1, bounded(d[2], (uint32_t)n));
+        const int kc = kth_free(grp, g, W, 1, xw - 1, 1, S - 2, ac, bounded(d[4], (uint32_t)(n - 1)));
         if (ac < 0 || kc < 0) return false;
-        a.x = ac % S;
-        a.y = ac / S;
+        a.x = ac % W;
+        a.y = ac / W;
         a.dir = bounded(d[3], 4u);
         grp.sync();
         if (grp.lane == 0) g[kc] = (uint8_t)C_KEY_YELLOW;
     } else if (family == NX_FOURROOMS) {
         const int m = S / 2;
         for (int i = grp.lane; i < S; i += G) {
-            g[i * S + m] = (uint8_t)C_WALL;
-            g[m * S + i] = (uint8_t)C_WALL;
+            g[i * W + m] = (uint8_t)C_WALL;
+            g[m * W + i] = (uint8_t)C_WALL;
         }
         grp.sync();
         if (grp.lane == 0) {
-            g[(1 + bounded(d[0], (uint32_t)(m - 1))) * S + m] = (uint8_t)C_EMPTY;
-            g[(m + 1 + bounded(d[1], (uint32_t)(S - 2 - m))) * S + m] = (uint8_t)C_EMPTY;
-            g[m * S + 1 + bounded(d[2], (uint32_t)(m - 1))] = (uint8_t)C_EMPTY;
-            g[m * S + m + 1 + bounded(d[3], (uint32_t)(S - 2 - m))] = (uint8_t)C_EMPTY;
+            g[(1 + bounded(d[0], (uint32_t)(m - 1))) * W + m] = (uint8_t)C_EMPTY;
+            g[(m + 1 + bounded(d[1], (uint32_t)(S - 2 - m))) * W + m] = (uint8_t)C_EMPTY;
+            g[m * W + 1 + bounded(d[2], (uint32_t)(m - 1))] = (uint8_t)C_EMPTY;
+            g[m * W + m + 1 + bounded(d[3], (uint32_t)(S - 2 - m))] = (uint8_t)C_EMPTY;
         }
         grp.sync();
-        const int n = count_free(grp, g, S, 1, S - 2, 1, S - 2, -1);
-        const int gc = kth_free(grp, g, S, 1, S - 2, 1, S - 2, -1, bounded(d[4], (uint32_t)n));
+        const int n = count_free(grp, g, W, 1, S - 2, 1, S - 2, -1);
+        const int gc = kth_free(grp, g, W, 1, S - 2, 1, S - 2, -1, bounded(d[4], (uint32_t)n));
         if (gc < 0) return false;
         grp.sync();
         if (grp.lane == 0) g[gc] = (uint8_t)C_GOAL;
         grp.sync();
-        const int ac = kth_free(grp, g, S, 1, S - 2, 1, S - 2, -1, bounded(d[5], (uint32_t)(n - 1)));
+        const int ac = kth_free(grp, g, W, 1, S - 2, 1, S - 2, -1, bounded(d[5], (uint32_t)(n - 1)));
         if (ac < 0) return false;
-        a.x = ac % S;
-        a.y = ac / S;
+        a.x = ac % W;
+        a.y = ac / W;
         a.dir = bounded(d[6], 4u);
     } else if (family == NX_LAVAGAP) {
         const int xl = 2 + bounded(d[0], (uint32_t)(S - 4));
         const int gap = 1 + bounded(d[1], (uint32_t)(S - 2));
         for (int y = 1 + grp.lane; y <= S - 2; y += G)
-            if (y != gap) g[y * S + xl] = (uint8_t)C_LAVA;
+            if (y != gap) g[y * W + xl] = (uint8_t)C_LAVA;
     } else if (family == NX_EMPTY_RANDOM) {
         grp.sync();
-        const int n = count_free(grp, g, S, 1, S - 2, 1, S - 2, -1);
-        const int ac = kth_free(grp, g, S, 1, S - 2, 1, S - 2, -1, bounded(d[0], (uint32_t)n));
+        const int n = count_free(grp, g, W, 1, S - 2, 1, S - 2, -1);
+        const int ac = kth_free(grp, g, W, 1, S - 2, 1, S - 2, -1, bounded(d[0], (uint32_t)n));
         if (ac < 0) return false;
-        a.x = ac % S;
-        a.y = ac / S;
+        a.x = ac % W;
+        a.y = ac / W;
         a.dir = bounded(d[1], 4u);
     } else if (family == NX_GOTODOOR) {
         // L8: one closed door on each wall (top, bottom, left, right) at drawn
@@ -517,9 +524,9 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         }
         if (grp.lane == 0) {
             g[1 + bounded(d[0], (uint32_t)(S - 2))] = (uint8_t)make_code(K_DOOR_CLOSED, perm & 15u);
-            g[(S - 1) * S + 1 + bounded(d[1], (uint32_t)(S - 2))] = (uint8_t)make_code(K_DOOR_CLOSED, (perm >> 4) & 15u);
-            g[(1 + bounded(d[2], (uint32_t)(S - 2))) * S] = (uint8_t)make_code(K_DOOR_CLOSED, (perm >> 8) & 15u);
-            g[(1 + bounded(d[3], (uint32_t)(S - 2))) * S + S - 1] =
+            g[(S - 1) * W + 1 + bounded(d[1], (uint32_t)(S - 2))] = (uint8_t)make_code(K_DOOR_CLOSED, (perm >> 4) & 15u);
+            g[(1 + bounded(d[2], (uint32_t)(S - 2))) * W] = (uint8_t)make_code(K_DOOR_CLOSED, (perm >> 8) & 15u);
+            g[(1 + bounded(d[3], (uint32_t)(S - 2))) * W + S - 1] =
                 (uint8_t)make_code(K_DOOR_CLOSED, (perm >> 12) & 15u);
         }
         group_draws(grp, 3, d,
@@ -534,19 +541,19 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         // S-2 (variant 1); the goal is at (S-2, 1); no draws
         const int r2 = variant == 0 ? 3 : S - 2;
         for (int x = 2 + grp.lane; x <= S - 3; x += G) {
-            g[S + x] = (uint8_t)C_LAVA;
-            g[r2 * S + x] = (uint8_t)C_LAVA;
+            g[W + x] = (uint8_t)C_LAVA;
+            g[r2 * W + x] = (uint8_t)C_LAVA;
         }
     } else if (family == NX_KEYCORRIDOR) {
-        const uint32_t ag = keycorridor_layout(grp, g, S, variant, seed, key_env, episode);
+        const uint32_t ag = keycorridor_layout(grp, g, S, W, variant, seed, key_env, episode);
         a.x = ag & 0xFF;
         a.y = (ag >> 8) & 0xFF;
         a.dir = ag >> 16;
     } else if (family == NX_LAVA_CROSSING || family == NX_SIMPLE_CROSSING) {
-        crossing_layout(grp, g, S, family, variant, seed, key_env, episode);
+        crossing_layout(grp, g, S, W, family, variant, seed, key_env, episode);
     } else if (family == NX_DYNOBS) {
         grp.sync();
-        const int agent = 1 * S + 1;
+        const int agent = 1 * W + 1;
         a.nb = n_balls;
         // ball b's column / row go to byte b of px / py and its draw k = b is
         // taken in the loop, so that no array is indexed by the loop counter
@@ -554,14 +561,14 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         uint32_t px = 0, py = 0;
         for (int b = 0; b < n_balls; ++b) {
             const uint32_t db = draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, (uint32_t)b);
-            const int n = count_free(grp, g, S, 1, S - 2, 1, S - 2, agent);
-            const int bc = kth_free(grp, g, S, 1, S - 2, 1, S - 2, agent, bounded(db, (uint32_t)n));
+            const int n = count_free(grp, g, W, 1, S - 2, 1, S - 2, agent);
+            const int bc = kth_free(grp, g, W, 1, S - 2, 1, S - 2, agent, bounded(db, (uint32_t)n));
             if (bc < 0) return false;
             grp.sync();
             if (grp.lane == 0) g[bc] = (uint8_t)C_BALL_BLUE;
             grp.sync();
-            const int by = bc / S;
-            px |= (uint32_t)(bc - by * S) << (8 * b);
+            const int by = bc / W;
+            px |= (uint32_t)(bc - by * W) << (8 * b);
             py |= (uint32_t)by << (8 * b);
         }
 #pragma unroll
@@ -582,7 +589,7 @@ template <int FAM>
 __device__ __noinline__ bool reset_layout_warp(uint8_t* g, int S, int family, int n_balls, int variant, uint64_t seed,
                                                uint32_t key_env, uint32_t episode, AgentReg& a)
 {
-    return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, FAM >= 0 ? FAM : family, n_balls, variant, seed,
+    return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, S, FAM >= 0 ? FAM : family, n_balls, variant, seed,
                         key_env, episode, a);
 }
 
@@ -662,8 +669,9 @@ __device__ __forceinline__ uint64_t occlusion(uint64_t tmask, const uint16_t* ta
 // Geometry of one env's view for one step: view cell (vx, vy) shows world
 // cell pos + (6 - vy) F + (vx - 3) R (F the facing direction, R its
 // right-hand side, y growing downward), i.e. linear index
-// idx0 + vx dR - vy dF; it lies inside the grid iff bit vx of colmask and bit
-// vy of rowmask are set (outside cells read as a grey wall).
+// idx0 + vx dR - vy dF for row stride W; it lies inside the grid iff bit vx
+// of colmask and bit vy of rowmask are set (outside cells read as a grey
+// wall).
 struct ViewGeom {
     int idx0, dR, dF;
     uint32_t colmask, rowmask;
@@ -676,14 +684,14 @@ __device__ __forceinline__ uint32_t bit_range(int lo, int hi)  // bits lo..hi of
     return lo > hi ? 0u : ((2u << hi) - (1u << lo));
 }
 
-__device__ __forceinline__ ViewGeom view_geom(const AgentReg& a, int S)
+__device__ __forceinline__ ViewGeom view_geom(const AgentReg& a, int S, int W)
 {
     const int fx = (a.dir == 0) - (a.dir == 2), fy = (a.dir == 1) - (a.dir == 3);
     const int rx = -fy, ry = fx;
     ViewGeom g;
-    g.dF = fy * S + fx;
-    g.dR = ry * S + rx;
-    g.idx0 = a.y * S + a.x + 6 * g.dF - 3 * g.dR;
+    g.dF = fy * W + fx;
+    g.dR = ry * W + rx;
+    g.idx0 = a.y * W + a.x + 6 * g.dF - 3 * g.dR;
     // along R: coordinate a_r + (vx - 3) * sign(R)
     const int ar = rx != 0 ? a.x : a.y, sr = rx + ry;
     g.colmask = sr > 0 ? bit_range(3 - ar, 3 + (S - 1 - ar)) : bit_range(3 - (S - 1 - ar), 3 + ar);
@@ -729,11 +737,16 @@ struct ViewOut<1> {
 // Byte mask of the four low bits of m (bit i set -> byte i = 0xFF).
 __device__ __forceinline__ uint32_t byte_mask4(uint32_t m) { return ((m * 0x00204081u) & 0x01010101u) * 0xFFu; }
 
+// Groups of 8 or more lanes read a grid with a wall margin of at least six
+// cells on every side (row stride W >= S + 12): every cell of the view, and of
+// the idle lanes' positions (one row behind the agent, four columns to its
+// right), lies in the margin or the grid, so they read without an in-grid
+// test.  Narrower groups read a packed grid (W = S) with the masks.
 template <int G>
-__device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g, int S, const AgentReg& a,
+__device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g, int S, int W, const AgentReg& a,
                                             const uint32_t* dec, const uint16_t* occ, ViewOut<G>& out, uint16_t* tiles)
 {
-    const ViewGeom v = view_geom(a, S);
+    const ViewGeom v = view_geom(a, S, W);
     if constexpr (G == 1) {
         // Strided gather: cell (vx, vy) is read at g[idx0 + vx dR - vy dF]
         // without a bounds test (guard bytes around the grid region keep every
@@ -791,9 +804,9 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
         for (int k = 0; k < K; ++k) {
             const int vy = k * RPK + r0;
             const bool cell = vx < 7 && vy < 7;
-            // the in-grid test and the agent's cell (3, 6) as selects
-            const bool in = cell && ((v.colmask >> vx) & (v.rowmask >> vy) & 1u);
-            const uint32_t ld = in ? (uint32_t)g[v.idx0 + vx * v.dR - vy * v.dF] : (uint32_t)C_WALL;
+            // cells beyond the grid read the wall margin; the agent's cell
+            // (3, 6) shows what it carries
+            const uint32_t ld = g[v.idx0 + vx * v.dR - vy * v.dF];
             const uint32_t cd = (vy == 6 && vx == 3) ? carried : ld;
             code[k] = cd;
             tw[k] = grp.ballot(cell && !(cd & OPAQUE));  // row k RPK + r: bits 8 r .. 8 r + 6

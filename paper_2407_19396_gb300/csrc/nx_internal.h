@@ -101,7 +101,7 @@ struct nx_kparams {
     nx_req* reqs;
     nx_ctl* ctl;
     const uint8_t* atlas;
-    int32_t cell_stride;   // smem bytes per env grid (nx_cell_stride: >= max size^2, an odd number of words)
+    int32_t cell_stride;   // smem bytes per env slot (nx_slot_stride of the launch shape)
     int32_t envs_per_cta;
     int32_t reset_all;     // 1: start every env at episode 0 and emit its observation (no steps)
     int32_t phases;        // symbolic staging parts per step (1 or 2)
@@ -128,8 +128,18 @@ inline int nx_cell_stride(int max_cells)
     const int s = (max_cells + 3) & ~3;
     return ((s >> 2) & 1) ? s : s + 4;
 }
-int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride);
-int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err);  // resident CTAs on the device
+// Groups of 8 or more lanes keep NX_VIEW_PAD wall cells around each grid in
+// shared memory (the view reaches six cells ahead), narrower ones pack it.
+#define NX_VIEW_PAD 6
+// Bytes per env slot of a launch shape for grids of side up to max_side
+// (nx_kparams::cell_stride).
+inline int nx_slot_stride(const nx_launch_shape& s, int max_side)
+{
+    const int side = s.group_lanes >= 8 ? max_side + 2 * NX_VIEW_PAD : max_side;
+    return nx_cell_stride(side * side);
+}
+int nx_kernel_smem_bytes(const nx_launch_shape& s, int max_side);
+int nx_kernel_max_ctas(const nx_launch_shape& s, int max_side, int* err);  // resident CTAs on the device
 int nx_launch_step_kernel(const nx_launch_shape& s, const nx_kparams& p, int grid, void* stream);
 int nx_launch_advance(nx_req* reqs, int n_reqs, void* stream);
 int nx_launch_configure(nx_req* r, const nx_req& v, int gstep_mode, void* stream);

@@ -54,7 +54,8 @@ int nx_lean_supported(const nx_launch_shape& s)
     return (G == 1 || G == 4 || G == 8 || G == 16 || G == 32) && !s.rgb && !s.full && !s.policy;
 }
 
-int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride)
+// dynamic shared memory of a launch with env slots of cell_stride bytes
+static int smem_for_stride(const nx_launch_shape& s, int cell_stride)
 {
     const int E = s.envs_per_cta;
     const int epw = 32 / s.group_lanes, warps = E * s.group_lanes / 32;
@@ -68,9 +69,14 @@ int nx_kernel_smem_bytes(const nx_launch_shape& s, int cell_stride)
     return b;
 }
 
-int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err)
+int nx_kernel_smem_bytes(const nx_launch_shape& s, int max_side)
 {
-    const int smem = nx_kernel_smem_bytes(s, cell_stride);
+    return smem_for_stride(s, nx_slot_stride(s, max_side));
+}
+
+int nx_kernel_max_ctas(const nx_launch_shape& s, int max_side, int* err)
+{
+    const int smem = nx_kernel_smem_bytes(s, max_side);
     const int threads = s.envs_per_cta * s.group_lanes;
     if (s.full) return nx_kernel_max_ctas_full(s, threads, smem, err);
     if (s.policy) return policy_occupancy(threads, smem, err);
@@ -89,7 +95,7 @@ int nx_kernel_max_ctas(const nx_launch_shape& s, int cell_stride, int* err)
 
 int nx_launch_step_kernel(const nx_launch_shape& s, const nx_kparams& p, int grid, void* stream)
 {
-    const int smem = nx_kernel_smem_bytes(s, p.cell_stride);
+    const int smem = smem_for_stride(s, p.cell_stride);
     cudaStream_t st = (cudaStream_t)stream;
     if (s.full) return nx_launch_step_kernel_full(s, p, grid, smem, st);
     if (s.policy) return launch_t<1, false, false, true>(p, grid, smem, st);

@@ -32,7 +32,6 @@ struct nx_env {
     std::vector<nx_desc> descs;
     std::vector<uint32_t> grid_offset;
     size_t grid_pool = 0;
-    int cell_stride = 0;
     int max_side = 0;
     int device = 0;
     int sm_count = 0;

@@ -457,7 +457,7 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
         delete s;
         return nx_fail(nullptr, NX_E_INVAL, "unsupported launch shape");
     }
-    s->cell_stride = nx_cell_stride(NX_MAX_SIZE * NX_MAX_SIZE);
+    s->cell_stride = nx_slot_stride(s->shape, NX_MAX_SIZE);
     int dev = 0, err = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
@@ -465,7 +465,7 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
         return nx_fail(nullptr, NX_E_CUDA, "no CUDA device available");
     }
     s->device = dev;
-    s->per_sm = nx_kernel_max_ctas(s->shape, s->cell_stride, &err);
+    s->per_sm = nx_kernel_max_ctas(s->shape, NX_MAX_SIZE, &err);
     if (err || s->per_sm < 1) {
         delete s;
         return nx_fail(nullptr, NX_E_CUDA, "occupancy query failed");

@@ -118,10 +118,10 @@ nx_status nx_rollout_noalloc(int32_t family, int32_t size, int32_t n_envs, uint6
     const size_t agents_off = (kItemsOff + (size_t)n_items * sizeof(nx_item) + 255) & ~(size_t)255;
     const size_t grids_off = (agents_off + (size_t)n_envs * sizeof(nx_agent) + 255) & ~(size_t)255;
     const int max_steps = nx_default_max_steps(family, size);
-    const int cell_stride = nx_cell_stride(size * size);
     const nx_launch_shape shape{kLanes, kEnvsPerCta, 0};
+    const int cell_stride = nx_slot_stride(shape, size);
     int err = 0;
-    const int per_sm = nx_kernel_max_ctas(shape, cell_stride, &err);
+    const int per_sm = nx_kernel_max_ctas(shape, size, &err);
     if (err) return nx_cuda_fail(nullptr, err, "occupancy query");
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -34,6 +34,11 @@ using namespace nxd;
 // after it); reads that land in a neighbour's grid or a guard are replaced by
 // walls.
 constexpr int kGridGuard = 128;
+// Groups of 8 or more lanes keep this many wall cells around each grid in
+// shared memory (row stride S + 2 kViewPad): the view reaches six cells
+// ahead and three to the side, so every read of the view or of the forward
+// cell lands in the env's slot, and beyond the grid it reads a wall.
+constexpr int kViewPad = NX_VIEW_PAD;
 constexpr int kMaxThreads = 256;
 
 __host__ __device__ __forceinline__ int align16(int v) { return (v + 15) & ~15; }
@@ -44,7 +49,7 @@ __device__ __forceinline__ uint64_t digest_word(uint64_t h, uint32_t w) { return
 // Intervention (rotate / forward / pickup / drop / toggle / done), the
 // Dynamic-Obstacles transition, then time, truncation, reward and termination.
 template <int G>
-__device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int family, int max_steps, AgentReg& a,
+__device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int W, int family, int max_steps, AgentReg& a,
                                          int action, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
                                          float action_cost, float time_cost, float& reward, int& term, int& trunc)
 {
@@ -62,7 +67,7 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
                 for (int dx = -1; dx <= 1; ++dx) {
                     if (dx == 0 && dy == 0) continue;
                     const int x = a.bx[b] + dx, y = a.by[b] + dy;
-                    const bool f = (unsigned)x < (unsigned)S && (unsigned)y < (unsigned)S && g[y * S + x] == C_EMPTY &&
+                    const bool f = (unsigned)x < (unsigned)S && (unsigned)y < (unsigned)S && g[y * W + x] == C_EMPTY &&
                                    !(x == a.x && y == a.y);
                     cand |= (f ? 1u : 0u) << j;
                     ++j;
@@ -77,8 +82,8 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
                 const int nx = a.bx[b] + (o % 3) - 1, ny = a.by[b] + (o / 3) - 1;
                 grp.sync();
                 if (grp.lane == 0) {
-                    g[a.by[b] * S + a.bx[b]] = (uint8_t)C_EMPTY;
-                    g[ny * S + nx] = (uint8_t)C_BALL_BLUE;
+                    g[a.by[b] * W + a.bx[b]] = (uint8_t)C_EMPTY;
+                    g[ny * W + nx] = (uint8_t)C_BALL_BLUE;
                 }
                 grp.sync();
                 a.bx[b] = nx;
@@ -96,8 +101,9 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
     const int act = (unsigned)action < (unsigned)n_act ? action : 7;  // 7: no-op
     const int fxd = (a.dir == 0) - (a.dir == 2), fyd = (a.dir == 1) - (a.dir == 3);
     const int fx = a.x + fxd, fy = a.y + fyd;
-    const bool in = (unsigned)fx < (unsigned)S && (unsigned)fy < (unsigned)S;
-    const int fi = fy * S + fx;
+    // (with a wall margin, W > S, a cell beyond the grid reads as a wall)
+    const bool in = W > S || ((unsigned)fx < (unsigned)S && (unsigned)fy < (unsigned)S);
+    const int fi = fy * W + fx;
     const uint32_t fc = in ? (uint32_t)g[fi] : (uint32_t)C_WALL;
     const uint32_t fcol = cell_col(fc), kb = 1u << cell_kind(fc);
     constexpr uint32_t kDoors = (1u << K_DOOR_OPEN) | (1u << K_DOOR_CLOSED) | (1u << K_DOOR_LOCKED);
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     uint16_t* sfull = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(stiles) + align16(E * 49 * 2));
     const int gi = tid / G;
     const Grp<G> grp(tid);
-    uint8_t* mygrid = sgrid + gi * cs;
+    constexpr int kPad = G >= 8 ? kViewPad : 0;
     // fused policy: the A tile of the 128 envs' rows, then the agent's weights
     uint8_t* sA = smem + policy_smem_offset(grid_bytes, (nthreads >> 5) * wbytes);
     uint8_t* sW = sA + nxp::kATileBytes;
@@ -324,6 +330,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         const int F = FULL ? rq->full_side : 0;
 
         const int n = (int)item.n_envs, S = item.size, HW = S * S, variant = (int)item.variant;
+        const int W = S + 2 * kPad;                                 // row stride of the env's grid in its slot
+        uint8_t* mygrid = sgrid + gi * cs + kPad * (W + 1);         // cell (0, 0)
         const int family = kLean ? FAM : (int)item.family;
         const int max_steps = item.max_steps;
         const bool active = gi < n;
@@ -335,13 +343,19 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         uint64_t dig = 0;
         uint32_t eps = 0;
 
+        if constexpr (kPad > 0) {
+            // every slot starts as walls (the margins stay so)
+            constexpr uint32_t kWall4 = C_WALL * 0x01010101u;
+            for (int i = tid; i < n * cs / 4; i += nthreads) reinterpret_cast<uint32_t*>(sgrid)[i] = kWall4;
+            __syncthreads();
+        }
         if (!p.reset_all) {
             const uint8_t* src = p.grids + item.grid_offset;
             for (int i = tid; i < n * HW; i += nthreads) {
                 const int e = i / HW, c = i - e * HW;
                 const uint8_t* b = src + (size_t)e * 3 * HW;
-                sgrid[e * cs + c] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
-
+                const int y = c / S, x = c - y * S;
+                sgrid[e * cs + (y + kPad) * W + x + kPad] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
             }
             if (active) load_agent(p.agents + env, a);
         }
@@ -359,7 +373,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             for (int i = tid; i < nxp::kImageBytes / 16; i += nthreads) reinterpret_cast<uint4*>(sW)[i] = src[i];
             if (active) {
                 ViewOut<G> v0;
-                render_view(grp, mygrid, S, a, s_dec, nullptr, v0, nullptr);
+                render_view(grp, mygrid, S, W, a, s_dec, nullptr, v0, nullptr);
                 nxp::store_obs_row(sA, tid, v0.sw);
             } else {
                 nxp::store_zero_row(sA, tid);
@@ -402,7 +416,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             if constexpr (G >= 8) {
                 if (starts) {
                     const int inv = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
-                    if (!reset_layout(grp, mygrid, S, family, n_balls, variant, seed, key,
+                    if (!reset_layout(grp, mygrid, S, W, family, n_balls, variant, seed, key,
                                       p.reset_all ? 0u : a.episode + 1u, a))
                         if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
                     a.invalid = inv;
@@ -455,12 +469,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                             return draw(seed, key, episode, t, PURPOSE_BALL, k);
                         });
                     }
-                    env_step(grp, mygrid, S, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
+                    env_step(grp, mygrid, S, W, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
                              time_cost, reward, term, trunc);
                 }
                 // (every grid write above -- a reset, a ball move, the action's
                 // write -- ends with a group barrier, so the view sees it)
-                render_view(grp, mygrid, S, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
+                render_view(grp, mygrid, S, W, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
                             RGB && obs_rgb ? stiles + gi * 49 : nullptr);
                 if constexpr (POL) nxp::store_obs_row(sA, tid, vo.sw);  // the next step's policy input
                 if constexpr (FULL) if (obs_full || obs_cat || obs_rgb_full) {
@@ -474,7 +488,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                         const int y = c / F, x = c - y * F;
                         uint32_t tri = 0;
                         const bool agent_cell = x == a.x && y == a.y;
-                        if (x < S && y < S) tri = agent_cell ? (10u | ((uint32_t)a.dir << 16)) : s_dec[mygrid[y * S + x]];
+                        if (x < S && y < S) tri = agent_cell ? (10u | ((uint32_t)a.dir << 16)) : s_dec[mygrid[y * W + x]];
                         if (fo) {
                             fo[3 * c] = (uint8_t)tri;
                             fo[3 * c + 1] = (uint8_t)(tri >> 8);
@@ -608,7 +622,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             uint8_t* dst = p.grids + item.grid_offset;
             for (int i = tid; i < n * HW; i += nthreads) {
                 const int e = i / HW, c = i - e * HW;
-                const uint32_t code = sgrid[e * cs + c];
+                const int y = c / S, x = c - y * S;
+                const uint32_t code = sgrid[e * cs + (y + kPad) * W + x + kPad];
                 uint8_t* b = dst + (size_t)e * 3 * HW;
                 b[c] = (uint8_t)cell_ent(code);
                 b[HW + c] = (uint8_t)cell_col(code);
