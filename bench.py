@@ -485,7 +485,9 @@ def main():
     # end to end through the C ABI with host buffers: host actions in, host outputs back, every step
     e2e = None
     if True:  # every rank: the e2e leg is timed like the device leg (max over ranks)
-        T = w["T"]
+        # the whole horizon's outputs in pinned host memory, at most 4 GiB of
+        # it (a shorter horizon for the largest batches)
+        T = max(1, min(w["T"], (4 << 30) // (n * (OUT_BYTES_SYM + 1))))
         acts = torch.from_numpy(inputs.random_actions(w["seed"], (T, n), n_actions=3 if w["parts"][0][0] == 4 else 7))
         acts = acts.pin_memory()
         hout = {"obs_sym": torch.empty((T, n, 7, 7, 3), dtype=torch.uint8).pin_memory(),
@@ -515,7 +517,7 @@ def main():
         h2d = T * n
         d2h = T * n * OUT_BYTES_SYM
         e2e = {"value": world * n * T * ks / el, "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": ks, "actions": "host int8, seeded numpy draws"}
+               "d2h_bytes_per_step": d2h, "steps": ks, "horizon": T, "actions": "host int8, seeded numpy draws"}
         e2e_env.close()
 
     line = {

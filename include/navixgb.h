@@ -177,8 +177,10 @@ typedef struct {
 /* Launch shape in use (after autotuning); policy_* describe the fused-policy
  * launches (0 before nx_set_policy).  lean_family >= 0: rollouts of this
  * context with random actions, no action output and the Markov reward (and
- * no RGB or fully observable views) launch the step kernel compiled for that
- * one family, on lean_grid_ctas CTAs; -1: every call runs the general one. */
+ * no RGB or fully observable views) launch a step kernel compiled for such
+ * calls -- for that one family, or for any family where it is
+ * NX_N_FAMILIES -- on lean_grid_ctas CTAs; -1: every call runs the general
+ * one. */
 typedef struct {
     int32_t group_lanes, envs_per_cta, staging, n_items, grid_ctas, smem_bytes, steps_per_launch;
     int32_t n_envs, n_families;

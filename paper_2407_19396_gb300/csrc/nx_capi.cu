@@ -276,7 +276,7 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
     env->grid_pool = off;
     env->n_families = 0;
     for (bool b : seen) env->n_families += b ? 1 : 0;
-    env->lean_family = env->n_families == 1 ? (int)env->descs[0].family : -1;
+    env->lean_family = env->n_families == 1 ? (int)env->descs[0].family : NX_N_FAMILIES;
 
     env->d_agents = (nx_agent*)nx_dev_alloc(env, sizeof(nx_agent) * (size_t)env->n_envs);
     env->d_grids = (uint8_t*)nx_dev_alloc(env, env->grid_pool);
@@ -437,8 +437,9 @@ static nx_status prof_mark(nx_env* env, bool begin)
     return NX_OK;
 }
 
-// The lean instantiation of the context's shape (one family, the Markov
-// reward; see nx_step_kernel), with its grid; false where there is none.  Its
+// The lean instantiation of the context's shape (for its one family, or for
+// any family; the Markov reward; see nx_step_kernel), with its grid; false
+// where there is none.  Its
 // occupancy query (which sets a kernel attribute) runs on first use, outside
 // any stream capture.
 static bool lean_shape(const nx_env* env, nx_launch_shape* s, int* grid)

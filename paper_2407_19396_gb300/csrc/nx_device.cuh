@@ -583,14 +583,14 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
 
 // The same generator run by a whole warp for one env, kept out of line: it is
 // the rare path of narrow groups, and inlining it would raise the register
-// allocation of the whole step kernel.  FAM >= 0 fixes the family (the lean
-// step kernels).
+// allocation of the whole step kernel.  0 <= FAM < NX_N_FAMILIES fixes the
+// family (the lean step kernels of one family).
 template <int FAM>
 __device__ __noinline__ bool reset_layout_warp(uint8_t* g, int S, int family, int n_balls, int variant, uint64_t seed,
                                                uint32_t key_env, uint32_t episode, AgentReg& a)
 {
-    return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, S, FAM >= 0 ? FAM : family, n_balls, variant, seed,
-                        key_env, episode, a);
+    return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, S, (FAM >= 0 && FAM < NX_N_FAMILIES) ? FAM : family,
+                        n_balls, variant, seed, key_env, episode, a);
 }
 
 // ---------------------------------------------------------------------------

@@ -118,7 +118,7 @@ struct nx_launch_shape {
     int rgb_full_side = 0;  // reserve smem for full-view RGB tile ids of this grid side
     bool full = false;      // the instantiation that writes the fully observable views
     bool policy = false;    // the fused-policy instantiation (1 lane, 128 envs per CTA)
-    int lean_family = -1;   // >= 0: the lean instantiation for this family (nx_lean_supported)
+    int lean_family = -1;   // >= 0: the lean instantiation for this family, NX_N_FAMILIES: any family
 };
 // Shared-memory bytes per env grid for grids of up to max_cells cells: a
 // whole number of 4-byte words, and an odd one, so that the grids of the 32
@@ -145,8 +145,9 @@ int nx_launch_advance(nx_req* reqs, int n_reqs, void* stream);
 int nx_launch_configure(nx_req* r, const nx_req& v, int gstep_mode, void* stream);
 int nx_launch_set_steps(nx_req* r, int steps, void* stream);
 int nx_shape_supported(const nx_launch_shape& s);
-// Whether a shape has lean instantiations (one family, random actions, no
-// action output or digest, Markov reward, symbolic outputs only).
+// Whether a shape has lean instantiations (random actions, no action output
+// or digest, Markov reward, symbolic outputs only; one per family and one for
+// any family).
 int nx_lean_supported(const nx_launch_shape& s);
 #ifdef __CUDACC__
 int nx_kernel_max_ctas_full(const nx_launch_shape& s, int threads, int smem, int* err);

@@ -57,7 +57,7 @@ struct nx_env {
     int grid_ctas = 0;
     int per_sm = 0;
     int per_sm_full = 0;  // resident CTAs of the instantiation with the fully observable views
-    int lean_family = -1;  // the one family of every env (-1: several), for the lean step kernels
+    int lean_family = -1;  // lean step kernels: the one family of every env, or NX_N_FAMILIES (several)
     mutable int per_sm_lean = 0;  // resident CTAs of the lean instantiation (cache; 0: not queried, -1: none)
     std::vector<int> fam_begin;
     bool tuned = false;

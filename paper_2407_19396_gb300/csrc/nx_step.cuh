@@ -227,19 +227,19 @@ __host__ __device__ __forceinline__ int policy_smem_offset(int grid_bytes, int s
     return (grid_bytes + staging_bytes + 127) & ~127;
 }
 
-// FAM >= 0 is the lean instantiation for launches whose every work item has
-// family FAM and whose request is of the common kind: random actions, no
-// action output, no digest, the Markov reward, symbolic outputs only.  The
-// compiler then drops the other families' generators and rules and the
-// per-call branches of the step loop (the paper's implementation likewise
-// compiles one program per environment); the host launches it only for such
-// calls.
+// FAM >= 0 is a lean instantiation, for requests of the common kind: random
+// actions, no action output, no digest, the Markov reward, symbolic outputs
+// only.  FAM < NX_N_FAMILIES: every work item of the launch has family FAM,
+// so the compiler also drops the other families' generators and rules (the
+// paper's implementation likewise compiles one program per environment);
+// FAM = NX_N_FAMILIES: items of any family.  The host launches them only for
+// such calls.
 template <int G, bool RGB, bool FULL, bool POL = false, int FAM = -1>
 __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparams p)
 {
     static_assert(!POL || (G == 1 && !RGB && !FULL), "the fused policy runs one lane per env");
     constexpr bool kLean = FAM >= 0;
-    static_assert(!kLean || (!RGB && !FULL && !POL && FAM < NX_N_FAMILIES), "lean: one family, symbolic outputs");
+    static_assert(!kLean || (!RGB && !FULL && !POL && FAM <= NX_N_FAMILIES), "lean: symbolic outputs only");
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar;  // fused policy: MMA completion
     __shared__ uint32_t s_tmem;               // fused policy: tensor-memory base address
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         const int n = (int)item.n_envs, S = item.size, HW = S * S, variant = (int)item.variant;
         const int W = S + 2 * kPad;                                 // row stride of the env's grid in its slot
         uint8_t* mygrid = sgrid + gi * cs + kPad * (W + 1);         // cell (0, 0)
-        const int family = kLean ? FAM : (int)item.family;
+        const int family = (kLean && FAM < NX_N_FAMILIES) ? FAM : (int)item.family;
         const int max_steps = item.max_steps;
         const bool active = gi < n;
         const uint32_t local = item.local_begin + (uint32_t)gi;
@@ -735,8 +735,9 @@ inline int policy_occupancy(int threads, int smem, int* err)
     case 8: return FN<G_, false, false, false, 8>(__VA_ARGS__);             \
     case 9: return FN<G_, false, false, false, 9>(__VA_ARGS__);             \
     case 10: return FN<G_, false, false, false, 10>(__VA_ARGS__);           \
+    case 11: return FN<G_, false, false, false, 11>(__VA_ARGS__);           \
     default: return -1;                                                     \
     }
-static_assert(NX_N_FAMILIES == 11, "NX_DISPATCH_FAM lists every family");
+static_assert(NX_N_FAMILIES == 11, "NX_DISPATCH_FAM lists every family, then any family (11)");
 
 }  // namespace nxk
