@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnavixgb.so")
 SOURCES = ["nx_kernels.cu", "nx_kernels_full.cu", "nx_capi.cu", "nx_static.cu", "nx_server.cu", "nx_lean_g1.cu",
-           "nx_lean_g4.cu", "nx_lean_g8.cu", "nx_lean_g16.cu", "nx_lean_g32.cu"]
+           "nx_lean_g4.cu", "nx_lean_g8.cu", "nx_lean_g16.cu", "nx_lean_g32.cu", "nx_lean_pol.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <string>
 #include <thread>
 #include <vector>
@@ -437,6 +438,15 @@ static nx_status prof_mark(nx_env* env, bool begin)
     return NX_OK;
 }
 
+// The fused-policy launch shape: 1 lane per env, 128 envs per block; its lean
+// instantiation (the context's family or any family) with the Markov reward.
+static nx_launch_shape policy_shape(const nx_env* env)
+{
+    nx_launch_shape ps{1, nxp::kRows, 0, 1, 0, false, true};
+    if (env->lean_family >= 0 && env->req_host.reward_mode == NX_REWARD_MARKOV) ps.lean_family = env->lean_family;
+    return ps;
+}
+
 // The lean instantiation of the context's shape (for its one family, or for
 // any family; the Markov reward; see nx_step_kernel), with its grid; false
 // where there is none.  Its
@@ -467,7 +477,7 @@ static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid
                            bool lean = false)
 {
     if (policy) {
-        *s = nx_launch_shape{1, nxp::kRows, 0, 1, 0, false, true};
+        *s = policy_shape(env);
         *grid = std::min(env->n_items_pol, env->per_sm_pol * env->sm_count);
         return NX_OK;
     }
@@ -735,12 +745,13 @@ nx_status nx_set_policy(nx_env* env, const nx_policy* pol)
         if (first / epa != last / epa)
             return nx_fail(env, NX_E_INVAL, "a weight set boundary splits a 128-env block of the work list");
     }
-    nx_launch_shape ps{1, nxp::kRows, 0, 1, 0, false, true};
+    const nx_launch_shape ps = policy_shape(env);
     int err = 0;
     const int per_sm = nx_kernel_max_ctas(ps, env->max_side, &err);
     if (err) return nx_cuda_fail(env, err, "occupancy query");
     if (per_sm < 1) return nx_fail(env, NX_E_INVAL, "the fused policy does not fit on an SM with these grids");
-    // weight images: bf16 bits of int8 values (exact), biases as int32
+    // weight images: bf16 bits of int8 values (exact); biases of layers 1, 2 as
+    // f32 times 2^-shift (exact for |b| <= 2^22), of layer 3 as int32
     std::vector<uint8_t> img((size_t)A * nxp::kImageBytes, 0);
     auto bf16 = [](int v) -> uint16_t {
         float f = (float)v;
@@ -760,8 +771,12 @@ nx_status nx_set_policy(nx_env* env, const nx_policy* pol)
                 put(nxp::kW2, n, k, pol->w2[((size_t)a * 64 + n) * 64 + k]);
                 if (n < 16) put(nxp::kW3, n, k, n < 7 ? pol->w3[((size_t)a * 7 + n) * 64 + k] : 0);
             }
-        memcpy(im + nxp::kB1, pol->b1 + (size_t)a * 64, 64 * 4);
-        memcpy(im + nxp::kB2, pol->b2 + (size_t)a * 64, 64 * 4);
+        for (int j = 0; j < 64; ++j) {
+            const float s1 = std::ldexp((float)pol->b1[(size_t)a * 64 + j], -pol->shift1);
+            const float s2 = std::ldexp((float)pol->b2[(size_t)a * 64 + j], -pol->shift2);
+            memcpy(im + nxp::kB1 + 4 * j, &s1, 4);
+            memcpy(im + nxp::kB2 + 4 * j, &s2, 4);
+        }
         memcpy(im + nxp::kB3, pol->b3 + (size_t)a * 7, 7 * 4);
     }
     NX_CK(env, cudaStreamSynchronize(env->stream), "policy upload");  // the previous images are no longer read
@@ -1114,7 +1129,7 @@ nx_status nx_get_info(const nx_env* env, nx_info* info)
     info->state_bytes = nx_state_bytes(env);
     info->device_bytes = env->device_bytes;
     if (env->d_policy) {
-        nx_launch_shape ps{1, nxp::kRows, 0, 1, 0, false, true};
+        const nx_launch_shape ps = policy_shape(env);
         info->policy_items = env->n_items_pol;
         info->policy_ctas_per_sm = env->per_sm_pol;
         info->policy_grid_ctas = std::min(env->n_items_pol, env->per_sm_pol * env->sm_count);

@@ -162,4 +162,6 @@ NX_LEAN_DECL(8)
 NX_LEAN_DECL(16)
 NX_LEAN_DECL(32)
 #undef NX_LEAN_DECL
+int nx_lean_pol_occupancy(int family, int threads, int smem, int* err);
+int nx_lean_pol_launch(int family, const nx_kparams& p, int grid, int smem, cudaStream_t st);
 #endif

@@ -51,7 +51,7 @@ int nx_shape_supported(const nx_launch_shape& s)
 int nx_lean_supported(const nx_launch_shape& s)
 {
     const int G = s.group_lanes;
-    return (G == 1 || G == 4 || G == 8 || G == 16 || G == 32) && !s.rgb && !s.full && !s.policy;
+    return (G == 1 || G == 4 || G == 8 || G == 16 || G == 32) && !s.rgb && !s.full && (!s.policy || G == 1);
 }
 
 // dynamic shared memory of a launch with env slots of cell_stride bytes
@@ -79,7 +79,9 @@ int nx_kernel_max_ctas(const nx_launch_shape& s, int max_side, int* err)
     const int smem = nx_kernel_smem_bytes(s, max_side);
     const int threads = s.envs_per_cta * s.group_lanes;
     if (s.full) return nx_kernel_max_ctas_full(s, threads, smem, err);
-    if (s.policy) return policy_occupancy(threads, smem, err);
+    if (s.policy)
+        return s.lean_family >= 0 ? nx_lean_pol_occupancy(s.lean_family, threads, smem, err)
+                                  : policy_occupancy(threads, smem, err);
     if (s.lean_family >= 0) {
         if (!nx_lean_supported(s)) return -1;
         switch (s.group_lanes) {
@@ -98,7 +100,9 @@ int nx_launch_step_kernel(const nx_launch_shape& s, const nx_kparams& p, int gri
     const int smem = smem_for_stride(s, p.cell_stride);
     cudaStream_t st = (cudaStream_t)stream;
     if (s.full) return nx_launch_step_kernel_full(s, p, grid, smem, st);
-    if (s.policy) return launch_t<1, false, false, true>(p, grid, smem, st);
+    if (s.policy)
+        return s.lean_family >= 0 ? nx_lean_pol_launch(s.lean_family, p, grid, smem, st)
+                                  : launch_t<1, false, false, true>(p, grid, smem, st);
     if (s.lean_family >= 0) {
         if (!nx_lean_supported(s)) return -1;
         switch (s.group_lanes) {

@@ -37,7 +37,9 @@ constexpr int kIn = 49;
 constexpr int kATileBytes = kRows * kK * 2;  // 16 KB
 // one agent's image of weights and biases in shared memory
 constexpr int kW1 = 0, kW2 = 8192, kW3 = 16384;  // W1^T, W2^T: 64 x 64; W3^T: 16 x 64 (rows >= 7 zero)
-constexpr int kB1 = 18432, kB2 = 18688, kB3 = 18944;  // int32 biases: 64, 64, 16
+// biases: layers 1 and 2 as f32 scaled by 2^-shift of their layer (exact:
+// |b| <= 2^22), layer 3 as int32: 64, 64, 16
+constexpr int kB1 = 18432, kB2 = 18688, kB3 = 18944;
 constexpr int kImageBytes = 19008;
 constexpr uint32_t kSbo = 1024, kLbo = 128;
 
@@ -157,14 +159,17 @@ __device__ __forceinline__ void store_zero_row(uint8_t* sA, int r)
 // Requantises 16 accumulators of this thread's row into bf16 activations:
 // clamp(floor((acc + b) / 2^sh), 0, 255) in f32, exact since acc + b is an
 // integer below 2^24 and the scaling is by a power of two.
-__device__ __forceinline__ void requant_row16(uint8_t* sA, int r, int k0, const uint32_t (&v)[16], const int32_t* b,
+// floor((acc + b) 2^-shift) as one fused multiply-add of the accumulator
+// with the pre-scaled bias bs = b 2^-shift: |acc + b| < 2^23, so the product,
+// the sum and hence the result are exact.
+__device__ __forceinline__ void requant_row16(uint8_t* sA, int r, int k0, const uint32_t (&v)[16], const float* bs,
                                               float scale)
 {
     uint32_t w[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        float h0 = floorf((__uint_as_float(v[2 * j]) + (float)b[2 * j]) * scale);
-        float h1 = floorf((__uint_as_float(v[2 * j + 1]) + (float)b[2 * j + 1]) * scale);
+        float h0 = floorf(__fmaf_rn(__uint_as_float(v[2 * j]), scale, bs[2 * j]));
+        float h1 = floorf(__fmaf_rn(__uint_as_float(v[2 * j + 1]), scale, bs[2 * j + 1]));
         h0 = fminf(fmaxf(h0, 0.0f), 255.0f);
         h1 = fminf(fmaxf(h1, 0.0f), 255.0f);
         const __nv_bfloat162 p2 = __floats2bfloat162_rn(h0, h1);  // low half: h0
@@ -209,13 +214,13 @@ __device__ __forceinline__ int policy_finish(uint8_t* sA, const uint8_t* sW, uin
         phase ^= 1u;
         __syncwarp();  // tcgen05.ld is warp-collective: converge after the per-thread wait
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int32_t* b = reinterpret_cast<const int32_t*>(sW + (layer ? kB2 : kB1));
+        const float* bs = reinterpret_cast<const float*>(sW + (layer ? kB2 : kB1));
         const float scale = pow2_neg(layer ? shift2 : shift1);
 #pragma unroll 1
         for (int c0 = 0; c0 < kK; c0 += 16) {
             uint32_t v[16];
             tmem_ld16(trow + (uint32_t)c0, v);
-            requant_row16(sA, tid, c0, v, b + c0, scale);
+            requant_row16(sA, tid, c0, v, bs + c0, scale);
         }
     }
     sync_for_mma();

@@ -227,19 +227,19 @@ __host__ __device__ __forceinline__ int policy_smem_offset(int grid_bytes, int s
     return (grid_bytes + staging_bytes + 127) & ~127;
 }
 
-// FAM >= 0 is a lean instantiation, for requests of the common kind: random
-// actions, no action output, no digest, the Markov reward, symbolic outputs
-// only.  FAM < NX_N_FAMILIES: every work item of the launch has family FAM,
-// so the compiler also drops the other families' generators and rules (the
-// paper's implementation likewise compiles one program per environment);
-// FAM = NX_N_FAMILIES: items of any family.  The host launches them only for
-// such calls.
+// FAM >= 0 is a lean instantiation, for requests of the common kind: no
+// digest, the Markov reward, symbolic outputs only, and (except the fused
+// policy) random actions without an action output.  FAM < NX_N_FAMILIES:
+// every work item of the launch has family FAM, so the compiler also drops
+// the other families' generators and rules (the paper's implementation
+// likewise compiles one program per environment); FAM = NX_N_FAMILIES: items
+// of any family.  The host launches them only for such calls.
 template <int G, bool RGB, bool FULL, bool POL = false, int FAM = -1>
 __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparams p)
 {
     static_assert(!POL || (G == 1 && !RGB && !FULL), "the fused policy runs one lane per env");
-    constexpr bool kLean = FAM >= 0;
-    static_assert(!kLean || (!RGB && !FULL && !POL && FAM <= NX_N_FAMILIES), "lean: symbolic outputs only");
+    constexpr bool kLean = FAM >= 0, kLeanRandom = kLean && !POL;
+    static_assert(!kLean || (!RGB && !FULL && FAM <= NX_N_FAMILIES), "lean: symbolic outputs only");
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar;  // fused policy: MMA completion
     __shared__ uint32_t s_tmem;               // fused policy: tensor-memory base address
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         uint8_t* out_term = rq->terminated;
         uint8_t* out_trunc = rq->truncated;
         uint8_t* out_mission = rq->mission;
-        int8_t* out_action = kLean ? nullptr : rq->action_out;
+        int8_t* out_action = kLeanRandom ? nullptr : rq->action_out;
         const uint32_t reward_mode = kLean ? (uint32_t)NX_REWARD_MARKOV : rq->reward_mode;
         const float lava_reward = rq->lava_reward;
         const float action_cost = rq->action_cost, time_cost = rq->time_cost;
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 
         // steps == 0 with reset_all: one emission of the episode-0 start state
         const int emissions = p.reset_all ? 1 : steps;
-        const bool rnd = kLean || act_mode == NX_ACT_RANDOM;
+        const bool rnd = kLeanRandom || act_mode == NX_ACT_RANDOM;
         const uint32_t n_act = family == NX_DYNOBS ? 3u : 7u;
         uint32_t slot = call0 % (uint32_t)depth;
         // this env's row of the output ring (slot * n_envs + local), advanced
@@ -683,9 +683,16 @@ int occupancy_t(int threads, int smem, int* err)
 // not size the tensor memory a kernel allocates at run time), while the
 // launch itself fits as many blocks as the resources allow; a block whose
 // allocation found the columns taken would wait for them, never fail.
-inline int policy_occupancy(int threads, int smem, int* err)
+template <int FAM>
+int launch_policy_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
 {
-    auto k = nx_step_kernel<1, false, false, true>;
+    return launch_t<1, false, false, true, FAM>(p, grid, smem, st);
+}
+
+template <int FAM = -1>
+int policy_occupancy(int threads, int smem, int* err)
+{
+    auto k = nx_step_kernel<1, false, false, true, FAM>;
     int dev = 0, optin = 0, smem_sm = 0, reserved = 0, regs_sm = 0, threads_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -739,5 +746,23 @@ inline int policy_occupancy(int threads, int smem, int* err)
     default: return -1;                                                     \
     }
 static_assert(NX_N_FAMILIES == 11, "NX_DISPATCH_FAM lists every family, then any family (11)");
+
+// The lean fused-policy instantiations, by family.
+#define NX_DISPATCH_POL_FAM(FAM_, FN, ...)                             \
+    switch (FAM_) {                                                    \
+    case 0: return FN<0>(__VA_ARGS__);                                 \
+    case 1: return FN<1>(__VA_ARGS__);                                 \
+    case 2: return FN<2>(__VA_ARGS__);                                 \
+    case 3: return FN<3>(__VA_ARGS__);                                 \
+    case 4: return FN<4>(__VA_ARGS__);                                 \
+    case 5: return FN<5>(__VA_ARGS__);                                 \
+    case 6: return FN<6>(__VA_ARGS__);                                 \
+    case 7: return FN<7>(__VA_ARGS__);                                 \
+    case 8: return FN<8>(__VA_ARGS__);                                 \
+    case 9: return FN<9>(__VA_ARGS__);                                 \
+    case 10: return FN<10>(__VA_ARGS__);                               \
+    case 11: return FN<11>(__VA_ARGS__);                               \
+    default: return -1;                                                \
+    }
 
 }  // namespace nxk
