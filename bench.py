@@ -116,7 +116,7 @@ def measured_tensor_peak():
 # the files that define the step kernels (host-side files do not change a
 # captured kernel)
 KERNEL_SOURCES = ("nx_device.cuh", "nx_internal.h", "nx_kernels.cu", "nx_kernels_full.cu", "nx_lean_g1.cu", "nx_lean_g4.cu",
-                  "nx_lean_g8.cu", "nx_lean_g16.cu", "nx_lean_g32.cu", "nx_policy.cuh", "nx_step.cuh")
+                  "nx_lean_g8.cu", "nx_lean_g16.cu", "nx_lean_g32.cu", "nx_lean_pol.cu", "nx_policy.cuh", "nx_step.cuh")
 
 
 def kernel_source_hash():
