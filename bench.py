@@ -127,9 +127,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel sources changed since."""
+def profile_field(workload, key):
+    """A machine-read field of the committed ncu summary of the step kernel on
+    this workload, or None when the summary is missing or the kernel sources
+    changed since it was captured."""
     p = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
     if not os.path.exists(p):
         return None
@@ -138,13 +139,19 @@ def ncu_traffic(workload):
         for line in f:
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
-                vals[k.strip()] = v.strip().strip("`")
+                v = v.strip()
+                vals[k.strip()] = v[1:].split("`", 1)[0] if v.startswith("`") else v  # the quoted value
     if vals.get("kernel_source_hash") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_full_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def ncu_traffic(workload):
+    """Per-launch DRAM bytes of the step kernel (ncu), or None."""
+    return profile_field(workload, "dram_bytes_per_full_launch")
 
 
 class ClockSampler:
@@ -479,9 +486,22 @@ def main():
     launches_per_rollout = -(-w["T"] // C)
     traffic = ncu_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_src,
+                "traffic": traffic, "peak_source": peak_src, "issue": None,
                 "algorithmic_bytes_per_launch": per_rollout_bytes / launches_per_rollout,
                 "kernel_ms_per_launch": kernel_ms / max(k_launches, 1), "kernel": "nx_step_kernel"}
+
+    # issue rate beside the HBM fraction: the symbolic configs are bound by
+    # their instruction chain; warp-instructions per env-step come from the
+    # committed ncu capture, the peak is one warp-instruction per cycle per
+    # scheduler (4 per SM) at the SM clock sampled during the timed region
+    ipe = profile_field(args.workload, "warp_instructions_per_env_step")
+    issue = None
+    if ipe is not None and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_ips = sms * 4 * clk["sm_mhz"] * 1e6
+        issue = {"warp_instructions_per_env_step": ipe, "achieved": value / world * ipe, "peak": peak_ips,
+                 "unit": "warp-instructions/s", "frac": value / world * ipe / peak_ips,
+                 "source": "ncu smsp__inst_executed.sum of the committed capture; peak = SMs x 4 x SM clock"}
 
     # end to end through the C ABI with host buffers: host actions in, host outputs back, every step
     e2e = None
@@ -528,7 +548,8 @@ def main():
         "config": {"workload": w["desc"], "n_envs_per_gpu": n, "env_steps_per_bench_step": n * w["T"] * world,
                    "steps_per_launch": C, "launch_shape": {k: env.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas")},
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-        "roofline": roofline, "e2e": e2e, "gpu_launches": all_launches, "clocks": clk, "wall_s": wall,
+        "roofline": dict(roofline, issue=issue), "e2e": e2e, "gpu_launches": all_launches, "clocks": clk,
+        "wall_s": wall,
     }
     env.close()
     del out
