@@ -45,11 +45,14 @@ ALL_FAMILIES = [(O.EMPTY, 5, 0), (O.EMPTY, 8, 0), (O.EMPTY, 16, 0), (O.DOORKEY, 
                 (O.KEYCORRIDOR, 16, 2), (O.KEYCORRIDOR, 19, 1)]
 
 
+@pytest.mark.parametrize("lanes,envs", [(0, 0), (16, 4)])
 @pytest.mark.parametrize("family,size,variant", ALL_FAMILIES)
-def test_reset_matches_oracle(family, size, variant):
+def test_reset_matches_oracle(family, size, variant, lanes, envs):
+    """Every generator at every listed size and variant, in the default shape
+    and with 16 lanes per env (grids inside a wall margin)."""
     nx = nxmod()
     n = 37  # ragged against every envs-per-CTA choice
-    env = nx.Env(family, size, n, seed=11, autotune=False, variant=variant)
+    env = nx.Env(family, size, n, seed=11, autotune=False, variant=variant, group_lanes=lanes, envs_per_cta=envs)
     out = env.reset()
     ob = O.Batch([family] * n, [size] * n, seed=11, variants=[variant] * n)
     oo = ob.reset()
@@ -173,18 +176,22 @@ def test_config_rgb_dynobs16_8192envs_512steps():
     env.close()
 
 
-def test_rgb_every_step_small():
+@pytest.mark.parametrize("lanes,envs", [(0, 0), (1, 64), (2, 32), (4, 16), (8, 8), (16, 4), (32, 2)])
+def test_rgb_every_step_small(lanes, envs):
+    """Egocentric RGB tiles and symbolic views every step, at every lane count
+    (0: the library's default shape)."""
     nx = nxmod()
     atlas = inputs.atlas()
     descs = mixed_descs(40, [(O.DYNOBS, 6), (O.DOORKEY, 8), (O.FOURROOMS, 11)])
-    env = nx.Env(descs=descs, seed=21, obs_rgb=True, atlas=atlas, autotune=False, steps_per_launch=16)
+    env = nx.Env(descs=descs, seed=21, obs_rgb=True, atlas=atlas, autotune=False, steps_per_launch=16,
+                 group_lanes=lanes, envs_per_cta=envs)
     r = env.reset()
     out = env.rollout(48)
     ob = oracle_batch_for(descs, 21)
     orr = ob.reset(rgb=True, atlas=atlas)
     oo = ob.rollout(48, rgb=True, atlas=atlas)
     assert_outputs_equal(r, orr, keys=("obs_sym", "obs_rgb"), what="rgb reset")
-    assert_outputs_equal(out, oo, keys=("obs_sym", "obs_rgb", "reward", "terminated", "truncated"), what="rgb")
+    assert_outputs_equal(out, oo, keys=("obs_sym", "obs_rgb", "reward", "terminated", "truncated"), what=f"rgb G={lanes}")
     env.close()
 
 
