@@ -327,10 +327,12 @@ nx_status nx_get_info(const nx_env* env, nx_info* info);
  * requests advance together in each persistent chunk launch, so results do
  * not depend on what else is in flight.
  */
+#define NX_REQ_DIGEST 1u  /* nx_request.flags: compute nx_result.digest (else it is 0) */
+
 typedef struct {
     int32_t family, size, n_envs, horizon;  /* size 5..19, n_envs >= 1, horizon >= 1 */
     int32_t variant;                        /* the family's variant (rivers of a crossing family) */
-    int32_t reserved;
+    uint32_t flags;                         /* NX_REQ_DIGEST or 0; other bits: NX_E_INVAL */
     uint64_t seed;
     /* optional host outputs, written when the request finishes:
      * returns [n_envs] float32 (sum of rewards over the horizon, in step
@@ -342,11 +344,12 @@ typedef struct {
 typedef struct {
     nx_status status;          /* NX_OK when finished */
     double t_submit, t_start, t_done;  /* seconds on the server's steady clock */
-    uint64_t digest;           /* 64-bit digest of every per-step output (see below) */
+    uint64_t digest;           /* 64-bit digest of every per-step output (see below), 0 without NX_REQ_DIGEST */
     uint64_t env_steps;        /* n_envs x horizon */
     uint32_t episodes;         /* episodes that ended (terminated or truncated) */
 } nx_result;
-/* Digest: per env, h = 0; for the reset record and then every step record
+/* Digest (requests with NX_REQ_DIGEST; the folds cost the kernel more than
+ * the step itself): per env, h = 0; for the reset record and then every step record
  * fold the 49 view cells as words (ent | col << 8 | st << 16), the reward's
  * float32 bits and (terminated | truncated << 8), each by
  * h = (h ^ w) * 0x100000001B3 (mod 2^64); the request digest folds the

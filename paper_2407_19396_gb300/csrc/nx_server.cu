@@ -194,7 +194,7 @@ nx_req record_of(const nx_server* s, const SReq& q, int steps)
     r.act_mode = NX_ACT_RANDOM;
     r.obs_sym = base + q.lay.obs;
     r.returns = (float*)(base + q.lay.returns);
-    r.digest = (uint64_t*)(base + q.lay.digest);
+    r.digest = (q.r.flags & NX_REQ_DIGEST) ? (uint64_t*)(base + q.lay.digest) : nullptr;
     r.episodes = (uint32_t*)(base + q.lay.episodes);
     r.reward_mode = (uint32_t)s->opt.reward_mode;
     r.lava_reward = s->opt.lava_reward;
@@ -242,9 +242,12 @@ void retire(nx_server* s, uint64_t t)
     if (q.r.final_obs) memcpy(q.r.final_obs, obs, (size_t)n * NX_OBS_SYM_BYTES);
     uint64_t d = 0;
     uint32_t e = 0;
+    const bool with_digest = (q.r.flags & NX_REQ_DIGEST) != 0;
     for (int i = 0; i < n; ++i) {
-        d = fold(d, (uint32_t)dig[i]);
-        d = fold(d, (uint32_t)(dig[i] >> 32));
+        if (with_digest) {
+            d = fold(d, (uint32_t)dig[i]);
+            d = fold(d, (uint32_t)(dig[i] >> 32));
+        }
         e += eps[i];
     }
     lk.lock();
@@ -505,9 +508,11 @@ nx_status nx_submit(nx_server* s, const nx_request* r, uint64_t* ticket)
 {
     if (!s || !r || !ticket) return nx_fail(nullptr, NX_E_INVAL, "NULL argument");
     if (r->family < NX_EMPTY || r->family >= NX_N_FAMILIES || r->size < NX_MIN_SIZE || r->size > NX_MAX_SIZE ||
-        r->n_envs < 1 || r->horizon < 1 || r->variant < 0 || r->variant > nx_max_variant(r->family, r->size))
+        r->n_envs < 1 || r->horizon < 1 || r->variant < 0 || r->variant > nx_max_variant(r->family, r->size) ||
+        (r->flags & ~NX_REQ_DIGEST) != 0)
         return nx_fail(nullptr, NX_E_INVAL,
-                       "request: known family, size 5..19, n_envs >= 1, horizon >= 1, variant <= nx_max_variant");
+                       "request: known family, size 5..19, n_envs >= 1, horizon >= 1, variant <= nx_max_variant, "
+                       "flags NX_REQ_DIGEST or 0");
     SReq q;
     q.r = *r;
     q.max_steps = nx_default_max_steps(r->family, r->size);

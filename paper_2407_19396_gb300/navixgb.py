@@ -23,6 +23,7 @@ NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET,
 (NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS, NX_EMPTY_RANDOM, NX_LAVA_CROSSING, NX_SIMPLE_CROSSING,
  NX_GOTODOOR, NX_DISTSHIFT, NX_KEYCORRIDOR) = range(11)
 NX_N_FAMILIES = 11
+NX_REQ_DIGEST = 1
 NX_NO_MISSION = 255
 NX_OBS_SYM, NX_OBS_RGB, NX_OBS_RGB_FULL = 1, 2, 4
 NX_ACT_BUFFER, NX_ACT_RANDOM, NX_ACT_POLICY = 0, 1, 2
@@ -83,7 +84,7 @@ class nx_info(ctypes.Structure):
 
 class nx_request(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("size", ctypes.c_int32), ("n_envs", ctypes.c_int32),
-                ("horizon", ctypes.c_int32), ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("horizon", ctypes.c_int32), ("variant", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("returns", ctypes.c_void_p), ("final_obs", ctypes.c_void_p)]
 
 
@@ -602,11 +603,12 @@ class Server:
         self.h = nx_server_create(budget_bytes, o, stream)
         self._bufs = {}
 
-    def submit(self, family, size, n_envs, horizon, seed, variant=0):
+    def submit(self, family, size, n_envs, horizon, seed, variant=0, digest=True):
+        """digest: also compute the request's digest of every per-step output."""
         ret = np.zeros(n_envs, np.float32)
         obs = np.zeros((n_envs, 7, 7, 3), np.uint8)
-        r = nx_request(int(family), int(size), int(n_envs), int(horizon), int(variant), 0, int(seed), ret.ctypes.data,
-                       obs.ctypes.data)
+        r = nx_request(int(family), int(size), int(n_envs), int(horizon), int(variant),
+                       NX_REQ_DIGEST if digest else 0, int(seed), ret.ctypes.data, obs.ctypes.data)
         t = nx_submit(self.h, r)
         self._bufs[t] = (ret, obs)
         return t

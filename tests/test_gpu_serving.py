@@ -64,6 +64,24 @@ def test_results_same_alone_in_the_mix_and_in_the_oracle():
         _same(m, oracle_request(r[0], r[1], r[2], r[3], r[4]))
 
 
+def test_digest_is_optional_and_changes_nothing_else():
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    reqs = _mix(11, 8, max_envs=200, max_h=200)
+    srv = nx.Server(budget_bytes=256 << 20, steps_per_launch=32)
+    with_d = [srv.wait(srv.submit(*r), timeout_s=120.0) for r in reqs]
+    without = [srv.wait(srv.submit(*r, digest=False), timeout_s=120.0) for r in reqs]
+    for r, a, b in zip(reqs, with_d, without):
+        np.testing.assert_array_equal(a["returns"], b["returns"])
+        np.testing.assert_array_equal(a["final_obs"], b["final_obs"])
+        assert a["episodes"] == b["episodes"] and b["digest"] == 0
+        assert a["digest"] == oracle_request(r[0], r[1], r[2], r[3], r[4])["digest"]
+    with pytest.raises(nx.NavixError):
+        bad = nx.nx_request(0, 5, 1, 1, 0, 2, 1, 0, 0)  # an unknown flag bit
+        nx.nx_submit(srv.h, bad)
+    srv.close()
+
+
 def test_requests_arriving_while_others_run_are_admitted_and_correct():
     from paper_2407_19396_gb300 import navixgb as nx
     import time
