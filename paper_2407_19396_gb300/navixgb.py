@@ -583,11 +583,12 @@ class Server:
 
     def __init__(self, budget_bytes=1 << 30, steps_per_launch=128, group_lanes=0, envs_per_cta=0,
                  reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, action_cost=0.0, time_cost=0.0,
-                 stream=None):
+                 stream=None, staging=0):
         o = nx_options_default()
         o.steps_per_launch = steps_per_launch
         o.group_lanes = group_lanes
         o.envs_per_cta = envs_per_cta
+        o.staging = staging
         o.reward_mode = reward_mode
         o.lava_reward = lava_reward
         o.action_cost = action_cost
