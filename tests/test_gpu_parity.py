@@ -318,6 +318,15 @@ def test_host_buffer_rollout_equals_device_rollout():
     assert_outputs_equal(hc, ob.rollout(T, actions=acts), what="host rollout, buffered actions")
     for e in (a, b, c):
         e.close()
+    # one family: host rollouts with random actions run that family's lean kernel
+    d = nx.Env(O.DOORKEY, 8, 100, seed=29, autotune=False, group_lanes=16, envs_per_cta=4, steps_per_launch=32)
+    assert d.info()["lean_family"] == O.DOORKEY
+    d.reset()
+    hd = d.rollout_host(T)
+    od = O.Batch([O.DOORKEY] * 100, [8] * 100, seed=29)
+    od.reset()
+    assert_outputs_equal(hd, od.rollout(T), what="host rollout, one family, random actions")
+    d.close()
 
 
 @pytest.mark.parametrize("reward_mode,lava", [(1, 0.0), (0, -1.0), (1, -1.0)])
