@@ -322,6 +322,42 @@ def test_full_views_agree_with_the_grid_and_the_egocentric_view(family, size, se
                         assert tuple(v) == (2, 5, 0)
 
 
+def test_egocentric_rgb_assembles_the_atlas_tiles_of_the_symbolic_view(atlas):
+    """rgb_first_person (Table 4): each 32x32 block (vx, vy) of the oracle's
+    224x224 view is the atlas tile of that view cell's symbolic triple: the
+    unseen tile where the triple is (0, 0, 0), the agent-cell tile of what the
+    agent carries (or of an empty cell) at (3, 6), the plain tile elsewhere;
+    on the reset and on every step."""
+    from paper_2407_19396_gb300 import inputs
+
+    index = {atlas[k].tobytes(): k for k in range(atlas.shape[0])}
+    fams, sizes = [O.DOORKEY, O.DYNOBS, O.FOURROOMS, O.LAVAGAP], [8, 6, 9, 7]
+    b = O.Batch(fams, sizes, seed=9)
+
+    def check(o):
+        for i in range(len(fams)):
+            for vy in range(7):
+                for vx in range(7):
+                    blk = o["obs_rgb"][i, 32 * vy:32 * vy + 32, 32 * vx:32 * vx + 32]
+                    tile = index[np.ascontiguousarray(blk).tobytes()]
+                    vis, agent, e, c, st = inputs.tile_params(tile)
+                    tri = tuple(int(v) for v in o["obs_sym"][i, vy, vx])
+                    if (vx, vy) == (3, 6):
+                        assert vis == 1 and agent == 1 and (e, c, st) == tri
+                    elif tri == (0, 0, 0):
+                        assert tile == 0
+                    else:
+                        assert vis == 1 and agent == 0 and (e, c, st) == tri
+
+    check(b.reset(rgb=True, atlas=atlas))
+    carried = 0
+    for _ in range(60):
+        o = b.step(rgb=True, atlas=atlas)
+        check(o)
+        carried += int((o["obs_sym"][:, 6, 3, 0] != 1).sum())
+    assert carried > 0  # some step shows a carried object in the agent's cell
+
+
 def test_full_rgb_view_assembles_the_atlas_tiles_of_the_full_symbolic_view(atlas):
     """rgb (Table 4): each 32x32 block of the oracle's full RGB view is the atlas
     tile the atlas module assigns to that cell's triple (the agent's cell: the
