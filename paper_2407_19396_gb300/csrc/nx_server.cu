@@ -132,6 +132,7 @@ struct nx_server {
     int sm_count = 0;
     nx_launch_shape shape{1, 128, 0, 2};  // measured best for the serving mix
     int cell_stride = 0, per_sm = 0, chunk = 128;
+    int per_sm_lean = 0;  // the lean kernel for several families (chunks without a digest), 0: none
     int max_slots = 4096;
     size_t max_items = 0;
 
@@ -325,17 +326,20 @@ bool iterate(nx_server* s, int& cur, bool* idle)
     // race with nx_submit's insertions: take the pointers under the lock
     std::vector<const SReq*> fresh_q, finishing_q;
     int launch_steps = 0;
+    bool digest_reset = false, digest_step = false;  // some request of the launch wants its digest
     {
         std::lock_guard<std::mutex> lk(s->mu);
         for (uint64_t t : fresh) {
             fresh_q.push_back(&s->reqs.at(t));
             items_of(s, *fresh_q.back(), reset_items);
+            digest_reset |= (fresh_q.back()->r.flags & NX_REQ_DIGEST) != 0;
         }
         for (uint64_t t : s->active) {
             SReq& q = s->reqs.at(t);
             const int k = std::min(s->chunk, q.r.horizon - q.launched);
             hr[q.slot] = record_of(s, q, k);
             items_of(s, q, step_items);
+            digest_step |= (q.r.flags & NX_REQ_DIGEST) != 0;
             launch_steps = std::max(launch_steps, k);
             q.launched += k;
             if (q.launched >= q.r.horizon) {
@@ -368,7 +372,19 @@ bool iterate(nx_server* s, int& cur, bool* idle)
     p.cell_stride = s->cell_stride;
     p.envs_per_cta = s->shape.envs_per_cta;
     p.phases = s->shape.phases;
-    const int max_grid = s->per_sm * s->sm_count;
+    // launches whose requests want no digest run the lean kernel (random
+    // actions, no action output, the server's Markov reward, any family)
+    auto shape_of = [&](bool digest, int n, int* grid) {
+        nx_launch_shape sh = s->shape;
+        int per_sm = s->per_sm;
+        if (!digest && s->per_sm_lean > 0) {
+            sh.lean_family = NX_N_FAMILIES;
+            per_sm = s->per_sm_lean;
+        }
+        *grid = std::min(n, per_sm * s->sm_count);
+        return sh;
+    };
+    int grid = 0;
     if (nr) {
         for (const SReq* qp : fresh_q) {
             const SReq& q = *qp;
@@ -379,7 +395,8 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         p.n_items = (int)nr;
         p.reset_all = 1;
         p.launch_steps = 0;
-        int rc = nx_launch_step_kernel(s->shape, p, std::min((int)nr, max_grid), s->stream);
+        const nx_launch_shape sh = shape_of(digest_reset, (int)nr, &grid);
+        int rc = nx_launch_step_kernel(sh, p, grid, s->stream);
         if (rc) SRV_CK((cudaError_t)rc, "reset launch");
     }
     if (ns) {
@@ -387,7 +404,8 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         p.n_items = (int)ns;
         p.reset_all = 0;
         p.launch_steps = launch_steps;
-        int rc = nx_launch_step_kernel(s->shape, p, std::min((int)ns, max_grid), s->stream);
+        const nx_launch_shape sh = shape_of(digest_step, (int)ns, &grid);
+        int rc = nx_launch_step_kernel(sh, p, grid, s->stream);
         if (rc) SRV_CK((cudaError_t)rc, "step launch");
     }
     for (const SReq* qp : finishing_q) {
@@ -472,6 +490,16 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
     if (err || s->per_sm < 1) {
         delete s;
         return nx_fail(nullptr, NX_E_CUDA, "occupancy query failed");
+    }
+    {
+        nx_launch_shape ls = s->shape;
+        ls.lean_family = NX_N_FAMILIES;
+        if (nx_lean_supported(ls) && o.reward_mode == NX_REWARD_MARKOV) {
+            int lerr = 0;
+            const int n = nx_kernel_max_ctas(ls, NX_MAX_SIZE, &lerr);
+            if (lerr) cudaGetLastError();
+            s->per_sm_lean = (!lerr && n >= 1) ? n : 0;  // else every chunk runs the general kernel
+        }
     }
     // the smallest request (1 env of 5x5) needs about 1.8 KB: bound the work list by that
     s->max_items = std::min<size_t>(budget / 1536 + 1, (size_t)1 << 20);
