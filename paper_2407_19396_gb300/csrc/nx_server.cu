@@ -133,6 +133,14 @@ struct nx_server {
     nx_launch_shape shape{1, 128, 0, 2};  // measured best for the serving mix
     int cell_stride = 0, per_sm = 0, chunk = 128;
     int per_sm_lean = 0;  // the lean kernel for several families (chunks without a digest), 0: none
+    // Requests of at most small_envs envs run with 16 lanes per env on a second
+    // stream, beside the one-lane launch of the larger ones: at one lane per
+    // env a small request's step is one long dependent chain (about 9 us),
+    // which would set the floor of every chunk.  0: one shape for all.
+    nx_launch_shape small{16, 8, 0, 1};
+    int small_envs = 0, cell_stride_small = 0, per_sm_small = 0, per_sm_small_lean = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     int max_slots = 4096;
     size_t max_items = 0;
 
@@ -206,9 +214,15 @@ nx_req record_of(const nx_server* s, const SReq& q, int steps)
     return r;
 }
 
+// The launch shape of a request's work items.
+const nx_launch_shape& shape_of_req(const nx_server* s, const nx_request& r)
+{
+    return r.n_envs <= s->small_envs ? s->small : s->shape;
+}
+
 void items_of(const nx_server* s, const SReq& q, std::vector<nx_item>& out)
 {
-    const int E = s->shape.envs_per_cta, n = q.r.n_envs, S = q.r.size;
+    const int E = shape_of_req(s, q.r).envs_per_cta, n = q.r.n_envs, S = q.r.size;
     const uint32_t agent0 = (uint32_t)((q.dev_off + q.lay.agents) / sizeof(nx_agent));
     for (int b = 0; b < n; b += E) {
         nx_item it;
@@ -320,26 +334,30 @@ bool iterate(nx_server* s, int& cur, bool* idle)
     if (!wait_chunk(s, c)) return false;  // normally retired already by the previous iteration
     nx_req* hr = s->h_reqs[cur];
     nx_item* hi = s->h_items[cur];
-    std::vector<nx_item> reset_items, step_items;
+    std::vector<nx_item> reset_items, step_items, reset_small, step_small;
     std::vector<uint64_t> finishing, still;
     // element addresses of the request map never move, but lookups must not
     // race with nx_submit's insertions: take the pointers under the lock
     std::vector<const SReq*> fresh_q, finishing_q;
     int launch_steps = 0;
     bool digest_reset = false, digest_step = false;  // some request of the launch wants its digest
+    bool digest_reset_s = false, digest_step_s = false;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         for (uint64_t t : fresh) {
             fresh_q.push_back(&s->reqs.at(t));
-            items_of(s, *fresh_q.back(), reset_items);
-            digest_reset |= (fresh_q.back()->r.flags & NX_REQ_DIGEST) != 0;
+            const nx_request& r = fresh_q.back()->r;
+            const bool sm = r.n_envs <= s->small_envs;
+            items_of(s, *fresh_q.back(), sm ? reset_small : reset_items);
+            (sm ? digest_reset_s : digest_reset) |= (r.flags & NX_REQ_DIGEST) != 0;
         }
         for (uint64_t t : s->active) {
             SReq& q = s->reqs.at(t);
             const int k = std::min(s->chunk, q.r.horizon - q.launched);
             hr[q.slot] = record_of(s, q, k);
-            items_of(s, q, step_items);
-            digest_step |= (q.r.flags & NX_REQ_DIGEST) != 0;
+            const bool sm = q.r.n_envs <= s->small_envs;
+            items_of(s, q, sm ? step_small : step_items);
+            (sm ? digest_step_s : digest_step) |= (q.r.flags & NX_REQ_DIGEST) != 0;
             launch_steps = std::max(launch_steps, k);
             q.launched += k;
             if (q.launched >= q.r.horizon) {
@@ -352,15 +370,18 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         s->active = still;
         s->stats.chunks += 1;
     }
-    const size_t nr = reset_items.size(), ns = step_items.size();
-    if (nr + ns > 2 * s->max_items) {
+    const size_t nr = reset_items.size(), ns = step_items.size(), nrs = reset_small.size(), nss = step_small.size();
+    if (nr + ns + nrs + nss > 2 * s->max_items) {
         set_fatal(s, NX_E_INVAL, "work list larger than the server's capacity");
         return false;
     }
     memcpy(hi, reset_items.data(), nr * sizeof(nx_item));
     memcpy(hi + nr, step_items.data(), ns * sizeof(nx_item));
+    memcpy(hi + nr + ns, reset_small.data(), nrs * sizeof(nx_item));
+    memcpy(hi + nr + ns + nrs, step_small.data(), nss * sizeof(nx_item));
     nx_item* di = s->d_items + (size_t)cur * 2 * s->max_items;
-    SRV_CK(cudaMemcpyAsync(di, hi, (nr + ns) * sizeof(nx_item), cudaMemcpyHostToDevice, s->stream), "item upload");
+    SRV_CK(cudaMemcpyAsync(di, hi, (nr + ns + nrs + nss) * sizeof(nx_item), cudaMemcpyHostToDevice, s->stream),
+           "item upload");
     SRV_CK(cudaMemcpyAsync(s->d_reqs, hr, sizeof(nx_req) * (size_t)s->max_slots, cudaMemcpyHostToDevice, s->stream),
            "record upload");
     nx_kparams p;
@@ -374,28 +395,57 @@ bool iterate(nx_server* s, int& cur, bool* idle)
     p.phases = s->shape.phases;
     // launches whose requests want no digest run the lean kernel (random
     // actions, no action output, the server's Markov reward, any family)
-    auto shape_of = [&](bool digest, int n, int* grid) {
-        nx_launch_shape sh = s->shape;
-        int per_sm = s->per_sm;
-        if (!digest && s->per_sm_lean > 0) {
+    auto shape_of = [&](bool small, bool digest, int n, int* grid) {
+        nx_launch_shape sh = small ? s->small : s->shape;
+        int per_sm = small ? s->per_sm_small : s->per_sm;
+        const int per_sm_lean = small ? s->per_sm_small_lean : s->per_sm_lean;
+        if (!digest && per_sm_lean > 0) {
             sh.lean_family = NX_N_FAMILIES;
-            per_sm = s->per_sm_lean;
+            per_sm = per_sm_lean;
         }
         *grid = std::min(n, per_sm * s->sm_count);
         return sh;
     };
     int grid = 0;
-    if (nr) {
-        for (const SReq* qp : fresh_q) {
-            const SReq& q = *qp;
-            SRV_CK(cudaMemsetAsync(s->d_pool + q.dev_off + q.lay.returns, 0, q.lay.obs - q.lay.returns, s->stream),
-                   "accumulator clear");
+    for (const SReq* qp : fresh_q) {
+        const SReq& q = *qp;
+        SRV_CK(cudaMemsetAsync(s->d_pool + q.dev_off + q.lay.returns, 0, q.lay.obs - q.lay.returns, s->stream),
+               "accumulator clear");
+    }
+    if (nrs + nss) {
+        // the small requests' launches on the side stream, after the uploads
+        SRV_CK(cudaEventRecord(s->fork_ev, s->stream), "fork");
+        SRV_CK(cudaStreamWaitEvent(s->side, s->fork_ev, 0), "fork");
+        nx_kparams ps = p;
+        ps.cell_stride = s->cell_stride_small;
+        ps.envs_per_cta = s->small.envs_per_cta;
+        ps.phases = s->small.phases;
+        if (nrs) {
+            ps.items = di + nr + ns;
+            ps.n_items = (int)nrs;
+            ps.reset_all = 1;
+            ps.launch_steps = 0;
+            const nx_launch_shape sh = shape_of(true, digest_reset_s, (int)nrs, &grid);
+            int rc = nx_launch_step_kernel(sh, ps, grid, s->side);
+            if (rc) SRV_CK((cudaError_t)rc, "reset launch");
         }
+        if (nss) {
+            ps.items = di + nr + ns + nrs;
+            ps.n_items = (int)nss;
+            ps.reset_all = 0;
+            ps.launch_steps = launch_steps;
+            const nx_launch_shape sh = shape_of(true, digest_step_s, (int)nss, &grid);
+            int rc = nx_launch_step_kernel(sh, ps, grid, s->side);
+            if (rc) SRV_CK((cudaError_t)rc, "step launch");
+        }
+        SRV_CK(cudaEventRecord(s->join_ev, s->side), "join");
+    }
+    if (nr) {
         p.items = di;
         p.n_items = (int)nr;
         p.reset_all = 1;
         p.launch_steps = 0;
-        const nx_launch_shape sh = shape_of(digest_reset, (int)nr, &grid);
+        const nx_launch_shape sh = shape_of(false, digest_reset, (int)nr, &grid);
         int rc = nx_launch_step_kernel(sh, p, grid, s->stream);
         if (rc) SRV_CK((cudaError_t)rc, "reset launch");
     }
@@ -404,10 +454,11 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         p.n_items = (int)ns;
         p.reset_all = 0;
         p.launch_steps = launch_steps;
-        const nx_launch_shape sh = shape_of(digest_step, (int)ns, &grid);
+        const nx_launch_shape sh = shape_of(false, digest_step, (int)ns, &grid);
         int rc = nx_launch_step_kernel(sh, p, grid, s->stream);
         if (rc) SRV_CK((cudaError_t)rc, "step launch");
     }
+    if (nrs + nss) SRV_CK(cudaStreamWaitEvent(s->stream, s->join_ev, 0), "join");
     for (const SReq* qp : finishing_q) {
         const SReq& q = *qp;
         SRV_CK(cudaMemcpyAsync(s->h_pool + q.host_off, s->d_pool + q.dev_off + q.lay.returns, q.lay.tail,
@@ -501,6 +552,27 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
             s->per_sm_lean = (!lerr && n >= 1) ? n : 0;  // else every chunk runs the general kernel
         }
     }
+    if (!o.group_lanes) {
+        // the small requests' shape, on its own stream (none if it cannot run)
+        int serr = 0;
+        s->cell_stride_small = nx_slot_stride(s->small, NX_MAX_SIZE);
+        s->per_sm_small = nx_kernel_max_ctas(s->small, NX_MAX_SIZE, &serr);
+        if (!serr && s->per_sm_small >= 1) {
+            nx_launch_shape ls = s->small;
+            ls.lean_family = NX_N_FAMILIES;
+            if (o.reward_mode == NX_REWARD_MARKOV) {
+                const int n = nx_kernel_max_ctas(ls, NX_MAX_SIZE, &serr);
+                s->per_sm_small_lean = (!serr && n >= 1) ? n : 0;
+                serr = 0;
+            }
+        }
+        if (!serr && s->per_sm_small >= 1 &&
+            cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming) == cudaSuccess)
+            s->small_envs = 64;
+        cudaGetLastError();
+    }
     // the smallest request (1 env of 5x5) needs about 1.8 KB: bound the work list by that
     s->max_items = std::min<size_t>(budget / 1536 + 1, (size_t)1 << 20);
     const size_t host_cap = budget / 4 + (1u << 20);  // result staging: returns, digests, episodes, final views
@@ -549,7 +621,8 @@ nx_status nx_submit(nx_server* s, const nx_request* r, uint64_t* ticket)
     if (s->fatal != NX_OK) return nx_fail(nullptr, s->fatal, s->fatal_msg);
     if (s->stop) return nx_fail(nullptr, NX_E_STATE, "server is shutting down");
     if (up256(q.lay.total) > s->budget || up256(q.lay.tail) > s->host_alloc.cap ||
-        (size_t)((r->n_envs + s->shape.envs_per_cta - 1) / s->shape.envs_per_cta) * 2 > s->max_items) {
+        (size_t)((r->n_envs + shape_of_req(s, *r).envs_per_cta - 1) / shape_of_req(s, *r).envs_per_cta) * 2 >
+            s->max_items) {
         s->stats.rejected += 1;
         return nx_fail(nullptr, NX_E_BUDGET, "request needs " + std::to_string(q.lay.total) +
                                                  " bytes, more than the whole budget of " + std::to_string(s->budget));
@@ -623,6 +696,10 @@ void nx_server_destroy(nx_server* s)
         s->worker.join();
     }
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->side) cudaStreamSynchronize(s->side);
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+    if (s->join_ev) cudaEventDestroy(s->join_ev);
     for (int b = 0; b < 2; ++b) {
         if (s->chunks[b].ev) cudaEventDestroy(s->chunks[b].ev);
         if (s->h_reqs[b]) cudaFreeHost(s->h_reqs[b]);
