@@ -75,6 +75,26 @@ def test_many_more_envs_than_resident_ctas():
     env.close()
 
 
+def test_paper_batch_scale_sampled():
+    """The paper's batch-mode scale: Empty-8x8, 2^21 envs (autotuned shape,
+    the lean kernel), a 1-slot output ring; after 40 steps the last step's
+    outputs of sampled envs equal the oracle's."""
+    nx = nxmod()
+    n, T = 1 << 21, 40
+    env = nx.Env(O.EMPTY, 8, n, seed=6)
+    env.reset()
+    out = env.rollout(T, depth=1)
+    sample = sorted(set([0, 1, 31, 32, n // 2, n - 33, n - 1] + list(range(777, n, 65537))))
+    idx = torch.tensor(sample, device="cuda")
+    got = {k: out[k].index_select(1, idx).cpu().numpy() for k in ("obs_sym", "reward", "terminated", "truncated")}
+    ob = O.Batch([O.EMPTY] * len(sample), [8] * len(sample), seed=6, env_indices=sample)
+    ob.reset()
+    oo = ob.rollout(T)
+    want = {k: oo[k][T - 1:] for k in ("obs_sym", "reward", "terminated", "truncated")}
+    assert_outputs_equal(got, want, what="2^21 envs, last step")
+    env.close()
+
+
 def test_reset_twice_restarts_everything():
     nx = nxmod()
     env = nx.Env(O.FOURROOMS, 11, 50, seed=3, autotune=False)

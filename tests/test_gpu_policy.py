@@ -71,6 +71,33 @@ def test_policy_rollout_matches_the_oracle(parts, A, epa, eps, T):
     env.close()
 
 
+def test_policy_workload_full_size_sampled():
+    """The benchmark's policy workload at full size -- Empty-8x8, 32,768 envs =
+    256 agents x 128 envs, the seeded weights, shifts 3 and 6, exploration
+    1/16 -- for 200 steps; envs sampled across the agents (first, last and
+    interior ones) against the oracle, every step."""
+    from paper_2407_19396_gb300 import inputs
+
+    nx = nxmod()
+    n, A, epa, T = 32768, 256, 128, 200
+    pw = inputs.policy_weights(5, A)
+    env = nx.Env(O.EMPTY, 8, n, seed=5, action=True)
+    env.set_policy(pw["w1"], pw["b1"], pw["w2"], pw["b2"], pw["w3"], pw["b3"], 3, 6, 1 << 28, epa)
+    env.reset()
+    out = env.rollout(T, policy=True)
+    sample = sorted(set([0, 1, 127, 128, 255, 16383, 16384, n - 129, n - 2, n - 1] + list(range(300, n, 1031))))
+    idx = torch.tensor(sample, device="cuda")
+    got = {k: out[k].index_select(1, idx).cpu().numpy() for k in KEYS}
+    pol = O.Policy(**pw, shift1=3, shift2=6, epsilon=1 << 28, envs_per_agent=epa)
+    ob = O.Batch([O.EMPTY] * len(sample), [8] * len(sample), seed=5, env_indices=sample)
+    ob.reset()
+    oo = ob.rollout_policy(T, pol)
+    oo["action"] = oo.pop("actions")
+    assert_outputs_equal(got, oo, keys=KEYS, what="policy workload, sampled")
+    assert env.flags() & 4 == 0
+    env.close()
+
+
 def test_hand_built_policy_on_the_gpu():
     nx = nxmod()
     pol = wall_turner()
