@@ -51,6 +51,14 @@ def test_status_strings_and_creation_errors_without_gpu(built):
         with pytest.raises(nx.NavixError) as ei:
             nx.nx_create(fam, size, n, 0)
         assert ei.value.status == nx.NX_E_INVAL
+    # mixed descriptors: the 16-bit step counter's limit, variants beyond the
+    # family's range, sizes outside 5..19 (one bad descriptor among good ones)
+    good = (nx.NX_DOORKEY, 8, 0, 0)
+    for bad in [(nx.NX_EMPTY, 5, 65536, 0), (nx.NX_LAVA_CROSSING, 9, 0, 99), (nx.NX_DISTSHIFT, 7, 0, 2),
+                (nx.NX_EMPTY, 21, 0, 0), (nx.NX_DOORKEY, 8, 0, -1)]:
+        with pytest.raises(nx.NavixError) as ei:
+            nx.nx_create_mixed([good, bad, good], 0)
+        assert ei.value.status == nx.NX_E_INVAL, bad
 
 
 def test_product_binding_does_not_import_the_oracle():

@@ -95,6 +95,27 @@ def test_paper_batch_scale_sampled():
     env.close()
 
 
+@pytest.mark.parametrize("lanes,envs", [(1, 64), (16, 4)])
+def test_tiny_max_steps_truncate_every_few_steps(lanes, envs):
+    """max_steps 1, 2 and 3 (a truncation on every step or every few, so an
+    autoreset every other call) beside a long horizon, several families, and
+    one family alone (its lean kernel); every step against the oracle."""
+    nx = nxmod()
+    descs = mixed_descs(60, [(O.DOORKEY, 8, 1), (O.FOURROOMS, 9, 2), (O.DYNOBS, 6, 3), (O.LAVAGAP, 7, 1000),
+                             (O.KEYCORRIDOR, 7, 2, 1)])
+    for d in (descs, [(O.DOORKEY, 8, 2)] * 37):
+        env = nx.Env(descs=d, seed=44, group_lanes=lanes, envs_per_cta=envs, autotune=False, steps_per_launch=16)
+        env.reset()
+        out = env.rollout(100)
+        ob = oracle_batch_for(d, 44)
+        ob.reset()
+        oo = ob.rollout(100)
+        assert_outputs_equal(out, oo, what=f"tiny max_steps G={lanes}")
+        assert_states_equal(env.state()["envs"], ob, what=f"tiny max_steps G={lanes}")
+        assert oo["truncated"].sum() > 0
+        env.close()
+
+
 def test_reset_twice_restarts_everything():
     nx = nxmod()
     env = nx.Env(O.FOURROOMS, 11, 50, seed=3, autotune=False)
