@@ -440,10 +440,11 @@ static nx_status prof_mark(nx_env* env, bool begin)
 
 // The fused-policy launch shape: 1 lane per env, 128 envs per block; its lean
 // instantiation (the context's family or any family) with the Markov reward.
-static nx_launch_shape policy_shape(const nx_env* env)
+static nx_launch_shape policy_shape(const nx_env* env, int agents)
 {
     nx_launch_shape ps{1, nxp::kRows, 0, 1, 0, false, true};
     if (env->lean_family >= 0 && env->req_host.reward_mode == NX_REWARD_MARKOV) ps.lean_family = env->lean_family;
+    ps.policy_agents = agents;
     return ps;
 }
 
@@ -477,7 +478,7 @@ static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid
                            bool lean = false)
 {
     if (policy) {
-        *s = policy_shape(env);
+        *s = policy_shape(env, env->policy_agents);
         *grid = std::min(env->n_items_pol, env->per_sm_pol * env->sm_count);
         return NX_OK;
     }
@@ -509,6 +510,7 @@ static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full
         p.n_items = env->n_items_pol;
         p.envs_per_cta = nxp::kRows;
         p.cell_stride = nx_slot_stride(s, env->max_side);
+        p.policy_agents = env->policy_agents;
         p.phases = 1;
         p.rgb_full_side = 0;
     }
@@ -739,13 +741,17 @@ nx_status nx_set_policy(nx_env* env, const nx_policy* pol)
     };
     if (!bias_ok(pol->b1, (size_t)A * 64) || !bias_ok(pol->b2, (size_t)A * 64) || !bias_ok(pol->b3, (size_t)A * 7))
         return nx_fail(env, NX_E_INVAL, "biases must lie in [-2^22, 2^22]");
+    // a block of 128 envs holds one weight set, or 128 / envs_per_agent of them
+    if (epa < (uint64_t)nxp::kRows && (epa < 16 || nxp::kRows % epa != 0))
+        return nx_fail(env, NX_E_INVAL, "envs_per_agent must be 16, 32, 64 or at least 128");
+    const int agents = epa < (uint64_t)nxp::kRows ? (int)(nxp::kRows / epa) : 1;
     std::vector<nx_item> items = nx_build_items(env, nxp::kRows);
     for (const nx_item& it : items) {
         const uint64_t first = base + it.local_begin, last = first + it.n_envs - 1;
-        if (first / epa != last / epa)
+        if (epa >= (uint64_t)nxp::kRows ? first / epa != last / epa : first % epa != 0)
             return nx_fail(env, NX_E_INVAL, "a weight set boundary splits a 128-env block of the work list");
     }
-    const nx_launch_shape ps = policy_shape(env);
+    const nx_launch_shape ps = policy_shape(env, agents);
     int err = 0;
     const int per_sm = nx_kernel_max_ctas(ps, env->max_side, &err);
     if (err) return nx_cuda_fail(env, err, "occupancy query");
@@ -795,6 +801,7 @@ nx_status nx_set_policy(nx_env* env, const nx_policy* pol)
                                cudaMemcpyHostToDevice, env->stream), "policy work list upload");
     env->n_items_pol = (int)env->items_pol.size();
     env->per_sm_pol = per_sm;
+    env->policy_agents = agents;
     env->policy_epa = (uint32_t)epa;
     env->policy_shift1 = pol->shift1;
     env->policy_shift2 = pol->shift2;
@@ -1129,7 +1136,7 @@ nx_status nx_get_info(const nx_env* env, nx_info* info)
     info->state_bytes = nx_state_bytes(env);
     info->device_bytes = env->device_bytes;
     if (env->d_policy) {
-        const nx_launch_shape ps = policy_shape(env);
+        const nx_launch_shape ps = policy_shape(env, env->policy_agents);
         info->policy_items = env->n_items_pol;
         info->policy_ctas_per_sm = env->per_sm_pol;
         info->policy_grid_ctas = std::min(env->n_items_pol, env->per_sm_pol * env->sm_count);

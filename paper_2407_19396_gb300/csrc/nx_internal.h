@@ -106,7 +106,7 @@ struct nx_kparams {
     int32_t reset_all;     // 1: start every env at episode 0 and emit its observation (no steps)
     int32_t phases;        // symbolic staging parts per step (1 or 2)
     int32_t rgb_full_side; // side of the smem full-view tile buffer (0: none)
-    int32_t pad;
+    int32_t policy_agents; // fused policy: weight sets per 128-env block (1, 2, 4 or 8)
 };
 
 // Host-side launch helpers implemented in nx_kernels.cu.
@@ -119,6 +119,7 @@ struct nx_launch_shape {
     bool full = false;      // the instantiation that writes the fully observable views
     bool policy = false;    // the fused-policy instantiation (1 lane, 128 envs per CTA)
     int lean_family = -1;   // >= 0: the lean instantiation for this family, NX_N_FAMILIES: any family
+    int policy_agents = 1;  // the fused policy's weight sets per block (shared memory, tensor memory)
 };
 // Shared-memory bytes per env grid for grids of up to max_cells cells: a
 // whole number of 4-byte words, and an odd one, so that the grids of the 32
@@ -162,6 +163,6 @@ NX_LEAN_DECL(8)
 NX_LEAN_DECL(16)
 NX_LEAN_DECL(32)
 #undef NX_LEAN_DECL
-int nx_lean_pol_occupancy(int family, int threads, int smem, int* err);
+int nx_lean_pol_occupancy(int family, int threads, int smem, int agents, int* err);
 int nx_lean_pol_launch(int family, const nx_kparams& p, int grid, int smem, cudaStream_t st);
 #endif

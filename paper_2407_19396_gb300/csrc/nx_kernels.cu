@@ -64,7 +64,7 @@ static int smem_for_stride(const nx_launch_shape& s, int cell_stride)
     const int grid_bytes = align16(s.group_lanes == 1 ? E * cell_stride + 2 * kGridGuard : E * cell_stride);
     int b = grid_bytes + warps * align16(whalf * NX_OBS_SYM_BYTES + 16);
     if (s.policy) b = policy_smem_offset(grid_bytes, warps * align16(whalf * NX_OBS_SYM_BYTES + 16)) +
-                      nxp::kATileBytes + nxp::kImageBytes;
+                      nxp::kATileBytes + s.policy_agents * nxp::kImageBytes;
     if (s.rgb) b += align16(E * 49 * 2) + align16(E * s.rgb_full_side * s.rgb_full_side * 2);
     return b;
 }
@@ -80,8 +80,8 @@ int nx_kernel_max_ctas(const nx_launch_shape& s, int max_side, int* err)
     const int threads = s.envs_per_cta * s.group_lanes;
     if (s.full) return nx_kernel_max_ctas_full(s, threads, smem, err);
     if (s.policy)
-        return s.lean_family >= 0 ? nx_lean_pol_occupancy(s.lean_family, threads, smem, err)
-                                  : policy_occupancy(threads, smem, err);
+        return s.lean_family >= 0 ? nx_lean_pol_occupancy(s.lean_family, threads, smem, s.policy_agents, err)
+                                  : policy_occupancy(threads, smem, s.policy_agents, err);
     if (s.lean_family >= 0) {
         if (!nx_lean_supported(s)) return -1;
         switch (s.group_lanes) {

@@ -10,9 +10,9 @@
 
 using namespace nxk;
 
-int nx_lean_pol_occupancy(int family, int threads, int smem, int* err)
+int nx_lean_pol_occupancy(int family, int threads, int smem, int agents, int* err)
 {
-    NX_DISPATCH_POL_FAM(family, policy_occupancy, threads, smem, err)
+    NX_DISPATCH_POL_FAM(family, policy_occupancy, threads, smem, agents, err)
 }
 
 int nx_lean_pol_launch(int family, const nx_kparams& p, int grid, int smem, cudaStream_t st)

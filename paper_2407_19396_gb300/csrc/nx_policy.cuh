@@ -17,7 +17,11 @@
 // four tcgen05.mma (K = 16 each) against the layer's weights (the B operand,
 // N x K) with the accumulator in tensor memory and commits them to an
 // mbarrier; every thread waits (bounded), reads its row back with
-// tcgen05.ld, requantises and writes the next layer's A row.
+// tcgen05.ld, requantises and writes the next layer's A row.  With fewer than
+// 128 envs per weight set (16, 32 or 64) a block holds the images of its
+// 8, 4 or 2 weight sets: each layer runs one MMA group per set over all 128
+// rows into that set's own 64 tensor-memory columns (one commit), and each
+// row reads the columns of its own set.
 //
 // Shared-memory operand layout (no swizzle, K-major): 8 x 16-byte core
 // matrices; element (r, k) of a tile lives at
@@ -184,11 +188,12 @@ __device__ __forceinline__ float pow2_neg(int sh) { return __int_as_float((127 -
 
 // All 128 threads of the block: after every thread wrote its input row, the
 // first layer's MMA is issued (it then runs while the block does other work).
-__device__ __forceinline__ void policy_issue_first(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar)
+__device__ __forceinline__ void policy_issue_first(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar,
+                                                   int agents)
 {
     sync_for_mma();
     if (threadIdx.x == 0) {
-        mma_k64(tmem, sA, sW + kW1, idesc_bf16(kRows, kK));
+        for (int a = 0; a < agents; ++a) mma_k64(tmem + 64u * a, sA, sW + a * kImageBytes + kW1, idesc_bf16(kRows, kK));
         mma_commit(mbar);
     }
 }
@@ -196,17 +201,26 @@ __device__ __forceinline__ void policy_issue_first(uint8_t* sA, const uint8_t* s
 // All 128 threads of the block, after policy_issue_first: the greedy action
 // of this thread's row (rows of inactive threads are computed and ignored).
 // `phase` tracks the mbarrier's parity; `ok` turns false if a wait gave up.
+// `agents` weight sets of `epa` envs each in this block (one set of every row
+// when epa >= 128).
 __device__ __forceinline__ int policy_finish(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar,
-                                             uint32_t& phase, int n_act, int shift1, int shift2, bool& ok)
+                                             uint32_t& phase, int n_act, int shift1, int shift2, bool& ok, int agents,
+                                             int epa)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
+    // this row's weight set, and the sets of the warp's rows (one, or two for
+    // 16 envs per set); each is below 128 / epa, inside the allocated columns
+    const int mine = epa < kRows ? tid / epa : 0;
+    const int first = epa < kRows ? (32 * warp) / epa : 0, per_warp = epa < 32 ? 32 / epa : 1;
+    const uint8_t* myW = sW + mine * kImageBytes;
 #pragma unroll 1
     for (int layer = 0; layer < 2; ++layer) {
         if (layer == 1) {
             sync_for_mma();
             if (tid == 0) {
-                mma_k64(tmem, sA, sW + kW2, idesc_bf16(kRows, kK));
+                for (int a = 0; a < agents; ++a)
+                    mma_k64(tmem + 64u * a, sA, sW + a * kImageBytes + kW2, idesc_bf16(kRows, kK));
                 mma_commit(mbar);
             }
         }
@@ -214,27 +228,38 @@ __device__ __forceinline__ int policy_finish(uint8_t* sA, const uint8_t* sW, uin
         phase ^= 1u;
         __syncwarp();  // tcgen05.ld is warp-collective: converge after the per-thread wait
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const float* bs = reinterpret_cast<const float*>(sW + (layer ? kB2 : kB1));
+        const float* bs = reinterpret_cast<const float*>(myW + (layer ? kB2 : kB1));
         const float scale = pow2_neg(layer ? shift2 : shift1);
 #pragma unroll 1
         for (int c0 = 0; c0 < kK; c0 += 16) {
-            uint32_t v[16];
-            tmem_ld16(trow + (uint32_t)c0, v);
-            requant_row16(sA, tid, c0, v, bs + c0, scale);
+#pragma unroll 1
+            for (int j = 0; j < per_warp; ++j) {
+                uint32_t v[16];
+                tmem_ld16(trow + 64u * (uint32_t)(first + j) + (uint32_t)c0, v);
+                if (mine == first + j) requant_row16(sA, tid, c0, v, bs + c0, scale);
+            }
         }
     }
     sync_for_mma();
     if (tid == 0) {
-        mma_k64(tmem, sA, sW + kW3, idesc_bf16(kRows, 16));
+        for (int a = 0; a < agents; ++a) mma_k64(tmem + 64u * a, sA, sW + a * kImageBytes + kW3, idesc_bf16(kRows, 16));
         mma_commit(mbar);
     }
     ok = mbar_wait(mbar, phase) && ok;
     phase ^= 1u;
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    uint32_t v[16];
-    tmem_ld16(trow, v);
-    const int32_t* b3 = reinterpret_cast<const int32_t*>(sW + kB3);
+    uint32_t v[16] = {};
+#pragma unroll 1
+    for (int j = 0; j < per_warp; ++j) {
+        uint32_t w[16];
+        tmem_ld16(trow + 64u * (uint32_t)(first + j), w);
+        if (mine == first + j) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = w[i];
+        }
+    }
+    const int32_t* b3 = reinterpret_cast<const int32_t*>(myW + kB3);
     int best = 0, bz = __float2int_rn(__uint_as_float(v[0])) + b3[0];
 #pragma unroll
     for (int a = 1; a < 7; ++a) {

@@ -59,6 +59,7 @@ struct nx_env {
     int per_sm_full = 0;  // resident CTAs of the instantiation with the fully observable views
     int lean_family = -1;  // lean step kernels: the one family of every env, or NX_N_FAMILIES (several)
     mutable int per_sm_lean = 0;  // resident CTAs of the lean instantiation (cache; 0: not queried, -1: none)
+    int policy_agents = 1;        // the fused policy's weight sets per 128-env block
     std::vector<int> fam_begin;
     bool tuned = false;
     std::vector<nx_tune_entry> tune_log;

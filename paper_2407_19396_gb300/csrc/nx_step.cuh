@@ -278,10 +278,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     uint8_t* sW = sA + nxp::kATileBytes;
     uint32_t tmem = 0, phase = 0;
     bool pol_ok = true;
+    int pol_agents = 1;  // fused policy: weight sets of the current item
     if constexpr (POL) {
         // 64 tensor-memory columns: the 128 x 64 f32 accumulator of a layer
         if (warp == 0) {
-            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(nxp::smem_u32(&s_tmem)));
+            // 64 columns per weight set of the block (a power of two, <= 512)
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(nxp::smem_u32(&s_tmem)),
+                         "r"(64u * (uint32_t)p.policy_agents));
             asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         }
         if (tid == 0) {
@@ -368,9 +371,14 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 
         if constexpr (POL) {
             // the item's weight set, and every env's current view as its input row
-            const uint32_t agent = (rq->key_base + item.local_begin) / rq->policy_epa;
+            // the weight sets of the item's envs (one, or with fewer than 128
+            // envs per set those of each aligned group of envs_per_agent)
+            const uint32_t epa = rq->policy_epa;
+            const uint32_t agent = (rq->key_base + item.local_begin) / epa;
+            pol_agents = epa < (uint32_t)nxp::kRows ? (int)((item.n_envs + epa - 1) / epa) : 1;
             const uint4* src = reinterpret_cast<const uint4*>(rq->policy + (size_t)agent * nxp::kImageBytes);
-            for (int i = tid; i < nxp::kImageBytes / 16; i += nthreads) reinterpret_cast<uint4*>(sW)[i] = src[i];
+            for (int i = tid; i < pol_agents * (nxp::kImageBytes / 16); i += nthreads)
+                reinterpret_cast<uint4*>(sW)[i] = src[i];
             if (active) {
                 ViewOut<G> v0;
                 render_view(grp, mygrid, S, W, a, s_dec, nullptr, v0, nullptr);
@@ -378,7 +386,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             } else {
                 nxp::store_zero_row(sA, tid);
             }
-            if (steps > 0) nxp::policy_issue_first(sA, sW, tmem, &s_mbar);
+            if (steps > 0) nxp::policy_issue_first(sA, sW, tmem, &s_mbar, pol_agents);
         }
 
         // steps == 0 with reset_all: one emission of the episode-0 start state
@@ -398,7 +406,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             int term = 0, trunc = 0;
             int pol_act = 0;  // fused policy: the greedy action of every env (all threads take part)
             if constexpr (POL)
-                pol_act = nxp::policy_finish(sA, sW, tmem, &s_mbar, phase, (int)n_act, rq->shift1, rq->shift2, pol_ok);
+                pol_act = nxp::policy_finish(sA, sW, tmem, &s_mbar, phase, (int)n_act, rq->shift1, rq->shift2, pol_ok,
+                                             pol_agents, (int)rq->policy_epa);
             if (G > 1 && rnd && (s % G) == 0) {
                 // the random actions of the next G steps depend only on the step
                 // counter, so the group's lanes draw them in parallel
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             }
             // fused policy: the next step's first layer runs during the stores
             if constexpr (POL)
-                if (s + 1 < emissions) nxp::policy_issue_first(sA, sW, tmem, &s_mbar);
+                if (s + 1 < emissions) nxp::policy_issue_first(sA, sW, tmem, &s_mbar, pol_agents);
             // Groups of 8 or more lanes (at most 4 envs per warp) write each
             // cell's three bytes straight to global memory (measured faster
             // than staging there); the staged path serves the narrow groups
@@ -637,7 +646,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64u * (uint32_t)p.policy_agents));
         if (!pol_ok) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_WAIT_TIMEOUT);
     }
 }
@@ -679,7 +689,7 @@ int occupancy_t(int threads, int smem, int* err)
 
 // Resident blocks per SM of the fused-policy instantiation, from its shared
 // memory, registers and threads and the SM's 512 tensor-memory columns (64
-// per block).  The occupancy API reports one block for this kernel (it does
+// per weight set of a block).  The occupancy API reports one block for this kernel (it does
 // not size the tensor memory a kernel allocates at run time), while the
 // launch itself fits as many blocks as the resources allow; a block whose
 // allocation found the columns taken would wait for them, never fail.
@@ -690,7 +700,7 @@ int launch_policy_t(const nx_kparams& p, int grid, int smem, cudaStream_t st)
 }
 
 template <int FAM = -1>
-int policy_occupancy(int threads, int smem, int* err)
+int policy_occupancy(int threads, int smem, int agents, int* err)
 {
     auto k = nx_step_kernel<1, false, false, true, FAM>;
     int dev = 0, optin = 0, smem_sm = 0, reserved = 0, regs_sm = 0, threads_sm = 0;
@@ -713,7 +723,7 @@ int policy_occupancy(int threads, int smem, int* err)
     int n = smem_sm / (smem + (int)fa.sharedSizeBytes + reserved);
     n = std::min(n, regs_sm / std::max(regs_block, 1));
     n = std::min(n, threads_sm / threads);
-    n = std::min(n, 512 / 64);
+    n = std::min(n, 512 / (64 * std::max(agents, 1)));
     return std::max(n, 0);
 }
 

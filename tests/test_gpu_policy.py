@@ -51,6 +51,11 @@ KEYS = ("obs_sym", "reward", "terminated", "truncated", "action")
     ([(O.DYNOBS, 6)], 1, 256, 2**30, 260),
     ([(O.EMPTY, 5), (O.FOURROOMS, 11)], 4, 128, 2**28, 300),
     ([(O.KEYCORRIDOR, 10, 0, 2), (O.LAVA_CROSSING, 9, 0, 2)], 2, 256, 0, 200),
+    # several weight sets per 128-env block: the PPO pattern of many agents x 16 envs
+    ([(O.DOORKEY, 8)], 16, 16, 0, 200),
+    ([(O.EMPTY, 5), (O.FOURROOMS, 11)], 8, 32, 2**28, 200),
+    ([(O.DYNOBS, 6)], 4, 64, 0, 200),
+    ([(O.EMPTY, 6)], 11, 16, 2**30, 150),  # a ragged last block: 176 envs, 3 of 8 sets in it
 ])
 def test_policy_rollout_matches_the_oracle(parts, A, epa, eps, T):
     nx = nxmod()
@@ -146,6 +151,20 @@ def test_policy_validation():
     env = nx.Env(descs=[(O.DOORKEY, 6)] * 100 + [(O.EMPTY, 6)] * 156, seed=0, autotune=False)
     with pytest.raises(nx.NavixError) as ei:
         env.set_policy(pol.w1, pol.b1, pol.w2, pol.b2, pol.w3, pol.b3, 3, 6, 0, 128)
+    assert ei.value.status == nx.NX_E_INVAL
+    env.close()
+    # envs per weight set below 128 must divide the block and be >= 16, and the
+    # blocks must start at a weight-set boundary
+    p16 = random_policy(16, seed=2, epa=16)
+    env = nx.Env(O.DOORKEY, 6, 256, seed=0, autotune=False)
+    for epa in (8, 48, 100):
+        with pytest.raises(nx.NavixError) as ei:
+            env.set_policy(p16.w1, p16.b1, p16.w2, p16.b2, p16.w3, p16.b3, 3, 6, 0, epa)
+        assert ei.value.status == nx.NX_E_INVAL
+    env.close()
+    env = nx.Env(descs=[(O.DOORKEY, 6)] * 40 + [(O.EMPTY, 6)] * 216, seed=0, autotune=False)
+    with pytest.raises(nx.NavixError) as ei:
+        env.set_policy(p16.w1, p16.b1, p16.w2, p16.b2, p16.w3, p16.b3, 3, 6, 0, 16)  # a block starts at env 40
     assert ei.value.status == nx.NX_E_INVAL
     env.close()
     env = nx.Env(O.DOORKEY, 6, 256, seed=0, autotune=False)
