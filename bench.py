@@ -56,6 +56,10 @@ WORKLOADS = {
                         "agent's integer MLP policy on the tensor cores (categorical first-person view -> 64 -> 64 "
                         "-> 7, seeded int8 weights), exploration 1/16, symbolic obs",
                    parts=[(0, 8)], n=32768, T=1000, seed=5, rgb=False, depth=128, policy=True, agents=256),
+    "policy_paper": dict(desc="Empty-8x8, 32,768 envs = 2048 agents x 16 envs (the paper's PPO batch) x 1000 steps, "
+                              "seed 5, actions from each agent's integer MLP policy on the tensor cores (8 weight sets "
+                              "per 128-env block), exploration 1/16, symbolic obs",
+                         parts=[(0, 8)], n=32768, T=1000, seed=5, rgb=False, depth=128, policy=True, agents=2048),
     # the paper's own batch-mode scale: 2^21 envs of Empty-8x8 unrolled for
     # 1000 steps (its reported wall time: almost always below 1 s on an A100)
     "paper_scale": dict(desc="Empty-8x8, 2,097,152 envs x 1000 steps, seed 6, uniform random actions over 7, "
@@ -597,26 +601,31 @@ def main():
                                  "workload": wx["desc"]}
         ex.close()
         del ox
-        # the fused policy rollout, beside the random-action rollout of the same envs
-        wx = WORKLOADS["policy"]
-        dx = descs_of(wx)
-        ex = nx.Env(descs=dx, seed=wx["seed"])
-        ex.reset()
-        set_bench_policy(ex, wx)
-        ox = ex.alloc_out(wx["depth"])
-        ms, kms, kl, _ = time_rollouts(ex, wx, ox, 2, 1, flush, policy=True)
-        ms_r, _, _, _ = time_rollouts(ex, wx, ox, 2, 1, flush)
-        rate = len(dx) * wx["T"] * len(ms) / (sum(ms) / 1000)
-        kern_rate = len(dx) * wx["T"] * len(ms) / (kms / 1000)
-        tf = kern_rate * POLICY_FLOPS / 1e12
-        tpeak, tsrc = measured_tensor_peak()
-        extras["policy"] = {"env_steps_per_s": rate, "random_action_env_steps_per_s":
-                            len(dx) * wx["T"] * len(ms_r) / (sum(ms_r) / 1000),
-                            "tensor_tflops": tf, "tensor_frac": tf / tpeak, "tensor_peak": tpeak,
-                            "tensor_peak_source": tsrc, "tensor_flops_per_env_step": POLICY_FLOPS,
-                            "workload": wx["desc"]}
-        ex.close()
-        del ox
+        # the fused policy rollouts (256 agents x 128 envs, and the paper's
+        # 2048 agents x 16 envs), beside the random-action rollout of the same envs
+        for key in ("policy", "policy_paper"):
+            wx = WORKLOADS[key]
+            dx = descs_of(wx)
+            ex = nx.Env(descs=dx, seed=wx["seed"])
+            ex.reset()
+            set_bench_policy(ex, wx)
+            ox = ex.alloc_out(wx["depth"])
+            ms, kms, kl, _ = time_rollouts(ex, wx, ox, 2, 1, flush, policy=True)
+            ms_r, _, _, _ = time_rollouts(ex, wx, ox, 2, 1, flush)
+            rate = len(dx) * wx["T"] * len(ms) / (sum(ms) / 1000)
+            kern_rate = len(dx) * wx["T"] * len(ms) / (kms / 1000)
+            tf = kern_rate * POLICY_FLOPS / 1e12
+            tpeak, tsrc = measured_tensor_peak()
+            extras[key] = {"env_steps_per_s": rate, "random_action_env_steps_per_s":
+                           len(dx) * wx["T"] * len(ms_r) / (sum(ms_r) / 1000),
+                           "tensor_tflops": tf, "tensor_frac": tf / tpeak, "tensor_peak": tpeak,
+                           "tensor_peak_source": tsrc, "tensor_flops_per_env_step": POLICY_FLOPS,
+                           "envs_per_agent": len(dx) // wx["agents"],
+                           # each weight set's MMA spans its block's 128 rows
+                           "tensor_flops_issued_per_env_step": POLICY_FLOPS * max(1, 128 // (len(dx) // wx["agents"])),
+                           "workload": wx["desc"]}
+            ex.close()
+            del ox
         line["extras"] = extras
     if rank == 0 and world == 1 and not args.no_extras:
         line.setdefault("extras", {})["serving"] = run_serving()

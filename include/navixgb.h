@@ -265,9 +265,11 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
  * e / envs_per_agent.  Host arrays: w1 [n_agents][64][49], b1 [n_agents][64],
  * w2 [n_agents][64][64], b2 [n_agents][64], w3 [n_agents][7][64],
  * b3 [n_agents][7]; |bias| <= 2^22, shifts 0..24.  The policy runs 128 envs
- * per thread block, so a weight set must cover whole aligned blocks of 128
- * envs of the context's work list (NX_E_INVAL otherwise); it copies the
- * weights to the device (the host arrays may be freed on return). */
+ * per thread block: envs_per_agent is 16, 32 or 64 (each block then holds
+ * 8, 4 or 2 weight sets, and every block of the context's work list must
+ * start at a weight-set boundary) or at least 128 (a weight set must cover
+ * whole blocks); NX_E_INVAL otherwise.  The weights are copied to the device
+ * (the host arrays may be freed on return). */
 typedef struct {
     int32_t n_agents, envs_per_agent;
     const int8_t* w1;

@@ -443,7 +443,9 @@ static nx_status prof_mark(nx_env* env, bool begin)
 static nx_launch_shape policy_shape(const nx_env* env, int agents)
 {
     nx_launch_shape ps{1, nxp::kRows, 0, 1, 0, false, true};
-    if (env->lean_family >= 0 && env->req_host.reward_mode == NX_REWARD_MARKOV) ps.lean_family = env->lean_family;
+    // the lean instantiations hold one weight set per block
+    if (agents == 1 && env->lean_family >= 0 && env->req_host.reward_mode == NX_REWARD_MARKOV)
+        ps.lean_family = env->lean_family;
     ps.policy_agents = agents;
     return ps;
 }

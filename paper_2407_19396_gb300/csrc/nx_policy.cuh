@@ -188,31 +188,47 @@ __device__ __forceinline__ float pow2_neg(int sh) { return __int_as_float((127 -
 
 // All 128 threads of the block: after every thread wrote its input row, the
 // first layer's MMA is issued (it then runs while the block does other work).
+// MULTI: the block may hold several weight sets (`agents`), else one.
+template <bool MULTI>
 __device__ __forceinline__ void policy_issue_first(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar,
                                                    int agents)
 {
     sync_for_mma();
     if (threadIdx.x == 0) {
-        for (int a = 0; a < agents; ++a) mma_k64(tmem + 64u * a, sA, sW + a * kImageBytes + kW1, idesc_bf16(kRows, kK));
+        if constexpr (MULTI) {
+            for (int a = 0; a < agents; ++a)
+                mma_k64(tmem + 64u * a, sA, sW + a * kImageBytes + kW1, idesc_bf16(kRows, kK));
+        } else {
+            mma_k64(tmem, sA, sW + kW1, idesc_bf16(kRows, kK));
+        }
         mma_commit(mbar);
     }
 }
 
-// All 128 threads of the block, after policy_issue_first: the greedy action
-// of this thread's row (rows of inactive threads are computed and ignored).
-// `phase` tracks the mbarrier's parity; `ok` turns false if a wait gave up.
-// `agents` weight sets of `epa` envs each in this block (one set of every row
-// when epa >= 128).
+// The weight sets of a block's rows (computed once per work item): the
+// block's sets, this row's set, and the sets of this warp's rows (first, and
+// one or two of them) -- each below 128 / envs_per_agent, so inside the
+// allocated tensor-memory columns.
+struct PolRows {
+    int agents, mine, first, per_warp;
+};
+__device__ __forceinline__ PolRows pol_rows(int agents, int epa)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (epa >= kRows) return PolRows{1, 0, 0, 1};
+    return PolRows{agents, tid / epa, (32 * warp) / epa, epa < 32 ? 32 / epa : 1};
+}
+
+template <bool MULTI>
 __device__ __forceinline__ int policy_finish(uint8_t* sA, const uint8_t* sW, uint32_t tmem, uint64_t* mbar,
-                                             uint32_t& phase, int n_act, int shift1, int shift2, bool& ok, int agents,
-                                             int epa)
+                                             uint32_t& phase, int n_act, int shift1, int shift2, bool& ok,
+                                             const PolRows& pr)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
-    // this row's weight set, and the sets of the warp's rows (one, or two for
-    // 16 envs per set); each is below 128 / epa, inside the allocated columns
-    const int mine = epa < kRows ? tid / epa : 0;
-    const int first = epa < kRows ? (32 * warp) / epa : 0, per_warp = epa < 32 ? 32 / epa : 1;
+    // (one weight set: the constants of pol_rows for envs_per_agent >= 128)
+    const int agents = MULTI ? pr.agents : 1, mine = MULTI ? pr.mine : 0, first = MULTI ? pr.first : 0,
+              per_warp = MULTI ? pr.per_warp : 1;
     const uint8_t* myW = sW + mine * kImageBytes;
 #pragma unroll 1
     for (int layer = 0; layer < 2; ++layer) {
@@ -230,13 +246,24 @@ __device__ __forceinline__ int policy_finish(uint8_t* sA, const uint8_t* sW, uin
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const float* bs = reinterpret_cast<const float*>(myW + (layer ? kB2 : kB1));
         const float scale = pow2_neg(layer ? shift2 : shift1);
+        if (per_warp == 1) {
+            // every row of the warp has the warp's set
+            const uint32_t tcol = trow + 64u * (uint32_t)first;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kK; c0 += 16) {
-#pragma unroll 1
-            for (int j = 0; j < per_warp; ++j) {
+            for (int c0 = 0; c0 < kK; c0 += 16) {
                 uint32_t v[16];
-                tmem_ld16(trow + 64u * (uint32_t)(first + j) + (uint32_t)c0, v);
-                if (mine == first + j) requant_row16(sA, tid, c0, v, bs + c0, scale);
+                tmem_ld16(tcol + (uint32_t)c0, v);
+                requant_row16(sA, tid, c0, v, bs + c0, scale);
+            }
+        } else {
+#pragma unroll 1
+            for (int c0 = 0; c0 < kK; c0 += 16) {
+#pragma unroll 1
+                for (int j = 0; j < per_warp; ++j) {
+                    uint32_t v[16];
+                    tmem_ld16(trow + 64u * (uint32_t)(first + j) + (uint32_t)c0, v);
+                    if (mine == first + j) requant_row16(sA, tid, c0, v, bs + c0, scale);
+                }
             }
         }
     }
@@ -250,13 +277,17 @@ __device__ __forceinline__ int policy_finish(uint8_t* sA, const uint8_t* sW, uin
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     uint32_t v[16] = {};
+    if (per_warp == 1) {
+        tmem_ld16(trow + 64u * (uint32_t)first, v);
+    } else {
 #pragma unroll 1
-    for (int j = 0; j < per_warp; ++j) {
-        uint32_t w[16];
-        tmem_ld16(trow + 64u * (uint32_t)(first + j), w);
-        if (mine == first + j) {
+        for (int j = 0; j < per_warp; ++j) {
+            uint32_t w[16];
+            tmem_ld16(trow + 64u * (uint32_t)(first + j), w);
+            if (mine == first + j) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = w[i];
+                for (int i = 0; i < 16; ++i) v[i] = w[i];
+            }
         }
     }
     const int32_t* b3 = reinterpret_cast<const int32_t*>(myW + kB3);

@@ -239,6 +239,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 {
     static_assert(!POL || (G == 1 && !RGB && !FULL), "the fused policy runs one lane per env");
     constexpr bool kLean = FAM >= 0, kLeanRandom = kLean && !POL;
+    // the fused policy with several weight sets per block (fewer than 128 envs
+    // per set) runs in the general instantiation; the lean ones hold one set
+    constexpr bool kMultiPol = POL && !kLean;
     static_assert(!kLean || (!RGB && !FULL && FAM <= NX_N_FAMILIES), "lean: symbolic outputs only");
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_mbar;  // fused policy: MMA completion
@@ -279,6 +282,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     uint32_t tmem = 0, phase = 0;
     bool pol_ok = true;
     int pol_agents = 1;  // fused policy: weight sets of the current item
+    nxp::PolRows pol_rows{1, 0, 0, 1};
     if constexpr (POL) {
         // 64 tensor-memory columns: the 128 x 64 f32 accumulator of a layer
         if (warp == 0) {
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             const uint32_t epa = rq->policy_epa;
             const uint32_t agent = (rq->key_base + item.local_begin) / epa;
             pol_agents = epa < (uint32_t)nxp::kRows ? (int)((item.n_envs + epa - 1) / epa) : 1;
+            pol_rows = nxp::pol_rows(pol_agents, (int)epa);
             const uint4* src = reinterpret_cast<const uint4*>(rq->policy + (size_t)agent * nxp::kImageBytes);
             for (int i = tid; i < pol_agents * (nxp::kImageBytes / 16); i += nthreads)
                 reinterpret_cast<uint4*>(sW)[i] = src[i];
@@ -386,7 +391,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             } else {
                 nxp::store_zero_row(sA, tid);
             }
-            if (steps > 0) nxp::policy_issue_first(sA, sW, tmem, &s_mbar, pol_agents);
+            if (steps > 0) nxp::policy_issue_first<kMultiPol>(sA, sW, tmem, &s_mbar, pol_agents);
         }
 
         // steps == 0 with reset_all: one emission of the episode-0 start state
@@ -406,8 +411,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             int term = 0, trunc = 0;
             int pol_act = 0;  // fused policy: the greedy action of every env (all threads take part)
             if constexpr (POL)
-                pol_act = nxp::policy_finish(sA, sW, tmem, &s_mbar, phase, (int)n_act, rq->shift1, rq->shift2, pol_ok,
-                                             pol_agents, (int)rq->policy_epa);
+                pol_act = nxp::policy_finish<kMultiPol>(sA, sW, tmem, &s_mbar, phase, (int)n_act, rq->shift1,
+                                                        rq->shift2, pol_ok, pol_rows);
             if (G > 1 && rnd && (s % G) == 0) {
                 // the random actions of the next G steps depend only on the step
                 // counter, so the group's lanes draw them in parallel
@@ -526,7 +531,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             }
             // fused policy: the next step's first layer runs during the stores
             if constexpr (POL)
-                if (s + 1 < emissions) nxp::policy_issue_first(sA, sW, tmem, &s_mbar, pol_agents);
+                if (s + 1 < emissions) nxp::policy_issue_first<kMultiPol>(sA, sW, tmem, &s_mbar, pol_agents);
             // Groups of 8 or more lanes (at most 4 envs per warp) write each
             // cell's three bytes straight to global memory (measured faster
             // than staging there); the staged path serves the narrow groups
