@@ -326,8 +326,8 @@ nx_status nx_get_info(const nx_env* env, nx_info* info);
  * nx_reset + nx_rollout(horizon, NX_ACT_RANDOM) would.  Requests that arrive
  * while others run are admitted (strictly first come, first served) as soon
  * as their device memory fits in the server's fixed HBM budget; all admitted
- * requests advance together in each persistent chunk launch, so results do
- * not depend on what else is in flight.
+ * requests advance together in each chunk (one persistent launch per launch
+ * shape), so results do not depend on what else is in flight.
  */
 #define NX_REQ_DIGEST 1u  /* nx_request.flags: compute nx_result.digest (else it is 0) */
 
@@ -366,9 +366,11 @@ typedef struct {
 /* nx_server_create: hbm_budget_bytes (at most 4 GiB) is allocated once, up
  * front, and every admitted request's state and outputs are carved from it.
  * opts: steps_per_launch is the chunk length (latency vs launch overhead),
- * group_lanes / envs_per_cta / staging fix the launch shape (0: 1 lane per
- * env, 128 envs per block, half staging), reward options apply to every
- * request; obs_flags must be NX_OBS_SYM. */
+ * group_lanes / envs_per_cta / staging fix one launch shape for every
+ * request (0: 1 lane per env, 128 envs per block, half staging, with
+ * requests of at most 64 envs run at 16 lanes per env on a second stream
+ * beside them), reward options apply to every request; obs_flags must be
+ * NX_OBS_SYM. */
 nx_status nx_server_create(nx_server** server, size_t hbm_budget_bytes, const nx_options* opts, void* cuda_stream);
 /* nx_submit: queue a request; NX_E_BUDGET if it can never fit the budget,
  * NX_E_INVAL on bad arguments.  The host output buffers must stay valid until
