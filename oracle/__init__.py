@@ -5,6 +5,10 @@ CPU-baseline leg of ``bench.py`` use this module to compute expected values;
 the product package never imports it.  The oracle shares no code with the CUDA
 library: it has its own Philox, layouts, rules, view and visibility, all in
 ``navix_oracle.c``.
+
+``NAVIX_ORACLE_SO`` names another build of the same source to load instead;
+the mutation tests use it to check that the pins catch deliberately planted
+mistakes in a copy of the oracle.
 """
 from __future__ import annotations
 
@@ -67,7 +71,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            L = ctypes.CDLL(os.environ.get("NAVIX_ORACLE_SO") or build())
             P = ctypes.POINTER
             u8p, i8p, f32p, i32p = P(ctypes.c_uint8), P(ctypes.c_int8), P(ctypes.c_float), P(ctypes.c_int32)
             L.orc_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]

@@ -161,3 +161,150 @@ def bfs_goal(start, W, H, max_depth=64, mission=None):
                 parent[n] = (s, a)
                 q.append(n)
     return None
+
+
+# ---------------------------------------------------------------------------
+# Counter-based draws (reading R1), restated with Python integers from the
+# definition of Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds,
+# each two 32x32 -> 64-bit products whose high halves are mixed with the other
+# two words and the round key; the key advances by the Weyl constants.  It
+# shares nothing with the oracle and is pinned by the published known-answer
+# vectors (tests/golden/philox4x32_10_kat.txt).
+_U32 = 0xFFFFFFFF
+_MULT = (0xD2511F53, 0xCD9E8D57)
+_WEYL = (0x9E3779B9, 0xBB67AE85)
+
+
+def philox4x32_10(ctr, key):
+    x = [int(v) & _U32 for v in ctr]
+    k = [int(v) & _U32 for v in key]
+    for _ in range(10):
+        (hi0, lo0), (hi1, lo1) = divmod(_MULT[0] * x[0], 1 << 32), divmod(_MULT[1] * x[2], 1 << 32)
+        x = [hi1 ^ x[1] ^ k[0], lo1, hi0 ^ x[3] ^ k[1], lo0]
+        k = [(k[0] + _WEYL[0]) & _U32, (k[1] + _WEYL[1]) & _U32]
+    return x
+
+
+LAYOUT, BALL, ACTION = 1, 2, 3  # the purposes of reading R1
+
+
+def draw(seed, env, episode, step, purpose, k):
+    """Word 0 at counter (env, episode, step, purpose << 24 | k), key (seed lo, seed hi)."""
+    return philox4x32_10([env, episode, step, (purpose << 24) | k], [seed & _U32, seed >> 32])[0]
+
+
+def bounded(x, n):
+    """floor(x n / 2^32): a draw in [0, n) (reading R1)."""
+    return (int(x) * int(n)) >> 32
+
+
+def random_action(seed, env, gstep, n_actions=7):
+    """Random-action mode: the episode word is all ones, the step word the
+    step count since the reset call (reading R1, purpose 3; R13)."""
+    return bounded(draw(seed, env, 0xFFFFFFFF, gstep, ACTION, 0), n_actions)
+
+
+# ---------------------------------------------------------------------------
+# Layout generators L2, L3, L5 and the ball moves of reading R12, restated on a
+# numpy grid [H, W, 3] of (entity, colour, state).  Free cells of a rectangle
+# are listed by numpy.argwhere, whose order is C order over (y, x): rows
+# outer, columns inner, the row-major order of reading R18.
+GOAL = (8, 1, 0)
+LOCKED_YELLOW_DOOR = (4, 4, 2)
+YELLOW_KEY = (5, 4, 0)
+BLUE_BALL = (6, 2, 0)
+
+
+def walled_grid(S):
+    g = np.zeros((S, S, 3), np.int64)
+    g[:, :] = EMPTY
+    g[0, :] = WALL
+    g[-1, :] = WALL
+    g[:, 0] = WALL
+    g[:, -1] = WALL
+    return g
+
+
+def free_cells(g, x0, x1, y0, y1, skip=None):
+    """Empty cells of [x0, x1] x [y0, y1] as (x, y), rows outer (reading R18)."""
+    sub = g[y0:y1 + 1, x0:x1 + 1]
+    mask = np.all(sub == np.array(EMPTY), axis=2)
+    out = [(int(x0 + c[1]), int(y0 + c[0])) for c in np.argwhere(mask)]
+    return [c for c in out if c != skip]
+
+
+def doorkey_start(S, seed, env, episode):
+    """L2; returns (grid, agent (x, y, dir), wall column, door (x, y), key (x, y), draws)."""
+    d = [draw(seed, env, episode, 0, LAYOUT, k) for k in range(5)]
+    g = walled_grid(S)
+    g[S - 2, S - 2] = GOAL
+    xw = 2 + bounded(d[0], S - 4)
+    g[1:S - 1, xw] = WALL
+    door = (xw, 1 + bounded(d[1], S - 3))
+    g[door[1], door[0]] = LOCKED_YELLOW_DOOR
+    cells = free_cells(g, 1, xw - 1, 1, S - 2)
+    ax, ay = cells[bounded(d[2], len(cells))]
+    adir = bounded(d[3], 4)
+    rest = [c for c in cells if c != (ax, ay)]
+    key = rest[bounded(d[4], len(rest))]
+    g[key[1], key[0]] = YELLOW_KEY
+    return g, (ax, ay, adir), xw, door, key, d
+
+
+def fourrooms_start(S, seed, env, episode):
+    """L3; returns (grid, agent (x, y, dir), goal (x, y), gaps, draws)."""
+    d = [draw(seed, env, episode, 0, LAYOUT, k) for k in range(7)]
+    m = S // 2
+    g = walled_grid(S)
+    g[:, m] = WALL
+    g[m, :] = WALL
+    gaps = [(m, 1 + bounded(d[0], m - 1)), (m, m + 1 + bounded(d[1], S - 2 - m)),
+            (1 + bounded(d[2], m - 1), m), (m + 1 + bounded(d[3], S - 2 - m), m)]
+    for x, y in gaps:
+        g[y, x] = EMPTY
+    cells = free_cells(g, 1, S - 2, 1, S - 2)
+    goal = cells[bounded(d[4], len(cells))]
+    g[goal[1], goal[0]] = GOAL
+    rest = [c for c in cells if c != goal]
+    ax, ay = rest[bounded(d[5], len(rest))]
+    return g, (ax, ay, bounded(d[6], 4)), goal, gaps, d
+
+
+def dynobs_start(S, seed, env, episode, n_balls=4):
+    """L5; returns (grid, balls [(x, y)], draws)."""
+    g = walled_grid(S)
+    g[S - 2, S - 2] = GOAL
+    balls, ds = [], []
+    for b in range(n_balls):
+        cells = free_cells(g, 1, S - 2, 1, S - 2, skip=(1, 1))
+        ds.append(draw(seed, env, episode, 0, LAYOUT, b))
+        x, y = cells[bounded(ds[-1], len(cells))]
+        g[y, x] = BLUE_BALL
+        balls.append((x, y))
+    return g, balls, ds
+
+
+# the 8-neighbourhood in reading R12's candidate order: dy outer, dx inner
+NEIGHBOURS = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0)]
+
+
+def move_balls(g, balls, agent_xy, seed, env, episode, t):
+    """R12: balls in index order, each onto a drawn free neighbour (empty, not
+    the agent's cell) of the grid as the earlier balls left it.  Returns the
+    new positions and, per ball, (candidates, draw)."""
+    H, W = g.shape[:2]
+    balls = list(balls)
+    trace = []
+    for b, (bx, by) in enumerate(balls):
+        cand = [(bx + dx, by + dy) for dx, dy in NEIGHBOURS
+                if 0 <= bx + dx < W and 0 <= by + dy < H and tuple(g[by + dy, bx + dx]) == EMPTY
+                and (bx + dx, by + dy) != tuple(agent_xy)]
+        x = draw(seed, env, episode, t, BALL, b)
+        trace.append((cand, x))
+        if not cand:
+            continue
+        nx_, ny_ = cand[bounded(x, len(cand))]
+        g[by, bx] = EMPTY
+        g[ny_, nx_] = BLUE_BALL
+        balls[b] = (nx_, ny_)
+    return balls, trace

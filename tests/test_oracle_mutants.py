@@ -1,0 +1,68 @@
+"""The draw-to-placement pins catch the plausible misreadings (CPU only).
+
+Each case copies the oracle's C source, plants one mistake, builds the copy
+and runs tests/test_oracle_draw_pins.py against it in a child process
+(``NAVIX_ORACLE_SO``); the pins must fail.  The unmodified copy must pass, so
+a failure is the planted mistake's and not the mechanism's.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "navix_oracle.c")
+
+MUTANTS = {
+    # reading R18 read as "columns outer": the k-th free cell scanned x first
+    "free_cells_column_major": [(
+        "    for (int y = y0; y <= y1; y++)\n        for (int x = x0; x <= x1; x++) {\n"
+        "            if (!is_empty_cell(e, x, y) || (x == skip_x && y == skip_y)) continue;",
+        "    for (int x = x0; x <= x1; x++)\n        for (int y = y0; y <= y1; y++) {\n"
+        "            if (!is_empty_cell(e, x, y) || (x == skip_x && y == skip_y)) continue;")],
+    # reading R12 read as simultaneous moves: every ball sees the grid of the step's start
+    "balls_move_on_a_snapshot": [
+        ("static void move_balls(orc_env* e)\n{\n", "static void move_balls(orc_env* e)\n{\n    orc_env snap = *e;\n"),
+        ("                if (!is_empty_cell(e, x, y)) continue;", "                if (!is_empty_cell(&snap, x, y)) continue;")],
+    # reading R12's candidate order read column first (dx outer)
+    "ball_candidates_dx_outer": [(
+        "        for (int dy = -1; dy <= 1; dy++)\n            for (int dx = -1; dx <= 1; dx++) {",
+        "        for (int dx = -1; dx <= 1; dx++)\n            for (int dy = -1; dy <= 1; dy++) {")],
+    # reading R1's random-action counter with the episode word 0 instead of all ones
+    "action_counter_episode_word": [(
+        "orc_draw(e->seed, e->env_index, 0xFFFFFFFFu, gstep, PURPOSE_ACTION, 0)",
+        "orc_draw(e->seed, e->env_index, 0u, gstep, PURPOSE_ACTION, 0)")],
+}
+
+
+def _build(tmp_path, edits):
+    src = open(SRC).read()
+    for old, new in edits:
+        assert src.count(old) == 1, f"mutation site not found exactly once: {old[:60]!r}"
+        src = src.replace(old, new)
+    c = tmp_path / "navix_oracle.c"
+    c.write_text(src)
+    so = tmp_path / "liboracle_mutant.so"
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-I",
+                    os.path.join(ROOT, "oracle"), "-o", str(so), str(c)], check=True)
+    return str(so)
+
+
+def _run_pins(so):
+    env = dict(os.environ, NAVIX_ORACLE_SO=so)
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_draw_pins.py")],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmodified_copy_passes_the_pins(tmp_path):
+    r = _run_pins(_build(tmp_path, []))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_the_planted_mistake(tmp_path, name):
+    r = _run_pins(_build(tmp_path, MUTANTS[name]))
+    assert r.returncode != 0, f"the pins did not catch {name}"
+    assert "failed" in r.stdout, r.stdout[-2000:]
