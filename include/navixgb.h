@@ -394,20 +394,27 @@ void nx_server_destroy(nx_server* server);
  *
  * It does what nx_create(family, size, n_envs, seed, default options) +
  * nx_reset(NULL) + nx_rollout(n_steps, act_mode, d_actions_TN, traj) do, with
- * identical outputs, but allocates nothing: the state, work list and request
- * record live in one fixed device array of NX_NOALLOC_SCRATCH_BYTES that
- * every GPU loading the library holds until the process exits.  The caller
- * passes the actions (device int8 [n_steps, n_envs], or NULL with
- * NX_ACT_RANDOM) and the outputs (device, [depth, n_envs, ...]; obs_rgb must
- * be NULL).  Enqueued on cuda_stream, asynchronous.
+ * identical obs_sym, reward, terminated and truncated outputs, but allocates
+ * nothing: the state, work list and request record live in one fixed device
+ * array of NX_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits.  The caller passes the actions (device int8
+ * [n_steps, n_envs], or NULL with NX_ACT_RANDOM) and the outputs (device,
+ * [depth, n_envs, ...]).  Only obs_sym, reward, terminated and truncated are
+ * written; every other nx_out pointer must be NULL (NX_E_INVAL otherwise).
+ * Enqueued on cuda_stream, asynchronous.
  *
  * Limit: n_envs x (3 size^2 + 32) bytes plus a small work list must fit the
- * array; larger requests return NX_E_INVAL with the sizes in
- * nx_last_error(NULL).  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call uses the same array and re-initialises what
- * must start from zero, so two calls that overlap on the GPU (different
- * streams, or different host threads) race and corrupt each other. */
+ * array (for example 3757 FourRooms-19x19 envs, or 4096 DoorKey-8x8 envs);
+ * larger requests return NX_E_INVAL with the sizes in nx_last_error(NULL).
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, a host-side lookup); the first call on a device may
+ * load the library's device code, so make that first call before any stream
+ * capture.  Every call uses the same array and re-initialises what must
+ * start from zero, so two calls that overlap on the GPU (different streams,
+ * or different host threads) race and corrupt each other.  The sticky device
+ * flags of nx_device_flags (an out-of-range action, a failed bounds check)
+ * stay inside that array and no call reads them back: with NX_ACT_BUFFER,
+ * pass actions in 0..6, since an out-of-range one runs as a no-op unseen. */
 #define NX_NOALLOC_SCRATCH_BYTES (4u << 20)
 nx_status nx_rollout_noalloc(int32_t family, int32_t size, int32_t n_envs, uint64_t seed, int32_t n_steps,
                              int32_t act_mode, const int8_t* d_actions_TN, const nx_out* traj, void* cuda_stream);

@@ -14,7 +14,6 @@
 #include <stdint.h>
 #include <string.h>
 
-#include <mutex>
 #include <string>
 
 #include "navixgb.h"
@@ -32,9 +31,6 @@ constexpr size_t kItemsOff = 512;
 constexpr int kLanes = 8;
 constexpr int kEnvsPerCta = 32;
 constexpr int kStepsPerLaunch = 128;
-
-std::mutex g_mu;
-uint8_t* g_dev_ptr[64] = {nullptr};  // device address of the array, per device
 
 // Fills the work list (runs of kEnvsPerCta consecutive envs) and clears the
 // flags, so nothing from an earlier call leaks into this one.
@@ -60,22 +56,22 @@ __global__ void nx_noalloc_setup_kernel(uint8_t* scratch, int n_envs, int family
     }
 }
 
-// Device address of the array on the current device, looked up once per
-// device (the first call on each device does this).
+// Device address of the array in the current device's context.  In host
+// code the array's name is only a host-side stand-in, so its device address
+// is looked up, with the device current, on every call: a host-side lookup,
+// and never stale, also after cudaDeviceReset gave the device a new context
+// (and the array possibly a new address).  The first lookup on a device may
+// load the library's device code, which is why the first call on a device
+// must come before any stream capture.
 nx_status device_scratch(uint8_t** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return nx_cuda_fail(nullptr, (int)e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return nx_fail(nullptr, NX_E_INVAL, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return nx_cuda_fail(nullptr, (int)e, "cudaGetSymbolAddress of the scratch array");
-        g_dev_ptr[dev] = (uint8_t*)p;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nx_cuda_fail(nullptr, (int)e, "cudaGetSymbolAddress of the scratch array");
     }
-    *out = g_dev_ptr[dev];
+    *out = (uint8_t*)p;
     return NX_OK;
 }
 
@@ -101,7 +97,10 @@ nx_status nx_rollout_noalloc(int32_t family, int32_t size, int32_t n_envs, uint6
     if (n_steps < 0) return nx_fail(nullptr, NX_E_INVAL, "n_steps must be >= 0");
     if (act_mode != NX_ACT_RANDOM && act_mode != NX_ACT_BUFFER) return nx_fail(nullptr, NX_E_INVAL, "unknown act_mode");
     if (act_mode == NX_ACT_BUFFER && !d_actions_TN) return nx_fail(nullptr, NX_E_INVAL, "NX_ACT_BUFFER needs actions");
-    if (traj && traj->obs_rgb) return nx_fail(nullptr, NX_E_INVAL, "nx_rollout_noalloc has no RGB output");
+    if (traj && (traj->obs_rgb || traj->obs_full || traj->obs_cat || traj->obs_cat_fp || traj->obs_rgb_full ||
+                 traj->mission || traj->action))
+        return nx_fail(nullptr, NX_E_INVAL,
+                       "nx_rollout_noalloc writes obs_sym, reward, terminated and truncated only (the other outputs must be NULL)");
     const size_t need = scratch_needed(size, n_envs);
     if (need > (size_t)NX_NOALLOC_SCRATCH_BYTES) {
         return nx_fail(nullptr, NX_E_INVAL,

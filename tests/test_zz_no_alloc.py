@@ -37,18 +37,28 @@ def _regular(nx, family, size, n, seed, T, actions):
     return out
 
 
-def _noalloc(nx, family, size, n, seed, T, actions):
-    env_like = {"obs_sym": torch.empty((T, n, 7, 7, 3), dtype=torch.uint8, device="cuda"),
-                "reward": torch.empty((T, n), dtype=torch.float32, device="cuda"),
-                "terminated": torch.empty((T, n), dtype=torch.uint8, device="cuda"),
-                "truncated": torch.empty((T, n), dtype=torch.uint8, device="cuda")}
+def _regular_ring(nx, family, size, n, seed, T, actions, depth):
+    env = nx.Env(family, size, n, seed=seed, autotune=False)
+    env.reset()
+    out = env.rollout(T, actions=actions, depth=depth)
+    torch.cuda.synchronize()
+    env.close()
+    return out
+
+
+def _noalloc(nx, family, size, n, seed, T, actions, depth=None):
+    D = depth or T
+    env_like = {"obs_sym": torch.empty((D, n, 7, 7, 3), dtype=torch.uint8, device="cuda"),
+                "reward": torch.empty((D, n), dtype=torch.float32, device="cuda"),
+                "terminated": torch.empty((D, n), dtype=torch.uint8, device="cuda"),
+                "truncated": torch.empty((D, n), dtype=torch.uint8, device="cuda")}
     o = nx.nx_out()
     o.obs_sym = env_like["obs_sym"].data_ptr()
     o.obs_rgb = None
     o.reward = env_like["reward"].data_ptr()
     o.terminated = env_like["terminated"].data_ptr()
     o.truncated = env_like["truncated"].data_ptr()
-    o.depth = T
+    o.depth = D
     mode = nx.NX_ACT_RANDOM if actions is None else nx.NX_ACT_BUFFER
     ptr = None if actions is None else actions.data_ptr()
     nx.nx_rollout_noalloc(family, size, n, seed, T, mode, ptr, o, torch.cuda.current_stream().cuda_stream)
@@ -79,3 +89,50 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         nx.nx_rollout_noalloc(nx.NX_FOURROOMS, 19, 8192, 0, 1, nx.NX_ACT_RANDOM, None, None, 0)
     assert ei.value.status == nx.NX_E_INVAL
     assert "fixed scratch" in str(ei.value)
+
+
+def test_noalloc_at_its_size_limit_and_with_an_output_ring():
+    """3757 FourRooms-19x19 envs fill the scratch array to within a few
+    hundred bytes (3758 no longer fit); a ring shorter than the horizon keeps
+    step i in slot i % depth.  Both equal the regular entry points exactly."""
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    got = _noalloc(nx, nx.NX_FOURROOMS, 19, 3757, 7, 130, None)
+    want = _regular(nx, nx.NX_FOURROOMS, 19, 3757, 7, 130, None)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        assert torch.equal(got[k], want[k]), f"FourRooms-19 at the limit: {k} differs"
+    with pytest.raises(nx.NavixError) as ei:
+        nx.nx_rollout_noalloc(nx.NX_FOURROOMS, 19, 3758, 7, 1, nx.NX_ACT_RANDOM, None, None, 0)
+    assert ei.value.status == nx.NX_E_INVAL and "fixed scratch" in str(ei.value)
+    got = _noalloc(nx, nx.NX_LAVAGAP, 7, 300, 9, 150, None, depth=64)
+    want = _regular_ring(nx, nx.NX_LAVAGAP, 7, 300, 9, 150, None, 64)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        assert torch.equal(got[k], want[k]), f"64-slot ring: {k} differs"
+
+
+def test_noalloc_against_the_oracle_and_degenerate_calls():
+    """The outputs equal the CPU oracle's; a call with no outputs, a call of
+    zero steps and a call asking for an output it does not write behave as
+    documented, and the next call is unaffected."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    s = torch.cuda.current_stream().cuda_stream
+    nx.nx_rollout_noalloc(nx.NX_DOORKEY, 8, 100, 3, 40, nx.NX_ACT_RANDOM, None, None, s)  # no outputs
+    nx.nx_rollout_noalloc(nx.NX_DOORKEY, 8, 100, 3, 0, nx.NX_ACT_RANDOM, None, None, s)  # reset only
+    o = nx.nx_out()
+    extra = torch.empty((4, 37), dtype=torch.uint8, device="cuda")
+    o.mission = extra.data_ptr()
+    o.depth = 4
+    with pytest.raises(nx.NavixError) as ei:
+        nx.nx_rollout_noalloc(nx.NX_DOORKEY, 5, 37, 3, 4, nx.NX_ACT_RANDOM, None, o, s)
+    assert ei.value.status == nx.NX_E_INVAL
+    T = 90
+    got = _noalloc(nx, nx.NX_DOORKEY, 5, 37, 3, T, None)
+    b = O.Batch([O.DOORKEY] * 37, [5] * 37, seed=3)
+    b.reset()
+    want = b.rollout(T)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        np.testing.assert_array_equal(got[k].cpu().numpy(), want[k], err_msg=k)
