@@ -10,12 +10,15 @@ chunks.  ``value`` counts env-steps (one env advanced by one step) per second.
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 Workloads (synthetic, seeded; no dataset exists for this path):
-  doorkey8  DoorKey-8x8, 4096 envs x 1000 steps, seed 1 (default)
-  empty5    Empty-5x5, 64 envs x 1000 steps, seed 0
   mixed     65,536 envs over Empty-5/8/16, DoorKey-16, FourRooms-19,
-            LavaGap-7 x 2048 steps, seed 2, 128-step chunks
+            LavaGap-7 x 2048 steps, seed 2, 128-step chunks (default: the
+            largest single-GPU configuration)
+  doorkey8  DoorKey-8x8, 4096 envs x 1000 steps, seed 1
+  empty5    Empty-5x5, 64 envs x 1000 steps, seed 0
   rgb       Dynamic-Obstacles-16, 4 balls, 8192 envs x 512 steps, seed 3,
             RGB 224x224x3 + symbolic observations
+The other configurations, the fused policy rollouts and the serving run are
+reported under ``extras`` of the same line.
 Multi-GPU: every rank runs the full workload on its own env-index range
 (weak scaling, no collective on the data path).
 """
@@ -154,8 +157,35 @@ def profile_field(workload, key):
 
 
 def ncu_traffic(workload):
-    """Per-launch DRAM bytes of the step kernel (ncu), or None."""
+    """Per-launch DRAM bytes of the step kernel (ncu), or None.  The RGB
+    workload's launches are too large to capture; its summary holds the
+    reduced capture's bytes scaled to a full launch by env-steps."""
     return profile_field(workload, "dram_bytes_per_full_launch")
+
+
+def oracle_sample(w):
+    """The bounded sample of a workload the CPU oracle is timed on: the whole
+    batch for the small configurations; for the larger ones the first (up to)
+    1024 envs of every family block, with their own global env indices (so
+    the sample is a subset of the workload, keyed identically), over the first
+    (up to) 512 steps.  Returns (families, sizes, env indices, steps)."""
+    descs = descs_of(w)
+    if len(descs) * w["T"] <= 4096 * 1000:
+        return [d[0] for d in descs], [d[1] for d in descs], list(range(len(descs))), w["T"]
+    idx, start = [], 0
+    for p in w["parts"]:
+        cnt = sum(1 for d in descs if d == p)
+        idx += list(range(start, start + min(cnt, 1024)))
+        start += cnt
+    return [descs[i][0] for i in idx], [descs[i][1] for i in idx], idx, min(w["T"], 512)
+
+
+def sample_text(w):
+    fam, _, idx, T = oracle_sample(w)
+    if len(idx) == w["n"] and T == w["T"]:
+        return f"{len(idx)} envs x {T} steps (the full workload)"
+    return (f"{len(idx)} envs (the first {len(idx) // len(w['parts'])} of each of the {len(w['parts'])} family "
+            f"blocks, their own env indices) x {T} steps")
 
 
 class ClockSampler:
@@ -229,42 +259,41 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
-def cpu_oracle_rate(w, seed_offset=0, min_s=10.0, max_s=30.0, n_envs=None, T=None):
-    """Env-steps/s of the oracle on this host (single thread) on the workload's
-    own batch, repeated until at least min_s of work (bounded by max_s)."""
+def cpu_oracle_rate(w, min_s=10.0):
+    """Env-steps/s of the oracle on this host (single thread) on the
+    workload's bounded sample (oracle_sample), repeated until at least min_s
+    of work."""
     import oracle as O
 
-    n_envs = n_envs or w["n"]
-    T = T or w["T"]
-    descs = descs_of(w, n_envs)
+    fam, siz, idx, T = oracle_sample(w)
     done, t0 = 0, time.perf_counter()
     reps = 0
     while True:
-        b = O.Batch([d[0] for d in descs], [d[1] for d in descs], seed=w["seed"] + seed_offset)
+        b = O.Batch(fam, siz, seed=w["seed"], env_indices=idx)
         b.reset(sym=True)
         b.rollout(T, sym=True)
-        done += n_envs * T
+        done += len(idx) * T
         reps += 1
         el = time.perf_counter() - t0
-        if el >= min_s or el >= max_s:
+        if el >= min_s:
             break
-    return done / el, reps, el, n_envs, T
+    return done / el, reps, el, len(idx), T
 
 
 def _oracle_range(args):
     """One worker of the all-cores oracle timing: envs [lo, hi) of the
-    workload's batch, rolled out until at least min_s of work."""
+    workload's bounded sample, rolled out until at least min_s of work."""
     w_name, lo, hi, min_s = args
     import oracle as O
 
     w = WORKLOADS[w_name]
-    descs = descs_of(w)[lo:hi]
+    fam, siz, idx, T = oracle_sample(w)
     done, t0 = 0, time.perf_counter()
     while True:
-        b = O.Batch([d[0] for d in descs], [d[1] for d in descs], seed=w["seed"], env_indices=list(range(lo, hi)))
+        b = O.Batch(fam[lo:hi], siz[lo:hi], seed=w["seed"], env_indices=idx[lo:hi])
         b.reset(sym=True)
-        b.rollout(w["T"], sym=True)
-        done += (hi - lo) * w["T"]
+        b.rollout(T, sym=True)
+        done += (hi - lo) * T
         el = time.perf_counter() - t0
         if el >= min_s:
             return done, el
@@ -272,13 +301,14 @@ def _oracle_range(args):
 
 def cpu_oracle_rate_all_cores(w_name, min_s=4.0):
     """Env-steps/s of the oracle on every host core: one spawned process per
-    core, each on a contiguous range of the workload's envs (their rates add,
-    since they run at the same time)."""
+    core, each on a contiguous range of the workload's bounded sample (their
+    rates add, since they run at the same time)."""
     import multiprocessing as mp
 
     w = WORKLOADS[w_name]
-    P = max(1, min(os.cpu_count() or 1, w["n"]))
-    cuts = [w["n"] * i // P for i in range(P + 1)]
+    n = len(oracle_sample(w)[2])
+    P = max(1, min(os.cpu_count() or 1, n))
+    cuts = [n * i // P for i in range(P + 1)]
     with mp.get_context("spawn").Pool(P) as pool:
         res = pool.map(_oracle_range, [(w_name, cuts[i], cuts[i + 1], min_s) for i in range(P)])
     return sum(d / el for d, el in res), P, sum(d for d, _ in res)
@@ -290,11 +320,10 @@ def run_reference(args, w, world, rank):
         return 0
     import oracle as O
 
-    oracle_T = min(w["T"], 1000)
-    descs = descs_of(w)
+    fam, siz, idx, oracle_T = oracle_sample(w)
     times = []
     for k in range(args.warmup + args.steps):
-        b = O.Batch([d[0] for d in descs], [d[1] for d in descs], seed=w["seed"])
+        b = O.Batch(fam, siz, seed=w["seed"], env_indices=idx)
         t0 = time.perf_counter()
         b.reset(sym=True, rgb=False)
         b.rollout(oracle_T, sym=True)
@@ -302,14 +331,15 @@ def run_reference(args, w, world, rank):
         if k >= args.warmup:
             times.append(dt)
     total = sum(times)
-    units = len(descs) * oracle_T * len(times)
+    units = len(idx) * oracle_T * len(times)
     v = units / total
-    sample = f"{len(descs)} envs x {oracle_T} steps per bench step (symbolic obs), {len(times)} timed steps"
+    sample = f"{sample_text(w)} per bench step (symbolic obs), {len(times)} timed steps, one thread"
     line = {
         "impl": "reference", "metric": "env steps/sec", "value": v, "unit": "env-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": w["desc"], "n_envs": len(descs), "env_steps_per_bench_step": len(descs) * oracle_T},
+        "config": {"workload": w["desc"], "n_envs_per_gpu": w["n"], "sample_envs": len(idx), "sample_steps": oracle_T,
+                   "env_steps_per_bench_step": len(idx) * oracle_T},
         "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -333,9 +363,11 @@ def serving_requests(seed, n):
     return out
 
 
-def run_serving(n_req=2000, budget=2 << 30, load=0.7, seed=4, chunk=64):
-    """Poisson arrivals at `load` x the server's measured capacity; returns
-    latency percentiles and throughput.  Capacity is measured first by
+def run_serving(mixed_capacity=None, n_req=2000, budget=2 << 30, load=0.7, seed=4, chunk=64):
+    """Poisson arrivals of the serving mix; returns latency percentiles and
+    throughput.  The arrival rate is `load` x the measured capacity of the
+    65,536-env mixed configuration (its env-steps/s, when given), and, as a
+    second run, `load` x the server's own capacity, measured first by
     submitting a saturating burst of requests from the same mix."""
     import numpy as np
 
@@ -353,28 +385,41 @@ def run_serving(n_req=2000, budget=2 << 30, load=0.7, seed=4, chunk=64):
     cap = sum(r[2] * r[3] for r in burst) / (time.perf_counter() - t0)
     reqs = serving_requests(seed, n_req)
     mean_work = sum(r[2] * r[3] for r in reqs) / len(reqs)
-    lam = load * cap / mean_work  # requests per second
-    rng = np.random.default_rng(seed + 1)
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
-    tickets = []
-    start = time.perf_counter()
-    for r, a in zip(reqs, arrivals):
-        while time.perf_counter() - start < a:
-            pass
-        tickets.append(srv.submit(*r, digest=False))
-    res = [srv.wait(t, timeout_s=600.0) for t in tickets]
-    st = srv.stats()
+
+    def one_run(rate_basis, arrival_seed):
+        lam = load * rate_basis / mean_work  # requests per second
+        rng = np.random.default_rng(arrival_seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+        tickets = []
+        c0 = srv.stats()["chunks"]
+        start = time.perf_counter()
+        for r, a in zip(reqs, arrivals):
+            while time.perf_counter() - start < a:
+                pass
+            tickets.append(srv.submit(*r, digest=False))
+        res = [srv.wait(t, timeout_s=600.0) for t in tickets]
+        lat = np.array([x["t_done"] - x["t_submit"] for x in res]) * 1000.0
+        first = min(x["t_submit"] for x in res)
+        last = max(x["t_done"] for x in res)
+        work = sum(x["env_steps"] for x in res)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "env_steps_per_s": work / (last - first),
+                "arrival_rate_per_s": lam, "offered_env_steps_per_s": load * rate_basis,
+                "chunks": srv.stats()["chunks"] - c0}
+
+    out = {"requests": n_req, "offered_load": load, "budget_bytes": budget, "steps_per_launch": chunk,
+           "server_capacity_env_steps_per_s": cap,
+           "mix": "family U{5}, size U{5..19}, n_envs log-U[1, 4096], horizon U{1..512}, seed 4",
+           "outputs": "per-env returns, final views, ended episodes (no per-step digest)"}
+    if mixed_capacity:
+        out.update(one_run(mixed_capacity, seed + 1), rate_basis="0.7 x the measured env-steps/s of the "
+                   "65,536-env mixed configuration", mixed_capacity_env_steps_per_s=mixed_capacity)
+        out["at_server_capacity"] = one_run(cap, seed + 2)
+    else:
+        out.update(one_run(cap, seed + 1), rate_basis="0.7 x the server's burst capacity")
+    out["peak_bytes"] = srv.stats()["peak_bytes"]
     srv.close()
-    lat = np.array([x["t_done"] - x["t_submit"] for x in res]) * 1000.0
-    first = min(x["t_submit"] for x in res)
-    last = max(x["t_done"] for x in res)
-    work = sum(x["env_steps"] for x in res)
-    return {"requests": n_req, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "env_steps_per_s": work / (last - first),
-            "capacity_env_steps_per_s": cap, "offered_load": load, "arrival_rate_per_s": lam,
-            "budget_bytes": budget, "peak_bytes": st["peak_bytes"], "chunks": st["chunks"],
-            "steps_per_launch": chunk, "mix": "family U{5}, size U{5..19}, n_envs log-U[1, 4096], horizon U{1..512}, seed 4",
-            "outputs": "per-env returns, final views, ended episodes (no per-step digest)"}
+    return out
 
 
 POLICY_FLOPS = 2 * (64 * 64 + 64 * 64 + 16 * 64)  # per env-step on the tensor cores (K and N padded)
@@ -412,13 +457,99 @@ def time_rollouts(env, w, out, K, W, flush, per_family=False, policy=False):
     return [a.elapsed_time(b) for a, b in evs], kernel_ms, kl, l1[1] - l0[1]
 
 
+def roofline_of(w, descs, kernel_ms, k_launches, rollouts, C, peak, peak_src, workload):
+    """HBM roofline of the step kernel: algorithmic bytes per launch over the
+    live average launch time (CUDA events on the launching stream), with the
+    committed ncu capture's DRAM bytes per launch beside it."""
+    per_rollout = alg_bytes(w, descs, C)
+    achieved = per_rollout * rollouts / (kernel_ms / 1000.0) / 1e9
+    launches = -(-w["T"] // C)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(workload), "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": per_rollout / launches,
+            "kernel_ms_per_launch": kernel_ms / max(k_launches, 1), "kernel": "nx_step_kernel"}
+
+
+def issue_rate(workload, rate_per_gpu, clk, sms):
+    """Issue rate beside the HBM fraction: the symbolic configs are bound by
+    their instruction chain; warp-instructions per env-step come from the
+    committed ncu capture, the peak is one warp-instruction per cycle per
+    scheduler (4 per SM) at the SM clock sampled during the timed region."""
+    ipe = profile_field(workload, "warp_instructions_per_env_step")
+    if ipe is None or not clk.get("sm_mhz"):
+        return None
+    peak_ips = sms * 4 * clk["sm_mhz"] * 1e6
+    return {"warp_instructions_per_env_step": ipe, "achieved": rate_per_gpu * ipe, "peak": peak_ips,
+            "unit": "warp-instructions/s", "frac": rate_per_gpu * ipe / peak_ips,
+            "source": "ncu smsp__inst_executed.sum of the committed capture; peak = SMs x 4 x SM clock"}
+
+
+def run_e2e(nx, inputs, torch, w, descs, atlas, rank, world, steps, dist):
+    """End to end through the C ABI with host buffers: every bench step copies
+    that step's host actions in and every env-step's outputs (symbolic view,
+    reward, both flags) back into pinned host memory.  Outputs stream through
+    a pinned ring of at most 4 GiB (step i in slot i % D, D a multiple of the
+    128-step chunk), so the whole horizon is copied back."""
+    n, T = w["n"], w["T"]
+    C = 128
+    D = max(C, min(T, (4 << 30) // (n * (OUT_BYTES_SYM + 1)) // C * C))
+    acts = torch.from_numpy(inputs.random_actions(w["seed"], (T, n), n_actions=3 if w["parts"][0][0] == 4 else 7))
+    acts = acts.pin_memory()
+    hout = {"obs_sym": torch.empty((D, n, 7, 7, 3), dtype=torch.uint8).pin_memory(),
+            "reward": torch.empty((D, n), dtype=torch.float32).pin_memory(),
+            "terminated": torch.empty((D, n), dtype=torch.uint8).pin_memory(),
+            "truncated": torch.empty((D, n), dtype=torch.uint8).pin_memory(),
+            # (the 150 KB images of an RGB workload are not brought to the host here)
+            "obs_rgb": None}
+    e = nx.Env(descs=descs, seed=w["seed"], obs_rgb=w["rgb"], atlas=atlas, env_index_base=rank * n)
+    e.reset()
+    ks = max(1, min(steps, 5))
+    for _ in range(2):
+        e.rollout_host(T, actions=acts.numpy(), out=hout)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ks):
+        e.rollout_host(T, actions=acts.numpy(), out=hout)
+    el = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    e.close()
+    return {"value": world * n * T * ks / el, "unit": "env-steps/s", "h2d_bytes_per_step": T * n,
+            "d2h_bytes_per_step": T * n * OUT_BYTES_SYM, "steps": ks, "horizon": T, "host_ring_steps": D,
+            "actions": "host int8, seeded numpy draws", "call": "nx_rollout_host"}
+
+
+def run_extra(nx, inputs, name, flush, peak, peak_src, reps=5):
+    """One other configuration: reps timed rollouts after one warm-up, with
+    its own HBM roofline block."""
+    wx = WORKLOADS[name]
+    dx = descs_of(wx)
+    fv = bool(wx.get("full"))
+    ex = nx.Env(descs=dx, seed=wx["seed"], obs_rgb=wx["rgb"], atlas=inputs.atlas() if wx["rgb"] else None,
+                obs_full=fv, obs_cat=fv, obs_cat_fp=fv)
+    ex.reset()
+    ox = ex.alloc_out(wx["depth"])
+    ms, kms, kl, _ = time_rollouts(ex, wx, ox, reps, 1, flush)
+    cx = ex.info()["steps_per_launch"]
+    rec = {"workload": wx["desc"], "env_steps_per_s": len(dx) * wx["T"] * len(ms) / (sum(ms) / 1000),
+           "ms_per_rollout": sum(ms) / len(ms), "timed_rollouts": len(ms),
+           "roofline": roofline_of(wx, dx, kms, kl, len(ms), cx, peak, peak_src, name),
+           "launch_shape": {k: ex.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas")}}
+    ex.close()
+    del ox
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="navixgb", choices=["navixgb", "reference"])
-    ap.add_argument("--workload", default="doorkey8", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="mixed", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the other configs and the CPU baseline")
     ap.add_argument("--ncu-case", action="store_true", help="one rollout of the workload for an ncu capture")
     ap.add_argument("--shape", default="", help="force the launch shape as LANES,ENVS_PER_CTA[,STAGING] (no autotuning)")
@@ -486,68 +617,23 @@ def main():
     units = world * n * w["T"] * args.steps
     value = units / (total_ms / 1000.0)
 
-    # roofline of the step kernel: algorithmic bytes / live kernel time
-    C = env.info()["steps_per_launch"]
-    per_rollout_bytes = alg_bytes(w, descs, C)
-    achieved = per_rollout_bytes * args.steps / (kernel_ms / 1000.0) / 1e9
     peak, peak_src = measured_peaks()
-    launches_per_rollout = -(-w["T"] // C)
-    traffic = ncu_traffic(args.workload)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_src, "issue": None,
-                "algorithmic_bytes_per_launch": per_rollout_bytes / launches_per_rollout,
-                "kernel_ms_per_launch": kernel_ms / max(k_launches, 1), "kernel": "nx_step_kernel"}
+    C = env.info()["steps_per_launch"]
+    roofline = roofline_of(w, descs, kernel_ms, k_launches, args.steps, C, peak, peak_src, args.workload)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline["issue"] = issue_rate(args.workload, value / world, clk, sms)
 
-    # issue rate beside the HBM fraction: the symbolic configs are bound by
-    # their instruction chain; warp-instructions per env-step come from the
-    # committed ncu capture, the peak is one warp-instruction per cycle per
-    # scheduler (4 per SM) at the SM clock sampled during the timed region
-    ipe = profile_field(args.workload, "warp_instructions_per_env_step")
-    issue = None
-    if ipe is not None and clk.get("sm_mhz"):
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak_ips = sms * 4 * clk["sm_mhz"] * 1e6
-        issue = {"warp_instructions_per_env_step": ipe, "achieved": value / world * ipe, "peak": peak_ips,
-                 "unit": "warp-instructions/s", "frac": value / world * ipe / peak_ips,
-                 "source": "ncu smsp__inst_executed.sum of the committed capture; peak = SMs x 4 x SM clock"}
+    # the plain comparison form on the same envs: one single-step launch per
+    # family per step (spec: the persistent graph-captured form must beat it)
+    comparator = None
+    if len(w["parts"]) > 1:
+        ms_pf, _, _, _ = time_rollouts(env, w, out, 2, 1, flush, per_family=True)
+        pf = world * n * w["T"] * len(ms_pf) / (sum(ms_pf) / 1000)
+        comparator = {"per_family_env_steps_per_s": pf, "persistent_over_per_family": value / pf,
+                      "form": "nx_rollout_per_family: one single-step launch per family per step, no graph",
+                      "timed_rollouts": len(ms_pf)}
 
-    # end to end through the C ABI with host buffers: host actions in, host outputs back, every step
-    e2e = None
-    if True:  # every rank: the e2e leg is timed like the device leg (max over ranks)
-        # the whole horizon's outputs in pinned host memory, at most 4 GiB of
-        # it (a shorter horizon for the largest batches)
-        T = max(1, min(w["T"], (4 << 30) // (n * (OUT_BYTES_SYM + 1))))
-        acts = torch.from_numpy(inputs.random_actions(w["seed"], (T, n), n_actions=3 if w["parts"][0][0] == 4 else 7))
-        acts = acts.pin_memory()
-        hout = {"obs_sym": torch.empty((T, n, 7, 7, 3), dtype=torch.uint8).pin_memory(),
-                "reward": torch.empty((T, n), dtype=torch.float32).pin_memory(),
-                "terminated": torch.empty((T, n), dtype=torch.uint8).pin_memory(),
-                "truncated": torch.empty((T, n), dtype=torch.uint8).pin_memory(),
-                "obs_rgb": None}
-        if w["rgb"]:
-            # the end-to-end leg copies the symbolic outputs back; the 150 KB
-            # images of an RGB workload are not brought to the host here
-            hout["obs_rgb"] = None
-        e2e_env = nx.Env(descs=descs, seed=w["seed"], obs_rgb=w["rgb"], atlas=atlas, env_index_base=rank * n)
-        e2e_env.reset()
-        ks = max(1, min(args.steps, 5))
-        for _ in range(2):
-            e2e_env.rollout_host(T, actions=acts.numpy(), out=hout)
-        if dist:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(ks):
-            e2e_env.rollout_host(T, actions=acts.numpy(), out=hout)
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        h2d = T * n
-        d2h = T * n * OUT_BYTES_SYM
-        e2e = {"value": world * n * T * ks / el, "unit": "env-steps/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": ks, "horizon": T, "actions": "host int8, seeded numpy draws"}
-        e2e_env.close()
+    e2e = run_e2e(nx, inputs, torch, w, descs, atlas, rank, world, args.steps, dist)
 
     line = {
         "metric": "env steps/sec", "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
@@ -556,37 +642,19 @@ def main():
         "config": {"workload": w["desc"], "n_envs_per_gpu": n, "env_steps_per_bench_step": n * w["T"] * world,
                    "steps_per_launch": C, "launch_shape": {k: env.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas")},
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-        "roofline": dict(roofline, issue=issue), "e2e": e2e, "gpu_launches": all_launches, "clocks": clk,
+        "roofline": roofline, "e2e": e2e, "gpu_launches": all_launches, "clocks": clk,
         "wall_s": wall,
     }
+    if comparator:
+        line["comparator"] = comparator
     env.close()
     del out
 
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {}
-        for name in ("mixed", "rgb", "empty5", "doorkey8_full"):
-            if name == args.workload:
-                continue
-            wx = WORKLOADS[name]
-            dx = descs_of(wx)
-            fv = bool(wx.get("full"))
-            ex = nx.Env(descs=dx, seed=wx["seed"], obs_rgb=wx["rgb"], atlas=inputs.atlas() if wx["rgb"] else None,
-                        obs_full=fv, obs_cat=fv, obs_cat_fp=fv)
-            ex.reset()
-            ox = ex.alloc_out(wx["depth"])
-            ms, kms, kl, _ = time_rollouts(ex, wx, ox, 2, 1, flush)
-            cx = ex.info()["steps_per_launch"]
-            bx = alg_bytes(wx, dx, cx)
-            rec = {"env_steps_per_s": len(dx) * wx["T"] * len(ms) / (sum(ms) / 1000),
-                   "hbm_frac": bx * len(ms) / (kms / 1000) / 1e9 / peak,
-                   "achieved_GBps": bx * len(ms) / (kms / 1000) / 1e9,
-                   "launch_shape": {k: ex.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas")}}
-            if name == "mixed":
-                ms2, _, _, _ = time_rollouts(ex, wx, ox, 1, 0, flush, per_family=True)
-                rec["per_family_env_steps_per_s"] = len(dx) * wx["T"] / (sum(ms2) / 1000)
-            extras[name] = rec
-            ex.close()
-            del ox
+        for name in ("doorkey8", "rgb", "empty5", "doorkey8_full", "mixed"):
+            if name != args.workload:
+                extras[name] = run_extra(nx, inputs, name, flush, peak, peak_src)
         # the paper's batch-mode scale: wall time of one 1000-step rollout of 2^21 envs
         wx = WORKLOADS["paper_scale"]
         dx = descs_of(wx)
@@ -628,15 +696,16 @@ def main():
             del ox
         line["extras"] = extras
     if rank == 0 and world == 1 and not args.no_extras:
-        line.setdefault("extras", {})["serving"] = run_serving()
+        cap = value if args.workload == "mixed" else line.get("extras", {}).get("mixed", {}).get("env_steps_per_s")
+        line.setdefault("extras", {})["serving"] = run_serving(mixed_capacity=cap)
     if rank == 0 and world == 1 and not args.no_extras:
         rate, reps, el, ne, nt = cpu_oracle_rate(w)
         line["cpu_baseline"] = {"value": rate, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{ne} envs x {nt} steps (the full workload) x {reps}, {el:.1f} s, one thread"}
+                                "sample": f"{sample_text(w)} x {reps}, {el:.1f} s, one thread"}
         arate, P, asteps = cpu_oracle_rate_all_cores(args.workload)
         line["cpu_baseline"]["all_cores"] = {
             "value": arate, "unit": "env-steps/s", "cores": P, "kind": "oracle",
-            "sample": f"the same workload's envs in {P} contiguous ranges, one spawned process each, "
+            "sample": f"the same sample's envs in {P} contiguous ranges, one spawned process each, "
                       f"{asteps} env-steps in about 4 s"}
     if rank == 0:
         print(json.dumps(line), flush=True)

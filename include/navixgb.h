@@ -246,8 +246,11 @@ nx_status nx_rollout_per_family(nx_env* env, int32_t n_steps, int32_t act_mode, 
  * overlap): actions are copied in and outputs copied back chunk by chunk on
  * the context stream; returns when the copies have finished.  host_actions_TN
  * is int8 [n_steps, n_envs] (ignored for NX_ACT_RANDOM); the host outputs are
- * [n_steps, n_envs, ...] (depth is ignored).  Any output may be NULL; the
- * fully observable views are not available here (NX_E_INVAL). */
+ * [D, n_envs, ...] with D = host_traj->depth, step i written to host slot
+ * i % D (depth <= 0, or >= n_steps: D = n_steps, one slot per step), so a
+ * long rollout can stream through a bounded pinned ring.  Any output may be
+ * NULL; the fully observable views and the action output are not available
+ * here (NX_E_INVAL). */
 nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* host_actions_TN,
                           const nx_out* host_traj);
 

@@ -872,6 +872,9 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
             NX_CK(env, cudaEventCreateWithFlags(&env->ev_done[b], cudaEventDisableTiming), "event");
             NX_CK(env, cudaEventCreateWithFlags(&env->ev_copied[b], cudaEventDisableTiming), "event");
         }
+    // host outputs form a ring of D time slots: step i goes to slot i % D
+    // (D <= 0 or D >= n_steps: every step has its own slot)
+    const int D = (h && h->depth > 0 && h->depth < n_steps) ? h->depth : n_steps;
     bool used[2] = {false, false};
     for (int t0 = 0, k = 0; t0 < n_steps; t0 += C, ++k) {
         const int b = k & 1;
@@ -905,25 +908,23 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
         if (st != NX_OK) return st;
         NX_CK(env, cudaEventRecord(env->ev_done[b], env->stream), "record");
         NX_CK(env, cudaStreamWaitEvent(env->copy_stream, env->ev_done[b], 0), "wait compute");
-        const size_t T0 = (size_t)t0;
-        if (want_sym)
-            NX_CK(env, cudaMemcpyAsync(h->obs_sym + T0 * N * NX_OBS_SYM_BYTES, d.obs_sym, (size_t)Ck * N * NX_OBS_SYM_BYTES,
-                                       cudaMemcpyDeviceToHost, env->copy_stream), "copy back");
-        if (want_rgb)
-            NX_CK(env, cudaMemcpyAsync(h->obs_rgb + T0 * N * NX_OBS_RGB_BYTES, d.obs_rgb, (size_t)Ck * N * NX_OBS_RGB_BYTES,
-                                       cudaMemcpyDeviceToHost, env->copy_stream), "copy back");
-        if (want_r)
-            NX_CK(env, cudaMemcpyAsync(h->reward + T0 * N, d.reward, (size_t)Ck * N * 4, cudaMemcpyDeviceToHost,
-                                       env->copy_stream), "copy back");
-        if (want_te)
-            NX_CK(env, cudaMemcpyAsync(h->terminated + T0 * N, d.terminated, (size_t)Ck * N, cudaMemcpyDeviceToHost,
-                                       env->copy_stream), "copy back");
-        if (want_tr)
-            NX_CK(env, cudaMemcpyAsync(h->truncated + T0 * N, d.truncated, (size_t)Ck * N, cudaMemcpyDeviceToHost,
-                                       env->copy_stream), "copy back");
-        if (want_m)
-            NX_CK(env, cudaMemcpyAsync(h->mission + T0 * N, d.mission, (size_t)Ck * N, cudaMemcpyDeviceToHost,
-                                       env->copy_stream), "copy back");
+        // the chunk's Ck slots go to host slots t0 % D onwards, in two
+        // copies where they wrap around the end of the ring
+        const int s0 = t0 % D, first = std::min(Ck, D - s0);
+        auto copy_back = [&](void* host, const void* dev, size_t step_bytes) -> cudaError_t {
+            cudaError_t e = cudaMemcpyAsync((uint8_t*)host + (size_t)s0 * step_bytes, dev, (size_t)first * step_bytes,
+                                            cudaMemcpyDeviceToHost, env->copy_stream);
+            if (e == cudaSuccess && first < Ck)
+                e = cudaMemcpyAsync(host, (const uint8_t*)dev + (size_t)first * step_bytes, (size_t)(Ck - first) * step_bytes,
+                                    cudaMemcpyDeviceToHost, env->copy_stream);
+            return e;
+        };
+        if (want_sym) NX_CK(env, copy_back(h->obs_sym, d.obs_sym, N * NX_OBS_SYM_BYTES), "copy back");
+        if (want_rgb) NX_CK(env, copy_back(h->obs_rgb, d.obs_rgb, N * NX_OBS_RGB_BYTES), "copy back");
+        if (want_r) NX_CK(env, copy_back(h->reward, d.reward, N * 4), "copy back");
+        if (want_te) NX_CK(env, copy_back(h->terminated, d.terminated, N), "copy back");
+        if (want_tr) NX_CK(env, copy_back(h->truncated, d.truncated, N), "copy back");
+        if (want_m) NX_CK(env, copy_back(h->mission, d.mission, N), "copy back");
         NX_CK(env, cudaEventRecord(env->ev_copied[b], env->copy_stream), "record");
         used[b] = true;
     }

@@ -475,7 +475,8 @@ class Env:
         return out
 
     def rollout_host(self, n_steps, actions=None, out=None):
-        """Host numpy in, host numpy out (pinned numpy-backed torch tensors may be passed as ``out``)."""
+        """Host numpy in, host numpy out (pinned numpy-backed torch tensors may be passed as ``out``).
+        Outputs with a leading dimension D < n_steps form a ring: step i lands in slot i % D."""
         n = self.n
         if out is None:
             out = {
@@ -487,15 +488,19 @@ class Env:
                 "mission": np.empty((n_steps, n), np.uint8) if self.want_mission else None,
             }
         s = nx_out()
+        depth = n_steps
         for k in ("obs_sym", "obs_rgb", "reward", "terminated", "truncated", "mission"):
             a = out.get(k)
             if a is None:
                 setattr(s, k, None)
-            elif isinstance(a, np.ndarray):
+                continue
+            if isinstance(a, np.ndarray):
                 setattr(s, k, a.ctypes.data)
             else:
                 setattr(s, k, a.data_ptr())
-        s.depth = n_steps
+            depth = min(depth, int(a.shape[0]))
+            assert int(a.shape[1]) == n, f"{k}: second dimension must be n_envs"
+        s.depth = depth
         ptr, mode = None, NX_ACT_RANDOM
         if actions is not None:
             a = actions if isinstance(actions, np.ndarray) else actions.numpy()

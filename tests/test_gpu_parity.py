@@ -329,6 +329,31 @@ def test_host_buffer_rollout_equals_device_rollout():
     d.close()
 
 
+@pytest.mark.parametrize("depth", [45, 64, 149])
+def test_host_ring_holds_the_last_steps(depth):
+    """Host outputs shorter than the horizon form a ring (step i in slot
+    i % depth), including rings that wrap inside a 32-step chunk; every slot
+    equals the oracle's output of the last step written there."""
+    nx = nxmod()
+    descs = mixed_descs(300, MIXED)
+    T = 150
+    e = nx.Env(descs=descs, seed=31, autotune=False, steps_per_launch=32)
+    e.reset()
+    n = len(descs)
+    ring = {"obs_sym": np.zeros((depth, n, 7, 7, 3), np.uint8), "reward": np.zeros((depth, n), np.float32),
+            "terminated": np.zeros((depth, n), np.uint8), "truncated": np.zeros((depth, n), np.uint8)}
+    e.rollout_host(T, out=ring)
+    ob = oracle_batch_for(descs, 31)
+    ob.reset()
+    full = ob.rollout(T)
+    last = {k: np.empty_like(ring[k]) for k in ring}
+    for t in range(T):
+        for k in ring:
+            last[k][t % depth] = full[k][t]
+    assert_outputs_equal(ring, last, what=f"host ring of {depth} slots")
+    e.close()
+
+
 @pytest.mark.parametrize("reward_mode,lava", [(1, 0.0), (0, -1.0), (1, -1.0)])
 def test_reward_variants(reward_mode, lava):
     nx = nxmod()
