@@ -215,6 +215,32 @@ __device__ int kth_free(const Grp<G>& grp, const uint8_t* g, int W, int x0, int 
     return -1;
 }
 
+// The k-th free interior cell of a FourRooms-S grid (reading R18, rows
+// outer) before its goal is placed, in closed form: the walls x = m and
+// y = m (m = S / 2) leave S - 3 cells in every other interior row, plus the
+// gap (m, gy0) in the upper half and (m, gy1) in the lower one; row m holds
+// only its gaps (gx2, m) and (gx3, m).  Returns x | y << 8.
+__device__ __forceinline__ uint32_t fourrooms_kth(int S, int m, int gy0, int gy1, int gx2, int gx3, int k)
+{
+    const int w = S - 3;                 // cells of a row without a gap
+    const int upper = (m - 1) * w + 1;   // cells of rows 1 .. m-1 (one gap)
+    int y0 = 1, gy = gy0;                // the half holding k: first row, gap row
+    if (k >= upper + 2) {
+        k -= upper + 2;
+        y0 = m + 1;
+        gy = gy1;
+    } else if (k >= upper) {
+        return (uint32_t)(k == upper ? gx2 : gx3) | ((uint32_t)m << 8);
+    }
+    const int before = (gy - y0) * w;    // cells of the half's rows above its gap row
+    if (k >= before && k < before + w + 1)  // the gap row: x = 1 .. S-2 without a hole
+        return (uint32_t)(1 + k - before) | ((uint32_t)gy << 8);
+    const int kk = k < before ? k : k - 1;  // (past the gap row, one cell fewer per row index)
+    const int r = kk / w, j = kk - r * w;
+    const int x = j < m - 1 ? 1 + j : j + 2;  // skip the wall column x = m
+    return (uint32_t)x | ((uint32_t)(y0 + r) << 8);
+}
+
 // ---------------------------------------------------------------------------
 // Per-env registers (every lane of the group holds the same copy).
 struct AgentReg {
@@ -461,40 +487,45 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         const int door_y = 1 + bounded(d[1], (uint32_t)(S - 3));
         for (int y = 1 + grp.lane; y <= S - 2; y += G)
             g[y * W + xw] = (uint8_t)(y == door_y ? C_DOOR_LOCKED_YELLOW : C_WALL);
-        grp.sync();
-        const int n = count_free(grp, g, W, 1, xw - 1, 1, S - 2, -1);
-        const int ac = kth_free(grp, g, W, 1, xw - 1, 1, S - 2, -1, bounded(d[2], (uint32_t)n));
-        const int kc = kth_free(grp, g, W, 1, xw - 1, 1, S - 2, ac, bounded(d[4], (uint32_t)(n - 1)));
-        if (ac < 0 || kc < 0) return false;
-        a.x = ac % W;
-        a.y = ac / W;
+        // the region left of the wall, x 1..xw-1 by y 1..S-2, is all empty:
+        // its k-th cell row-major is (1 + k % w, 1 + k / w); the key's list
+        // is the same without the agent's cell
+        const int w = xw - 1, n = w * (S - 2);
+        const int ka = bounded(d[2], (uint32_t)n);
+        int kk = bounded(d[4], (uint32_t)(n - 1));
+        kk += kk >= ka ? 1 : 0;
+        const int ay = ka / w, ky = kk / w;
+        a.x = 1 + ka - ay * w;
+        a.y = 1 + ay;
         a.dir = bounded(d[3], 4u);
         grp.sync();
-        if (grp.lane == 0) g[kc] = (uint8_t)C_KEY_YELLOW;
+        if (grp.lane == 0) g[(1 + ky) * W + 1 + kk - ky * w] = (uint8_t)C_KEY_YELLOW;
     } else if (family == NX_FOURROOMS) {
         const int m = S / 2;
         for (int i = grp.lane; i < S; i += G) {
             g[i * W + m] = (uint8_t)C_WALL;
             g[m * W + i] = (uint8_t)C_WALL;
         }
+        const int gy0 = 1 + bounded(d[0], (uint32_t)(m - 1)), gy1 = m + 1 + bounded(d[1], (uint32_t)(S - 2 - m));
+        const int gx2 = 1 + bounded(d[2], (uint32_t)(m - 1)), gx3 = m + 1 + bounded(d[3], (uint32_t)(S - 2 - m));
+        // goal and agent by the closed-form k-th free cell; the agent's list
+        // is the same without the goal's cell
+        const int n = (S - 3) * (S - 3) + 4;
+        const int kg = bounded(d[4], (uint32_t)n);
+        int ka = bounded(d[5], (uint32_t)(n - 1));
+        ka += ka >= kg ? 1 : 0;
+        const uint32_t gc = fourrooms_kth(S, m, gy0, gy1, gx2, gx3, kg);
+        const uint32_t ac = fourrooms_kth(S, m, gy0, gy1, gx2, gx3, ka);
         grp.sync();
         if (grp.lane == 0) {
-            g[(1 + bounded(d[0], (uint32_t)(m - 1))) * W + m] = (uint8_t)C_EMPTY;
-            g[(m + 1 + bounded(d[1], (uint32_t)(S - 2 - m))) * W + m] = (uint8_t)C_EMPTY;
-            g[m * W + 1 + bounded(d[2], (uint32_t)(m - 1))] = (uint8_t)C_EMPTY;
-            g[m * W + m + 1 + bounded(d[3], (uint32_t)(S - 2 - m))] = (uint8_t)C_EMPTY;
+            g[gy0 * W + m] = (uint8_t)C_EMPTY;
+            g[gy1 * W + m] = (uint8_t)C_EMPTY;
+            g[m * W + gx2] = (uint8_t)C_EMPTY;
+            g[m * W + gx3] = (uint8_t)C_EMPTY;
+            g[(gc >> 8) * W + (gc & 0xFFu)] = (uint8_t)C_GOAL;
         }
-        grp.sync();
-        const int n = count_free(grp, g, W, 1, S - 2, 1, S - 2, -1);
-        const int gc = kth_free(grp, g, W, 1, S - 2, 1, S - 2, -1, bounded(d[4], (uint32_t)n));
-        if (gc < 0) return false;
-        grp.sync();
-        if (grp.lane == 0) g[gc] = (uint8_t)C_GOAL;
-        grp.sync();
-        const int ac = kth_free(grp, g, W, 1, S - 2, 1, S - 2, -1, bounded(d[5], (uint32_t)(n - 1)));
-        if (ac < 0) return false;
-        a.x = ac % W;
-        a.y = ac / W;
+        a.x = (int)(ac & 0xFFu);
+        a.y = (int)(ac >> 8);
         a.dir = bounded(d[6], 4u);
     } else if (family == NX_LAVAGAP) {
         const int xl = 2 + bounded(d[0], (uint32_t)(S - 4));
@@ -502,12 +533,11 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         for (int y = 1 + grp.lane; y <= S - 2; y += G)
             if (y != gap) g[y * W + xl] = (uint8_t)C_LAVA;
     } else if (family == NX_EMPTY_RANDOM) {
-        grp.sync();
-        const int n = count_free(grp, g, W, 1, S - 2, 1, S - 2, -1);
-        const int ac = kth_free(grp, g, W, 1, S - 2, 1, S - 2, -1, bounded(d[0], (uint32_t)n));
-        if (ac < 0) return false;
-        a.x = ac % W;
-        a.y = ac / W;
+        // the interior without the goal, its last cell row-major: the k-th
+        // cell is (1 + k % (S-2), 1 + k / (S-2))
+        const int w = S - 2, ka = bounded(d[0], (uint32_t)(w * w - 1)), ay = ka / w;
+        a.x = 1 + ka - ay * w;
+        a.y = 1 + ay;
         a.dir = bounded(d[1], 4u);
     } else if (family == NX_GOTODOOR) {
         // L8: one closed door on each wall (top, bottom, left, right) at drawn

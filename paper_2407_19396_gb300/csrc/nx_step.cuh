@@ -356,13 +356,20 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             for (int i = tid; i < n * cs / 4; i += nthreads) reinterpret_cast<uint32_t*>(sgrid)[i] = kWall4;
             __syncthreads();
         }
+        // i / HW and c / S by multiply-high with ceil(2^32 / d): exact for
+        // i < 2^32 / d, far above the n * HW <= 256 * 361 cells of an item
+        const uint32_t inv_hw = 0xFFFFFFFFu / (uint32_t)HW + 1u, inv_s = 0xFFFFFFFFu / (uint32_t)S + 1u;
         if (!p.reset_all) {
             const uint8_t* src = p.grids + item.grid_offset;
             for (int i = tid; i < n * HW; i += nthreads) {
-                const int e = i / HW, c = i - e * HW;
+                const int e = (int)__umulhi((uint32_t)i, inv_hw), c = i - e * HW;
                 const uint8_t* b = src + (size_t)e * 3 * HW;
-                const int y = c / S, x = c - y * S;
-                sgrid[e * cs + (y + kPad) * W + x + kPad] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
+                int si = e * cs + c;  // a packed grid: row stride S
+                if constexpr (kPad > 0) {
+                    const int y = (int)__umulhi((uint32_t)c, inv_s), x = c - y * S;
+                    si = e * cs + (y + kPad) * W + x + kPad;
+                }
+                sgrid[si] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
             }
             if (active) load_agent(p.agents + env, a);
         }
@@ -635,9 +642,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         {
             uint8_t* dst = p.grids + item.grid_offset;
             for (int i = tid; i < n * HW; i += nthreads) {
-                const int e = i / HW, c = i - e * HW;
-                const int y = c / S, x = c - y * S;
-                const uint32_t code = sgrid[e * cs + (y + kPad) * W + x + kPad];
+                const int e = (int)__umulhi((uint32_t)i, inv_hw), c = i - e * HW;
+                int si = e * cs + c;
+                if constexpr (kPad > 0) {
+                    const int y = (int)__umulhi((uint32_t)c, inv_s), x = c - y * S;
+                    si = e * cs + (y + kPad) * W + x + kPad;
+                }
+                const uint32_t code = sgrid[si];
                 uint8_t* b = dst + (size_t)e * 3 * HW;
                 b[c] = (uint8_t)cell_ent(code);
                 b[HW + c] = (uint8_t)cell_col(code);
