@@ -614,13 +614,29 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
 // The same generator run by a whole warp for one env, kept out of line: it is
 // the rare path of narrow groups, and inlining it would raise the register
 // allocation of the whole step kernel.  0 <= FAM < NX_N_FAMILIES fixes the
-// family (the lean step kernels of one family).
+// family (the lean step kernels of one family).  The new agent comes back in
+// registers (a reference argument would put it on the caller's stack):
+// x | y << 8 | dir << 16 | mission << 24, n_balls | ok << 8, then the balls'
+// columns and rows one byte each.
 template <int FAM>
-__device__ __noinline__ bool reset_layout_warp(uint8_t* g, int S, int family, int n_balls, int variant, uint64_t seed,
-                                               uint32_t key_env, uint32_t episode, AgentReg& a)
+__device__ __noinline__ uint4 reset_layout_warp(uint8_t* g, int S, int family, int n_balls, int variant, uint64_t seed,
+                                                uint32_t key_env, uint32_t episode)
 {
-    return reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, S, (FAM >= 0 && FAM < NX_N_FAMILIES) ? FAM : family,
-                        n_balls, variant, seed, key_env, episode, a);
+    AgentReg a;
+    const bool ok = reset_layout(Grp<32>((int)(threadIdx.x & 31u)), g, S, S,
+                                 (FAM >= 0 && FAM < NX_N_FAMILIES) ? FAM : family, n_balls, variant, seed, key_env,
+                                 episode, a);
+    uint4 r;
+    r.x = (uint32_t)a.x | ((uint32_t)a.y << 8) | ((uint32_t)a.dir << 16) | (a.mission << 24);
+    r.y = (uint32_t)a.nb | (ok ? 0x100u : 0u);
+    r.z = 0u;
+    r.w = 0u;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        r.z |= (uint32_t)a.bx[b] << (8 * b);
+        r.w |= (uint32_t)a.by[b] << (8 * b);
+    }
+    return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -809,13 +825,16 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
         }
         tmask &= (1ull << 49) - 1ull;
         const uint64_t vis = occlusion<G>(tmask, occ);
+        // an unseen cell's code becomes 0, whose triple is (0, 0, 0); a seen
+        // cell's code is never 0
+#pragma unroll
+        for (int w = 0; w < 13; ++w) packed[w] &= byte_mask4((uint32_t)(vis >> (4 * w)) & 15u);
         uint32_t tri[49];
 #pragma unroll
         for (int c = 0; c < 49; ++c) {
             const uint32_t code = (packed[c >> 2] >> (8 * (c & 3))) & 0xFFu;
-            const bool vb = (vis >> c) & 1ull;
-            tri[c] = vb ? dec[code] : 0u;
-            if (tiles) tiles[c] = (uint16_t)tile_of_triple(vb, c == 45, tri[c]);
+            tri[c] = dec[code];
+            if (tiles) tiles[c] = (uint16_t)tile_of_triple(code != 0u, c == 45, tri[c]);
         }
 #pragma unroll
         for (int m = 0; m < 12; ++m) {
@@ -894,11 +913,15 @@ __device__ __forceinline__ void write_view(const Grp<G>& grp, const ViewOut<G>& 
 {
     if constexpr (G == 1) {
         const uint32_t head = (4u - ((uint32_t)(uintptr_t)sym & 3u)) & 3u;  // bytes before the first aligned word
-        for (uint32_t i = 0; i < head; ++i) sym[i] = (uint8_t)(out.sw[0] >> (8 * i));
+#pragma unroll
+        for (uint32_t i = 0; i < 3; ++i)
+            if (i < head) sym[i] = (uint8_t)(out.sw[0] >> (8 * i));
         uint32_t* wd = reinterpret_cast<uint32_t*>(sym + head);
 #pragma unroll
         for (int i = 0; i < 36; ++i) wd[i] = __funnelshift_r(out.sw[i], out.sw[i + 1], 8 * head);
-        for (uint32_t i = head; i < 3; ++i) sym[144 + i] = (uint8_t)(out.sw[36] >> (8 * i));
+#pragma unroll
+        for (uint32_t i = 0; i < 3; ++i)
+            if (i >= head) sym[144 + i] = (uint8_t)(out.sw[36] >> (8 * i));
     } else if constexpr (G >= 8) {
         constexpr int RPK = G / 8, K = (7 + RPK - 1) / RPK;
         const int vx = grp.lane & 7, r0 = grp.lane >> 3;

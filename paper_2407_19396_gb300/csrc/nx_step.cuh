@@ -361,15 +361,36 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         const uint32_t inv_hw = 0xFFFFFFFFu / (uint32_t)HW + 1u, inv_s = 0xFFFFFFFFu / (uint32_t)S + 1u;
         if (!p.reset_all) {
             const uint8_t* src = p.grids + item.grid_offset;
-            for (int i = tid; i < n * HW; i += nthreads) {
-                const int e = (int)__umulhi((uint32_t)i, inv_hw), c = i - e * HW;
-                const uint8_t* b = src + (size_t)e * 3 * HW;
-                int si = e * cs + c;  // a packed grid: row stride S
-                if constexpr (kPad > 0) {
-                    const int y = (int)__umulhi((uint32_t)c, inv_s), x = c - y * S;
-                    si = e * cs + (y + kPad) * W + x + kPad;
+            // U cells per thread and round, their three global loads issued
+            // before any is used (one dependent round trip per cell made the
+            // loads of the larger grids latency-bound)
+            const int nhw = n * HW;
+            constexpr int U = 4;
+            for (int i0 = tid; i0 < nhw; i0 += U * nthreads) {
+                uint32_t pe[U], pc[U], ps[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * nthreads;
+                    const int e = (int)__umulhi((uint32_t)i, inv_hw), c = i - e * HW;
+                    const uint8_t* b = src + (size_t)e * 3 * HW + c;
+                    const bool ok = i < nhw;
+                    pe[u] = ok ? (uint32_t)b[0] : 0u;
+                    pc[u] = ok ? (uint32_t)b[HW] : 0u;
+                    ps[u] = ok ? (uint32_t)b[2 * HW] : 0u;
                 }
-                sgrid[si] = (uint8_t)pack_cell(b[c], b[HW + c], b[2 * HW + c]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * nthreads;
+                    if (i < nhw) {
+                        const int e = (int)__umulhi((uint32_t)i, inv_hw), c = i - e * HW;
+                        int si = e * cs + c;  // a packed grid: row stride S
+                        if constexpr (kPad > 0) {
+                            const int y = (int)__umulhi((uint32_t)c, inv_s), x = c - y * S;
+                            si = e * cs + (y + kPad) * W + x + kPad;
+                        }
+                        sgrid[si] = (uint8_t)pack_cell(pe[u], pc[u], ps[u]);
+                    }
+                }
             }
             if (active) load_agent(p.agents + env, a);
         }
@@ -450,13 +471,25 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     const uint32_t ep = __shfl_sync(0xFFFFFFFFu, p.reset_all ? 0u : a.episode + 1u, L);
                     const uint32_t k = __shfl_sync(0xFFFFFFFFu, key, L);
                     const int owner = ((tid & ~31) + L) / G;  // group (env slot) of lane L
-                    AgentReg na;
-                    const bool ok =
-                        reset_layout_warp<FAM>(sgrid + owner * cs, S, family, n_balls, variant, seed, k, ep, na);
-                    if (!ok && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    const uint4 r = reset_layout_warp<FAM>(sgrid + owner * cs, S, family, n_balls, variant, seed, k, ep);
+                    if (!(r.y & 0x100u) && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
                     if (gi == owner) {
-                        na.invalid = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
-                        a = na;
+                        // the new episode's start; the invalid-action flag is sticky
+                        a.x = (int)(r.x & 0xFFu);
+                        a.y = (int)((r.x >> 8) & 0xFFu);
+                        a.dir = (int)((r.x >> 16) & 0xFFu);
+                        a.mission = r.x >> 24;
+                        a.nb = (int)(r.y & 0xFFu);
+                        a.carry = 0u;
+                        a.done = 0;
+                        a.t = 0;
+                        a.episode = ep;
+                        a.invalid = p.reset_all ? 0 : a.invalid;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            a.bx[b] = (int)((r.z >> (8 * b)) & 0xFFu);
+                            a.by[b] = (int)((r.w >> (8 * b)) & 0xFFu);
+                        }
                     }
                 }
                 __syncwarp();
