@@ -12,8 +12,8 @@ torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
 from paper_2407_19396_gb300 import inputs  # noqa: E402
-from tests.gpu_util import (assert_outputs_equal, assert_states_equal, mixed_descs, oracle_batch_for,  # noqa: E402
-                            to_np)
+from tests.gpu_util import (STATE_KEYS, assert_outputs_equal, assert_states_equal, mixed_descs,  # noqa: E402
+                            oracle_batch_for, to_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -148,31 +148,72 @@ def test_config_mixed_65536envs_2048steps_sampled():
     env.close()
 
 
+def test_config_mixed_65536envs_2048steps_every_env():
+    """The full mixed configuration, every env: the reset outputs, every
+    env's outputs at the last step of each of the 16 graph-captured 128-step
+    chunks, and every env's final state (grid planes and agent block) equal
+    the oracle's, run in spawned processes over contiguous env ranges."""
+    from tests.oracle_pool import KEYS, chunk_ends
+
+    nx = nxmod()
+    n, T, C = 65536, 2048, 128
+    descs = mixed_descs(n, MIXED)
+    o_reset, o_ends, o_states = chunk_ends(n, MIXED, 2, T, C)
+    env = nx.Env(descs=descs, seed=2, steps_per_launch=C)
+    r = env.reset()
+    assert_outputs_equal(r, o_reset, what="mixed reset, every env")
+    out = env.alloc_out(C)
+    for chunk in range(T // C):
+        env.rollout(C, depth=C, out=out)
+        got = {k: to_np(out[k][C - 1]) for k in KEYS}
+        assert_outputs_equal(got, o_ends[chunk], what=f"mixed, every env, step {(chunk + 1) * C - 1}")
+    st = env.state()["envs"]
+    for i in range(n):
+        for k in STATE_KEYS:
+            if st[i][k] != o_states[i][k]:
+                raise AssertionError(f"mixed final state, env {i}, field {k}: gpu {st[i][k]!r} oracle {o_states[i][k]!r}")
+    env.close()
+
+
 def test_config_rgb_dynobs16_8192envs_512steps():
+    """The RGB configuration (Dynamic-Obstacles-16, 4 balls, 8192 envs x 512
+    steps, seed 3) on the comparison plan of its contract: envs 0..63 at every
+    step, symbolic and RGB; every env's symbolic outputs, plus the RGB images
+    of 64 envs spread over the batch, at steps 0..7, every 32nd and 511; every
+    env's final state.  The GPU writes an 8-slot ring, read back after each
+    8-step call."""
     nx = nxmod()
     atlas = inputs.atlas()
     n, T, D = 8192, 512, 8
     env = nx.Env(O.DYNOBS, 16, n, seed=3, obs_rgb=True, atlas=atlas)
     env.reset()
-    out = env.rollout(T, depth=D)
-    torch.cuda.synchronize()
-    # symbolic outputs of every env for the last D steps, and the final state of every env
-    ob = O.Batch([O.DYNOBS] * n, [16] * n, seed=3)
-    ob.reset()
-    ob.rollout(T - D, sym=False)
-    oo = ob.rollout(D)
-    slots = [(T - D + i) % D for i in range(D)]
-    got = {k: to_np(out[k])[slots] for k in ("obs_sym", "reward", "terminated", "truncated")}
-    assert_outputs_equal(got, oo, what="DynObs-16 last steps")
-    assert_states_equal(env.state()["envs"], ob, what="DynObs-16 final")
-    # RGB images of a sample of envs (both ends and a spread) for the last D steps
-    sample = sorted(set(list(range(8)) + list(range(n - 8, n)) + list(np.linspace(0, n - 1, 48).astype(int))))
-    osb = oracle_batch_for([(O.DYNOBS, 16)] * n, 3, indices=sample)
-    osb.reset(sym=False)
-    osb.rollout(T - D, sym=False)
-    orgb = osb.rollout(D, sym=True, rgb=True, atlas=atlas)
-    rgb = to_np(out["obs_rgb"][:, sample])[slots]
-    np.testing.assert_array_equal(rgb, orgb["obs_rgb"])
+    out = env.alloc_out(D)
+    head = oracle_batch_for([(O.DYNOBS, 16)] * n, 3, indices=list(range(64)))
+    head.reset()
+    spread = sorted(set(np.linspace(64, n - 1, 64).astype(int).tolist()))
+    ospread = oracle_batch_for([(O.DYNOBS, 16)] * n, 3, indices=spread)
+    ospread.reset()
+    whole = O.Batch([O.DYNOBS] * n, [16] * n, seed=3)
+    whole.reset()
+    sel = torch.tensor(spread, device="cuda")
+    for call in range(T // D):
+        env.rollout(D, depth=D, out=out)
+        selected = call == 0 or call % 4 == 0 or call == T // D - 1  # steps 0..7, 32 k, 511
+        oh = head.rollout(D, rgb=True, atlas=atlas)
+        got = {k: to_np(out[k][:, :64]) for k in ("obs_sym", "obs_rgb", "reward", "terminated", "truncated")}
+        assert_outputs_equal(got, oh, keys=("obs_sym", "obs_rgb", "reward", "terminated", "truncated"),
+                             what=f"DynObs-16 envs 0..63, steps {call * D}..{call * D + D - 1}")
+        ow = whole.rollout(D)
+        os_ = ospread.rollout(D, rgb=selected, atlas=atlas if selected else None)
+        if selected:
+            steps = list(range(D)) if call == 0 else ([0] if call % 4 == 0 else []) + ([D - 1] if call == T // D - 1 else [])
+            for j in steps:
+                gsym = {k: to_np(out[k][j]) for k in ("obs_sym", "reward", "terminated", "truncated")}
+                osym = {k: ow[k][j] for k in ("obs_sym", "reward", "terminated", "truncated")}
+                assert_outputs_equal(gsym, osym, what=f"DynObs-16 every env, step {call * D + j}")
+                np.testing.assert_array_equal(to_np(out["obs_rgb"][j].index_select(0, sel)), os_["obs_rgb"][j],
+                                              err_msg=f"RGB spread, step {call * D + j}")
+    assert_states_equal(env.state()["envs"], whole, what="DynObs-16 final, every env")
     env.close()
 
 
