@@ -55,7 +55,8 @@ enum {
     NX_E_TIMEOUT = -4,       /* a bounded host wait expired */
     NX_E_DEVICE_CHECK = -5,  /* a device-side consistency check fired */
     NX_E_BUDGET = -6,        /* a serving request can never fit the HBM budget */
-    NX_E_STATE = -7          /* call out of order (e.g. step before reset) */
+    NX_E_STATE = -7,         /* call out of order (e.g. step before reset) */
+    NX_E_CANCELED = -8       /* a serving request withdrawn by nx_cancel */
 };
 
 /* environment families of Table 8; the crossings take their number of
@@ -293,10 +294,12 @@ nx_status nx_set_policy(nx_env* env, const nx_policy* policy);
  *       u8 x, y, dir, carry_ent, carry_col, done, invalid, n_balls;
  *       u16 t, max_steps; u32 episode; u8 ball_x[4], ball_y[4];
  *       u8 family, size, mission (NX_NO_MISSION without one), reserved;
- *       u32 grid_offset
- *   [64 + 32 n, end)       grid pool: for each env at grid_offset, three
- *                          planes of size*size bytes (entity, colour, state),
- *                          row-major y * size + x.
+ *       u32 grid_offset: the low 32 bits of the env's byte offset in the pool
+ *   [64 + 32 n, end)       grid pool: the envs in order, each one's three
+ *                          planes of size*size bytes (entity, colour, state,
+ *                          row-major y * size + x) right after the previous
+ *                          env's, so env i starts at the sum of 3 size^2 over
+ *                          the envs before it (pools may exceed 4 GiB).
  * nx_set_state accepts only a snapshot of a context with the same
  * descriptors. */
 size_t nx_state_bytes(const nx_env* env);
@@ -364,9 +367,10 @@ typedef struct {
     uint64_t submitted, finished, rejected, env_steps, chunks;
     double busy_s;             /* time with at least one request on the GPU */
     size_t budget_bytes, in_use_bytes, peak_bytes;
+    uint64_t canceled;         /* requests withdrawn by nx_cancel */
 } nx_server_stats;
 
-/* nx_server_create: hbm_budget_bytes (at most 4 GiB) is allocated once, up
+/* nx_server_create: hbm_budget_bytes (1 MiB .. 1 TiB) is allocated once, up
  * front, and every admitted request's state and outputs are carved from it.
  * opts: steps_per_launch is the chunk length (latency vs launch overhead),
  * group_lanes / envs_per_cta / staging fix one launch shape for every
@@ -384,6 +388,14 @@ nx_status nx_poll(nx_server* server, uint64_t ticket, nx_result* result);
 /* nx_wait: blocks until the request finishes or timeout_s passes
  * (NX_E_TIMEOUT; <= 0 waits without bound). */
 nx_status nx_wait(nx_server* server, uint64_t ticket, nx_result* result, double timeout_s);
+/* nx_cancel: withdraws a request.  A queued request is dropped at once; an
+ * admitted one runs no further chunk, and its memory and request slot are
+ * released once the chunk in flight has completed.  Its result status
+ * becomes NX_E_CANCELED (nx_poll / nx_wait return it); its result buffers
+ * are not written.  NX_E_STATE when it is too late: the request has finished
+ * or its last chunk is already on the GPU (its result will arrive as
+ * usual); NX_E_INVAL for an unknown ticket. */
+nx_status nx_cancel(nx_server* server, uint64_t ticket);
 nx_status nx_server_get_stats(nx_server* server, nx_server_stats* stats);
 /* nx_server_destroy: finishes in-flight work, drops queued requests (their
  * status becomes NX_E_STATE) and releases everything. */

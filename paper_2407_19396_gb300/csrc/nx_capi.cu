@@ -17,6 +17,7 @@
 #include "nx_internal.h"
 #include "nx_runtime.h"
 #include "nx_policy.cuh"
+#include "nx_trace.h"
 
 // ---------------------------------------------------------------------------
 // errors
@@ -35,6 +36,7 @@ const char* nx_status_str(nx_status s)
     case NX_E_DEVICE_CHECK: return "device check failed";
     case NX_E_BUDGET: return "request exceeds the HBM budget";
     case NX_E_STATE: return "call out of order";
+    case NX_E_CANCELED: return "request canceled";
     default: return "unknown status";
     }
 }
@@ -265,14 +267,10 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
     env->grid_offset.resize(env->n_envs);
     for (int i = 0; i < env->n_envs; ++i) {
         const int S = env->descs[i].height;
-        env->grid_offset[i] = (uint32_t)off;
+        env->grid_offset[i] = off;
         off += (size_t)3 * S * S;
         env->max_side = std::max(env->max_side, S);
         seen[env->descs[i].family] = true;
-    }
-    if (off > 0xFFFFFFFFull) {
-        delete env;
-        return nx_fail(nullptr, NX_E_INVAL, "state pool larger than 4 GiB");
     }
     env->grid_pool = off;
     env->n_families = 0;
@@ -524,6 +522,7 @@ static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full
 // A direct (uncaptured) chunk launch on the context stream, counted and timed.
 static nx_status launch_chunk_direct(nx_env* env, int steps, bool full, bool policy = false, bool lean = false)
 {
+    nx_range range("nx_chunk");
     nx_status st = prof_mark(env, true);
     if (st == NX_OK) st = launch_chunk(env, steps, env->stream, full, policy, lean);
     if (st == NX_OK) st = prof_mark(env, false);
@@ -537,6 +536,7 @@ static nx_status launch_chunk_direct(nx_env* env, int steps, bool full, bool pol
 // device-side request record, so one graph serves every call.
 static nx_status launch_chunk_graph(nx_env* env, int steps, bool full, bool policy = false, bool lean = false)
 {
+    nx_range range("nx_chunk");
     nx_graph* g = nullptr;
     for (auto& c : env->graphs)
         if (c.steps == steps && c.full == full && c.policy == policy && c.lean == lean) g = &c;
@@ -632,6 +632,7 @@ static nx_status check_out(nx_env* env, const nx_out* out)
 
 nx_status nx_reset(nx_env* env, const nx_out* out)
 {
+    nx_range range("nx_reset");
     if (!env) return nx_fail(nullptr, NX_E_INVAL, "env is NULL");
     nx_status st = check_out(env, out);
     if (st != NX_OK) return st;
@@ -651,6 +652,7 @@ nx_status nx_reset(nx_env* env, const nx_out* out)
 static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* d_actions,
                               const nx_out* traj, bool per_family)
 {
+    nx_range range(per_family ? "nx_rollout_per_family" : "nx_rollout");
     if (!env) return nx_fail(nullptr, NX_E_INVAL, "env is NULL");
     if (!env->was_reset) return nx_fail(env, NX_E_STATE, "nx_reset must come first");
     if (n_steps < 0) return nx_fail(env, NX_E_INVAL, "n_steps must be >= 0");
@@ -833,6 +835,7 @@ nx_status nx_rollout_per_family(nx_env* env, int32_t n_steps, int32_t act_mode, 
 
 nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* h_actions, const nx_out* h)
 {
+    nx_range range("nx_rollout_host");
     if (!env) return nx_fail(nullptr, NX_E_INVAL, "env is NULL");
     if (!env->was_reset) return nx_fail(env, NX_E_STATE, "nx_reset must come first");
     if (n_steps < 0) return nx_fail(env, NX_E_INVAL, "n_steps must be >= 0");
@@ -940,6 +943,7 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
 
 nx_status nx_autotune(nx_env* env)
 {
+    nx_range range("nx_autotune");
     env->tuned = true;
     // (2 lanes per env, never the fastest in any measured workload and the
     // slowest to try, stays available as an explicit shape only)
@@ -1070,14 +1074,15 @@ nx_status nx_set_state(nx_env* env, const void* host_buf, size_t bytes)
         const nx_desc& d = env->descs[i];
         const nx_agent& a = ag[i];
         const int S = d.height;
-        if (a.family != d.family || a.size != S || a.grid_offset != env->grid_offset[i] || a.max_steps != d.max_steps)
+        if (a.family != d.family || a.size != S || a.grid_offset != (uint32_t)env->grid_offset[i] ||
+            a.max_steps != d.max_steps)
             return nx_fail(env, NX_E_INVAL, "snapshot descriptors differ from this context");
         // every index the kernels derive from the snapshot must stay inside the grid
         bool ok = a.x < S && a.y < S && a.dir < 4 && a.done <= 1 && a.invalid <= 1 && a.n_balls <= NX_MAX_BALLS &&
                   a.carry_ent <= 10 && a.carry_col <= 5 && (d.family == NX_DYNOBS || a.n_balls == 0) &&
                   (d.family == NX_GOTODOOR ? a.mission <= 5 : a.mission == NX_NO_MISSION);
         for (int k = 0; ok && k < a.n_balls; ++k) ok = a.ball_x[k] < S && a.ball_y[k] < S;
-        const uint8_t* g = pool_b + a.grid_offset;
+        const uint8_t* g = pool_b + env->grid_offset[i];
         for (int c = 0; ok && c < S * S; ++c) ok = g[c] <= 10 && g[S * S + c] <= 5 && g[2 * S * S + c] <= 2;
         if (!ok) return nx_fail(env, NX_E_INVAL, "snapshot holds out-of-range state");
     }

@@ -298,6 +298,30 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
     reinterpret_cast<uint4*>(dst)[1] = w1;
 }
 
+// Whether every index a step derives from the agent block stays inside an
+// S x S grid: the agent's cell and direction, and each ball's cell.  Blocks
+// written by the kernels and by nx_set_state (which validates) always pass;
+// the step kernel checks each block it loads, so that a block corrupted in
+// device memory can never make a step index outside its env's grid.
+__device__ __forceinline__ bool agent_in_range(const AgentReg& a, int S)
+{
+    bool ok = (unsigned)a.x < (unsigned)S && (unsigned)a.y < (unsigned)S && (unsigned)a.dir < 4u && (unsigned)a.nb <= 4u;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        ok = ok && (b >= a.nb || ((unsigned)a.bx[b] < (unsigned)S && (unsigned)a.by[b] < (unsigned)S));
+    return ok;
+}
+
+// Device checks of the NX_DEBUG build (explicit bounds tests before grid
+// writes and output stores; a failed test sets NX_FLAG_BOUNDS, which nx_sync
+// reports as NX_E_DEVICE_CHECK, and skips the access -- nothing traps).  The
+// release build compiles them out.
+#ifdef NX_DEBUG
+#define NX_DCHECK(ctl, cond) ((cond) ? true : (atomicOr(&(ctl)->flags, (unsigned)NX_FLAG_BOUNDS), false))
+#else
+#define NX_DCHECK(ctl, cond) true
+#endif
+
 // L7 crossings: N rivers of lava or wall (see reset_layout), kept out of line
 // to hold down the step kernel's registers.  Its shuffles run on registers:
 // an array indexed by a loop counter would sit in local memory and be charged

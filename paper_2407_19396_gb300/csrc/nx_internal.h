@@ -27,7 +27,7 @@ struct NX_ALIGN16 nx_agent {
     uint8_t family, size;
     uint8_t mission;       // GoToDoor: colour of the target door; 255 otherwise
     uint8_t reserved;
-    uint32_t grid_offset;
+    uint32_t grid_offset;  // the low 32 bits of the env's byte offset in the grid pool
 };
 static_assert(sizeof(nx_agent) == 32, "agent block is 32 bytes");
 
@@ -35,13 +35,12 @@ static_assert(sizeof(nx_agent) == 32, "agent block is 32 bytes");
 struct NX_ALIGN16 nx_item {
     uint32_t env_begin;    // first env (index into agents)
     uint32_t n_envs;       // number of envs (<= envs_per_cta)
-    uint32_t grid_offset;  // byte offset of env_begin's planes in the grid pool
+    uint64_t grid_offset;  // byte offset of env_begin's planes in the grid pool (pools may exceed 4 GiB)
     uint32_t req;          // request record index
     uint32_t local_begin;  // index of env_begin within its request (keys, output rows)
     uint16_t max_steps;
     uint8_t family, size;
     uint32_t variant;      // rivers of a crossing family, 0 otherwise
-    uint32_t pad;
 };
 static_assert(sizeof(nx_item) == 32, "item is 32 bytes");
 

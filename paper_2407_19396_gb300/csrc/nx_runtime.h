@@ -30,7 +30,7 @@ struct nx_env {
     bool rgb = false;
     bool rgb_full = false;
     std::vector<nx_desc> descs;
-    std::vector<uint32_t> grid_offset;
+    std::vector<size_t> grid_offset;  // byte offset of each env's planes in the grid pool
     size_t grid_pool = 0;
     int max_side = 0;
     int device = 0;

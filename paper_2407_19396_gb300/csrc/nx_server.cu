@@ -27,6 +27,7 @@
 #include "navixgb.h"
 #include "nx_internal.h"
 #include "nx_runtime.h"
+#include "nx_trace.h"
 
 namespace {
 
@@ -110,6 +111,8 @@ struct SReq {
     int slot = -1;
     int launched = 0;  // steps enqueued so far
     bool admitted = false, reset_done = false;
+    bool cancel = false;  // nx_cancel on an admitted request: no further chunk
+    nvtxRangeId_t range = 0;  // NVTX range from admission to retirement
     nx_result res{};
     bool finished = false;
 };
@@ -229,7 +232,7 @@ void items_of(const nx_server* s, const SReq& q, std::vector<nx_item>& out)
         memset(&it, 0, sizeof it);
         it.env_begin = agent0 + (uint32_t)b;
         it.n_envs = (uint32_t)std::min(E, n - b);
-        it.grid_offset = (uint32_t)(q.dev_off + q.lay.grids + (size_t)b * 3 * S * S);
+        it.grid_offset = (uint64_t)(q.dev_off + q.lay.grids + (size_t)b * 3 * S * S);
         it.req = (uint32_t)q.slot;
         it.local_begin = (uint32_t)b;
         it.max_steps = (uint16_t)q.max_steps;
@@ -252,30 +255,35 @@ void retire(nx_server* s, uint64_t t)
     const uint64_t* dig = (const uint64_t*)(h + (q.lay.digest - q.lay.returns));
     const uint32_t* eps = (const uint32_t*)(h + (q.lay.episodes - q.lay.returns));
     const uint8_t* obs = h + (q.lay.obs - q.lay.returns);
+    const bool canceled = q.cancel;
     lk.unlock();
-    if (q.r.returns) memcpy(q.r.returns, ret, (size_t)n * 4);
-    if (q.r.final_obs) memcpy(q.r.final_obs, obs, (size_t)n * NX_OBS_SYM_BYTES);
     uint64_t d = 0;
     uint32_t e = 0;
-    const bool with_digest = (q.r.flags & NX_REQ_DIGEST) != 0;
-    for (int i = 0; i < n; ++i) {
-        if (with_digest) {
-            d = fold(d, (uint32_t)dig[i]);
-            d = fold(d, (uint32_t)(dig[i] >> 32));
+    if (!canceled) {
+        if (q.r.returns) memcpy(q.r.returns, ret, (size_t)n * 4);
+        if (q.r.final_obs) memcpy(q.r.final_obs, obs, (size_t)n * NX_OBS_SYM_BYTES);
+        const bool with_digest = (q.r.flags & NX_REQ_DIGEST) != 0;
+        for (int i = 0; i < n; ++i) {
+            if (with_digest) {
+                d = fold(d, (uint32_t)dig[i]);
+                d = fold(d, (uint32_t)(dig[i] >> 32));
+            }
+            e += eps[i];
         }
-        e += eps[i];
     }
     lk.lock();
     q.res.digest = d;
     q.res.episodes = e;
-    q.res.env_steps = (uint64_t)n * (uint64_t)q.r.horizon;
-    q.res.status = NX_OK;
+    q.res.env_steps = (uint64_t)n * (uint64_t)q.launched;  // the steps that ran
+    q.res.status = canceled ? NX_E_CANCELED : NX_OK;
     q.res.t_done = now_s();
+    nvtxRangeEnd(q.range);
     q.finished = true;
     s->dev_alloc.release(q.dev_off, q.lay.total);
     s->host_alloc.release(q.host_off, q.lay.tail);
     s->free_slots.push_back(q.slot);
-    s->stats.finished += 1;
+    s->stats.finished += canceled ? 0 : 1;
+    s->stats.canceled += canceled ? 1 : 0;
     s->stats.env_steps += q.res.env_steps;
     s->stats.in_use_bytes = s->dev_alloc.used;
     s->cv_done.notify_all();
@@ -296,6 +304,7 @@ bool wait_chunk(nx_server* s, Chunk& c)
 // the new one runs.  Returns false on a fatal CUDA error.
 bool iterate(nx_server* s, int& cur, bool* idle)
 {
+    nx_range range("nx_server_iteration");
     std::vector<uint64_t> fresh;
     {
         std::unique_lock<std::mutex> lk(s->mu);
@@ -315,6 +324,7 @@ bool iterate(nx_server* s, int& cur, bool* idle)
             s->free_slots.pop_back();
             q.admitted = true;
             q.res.t_start = now_s();
+            q.range = nvtxRangeStartA("nx_request");
             s->active.push_back(t);
             fresh.push_back(t);
         }
@@ -353,6 +363,15 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         }
         for (uint64_t t : s->active) {
             SReq& q = s->reqs.at(t);
+            if (q.cancel) {
+                // withdrawn: no steps in this chunk (a request admitted in this
+                // very iteration still has its reset items, which read this
+                // record); its memory is released when this chunk, queued
+                // behind every earlier use, completes
+                hr[q.slot] = record_of(s, q, 0);
+                finishing.push_back(t);
+                continue;
+            }
             const int k = std::min(s->chunk, q.r.horizon - q.launched);
             hr[q.slot] = record_of(s, q, k);
             const bool sm = q.r.n_envs <= s->small_envs;
@@ -460,7 +479,7 @@ bool iterate(nx_server* s, int& cur, bool* idle)
     }
     if (nrs + nss) SRV_CK(cudaStreamWaitEvent(s->stream, s->join_ev, 0), "join");
     for (const SReq* qp : finishing_q) {
-        const SReq& q = *qp;
+        const SReq& q = *qp;  // (requests that finish normally; withdrawn ones copy nothing back)
         SRV_CK(cudaMemcpyAsync(s->h_pool + q.host_off, s->d_pool + q.dev_off + q.lay.returns, q.lay.tail,
                                cudaMemcpyDeviceToHost, s->stream),
                "result copy");
@@ -513,7 +532,7 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
         o = *opts;
     else
         nx_options_default(&o);
-    if (budget < (1u << 20) || budget > ((size_t)4 << 30)) return nx_fail(nullptr, NX_E_INVAL, "budget must be 1 MiB..4 GiB");
+    if (budget < (1u << 20) || budget > ((size_t)1 << 40)) return nx_fail(nullptr, NX_E_INVAL, "budget must be 1 MiB..1 TiB");
     if (o.obs_flags != NX_OBS_SYM) return nx_fail(nullptr, NX_E_INVAL, "the server produces symbolic observations only");
     if (o.steps_per_launch <= 0) o.steps_per_launch = 128;
     if (o.steps_per_launch > 1024) return nx_fail(nullptr, NX_E_INVAL, "steps_per_launch must be <= 1024");
@@ -575,7 +594,9 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
     }
     // the smallest request (1 env of 5x5) needs about 1.8 KB: bound the work list by that
     s->max_items = std::min<size_t>(budget / 1536 + 1, (size_t)1 << 20);
-    const size_t host_cap = budget / 4 + (1u << 20);  // result staging: returns, digests, episodes, final views
+    // pinned result staging (returns, digests, episodes, final views: 163
+    // bytes per env in flight), at most 1 GiB whatever the budget
+    const size_t host_cap = std::min(budget / 4, (size_t)1 << 30) + (1u << 20);
     cudaError_t e = cudaMalloc(&s->d_pool, budget);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_reqs, sizeof(nx_req) * (size_t)s->max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_items, sizeof(nx_item) * s->max_items * 4);
@@ -667,6 +688,30 @@ nx_status nx_wait(nx_server* s, uint64_t ticket, nx_result* res, double timeout_
     }
     if (res) *res = q->res;
     return q->res.status;
+}
+
+nx_status nx_cancel(nx_server* s, uint64_t ticket)
+{
+    if (!s) return nx_fail(nullptr, NX_E_INVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return nx_fail(nullptr, NX_E_INVAL, "unknown ticket");
+    SReq& q = it->second;
+    if (q.finished || q.cancel || (q.admitted && q.launched >= q.r.horizon))
+        return nx_fail(nullptr, NX_E_STATE, "the request has finished or its last chunk is on the GPU");
+    if (!q.admitted) {
+        // still queued: nothing of it ever reached the GPU
+        s->waiting.erase(std::find(s->waiting.begin(), s->waiting.end(), ticket));
+        q.finished = true;
+        q.res.status = NX_E_CANCELED;
+        q.res.t_done = now_s();
+        s->stats.canceled += 1;
+        s->cv_done.notify_all();
+        s->cv_work.notify_one();
+        return NX_OK;
+    }
+    q.cancel = true;
+    return NX_OK;
 }
 
 nx_status nx_server_get_stats(nx_server* s, nx_server_stats* st)

@@ -19,6 +19,7 @@
 #include "navixgb.h"
 #include "nx_internal.h"
 #include "nx_runtime.h"
+#include "nx_trace.h"
 
 namespace {
 
@@ -90,6 +91,7 @@ size_t scratch_needed(int32_t size, int32_t n_envs)
 nx_status nx_rollout_noalloc(int32_t family, int32_t size, int32_t n_envs, uint64_t seed, int32_t n_steps,
                              int32_t act_mode, const int8_t* d_actions_TN, const nx_out* traj, void* cuda_stream)
 {
+    nx_range range("nx_rollout_noalloc");
     if (family < NX_EMPTY || family >= NX_N_FAMILIES) return nx_fail(nullptr, NX_E_INVAL, "unknown family");
     if (size < NX_MIN_SIZE || size > NX_MAX_SIZE) return nx_fail(nullptr, NX_E_INVAL, "grid size must be in 5..19");
     if (nx_max_variant(family, size) < 0) return nx_fail(nullptr, NX_E_INVAL, "the family has no grid of this size");

@@ -51,7 +51,8 @@ __device__ __forceinline__ uint64_t digest_word(uint64_t h, uint32_t w) { return
 template <int G>
 __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int W, int family, int max_steps, AgentReg& a,
                                          int action, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
-                                         float action_cost, float time_cost, float& reward, int& term, int& trunc)
+                                         float action_cost, float time_cost, float& reward, int& term, int& trunc,
+                                         nx_ctl* ctl)
 {
     // transition system: each ball, in index order, moves to a uniformly drawn
     // empty cell of its 8-neighbourhood that is not the agent's cell
@@ -81,7 +82,8 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
                 const int o = jj < 4 ? jj : jj + 1;   // position in the 3x3 block, skipping the centre
                 const int nx = a.bx[b] + (o % 3) - 1, ny = a.by[b] + (o / 3) - 1;
                 grp.sync();
-                if (grp.lane == 0) {
+                if (grp.lane == 0 && NX_DCHECK(ctl, (unsigned)nx < (unsigned)S && (unsigned)ny < (unsigned)S &&
+                                                        (unsigned)a.bx[b] < (unsigned)S && (unsigned)a.by[b] < (unsigned)S)) {
                     g[a.by[b] * W + a.bx[b]] = (uint8_t)C_EMPTY;
                     g[ny * W + nx] = (uint8_t)C_BALL_BLUE;
                 }
@@ -128,7 +130,7 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
     a.carry = pick ? fc : (drop ? 0u : a.carry);
     if (write) {
         grp.sync();
-        if (grp.lane == 0) g[fi] = (uint8_t)wcode;
+        if (grp.lane == 0 && NX_DCHECK(ctl, (unsigned)fx < (unsigned)S && (unsigned)fy < (unsigned)S)) g[fi] = (uint8_t)wcode;
         grp.sync();
     }
     // time and truncation; reward and termination on the goal / lava / hit events
@@ -392,7 +394,19 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     }
                 }
             }
-            if (active) load_agent(p.agents + env, a);
+            if (active) {
+                load_agent(p.agents + env, a);
+                if (!agent_in_range(a, S)) {
+                    // only a block corrupted in device memory gets here: flag
+                    // it (nx_sync: NX_E_DEVICE_CHECK) and continue the env from
+                    // a safe pose instead of indexing outside its grid
+                    if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    a.x = 1;
+                    a.y = 1;
+                    a.dir = 0;
+                    a.nb = 0;
+                }
+            }
         }
         if (active) {
             if (returns) ret = returns[local];
@@ -494,7 +508,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 }
                 __syncwarp();
             }
-            if (active) {
+            // (NX_DEBUG: the output row lies inside the caller's [depth, n_envs] buffers)
+            const bool row_ok = NX_DCHECK(p.ctl, !active || o < (size_t)depth * nreq);
+            if (active && row_ok) {
                 // the step's action (an env that starts an episode ignores it)
                 int action;
                 if (POL) {
@@ -524,7 +540,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                         });
                     }
                     env_step(grp, mygrid, S, W, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
-                             time_cost, reward, term, trunc);
+                             time_cost, reward, term, trunc, p.ctl);
                 }
                 // (every grid write above -- a reset, a ball move, the action's
                 // write -- ends with a group barrier, so the view sees it)
@@ -578,7 +594,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             // and the outputs that read the staged record (digest, the
             // categorical first-person view).
             if (G >= 8 && !digest && !(FULL && obs_cat_fp)) {
-                if (active && obs_sym) write_view(grp, vo, obs_sym + o * NX_OBS_SYM_BYTES);
+                if (active && row_ok && obs_sym) write_view(grp, vo, obs_sym + o * NX_OBS_SYM_BYTES);
             } else {
             // Each warp stages the symbolic outputs of its own envs (placed at
             // the same address modulo 16 as their destination) and stores them
@@ -586,7 +602,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             // each other here.
             for (int ph = 0; ph < phases; ++ph) {
                 const int lo = wenv0 + ph * whalf, hi = min(n, min(wenv0 + epw, lo + whalf));
-                uint8_t* dst = sym_dst ? sym_dst + (size_t)lo * NX_OBS_SYM_BYTES : nullptr;
+                // (NX_DEBUG: the warp's block of rows lies inside the caller's buffer)
+                const bool blk_ok = NX_DCHECK(p.ctl, hi <= lo || row0 + (size_t)hi <= (size_t)depth * nreq);
+                uint8_t* dst = (sym_dst && blk_ok) ? sym_dst + (size_t)lo * NX_OBS_SYM_BYTES : nullptr;
                 uint8_t* stage = wstage + ((uint32_t)(uintptr_t)dst & 15u);
                 if constexpr (kBulk) {
                     // the previous bulk copy out of this buffer must have read it
@@ -596,7 +614,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 if (active && gi >= lo && gi < hi) {
                     uint8_t* my_sym = stage + (gi - lo) * NX_OBS_SYM_BYTES;
                     write_view(grp, vo, my_sym);
-                    if (FULL && obs_cat_fp) {
+                    if (FULL && obs_cat_fp && row_ok) {
                         // categorical_first_person: the entity bytes of the staged view
                         grp.sync();
                         uint8_t* cf = obs_cat_fp + o * 49;
@@ -649,7 +667,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 }
             }
             }
-            if (RGB && (obs_rgb || obs_rgb_full)) {
+            // (NX_DEBUG: the item's image rows lie inside the caller's buffers)
+            if (RGB && (obs_rgb || obs_rgb_full) && NX_DCHECK(p.ctl, row0 + (size_t)n <= (size_t)depth * nreq)) {
                 __syncthreads();
                 if (obs_rgb) coop_rgb(obs_rgb + row0 * NX_OBS_RGB_BYTES, stiles, p.atlas, n, tid, nthreads);
                 if (FULL && obs_rgb_full)
@@ -667,7 +686,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         __syncthreads();
         if (active && grp.lane == 0) {
             if (a.invalid) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_INVALID_ACTION);
-            store_agent(p.agents + env, a, item, item.grid_offset + (uint32_t)(gi * 3 * HW));
+            store_agent(p.agents + env, a, item, (uint32_t)(item.grid_offset + (uint64_t)(gi * 3 * HW)));
             if (returns) returns[local] = ret;
             if (digest) digest[local] = dig;
             if (episodes) episodes[local] = eps;

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libnavixgb.so")
 
 NX_OK, NX_PENDING = 0, 1
 NX_E_INVAL, NX_E_NOMEM, NX_E_CUDA, NX_E_TIMEOUT, NX_E_DEVICE_CHECK, NX_E_BUDGET, NX_E_STATE = -1, -2, -3, -4, -5, -6, -7
+NX_E_CANCELED = -8
 (NX_EMPTY, NX_DOORKEY, NX_FOURROOMS, NX_LAVAGAP, NX_DYNOBS, NX_EMPTY_RANDOM, NX_LAVA_CROSSING, NX_SIMPLE_CROSSING,
  NX_GOTODOOR, NX_DISTSHIFT, NX_KEYCORRIDOR) = range(11)
 NX_N_FAMILIES = 11
@@ -98,7 +99,7 @@ class nx_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("finished", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("env_steps", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("busy_s", ctypes.c_double),
                 ("budget_bytes", ctypes.c_size_t), ("in_use_bytes", ctypes.c_size_t),
-                ("peak_bytes", ctypes.c_size_t)]
+                ("peak_bytes", ctypes.c_size_t), ("canceled", ctypes.c_uint64)]
 
 
 # every symbol include/navixgb.h declares, with its signature
@@ -130,6 +131,7 @@ SIGNATURES = {
     "nx_submit": (_i32, [_vp, _P(nx_request), _P(_u64)]),
     "nx_poll": (_i32, [_vp, _u64, _P(nx_result)]),
     "nx_wait": (_i32, [_vp, _u64, _P(nx_result), ctypes.c_double]),
+    "nx_cancel": (_i32, [_vp, _u64]),
     "nx_server_get_stats": (_i32, [_vp, _P(nx_server_stats)]),
     "nx_server_destroy": (None, [_vp]),
     "nx_status_str": (ctypes.c_char_p, [_i32]),
@@ -307,10 +309,11 @@ def parse_state(data: bytes) -> dict:
     ag = np.frombuffer(data, np.uint8, count=n * AGENT_BYTES, offset=64).reshape(n, AGENT_BYTES)
     grids = np.frombuffer(data, np.uint8, count=pool, offset=64 + n * AGENT_BYTES)
     envs = []
+    off = 0  # envs are stored in order; the block holds the offset's low 32 bits
     for i in range(n):
         a = ag[i]
         size = int(a[25])
-        off = int(a[28:32].view(np.uint32)[0])
+        assert int(a[28:32].view(np.uint32)[0]) == off & 0xFFFFFFFF, "snapshot grid offsets out of order"
         hw = size * size
         nb = int(a[7])
         envs.append({
@@ -323,6 +326,7 @@ def parse_state(data: bytes) -> dict:
             "ent": grids[off:off + hw].tobytes(), "col": grids[off + hw:off + 2 * hw].tobytes(),
             "st": grids[off + 2 * hw:off + 3 * hw].tobytes(),
         })
+        off += 3 * hw
     return {"n": n, "gstep": gstep, "envs": envs}
 
 
@@ -573,6 +577,10 @@ def nx_wait(h, ticket, timeout_s=0.0):
     return _result_dict(r)
 
 
+def nx_cancel(h, ticket):
+    return check(lib().nx_cancel(h, ticket))
+
+
 def nx_server_get_stats(h) -> dict:
     st = nx_server_stats()
     check(lib().nx_server_get_stats(h, ctypes.byref(st)))
@@ -631,6 +639,9 @@ class Server:
             ret, obs = self._bufs[ticket]
             res["returns"], res["final_obs"] = ret, obs
         return res
+
+    def cancel(self, ticket):
+        nx_cancel(self.h, ticket)
 
     def stats(self):
         return nx_server_get_stats(self.h)
