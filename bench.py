@@ -363,7 +363,7 @@ def serving_requests(seed, n):
     return out
 
 
-def run_serving(mixed_capacity=None, n_req=2000, budget=2 << 30, load=0.7, seed=4, chunk=64):
+def run_serving(mixed_capacity=None, n_req=2000, budget=16 << 30, load=0.7, seed=4, chunk=64):
     """Poisson arrivals of the serving mix; returns latency percentiles and
     throughput.  The arrival rate is `load` x the measured capacity of the
     65,536-env mixed configuration (its env-steps/s, when given), and, as a

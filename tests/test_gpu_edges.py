@@ -95,6 +95,55 @@ def test_paper_batch_scale_sampled():
     env.close()
 
 
+def test_state_pool_beyond_4_gib():
+    """4,000,000 FourRooms-19x19 envs: a 4.33 GB grid pool, so the envs past
+    index 3,965,000 have their planes beyond the first 4 GiB (64-bit work
+    item offsets); sampled envs on both sides of that mark, after 6 steps
+    with a 1-slot ring, equal the oracle."""
+    nx = nxmod()
+    n, T = 4_000_000, 6
+    assert n * 3 * 19 * 19 > 1 << 32
+    env = nx.Env(O.FOURROOMS, 19, n, seed=15, autotune=False, group_lanes=1, envs_per_cta=64)
+    env.reset()
+    out = env.rollout(T, depth=1)
+    edge = (1 << 32) // (3 * 19 * 19)
+    sample = sorted(set([0, 1, edge - 2, edge - 1, edge, edge + 1, n - 2, n - 1] + list(range(12345, n, 333331))))
+    idx = torch.tensor(sample, device="cuda")
+    got = {k: out[k].index_select(1, idx).cpu().numpy() for k in ("obs_sym", "reward", "terminated", "truncated")}
+    del out
+    ob = O.Batch([O.FOURROOMS] * len(sample), [19] * len(sample), seed=15, env_indices=sample)
+    ob.reset()
+    oo = ob.rollout(T)
+    want = {k: oo[k][T - 1:] for k in ("obs_sym", "reward", "terminated", "truncated")}
+    assert_outputs_equal(got, want, what="4M FourRooms-19 envs, last step")
+    env.close()
+
+
+def test_server_places_requests_beyond_4_gib():
+    """A 16 GiB serving budget: a blocker request of 3.4 M FourRooms-19x19
+    envs (about 4.4 GB) takes the start of the pool, so the next request's
+    block lies past the first 4 GiB; its result equals the oracle's, and the
+    blocker is then withdrawn."""
+    from tests.gpu_util import oracle_request
+
+    nx = nxmod()
+    srv = nx.Server(budget_bytes=16 << 30, steps_per_launch=64)
+    blocker = srv.submit(O.FOURROOMS, 19, 3_400_000, 100000, 21, digest=False)
+    small = srv.submit(O.DOORKEY, 9, 300, 77, 22)
+    res = srv.wait(small, timeout_s=300.0)
+    want = oracle_request(O.DOORKEY, 9, 300, 77, 22)
+    np.testing.assert_array_equal(res["returns"], want["returns"])
+    np.testing.assert_array_equal(res["final_obs"], want["final_obs"])
+    assert res["digest"] == want["digest"] and res["episodes"] == want["episodes"]
+    assert srv.stats()["peak_bytes"] > (4 << 30)
+    srv.cancel(blocker)
+    with pytest.raises(nx.NavixError) as ei:
+        srv.wait(blocker, timeout_s=300.0)
+    assert ei.value.status == nx.NX_E_CANCELED
+    assert srv.stats()["in_use_bytes"] == 0
+    srv.close()
+
+
 @pytest.mark.parametrize("lanes,envs", [(1, 64), (16, 4)])
 def test_tiny_max_steps_truncate_every_few_steps(lanes, envs):
     """max_steps 1, 2 and 3 (a truncation on every step or every few, so an
