@@ -552,7 +552,8 @@ def main():
     ap.add_argument("--workload", default="mixed", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the other configs and the CPU baseline")
     ap.add_argument("--ncu-case", action="store_true", help="one rollout of the workload for an ncu capture")
-    ap.add_argument("--shape", default="", help="force the launch shape as LANES,ENVS_PER_CTA[,STAGING] (no autotuning)")
+    ap.add_argument("--shape", default="", help="force the launch shape as LANES,ENVS_PER_CTA[,STAGING[,GRID_SIDE]] "
+                                               "(no autotuning)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.ncu_case:
         args.warmup = 3
@@ -580,7 +581,7 @@ def main():
     if args.shape:
         vals = [int(v) for v in args.shape.split(",")]
         shape = dict(group_lanes=vals[0], envs_per_cta=vals[1], staging=vals[2] if len(vals) > 2 else 1,
-                     autotune=False)
+                     autotune=False, grid_side=vals[3] if len(vals) > 3 else 0)
     if "steps_per_launch" in w:
         shape["steps_per_launch"] = w["steps_per_launch"]
     fv = bool(w.get("full"))
@@ -640,7 +641,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": w["desc"], "n_envs_per_gpu": n, "env_steps_per_bench_step": n * w["T"] * world,
-                   "steps_per_launch": C, "launch_shape": {k: env.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas")},
+                   "steps_per_launch": C,
+                   "launch_shape": {k: env.info()[k] for k in ("group_lanes", "envs_per_cta", "grid_ctas", "grid_side")},
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": all_launches, "clocks": clk,
         "wall_s": wall,

@@ -135,6 +135,11 @@ typedef struct {
      * time_cost (default 0 and 0; not applied to autoreset steps) */
     float action_cost;
     float time_cost;
+    /* shared-memory slots of the step kernel sized for grids of this side
+     * (0: chosen by the autotuner with the launch shape, else the largest
+     * side of the batch); work items of larger grids then hold fewer envs.
+     * Results never depend on it. */
+    int32_t grid_side;
 } nx_options;
 
 /* Per-step outputs, device pointers owned by the caller; any may be NULL (not
@@ -188,6 +193,7 @@ typedef struct {
     size_t state_bytes, device_bytes;
     int32_t policy_items, policy_ctas_per_sm, policy_grid_ctas, policy_smem_bytes;
     int32_t lean_family, lean_grid_ctas;
+    int32_t grid_side;   /* the grid side the block's shared-memory slots are sized for */
 } nx_info;
 
 void nx_options_default(nx_options* opts);

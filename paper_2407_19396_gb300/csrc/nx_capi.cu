@@ -179,9 +179,10 @@ static nx_status validate_desc(const nx_desc& d, int n_balls, std::string* why)
     return NX_OK;
 }
 
-// Splits the env list into runs of equal descriptors and runs into items of
-// at most E envs.
-std::vector<nx_item> nx_build_items(const nx_env* env, int E)
+// Splits the env list into runs of equal descriptors and runs into items:
+// envs_per_cta envs each, or fewer for grids larger than ref_side (their
+// slots are larger, the block's grid region the same; nx_item_envs).
+std::vector<nx_item> nx_build_items(const nx_env* env, const nx_launch_shape& s, int ref_side)
 {
     std::vector<nx_item> items;
     const int n = env->n_envs;
@@ -192,6 +193,7 @@ std::vector<nx_item> nx_build_items(const nx_env* env, int E)
         while (j < n && env->descs[j].family == d.family && env->descs[j].height == d.height &&
                env->descs[j].max_steps == d.max_steps && env->descs[j].variant == d.variant)
             ++j;
+        const int E = nx_item_envs(s, ref_side, d.height);
         for (int b = i; b < j; b += E) {
             nx_item it;
             memset(&it, 0, sizeof it);
@@ -273,6 +275,7 @@ static nx_status create_common(nx_env** out, std::vector<nx_desc>&& descs, uint6
         seen[env->descs[i].family] = true;
     }
     env->grid_pool = off;
+    env->grid_side = o.grid_side > 0 ? std::min(std::max((int)o.grid_side, (int)NX_MIN_SIZE), env->max_side) : env->max_side;
     env->n_families = 0;
     for (bool b : seen) env->n_families += b ? 1 : 0;
     env->lean_family = env->n_families == 1 ? (int)env->descs[0].family : NX_N_FAMILIES;
@@ -355,10 +358,10 @@ nx_status nx_apply_shape(nx_env* env, const nx_launch_shape& s)
 {
     if (!nx_shape_supported(s)) return nx_fail(env, NX_E_INVAL, "unsupported launch shape");
     int err = 0;
-    const int per_sm = nx_kernel_max_ctas(s, env->max_side, &err);
+    const int per_sm = nx_kernel_max_ctas(s, env->grid_side, &err);
     if (err) return nx_cuda_fail(env, err, "occupancy query");
     if (per_sm < 1) return nx_fail(env, NX_E_INVAL, "launch shape does not fit on an SM");
-    std::vector<nx_item> items = nx_build_items(env, s.envs_per_cta);
+    std::vector<nx_item> items = nx_build_items(env, s, env->grid_side);
     // family-ordered copy for the per-family form
     std::vector<nx_item> fam;
     std::vector<int> fam_begin(NX_N_FAMILIES + 1, 0);
@@ -411,7 +414,8 @@ nx_kparams nx_params(const nx_env* env, int launch_steps, int reset_all)
     p.reqs = env->d_req;
     p.ctl = env->d_ctl;
     p.atlas = env->d_atlas;
-    p.cell_stride = nx_slot_stride(env->shape, env->max_side);
+    p.cell_stride = nx_slot_stride(env->shape, env->grid_side);
+    p.item_strides = env->grid_side < env->max_side ? 1 : 0;
     p.envs_per_cta = env->shape.envs_per_cta;
     p.reset_all = reset_all;
     p.phases = env->shape.phases;
@@ -461,7 +465,7 @@ static bool lean_shape(const nx_env* env, nx_launch_shape* s, int* grid)
     if (!nx_lean_supported(ls)) return false;
     if (env->per_sm_lean == 0) {
         int err = 0;
-        const int n = nx_kernel_max_ctas(ls, env->max_side, &err);
+        const int n = nx_kernel_max_ctas(ls, env->grid_side, &err);
         if (err) cudaGetLastError();
         env->per_sm_lean = (!err && n >= 1) ? n : -1;  // the general kernel serves where it is unavailable
     }
@@ -489,7 +493,7 @@ static nx_status shape_for(nx_env* env, bool full, nx_launch_shape* s, int* grid
     s->full = true;
     if (env->per_sm_full <= 0) {
         int err = 0;
-        env->per_sm_full = nx_kernel_max_ctas(*s, env->max_side, &err);
+        env->per_sm_full = nx_kernel_max_ctas(*s, env->grid_side, &err);
         if (err) return nx_cuda_fail(env, err, "occupancy query");
         if (env->per_sm_full < 1) return nx_fail(env, NX_E_INVAL, "launch shape does not fit on an SM");
     }
@@ -510,6 +514,7 @@ static nx_status launch_chunk(nx_env* env, int steps, cudaStream_t st, bool full
         p.n_items = env->n_items_pol;
         p.envs_per_cta = nxp::kRows;
         p.cell_stride = nx_slot_stride(s, env->max_side);
+        p.item_strides = 0;  // the policy's work list: 128 envs per item, uniform slots
         p.policy_agents = env->policy_agents;
         p.phases = 1;
         p.rgb_full_side = 0;
@@ -749,7 +754,7 @@ nx_status nx_set_policy(nx_env* env, const nx_policy* pol)
     if (epa < (uint64_t)nxp::kRows && (epa < 16 || nxp::kRows % epa != 0))
         return nx_fail(env, NX_E_INVAL, "envs_per_agent must be 16, 32, 64 or at least 128");
     const int agents = epa < (uint64_t)nxp::kRows ? (int)(nxp::kRows / epa) : 1;
-    std::vector<nx_item> items = nx_build_items(env, nxp::kRows);
+    std::vector<nx_item> items = nx_build_items(env, nx_launch_shape{1, nxp::kRows, 0}, env->max_side);
     for (const nx_item& it : items) {
         const uint64_t first = base + it.local_begin, last = first + it.n_envs - 1;
         if (epa >= (uint64_t)nxp::kRows ? first / epa != last / epa : first % epa != 0)
@@ -975,12 +980,28 @@ nx_status nx_autotune(nx_env* env)
     NX_CK(env, cudaEventCreate(&e1), "event");
     const nx_launch_shape orig = env->shape;
     nx_launch_shape best = orig;
+    int best_side = env->grid_side;
     float best_ms = 1e30f;
+    // slot sides to try: the largest grid's (every item holds envs_per_cta
+    // envs), and the next largest side of the batch (items of the largest
+    // grids hold fewer envs, every block needs less shared memory); an
+    // explicit nx_options.grid_side is kept
+    std::vector<int> sides{env->max_side};
+    if (env->opt.grid_side <= 0) {
+        int next = 0;
+        for (const nx_desc& d : env->descs)
+            if (d.height < env->max_side) next = std::max(next, d.height);
+        if (next > 0) sides.push_back(next);
+    } else {
+        sides[0] = env->grid_side;
+    }
+    for (int side : sides)
     for (int G : lanes)
         for (int th : threads)
             for (int ph = 1; ph <= 2; ++ph) {
             nx_launch_shape s{G, th / G, env->rgb ? 1 : 0, ph, env->rgb_full ? env->max_side : 0};
             if (!nx_shape_supported(s)) continue;
+            env->grid_side = side;
             if (nx_apply_shape(env, s) != NX_OK) {
                 cudaGetLastError();
                 continue;
@@ -1013,6 +1034,7 @@ nx_status nx_autotune(nx_env* env)
             if (ms_min < best_ms) {
                 best_ms = ms_min;
                 best = s;
+                best_side = side;
             }
             env->tune_log.push_back(nx_tune_entry{s.group_lanes, s.envs_per_cta, ms_min});
             }
@@ -1020,6 +1042,7 @@ nx_status nx_autotune(nx_env* env)
     cudaEventDestroy(e1);
     cudaStreamSynchronize(env->stream);
     for (void* q : {(void*)sa, (void*)sg, (void*)sr, (void*)so, (void*)srgb, (void*)srew, (void*)sflag}) nx_dev_free(env, q);
+    env->grid_side = best_side;
     return nx_apply_shape(env, best);
 }
 
@@ -1137,7 +1160,8 @@ nx_status nx_get_info(const nx_env* env, nx_info* info)
     info->staging = env->shape.phases > 1 ? NX_STAGE_HALF : NX_STAGE_FULL;
     info->n_items = env->n_items;
     info->grid_ctas = env->grid_ctas;
-    info->smem_bytes = nx_kernel_smem_bytes(env->shape, env->max_side);
+    info->smem_bytes = nx_kernel_smem_bytes(env->shape, env->grid_side);
+    info->grid_side = env->grid_side;
     info->steps_per_launch = env->opt.steps_per_launch;
     info->n_envs = env->n_envs;
     info->n_families = env->n_families;

@@ -100,12 +100,16 @@ struct nx_kparams {
     nx_req* reqs;
     nx_ctl* ctl;
     const uint8_t* atlas;
-    int32_t cell_stride;   // smem bytes per env slot (nx_slot_stride of the launch shape)
+    int32_t cell_stride;   // smem bytes per env slot (nx_slot_stride of the launch shape and its reference side)
+    // nonzero: each work item's slots are sized for its own grid side (an
+    // item of a grid larger than the reference side holds fewer envs, so
+    // that its slots fit the block's region of envs_per_cta * cell_stride)
     int32_t envs_per_cta;
     int32_t reset_all;     // 1: start every env at episode 0 and emit its observation (no steps)
     int32_t phases;        // symbolic staging parts per step (1 or 2)
     int32_t rgb_full_side; // side of the smem full-view tile buffer (0: none)
     int32_t policy_agents; // fused policy: weight sets per 128-env block (1, 2, 4 or 8)
+    int32_t item_strides;
 };
 
 // Host-side launch helpers implemented in nx_kernels.cu.
@@ -123,7 +127,12 @@ struct nx_launch_shape {
 // Shared-memory bytes per env grid for grids of up to max_cells cells: a
 // whole number of 4-byte words, and an odd one, so that the grids of the 32
 // envs a warp steps one lane each start in 32 different banks.
-inline int nx_cell_stride(int max_cells)
+#ifdef __CUDACC__
+#define NX_HD __host__ __device__
+#else
+#define NX_HD
+#endif
+NX_HD inline int nx_cell_stride(int max_cells)
 {
     const int s = (max_cells + 3) & ~3;
     return ((s >> 2) & 1) ? s : s + 4;
@@ -133,10 +142,20 @@ inline int nx_cell_stride(int max_cells)
 #define NX_VIEW_PAD 6
 // Bytes per env slot of a launch shape for grids of side up to max_side
 // (nx_kparams::cell_stride).
-inline int nx_slot_stride(const nx_launch_shape& s, int max_side)
+NX_HD inline int nx_side_stride(int group_lanes, int side)
 {
-    const int side = s.group_lanes >= 8 ? max_side + 2 * NX_VIEW_PAD : max_side;
-    return nx_cell_stride(side * side);
+    const int w = group_lanes >= 8 ? side + 2 * NX_VIEW_PAD : side;
+    return nx_cell_stride(w * w);
+}
+inline int nx_slot_stride(const nx_launch_shape& s, int max_side) { return nx_side_stride(s.group_lanes, max_side); }
+// Envs per work item for grids of side `side` in a launch whose blocks hold
+// envs_per_cta slots sized for `ref_side`: all of them for grids up to the
+// reference side, as many as fit the same region for larger ones.
+inline int nx_item_envs(const nx_launch_shape& s, int ref_side, int side)
+{
+    if (side <= ref_side) return s.envs_per_cta;
+    const int n = s.envs_per_cta * nx_slot_stride(s, ref_side) / nx_slot_stride(s, side);
+    return n < 1 ? 1 : n;
 }
 int nx_kernel_smem_bytes(const nx_launch_shape& s, int max_side);
 int nx_kernel_max_ctas(const nx_launch_shape& s, int max_side, int* err);  // resident CTAs on the device

@@ -33,6 +33,9 @@ struct nx_env {
     std::vector<size_t> grid_offset;  // byte offset of each env's planes in the grid pool
     size_t grid_pool = 0;
     int max_side = 0;
+    // slots are sized for grids of this side (<= max_side): items of larger
+    // grids hold fewer envs (nx_item_envs); chosen by the autotuner
+    int grid_side = 0;
     int device = 0;
     int sm_count = 0;
     cudaStream_t stream = nullptr;
@@ -102,7 +105,7 @@ void* nx_dev_alloc(nx_env* env, size_t bytes);
 void nx_dev_free(nx_env* env, void* p);
 void nx_dev_free_all(nx_env* env);
 int nx_default_max_steps(int family, int size);
-std::vector<nx_item> nx_build_items(const nx_env* env, int E);
+std::vector<nx_item> nx_build_items(const nx_env* env, const nx_launch_shape& s, int ref_side);
 nx_status nx_apply_shape(nx_env* env, const nx_launch_shape& s);
 void nx_drop_graphs(nx_env* env);
 nx_kparams nx_params(const nx_env* env, int launch_steps, int reset_all);

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     // One lane per env reads its view cells without bounds tests
     // (render_view), so guards pad its grid region on both sides.
     constexpr bool kGuard = G == 1;
-    const int cs = p.cell_stride;  // bytes per env slot
+    const int cs = p.cell_stride;  // bytes per env slot of the reference side (the block's grid region)
     const int grid_bytes = align16(kGuard ? E * cs + 2 * kGridGuard : E * cs);  // the staging after it is 16-aligned
     uint8_t* sgrid = smem + (kGuard ? kGridGuard : 0);
     uint8_t* wstage = smem + grid_bytes + warp * wbytes;
@@ -343,7 +343,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 
         const int n = (int)item.n_envs, S = item.size, HW = S * S, variant = (int)item.variant;
         const int W = S + 2 * kPad;                                 // row stride of the env's grid in its slot
-        uint8_t* mygrid = sgrid + gi * cs + kPad * (W + 1);         // cell (0, 0)
+        const int ics = p.item_strides ? nx_side_stride(G, S) : cs;  // this item's bytes per env slot
+        uint8_t* mygrid = sgrid + gi * ics + kPad * (W + 1);        // cell (0, 0)
         const int family = (kLean && FAM < NX_N_FAMILIES) ? FAM : (int)item.family;
         const int max_steps = item.max_steps;
         const bool active = gi < n;
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         if constexpr (kPad > 0) {
             // every slot starts as walls (the margins stay so)
             constexpr uint32_t kWall4 = C_WALL * 0x01010101u;
-            for (int i = tid; i < n * cs / 4; i += nthreads) reinterpret_cast<uint32_t*>(sgrid)[i] = kWall4;
+            for (int i = tid; i < n * ics / 4; i += nthreads) reinterpret_cast<uint32_t*>(sgrid)[i] = kWall4;
             __syncthreads();
         }
         // i / HW and c / S by multiply-high with ceil(2^32 / d): exact for
@@ -388,10 +389,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     const int i = i0 + u * nthreads;
                     if (i < nhw) {
                         const int e = (int)__umulhi((uint32_t)i, inv_hw), c = i - e * HW;
-                        int si = e * cs + c;  // a packed grid: row stride S
+                        int si = e * ics + c;  // a packed grid: row stride S
                         if constexpr (kPad > 0) {
                             const int y = (int)__umulhi((uint32_t)c, inv_s), x = c - y * S;
-                            si = e * cs + (y + kPad) * W + x + kPad;
+                            si = e * ics + (y + kPad) * W + x + kPad;
                         }
                         sgrid[si] = (uint8_t)pack_cell(pe[u], pc[u], ps[u]);
                     }
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     const uint32_t ep = __shfl_sync(0xFFFFFFFFu, p.reset_all ? 0u : a.episode + 1u, L);
                     const uint32_t k = __shfl_sync(0xFFFFFFFFu, key, L);
                     const int owner = ((tid & ~31) + L) / G;  // group (env slot) of lane L
-                    const uint4 r = reset_layout_warp<FAM>(sgrid + owner * cs, S, family, n_balls, variant, seed, k, ep);
+                    const uint4 r = reset_layout_warp<FAM>(sgrid + owner * ics, S, family, n_balls, variant, seed, k, ep);
                     if (!(r.y & 0x100u) && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
                     if (gi == owner) {
                         // the new episode's start; the invalid-action flag is sticky
@@ -698,10 +699,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             uint8_t* dst = p.grids + item.grid_offset;
             for (int i = tid; i < n * HW; i += nthreads) {
                 const int e = (int)__umulhi((uint32_t)i, inv_hw), c = i - e * HW;
-                int si = e * cs + c;
+                int si = e * ics + c;
                 if constexpr (kPad > 0) {
                     const int y = (int)__umulhi((uint32_t)c, inv_s), x = c - y * S;
-                    si = e * cs + (y + kPad) * W + x + kPad;
+                    si = e * ics + (y + kPad) * W + x + kPad;
                 }
                 const uint32_t code = sgrid[si];
                 uint8_t* b = dst + (size_t)e * 3 * HW;

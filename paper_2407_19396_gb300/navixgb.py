@@ -52,7 +52,7 @@ class nx_options(ctypes.Structure):
                 ("group_lanes", ctypes.c_int32), ("envs_per_cta", ctypes.c_int32), ("staging", ctypes.c_int32),
                 ("atlas", ctypes.POINTER(ctypes.c_uint8)), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_user", ctypes.c_void_p), ("env_index_base", ctypes.c_uint32), ("variant", ctypes.c_int32),
-                ("action_cost", ctypes.c_float), ("time_cost", ctypes.c_float)]
+                ("action_cost", ctypes.c_float), ("time_cost", ctypes.c_float), ("grid_side", ctypes.c_int32)]
 
 
 class nx_out(ctypes.Structure):
@@ -80,7 +80,7 @@ class nx_info(ctypes.Structure):
                 ("state_bytes", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
                 ("policy_items", ctypes.c_int32), ("policy_ctas_per_sm", ctypes.c_int32),
                 ("policy_grid_ctas", ctypes.c_int32), ("policy_smem_bytes", ctypes.c_int32),
-                ("lean_family", ctypes.c_int32), ("lean_grid_ctas", ctypes.c_int32)]
+                ("lean_family", ctypes.c_int32), ("lean_grid_ctas", ctypes.c_int32), ("grid_side", ctypes.c_int32)]
 
 
 class nx_request(ctypes.Structure):
@@ -345,7 +345,7 @@ class Env:
                  atlas=None, reward_mode=NX_REWARD_MARKOV, lava_reward=0.0, n_balls=4, steps_per_launch=128,
                  autotune=True, group_lanes=0, envs_per_cta=0, staging=0, env_index_base=0, variant=0,
                  obs_full=False, obs_cat=False, obs_cat_fp=False, obs_rgb_full=False, mission=None,
-                 action_cost=0.0, time_cost=0.0, action=False, torch_allocator=True):
+                 action_cost=0.0, time_cost=0.0, action=False, torch_allocator=True, grid_side=0):
         import torch
 
         self.torch = torch
@@ -360,6 +360,7 @@ class Env:
         o.lava_reward = lava_reward
         o.action_cost = action_cost
         o.time_cost = time_cost
+        o.grid_side = grid_side
         o.n_balls = n_balls
         o.steps_per_launch = steps_per_launch
         o.autotune = 1 if autotune else 0

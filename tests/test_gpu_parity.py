@@ -395,6 +395,29 @@ def test_host_ring_holds_the_last_steps(depth):
     e.close()
 
 
+@pytest.mark.parametrize("lanes,envs,side", [(1, 64, 8), (1, 32, 16), (4, 16, 7), (8, 8, 11), (16, 4, 5), (32, 2, 9)])
+def test_slots_sized_below_the_largest_grid(lanes, envs, side):
+    """Shared-memory slots sized for a grid side below the batch's largest:
+    items of larger grids hold fewer envs (down to one per block), their
+    slots laid out at their own size; every step of every env, with RGB
+    tiles, equals the oracle."""
+    nx = nxmod()
+    atlas = inputs.atlas()
+    descs = mixed_descs(150, [(O.EMPTY, 5), (O.DOORKEY, 8), (O.FOURROOMS, 19), (O.DYNOBS, 11), (O.LAVAGAP, 7),
+                              (O.KEYCORRIDOR, 19, 0, 2), (O.DOORKEY, 16)])
+    env = nx.Env(descs=descs, seed=37, obs_rgb=True, atlas=atlas, autotune=False, group_lanes=lanes,
+                 envs_per_cta=envs, steps_per_launch=16, grid_side=side)
+    assert env.info()["grid_side"] == side
+    r = env.reset()
+    out = env.rollout(40)
+    ob = oracle_batch_for(descs, 37)
+    assert_outputs_equal(r, ob.reset(rgb=True, atlas=atlas), keys=("obs_sym", "obs_rgb"), what="reset")
+    assert_outputs_equal(out, ob.rollout(40, rgb=True, atlas=atlas),
+                         keys=("obs_sym", "obs_rgb", "reward", "terminated", "truncated"), what=f"G={lanes} side {side}")
+    assert_states_equal(env.state()["envs"], ob, what="final")
+    env.close()
+
+
 @pytest.mark.parametrize("reward_mode,lava", [(1, 0.0), (0, -1.0), (1, -1.0)])
 def test_reward_variants(reward_mode, lava):
     nx = nxmod()
