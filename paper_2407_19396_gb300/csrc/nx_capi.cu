@@ -965,7 +965,8 @@ nx_status nx_autotune(nx_env* env)
     uint8_t* sflag = (uint8_t*)nx_dev_alloc(env, N * 2);
     if (!sa || !sg || !sr || !so || !srew || !sflag || (env->rgb && !srgb))
         return nx_fail(env, NX_E_NOMEM, "autotune scratch allocation failed");
-    const int T = std::min(env->opt.steps_per_launch, 32);
+    // 64-step trials (32-step ones could not separate shapes 1-2 % apart)
+    const int T = std::min(env->opt.steps_per_launch, 64);
     nx_out o;
     memset(&o, 0, sizeof o);
     o.obs_sym = so;
@@ -1018,7 +1019,7 @@ nx_status nx_autotune(nx_env* env)
             p.reqs = sr;
             float ms_min = 1e30f;
             bool ok = true;
-            for (int rep = 0; rep < 3 && ok; ++rep) {
+            for (int rep = 0; rep < 4 && ok; ++rep) {
                 ok = cudaMemcpyAsync(sa, env->d_agents, sizeof(nx_agent) * N, cudaMemcpyDeviceToDevice, env->stream) == cudaSuccess &&
                      cudaMemcpyAsync(sg, env->d_grids, env->grid_pool, cudaMemcpyDeviceToDevice, env->stream) == cudaSuccess &&
                      nx_launch_configure(sr, r, 1, env->stream) == 0 && cudaEventRecord(e0, env->stream) == cudaSuccess &&

@@ -250,8 +250,17 @@ struct AgentReg {
     uint32_t episode;
     uint32_t mission;  // GoToDoor target colour, NX_NO_MISSION otherwise
     int nb;
-    int bx[4], by[4];
+    uint32_t bxp, byp;  // ball b's column / row in byte b (two registers for the four balls)
 };
+
+__device__ __forceinline__ int ball_x(const AgentReg& a, int b) { return (int)((a.bxp >> (8 * b)) & 0xFFu); }
+__device__ __forceinline__ int ball_y(const AgentReg& a, int b) { return (int)((a.byp >> (8 * b)) & 0xFFu); }
+__device__ __forceinline__ void set_ball(AgentReg& a, int b, int x, int y)
+{
+    const uint32_t m = ~(0xFFu << (8 * b));
+    a.bxp = (a.bxp & m) | ((uint32_t)x << (8 * b));
+    a.byp = (a.byp & m) | ((uint32_t)y << (8 * b));
+}
 
 __device__ __forceinline__ void load_agent(const nx_agent* src, AgentReg& a)
 {
@@ -268,11 +277,8 @@ __device__ __forceinline__ void load_agent(const nx_agent* src, AgentReg& a)
     a.t = w0.z & 0xFFFF;
     a.episode = w0.w;
     a.mission = (w1.z >> 16) & 0xFF;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        a.bx[b] = (w1.x >> (8 * b)) & 0xFF;
-        a.by[b] = (w1.y >> (8 * b)) & 0xFF;
-    }
+    a.bxp = w1.x;
+    a.byp = w1.y;
 }
 
 // Writes the agent block; the descriptor fields (max_steps, family, size,
@@ -285,13 +291,8 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
     w0.y = cc | ((uint32_t)a.done << 8) | ((uint32_t)a.invalid << 16) | ((uint32_t)a.nb << 24);
     w0.z = (uint32_t)a.t | ((uint32_t)it.max_steps << 16);
     w0.w = a.episode;
-    w1.x = 0;
-    w1.y = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        w1.x |= (uint32_t)a.bx[b] << (8 * b);
-        w1.y |= (uint32_t)a.by[b] << (8 * b);
-    }
+    w1.x = a.bxp;
+    w1.y = a.byp;
     w1.z = (uint32_t)it.family | ((uint32_t)it.size << 8) | (a.mission << 16);
     w1.w = grid_offset;
     reinterpret_cast<uint4*>(dst)[0] = w0;
@@ -308,7 +309,7 @@ __device__ __forceinline__ bool agent_in_range(const AgentReg& a, int S)
     bool ok = (unsigned)a.x < (unsigned)S && (unsigned)a.y < (unsigned)S && (unsigned)a.dir < 4u && (unsigned)a.nb <= 4u;
 #pragma unroll
     for (int b = 0; b < 4; ++b)
-        ok = ok && (b >= a.nb || ((unsigned)a.bx[b] < (unsigned)S && (unsigned)a.by[b] < (unsigned)S));
+        ok = ok && (b >= a.nb || ((unsigned)ball_x(a, b) < (unsigned)S && (unsigned)ball_y(a, b) < (unsigned)S));
     return ok;
 }
 
@@ -490,11 +491,8 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
     a.episode = episode;
     a.mission = NX_NO_MISSION;
     a.nb = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        a.bx[b] = 0;
-        a.by[b] = 0;
-    }
+    a.bxp = 0u;
+    a.byp = 0u;
     uint32_t d[8];
     const int n_draws = family == NX_DOORKEY ? 5 : family == NX_FOURROOMS ? 7 : family == NX_LAVAGAP ? 2
                         : family == NX_EMPTY_RANDOM ? 2
@@ -611,7 +609,7 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
         a.nb = n_balls;
         // ball b's column / row go to byte b of px / py and its draw k = b is
         // taken in the loop, so that no array is indexed by the loop counter
-        // (that would move a.bx / a.by and the draws to local memory)
+        // (that would move the draws to local memory)
         uint32_t px = 0, py = 0;
         for (int b = 0; b < n_balls; ++b) {
             const uint32_t db = draw(seed, key_env, episode, 0u, PURPOSE_LAYOUT, (uint32_t)b);
@@ -625,11 +623,8 @@ __device__ __forceinline__ bool reset_layout(const Grp<G>& grp, uint8_t* g, int 
             px |= (uint32_t)(bc - by * W) << (8 * b);
             py |= (uint32_t)by << (8 * b);
         }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            a.bx[b] = (px >> (8 * b)) & 0xFFu;
-            a.by[b] = (py >> (8 * b)) & 0xFFu;
-        }
+        a.bxp = px;
+        a.byp = py;
     }
     grp.sync();
     return true;
@@ -653,13 +648,8 @@ __device__ __noinline__ uint4 reset_layout_warp(uint8_t* g, int S, int family, i
     uint4 r;
     r.x = (uint32_t)a.x | ((uint32_t)a.y << 8) | ((uint32_t)a.dir << 16) | (a.mission << 24);
     r.y = (uint32_t)a.nb | (ok ? 0x100u : 0u);
-    r.z = 0u;
-    r.w = 0u;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        r.z |= (uint32_t)a.bx[b] << (8 * b);
-        r.w |= (uint32_t)a.by[b] << (8 * b);
-    }
+    r.z = a.bxp;
+    r.w = a.byp;
     return r;
 }
 
@@ -708,9 +698,8 @@ __device__ const OccTable occ_table = make_occ_table();
 // G = 1 evaluates occ_row directly, which measures faster there than either
 // table (its single thread per env is bound by the latency of the chain).
 // ROWS7: one lane per env evaluates all seven rows without a branch (a zero
-// seed gives a zero row) -- measured 2-9 % faster in the kernels compiled for
-// one family, slower in the one for several families, which keeps the loop
-// that stops at the first dark row.
+// seed gives a zero row) -- measured 1-9 % faster in the lean kernels; the
+// general one keeps the loop that stops at the first dark row.
 template <int G, bool ROWS7 = false>
 __device__ __forceinline__ uint64_t occlusion(uint64_t tmask, const uint16_t* tab)
 {

@@ -67,7 +67,7 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
 #pragma unroll
                 for (int dx = -1; dx <= 1; ++dx) {
                     if (dx == 0 && dy == 0) continue;
-                    const int x = a.bx[b] + dx, y = a.by[b] + dy;
+                    const int x = ball_x(a, b) + dx, y = ball_y(a, b) + dy;
                     const bool f = (unsigned)x < (unsigned)S && (unsigned)y < (unsigned)S && g[y * W + x] == C_EMPTY &&
                                    !(x == a.x && y == a.y);
                     cand |= (f ? 1u : 0u) << j;
@@ -80,16 +80,16 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
                 for (int i = 0; i < k; ++i) c &= c - 1u;
                 const int jj = __ffs(c) - 1;          // 0..7 over the 8 neighbours, row-major
                 const int o = jj < 4 ? jj : jj + 1;   // position in the 3x3 block, skipping the centre
-                const int nx = a.bx[b] + (o % 3) - 1, ny = a.by[b] + (o / 3) - 1;
+                const int bx = ball_x(a, b), by = ball_y(a, b);
+                const int nx = bx + (o % 3) - 1, ny = by + (o / 3) - 1;
                 grp.sync();
                 if (grp.lane == 0 && NX_DCHECK(ctl, (unsigned)nx < (unsigned)S && (unsigned)ny < (unsigned)S &&
-                                                        (unsigned)a.bx[b] < (unsigned)S && (unsigned)a.by[b] < (unsigned)S)) {
-                    g[a.by[b] * W + a.bx[b]] = (uint8_t)C_EMPTY;
+                                                        (unsigned)bx < (unsigned)S && (unsigned)by < (unsigned)S)) {
+                    g[by * W + bx] = (uint8_t)C_EMPTY;
                     g[ny * W + nx] = (uint8_t)C_BALL_BLUE;
                 }
                 grp.sync();
-                a.bx[b] = nx;
-                a.by[b] = ny;
+                set_ball(a, b, nx, ny);
             }
         }
     }
@@ -241,9 +241,9 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 {
     static_assert(!POL || (G == 1 && !RGB && !FULL), "the fused policy runs one lane per env");
     constexpr bool kLean = FAM >= 0, kLeanRandom = kLean && !POL;
-    // the kernels compiled for one family evaluate every occlusion row
-    // without a branch (one lane per env; see occlusion())
-    constexpr bool kRows7 = kLean && FAM < NX_N_FAMILIES;
+    // the lean kernels evaluate every occlusion row without a branch (one
+    // lane per env; see occlusion())
+    constexpr bool kRows7 = kLean;
     // the fused policy with several weight sets per block (fewer than 128 envs
     // per set) runs in the general instantiation; the lean ones hold one set
     constexpr bool kMultiPol = POL && !kLean;
@@ -503,11 +503,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                         a.t = 0;
                         a.episode = ep;
                         a.invalid = p.reset_all ? 0 : a.invalid;
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            a.bx[b] = (int)((r.z >> (8 * b)) & 0xFFu);
-                            a.by[b] = (int)((r.w >> (8 * b)) & 0xFFu);
-                        }
+                        a.bxp = r.z;
+                        a.byp = r.w;
                     }
                 }
                 __syncwarp();
