@@ -509,9 +509,12 @@ def run_e2e(nx, inputs, torch, w, descs, atlas, rank, world, steps, dist):
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
+    laps = []
     for _ in range(ks):
         e.rollout_host(T, actions=acts.numpy(), out=hout)
+        laps.append(time.perf_counter())
     el = time.perf_counter() - t0
+    laps = [1000.0 * (b - a) for a, b in zip([t0] + laps[:-1], laps)]
     if dist:
         t = torch.tensor([el], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -519,6 +522,7 @@ def run_e2e(nx, inputs, torch, w, descs, atlas, rank, world, steps, dist):
     e.close()
     return {"value": world * n * T * ks / el, "unit": "env-steps/s", "h2d_bytes_per_step": T * n,
             "d2h_bytes_per_step": T * n * OUT_BYTES_SYM, "steps": ks, "horizon": T, "host_ring_steps": D,
+            "rollout_ms": [round(v, 2) for v in laps],
             "actions": "host int8, seeded numpy draws", "call": "nx_rollout_host"}
 
 
