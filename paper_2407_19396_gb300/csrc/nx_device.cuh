@@ -693,46 +693,67 @@ constexpr OccTable make_occ_table()
 }
 __device__ const OccTable occ_table = make_occ_table();
 
-// Rows are looked up in `tab` (the table staged in shared memory by groups of
-// eight or more lanes), or in the global table (L1-cached) when tab is null;
-// G = 1 evaluates occ_row directly, which measures faster there than either
-// table (its single thread per env is bound by the latency of the chain).
-// ROWS7: one lane per env evaluates all seven rows without a branch (a zero
-// seed gives a zero row) -- measured 1-9 % faster in the lean kernels; the
-// general one keeps the loop that stops at the first dark row.
-template <int G, bool ROWS7 = false>
+// The same row by carries.  Adding (seed & p) to p sends a carry from every
+// lit transparent cell up through the run of transparent cells above it to
+// the first opaque (or edge) cell; the bits the addition changes are that run
+// and its stopping cell -- the forward fill -- except for seeds inside the
+// run, which the OR puts back.  The backward fill is the forward fill of the
+// bit-reversed row.  About half the operations of occ_row's doubling shifts;
+// carry_rows_agree() checks the two against each other for every input.
+struct RevSwap {  // 32-bit reversal by swapping halves, bytes, nibbles, pairs, bits
+    __host__ __device__ static constexpr uint32_t apply(uint32_t x)
+    {
+        x = ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+        x = ((x >> 2) & 0x33333333u) | ((x & 0x33333333u) << 2);
+        x = ((x >> 4) & 0x0F0F0F0Fu) | ((x & 0x0F0F0F0Fu) << 4);
+        x = ((x >> 8) & 0x00FF00FFu) | ((x & 0x00FF00FFu) << 8);
+        return (x >> 16) | (x << 16);
+    }
+};
+#ifdef __CUDACC__
+struct RevBrev {
+    __device__ static __forceinline__ uint32_t apply(uint32_t x) { return __brev(x); }
+};
+#endif
+template <class Rev>
+__host__ __device__ constexpr uint32_t occ_row_carry(uint32_t seed, uint32_t t)
+{
+    const uint32_t p1 = t & 0x3Fu, q1 = t & 0x7Eu;  // may pass light toward +vx / -vx
+    uint32_t m = seed | ((p1 + (seed & p1)) ^ p1);
+    const uint32_t fa = m & p1;
+    const uint32_t rq = Rev::apply(q1);
+    uint32_t r = Rev::apply(m);
+    r |= (rq + (r & rq)) ^ rq;  // rq's top bit (q1's bit 0) is clear: no carry leaves the word
+    m = Rev::apply(r);
+    const uint32_t ba = m & q1;
+    return m | ((fa | (fa << 1) | ba | (ba >> 1)) << 7);
+}
+constexpr bool carry_rows_agree()
+{
+    for (uint32_t i = 0; i < (1u << 14); ++i)
+        if (occ_row_carry<RevSwap>(i >> 7, i & 0x7Fu) != occ_row(i >> 7, i & 0x7Fu)) return false;
+    return true;
+}
+static_assert(carry_rows_agree(), "the carry form of an occlusion row equals the doubling-shift form");
+
+// Groups of two or more lanes (the ballot-assembled 49-bit mask of
+// transparent cells, bit c = vy * 7 + vx): rows are looked up in `tab` (the
+// table staged in shared memory by groups of eight or more lanes), or in the
+// global table (L1-cached) when tab is null, all seven without a branch (a
+// zero seed gives a zero row and a zero seed).  One lane per env evaluates
+// each row in its carry form instead (render_view), which measures faster
+// there than either table: a lane per env is bound by issue and by the
+// latency of the chain.
+template <int G>
 __device__ __forceinline__ uint64_t occlusion(uint64_t tmask, const uint16_t* tab)
 {
+    static_assert(G > 1, "one lane per env evaluates the rows in render_view");
     uint64_t vis = 0;
     uint32_t seed = 1u << 3;
-    if constexpr (G > 1) {
-        // table rows: all seven in a row without a branch (a zero seed gives a
-        // zero row and a zero seed)
 #pragma unroll
-        for (int j = 6; j >= 0; --j) {
-            const uint32_t t = (uint32_t)(tmask >> (7 * j)) & 0x7Fu;
-            const uint32_t e = tab ? (uint32_t)tab[(seed << 7) | t] : (uint32_t)__ldg(&occ_table.v[(seed << 7) | t]);
-            vis |= (uint64_t)(e & 0x7Fu) << (7 * j);
-            seed = e >> 7;
-        }
-        return vis;
-    }
-    if constexpr (ROWS7) {
-#pragma unroll
-        for (int j = 6; j >= 0; --j) {
-            const uint32_t t = (uint32_t)(tmask >> (7 * j)) & 0x7Fu;
-            const uint32_t e = occ_row(seed, t);
-            vis |= (uint64_t)(e & 0x7Fu) << (7 * j);
-            seed = e >> 7;
-        }
-        return vis;
-    }
-    // one lane per env: once a row lights nothing ahead, every farther row
-    // stays unseen
-#pragma unroll 1
-    for (int j = 6; j >= 0 && seed != 0u; --j) {
+    for (int j = 6; j >= 0; --j) {
         const uint32_t t = (uint32_t)(tmask >> (7 * j)) & 0x7Fu;
-        const uint32_t e = occ_row(seed, t);
+        const uint32_t e = tab ? (uint32_t)tab[(seed << 7) | t] : (uint32_t)__ldg(&occ_table.v[(seed << 7) | t]);
         vis |= (uint64_t)(e & 0x7Fu) << (7 * j);
         seed = e >> 7;
     }
@@ -807,15 +828,27 @@ struct ViewOut<1> {
     uint32_t sw[37];  // stream words of the 147-byte record
 };
 
-// Byte mask of the four low bits of m (bit i set -> byte i = 0xFF).
-__device__ __forceinline__ uint32_t byte_mask4(uint32_t m) { return ((m * 0x00204081u) & 0x01010101u) * 0xFFu; }
+// Byte masks of a 7-bit row mask m: spread_bits_lo sets byte i to 0xFF iff
+// bit i of m is set (i = 0..3), spread_bits_hi byte i iff bit i + 4 is (byte
+// 3 stays 0).  The multiply copies m four times, seven bits apart, so that
+// bit i of m lands on bit 8 i + 7 (resp. bit i + 4 on 8 i + 7) with no two
+// copies overlapping; the byte permute's sign-replicating selectors then fill
+// each byte with its top bit.
+__device__ __forceinline__ uint32_t sign_fill_bytes(uint32_t x)
+{
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(0u), "n"(0xBA98));
+    return r;
+}
+__device__ __forceinline__ uint32_t spread_bits_lo(uint32_t m) { return sign_fill_bytes(m * 0x10204080u); }
+__device__ __forceinline__ uint32_t spread_bits_hi(uint32_t m) { return sign_fill_bytes(m * 0x01020408u); }
 
 // Groups of 8 or more lanes read a grid with a wall margin of at least six
 // cells on every side (row stride W >= S + 12): every cell of the view, and of
 // the idle lanes' positions (one row behind the agent, four columns to its
 // right), lies in the margin or the grid, so they read without an in-grid
 // test.  Narrower groups read a packed grid (W = S) with the masks.
-template <int G, bool ROWS7 = false>
+template <int G>
 __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g, int S, int W, const AgentReg& a,
                                             const uint32_t* dec, const uint16_t* occ, ViewOut<G>& out, uint16_t* tiles)
 {
@@ -823,43 +856,55 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
     if constexpr (G == 1) {
         // Strided gather: cell (vx, vy) is read at g[idx0 + vx dR - vy dF]
         // without a bounds test (guard bytes around the grid region keep every
-        // read inside shared memory); cells outside the grid are replaced by
-        // grey walls four at a time with byte masks of the in-grid bits.
+        // read inside shared memory).  View row vy is held in two words,
+        // row[2 vy] (cells 0-3) and row[2 vy + 1] (cells 4-6, byte 3 spare),
+        // so that the row's in-grid walls, its transparency bits and, after
+        // the occlusion pass, its visibility each take a few word operations.
         constexpr uint32_t kWall4 = C_WALL * 0x01010101u;
         const uint8_t* p0 = g + v.idx0;
-        uint64_t inmask = 0;
+        const uint32_t cm0 = spread_bits_lo(v.colmask), cm1 = spread_bits_hi(v.colmask);  // in-grid columns
+        uint32_t row[14], trow[7];
 #pragma unroll
-        for (int vy = 0; vy < 7; ++vy)
-            inmask |= (uint64_t)(((v.rowmask >> vy) & 1u) ? v.colmask : 0u) << (7 * vy);
-        uint32_t packed[13];
-        uint64_t tmask = 0;
+        for (int vy = 0; vy < 7; ++vy) {
+            uint32_t w0 = 0, w1 = 0;
 #pragma unroll
-        for (int w = 0; w < 13; ++w) {
-            uint32_t word = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int c = 4 * w + b;
-                if (c < 49 && c != 45) word |= (uint32_t)p0[(c % 7) * v.dR - (c / 7) * v.dF] << (8 * b);
+            for (int vx = 0; vx < 7; ++vx) {
+                if (vy == 6 && vx == 3) continue;  // the agent's cell
+                const uint32_t b = p0[vx * v.dR - vy * v.dF];
+                if (vx < 4) w0 |= b << (8 * vx);
+                else w1 |= b << (8 * (vx - 4));
             }
-            const uint32_t m = byte_mask4((uint32_t)(inmask >> (4 * w)) & 15u);
-            word = (word & m) | (kWall4 & ~m);
-            if (w == 11)  // the agent's cell, c = 45: what it carries, else empty
-                word = (word & 0xFFFF00FFu) | ((a.carry ? a.carry : (uint32_t)C_EMPTY) << 8);
-            if (w == 12) word &= 0xFFu;  // c = 48 only
-            packed[w] = word;
-            const uint32_t opq = (uint32_t)(((word & 0x80808080u) * 0x00204081u) >> 28);
-            tmask |= (uint64_t)(~opq & 0xFu) << (4 * w);
+            // cells outside the grid read as grey walls
+            const uint32_t rin = 0u - ((v.rowmask >> vy) & 1u);
+            const uint32_t k0 = cm0 & rin, k1 = cm1 & rin;
+            w0 = (w0 & k0) | (kWall4 & ~k0);
+            w1 = (w1 & k1) | (kWall4 & ~k1);
+            if (vy == 6)  // the agent's cell (3, 6): what it carries, else empty
+                w0 = (w0 & 0x00FFFFFFu) | ((a.carry ? a.carry : (uint32_t)C_EMPTY) << 24);
+            row[2 * vy] = w0;
+            row[2 * vy + 1] = w1;
+            // transparency bit vx = inverted top bit of cell vx's code: the
+            // inverted top bits sit at bits 0, 8, 16, 24 (cells 0-3) and 4,
+            // 12, 20 (cells 4-6); one multiply gathers them to bits 24-30
+            // (the partial products never overlap, so nothing carries)
+            const uint32_t x = ((~w0 >> 7) & 0x01010101u) | ((~w1 >> 3) & 0x00101010u);
+            trow[vy] = (x * 0x01020408u) >> 24;
         }
-        tmask &= (1ull << 49) - 1ull;
-        const uint64_t vis = occlusion<G, ROWS7>(tmask, occ);
-        // an unseen cell's code becomes 0, whose triple is (0, 0, 0); a seen
-        // cell's code is never 0
+        // occlusion: rows from the agent's (6) outward; an unseen cell's code
+        // becomes 0, whose triple is (0, 0, 0) (a seen cell's code is never 0)
+        uint32_t seed = 1u << 3;
 #pragma unroll
-        for (int w = 0; w < 13; ++w) packed[w] &= byte_mask4((uint32_t)(vis >> (4 * w)) & 15u);
+        for (int vy = 6; vy >= 0; --vy) {
+            const uint32_t e = occ_row_carry<RevBrev>(seed, trow[vy]);
+            row[2 * vy] &= spread_bits_lo(e & 0x7Fu);
+            row[2 * vy + 1] &= spread_bits_hi(e & 0x7Fu);
+            seed = e >> 7;
+        }
         uint32_t tri[49];
 #pragma unroll
         for (int c = 0; c < 49; ++c) {
-            const uint32_t code = (packed[c >> 2] >> (8 * (c & 3))) & 0xFFu;
+            const int vy = c / 7, vx = c % 7;
+            const uint32_t code = (row[2 * vy + (vx >> 2)] >> (8 * (vx & 3))) & 0xFFu;
             tri[c] = dec[code];
             if (tiles) tiles[c] = (uint16_t)tile_of_triple(code != 0u, c == 45, tri[c]);
         }

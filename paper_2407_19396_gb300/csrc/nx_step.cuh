@@ -241,9 +241,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 {
     static_assert(!POL || (G == 1 && !RGB && !FULL), "the fused policy runs one lane per env");
     constexpr bool kLean = FAM >= 0, kLeanRandom = kLean && !POL;
-    // the lean kernels evaluate every occlusion row without a branch (one
-    // lane per env; see occlusion())
-    constexpr bool kRows7 = kLean;
     // the fused policy with several weight sets per block (fewer than 128 envs
     // per set) runs in the general instantiation; the lean ones hold one set
     constexpr bool kMultiPol = POL && !kLean;
@@ -432,7 +429,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 reinterpret_cast<uint4*>(sW)[i] = src[i];
             if (active) {
                 ViewOut<G> v0;
-                render_view<G, kRows7>(grp, mygrid, S, W, a, s_dec, nullptr, v0, nullptr);
+                render_view<G>(grp, mygrid, S, W, a, s_dec, nullptr, v0, nullptr);
                 nxp::store_obs_row(sA, tid, v0.sw);
             } else {
                 nxp::store_zero_row(sA, tid);
@@ -545,7 +542,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 }
                 // (every grid write above -- a reset, a ball move, the action's
                 // write -- ends with a group barrier, so the view sees it)
-                render_view<G, kRows7>(grp, mygrid, S, W, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
+                render_view<G>(grp, mygrid, S, W, a, s_dec, kSmemOcc ? s_occ : nullptr, vo,
                             RGB && obs_rgb ? stiles + gi * 49 : nullptr);
                 if constexpr (POL) nxp::store_obs_row(sA, tid, vo.sw);  // the next step's policy input
                 if constexpr (FULL) if (obs_full || obs_cat || obs_rgb_full) {
