@@ -520,10 +520,34 @@ def run_e2e(nx, inputs, torch, w, descs, atlas, rank, world, steps, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         el = float(t.item())
     e.close()
-    return {"value": world * n * T * ks / el, "unit": "env-steps/s", "h2d_bytes_per_step": T * n,
+    value = world * n * T * ks / el
+    link = host_link_d2h_gbs(torch)
+    # the leg's ceiling: every env-step brings OUT_BYTES_SYM bytes back over
+    # its GPU's host link (its 1-byte action goes the other way, concurrently)
+    bound = link * 1e9 / OUT_BYTES_SYM
+    return {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": T * n,
             "d2h_bytes_per_step": T * n * OUT_BYTES_SYM, "steps": ks, "horizon": T, "host_ring_steps": D,
             "rollout_ms": [round(v, 2) for v in laps],
+            "host_link": {"d2h_gbs": round(link, 1), "bound_env_steps_per_s": bound * world,
+                          "frac": value / (bound * world),
+                          "measured": "best of 3 copies of 1 GiB from device to pinned host memory"},
             "actions": "host int8, seeded numpy draws", "call": "nx_rollout_host"}
+
+
+def host_link_d2h_gbs(torch, nbytes=1 << 30, reps=3):
+    """Device-to-host copy rate into pinned memory (GB/s), best of reps."""
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d.fill_(1)
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    best = 0.0
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        best = max(best, nbytes / (time.perf_counter() - t) / 1e9)
+    del d, h
+    return best
 
 
 def run_extra(nx, inputs, name, flush, peak, peak_src, reps=5):
