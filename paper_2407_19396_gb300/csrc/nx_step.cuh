@@ -256,6 +256,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
     // records with bulk copies; wider ones with the warp's vector copy
     constexpr bool kBulk = G <= 4;
     __shared__ __align__(16) uint16_t s_occ[kSmemOcc ? (1 << 14) : 8];
+    // the lean kernels of groups of 8 or more lanes draw the random actions of
+    // up to kActChunk steps ahead, one per lane and step, into shared memory
+    // (a byte per env and step), so the step loop reads its action with one
+    // load instead of a shuffle and a branch every G steps
+    constexpr bool kPreAct = kLeanRandom && G >= 8;
+    constexpr int kActChunk = kPreAct ? 128 : (1 << 30);
+    __shared__ uint8_t s_act[kPreAct ? (kMaxThreads / G) * kActChunk : 1];
     const int E = p.envs_per_cta;
     // groups of 16 or more lanes stage at most two records per warp: always
     // in one part (the host sizes the staging the same way)
@@ -445,8 +452,19 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         // this env's row of the output ring (slot * n_envs + local), advanced
         // by one add per step
         size_t o = (size_t)slot * nreq + local;
-        uint32_t my_draw = 0;  // G > 1: this lane's random-action draw for step s0 + lane
-        for (int s = 0; s < emissions; ++s) {
+        uint32_t my_draw = 0;  // G > 1 (unless kPreAct): this lane's random-action draw for step s0 + lane
+        for (int s0 = 0; s0 < emissions; s0 += kActChunk) {
+        if constexpr (kPreAct) {
+            // the actions of steps s0 .. s0 + kActChunk - 1, drawn by the group's lanes
+            const int cnt = min(kActChunk, steps - s0);
+            if (active)
+                for (int j = grp.lane; j < cnt; j += G)
+                    s_act[gi * kActChunk + j] = (uint8_t)bounded(
+                        draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)(s0 + j), PURPOSE_ACTION, 0u), n_act);
+            grp.sync();
+        }
+        const int s_end = min(emissions, s0 + kActChunk);
+        for (int s = s0; s < s_end; ++s) {
             const size_t row0 = o - (size_t)gi;  // the item's first env in this slot
             uint8_t* sym_dst = obs_sym ? obs_sym + row0 * NX_OBS_SYM_BYTES : nullptr;
             ViewOut<G> vo;
@@ -456,7 +474,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             if constexpr (POL)
                 pol_act = nxp::policy_finish<kMultiPol>(sA, sW, tmem, &s_mbar, phase, (int)n_act, rq->shift1,
                                                         rq->shift2, pol_ok, pol_rows);
-            if (G > 1 && rnd && (s % G) == 0) {
+            if (!kPreAct && G > 1 && rnd && (s % G) == 0) {
                 // the random actions of the next G steps depend only on the step
                 // counter, so the group's lanes draw them in parallel
                 my_draw = (s + grp.lane < steps) ? draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)(s + grp.lane),
@@ -472,11 +490,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             const bool starts = active && (p.reset_all || a.done);
             if constexpr (G >= 8) {
                 if (starts) {
-                    const int inv = p.reset_all ? 0 : a.invalid;  // the invalid-action flag is sticky
-                    if (!reset_layout(grp, mygrid, S, W, family, n_balls, variant, seed, key,
-                                      p.reset_all ? 0u : a.episode + 1u, a))
-                        if (grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
-                    a.invalid = inv;
+                    // (out of line: the rare path's code stays out of the step loop)
+                    const uint32_t ep = p.reset_all ? 0u : a.episode + 1u;
+                    const uint4 r = reset_layout_grp<G, FAM>(grp, mygrid, S, W, family, n_balls, variant, seed, key, ep);
+                    if (!(r.y & 0x100u) && grp.lane == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
+                    unpack_reset(r, ep, p.reset_all != 0, a);
                 }
             } else {
                 unsigned lead = __ballot_sync(0xFFFFFFFFu, starts && grp.lane == 0);
@@ -488,21 +506,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     const int owner = ((tid & ~31) + L) / G;  // group (env slot) of lane L
                     const uint4 r = reset_layout_warp<FAM>(sgrid + owner * ics, S, family, n_balls, variant, seed, k, ep);
                     if (!(r.y & 0x100u) && (tid & 31) == 0) atomicOr(&p.ctl->flags, (unsigned)NX_FLAG_BOUNDS);
-                    if (gi == owner) {
-                        // the new episode's start; the invalid-action flag is sticky
-                        a.x = (int)(r.x & 0xFFu);
-                        a.y = (int)((r.x >> 8) & 0xFFu);
-                        a.dir = (int)((r.x >> 16) & 0xFFu);
-                        a.mission = r.x >> 24;
-                        a.nb = (int)(r.y & 0xFFu);
-                        a.carry = 0u;
-                        a.done = 0;
-                        a.t = 0;
-                        a.episode = ep;
-                        a.invalid = p.reset_all ? 0 : a.invalid;
-                        a.bxp = r.z;
-                        a.byp = r.w;
-                    }
+                    if (gi == owner) unpack_reset(r, ep, p.reset_all != 0, a);
                 }
                 __syncwarp();
             }
@@ -519,6 +523,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     action = coin < eps_t
                                  ? bounded(draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)s, PURPOSE_ACTION, 0u), n_act)
                                  : pol_act;
+                } else if (kPreAct) {
+                    action = s_act[gi * kActChunk + (s - s0)];
                 } else if (rnd) {
                     const uint32_t x = G > 1 ? grp.shfl(my_draw, s % G)
                                              : draw(seed, key, 0xFFFFFFFFu, gstep0 + (uint32_t)s, PURPOSE_ACTION, 0u);
@@ -582,17 +588,19 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     ret += reward;
                     eps += (uint32_t)(term || trunc);
                 }
+                // Groups of 8 or more lanes (at most 4 envs per warp) write each
+                // cell's three bytes straight to global memory (measured faster
+                // than staging there); the staged path below serves the narrow
+                // groups and the outputs that read the staged record (digest,
+                // the categorical first-person view).
+                if (G >= 8 && !digest && !(FULL && obs_cat_fp) && obs_sym)
+                    write_view(grp, vo, obs_sym + o * NX_OBS_SYM_BYTES);
             }
             // fused policy: the next step's first layer runs during the stores
             if constexpr (POL)
                 if (s + 1 < emissions) nxp::policy_issue_first<kMultiPol>(sA, sW, tmem, &s_mbar, pol_agents);
-            // Groups of 8 or more lanes (at most 4 envs per warp) write each
-            // cell's three bytes straight to global memory (measured faster
-            // than staging there); the staged path serves the narrow groups
-            // and the outputs that read the staged record (digest, the
-            // categorical first-person view).
             if (G >= 8 && !digest && !(FULL && obs_cat_fp)) {
-                if (active && row_ok && obs_sym) write_view(grp, vo, obs_sym + o * NX_OBS_SYM_BYTES);
+                // (stored above)
             } else {
             // Each warp stages the symbolic outputs of its own envs (placed at
             // the same address modulo 16 as their destination) and stores them
@@ -676,6 +684,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
             const bool wrap = slot + 1u == (uint32_t)depth;
             slot = wrap ? 0u : slot + 1u;
             o = wrap ? (size_t)local : o + nreq;
+        }
         }
 
         if (kBulk && lane32 == 0) bulk_wait_all();  // every record of this item is in global memory
