@@ -117,6 +117,34 @@ struct SReq {
     bool finished = false;
 };
 
+// One block of a chunk's batched clears and result copies: bytes from src
+// (or zeros when src is NULL) to dst; every block is 256-byte aligned and a
+// whole number of 256-byte units (the request layout pads every part).
+struct BlockCopy {
+    const uint8_t* src;
+    uint8_t* dst;
+    uint64_t bytes;
+};
+
+// All of a chunk's blocks in one launch: blockIdx.y picks the block, the x
+// dimension strides its 16-byte words.  The result copies write the pinned
+// host staging through its device mapping (SM stores over the host link run
+// at the copy engines' rate), so a chunk that finishes many requests needs
+// one launch instead of one copy per request, and the clears of the
+// accumulators of its new requests one launch instead of one memset each.
+__global__ void nx_block_copy_kernel(const BlockCopy* blocks)
+{
+    const BlockCopy b = blocks[blockIdx.y];
+    const uint64_t n = b.bytes / 16, stride = (uint64_t)gridDim.x * blockDim.x;
+    uint4* d = reinterpret_cast<uint4*>(b.dst);
+    if (b.src) {
+        const uint4* src = reinterpret_cast<const uint4*>(b.src);
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) d[i] = src[i];
+    } else {
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) d[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
 struct Chunk {
     cudaEvent_t ev = nullptr;
     std::vector<uint64_t> finishing;
@@ -154,6 +182,10 @@ struct nx_server {
     nx_req* h_reqs[2] = {nullptr, nullptr};
     nx_item* d_items = nullptr;  // [2 staging buffers][2 * max_items]
     nx_item* h_items[2] = {nullptr, nullptr};
+    // batched clears and result copies: [2 staging buffers][2 * max_slots]
+    BlockCopy* d_blocks = nullptr;
+    BlockCopy* h_blocks[2] = {nullptr, nullptr};
+    uint8_t* h_pool_dev = nullptr;  // the pinned staging as the device addresses it
     nx_ctl* d_ctl = nullptr;
     Chunk chunks[2];
 
@@ -289,6 +321,19 @@ void retire(nx_server* s, uint64_t t)
     s->cv_done.notify_all();
 }
 
+// Launches the blocks [first, first + n) of buffer `cur` (already uploaded).
+bool launch_blocks(nx_server* s, int cur, size_t first, size_t n, uint64_t max_bytes)
+{
+    if (n == 0) return true;
+    const unsigned threads = 256;
+    const uint64_t per_x = (uint64_t)threads * 16 * 4;  // four 16-byte words per thread and pass
+    const unsigned gx = (unsigned)std::min<uint64_t>(128, std::max<uint64_t>(1, (max_bytes + per_x - 1) / per_x));
+    nx_block_copy_kernel<<<dim3(gx, (unsigned)n), threads, 0, s->stream>>>(s->d_blocks + (size_t)cur * 2 * s->max_slots +
+                                                                            first);
+    SRV_CK(cudaGetLastError(), "block copy launch");
+    return true;
+}
+
 bool wait_chunk(nx_server* s, Chunk& c)
 {
     if (!c.valid) return true;
@@ -394,6 +439,26 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         set_fatal(s, NX_E_INVAL, "work list larger than the server's capacity");
         return false;
     }
+    // the new requests' accumulator clears, then the finished requests' result copies
+    BlockCopy* hb = s->h_blocks[cur];
+    size_t n_clear = 0, n_copy = 0;
+    uint64_t max_clear = 0, max_copy = 0;
+    for (const SReq* qp : fresh_q) {
+        const SReq& q = *qp;
+        hb[n_clear++] = BlockCopy{nullptr, s->d_pool + q.dev_off + q.lay.returns, (uint64_t)(q.lay.obs - q.lay.returns)};
+        max_clear = std::max<uint64_t>(max_clear, q.lay.obs - q.lay.returns);
+    }
+    if (s->h_pool_dev)
+        for (const SReq* qp : finishing_q) {
+            const SReq& q = *qp;
+            hb[n_clear + n_copy++] = BlockCopy{s->d_pool + q.dev_off + q.lay.returns, s->h_pool_dev + q.host_off,
+                                               (uint64_t)q.lay.tail};
+            max_copy = std::max<uint64_t>(max_copy, q.lay.tail);
+        }
+    if (n_clear + n_copy)
+        SRV_CK(cudaMemcpyAsync(s->d_blocks + (size_t)cur * 2 * s->max_slots, hb, (n_clear + n_copy) * sizeof(BlockCopy),
+                               cudaMemcpyHostToDevice, s->stream),
+               "block list upload");
     memcpy(hi, reset_items.data(), nr * sizeof(nx_item));
     memcpy(hi + nr, step_items.data(), ns * sizeof(nx_item));
     memcpy(hi + nr + ns, reset_small.data(), nrs * sizeof(nx_item));
@@ -426,11 +491,7 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         return sh;
     };
     int grid = 0;
-    for (const SReq* qp : fresh_q) {
-        const SReq& q = *qp;
-        SRV_CK(cudaMemsetAsync(s->d_pool + q.dev_off + q.lay.returns, 0, q.lay.obs - q.lay.returns, s->stream),
-               "accumulator clear");
-    }
+    if (!launch_blocks(s, cur, 0, n_clear, max_clear)) return false;  // the new requests' accumulators
     if (nrs + nss) {
         // the small requests' launches on the side stream, after the uploads
         SRV_CK(cudaEventRecord(s->fork_ev, s->stream), "fork");
@@ -478,11 +539,17 @@ bool iterate(nx_server* s, int& cur, bool* idle)
         if (rc) SRV_CK((cudaError_t)rc, "step launch");
     }
     if (nrs + nss) SRV_CK(cudaStreamWaitEvent(s->stream, s->join_ev, 0), "join");
-    for (const SReq* qp : finishing_q) {
-        const SReq& q = *qp;  // (requests that finish normally; withdrawn ones copy nothing back)
-        SRV_CK(cudaMemcpyAsync(s->h_pool + q.host_off, s->d_pool + q.dev_off + q.lay.returns, q.lay.tail,
-                               cudaMemcpyDeviceToHost, s->stream),
-               "result copy");
+    // the results of the requests this chunk finishes (withdrawn ones copy
+    // nothing back), into the pinned staging
+    if (s->h_pool_dev) {
+        if (!launch_blocks(s, cur, n_clear, n_copy, max_copy)) return false;
+    } else {
+        for (const SReq* qp : finishing_q) {
+            const SReq& q = *qp;
+            SRV_CK(cudaMemcpyAsync(s->h_pool + q.host_off, s->d_pool + q.dev_off + q.lay.returns, q.lay.tail,
+                                   cudaMemcpyDeviceToHost, s->stream),
+                   "result copy");
+        }
     }
     SRV_CK(cudaEventRecord(c.ev, s->stream), "chunk event");
     c.finishing = finishing;
@@ -602,9 +669,15 @@ nx_status nx_server_create(nx_server** out, size_t budget, const nx_options* opt
     if (e == cudaSuccess) e = cudaMalloc(&s->d_items, sizeof(nx_item) * s->max_items * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ctl, sizeof(nx_ctl));
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_pool, host_cap);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_blocks, sizeof(BlockCopy) * 2 * (size_t)s->max_slots * 2);
+    if (e == cudaSuccess && cudaHostGetDevicePointer((void**)&s->h_pool_dev, s->h_pool, 0) != cudaSuccess) {
+        cudaGetLastError();  // no device mapping of pinned memory: one copy per finished request
+        s->h_pool_dev = nullptr;
+    }
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaMallocHost(&s->h_reqs[b], sizeof(nx_req) * (size_t)s->max_slots);
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_items[b], sizeof(nx_item) * 2 * s->max_items);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->h_blocks[b], sizeof(BlockCopy) * 2 * (size_t)s->max_slots);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->chunks[b].ev, cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ctl, 0, sizeof(nx_ctl), s->stream);
@@ -749,11 +822,13 @@ void nx_server_destroy(nx_server* s)
         if (s->chunks[b].ev) cudaEventDestroy(s->chunks[b].ev);
         if (s->h_reqs[b]) cudaFreeHost(s->h_reqs[b]);
         if (s->h_items[b]) cudaFreeHost(s->h_items[b]);
+        if (s->h_blocks[b]) cudaFreeHost(s->h_blocks[b]);
     }
     if (s->h_pool) cudaFreeHost(s->h_pool);
     if (s->d_pool) cudaFree(s->d_pool);
     if (s->d_reqs) cudaFree(s->d_reqs);
     if (s->d_items) cudaFree(s->d_items);
+    if (s->d_blocks) cudaFree(s->d_blocks);
     if (s->d_ctl) cudaFree(s->d_ctl);
     delete s;
 }
