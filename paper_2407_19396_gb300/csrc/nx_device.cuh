@@ -752,8 +752,13 @@ struct RevBrev {
     __device__ static __forceinline__ uint32_t apply(uint32_t x) { return __brev(x); }
 };
 #endif
+// The row's visible cells and the next row's seed, both 7-bit: the one-lane
+// view keeps them apart, which saves packing and unpacking them per row.
+struct OccRow {
+    uint32_t vis, next;
+};
 template <class Rev>
-__host__ __device__ constexpr uint32_t occ_row_carry(uint32_t seed, uint32_t t)
+__host__ __device__ constexpr OccRow occ_row_carry2(uint32_t seed, uint32_t t)
 {
     const uint32_t p1 = t & 0x3Fu, q1 = t & 0x7Eu;  // may pass light toward +vx / -vx
     uint32_t m = seed | ((p1 + (seed & p1)) ^ p1);
@@ -763,12 +768,21 @@ __host__ __device__ constexpr uint32_t occ_row_carry(uint32_t seed, uint32_t t)
     r |= (rq + (r & rq)) ^ rq;  // rq's top bit (q1's bit 0) is clear: no carry leaves the word
     m = Rev::apply(r);
     const uint32_t ba = m & q1;
-    return m | ((fa | (fa << 1) | ba | (ba >> 1)) << 7);
+    return OccRow{m, fa | (fa << 1) | ba | (ba >> 1)};
+}
+template <class Rev>
+__host__ __device__ constexpr uint32_t occ_row_carry(uint32_t seed, uint32_t t)
+{
+    const OccRow o = occ_row_carry2<Rev>(seed, t);
+    return o.vis | (o.next << 7);
 }
 constexpr bool carry_rows_agree()
 {
-    for (uint32_t i = 0; i < (1u << 14); ++i)
-        if (occ_row_carry<RevSwap>(i >> 7, i & 0x7Fu) != occ_row(i >> 7, i & 0x7Fu)) return false;
+    for (uint32_t i = 0; i < (1u << 14); ++i) {
+        const OccRow o = occ_row_carry2<RevSwap>(i >> 7, i & 0x7Fu);
+        // both parts stay within 7 bits, so their packed form is occ_row's
+        if (o.vis > 0x7Fu || o.next > 0x7Fu || (o.vis | (o.next << 7)) != occ_row(i >> 7, i & 0x7Fu)) return false;
+    }
     return true;
 }
 static_assert(carry_rows_agree(), "the carry form of an occlusion row equals the doubling-shift form");
@@ -943,10 +957,10 @@ __device__ __forceinline__ void render_view(const Grp<G>& grp, const uint8_t* g,
         uint32_t seed = 1u << 3;
 #pragma unroll
         for (int vy = 6; vy >= 0; --vy) {
-            const uint32_t e = occ_row_carry<RevBrev>(seed, trow[vy]);
-            row[2 * vy] &= spread_bits_lo(e & 0x7Fu);
-            row[2 * vy + 1] &= spread_bits_hi(e & 0x7Fu);
-            seed = e >> 7;
+            const OccRow e = occ_row_carry2<RevBrev>(seed, trow[vy]);
+            row[2 * vy] &= spread_bits_lo(e.vis);
+            row[2 * vy + 1] &= spread_bits_hi(e.vis);
+            seed = e.next;
         }
         uint32_t tri[49];
 #pragma unroll
