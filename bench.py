@@ -363,28 +363,79 @@ def serving_requests(seed, n):
     return out
 
 
+def mix_static_rate(reqs, n_envs=262144, T=512, seed=4):
+    """Env-steps/s of the serving mix's envs as one static batch through the
+    context API (the first n_envs envs of the requests, autotuned, random
+    actions, T-step rollouts): the persistent kernel's rate on this mix of
+    families and sizes, without a server."""
+    import torch
+
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    descs = []
+    for fam, size, ne, _, _ in reqs:
+        descs += [(fam, size)] * ne
+        if len(descs) >= n_envs:
+            break
+    descs = descs[:n_envs]
+    env = nx.Env(descs=descs, seed=seed)
+    env.reset()
+    out = env.alloc_out(128)
+    env.rollout(T, depth=128, out=out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        env.rollout(T, depth=128, out=out)
+    torch.cuda.synchronize()
+    rate = len(descs) * T * 3 / (time.perf_counter() - t0)
+    env.close()
+    return rate, len(descs)
+
+
+def cpu_oracle_serving(reqs, min_s=5.0):
+    """Env-steps/s of the oracle (one thread) serving the mix's requests one
+    after another, each alone (its envs reset, then stepped for its
+    horizon), until at least min_s of work: the serving mix's CPU baseline."""
+    import oracle as O
+
+    done, n_req, t0 = 0, 0, time.perf_counter()
+    for fam, size, ne, hz, seed in reqs:
+        b = O.Batch([fam] * ne, [size] * ne, seed)
+        b.reset(sym=True)
+        b.rollout(hz, sym=True)
+        done += ne * hz
+        n_req += 1
+        if time.perf_counter() - t0 >= min_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"the mix's first {n_req} requests, each alone for its horizon ({done} env-steps, {el:.1f} s), "
+                      "one thread"}
+
+
 def run_serving(mixed_capacity=None, n_req=2000, budget=16 << 30, load=0.7, seed=4, chunk=64):
     """Poisson arrivals of the serving mix; returns latency percentiles and
     throughput.  The arrival rate is `load` x the measured capacity of the
     65,536-env mixed configuration (its env-steps/s, when given), and, as a
     second run, `load` x the server's own capacity, measured first by
-    submitting a saturating burst of requests from the same mix."""
+    submitting all the mix's requests at once.  Beside them, the mix's own
+    static-batch rate (mix_static_rate) bounds what any server reaches on it."""
     import numpy as np
 
     from paper_2407_19396_gb300 import navixgb as nx
 
+    reqs = serving_requests(seed, n_req)
+    mean_work = sum(r[2] * r[3] for r in reqs) / len(reqs)
+    static_rate, static_envs = mix_static_rate(reqs)
     srv = nx.Server(budget_bytes=budget, steps_per_launch=chunk)
-    burst = serving_requests(seed + 1000, 300)
     t0 = time.perf_counter()
     # the requests' outputs are per-env returns, final views and ended
     # episodes; the optional digest of every per-step output (a verification
     # aid, checked by the serving tests) is not asked for
-    ts = [srv.submit(*r, digest=False) for r in burst]
+    ts = [srv.submit(*r, digest=False) for r in reqs]
     for t in ts:
         srv.wait(t, timeout_s=600.0)
-    cap = sum(r[2] * r[3] for r in burst) / (time.perf_counter() - t0)
-    reqs = serving_requests(seed, n_req)
-    mean_work = sum(r[2] * r[3] for r in reqs) / len(reqs)
+    cap = sum(r[2] * r[3] for r in reqs) / (time.perf_counter() - t0)
 
     def one_run(rate_basis, arrival_seed):
         lam = load * rate_basis / mean_work  # requests per second
@@ -409,6 +460,9 @@ def run_serving(mixed_capacity=None, n_req=2000, budget=16 << 30, load=0.7, seed
 
     out = {"requests": n_req, "offered_load": load, "budget_bytes": budget, "steps_per_launch": chunk,
            "server_capacity_env_steps_per_s": cap,
+           "server_capacity_basis": f"all {n_req} requests of the mix submitted at once",
+           "mix_static_env_steps_per_s": static_rate,
+           "mix_static_basis": f"the mix's first {static_envs} envs as one autotuned static batch, 512-step rollouts",
            "mix": "family U{5}, size U{5..19}, n_envs log-U[1, 4096], horizon U{1..512}, seed 4",
            "outputs": "per-env returns, final views, ended episodes (no per-step digest)"}
     if mixed_capacity:
@@ -419,6 +473,7 @@ def run_serving(mixed_capacity=None, n_req=2000, budget=16 << 30, load=0.7, seed
         out.update(one_run(cap, seed + 1), rate_basis="0.7 x the server's burst capacity")
     out["peak_bytes"] = srv.stats()["peak_bytes"]
     srv.close()
+    out["cpu_baseline"] = cpu_oracle_serving(reqs)
     return out
 
 
