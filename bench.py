@@ -259,6 +259,18 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def cpu_model():
+    """The host CPU's model name as lscpu prints it (None when unavailable)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return None
+    for line in out.splitlines():
+        if line.strip().lower().startswith("model name:"):
+            return line.split(":", 1)[1].strip()
+    return None
+
+
 def cpu_oracle_rate(w, min_s=10.0):
     """Env-steps/s of the oracle on this host (single thread) on the
     workload's bounded sample (oracle_sample), repeated until at least min_s
@@ -340,7 +352,8 @@ def run_reference(args, w, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": w["desc"], "n_envs_per_gpu": w["n"], "sample_envs": len(idx), "sample_steps": oracle_T,
                    "env_steps_per_bench_step": len(idx) * oracle_T},
-        "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -786,7 +799,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         rate, reps, el, ne, nt = cpu_oracle_rate(w)
         line["cpu_baseline"] = {"value": rate, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{sample_text(w)} x {reps}, {el:.1f} s, one thread"}
+                                "sample": f"{sample_text(w)} x {reps}, {el:.1f} s, one thread", "cpu_model": cpu_model()}
         arate, P, asteps = cpu_oracle_rate_all_cores(args.workload)
         line["cpu_baseline"]["all_cores"] = {
             "value": arate, "unit": "env-steps/s", "cores": P, "kind": "oracle",
