@@ -1105,7 +1105,9 @@ nx_status nx_set_state(nx_env* env, const void* host_buf, size_t bytes)
         bool ok = a.x < S && a.y < S && a.dir < 4 && a.done <= 1 && a.invalid <= 1 && a.n_balls <= NX_MAX_BALLS &&
                   a.carry_ent <= 10 && a.carry_col <= 5 && (d.family == NX_DYNOBS || a.n_balls == 0) &&
                   (d.family == NX_GOTODOOR ? a.mission <= 5 : a.mission == NX_NO_MISSION);
-        for (int k = 0; ok && k < a.n_balls; ++k) ok = a.ball_x[k] < S && a.ball_y[k] < S;
+        // balls lie in the interior: placed there, they only move to empty cells
+        for (int k = 0; ok && k < a.n_balls; ++k)
+            ok = a.ball_x[k] >= 1 && a.ball_x[k] <= S - 2 && a.ball_y[k] >= 1 && a.ball_y[k] <= S - 2;
         const uint8_t* g = pool_b + env->grid_offset[i];
         for (int c = 0; ok && c < S * S; ++c) ok = g[c] <= 10 && g[S * S + c] <= 5 && g[2 * S * S + c] <= 2;
         if (!ok) return nx_fail(env, NX_E_INVAL, "snapshot holds out-of-range state");

@@ -300,16 +300,19 @@ __device__ __forceinline__ void store_agent(nx_agent* dst, const AgentReg& a, co
 }
 
 // Whether every index a step derives from the agent block stays inside an
-// S x S grid: the agent's cell and direction, and each ball's cell.  Blocks
-// written by the kernels and by nx_set_state (which validates) always pass;
-// the step kernel checks each block it loads, so that a block corrupted in
-// device memory can never make a step index outside its env's grid.
+// S x S grid: the agent's cell and direction, and each ball's cell, which
+// lies in the interior (1..S-2), so that its whole 8-neighbourhood is in the
+// grid.  Blocks written by the kernels and by nx_set_state (which validates
+// the same) always pass; the step kernel checks each block it loads, so that
+// a block corrupted in device memory can never make a step index outside
+// its env's grid.
 __device__ __forceinline__ bool agent_in_range(const AgentReg& a, int S)
 {
     bool ok = (unsigned)a.x < (unsigned)S && (unsigned)a.y < (unsigned)S && (unsigned)a.dir < 4u && (unsigned)a.nb <= 4u;
 #pragma unroll
     for (int b = 0; b < 4; ++b)
-        ok = ok && (b >= a.nb || ((unsigned)ball_x(a, b) < (unsigned)S && (unsigned)ball_y(a, b) < (unsigned)S));
+        ok = ok && (b >= a.nb || ((unsigned)(ball_x(a, b) - 1) < (unsigned)(S - 2) &&
+                                  (unsigned)(ball_y(a, b) - 1) < (unsigned)(S - 2)));
     return ok;
 }
 

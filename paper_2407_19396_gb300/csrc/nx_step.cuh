@@ -46,50 +46,72 @@ __host__ __device__ __forceinline__ int align16(int v) { return (v + 15) & ~15; 
 // 64-bit FNV-style running digest over 32-bit words
 __device__ __forceinline__ uint64_t digest_word(uint64_t h, uint32_t w) { return (h ^ (uint64_t)w) * 0x100000001B3ull; }
 
+// One Dynamic-Obstacles ball's move (reading R12): to a uniformly drawn empty
+// cell of its 8-neighbourhood that is not the agent's cell, with draw db.
+// Balls lie in the grid's interior (placed there, they only ever move to
+// empty cells, and the kernel checks every agent block it loads), so the
+// eight neighbours are read without a bounds test and the candidate mask,
+// the drawn candidate and the move are computed without a branch.
+template <int G>
+__device__ __forceinline__ void move_ball(const Grp<G>& grp, uint8_t* g, int S, int W, AgentReg& a, int b, uint32_t db,
+                                          nx_ctl* ctl)
+{
+    const int bx = ball_x(a, b), by = ball_y(a, b);
+    const uint8_t* c = g + by * W + bx;
+    // bit j: neighbour j of the 3x3 block in row-major order without the centre
+    uint32_t cand = (uint32_t)(c[-W - 1] == C_EMPTY) | ((uint32_t)(c[-W] == C_EMPTY) << 1) |
+                    ((uint32_t)(c[-W + 1] == C_EMPTY) << 2) | ((uint32_t)(c[-1] == C_EMPTY) << 3) |
+                    ((uint32_t)(c[1] == C_EMPTY) << 4) | ((uint32_t)(c[W - 1] == C_EMPTY) << 5) |
+                    ((uint32_t)(c[W] == C_EMPTY) << 6) | ((uint32_t)(c[W + 1] == C_EMPTY) << 7);
+    // the agent's cell, when it is a neighbour, is no candidate (it is never the ball's own cell)
+    const int ox = a.x - bx + 1, oy = a.y - by + 1, ao = oy * 3 + ox;
+    const bool adj = (unsigned)ox < 3u && (unsigned)oy < 3u;
+    cand &= adj ? ~(1u << (ao - (ao > 4 ? 1 : 0))) : 0xFFFFFFFFu;
+    const int cnt = __popc(cand);
+    const bool moved = cnt > 0;
+    const int jj = nth_set_bit(cand, bounded(db, (uint32_t)cnt)) & 7;  // 0..7 (any value when nothing is free)
+    // neighbour jj's offsets plus one, two bits each: dx + 1 = 0,1,2,0,2,0,1,2 and dy + 1 = 0,0,0,1,1,2,2,2
+    const int nx = bx + (int)((0x9224u >> (2 * jj)) & 3u) - 1, ny = by + (int)((0xA940u >> (2 * jj)) & 3u) - 1;
+    if (G == 1) {
+        if (moved && NX_DCHECK(ctl, (unsigned)nx < (unsigned)S && (unsigned)ny < (unsigned)S)) {
+            g[by * W + bx] = (uint8_t)C_EMPTY;
+            g[ny * W + nx] = (uint8_t)C_BALL_BLUE;
+        }
+    } else if (moved) {
+        grp.sync();
+        if (grp.lane == 0 && NX_DCHECK(ctl, (unsigned)nx < (unsigned)S && (unsigned)ny < (unsigned)S)) {
+            g[by * W + bx] = (uint8_t)C_EMPTY;
+            g[ny * W + nx] = (uint8_t)C_BALL_BLUE;
+        }
+        grp.sync();
+    }
+    set_ball(a, b, moved ? nx : bx, moved ? ny : by);
+}
+
 // Intervention (rotate / forward / pickup / drop / toggle / done), the
 // Dynamic-Obstacles transition, then time, truncation, reward and termination.
+// The balls' draws: d[b] for groups of several lanes (drawn in parallel by
+// the caller); one lane per env draws each ball's inside the ball loop,
+// which is not unrolled (a smaller loop body: the unrolled loop's code
+// missed the instruction cache).
 template <int G>
 __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int W, int family, int max_steps, AgentReg& a,
                                          int action, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
                                          float action_cost, float time_cost, float& reward, int& term, int& trunc,
-                                         nx_ctl* ctl)
+                                         nx_ctl* ctl, uint64_t seed, uint32_t key)
 {
-    // transition system: each ball, in index order, moves to a uniformly drawn
-    // empty cell of its 8-neighbourhood that is not the agent's cell
+    // transition system: each ball, in index order, moves (move_ball)
     if (family == NX_DYNOBS) {
+        if constexpr (G == 1) {
+            const uint32_t episode = a.episode, t = (uint32_t)a.t;
+#pragma unroll 1
+            for (int b = 0; b < a.nb; ++b)
+                move_ball(grp, g, S, W, a, b, draw(seed, key, episode, t, PURPOSE_BALL, (uint32_t)b), ctl);
+        } else {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            if (b >= a.nb) break;
-            uint32_t cand = 0;
-            int j = 0;
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if (dx == 0 && dy == 0) continue;
-                    const int x = ball_x(a, b) + dx, y = ball_y(a, b) + dy;
-                    const bool f = (unsigned)x < (unsigned)S && (unsigned)y < (unsigned)S && g[y * W + x] == C_EMPTY &&
-                                   !(x == a.x && y == a.y);
-                    cand |= (f ? 1u : 0u) << j;
-                    ++j;
-                }
-            const int cnt = __popc(cand);
-            if (cnt > 0) {
-                int k = bounded(d[b], (uint32_t)cnt);
-                uint32_t c = cand;
-                for (int i = 0; i < k; ++i) c &= c - 1u;
-                const int jj = __ffs(c) - 1;          // 0..7 over the 8 neighbours, row-major
-                const int o = jj < 4 ? jj : jj + 1;   // position in the 3x3 block, skipping the centre
-                const int bx = ball_x(a, b), by = ball_y(a, b);
-                const int nx = bx + (o % 3) - 1, ny = by + (o / 3) - 1;
-                grp.sync();
-                if (grp.lane == 0 && NX_DCHECK(ctl, (unsigned)nx < (unsigned)S && (unsigned)ny < (unsigned)S &&
-                                                        (unsigned)bx < (unsigned)S && (unsigned)by < (unsigned)S)) {
-                    g[by * W + bx] = (uint8_t)C_EMPTY;
-                    g[ny * W + nx] = (uint8_t)C_BALL_BLUE;
-                }
-                grp.sync();
-                set_ball(a, b, nx, ny);
+            for (int b = 0; b < 4; ++b) {
+                if (b >= a.nb) break;
+                move_ball(grp, g, S, W, a, b, d[b], ctl);
             }
         }
     }
@@ -537,14 +559,14 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     // the new episode's start: reward padding 0, the action is ignored
                 } else {
                     uint32_t d[8];
-                    if (family == NX_DYNOBS) {
+                    if (G > 1 && family == NX_DYNOBS) {  // (one lane per env draws inside env_step)
                         const uint32_t episode = a.episode, t = (uint32_t)a.t;
                         group_draws(grp, a.nb, d, [&](uint32_t k) -> uint32_t {
                             return draw(seed, key, episode, t, PURPOSE_BALL, k);
                         });
                     }
                     env_step(grp, mygrid, S, W, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
-                             time_cost, reward, term, trunc, p.ctl);
+                             time_cost, reward, term, trunc, p.ctl, seed, key);
                 }
                 // (every grid write above -- a reset, a ball move, the action's
                 // write -- ends with a group barrier, so the view sees it)
