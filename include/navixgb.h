@@ -307,7 +307,11 @@ nx_status nx_set_policy(nx_env* env, const nx_policy* policy);
  *                          env's, so env i starts at the sum of 3 size^2 over
  *                          the envs before it (pools may exceed 4 GiB).
  * nx_set_state accepts only a snapshot of a context with the same
- * descriptors. */
+ * descriptors, and only states the steps can reach: every index inside
+ * its env's grid, cell and carried codes in range, and each
+ * Dynamic-Obstacles ball in the grid's interior (1..size-2: balls are
+ * placed there and only move to empty cells); anything else is NX_E_INVAL
+ * and nothing is applied. */
 size_t nx_state_bytes(const nx_env* env);
 nx_status nx_get_state(nx_env* env, void* host_buf, size_t bytes);
 nx_status nx_set_state(nx_env* env, const void* host_buf, size_t bytes);

@@ -240,6 +240,38 @@ def test_corrupt_snapshots_are_rejected():
     env.close()
 
 
+def test_dynamic_obstacles_snapshot_balls_stay_in_the_interior():
+    """A restored Dynamic-Obstacles env must hold its balls in the grid's
+    interior (reset places them there and they only move to empty cells):
+    a ball on the border wall is refused, and a valid snapshot resumes the
+    oracle's trajectory exactly."""
+    nx = nxmod()
+    n, S = 6, 7
+    env = nx.Env(O.DYNOBS, S, n, seed=3, autotune=False)
+    env.reset()
+    env.rollout(25)
+    good = env.state_bytes()
+    st = nx.parse_state(good)
+    for e in st["envs"]:
+        assert e["n_balls"] == 4
+        assert all(1 <= v <= S - 2 for v in e["ball_x"] + e["ball_y"])
+    for field_off, bad in ((16, 0), (16, S - 1), (20, 0), (20, S - 1)):  # ball 0's column / row
+        b = bytearray(good)
+        b[64 + 2 * 32 + field_off] = bad  # env 2's agent block
+        with pytest.raises(nx.NavixError) as ei:
+            env.set_state(bytes(b))
+        assert ei.value.status == nx.NX_E_INVAL
+    env.set_state(good)
+    out = env.rollout(40)
+    ob = O.Batch([O.DYNOBS] * n, [S] * n, seed=3)
+    ob.reset()
+    ob.rollout(25)
+    oo = ob.rollout(40)
+    assert_outputs_equal({k: to_np(out[k]) for k in ("obs_sym", "reward", "terminated", "truncated")}, oo,
+                         what="Dynamic-Obstacles after a restore")
+    env.close()
+
+
 def test_snapshot_of_one_context_rejected_by_another_shape():
     nx = nxmod()
     a = nx.Env(O.DOORKEY, 6, 5, seed=1, autotune=False)
