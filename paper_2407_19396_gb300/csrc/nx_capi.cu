@@ -475,6 +475,14 @@ static bool lean_shape(const nx_env* env, nx_launch_shape* s, int* grid)
     return true;
 }
 
+// Whether a random-action call's outputs suit the lean kernels, which store
+// the symbolic view, the reward and both flags without testing for them and
+// write no mission and no action.
+static bool lean_outputs(const nx_out* o)
+{
+    return o && o->obs_sym && o->reward && o->terminated && o->truncated && !o->mission && !o->action;
+}
+
 // Launch shape and grid of a call: the plain instantiation, its lean form
 // (lean: a call with random actions and no action output), or (full) the
 // one that also writes the fully observable views.
@@ -709,9 +717,9 @@ static nx_status rollout_impl(nx_env* env, int32_t n_steps, int32_t act_mode, co
         }
         return NX_OK;
     }
-    // random actions without an action output run the lean kernel where the
-    // context has one (a single family, the Markov reward)
-    const bool lean = act_mode == NX_ACT_RANDOM && !(traj && traj->action);
+    // random actions with the lean kernels' outputs (lean_outputs) run the
+    // lean kernel where the context has one (the Markov reward)
+    const bool lean = act_mode == NX_ACT_RANDOM && lean_outputs(traj);
     const int nfull = n_steps / C, rem = n_steps % C;
     for (int k = 0; k < nfull; ++k) {
         st = launch_chunk_graph(env, C, full, policy, lean);
@@ -912,7 +920,7 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
         nx_req r = call_req(env, Ck, act_mode, dact, &d);
         NX_CK(env, nx_launch_configure(env->d_req, r, 0, env->stream), "configure");
         env->n_all_launches += 1;
-        st = launch_chunk_direct(env, Ck, false, false, act_mode == NX_ACT_RANDOM);
+        st = launch_chunk_direct(env, Ck, false, false, act_mode == NX_ACT_RANDOM && lean_outputs(&d));
         if (st != NX_OK) return st;
         NX_CK(env, cudaEventRecord(env->ev_done[b], env->stream), "record");
         NX_CK(env, cudaStreamWaitEvent(env->copy_stream, env->ev_done[b], 0), "wait compute");

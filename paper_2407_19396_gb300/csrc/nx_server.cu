@@ -85,15 +85,18 @@ struct RangeAlloc {
     }
 };
 
-// Per-request device block: [agents][grids][returns][digest][episodes][obs].
+// Per-request device block: [agents][grids][step][returns][digest][episodes][obs];
+// `step` takes each step's reward and flags (the lean kernels store them
+// unconditionally; the server returns per-env returns instead).
 struct Layout {
-    size_t agents, grids, returns, digest, episodes, obs, total, tail;  // tail = bytes from `returns` to the end
+    size_t agents, grids, step, returns, digest, episodes, obs, total, tail;  // tail = bytes from `returns` to the end
     static Layout of(int n, int S)
     {
         Layout l;
         l.agents = 0;
         l.grids = up256((size_t)n * sizeof(nx_agent));
-        l.returns = l.grids + up256((size_t)n * 3 * S * S);
+        l.step = l.grids + up256((size_t)n * 3 * S * S);
+        l.returns = l.step + up256((size_t)n * 4) + up256((size_t)n * 2);
         l.digest = l.returns + up256((size_t)n * 4);
         l.episodes = l.digest + up256((size_t)n * 8);
         l.obs = l.episodes + up256((size_t)n * 4);
@@ -237,6 +240,9 @@ nx_req record_of(const nx_server* s, const SReq& q, int steps)
     r.n_envs = (uint32_t)q.r.n_envs;
     r.act_mode = NX_ACT_RANDOM;
     r.obs_sym = base + q.lay.obs;
+    r.reward = (float*)(base + q.lay.step);
+    r.terminated = base + q.lay.step + up256((size_t)q.r.n_envs * 4);
+    r.truncated = r.terminated + q.r.n_envs;
     r.returns = (float*)(base + q.lay.returns);
     r.digest = (q.r.flags & NX_REQ_DIGEST) ? (uint64_t*)(base + q.lay.digest) : nullptr;
     r.episodes = (uint32_t*)(base + q.lay.episodes);

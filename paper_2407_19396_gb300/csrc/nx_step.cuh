@@ -263,6 +263,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
 {
     static_assert(!POL || (G == 1 && !RGB && !FULL), "the fused policy runs one lane per env");
     constexpr bool kLean = FAM >= 0, kLeanRandom = kLean && !POL;
+    // The lean random-action kernels run only for calls that ask for the
+    // symbolic view, the reward and both flags and for no mission (the host
+    // checks it; the server gives each request a place for them), so their
+    // stores need no test
+    constexpr bool kOuts = kLeanRandom;
     // the fused policy with several weight sets per block (fewer than 128 envs
     // per set) runs in the general instantiation; the lean ones hold one set
     constexpr bool kMultiPol = POL && !kLean;
@@ -488,7 +493,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
         const int s_end = min(emissions, s0 + kActChunk);
         for (int s = s0; s < s_end; ++s) {
             const size_t row0 = o - (size_t)gi;  // the item's first env in this slot
-            uint8_t* sym_dst = obs_sym ? obs_sym + row0 * NX_OBS_SYM_BYTES : nullptr;
+            uint8_t* sym_dst = (kOuts || obs_sym) ? obs_sym + row0 * NX_OBS_SYM_BYTES : nullptr;
             ViewOut<G> vo;
             float reward = 0.0f;
             int term = 0, trunc = 0;
@@ -603,10 +608,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 {
                     // every lane of the group stores the same values (one
                     // transaction); absent outputs are skipped
-                    if (out_reward) out_reward[o] = reward;
-                    if (out_term) out_term[o] = (uint8_t)term;
-                    if (out_trunc) out_trunc[o] = (uint8_t)trunc;
-                    if (out_mission) out_mission[o] = (uint8_t)a.mission;
+                    if (kOuts || out_reward) out_reward[o] = reward;
+                    if (kOuts || out_term) out_term[o] = (uint8_t)term;
+                    if (kOuts || out_trunc) out_trunc[o] = (uint8_t)trunc;
+                    if (!kOuts && out_mission) out_mission[o] = (uint8_t)a.mission;
                     ret += reward;
                     eps += (uint32_t)(term || trunc);
                 }
@@ -615,7 +620,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                 // than staging there); the staged path below serves the narrow
                 // groups and the outputs that read the staged record (digest,
                 // the categorical first-person view).
-                if (G >= 8 && !digest && !(FULL && obs_cat_fp) && obs_sym)
+                if (G >= 8 && !digest && !(FULL && obs_cat_fp) && (kOuts || obs_sym))
                     write_view(grp, vo, obs_sym + o * NX_OBS_SYM_BYTES);
             }
             // fused policy: the next step's first layer runs during the stores
