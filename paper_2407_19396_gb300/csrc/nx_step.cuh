@@ -90,20 +90,18 @@ __device__ __forceinline__ void move_ball(const Grp<G>& grp, uint8_t* g, int S, 
 
 // Intervention (rotate / forward / pickup / drop / toggle / done), the
 // Dynamic-Obstacles transition, then time, truncation, reward and termination.
-// skip: the env starts an episode in this step, which is then a no-op (no
-// ball move, no action, time unchanged, reward 0 and both flags 0).
 // The balls' draws: d[b] for groups of several lanes (drawn in parallel by
 // the caller); one lane per env draws each ball's inside the ball loop,
 // which is not unrolled (a smaller loop body: the unrolled loop's code
 // missed the instruction cache).
 template <int G>
 __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, int W, int family, int max_steps, AgentReg& a,
-                                         int action, bool skip, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
+                                         int action, const uint32_t (&d)[8], uint32_t reward_mode, float lava_reward,
                                          float action_cost, float time_cost, float& reward, int& term, int& trunc,
                                          nx_ctl* ctl, uint64_t seed, uint32_t key)
 {
     // transition system: each ball, in index order, moves (move_ball)
-    if (family == NX_DYNOBS && !skip) {
+    if (family == NX_DYNOBS) {
         if constexpr (G == 1) {
             const uint32_t episode = a.episode, t = (uint32_t)a.t;
 #pragma unroll 1
@@ -123,8 +121,8 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
     // action is a no-op that sets the sticky invalid flag (published to the
     // device flags when the work item ends).
     const int n_act = family == NX_DYNOBS ? 3 : 7;
-    a.invalid |= (!skip && (unsigned)action > 6u) ? 1 : 0;
-    const int act = (!skip && (unsigned)action < (unsigned)n_act) ? action : 7;  // 7: no-op
+    a.invalid |= (unsigned)action > 6u ? 1 : 0;
+    const int act = (unsigned)action < (unsigned)n_act ? action : 7;  // 7: no-op
     const int fxd = (a.dir == 0) - (a.dir == 2), fyd = (a.dir == 1) - (a.dir == 3);
     const int fx = a.x + fxd, fy = a.y + fyd;
     // (with a wall margin, W > S, a cell beyond the grid reads as a wall)
@@ -158,8 +156,8 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
         grp.sync();
     }
     // time and truncation; reward and termination on the goal / lava / hit events
-    a.t += skip ? 0 : 1;
-    trunc = !skip && a.t >= max_steps;
+    a.t += 1;
+    trunc = a.t >= max_steps;
     // (selects; only MiniGrid's success reward, a rare event, takes a branch)
     float rgoal = 1.0f;
     if (goal && reward_mode == NX_REWARD_MINIGRID)
@@ -168,8 +166,8 @@ __device__ __forceinline__ void env_step(const Grp<G>& grp, uint8_t* g, int S, i
     term = (goal || lava || hit) ? 1 : 0;
     // the shaping terms of Table 5: action_cost for every action but done
     // (0..5), then time_cost (subtracting 0 leaves a reward unchanged)
-    reward = __fsub_rn(reward, (!skip && (unsigned)action < 6u) ? action_cost : 0.0f);
-    reward = __fsub_rn(reward, skip ? 0.0f : time_cost);
+    reward = __fsub_rn(reward, (unsigned)action < 6u ? action_cost : 0.0f);
+    reward = __fsub_rn(reward, time_cost);
     a.done = term || trunc;
 }
 
@@ -562,18 +560,17 @@ __global__ void __launch_bounds__(kMaxThreads, 2) nx_step_kernel(const nx_kparam
                     action = actions[(size_t)(call0 + (uint32_t)s) * nreq + local];
                 }
                 if (out_action) out_action[o] = (int8_t)action;
-                // groups of 8 or more lanes step every env, one that starts an
-                // episode as a no-op (a branch fewer on their step's chain);
-                // narrower groups branch around the step of a starting env
-                if (G >= 8 || !starts) {
+                if (starts) {
+                    // the new episode's start: reward padding 0, the action is ignored
+                } else {
                     uint32_t d[8];
-                    if (G > 1 && family == NX_DYNOBS && !starts) {  // (one lane per env draws inside env_step; a starting env has no ball move)
+                    if (G > 1 && family == NX_DYNOBS) {  // (one lane per env draws inside env_step)
                         const uint32_t episode = a.episode, t = (uint32_t)a.t;
                         group_draws(grp, a.nb, d, [&](uint32_t k) -> uint32_t {
                             return draw(seed, key, episode, t, PURPOSE_BALL, k);
                         });
                     }
-                    env_step(grp, mygrid, S, W, family, max_steps, a, action, G >= 8 && starts, d, reward_mode, lava_reward, action_cost,
+                    env_step(grp, mygrid, S, W, family, max_steps, a, action, d, reward_mode, lava_reward, action_cost,
                              time_cost, reward, term, trunc, p.ctl, seed, key);
                 }
                 // (every grid write above -- a reset, a ball move, the action's
