@@ -282,6 +282,29 @@ def test_ball_moves_stay_on_free_neighbours():
         assert len(set(after)) == 4
 
 
+@pytest.mark.parametrize("size", [5, 6, 8, 16, 19])
+def test_balls_never_leave_the_interior(size):
+    """Balls are placed in the grid's interior and only move to empty cells,
+    so every ball of every reachable state lies in 1..size-2 on both axes and
+    sits on a ball cell of the grid (the step kernels read a ball's eight
+    neighbours without bounds tests, and a restored state must satisfy it)."""
+    n = 8
+    b = O.Batch([O.DYNOBS] * n, [size] * n, seed=size)
+    b.reset()
+    seen_move = False
+    for t in range(400):
+        b.step()
+        for i in range(n):
+            s = b.state(i)
+            ent = np.frombuffer(s["ent"], np.uint8).reshape(size, size)
+            assert s["n_balls"] == 4
+            for x, y in zip(s["ball_x"], s["ball_y"]):
+                assert 1 <= x <= size - 2 and 1 <= y <= size - 2, (t, i, x, y)
+                assert ent[y, x] == 6
+            seen_move = seen_move or t > 0
+    assert seen_move
+
+
 @pytest.mark.parametrize("family,size,seed", [(O.DOORKEY, 8, 1), (O.FOURROOMS, 19, 2), (O.DYNOBS, 8, 3),
                                               (O.SIMPLE_CROSSING, 11, 4)])
 def test_full_views_agree_with_the_grid_and_the_egocentric_view(family, size, seed):
