@@ -196,3 +196,61 @@ def test_concurrent_submitters_and_waiters():
     assert len(results) == len(reqs)
     for r in reqs[:30]:
         _same(results[r], oracle_request(*r))
+
+
+# (lanes per env, envs per block, staging parts); (0, 0, 0): the server's own shapes
+SERVER_SHAPES = [(0, 0, 0), (1, 64, 2), (1, 128, 1), (4, 32, 1), (8, 16, 1), (16, 8, 1), (32, 4, 1)]
+
+
+def _random_requests(rng, n, max_envs, max_h):
+    """Requests of every family at its valid sizes and variants."""
+    reqs = []
+    for _ in range(n):
+        f = int(rng.integers(0, 11))
+        s = int(rng.choice([x for x in range(5, 20) if O.max_variant(f, x) >= 0]))
+        v = int(rng.integers(0, O.max_variant(f, s) + 1))
+        ne = int(min(max_envs, max(1, np.floor(np.exp(rng.uniform(0, np.log(max_envs + 1)))))))
+        reqs.append((f, s, ne, int(rng.integers(1, max_h + 1)), int(rng.integers(0, 2**63)), v,
+                     bool(rng.random() < 0.7)))
+    return reqs
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_request_mixes_match_the_oracle(case):
+    """Seeded random servers (launch shape, chunk length, budget, reward mode,
+    lava reward, shaping costs, balls) serving random request mixes (every
+    family, size and variant, 1 to 600 envs, 1 to 300 steps, with or without
+    the digest) submitted in bursts: every result equals the oracle's."""
+    import time
+
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    rng = np.random.default_rng(9100 + case)
+    lanes, envs, staging = SERVER_SHAPES[int(rng.integers(0, len(SERVER_SHAPES)))]
+    kw = dict(reward_mode=int(rng.integers(0, 2)), lava_reward=float(rng.choice([0.0, -1.0])),
+              action_cost=float(rng.choice([0.0, 0.0125])), time_cost=float(rng.choice([0.0, 0.004])),
+              n_balls=int(rng.integers(0, 5)))
+    spl = int(rng.choice([1, 8, 32, 128]))
+    budget = int(rng.choice([16 << 20, 64 << 20, 256 << 20]))
+    reqs = _random_requests(rng, 20, 600, 300)
+    what = f"case {case}: shape {(lanes, envs, staging)} spl {spl} budget {budget} {kw}"
+    srv = nx.Server(budget_bytes=budget, steps_per_launch=spl, group_lanes=lanes, envs_per_cta=envs, staging=staging,
+                    **kw)
+    try:
+        tickets = []
+        for r in reqs:
+            tickets.append(srv.submit(*r[:6], digest=r[6]))
+            if rng.random() < 0.3:
+                time.sleep(float(rng.uniform(0.0, 0.003)))
+        res = [srv.wait(t, timeout_s=120.0) for t in tickets]
+        assert srv.stats()["peak_bytes"] <= budget, what
+    finally:
+        srv.close()
+    for r, m in zip(reqs, res):
+        f, s, ne, h, seed, v, dig = r
+        assert m["status"] == 0 and m["env_steps"] == ne * h, f"{what} {r}"
+        o = oracle_request(f, s, ne, h, seed, variant=v, **kw)
+        np.testing.assert_array_equal(m["returns"], o["returns"], err_msg=f"{what} {r}")
+        np.testing.assert_array_equal(m["final_obs"], o["final_obs"], err_msg=f"{what} {r}")
+        assert m["episodes"] == o["episodes"], f"{what} {r}"
+        assert m["digest"] == (o["digest"] if dig else 0), f"{what} {r}"
