@@ -209,3 +209,56 @@ def test_policy_snapshot_resume_and_shards():
     for k in KEYS:
         np.testing.assert_array_equal(b1[k], to_np(b2[k]), err_msg=k)
     whole.close()
+
+
+def _policy_case(i):
+    """Case i of the random sweep: a weight-set size, the agents, a family run
+    layout that respects the work list's weight-set boundaries (runs of a
+    multiple of envs_per_agent below 128 envs per set; runs inside one set
+    from 128 on), exploration, shifts, weight ranges and reward settings."""
+    rng = np.random.default_rng(9300 + i)
+    epa = int(rng.choice([16, 32, 64, 128, 256]))
+    A = int(rng.integers(1, max(1, 1024 // epa) + 1))
+    pool = []
+    for f in rng.choice(11, size=3, replace=False):
+        f = int(f)
+        s = int(rng.choice([x for x in range(5, 20) if O.max_variant(f, x) >= 0]))
+        pool.append((f, s, 0, int(rng.integers(0, O.max_variant(f, s) + 1))))
+    descs = []
+    for _ in range(A):
+        if epa < 128:
+            descs += [pool[int(rng.integers(0, 3))]] * epa
+        else:
+            cuts = sorted(int(c) for c in rng.choice(np.arange(1, epa), size=int(rng.integers(0, 3)), replace=False))
+            for k, (lo, hi) in enumerate(zip([0] + cuts, cuts + [epa])):
+                d = pool[int(rng.integers(0, 3))]
+                if k == 0 and descs and d == descs[-1]:
+                    d = pool[(pool.index(d) + 1) % 3]  # equal neighbours would merge into a run across the sets
+                descs += [d] * (hi - lo)
+    kw = dict(reward_mode=int(rng.integers(0, 2)), action_cost=float(rng.choice([0.0, 0.0125])),
+              time_cost=float(rng.choice([0.0, 0.004])), lava_reward=float(rng.choice([0.0, -1.0])))
+    return dict(epa=epa, A=A, descs=descs, kw=kw, eps=int(rng.choice([0, 2**28, 2**30])),
+                shift1=int(rng.integers(2, 5)), shift2=int(rng.integers(5, 8)), wmax=int(rng.choice([6, 12, 20])),
+                T=int(rng.integers(50, 200)), seed=int(rng.integers(0, 2**31)))
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_random_policy_configurations_match_the_oracle(case):
+    nx = nxmod()
+    c = _policy_case(case)
+    what = f"case {case}: epa {c['epa']} A {c['A']} eps {c['eps']} shifts {c['shift1']},{c['shift2']} {c['kw']}"
+    pol = random_policy(c["A"], seed=c["seed"] & 0xFFFF, wmax=c["wmax"], shift1=c["shift1"], shift2=c["shift2"],
+                        epsilon=c["eps"], epa=c["epa"])
+    env = gpu_env_with(nx, c["descs"], c["seed"], pol, **c["kw"])
+    try:
+        env.reset()
+        out = env.rollout(c["T"], policy=True)
+        ob = oracle_batch_for(c["descs"], c["seed"], **c["kw"])
+        ob.reset()
+        oo = ob.rollout_policy(c["T"], pol)
+        oo["action"] = oo.pop("actions")
+        assert_outputs_equal(out, oo, keys=KEYS, what=what)
+        assert_states_equal(env.state()["envs"], ob, what=what)
+        assert env.flags() & 4 == 0, what
+    finally:
+        env.close()
