@@ -255,7 +255,9 @@ nx_status nx_rollout_per_family(nx_env* env, int32_t n_steps, int32_t act_mode, 
  * is int8 [n_steps, n_envs] (ignored for NX_ACT_RANDOM); the host outputs are
  * [D, n_envs, ...] with D = host_traj->depth, step i written to host slot
  * i % D (depth <= 0, or >= n_steps: D = n_steps, one slot per step), so a
- * long rollout can stream through a bounded pinned ring.  Any output may be
+ * long rollout can stream through a bounded pinned ring; every slot ends
+ * holding the last step written there, and nothing is written beyond the
+ * D slots, whatever the chunk length (steps_per_launch).  Any output may be
  * NULL; the fully observable views and the action output are not available
  * here (NX_E_INVAL). */
 nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const int8_t* host_actions_TN,

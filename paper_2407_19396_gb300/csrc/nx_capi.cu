@@ -924,14 +924,19 @@ nx_status nx_rollout_host(nx_env* env, int32_t n_steps, int32_t act_mode, const 
         if (st != NX_OK) return st;
         NX_CK(env, cudaEventRecord(env->ev_done[b], env->stream), "record");
         NX_CK(env, cudaStreamWaitEvent(env->copy_stream, env->ev_done[b], 0), "wait compute");
-        // the chunk's Ck slots go to host slots t0 % D onwards, in two
-        // copies where they wrap around the end of the ring
-        const int s0 = t0 % D, first = std::min(Ck, D - s0);
+        // only the chunk's last min(Ck, D) steps survive in a ring of D
+        // slots (a chunk longer than the ring overwrites its own first
+        // steps); they go to host slots (t0 + skip) % D onwards, in two
+        // copies where they wrap around the end of the ring, never more
+        // than D slots in all
+        const int keep = std::min(Ck, D), skip = Ck - keep;
+        const int s0 = (t0 + skip) % D, first = std::min(keep, D - s0);
         auto copy_back = [&](void* host, const void* dev, size_t step_bytes) -> cudaError_t {
-            cudaError_t e = cudaMemcpyAsync((uint8_t*)host + (size_t)s0 * step_bytes, dev, (size_t)first * step_bytes,
+            const uint8_t* src = (const uint8_t*)dev + (size_t)skip * step_bytes;
+            cudaError_t e = cudaMemcpyAsync((uint8_t*)host + (size_t)s0 * step_bytes, src, (size_t)first * step_bytes,
                                             cudaMemcpyDeviceToHost, env->copy_stream);
-            if (e == cudaSuccess && first < Ck)
-                e = cudaMemcpyAsync(host, (const uint8_t*)dev + (size_t)first * step_bytes, (size_t)(Ck - first) * step_bytes,
+            if (e == cudaSuccess && first < keep)
+                e = cudaMemcpyAsync(host, src + (size_t)first * step_bytes, (size_t)(keep - first) * step_bytes,
                                     cudaMemcpyDeviceToHost, env->copy_stream);
             return e;
         };

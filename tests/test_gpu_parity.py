@@ -370,11 +370,13 @@ def test_host_buffer_rollout_equals_device_rollout():
     d.close()
 
 
-@pytest.mark.parametrize("depth", [45, 64, 149])
+@pytest.mark.parametrize("depth", [1, 3, 20, 45, 64, 149])
 def test_host_ring_holds_the_last_steps(depth):
     """Host outputs shorter than the horizon form a ring (step i in slot
-    i % depth), including rings that wrap inside a 32-step chunk; every slot
-    equals the oracle's output of the last step written there."""
+    i % depth), including rings that wrap inside a 32-step chunk and rings
+    shorter than a chunk (only the chunk's last steps are copied back, never
+    past the ring's end); every slot equals the oracle's output of the last
+    step written there."""
     nx = nxmod()
     descs = mixed_descs(300, MIXED)
     T = 150
