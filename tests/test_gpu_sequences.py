@@ -54,8 +54,15 @@ def draw_sequence(i):
         T = int(rng.integers(1, 150))
         ops.append(dict(op=op, T=T, depth=T if rng.random() < 0.5 else int(rng.integers(1, T + 1)),
                         buffered=bool(rng.random() < 0.4), aseed=int(rng.integers(0, 2**16))))
-    return dict(descs=descs, seed=int(rng.integers(0, 2**31)), lanes=lanes, envs=envs, staging=staging,
-                spl=int(rng.choice([1, 7, 64, 128])), kw=kw, ops=ops)
+    c = dict(descs=descs, seed=int(rng.integers(0, 2**31)), lanes=lanes, envs=envs, staging=staging,
+             spl=int(rng.choice([1, 7, 64, 128])), kw=kw, ops=ops)
+    # a snapshot is restored into a context of its own launch shape (or an
+    # autotuned one): snapshots do not depend on where the envs ran
+    c["autotune"] = bool(rng.random() < 0.25)
+    for op in ops:
+        op["shape"] = SHAPES[int(rng.integers(0, len(SHAPES)))]
+        op["autotune"] = bool(rng.random() < 0.25)
+    return c
 
 
 def _keys(missions):
@@ -69,11 +76,11 @@ def test_random_call_sequence_matches_the_oracle(case):
     c = draw_sequence(case)
     descs, n = c["descs"], len(c["descs"])
 
-    def make():
-        return nx.Env(descs=descs, seed=c["seed"], autotune=False, group_lanes=c["lanes"], envs_per_cta=c["envs"],
-                      staging=c["staging"], steps_per_launch=c["spl"], **c["kw"])
+    def make(shape, autotune):
+        return nx.Env(descs=descs, seed=c["seed"], autotune=autotune, group_lanes=shape[0], envs_per_cta=shape[1],
+                      staging=shape[2], steps_per_launch=c["spl"], **c["kw"])
 
-    env = make()
+    env = make((c["lanes"], c["envs"], c["staging"]), c["autotune"])
     ob = oracle_batch_for(descs, c["seed"], **c["kw"])
     missions = env.want_mission
     keys = _keys(missions)
@@ -106,7 +113,7 @@ def test_random_call_sequence_matches_the_oracle(case):
             elif op["op"] == "snapshot":
                 snap = env.state_bytes()
                 env.close()
-                env = make()
+                env = make(op["shape"], op["autotune"])
                 env.set_state(snap)
                 assert env.state_bytes() == snap, what
                 assert_states_equal(env.state()["envs"], ob, what=what)
@@ -130,3 +137,6 @@ def test_the_sequences_cover_every_call():
     assert sum(op["op"] == "snapshot" for s in seqs for op in s["ops"]) >= 5
     assert any(op["op"] == "rollout_host" and op["depth"] < op["T"] for s in seqs for op in s["ops"])
     assert any(s["lanes"] == 1 for s in seqs) and any(s["lanes"] >= 8 for s in seqs)
+    assert any(s["autotune"] for s in seqs)
+    assert any(op["op"] == "snapshot" and op["shape"] != (s["lanes"], s["envs"], s["staging"]) for s in seqs
+               for op in s["ops"])

@@ -254,3 +254,53 @@ def test_random_request_mixes_match_the_oracle(case):
         np.testing.assert_array_equal(m["final_obs"], o["final_obs"], err_msg=f"{what} {r}")
         assert m["episodes"] == o["episodes"], f"{what} {r}"
         assert m["digest"] == (o["digest"] if dig else 0), f"{what} {r}"
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_random_cancellations_leave_the_rest_exact(case):
+    """Random requests, a random third of them withdrawn at random moments
+    (queued, running or already finished): a withdrawn request reports
+    NX_E_CANCELED, one that finished first refuses the withdrawal and keeps
+    its result, every other result equals the oracle's, and the server
+    ends with all its memory back."""
+    import time
+
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    rng = np.random.default_rng(9200 + case)
+    reqs = _random_requests(rng, 30, 1000, 400)
+    srv = nx.Server(budget_bytes=int(rng.choice([8 << 20, 32 << 20])), steps_per_launch=int(rng.choice([8, 32, 128])))
+    try:
+        tickets, canceled = [], set()
+        for i, r in enumerate(reqs):
+            tickets.append(srv.submit(*r[:6], digest=r[6]))
+            if rng.random() < 0.3:
+                time.sleep(float(rng.uniform(0.0, 0.004)))
+            if i >= 2 and rng.random() < 0.35:
+                j = int(rng.integers(max(0, i - 5), i + 1))  # a recent request: queued, running or done
+                if j not in canceled:
+                    try:
+                        srv.cancel(tickets[j])
+                        canceled.add(j)
+                    except nx.NavixError as e:
+                        assert e.status == nx.NX_E_STATE  # finished before the withdrawal
+        finished = []
+        for i, t in enumerate(tickets):
+            if i in canceled:
+                with pytest.raises(nx.NavixError) as ei:
+                    srv.wait(t, timeout_s=120.0)
+                assert ei.value.status == nx.NX_E_CANCELED
+            else:
+                finished.append((reqs[i], srv.wait(t, timeout_s=120.0)))
+        st = srv.stats()
+        assert st["canceled"] == len(canceled) and st["finished"] == len(finished)
+        assert st["in_use_bytes"] == 0
+    finally:
+        srv.close()
+    assert canceled
+    for r, m in finished:
+        f, s, ne, h, seed, v, dig = r
+        o = oracle_request(f, s, ne, h, seed, variant=v)
+        np.testing.assert_array_equal(m["returns"], o["returns"], err_msg=str(r))
+        np.testing.assert_array_equal(m["final_obs"], o["final_obs"], err_msg=str(r))
+        assert m["episodes"] == o["episodes"] and m["digest"] == (o["digest"] if dig else 0), r
