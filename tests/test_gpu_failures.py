@@ -239,3 +239,36 @@ def test_debug_build_parity_and_a_corrupted_agent_block():
     r = subprocess.run([sys.executable, "-c", f"ROOT = {ROOT!r}\n" + DEBUG_CHECK], capture_output=True, text=True,
                        timeout=600, cwd=ROOT)
     assert r.returncode == 0 and "DEBUG-CHECKS-OK" in r.stdout, (r.stdout[-2000:], r.stderr[-4000:])
+
+
+DEBUG_FUZZ = r'''
+import sys
+sys.path.insert(0, ROOT)
+import torch
+from paper_2407_19396_gb300 import build, navixgb as nx
+nx.LIB_PATH = build.DEBUG_LIB
+torch.cuda.set_device(0)
+from tests import test_gpu_fuzz as F, test_gpu_sequences as Q
+for c in range(0, F.N_CASES, 3):
+    F.test_random_configuration_matches_the_oracle(c)
+for c in range(0, 32, 2):
+    F.test_random_output_subsets_match_the_oracle(c)
+for c in range(0, Q.N_CASES, 2):
+    Q.test_random_call_sequence_matches_the_oracle(c)
+assert nx.LIB_PATH == build.DEBUG_LIB
+print("DEBUG-FUZZ-OK")
+'''
+
+
+def test_debug_build_on_random_configurations():
+    """A third of the random rollouts, half of the random output subsets and
+    half of the random call sequences again with the NX_DEBUG library, whose
+    bounds checks before every grid write and output store would set the
+    bounds flag (each case asserts that no flag but the invalid-action one is
+    set, and that every output equals the oracle's)."""
+    from paper_2407_19396_gb300 import build
+
+    assert os.path.exists(build.DEBUG_LIB)
+    r = subprocess.run([sys.executable, "-c", f"ROOT = {ROOT!r}\n" + DEBUG_FUZZ], capture_output=True, text=True,
+                       timeout=900, cwd=ROOT)
+    assert r.returncode == 0 and "DEBUG-FUZZ-OK" in r.stdout, (r.stdout[-2000:], r.stderr[-4000:])

@@ -221,6 +221,7 @@ def test_random_output_subsets_match_the_oracle(case):
             if not want[key]:
                 assert g.get(key) is None, f"{what}: {key} was not asked for"
         assert_states_equal(env.state()["envs"], ob, what=what)
+        assert env.flags() & ~1 == 0, what  # no bounds or wait flag; bit 0 only for invalid buffered actions
     finally:
         env.close()
 
