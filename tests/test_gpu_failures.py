@@ -22,7 +22,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
-from tests.gpu_util import assert_outputs_equal, mixed_descs, oracle_batch_for, oracle_request  # noqa: E402
+from tests.gpu_util import mixed_descs, oracle_request  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))

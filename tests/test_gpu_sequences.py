@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
 from paper_2407_19396_gb300 import inputs  # noqa: E402
-from tests.gpu_util import assert_outputs_equal, assert_states_equal, oracle_batch_for, to_np  # noqa: E402
+from tests.gpu_util import assert_outputs_equal, assert_states_equal, oracle_batch_for  # noqa: E402
 from tests.test_gpu_fuzz import SHAPES, oracle_steps, ring_of  # noqa: E402
 
 pytestmark = pytest.mark.gpu
