@@ -140,3 +140,40 @@ def test_the_sequences_cover_every_call():
     assert any(s["autotune"] for s in seqs)
     assert any(op["op"] == "snapshot" and op["shape"] != (s["lanes"], s["envs"], s["staging"]) for s in seqs
                for op in s["ops"])
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_two_contexts_interleaved_on_two_streams(case):
+    """Two contexts of different batches and launch shapes, each on its own
+    stream, issue their rollouts alternately without waiting for each other;
+    each context's outputs equal the oracle's for its batch alone."""
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    cfg = [draw_sequence(case), draw_sequence(case + N_CASES // 2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    envs, outs = [], [[], []]
+    rng = np.random.default_rng(9900 + case)
+    Ts = [[int(t) for t in rng.integers(1, 150, size=3)] for _ in range(2)]
+    try:
+        for c, st in zip(cfg, streams):
+            with torch.cuda.stream(st):
+                e = nx.Env(descs=c["descs"], seed=c["seed"], autotune=False, group_lanes=c["lanes"],
+                           envs_per_cta=c["envs"], staging=c["staging"], steps_per_launch=c["spl"], **c["kw"])
+                e.reset()
+                envs.append(e)
+        for r in range(3):
+            for k in range(2):
+                with torch.cuda.stream(streams[k]):
+                    outs[k].append(envs[k].rollout(Ts[k][r]))
+        torch.cuda.synchronize()
+        for k in range(2):
+            c = cfg[k]
+            ob = oracle_batch_for(c["descs"], c["seed"], **c["kw"])
+            ob.reset()
+            for r in range(3):
+                oo = oracle_steps(ob, Ts[k][r], None, False)
+                assert_outputs_equal(outs[k][r], oo, what=f"case {case} context {k} rollout {r}")
+            assert_states_equal(envs[k].state()["envs"], ob, what=f"case {case} context {k}")
+    finally:
+        for e in envs:
+            e.close()

@@ -136,3 +136,33 @@ def test_noalloc_against_the_oracle_and_degenerate_calls():
     want = b.rollout(T)
     for k in ("obs_sym", "reward", "terminated", "truncated"):
         np.testing.assert_array_equal(got[k].cpu().numpy(), want[k], err_msg=k)
+
+
+@pytest.mark.parametrize("case", range(16))
+def test_noalloc_random_configurations_against_the_oracle(case):
+    """Seeded random calls -- any family at a random size, 1 to 600 envs, 1
+    to 300 steps, an output ring or not, random or buffered actions -- each
+    equal to the oracle at every kept step."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    rng = np.random.default_rng(9700 + case)
+    f = int(rng.integers(0, 11))
+    size = int(rng.choice([s for s in range(5, 20) if O.max_variant(f, s) >= 0]))
+    n, T = int(rng.integers(1, 601)), int(rng.integers(1, 301))
+    depth = T if rng.random() < 0.5 else int(rng.integers(1, T + 1))
+    seed = int(rng.integers(0, 2**31))
+    acts = (inputs.random_actions(seed & 0xFFFF, (T, n), n_actions=7, invalid_fraction=0.02)
+            if rng.random() < 0.4 else None)
+    got = _noalloc(nx, f, size, n, seed, T, None if acts is None else torch.from_numpy(acts).cuda(), depth)
+    b = O.Batch([f] * n, [size] * n, seed=seed)
+    b.reset()
+    want = b.rollout(T, actions=acts)
+    for k in ("obs_sym", "reward", "terminated", "truncated"):
+        ring = np.empty((depth,) + want[k].shape[1:], want[k].dtype)
+        for t in range(T - depth, T):
+            ring[t % depth] = want[k][t]
+        np.testing.assert_array_equal(got[k].cpu().numpy(), ring, err_msg=f"case {case} family {f} size {size} "
+                                                                             f"n {n} T {T} depth {depth} {k}")
