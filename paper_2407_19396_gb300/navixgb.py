@@ -66,6 +66,44 @@ OUT_KEYS = ("obs_sym", "obs_rgb", "reward", "terminated", "truncated", "obs_full
             "obs_rgb_full", "mission", "action")
 
 
+def out_layout(key, side):
+    """Element type and per-env shape of output `key` (side: the fully
+    observable views' side, the batch's largest grid)."""
+    return {"obs_sym": ("uint8", (7, 7, 3)), "obs_rgb": ("uint8", (224, 224, 3)), "reward": ("float32", ()),
+            "terminated": ("uint8", ()), "truncated": ("uint8", ()), "obs_full": ("uint8", (side, side, 3)),
+            "obs_cat": ("uint8", (side, side)), "obs_cat_fp": ("uint8", (7, 7)),
+            "obs_rgb_full": ("uint8", (32 * side, 32 * side, 3)), "mission": ("uint8", ()),
+            "action": ("int8", ())}[key]
+
+
+def check_out_buffer(key, a, n, side, slots, device):
+    """Refuses an output buffer the library would write outside of: it must
+    be contiguous, of the output's element type, shaped [slots', n, ...] with
+    slots' >= slots (or [n, ...] when slots is None), and on the device
+    (device=True) or in host memory."""
+    dtype, per_env = out_layout(key, side)
+    shape = tuple(int(x) for x in a.shape)
+    if slots is None:
+        ok_shape = shape == (n,) + per_env
+        want = f"[{n}, ...] = {(n,) + per_env}"
+    else:
+        ok_shape = len(shape) == 2 + len(per_env) and shape[0] >= slots and shape[1:] == (n,) + per_env
+        want = f"[>= {slots}, {n}, ...] = {(slots, n) + per_env}"
+    if not ok_shape:
+        raise ValueError(f"output {key}: shape {shape}, expected {want}")
+    if isinstance(a, np.ndarray):
+        if device:
+            raise ValueError(f"output {key}: a host array where a device tensor is needed")
+        if a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"output {key}: needs a C-contiguous {dtype} array, got {a.dtype}")
+        return
+    if str(a.dtype) != f"torch.{dtype}" or not a.is_contiguous():
+        raise ValueError(f"output {key}: needs a contiguous torch.{dtype} tensor, got {a.dtype}")
+    if bool(a.is_cuda) != device:
+        raise ValueError(f"output {key}: a {'host' if a.is_cuda is False else 'device'} tensor where a "
+                         f"{'device' if device else 'host'} one is needed")
+
+
 class nx_policy(ctypes.Structure):
     _fields_ = [("n_agents", ctypes.c_int32), ("envs_per_agent", ctypes.c_int32),
                 ("w1", ctypes.c_void_p), ("b1", ctypes.c_void_p), ("w2", ctypes.c_void_p), ("b2", ctypes.c_void_p),
@@ -441,12 +479,17 @@ class Env:
         o["action"] = torch.empty(lead + (n,), dtype=torch.int8, device=self.device) if self.want_action else None
         return o
 
-    def out_struct(self, o, depth=1):
+    def out_struct(self, o, depth=None):
+        """The nx_out of device buffers `o` ([n, ...] each for reset and step,
+        [>= depth, n, ...] for a rollout ring of `depth` slots), each checked
+        against the layout the library writes."""
         s = nx_out()
         for k in OUT_KEYS:
             t = o.get(k)
+            if t is not None:
+                check_out_buffer(k, t, self.n, self.side, depth, device=True)
             setattr(s, k, t.data_ptr() if t is not None else None)
-        s.depth = depth
+        s.depth = 1 if depth is None else depth
         s.full_side = self.side
         return s
 
@@ -499,6 +542,7 @@ class Env:
             if a is None:
                 setattr(s, k, None)
                 continue
+            check_out_buffer(k, a, n, self.side, 1, device=False)
             if isinstance(a, np.ndarray):
                 setattr(s, k, a.ctypes.data)
             else:

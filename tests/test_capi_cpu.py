@@ -66,3 +66,36 @@ def test_product_binding_does_not_import_the_oracle():
         if f.endswith(".py"):
             txt = open(os.path.join(ROOT, "paper_2407_19396_gb300", f)).read()
             assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_binding_refuses_output_buffers_the_library_would_overrun():
+    """The binding checks every caller-supplied output buffer before it
+    hands a pointer to the library: element type, contiguity, [slots, n, ...]
+    shape with enough slots, and host versus device memory."""
+    import numpy as np
+    import torch
+
+    from paper_2407_19396_gb300.navixgb import check_out_buffer
+
+    n, side = 5, 8
+    check_out_buffer("obs_sym", np.zeros((3, n, 7, 7, 3), np.uint8), n, side, 3, device=False)
+    check_out_buffer("obs_sym", np.zeros((4, n, 7, 7, 3), np.uint8), n, side, 3, device=False)  # more slots: fine
+    check_out_buffer("reward", np.zeros((n,), np.float32), n, side, None, device=False)
+    check_out_buffer("obs_full", torch.zeros((2, n, side, side, 3), dtype=torch.uint8), n, side, 2, device=False)
+    check_out_buffer("action", torch.zeros((2, n), dtype=torch.int8), n, side, 2, device=False)
+    bad = [
+        ("obs_sym", np.zeros((2, n, 7, 7, 3), np.uint8), 3, False),         # fewer slots than the ring
+        ("obs_sym", np.zeros((3, n + 1, 7, 7, 3), np.uint8), 3, False),     # another env count
+        ("reward", np.zeros((3, n), np.uint8), 3, False),                   # 1-byte elements for 4-byte rewards
+        ("reward", np.zeros((3, n), np.float64), 3, False),
+        ("terminated", np.zeros((n, 3), np.uint8).T, 3, False),             # not C-contiguous
+        ("obs_cat", np.zeros((3, n, side - 1, side - 1), np.uint8), 3, False),  # views of a smaller side
+        ("obs_sym", np.zeros((n, 7, 7, 3), np.uint8), 3, False),            # no slot dimension
+        ("mission", np.zeros((3, n), np.uint8), 3, True),                   # host array for a device output
+        ("action", torch.zeros((3, n), dtype=torch.uint8), 3, False),       # unsigned actions
+        ("reward", torch.zeros((3, n), dtype=torch.float32), 3, True),      # host tensor for a device output
+        ("obs_sym", torch.zeros((3, n, 7, 7, 3), dtype=torch.uint8)[:, :, :, :, :1].expand(3, n, 7, 7, 3), 3, False),
+    ]
+    for key, a, slots, dev in bad:
+        with pytest.raises(ValueError):
+            check_out_buffer(key, a, n, side, slots, device=dev)

@@ -282,3 +282,36 @@ def test_snapshot_of_one_context_rejected_by_another_shape():
         b.set_state(a.state_bytes())
     a.close()
     b.close()
+
+
+def test_binding_refuses_bad_output_buffers_before_any_launch():
+    """Output buffers too small, of another element type, non-contiguous or
+    in the wrong memory are refused by the binding (ValueError) before the
+    library sees a pointer; the context's state is untouched and the next
+    call with good buffers runs normally."""
+    nx = nxmod()
+    n = 40
+    env = nx.Env(O.DOORKEY, 8, n, seed=3, autotune=False, obs_full=True)
+    env.reset()
+    snap = env.state_bytes()
+    good = env.alloc_out(16)
+    bads = [dict(good, obs_sym=good["obs_sym"][:8]),                                    # 8 slots for a 16-step ring
+            dict(good, reward=torch.empty((16, n), dtype=torch.uint8, device="cuda")),  # 1-byte rewards
+            dict(good, terminated=torch.empty((n, 16), dtype=torch.uint8, device="cuda").t()),  # not contiguous
+            dict(good, truncated=torch.empty((16, n), dtype=torch.uint8)),              # host memory
+            dict(good, obs_full=torch.empty((16, n, 7, 7, 3), dtype=torch.uint8, device="cuda"))]  # side 7, not 8
+    for b in bads:
+        with pytest.raises(ValueError):
+            env.rollout(16, out=b)
+    with pytest.raises(ValueError):
+        env.step(out=dict(env.alloc_out(), obs_sym=torch.empty((n - 1, 7, 7, 3), dtype=torch.uint8, device="cuda")))
+    with pytest.raises(ValueError):
+        env.rollout_host(16, out={"obs_sym": np.zeros((16, n, 7, 7, 3), np.uint8), "reward": np.zeros((16, n), np.float64),
+                                  "terminated": None, "truncated": None, "mission": None})
+    torch.cuda.synchronize()
+    assert env.state_bytes() == snap
+    out = env.rollout(16, out=good)
+    ob = oracle_batch_for([(O.DOORKEY, 8)] * n, 3)
+    ob.reset()
+    assert_outputs_equal(out, ob.rollout(16), what="after the refused calls")
+    env.close()
