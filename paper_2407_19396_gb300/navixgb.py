@@ -260,8 +260,10 @@ def nx_set_policy(h, w1, b1, w2, b2, w3, b3, shift1, shift2, epsilon=0, envs_per
     arrs = [np.ascontiguousarray(w1, np.int8), np.ascontiguousarray(b1, np.int32), np.ascontiguousarray(w2, np.int8),
             np.ascontiguousarray(b2, np.int32), np.ascontiguousarray(w3, np.int8), np.ascontiguousarray(b3, np.int32)]
     A = arrs[0].shape[0]
-    assert arrs[0].shape == (A, 64, 49) and arrs[2].shape == (A, 64, 64) and arrs[4].shape == (A, 7, 64)
-    assert arrs[1].shape == (A, 64) and arrs[3].shape == (A, 64) and arrs[5].shape == (A, 7)
+    if not (arrs[0].shape == (A, 64, 49) and arrs[2].shape == (A, 64, 64) and arrs[4].shape == (A, 7, 64) and
+            arrs[1].shape == (A, 64) and arrs[3].shape == (A, 64) and arrs[5].shape == (A, 7)):
+        raise ValueError("policy weights: w1 [A, 64, 49], b1 [A, 64], w2 [A, 64, 64], b2 [A, 64], w3 [A, 7, 64], "
+                         "b3 [A, 7]")
     p = nx_policy(A, int(envs_per_agent), *[a.ctypes.data for a in arrs], int(shift1), int(shift2), int(epsilon))
     return check(lib().nx_set_policy(h, ctypes.byref(p)), h)
 
@@ -340,7 +342,8 @@ def nx_destroy(h):
 # --- snapshot parsing (format documented in navixgb.h) -----------------------
 
 def parse_state(data: bytes) -> dict:
-    assert data[:4] == b"NXST"
+    if data[:4] != b"NXST":
+        raise ValueError("not a navixgb snapshot")
     n = int.from_bytes(data[8:12], "little")
     gstep = int.from_bytes(data[12:16], "little")
     pool = int.from_bytes(data[16:24], "little")
@@ -351,7 +354,8 @@ def parse_state(data: bytes) -> dict:
     for i in range(n):
         a = ag[i]
         size = int(a[25])
-        assert int(a[28:32].view(np.uint32)[0]) == off & 0xFFFFFFFF, "snapshot grid offsets out of order"
+        if int(a[28:32].view(np.uint32)[0]) != off & 0xFFFFFFFF:
+            raise ValueError("snapshot grid offsets out of order")
         hw = size * size
         nb = int(a[7])
         envs.append({
@@ -413,7 +417,8 @@ class Env:
                 from . import inputs
                 atlas = inputs.atlas()
             self._atlas = np.ascontiguousarray(atlas, np.uint8).reshape(-1)
-            assert self._atlas.size == ATLAS_BYTES
+            if self._atlas.size != ATLAS_BYTES:
+                raise ValueError(f"the atlas holds {ATLAS_BYTES} bytes, got {self._atlas.size}")
             o.atlas = self._atlas.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
         self._cbs = None
         if torch_allocator:
@@ -502,7 +507,9 @@ class Env:
         out = out or self.alloc_out()
         ptr = None
         if actions is not None:
-            assert actions.dtype == self.torch.int8 and actions.is_cuda and actions.numel() == self.n
+            if not (actions.dtype == self.torch.int8 and actions.is_cuda and actions.numel() == self.n and
+                    actions.is_contiguous()):
+                raise ValueError(f"actions: a contiguous int8 device tensor of {self.n} entries")
             ptr = actions.data_ptr()
         nx_step(self.h, ptr, self.out_struct(out))
         return out
@@ -516,7 +523,9 @@ class Env:
         out = out or self.alloc_out(depth)
         ptr, mode = None, (NX_ACT_POLICY if policy else NX_ACT_RANDOM)
         if actions is not None:
-            assert actions.dtype == self.torch.int8 and actions.is_cuda and actions.shape == (n_steps, self.n)
+            if not (actions.dtype == self.torch.int8 and actions.is_cuda and tuple(actions.shape) == (n_steps, self.n)
+                    and actions.is_contiguous()):
+                raise ValueError(f"actions: a contiguous int8 device tensor [{n_steps}, {self.n}]")
             ptr, mode = actions.data_ptr(), NX_ACT_BUFFER
         fn = nx_rollout_per_family if per_family else nx_rollout
         fn(self.h, n_steps, mode, ptr, self.out_struct(out, depth))
@@ -548,12 +557,12 @@ class Env:
             else:
                 setattr(s, k, a.data_ptr())
             depth = min(depth, int(a.shape[0]))
-            assert int(a.shape[1]) == n, f"{k}: second dimension must be n_envs"
         s.depth = depth
         ptr, mode = None, NX_ACT_RANDOM
         if actions is not None:
             a = actions if isinstance(actions, np.ndarray) else actions.numpy()
-            assert a.dtype == np.int8 and a.shape == (n_steps, n) and a.flags["C_CONTIGUOUS"]
+            if not (a.dtype == np.int8 and a.shape == (n_steps, n) and a.flags["C_CONTIGUOUS"]):
+                raise ValueError(f"actions: a C-contiguous int8 host array [{n_steps}, {n}]")
             ptr, mode = a.ctypes.data, NX_ACT_BUFFER
         nx_rollout_host(self.h, n_steps, mode, ptr, s)
         return out
