@@ -407,3 +407,112 @@ def test_full_rgb_view_assembles_the_atlas_tiles_of_the_full_symbolic_view(atlas
                         assert agent == 2 and s == f[2]
                     else:
                         assert vis == 1 and agent == 0 and (e, c, s) == f
+
+
+def _rule_state(s):
+    """An oracle state dict as the independent rule model's tuple state."""
+    n = s["height"] * s["width"]
+    cells = tuple(zip(s["ent"][:n], s["col"][:n], s["st"][:n]))
+    carry = (s["carry_ent"], s["carry_col"]) if s["carry_ent"] else None
+    return (s["x"], s["y"], s["dir"], carry, cells)
+
+
+LOCKSTEP = [(O.EMPTY, 6, 0), (O.DOORKEY, 5, 0), (O.DOORKEY, 8, 0), (O.FOURROOMS, 9, 0), (O.LAVAGAP, 6, 0),
+            (O.EMPTY_RANDOM, 7, 0), (O.LAVA_CROSSING, 9, 2), (O.SIMPLE_CROSSING, 9, 2), (O.GOTODOOR, 6, 0),
+            (O.GOTODOOR, 8, 0), (O.DISTSHIFT, 8, 1), (O.KEYCORRIDOR, 7, 0), (O.KEYCORRIDOR, 10, 1)]
+
+
+@pytest.mark.parametrize("family,size,variant", LOCKSTEP)
+def test_every_step_matches_the_independent_rule_model(family, size, variant):
+    """Random play (every action, out-of-range ones included) of every family
+    without balls, step by step: the oracle's next agent pose, carried object
+    and grid equal the independent rule model's successor for the action
+    taken (no successor: nothing changes), termination happens exactly on its
+    goal / lava events, the reward is 1.0 on a goal and 0 otherwise, and
+    truncation exactly when t reaches max_steps."""
+    n, T = 12, 500
+    b = O.Batch([family] * n, [size] * n, seed=100 + family, variants=[variant] * n)
+    b.reset()
+    acts = np.random.default_rng(200 + family).integers(0, 8, size=(T, n)).astype(np.int8)
+    prev = [b.state(i) for i in range(n)]
+    events = {"goal": 0, "lava": 0, "write": 0}
+    for t in range(T):
+        o = b.step(acts[t])
+        cur = [b.state(i) for i in range(n)]
+        for i in range(n):
+            p, s = prev[i], cur[i]
+            if p["done"]:
+                continue  # the autoreset step (pinned elsewhere)
+            a = int(acts[t, i])
+            mission = p["mission"] if family == O.GOTODOOR else None
+            before = _rule_state(p)
+            want, ev = before, None
+            for act, nxt, e in M.successors(before, p["width"], p["height"], mission=mission):
+                if act == a:
+                    want, ev = nxt, e
+                    break
+            assert _rule_state(s) == want, (family, t, i, a)
+            assert o["terminated"][i] == (1 if ev else 0), (family, t, i, a, ev)
+            assert o["reward"][i] == (1.0 if ev == "goal" else 0.0), (family, t, i, a, ev)
+            assert o["truncated"][i] == (1 if s["t"] >= s["max_steps"] else 0)
+            if ev:
+                events[ev] += 1
+            if want[4] != before[4]:
+                events["write"] += 1
+        prev = cur
+    # the play reached the rules that change the grid (pickup, drop, toggle)
+    # wherever the layout has an object to change
+    if family in (O.DOORKEY, O.KEYCORRIDOR, O.GOTODOOR):
+        assert events["write"] > 0, events
+
+
+def _env_rule_state(e):
+    ent, col, st = e.grid()
+    cells = tuple(zip(ent.reshape(-1).tolist(), col.reshape(-1).tolist(), st.reshape(-1).tolist()))
+    carry = (e.s.carry_ent, e.s.carry_col) if e.s.carry_ent else None
+    return (e.s.ax, e.s.ay, e.s.dir, carry, cells)
+
+
+@pytest.mark.parametrize("family", [O.DOORKEY, O.GOTODOOR])
+def test_random_states_match_the_independent_rule_model(family):
+    """Hand-built random states no generator makes -- keys, balls and doors
+    of every colour and state, goals, lava and floor scattered over a 6x6
+    grid, the agent carrying nothing, a key or a ball of any colour -- and
+    every action from each: the oracle's next state, termination and reward
+    equal the independent rule model's (a key of another colour leaves a
+    locked door shut; a full hand picks up nothing; done only completes
+    GoToDoor at a door of the mission's colour)."""
+    rng = np.random.default_rng(300 + family)
+    S = 6
+    kinds = [(1, 0, 0), (1, 0, 0), (1, 0, 0), (3, 0, 0), (2, 5, 0), (8, 1, 0), (9, 0, 0)]
+    seen = set()
+    for trial in range(400):
+        e = O.Env(family, S, seed=trial)
+        e.reset()
+        for y in range(1, S - 1):
+            for x in range(1, S - 1):
+                r = rng.random()
+                if r < 0.15:
+                    e.set_cell(x, y, 4, int(rng.integers(0, 6)), int(rng.integers(0, 3)))   # door
+                elif r < 0.25:
+                    e.set_cell(x, y, 5, int(rng.integers(0, 6)), 0)                         # key
+                elif r < 0.35:
+                    e.set_cell(x, y, 6, int(rng.integers(0, 6)), 0)                         # ball
+                else:
+                    e.set_cell(x, y, *kinds[int(rng.integers(0, len(kinds)))])
+        ax, ay = int(rng.integers(1, S - 1)), int(rng.integers(1, S - 1))
+        e.set_cell(ax, ay, 1, 0, 0)
+        carry = [(0, 0), (5, int(rng.integers(0, 6))), (6, int(rng.integers(0, 6)))][int(rng.integers(0, 3))]
+        e.set_agent(ax, ay, int(rng.integers(0, 4)), *carry)
+        start = _env_rule_state(e)
+        mission = e.s.mission if family == O.GOTODOOR else None
+        succ = {a: (s, ev) for a, s, ev in M.successors(start, S, S, mission=mission)}
+        for a in range(8):
+            c = _clone(e)
+            r, term, trunc = c.step(a)
+            want, ev = succ.get(a, (start, None))
+            assert _env_rule_state(c) == want, (family, trial, a)
+            assert term == (1 if ev else 0) and r == (1.0 if ev == "goal" else 0.0), (family, trial, a, ev)
+            if want != start or ev:
+                seen.add(a)  # the action changed something (done: ended GoToDoor's episode)
+    assert seen >= ({0, 1, 2, 3, 4, 5, 6} if family == O.GOTODOOR else {0, 1, 2, 3, 4, 5}), seen

@@ -1,9 +1,12 @@
-"""The draw-to-placement pins catch the plausible misreadings (CPU only).
+"""The pins catch plausible mistakes planted in the oracle (CPU only).
 
 Each case copies the oracle's C source, plants one mistake, builds the copy
-and runs tests/test_oracle_draw_pins.py against it in a child process
-(``NAVIX_ORACLE_SO``); the pins must fail.  The unmodified copy must pass, so
-a failure is the planted mistake's and not the mechanism's.
+and runs a pin file against it in a child process (``NAVIX_ORACLE_SO``); the
+pins must fail.  The draw-to-placement misreadings go against
+tests/test_oracle_draw_pins.py, the rule mistakes against the step-by-step
+comparisons with the independent rule model in tests/test_oracle_model.py.
+The unmodified copy must pass each, so a failure is the planted mistake's and
+not the mechanism's.
 """
 import os
 import subprocess
@@ -65,4 +68,65 @@ def test_unmodified_copy_passes_the_pins(tmp_path):
 def test_pins_catch_the_planted_mistake(tmp_path, name):
     r = _run_pins(_build(tmp_path, MUTANTS[name]))
     assert r.returncode != 0, f"the pins did not catch {name}"
+    assert "failed" in r.stdout, r.stdout[-2000:]
+
+
+# Plausible mistakes in the intervention rules (Table 3, Appendix A), each of
+# which the step-by-step comparison with the independent rule model must catch.
+RULE_MUTANTS = {
+    # a locked door opened by a key of any colour
+    "unlock_any_colour": [(
+        "if (e->carry_ent == ORC_KEY && e->carry_col == fcol) orc_set_cell(e, fx, fy, ORC_DOOR, fcol, ORC_OPEN);",
+        "if (e->carry_ent == ORC_KEY) orc_set_cell(e, fx, fy, ORC_DOOR, fcol, ORC_OPEN);")],
+    # an open door toggled stays open
+    "open_door_does_not_close": [(
+        "                    orc_set_cell(e, fx, fy, ORC_DOOR, fcol, ORC_CLOSED);",
+        "                    orc_set_cell(e, fx, fy, ORC_DOOR, fcol, ORC_OPEN);")],
+    # the carried object dropped onto any walkable cell, not only an empty one
+    "drop_onto_walkable": [(
+        "if (e->carry_ent != 0 && is_empty_cell(e, fx, fy)) {",
+        "if (e->carry_ent != 0 && walkable(fent, fst) && fent != ORC_GOAL && fent != ORC_LAVA) {")],
+    # pickup with a full hand swaps nothing but picks again
+    "pickup_with_full_hand": [(
+        "if (e->carry_ent == 0 && (fent == ORC_KEY || fent == ORC_BALL)) {",
+        "if (fent == ORC_KEY || fent == ORC_BALL) {")],
+    # GoToDoor's done at a door of any colour
+    "done_at_any_door": [(
+        "if (e->family == ORC_GOTODOOR && fent == ORC_DOOR && fcol == e->mission) goal = 1;",
+        "if (e->family == ORC_GOTODOOR && fent == ORC_DOOR) goal = 1;")],
+    # a closed (unlocked) door walked through like an open one
+    "walk_through_closed_door": [(
+        "    if (ent == ORC_DOOR && st == ORC_OPEN) return 1;",
+        "    if (ent == ORC_DOOR && st != ORC_LOCKED) return 1;")],
+    # the picked-up object left in its cell
+    "pickup_leaves_the_object": [(
+        "                set_empty(e, fx, fy);\n",
+        "")],
+    # stepping onto lava not ending the episode
+    "lava_not_terminal": [(
+        "                if (fent == ORC_LAVA) lava = 1;\n",
+        "")],
+    # turning the wrong way for left
+    "left_turns_right": [(
+        "            e->dir = (e->dir + 3) % 4;\n        } else if (action == ORC_RIGHT) {",
+        "            e->dir = (e->dir + 1) % 4;\n        } else if (action == ORC_RIGHT) {")],
+}
+
+
+def _run_rule_pin(so):
+    env = dict(os.environ, NAVIX_ORACLE_SO=so)
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_model.py"), "-k", "independent_rule_model"],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmodified_copy_passes_the_rule_pin(tmp_path):
+    r = _run_rule_pin(_build(tmp_path, []))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(RULE_MUTANTS))
+def test_rule_pin_catches_the_planted_mistake(tmp_path, name):
+    r = _run_rule_pin(_build(tmp_path, RULE_MUTANTS[name]))
+    assert r.returncode != 0, f"the rule pin did not catch {name}"
     assert "failed" in r.stdout, r.stdout[-2000:]
