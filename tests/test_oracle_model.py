@@ -516,3 +516,37 @@ def test_random_states_match_the_independent_rule_model(family):
             if want != start or ev:
                 seen.add(a)  # the action changed something (done: ended GoToDoor's episode)
     assert seen >= ({0, 1, 2, 3, 4, 5, 6} if family == O.GOTODOOR else {0, 1, 2, 3, 4, 5}), seen
+
+
+def test_random_grids_view_matches_independent_window_model():
+    """Dense random grids no generator makes -- walls, doors of every state
+    (open ones see-through), keys, balls, goals, lava and floor in random
+    places, 5x5 to 12x12 -- and random poses, including poses on the border
+    looking out of the grid: the oracle's view equals the independent
+    window-and-rotate model's, so the occlusion is pinned on many more
+    opaque patterns than the layouts produce."""
+    rng = np.random.default_rng(400)
+    cells = [(1, 0, 0), (1, 0, 0), (1, 0, 0), (2, 5, 0), (3, 0, 0), (8, 1, 0), (9, 0, 0)]
+    n = 0
+    for trial in range(300):
+        S = int(rng.integers(5, 13))
+        e = O.Env(O.DOORKEY, S, seed=trial)
+        e.reset()
+        for y in range(S):
+            for x in range(S):
+                r = rng.random()
+                if r < 0.12:
+                    e.set_cell(x, y, 4, int(rng.integers(0, 6)), int(rng.integers(0, 3)))
+                elif r < 0.2:
+                    e.set_cell(x, y, int(rng.choice([5, 6])), int(rng.integers(0, 6)), 0)
+                else:
+                    e.set_cell(x, y, *cells[int(rng.integers(0, len(cells)))])
+        ent, col, st = e.grid()
+        for _ in range(12):
+            x, y, d = int(rng.integers(0, S)), int(rng.integers(0, S)), int(rng.integers(0, 4))
+            carry = [None, (5, int(rng.integers(0, 6))), (6, int(rng.integers(0, 6)))][int(rng.integers(0, 3))]
+            e.set_agent(x, y, d, *(carry or (0, 0)))
+            np.testing.assert_array_equal(e.obs(), M.observe(ent, col, st, x, y, d, carry),
+                                          err_msg=f"trial {trial} S {S} pose {(x, y, d, carry)}")
+            n += 1
+    assert n == 3600

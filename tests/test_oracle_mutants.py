@@ -4,7 +4,9 @@ Each case copies the oracle's C source, plants one mistake, builds the copy
 and runs a pin file against it in a child process (``NAVIX_ORACLE_SO``); the
 pins must fail.  The draw-to-placement misreadings go against
 tests/test_oracle_draw_pins.py, the rule mistakes against the step-by-step
-comparisons with the independent rule model in tests/test_oracle_model.py.
+comparisons with the independent rule model and the view mistakes against
+the independent window-and-rotate view model (both in
+tests/test_oracle_model.py).
 The unmodified copy must pass each, so a failure is the planted mistake's and
 not the mechanism's.
 """
@@ -129,4 +131,45 @@ def test_unmodified_copy_passes_the_rule_pin(tmp_path):
 def test_rule_pin_catches_the_planted_mistake(tmp_path, name):
     r = _run_rule_pin(_build(tmp_path, RULE_MUTANTS[name]))
     assert r.returncode != 0, f"the rule pin did not catch {name}"
+    assert "failed" in r.stdout, r.stdout[-2000:]
+
+
+# Plausible mistakes in the view and its occlusion (Table 4), each of which the
+# comparisons with the independent window-and-rotate view model must catch.
+VIEW_MUTANTS = {
+    # closed doors seen through like open ones
+    "closed_doors_transparent": [(
+        "    if (ent == ORC_DOOR && st != ORC_OPEN) return 0;",
+        "    if (ent == ORC_DOOR && st == ORC_LOCKED) return 0;")],
+    # light not spreading diagonally ahead to the right
+    "no_diagonal_right": [(
+        "                vis[j - 1][i + 1] = 1;\n",
+        "")],
+    # the rightward sweep only (cells left of a blocked one never lit)
+    "no_leftward_sweep": [(
+        "            vis[j][i - 1] = 1;\n",
+        "")],
+    # the right-hand direction taken as the left-hand one (a mirrored view)
+    "mirrored_view": [(
+        "    int F = e->dir, Rt = (e->dir + 1) % 4;",
+        "    int F = e->dir, Rt = (e->dir + 3) % 4;")],
+}
+
+
+def _run_view_pin(so):
+    env = dict(os.environ, NAVIX_ORACLE_SO=so)
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_model.py"), "-k", "window_model"],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmodified_copy_passes_the_view_pins(tmp_path):
+    r = _run_view_pin(_build(tmp_path, []))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(VIEW_MUTANTS))
+def test_view_pins_catch_the_planted_mistake(tmp_path, name):
+    r = _run_view_pin(_build(tmp_path, VIEW_MUTANTS[name]))
+    assert r.returncode != 0, f"the view pins did not catch {name}"
     assert "failed" in r.stdout, r.stdout[-2000:]
