@@ -308,3 +308,143 @@ def move_balls(g, balls, agent_xy, seed, env, episode, t):
         g[ny_, nx_] = BLUE_BALL
         balls[b] = (nx_, ny_)
     return balls, trace
+
+
+# ---------------------------------------------------------------------------
+# The other layout generators (L4, L6-L10), restated the same way.  Each
+# consumes the layout draws k = 0, 1, 2, ... of its episode in the order its
+# reading states, through a small stream object.
+LAVA = (9, 0, 0)
+GREY_WALL = WALL
+
+
+class _Draws:
+    """The layout draws of one episode, handed out in order."""
+
+    def __init__(self, seed, env, episode):
+        self.seed, self.env, self.episode, self.k = seed, env, episode, 0
+        self.words = []
+
+    def below(self, n):
+        w = draw(self.seed, self.env, self.episode, 0, LAYOUT, self.k)
+        self.k += 1
+        self.words.append(w)
+        return bounded(w, n)
+
+
+def lavagap_start(S, seed, env, episode):
+    """L4: a lava column at 2 + k(S - 4) with one gap at row 1 + k(S - 2)."""
+    r = _Draws(seed, env, episode)
+    g = walled_grid(S)
+    g[S - 2, S - 2] = GOAL
+    xl = 2 + r.below(S - 4)
+    gap = 1 + r.below(S - 2)
+    for y in range(1, S - 1):
+        if y != gap:
+            g[y, xl] = LAVA
+    return g, (1, 1, 0)
+
+
+def empty_random_start(S, seed, env, episode):
+    """L6: Empty-S with the agent on the k-th free interior cell, a drawn direction."""
+    r = _Draws(seed, env, episode)
+    g = walled_grid(S)
+    g[S - 2, S - 2] = GOAL
+    cells = free_cells(g, 1, S - 2, 1, S - 2)
+    ax, ay = cells[r.below(len(cells))]
+    return g, (ax, ay, r.below(4))
+
+
+def gotodoor_start(S, seed, env, episode):
+    """L8: closed doors at drawn places on the top, bottom, left and right
+    walls; colours from the first four of a partial shuffle of the six; the
+    mission one of the four; the agent on a free interior cell."""
+    r = _Draws(seed, env, episode)
+    g = walled_grid(S)
+    spots = [(1 + r.below(S - 2), 0), (1 + r.below(S - 2), S - 1), (0, 1 + r.below(S - 2)),
+             (S - 1, 1 + r.below(S - 2))]
+    palette = list(range(6))
+    for i in range(4):
+        j = i + r.below(6 - i)
+        palette[i], palette[j] = palette[j], palette[i]
+    for (x, y), c in zip(spots, palette[:4]):
+        g[y, x] = (4, c, 1)
+    mission = palette[r.below(4)]
+    cells = free_cells(g, 1, S - 2, 1, S - 2)
+    ax, ay = cells[r.below(len(cells))]
+    return g, (ax, ay, r.below(4)), mission
+
+
+def crossing_start(S, n_rivers, obstacle, seed, env, episode):
+    """L7: n_rivers of the candidate rivers (rows 2, 4, .., S-3, then columns
+    2, 4, .., S-3) by a partial shuffle, filled with the obstacle; the
+    crossing order (east per column river, south per row river) shuffled from
+    the last position down; walking it from the top-left room opens one cell
+    of each river within the current room's span."""
+    r = _Draws(seed, env, episode)
+    g = walled_grid(S)
+    cand = [("row", y) for y in range(2, S - 2, 2)] + [("col", x) for x in range(2, S - 2, 2)]
+    for i in range(n_rivers):
+        j = i + r.below(len(cand) - i)
+        cand[i], cand[j] = cand[j], cand[i]
+    rows = sorted(p for kind, p in cand[:n_rivers] if kind == "row")
+    cols = sorted(p for kind, p in cand[:n_rivers] if kind == "col")
+    for y in rows:
+        g[y, 1:S - 1] = obstacle
+    for x in cols:
+        g[1:S - 1, x] = obstacle
+    order = ["east"] * len(cols) + ["south"] * len(rows)
+    for i in range(len(order) - 1, 0, -1):
+        j = r.below(i + 1)
+        order[i], order[j] = order[j], order[i]
+    xs, ys = [0] + cols + [S - 1], [0] + rows + [S - 1]
+    room_x = room_y = 0
+    for move in order:
+        if move == "east":
+            room_x += 1
+            g[ys[room_y] + 1 + r.below(ys[room_y + 1] - ys[room_y] - 1), xs[room_x]] = EMPTY
+        else:
+            room_y += 1
+            g[ys[room_y], xs[room_x] + 1 + r.below(xs[room_x + 1] - xs[room_x] - 1)] = EMPTY
+    g[S - 2, S - 2] = GOAL
+    return g, (1, 1, 0)
+
+
+def keycorridor_start(S, variant, seed, env, episode):
+    """L10: a 3 x R block of rooms of side s (S = 3(s-1) + 1, R = variant + 1)
+    whose middle column is an open corridor; a door per side room (rows, then
+    colours, drawn left rooms first); the goal's side and room row, the key's
+    room row; goal and key on free cells of their rooms (the key in a room on
+    the other side, of the locked door's colour); the agent in the corridor."""
+    r = _Draws(seed, env, episode)
+    s, R = (S - 1) // 3 + 1, variant + 1
+    H = (s - 1) * R + 1
+    left, right = s - 1, 2 * (s - 1)
+    g = walled_grid(S)
+    g[H - 1:, :] = WALL
+    g[:, left] = WALL
+    g[:, right] = WALL
+    for y in range(0, H, s - 1):  # the walls between rooms, open in the corridor
+        g[y, :left + 1] = WALL
+        g[y, right:] = WALL
+    door_rows = [[j * (s - 1) + 1 + r.below(s - 2) for j in range(R)] for _ in range(2)]
+    door_cols = [[r.below(6) for _ in range(R)] for _ in range(2)]
+    gside, grow, krow = r.below(2), r.below(R), r.below(R)
+    for side, x in ((0, left), (1, right)):
+        for j in range(R):
+            g[door_rows[side][j], x] = (4, door_cols[side][j], 2 if (side, j) == (gside, grow) else 1)
+
+    def room(side, row):
+        x0 = 1 if side == 0 else right + 1
+        y0 = row * (s - 1) + 1
+        return free_cells(g, x0, x0 + s - 3, y0, y0 + s - 3)
+
+    cells = room(gside, grow)
+    gx, gy = cells[r.below(len(cells))]
+    g[gy, gx] = GOAL
+    cells = room(1 - gside, krow)
+    kx, ky = cells[r.below(len(cells))]
+    g[ky, kx] = (5, door_cols[gside][grow], 0)
+    cells = free_cells(g, left + 1, right - 1, 1, H - 2)
+    ax, ay = cells[r.below(len(cells))]
+    return g, (ax, ay, r.below(4))

@@ -14,12 +14,16 @@ are pinned here two ways:
   restatement in tests/indep_model.py (its Philox checked against the
   published known-answer vectors) and must be reproduced by the oracle;
 * sweeps comparing the oracle's start states and ball moves with the same
-  independent restatement over many seeds, envs and sizes.
+  independent restatement over many seeds, envs and sizes -- the start states
+  of every family with draws (DoorKey, FourRooms, Dynamic-Obstacles, LavaGap,
+  Empty-Random, GoToDoor with its mission, both crossings at every river
+  count, KeyCorridor at every room side and row count).
 
 tests/test_oracle_mutants.py plants the plausible mistakes (free cells scanned
 column-major, balls moved on a snapshot of the grid, neighbours scanned column
-first, the action counter's episode word) in copies of the oracle and checks
-that this file catches each.
+first, the action counter's episode word, a short draw range, a full instead
+of a partial shuffle, an off-by-one shuffle, two draws taken in the other
+order) in copies of the oracle and checks that this file catches each.
 """
 import os
 
@@ -212,3 +216,62 @@ def test_random_actions_equal_the_independent_counter():
             for g in (0, 1, 2, 127, 128, 5000):
                 assert e.random_action(g) == M.random_action(seed, env, g, 7)
                 assert d.random_action(g) == M.random_action(seed, env, g, 3)
+
+
+def _start_of(family, S, variant, seed, env, ep):
+    e = O.Env(family, S, seed=seed, env_index=env, variant=variant)
+    e.reset(ep)
+    ent, col, st = e.grid()
+    return np.stack([ent, col, st], -1), (e.s.ax, e.s.ay, e.s.dir), e.s.mission
+
+
+@pytest.mark.parametrize("S", [5, 7, 11, 19])
+def test_lavagap_and_empty_random_starts_equal_the_independent_generators(S):
+    for seed in (0, 4, 2**33 + 1):
+        for env in range(5):
+            for ep in (0, 7):
+                g, agent = M.lavagap_start(S, seed, env, ep)
+                got, a, _ = _start_of(O.LAVAGAP, S, 0, seed, env, ep)
+                np.testing.assert_array_equal(got, g)
+                assert a == agent
+                g, agent = M.empty_random_start(S, seed, env, ep)
+                got, a, _ = _start_of(O.EMPTY_RANDOM, S, 0, seed, env, ep)
+                np.testing.assert_array_equal(got, g)
+                assert a == agent
+
+
+@pytest.mark.parametrize("S", [5, 6, 9, 14, 19])
+def test_gotodoor_starts_and_missions_equal_the_independent_generator(S):
+    for seed in (0, 8):
+        for env in range(6):
+            for ep in (0, 3):
+                g, agent, mission = M.gotodoor_start(S, seed, env, ep)
+                got, a, m = _start_of(O.GOTODOOR, S, 0, seed, env, ep)
+                np.testing.assert_array_equal(got, g)
+                assert a == agent and m == mission
+
+
+@pytest.mark.parametrize("S", [5, 7, 9, 11, 13, 19])
+def test_crossing_starts_equal_the_independent_generator(S):
+    """Every river count the size allows, lava and wall rivers."""
+    for n_rivers in range(O.max_variant(O.LAVA_CROSSING, S) + 1):
+        for family, obstacle in ((O.LAVA_CROSSING, M.LAVA), (O.SIMPLE_CROSSING, M.WALL)):
+            for seed in (0, 6):
+                for env in range(3):
+                    g, agent = M.crossing_start(S, n_rivers, obstacle, seed, env, 1)
+                    got, a, _ = _start_of(family, S, n_rivers, seed, env, 1)
+                    np.testing.assert_array_equal(got, g, err_msg=f"{family} S {S} N {n_rivers}")
+                    assert a == agent
+
+
+@pytest.mark.parametrize("S", [7, 10, 13, 16, 19])
+def test_keycorridor_starts_equal_the_independent_generator(S):
+    """Room sides 3 to 7, one to three rows of rooms."""
+    for variant in range(3):
+        for seed in (0, 9):
+            for env in range(4):
+                for ep in (0, 2):
+                    g, agent = M.keycorridor_start(S, variant, seed, env, ep)
+                    got, a, _ = _start_of(O.KEYCORRIDOR, S, variant, seed, env, ep)
+                    np.testing.assert_array_equal(got, g, err_msg=f"S {S} R {variant + 1}")
+                    assert a == agent

@@ -34,6 +34,26 @@ MUTANTS = {
     "ball_candidates_dx_outer": [(
         "        for (int dy = -1; dy <= 1; dy++)\n            for (int dx = -1; dx <= 1; dx++) {",
         "        for (int dx = -1; dx <= 1; dx++)\n            for (int dy = -1; dy <= 1; dy++) {")],
+    # LavaGap's gap drawn over one row fewer (the last interior row never open)
+    "lavagap_gap_range": [(
+        "int gap = 1 + (int)orc_bounded(layout_draw(e, 1), (uint32_t)(S - 2));",
+        "int gap = 1 + (int)orc_bounded(layout_draw(e, 1), (uint32_t)(S - 3));")],
+    # GoToDoor's colours by a full shuffle step (any of the six each time)
+    "gotodoor_colour_shuffle": [(
+        "int j = i + (int)orc_bounded(layout_draw(e, k++), (uint32_t)(6 - i));",
+        "int j = (int)orc_bounded(layout_draw(e, k++), 6u);")],
+    # the crossing order shuffled with one position too few at each step
+    "crossing_order_shuffle": [(
+        "int j = (int)orc_bounded(layout_draw(e, k++), (uint32_t)(i + 1));",
+        "int j = (int)orc_bounded(layout_draw(e, k++), (uint32_t)i);")],
+    # KeyCorridor's key and goal cells drawn in the other order
+    "keycorridor_key_before_goal": [
+        ("    int gx0 = gside == 0 ? 1 : xr + 1, gy0 = grow * (s - 1) + 1;",
+         "    uint32_t kg = k++;\n    int gx0 = gside == 0 ? 1 : xr + 1, gy0 = grow * (s - 1) + 1;"),
+        ("    kth_free(e, (int)orc_bounded(layout_draw(e, k++), (uint32_t)n), gx0, gx0 + s - 3, gy0, gy0 + s - 3, -1, -1, &gx, &gy);",
+         "    kth_free(e, (int)orc_bounded(layout_draw(e, k++), (uint32_t)n), gx0, gx0 + s - 3, gy0, gy0 + s - 3, -1, -1, &gx, &gy);\n    (void)kg;"),
+        ("    kth_free(e, (int)orc_bounded(layout_draw(e, k++), (uint32_t)n), kx0, kx0 + s - 3, ky0, ky0 + s - 3, -1, -1, &kx, &ky);",
+         "    kth_free(e, (int)orc_bounded(layout_draw(e, kg), (uint32_t)n), kx0, kx0 + s - 3, ky0, ky0 + s - 3, -1, -1, &kx, &ky);")],
     # reading R1's random-action counter with the episode word 0 instead of all ones
     "action_counter_episode_word": [(
         "orc_draw(e->seed, e->env_index, 0xFFFFFFFFu, gstep, PURPOSE_ACTION, 0)",
