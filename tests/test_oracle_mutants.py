@@ -6,7 +6,9 @@ pins must fail.  The draw-to-placement misreadings go against
 tests/test_oracle_draw_pins.py, the rule mistakes against the step-by-step
 comparisons with the independent rule model and the view mistakes against
 the independent window-and-rotate view model (both in
-tests/test_oracle_model.py).
+tests/test_oracle_model.py), and the time, reward and cost mistakes against
+the hand-worked pins and the cost pins (tests/test_oracle_pins.py,
+tests/test_oracle_families.py).
 The unmodified copy must pass each, so a failure is the planted mistake's and
 not the mechanism's.
 """
@@ -192,4 +194,50 @@ def test_unmodified_copy_passes_the_view_pins(tmp_path):
 def test_view_pins_catch_the_planted_mistake(tmp_path, name):
     r = _run_view_pin(_build(tmp_path, VIEW_MUTANTS[name]))
     assert r.returncode != 0, f"the view pins did not catch {name}"
+    assert "failed" in r.stdout, r.stdout[-2000:]
+
+
+# Plausible mistakes in time, reward and termination (Tables 5, 6, Eq. 1),
+# each of which the hand-worked pins and the cost pins must catch.
+REWARD_MUTANTS = {
+    # Eq. 1 evaluated with the step count before the step
+    "eq1_step_before_increment": [(
+        "r = e->reward_mode == ORC_REWARD_MINIGRID ? minigrid_goal_reward(e->t, e->max_steps) : 1.0f;",
+        "r = e->reward_mode == ORC_REWARD_MINIGRID ? minigrid_goal_reward(e->t - 1, e->max_steps) : 1.0f;")],
+    # truncation one step late
+    "truncation_one_late": [(
+        "    int trunc = e->t >= e->max_steps;",
+        "    int trunc = e->t > e->max_steps;")],
+    # action_cost charged for done too
+    "action_cost_on_done": [(
+        "    if (action >= 0 && action < ORC_DONE) r = r - e->action_cost;",
+        "    if (action >= 0 && action <= ORC_DONE) r = r - e->action_cost;")],
+    # time_cost not charged
+    "no_time_cost": [(
+        "    r = r - e->time_cost;\n",
+        "")],
+    # lava ends the episode with the goal reward
+    "lava_pays_the_goal_reward": [(
+        "        r = e->lava_reward;",
+        "        r = 1.0f;")],
+}
+
+
+def _run_reward_pins(so):
+    env = dict(os.environ, NAVIX_ORACLE_SO=so)
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                           os.path.join(ROOT, "tests", "test_oracle_families.py")],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmodified_copy_passes_the_reward_pins(tmp_path):
+    r = _run_reward_pins(_build(tmp_path, []))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(REWARD_MUTANTS))
+def test_reward_pins_catch_the_planted_mistake(tmp_path, name):
+    r = _run_reward_pins(_build(tmp_path, REWARD_MUTANTS[name]))
+    assert r.returncode != 0, f"the reward pins did not catch {name}"
     assert "failed" in r.stdout, r.stdout[-2000:]
