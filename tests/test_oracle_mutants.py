@@ -8,7 +8,9 @@ comparisons with the independent rule model and the view mistakes against
 the independent window-and-rotate view model (both in
 tests/test_oracle_model.py), and the time, reward and cost mistakes against
 the hand-worked pins and the cost pins (tests/test_oracle_pins.py,
-tests/test_oracle_families.py).
+tests/test_oracle_families.py), and the observation and policy mistakes
+against the RGB, full-view and policy pins (tests/test_oracle_model.py,
+tests/test_oracle_policy.py).
 The unmodified copy must pass each, so a failure is the planted mistake's and
 not the mechanism's.
 """
@@ -240,4 +242,51 @@ def test_unmodified_copy_passes_the_reward_pins(tmp_path):
 def test_reward_pins_catch_the_planted_mistake(tmp_path, name):
     r = _run_reward_pins(_build(tmp_path, REWARD_MUTANTS[name]))
     assert r.returncode != 0, f"the reward pins did not catch {name}"
+    assert "failed" in r.stdout, r.stdout[-2000:]
+
+
+# Plausible mistakes in the other observations (Table 4) and in the fused
+# policy (reading P1), each caught by the model and policy pins.
+OBS_POLICY_MUTANTS = {
+    # the agent's own tile in the egocentric RGB view not marked
+    "rgb_agent_tile_unmarked": [(
+        "    if (agent_cell) t += 198;\n",
+        "")],
+    # the fully observable view showing what lies under the agent
+    "full_view_hides_no_agent": [(
+        "            } else if (x == e->ax && y == e->ay) {\n                o[0] = ORC_AGENT;",
+        "            } else if (0) {\n                o[0] = ORC_AGENT;")],
+    # the policy's hidden units not clamped from above
+    "policy_no_upper_clamp": [(
+        "static int64_t clamp255(int64_t v) { return v < 0 ? 0 : (v > 255 ? 255 : v); }",
+        "static int64_t clamp255(int64_t v) { return v < 0 ? 0 : v; }")],
+    # the policy's ties going to the last largest logit
+    "policy_last_max": [(
+        "        if (a == 0 || z > best_z) {",
+        "        if (a == 0 || z >= best_z) {")],
+    # the second hidden layer requantised with the first layer's shift
+    "policy_layer2_shift1": [(
+        "        h2[j] = clamp255(floor_shift(acc, p->shift2));",
+        "        h2[j] = clamp255(floor_shift(acc, p->shift1));")],
+}
+
+
+def _run_obs_policy_pins(so):
+    env = dict(os.environ, NAVIX_ORACLE_SO=so)
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_model.py"),
+                           os.path.join(ROOT, "tests", "test_oracle_policy.py"), "-k",
+                           "rgb or full or policy or greedy or shift or tie or wall or hand or exploration or agent"],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmodified_copy_passes_the_observation_and_policy_pins(tmp_path):
+    r = _run_obs_policy_pins(_build(tmp_path, []))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(OBS_POLICY_MUTANTS))
+def test_observation_and_policy_pins_catch_the_planted_mistake(tmp_path, name):
+    r = _run_obs_policy_pins(_build(tmp_path, OBS_POLICY_MUTANTS[name]))
+    assert r.returncode != 0, f"the observation and policy pins did not catch {name}"
     assert "failed" in r.stdout, r.stdout[-2000:]
