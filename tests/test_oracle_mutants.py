@@ -218,6 +218,14 @@ REWARD_MUTANTS = {
     "no_time_cost": [(
         "    r = r - e->time_cost;\n",
         "")],
+    # Dynamic-Obstacles with all seven actions instead of three
+    "dynobs_seven_actions": [(
+        "    int n_act = e->family == ORC_DYNOBS ? 3 : 7;\n    if (action < 0 || action > ORC_DONE) {",
+        "    int n_act = 7;\n    if (action < 0 || action > ORC_DONE) {")],
+    # a collision with a ball not penalised
+    "collision_not_penalised": [(
+        "        r = -1.0f;\n        term = 1;",
+        "        r = 0.0f;\n        term = 1;")],
     # lava ends the episode with the goal reward
     "lava_pays_the_goal_reward": [(
         "        r = e->lava_reward;",
