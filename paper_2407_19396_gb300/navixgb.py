@@ -35,7 +35,8 @@ ATLAS_BYTES = 401 * 3072
 AGENT_BYTES = 32
 FAMILIES = {"empty": NX_EMPTY, "doorkey": NX_DOORKEY, "fourrooms": NX_FOURROOMS, "lavagap": NX_LAVAGAP,
             "dynobs": NX_DYNOBS, "empty_random": NX_EMPTY_RANDOM, "lava_crossing": NX_LAVA_CROSSING,
-            "simple_crossing": NX_SIMPLE_CROSSING}
+            "simple_crossing": NX_SIMPLE_CROSSING, "gotodoor": NX_GOTODOOR, "distshift": NX_DISTSHIFT,
+            "keycorridor": NX_KEYCORRIDOR}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)

@@ -99,3 +99,57 @@ def test_binding_refuses_output_buffers_the_library_would_overrun():
     for key, a, slots, dev in bad:
         with pytest.raises(ValueError):
             check_out_buffer(key, a, n, side, slots, device=dev)
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has, compiled from include/navixgb.h
+    by the host C compiler, the size and field offsets of its ctypes twin: a
+    field added, dropped, retyped or moved on one side only would hand the
+    library records it misreads."""
+    import ctypes
+
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    classes = [nx.nx_desc, nx.nx_options, nx.nx_out, nx.nx_policy, nx.nx_info, nx.nx_request, nx.nx_result,
+               nx.nx_server_stats]
+    lines = ["#include <stdio.h>", '#include "navixgb.h"', "int main(void) {"]
+    for c in classes:
+        name = c.__name__
+        lines.append(f'printf("{name} - %zu\\n", sizeof({name}));')
+        for field in c._fields_:
+            lines.append(f'printf("{name} {field[0]} %zu\\n", offsetof({name}, {field[0]}));')
+    lines.append("return 0; }")
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    seen = 0
+    for line in out.splitlines():
+        name, field, value = line.split()
+        c = getattr(nx, name)
+        got = ctypes.sizeof(c) if field == "-" else getattr(c, field).offset
+        assert got == int(value), f"{name}.{field}: ctypes {got}, C {value}"
+        seen += 1
+    assert seen == sum(1 + len(c._fields_) for c in classes)
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Every NX_ constant of the binding, and its byte sizes, have the value
+    the header gives them (families, status codes, flags, modes, sizes)."""
+    from paper_2407_19396_gb300 import navixgb as nx
+
+    pairs = {k: k for k in dir(nx) if k.startswith("NX_") and isinstance(getattr(nx, k), int)}
+    pairs.update(OBS_SYM_BYTES="NX_OBS_SYM_BYTES", OBS_RGB_BYTES="NX_OBS_RGB_BYTES", ATLAS_BYTES="NX_ATLAS_BYTES",
+                 AGENT_BYTES="NX_AGENT_BYTES")
+    lines = ["#include <stdio.h>", '#include "navixgb.h"', "int main(void) {"]
+    lines += [f'printf("{py} %lld\\n", (long long)({c}));' for py, c in pairs.items()]
+    lines.append("return 0; }")
+    src, exe = tmp_path / "consts.c", tmp_path / "consts"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    values = dict(line.split() for line in out.splitlines())
+    assert len(values) == len(pairs) >= 35
+    for py, v in values.items():
+        assert getattr(nx, py) == int(v), f"{py}: binding {getattr(nx, py)}, header {v}"
+    assert sorted(nx.FAMILIES.values()) == list(range(nx.NX_N_FAMILIES))
