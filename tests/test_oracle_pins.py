@@ -212,3 +212,32 @@ def test_lava_reward_default_zero_and_option():
         e.set_cell(2, 1, 9, 0, 0)
         r, te, tr = e.step(2)
         assert (r, te, tr) == (want, 1, 0)
+
+
+def test_oracle_ctypes_structs_match_its_header(tmp_path):
+    """The oracle's ctypes mirrors of orc_env and orc_policy have the size and
+    field offsets of the C structs (compiled from oracle/navix_oracle.h by the
+    host C compiler), so no test reads a field at the wrong place."""
+    import ctypes
+    import subprocess
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    classes = [(O.OrcEnv, "orc_env"), (O.OrcPolicy, "orc_policy")]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "navix_oracle.h"', "int main(void) {"]
+    for c, cname in classes:
+        lines.append(f'printf("{c.__name__} - %zu\\n", sizeof({cname}));')
+        for field in c._fields_:
+            lines.append(f'printf("{c.__name__} {field[0]} %zu\\n", offsetof({cname}, {field[0]}));')
+    lines.append("return 0; }")
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "oracle"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    n = 0
+    for line in out.splitlines():
+        name, field, value = line.split()
+        c = getattr(O, name)
+        got = ctypes.sizeof(c) if field == "-" else getattr(c, field).offset
+        assert got == int(value), f"{name}.{field}: ctypes {got}, C {value}"
+        n += 1
+    assert n == sum(1 + len(c._fields_) for c, _ in classes)
