@@ -9,7 +9,8 @@ the random actions (reading R1, purpose 3) are this project's readings.  They
 are pinned here two ways:
 
 * hand-worked examples under tests/golden/ (DoorKey-8x8, FourRooms-19x19, one
-  Dynamic-Obstacles-5x5 step, the first random actions of one env), whose
+  Dynamic-Obstacles-5x5 step, the first random actions of one env, a
+  GoToDoor-6x6 start with its colour shuffle and mission), whose
   every draw word and derived placement is re-derived from the independent
   restatement in tests/indep_model.py (its Philox checked against the
   published known-answer vectors) and must be reproduced by the oracle;
@@ -275,3 +276,24 @@ def test_keycorridor_starts_equal_the_independent_generator(S):
                     got, a, _ = _start_of(O.KEYCORRIDOR, S, variant, seed, env, ep)
                     np.testing.assert_array_equal(got, g, err_msg=f"S {S} R {variant + 1}")
                     assert a == agent
+
+
+def test_golden_gotodoor6x6_seed0_env0_start():
+    """The hand-worked GoToDoor start: door places, the colour shuffle, the
+    mission and the agent, each draw re-derived independently, and the
+    oracle's start state equal to them."""
+    draws, exp = _golden("gotodoor6x6_seed0_env0_start.txt")
+    _check_draw_lines(draws, lambda kind, k: M.draw(0, 0, 0, 0, M.LAYOUT, k))
+    assert [k for _, k, *_ in draws] == list(range(11))  # every draw of the layout, in order
+    exp = dict(exp)
+    g, agent, mission = M.gotodoor_start(6, 0, 0, 0)
+    e = O.Env(O.GOTODOOR, 6, seed=0, env_index=0)
+    ent, col, st = e.grid()
+    for side in ("door_top", "door_bottom", "door_left", "door_right"):
+        x, y, c = exp[side]
+        assert tuple(int(v) for v in g[y, x]) == (4, c, 1)
+        assert (ent[y, x], col[y, x], st[y, x]) == (4, c, 1)
+    assert [mission] == exp["mission"] == [e.s.mission]
+    assert list(agent) == exp["agent"] == [e.s.ax, e.s.ay, e.s.dir]
+    assert int((ent == 4).sum()) == 4  # no other door
+    np.testing.assert_array_equal(np.stack([ent, col, st], -1), g)
