@@ -10,7 +10,8 @@ are pinned here two ways:
 
 * hand-worked examples under tests/golden/ (DoorKey-8x8, FourRooms-19x19, one
   Dynamic-Obstacles-5x5 step, the first random actions of one env, a
-  GoToDoor-6x6 start with its colour shuffle and mission), whose
+  GoToDoor-6x6 start with its colour shuffle and mission, a LavaCrossing-9x9
+  start with its river shuffle, crossing order and openings), whose
   every draw word and derived placement is re-derived from the independent
   restatement in tests/indep_model.py (its Philox checked against the
   published known-answer vectors) and must be reproduced by the oracle;
@@ -296,4 +297,32 @@ def test_golden_gotodoor6x6_seed0_env0_start():
     assert [mission] == exp["mission"] == [e.s.mission]
     assert list(agent) == exp["agent"] == [e.s.ax, e.s.ay, e.s.dir]
     assert int((ent == 4).sum()) == 4  # no other door
+    np.testing.assert_array_equal(np.stack([ent, col, st], -1), g)
+
+
+def test_golden_lavacrossing9x9_n3_seed6_env0_start():
+    """The hand-worked crossing start: the river shuffle, the crossing order,
+    the openings and the drawn grid, each draw re-derived independently, and
+    the oracle's start state equal to them."""
+    draws, exp = _golden("lavacrossing9x9_n3_seed6_env0_start.txt")
+    _check_draw_lines(draws, lambda kind, k: M.draw(6, 0, 0, 0, M.LAYOUT, k))
+    assert [k for _, k, *_ in draws] == list(range(8))
+    exp = dict(exp)
+    art = [line[1:].strip() for line in open(os.path.join(GOLDEN, "lavacrossing9x9_n3_seed6_env0_start.txt"))
+           if line.startswith("#   ") and set(line[1:].strip()) <= set("#~.G")]
+    assert len(art) == 9
+    code = {"#": 2, "~": 9, ".": 1, "G": 8}
+    g, agent = M.crossing_start(9, 3, M.LAVA, 6, 0, 0)
+    e = O.Env(O.LAVA_CROSSING, 9, seed=6, env_index=0, variant=3)
+    ent, col, st = e.grid()
+    for y in range(9):
+        assert [code[ch] for ch in art[y]] == ent[y].tolist() == g[y, :, 0].tolist(), y
+    openings = exp["openings"]
+    for x, y in zip(openings[0::2], openings[1::2]):
+        assert ent[y, x] == 1
+    assert all((ent[y, 1:8] != 1).sum() == 6 for y in exp["lava_rows"])  # one opening per row river
+    assert all((ent[1:8, x] != 1).sum() == 6 for x in exp["lava_cols"])
+    assert list(agent) == exp["agent"] == [e.s.ax, e.s.ay, e.s.dir]
+    gx, gy = exp["goal"]
+    assert ent[gy, gx] == 8
     np.testing.assert_array_equal(np.stack([ent, col, st], -1), g)
