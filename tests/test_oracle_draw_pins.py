@@ -11,7 +11,8 @@ are pinned here two ways:
 * hand-worked examples under tests/golden/ (DoorKey-8x8, FourRooms-19x19, one
   Dynamic-Obstacles-5x5 step, the first random actions of one env, a
   GoToDoor-6x6 start with its colour shuffle and mission, a LavaCrossing-9x9
-  start with its river shuffle, crossing order and openings), whose
+  start with its river shuffle, crossing order and openings, a KeyCorridor
+  S4R2 start with its doors, locked door, goal, key and agent), whose
   every draw word and derived placement is re-derived from the independent
   restatement in tests/indep_model.py (its Philox checked against the
   published known-answer vectors) and must be reproduced by the oracle;
@@ -325,4 +326,35 @@ def test_golden_lavacrossing9x9_n3_seed6_env0_start():
     assert list(agent) == exp["agent"] == [e.s.ax, e.s.ay, e.s.dir]
     gx, gy = exp["goal"]
     assert ent[gy, gx] == 8
+    np.testing.assert_array_equal(np.stack([ent, col, st], -1), g)
+
+
+def test_golden_keycorridor_s4r2_seed3_env0_start():
+    """The hand-worked KeyCorridor start: door rows and colours, the locked
+    door, the goal, the key of the locked door's colour on the other side and
+    the agent in the corridor, each draw re-derived independently, and the
+    oracle's start state equal to them."""
+    name = "keycorridor_s4r2_seed3_env0_start.txt"
+    draws, exp = _golden(name)
+    _check_draw_lines(draws, lambda kind, k: M.draw(3, 0, 0, 0, M.LAYOUT, k))
+    assert [k for _, k, *_ in draws] == list(range(15))
+    doors = [v for key, v in exp if key == "door"]
+    exp = dict(exp)
+    art = [line[1:].strip() for line in open(os.path.join(GOLDEN, name))
+           if line.startswith("#   ") and set(line[1:].strip()) <= set("#.DKG")]
+    assert len(art) == 10
+    code = {"#": 2, ".": 1, "D": 4, "K": 5, "G": 8}
+    g, agent = M.keycorridor_start(10, 1, 3, 0, 0)
+    e = O.Env(O.KEYCORRIDOR, 10, seed=3, env_index=0, variant=1)
+    ent, col, st = e.grid()
+    for y in range(10):
+        assert [code[ch] for ch in art[y]] == ent[y].tolist() == g[y, :, 0].tolist(), y
+    for x, y, c, state in doors:
+        assert (ent[y, x], col[y, x], st[y, x]) == (4, c, state)
+    assert sum(state == 2 for *_, state in doors) == 1
+    kx, ky, kc = exp["key"]
+    assert (ent[ky, kx], col[ky, kx]) == (5, kc)
+    gx, gy = exp["goal"]
+    assert ent[gy, gx] == 8
+    assert list(agent) == exp["agent"] == [e.s.ax, e.s.ay, e.s.dir]
     np.testing.assert_array_equal(np.stack([ent, col, st], -1), g)
