@@ -358,3 +358,20 @@ def test_golden_keycorridor_s4r2_seed3_env0_start():
     assert ent[gy, gx] == 8
     assert list(agent) == exp["agent"] == [e.s.ax, e.s.ay, e.s.dir]
     np.testing.assert_array_equal(np.stack([ent, col, st], -1), g)
+
+
+@pytest.mark.parametrize("S", [5, 6, 9, 14, 19])
+def test_dynobs_starts_for_every_ball_count_equal_the_independent_generator(S):
+    """Zero to four balls, each on the k-th free interior cell left by the
+    balls before it (never the agent's cell)."""
+    for n_balls in range(5):
+        for seed in (0, 12):
+            for env in range(4):
+                for ep in (0, 6):
+                    g, balls, _ = M.dynobs_start(S, seed, env, ep, n_balls=n_balls)
+                    e = O.Env(O.DYNOBS, S, seed=seed, env_index=env, n_balls=n_balls)
+                    e.reset(ep)
+                    ent, col, st = e.grid()
+                    np.testing.assert_array_equal(np.stack([ent, col, st], -1), g)
+                    assert [(e.s.ball_x[b], e.s.ball_y[b]) for b in range(n_balls)] == balls
+                    assert (e.s.ax, e.s.ay, e.s.dir, e.s.n_balls) == (1, 1, 0, n_balls)
